@@ -1,0 +1,174 @@
+"""CPU oracle for the running max-min filter (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The CUDA library never links or loads
+it, and it imports nothing from the library.
+
+The arithmetic lives in ``mmf_oracle.c`` (plain C, compiled by :func:`build`):
+
+* :func:`bf1d` -- the definition of Section 1 (max/min over every window
+  ``[j, j+w)``), i.e. the "naive" row of Table 1.
+* :func:`bf1d_at` -- the same at chosen window starts (for full-size checks).
+* :func:`wedge` -- Algorithm 1 of Section 4 with a comparison counter
+  (Section 1 cost model) and the wedge-size bound of Proposition 4.
+* :func:`envelope` -- centred, end-clipped windows of radius ``r`` (the
+  envelope use cited in Section 1).
+* :func:`bf2d` / :func:`bf2d_at` -- literal ``wy x wx`` rectangle max/min,
+  valid mode (the 2D filter of Section 1, written without separation).
+* :func:`stream_reference` -- the served outputs of a chunked stream are, by
+  the definition, the whole-array filter over the concatenated chunks.
+
+Python here does marshalling only; no arithmetic of the method is in it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mmf_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_SUFFIX = {np.dtype(np.float32): "f32", np.dtype(np.float64): "f64",
+           np.dtype(np.int16): "i16", np.dtype(np.uint8): "u8"}
+
+_I64 = ctypes.c_int64
+_VP = ctypes.c_void_p
+
+
+class WedgeStats(ctypes.Structure):
+    _fields_ = [("ncmp", _I64), ("max_size", _I64), ("stale_fronts", _I64),
+                ("steps", _I64)]
+
+
+def build(force: bool = False) -> str:
+    """Compile ``mmf_oracle.c`` into ``liboracle.so`` (gcc, no CUDA)."""
+    if force or not os.path.exists(_LIB_PATH) or \
+            os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC",
+                               "-Wall", "-Wextra", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            for suf in _SUFFIX.values():
+                getattr(lib, f"oracle_bf1d_{suf}").argtypes = [_VP, _I64, _I64, _VP, _VP]
+                getattr(lib, f"oracle_bf1d_at_{suf}").argtypes = [_VP, _I64, _I64, _VP, _I64, _VP, _VP]
+                getattr(lib, f"oracle_wedge_{suf}").argtypes = [_VP, _I64, _I64, _VP, _VP,
+                                                               ctypes.POINTER(WedgeStats)]
+                getattr(lib, f"oracle_envelope_{suf}").argtypes = [_VP, _I64, _I64, _VP, _VP]
+                getattr(lib, f"oracle_bf2d_{suf}").argtypes = [_VP, _I64, _I64, _I64, _I64, _I64, _VP, _VP]
+                getattr(lib, f"oracle_bf2d_at_{suf}").argtypes = [_VP, _I64, _I64, _I64, _I64, _I64,
+                                                                 _VP, _VP, _I64, _VP, _VP]
+                for name in ("bf1d", "bf1d_at", "wedge", "envelope", "bf2d", "bf2d_at"):
+                    getattr(lib, f"oracle_{name}_{suf}").restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _fn(name: str, dtype) -> object:
+    dt = np.dtype(dtype)
+    if dt not in _SUFFIX:
+        raise TypeError(f"oracle: unsupported dtype {dt}")
+    return getattr(_load(), f"oracle_{name}_{_SUFFIX[dt]}")
+
+
+def _ptr(x: np.ndarray | None):
+    return None if x is None else x.ctypes.data_as(_VP)
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != 0:
+        raise ValueError(f"oracle {what} failed with status {rc}")
+
+
+def n_out(n: int, w: int) -> int:
+    """Number of windows [j, j+w) inside a length-n array (0 if w > n)."""
+    return max(0, n - w + 1)
+
+
+def bf1d(a: np.ndarray, w: int):
+    """Max and min of every window [j, j+w), j = 0..n-w (Section 1)."""
+    a = np.ascontiguousarray(a)
+    m = n_out(a.size, w)
+    mx = np.empty(m, a.dtype)
+    mn = np.empty(m, a.dtype)
+    _check(_fn("bf1d", a.dtype)(_ptr(a), a.size, w, _ptr(mx), _ptr(mn)), "bf1d")
+    return mx, mn
+
+
+def bf1d_at(a: np.ndarray, w: int, starts: np.ndarray):
+    """Max and min of the windows [s, s+w) for each s in ``starts``."""
+    a = np.ascontiguousarray(a)
+    starts = np.ascontiguousarray(starts, dtype=np.int64)
+    mx = np.empty(starts.size, a.dtype)
+    mn = np.empty(starts.size, a.dtype)
+    _check(_fn("bf1d_at", a.dtype)(_ptr(a), a.size, w, _ptr(starts), starts.size,
+                                   _ptr(mx), _ptr(mn)), "bf1d_at")
+    return mx, mn
+
+
+def wedge(a: np.ndarray, w: int):
+    """Algorithm 1: returns (max, min, stats) with the comparison count."""
+    a = np.ascontiguousarray(a)
+    m = n_out(a.size, w)
+    mx = np.empty(m, a.dtype)
+    mn = np.empty(m, a.dtype)
+    st = WedgeStats()
+    _check(_fn("wedge", a.dtype)(_ptr(a), a.size, w, _ptr(mx), _ptr(mn),
+                                 ctypes.byref(st)), "wedge")
+    return mx, mn, {"ncmp": st.ncmp, "max_size": st.max_size,
+                    "stale_fronts": st.stale_fronts, "steps": st.steps}
+
+
+def envelope(a: np.ndarray, r: int):
+    """Centred end-clipped envelope of radius r: (upper, lower), n each."""
+    a = np.ascontiguousarray(a)
+    up = np.empty(a.size, a.dtype)
+    lo = np.empty(a.size, a.dtype)
+    _check(_fn("envelope", a.dtype)(_ptr(a), a.size, r, _ptr(up), _ptr(lo)), "envelope")
+    return up, lo
+
+
+def bf2d(img: np.ndarray, wy: int, wx: int):
+    """Valid-mode rectangle max/min of a 2D array (rows x cols)."""
+    img = np.ascontiguousarray(img)
+    H, W = img.shape
+    Ho, Wo = max(0, H - wy + 1), max(0, W - wx + 1)
+    mx = np.empty((Ho, Wo), img.dtype)
+    mn = np.empty((Ho, Wo), img.dtype)
+    _check(_fn("bf2d", img.dtype)(_ptr(img), H, W, W, wy, wx, _ptr(mx), _ptr(mn)), "bf2d")
+    return mx, mn
+
+
+def bf2d_at(img: np.ndarray, wy: int, wx: int, ys: np.ndarray, xs: np.ndarray):
+    """Rectangle max/min whose top-left corners are (ys[t], xs[t])."""
+    img = np.ascontiguousarray(img)
+    H, W = img.shape
+    ys = np.ascontiguousarray(ys, dtype=np.int64)
+    xs = np.ascontiguousarray(xs, dtype=np.int64)
+    mx = np.empty(ys.size, img.dtype)
+    mn = np.empty(ys.size, img.dtype)
+    _check(_fn("bf2d_at", img.dtype)(_ptr(img), H, W, W, wy, wx, _ptr(ys), _ptr(xs),
+                                     ys.size, _ptr(mx), _ptr(mn)), "bf2d_at")
+    return mx, mn
+
+
+def stream_reference(chunks, w: int):
+    """Outputs a zero-latency stream must have emitted after all ``chunks``:
+    the filter of the concatenation (each output depends only on its
+    window, Section 1)."""
+    return bf1d(np.concatenate([np.asarray(c) for c in chunks]), w)
