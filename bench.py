@@ -1,0 +1,345 @@
+"""Benchmark of the running max-min filter on the long-stream workload.
+
+Workload (one "step"): an n = 2^30 fp32 stream for each of three seeded
+distributions (i.i.d. uniform[0,1), N(0,1) random walk, piecewise monotone
+runs of mean length 1000), filtered at each window w in {3, 31, 1001, 65537}
+-- 12 calls of mmf_filter1d, 12 * 2^30 input elements.  Inputs (4 GiB each)
+are larger than L2, so no flush is needed between timed iterations.
+
+Prints ONE JSON line.  Metric: filtered Gelem/s (input elements per second,
+whole job over all ranks).  ``--impl reference`` times the CPU oracle (the
+paper's Algorithm 1, single thread) on a bounded sample of the same workload.
+
+Multi-GPU (torchrun): each rank filters its own independent streams (weak
+scaling, no data-path collective); the barrier and the max-over-ranks timing
+are the only communication.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "filtered Gelem/s"
+N = 1 << 30
+WINDOWS = (3, 31, 1001, 65537)
+DISTS = ("uniform", "random_walk", "piecewise_monotone")
+SEEDS = {"uniform": 21, "random_walk": 22, "piecewise_monotone": 23}
+WORKLOAD = "long 1D stream: n=2^30 fp32 x {uniform, random walk, piecewise monotone} x w in {3,31,1001,65537}"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _traffic():
+    """dram bytes per launch from a committed ncu summary (None if absent)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self._t.join(timeout=2)
+        sm, smax, reasons = [], 0.0, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    """CPU oracle (Algorithm 1, one thread) on a bounded sample per step."""
+    import oracle
+    import synth
+    ws, rank, _ = _dist_env()
+    if rank != 0:
+        return 0
+    oracle.build()
+    sample = args.ref_sample
+    data = {d: synth.by_name(d, sample, SEEDS[d], np.float32) for d in DISTS}
+    for _ in range(args.warmup):
+        oracle.wedge(data["random_walk"][: sample // 8], 101)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for d in DISTS:
+            for w in WINDOWS:
+                oracle.wedge(data[d], w)
+    dt = time.perf_counter() - t0
+    elems = args.steps * len(DISTS) * len(WINDOWS) * sample
+    value = elems / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gelem/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N, "windows": list(WINDOWS), "dists": list(DISTS),
+                   "reference_sample_elements": sample},
+        "cpu_baseline": {"value": value, "unit": "Gelem/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {sample} elements of each distribution (numpy-seeded), "
+                                   f"Algorithm 1 wedge per window, {args.steps} steps"},
+        "e2e": {"value": value, "unit": "Gelem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(sample: int):
+    import oracle
+    import synth
+    oracle.build()
+    a = {d: synth.by_name(d, sample, SEEDS[d], np.float32) for d in DISTS}
+    t0 = time.perf_counter()
+    for d in DISTS:
+        for w in WINDOWS:
+            oracle.wedge(a[d], w)
+    dt = time.perf_counter() - t0
+    return {"value": len(DISTS) * len(WINDOWS) * sample / dt / 1e9, "unit": "Gelem/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{sample} elements per distribution x 3 distributions x 4 windows, "
+                      f"Algorithm 1 wedge (single thread), {dt:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=N)
+    ap.add_argument("--ref-sample", type=int, default=1 << 24)
+    ap.add_argument("--cpu-sample", type=int, default=1 << 24)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_cs_0610046_gb300 as mmf
+    from paper_cs_0610046_gb300 import build
+    import synth
+
+    ws, rank, local = _dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if rank == 0:
+        build.build()
+    if ws > 1:
+        dist.barrier()
+    mmf.load()
+    stream = torch.cuda.current_stream()
+
+    n = args.n
+    xs = {d: synth.torch_by_name(d, n, SEEDS[d] + 1000 * rank, dev) for d in DISTS}
+    omax = torch.empty(n, dtype=torch.float32, device=dev)
+    omin = torch.empty(n, dtype=torch.float32, device=dev)
+
+    def step(events=None):
+        for d in DISTS:
+            for w in WINDOWS:
+                m = n - w + 1
+                if events is not None:
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                mmf.filter1d(xs[d], w, out_max=omax[:m], out_min=omin[:m], stream=stream)
+                if events is not None:
+                    e1.record(stream)
+                    events.append((w, e0, e1))
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+
+    sampler = ClockSampler(dev.index if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    sampler.start()
+    time.sleep(0.3)
+    launch_events = []
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        step(launch_events)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    if ws > 1:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+
+    per_step_elems = len(DISTS) * len(WINDOWS) * n
+    total_elems = per_step_elems * args.steps * ws
+    value = total_elems / (elapsed_ms * 1e-3) / 1e9
+
+    # Roofline of the (single) kernel: algorithmic bytes n*4 + 2*(n-w+1)*4.
+    peak, peak_kind = _peaks()
+    per_w = {}
+    tot_bytes = 0.0
+    tot_ms = 0.0
+    for w, e0, e1 in launch_events:
+        ms = e0.elapsed_time(e1)
+        b = 4.0 * n + 8.0 * (n - w + 1)
+        d = per_w.setdefault(w, {"ms": [], "bytes": b})
+        d["ms"].append(ms)
+        tot_bytes += b
+        tot_ms += ms
+    achieved = tot_bytes / (tot_ms * 1e-3) / 1e9
+    traffic = _traffic().get("blockscan_kernel<float>", {}).get("dram_bytes_per_elem")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": peak_kind,
+                "kernel": "mmf::blockscan_kernel<float>",
+                "traffic": (traffic * n) if traffic else None,
+                "algorithmic_bytes_per_launch": tot_bytes / max(1, len(launch_events)),
+                "frac_of_8TBps": achieved / 8000.0}
+    breakdown = {str(w): {"ms": statistics.median(v["ms"]),
+                          "GBps": v["bytes"] / (statistics.median(v["ms"]) * 1e-3) / 1e9,
+                          "Gelem_s": n / (statistics.median(v["ms"]) * 1e-3) / 1e9}
+                 for w, v in per_w.items()}
+
+    # End to end through the public API with host buffers: H2D of each
+    # distribution's stream, 4 filter calls, D2H of every output.
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        hx = {d: torch.empty(n, dtype=torch.float32, pin_memory=True) for d in DISTS}
+        for d in DISTS:
+            hx[d].copy_(xs[d])
+        hmax = torch.empty(n, dtype=torch.float32, pin_memory=True)
+        hmin = torch.empty(n, dtype=torch.float32, pin_memory=True)
+        dx = torch.empty(n, dtype=torch.float32, device=dev)
+
+        def e2e_step():
+            for d in DISTS:
+                dx.copy_(hx[d], non_blocking=True)
+                for w in WINDOWS:
+                    m = n - w + 1
+                    mmf.filter1d(dx, w, out_max=omax[:m], out_min=omin[:m], stream=stream)
+                    hmax[:m].copy_(omax[:m], non_blocking=True)
+                    hmin[:m].copy_(omin[:m], non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        ems = s0.elapsed_time(s1)
+        e2e = {"value": per_step_elems * args.e2e_steps / (ems * 1e-3) / 1e9, "unit": "Gelem/s",
+               "h2d_bytes_per_step": len(DISTS) * n * 4,
+               "d2h_bytes_per_step": sum(2 * 4 * (n - w + 1) for w in WINDOWS) * len(DISTS),
+               "steps": args.e2e_steps}
+        del hx, hmax, hmin, dx
+
+    status = mmf.device_status(reset=True)
+    cpu = None
+    if not args.no_cpu and rank == 0 and ws == 1:
+        cpu = cpu_baseline(args.cpu_sample)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "Gelem/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": elapsed_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "windows": list(WINDOWS), "dists": list(DISTS),
+                       "l2": "inputs of 4 GiB per stream exceed L2 (no flush needed)",
+                       "parallelism": f"{ws} independent streams per distribution (one per GPU)"},
+            "roofline": roofline, "per_window": breakdown, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": len(launch_events), "clocks": clocks, "device_status": status,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

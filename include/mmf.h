@@ -1,0 +1,116 @@
+/*
+ * mmf.h -- C ABI of the GB300 running maximum-minimum filter library.
+ *
+ * The operation (Lemire, "Streaming Maximum-Minimum Filter Using No More than
+ * Three Comparisons per Element", Section 1): for an array a_0..a_{n-1} and a
+ * window width w, output for every window [j, j+w), j = 0..n-w,
+ *     max[j] = max_{i in [j, j+w)} a_i      min[j] = min_{i in [j, j+w)} a_i
+ * (n-w+1 outputs of each; none when w > n).  Every output is one of the input
+ * elements, so results are exact (bit-identical to any correct CPU version)
+ * for inputs without NaN.  NaN inputs give unspecified results; -0.0 and +0.0
+ * compare equal and either may be returned.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* are DEVICE pointers (cudaMalloc / torch CUDA tensors)
+ *     on the current CUDA device; h_* are HOST pointers.  The caller owns all
+ *     of them; the library never frees caller memory.
+ *   - Arrays are contiguous, element type given by mmf_dtype.  Element
+ *     pointers must be aligned to their element size.  16-byte alignment of
+ *     the start of each array gives the fastest path; any element-aligned
+ *     address is accepted.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *     enqueued asynchronously on it; the call returns before it finishes.
+ *   - Errors are returned as mmf_status; no C++ exception crosses the ABI.
+ *     mmf_last_error() gives a thread-local message for the last failure.
+ *     Failures detected on the device (a bounded wait that ran out) are
+ *     recorded in a device status word read by mmf_device_status().
+ *   - Sizes and indices are int64_t.
+ */
+#ifndef MMF_H_
+#define MMF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { MMF_F32 = 0, MMF_F64 = 1, MMF_I16 = 2, MMF_U8 = 3 } mmf_dtype;
+
+/* MMF_VALID: windows [j, j+w), n-w+1 outputs (Section 1).
+ * MMF_CENTERED_CLIPPED: envelope windows [i-r, i+r] clipped to [0, n), n
+ * outputs; the window argument is the radius r >= 0 (the upper/lower
+ * envelopes used for time-warping lower bounds, cited in Section 1). */
+typedef enum { MMF_VALID = 0, MMF_CENTERED_CLIPPED = 1 } mmf_mode;
+
+typedef enum {
+    MMF_OK = 0,
+    MMF_EINVAL = 1,    /* bad argument (null pointer, negative size, ...)   */
+    MMF_ENOMEM = 2,    /* host or device allocation failed / over budget    */
+    MMF_ECUDA = 3,     /* a CUDA runtime call failed                        */
+    MMF_EBUSY = 4,     /* serving: admission refused, retry later           */
+    MMF_ETIMEOUT = 5,  /* a bounded wait ran out                            */
+    MMF_ECLOSED = 6,   /* serving: stream already closed / unknown          */
+    MMF_ENOTIMPL = 7,  /* combination not supported                         */
+    MMF_EDEVICE = 8    /* the device reported an error in its status word   */
+} mmf_status;
+
+/* Kernel choice for the 1D filter.  AUTO consults the dispatch table. */
+typedef enum {
+    MMF_KERNEL_AUTO = 0,
+    MMF_KERNEL_BLOCKSCAN = 1, /* van Herk/Gil-Werman block prefix/suffix scan
+                                 (Section 2 related work; Table 1 row 2)    */
+    MMF_KERNEL_SLIDE = 2,     /* register slide: naive windows of Table 1
+                                 row 1, for small w                         */
+    MMF_KERNEL_WEDGE = 3      /* chunked monotonic wedge, Algorithm 1 of
+                                 Section 4 per chunk with a w-1 halo        */
+} mmf_kernel;
+
+/* Largest window handled (w - 1 < MMF_MAX_WINDOW_TILES * tile; the tile is
+ * 4096 elements for f32/i16/u8 and 2048 for f64). */
+#define MMF_MAX_WINDOW_TILES 1024
+
+/* ---------------------------------------------------------------- 1D ---- */
+
+/* mmf_filter1d -- running max-min filter of one array (Section 1 definition;
+ * MMF_CENTERED_CLIPPED gives the envelope variant).
+ *   d_in    n elements of `dtype` (may be NULL when n == 0)
+ *   n       number of input elements, >= 0
+ *   w_or_r  window width w >= 1 (VALID) or radius r >= 0 (CENTERED_CLIPPED)
+ *   d_max   output, n-w+1 (VALID, 0 if w > n) or n (CENTERED_CLIPPED)
+ *           elements; NULL skips the max side
+ *   d_min   same for the min side; NULL skips it (not both NULL)
+ * Outputs must not overlap the input.  Allocates nothing.
+ * Returns MMF_EINVAL for w < 1, r < 0, n < 0, both outputs NULL, or a NULL
+ * input with n > 0; MMF_ENOTIMPL if w exceeds the window limit above. */
+mmf_status mmf_filter1d(const void *d_in, int64_t n, int64_t w_or_r, mmf_dtype dtype,
+                        mmf_mode mode, void *d_max, void *d_min, void *stream);
+
+/* Same as mmf_filter1d with an explicit kernel choice (for tests and the
+ * autotuner).  MMF_KERNEL_SLIDE requires w <= 32. */
+mmf_status mmf_filter1d_ex(const void *d_in, int64_t n, int64_t w_or_r, mmf_dtype dtype,
+                           mmf_mode mode, void *d_max, void *d_min, void *stream,
+                           mmf_kernel kernel);
+
+/* Number of outputs of one side for (n, w_or_r, mode); -1 if invalid. */
+int64_t mmf_output_length(int64_t n, int64_t w_or_r, mmf_mode mode);
+
+/* --------------------------------------------------------- device status */
+
+/* Reads (and, if reset != 0, clears) the device status word that kernels set
+ * when a bounded wait runs out (bit 0: pipeline wait timeout).  Synchronises
+ * the current device.  Returns MMF_OK and writes the word to *out. */
+mmf_status mmf_device_status(uint32_t *out, int reset);
+
+/* Thread-local, NUL-terminated description of the last failure. */
+const char *mmf_last_error(void);
+
+/* Library version string. */
+const char *mmf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MMF_H_ */

@@ -1,0 +1,144 @@
+"""GB300-native running max-min filter: Python binding of ``libmmf.so``.
+
+This module only marshals arguments for the C ABI declared in
+``include/mmf.h``; every step of the filter runs in the library's CUDA
+kernels.  PyTorch supplies device memory and streams.  There is no CPU
+fallback: if the library is missing or the tensors are not on a CUDA device,
+calls raise.
+
+Build the library with ``python -m paper_cs_0610046_gb300.build`` (or
+``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+__all__ = ["MMFError", "load", "filter1d", "output_length", "device_status", "DTYPES", "KERNELS"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmmf.so")
+
+MMF_OK = 0
+STATUS_NAMES = {0: "MMF_OK", 1: "MMF_EINVAL", 2: "MMF_ENOMEM", 3: "MMF_ECUDA", 4: "MMF_EBUSY",
+                5: "MMF_ETIMEOUT", 6: "MMF_ECLOSED", 7: "MMF_ENOTIMPL", 8: "MMF_EDEVICE"}
+DTYPES = {torch.float32: 0, torch.float64: 1, torch.int16: 2, torch.uint8: 3}
+MODES = {"valid": 0, "envelope": 1, "centered_clipped": 1}
+KERNELS = {"auto": 0, "blockscan": 1, "slide": 2, "wedge": 3}
+
+_I64 = ctypes.c_int64
+_VP = ctypes.c_void_p
+_INT = ctypes.c_int
+
+_lock = threading.Lock()
+_lib = None
+
+
+class MMFError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def load() -> ctypes.CDLL:
+    """Load ``libmmf.so`` (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"CUDA library {LIB_PATH} is missing; build it with "
+                                   "`python -m paper_cs_0610046_gb300.build`")
+            lib = ctypes.CDLL(LIB_PATH)
+            lib.mmf_last_error.restype = ctypes.c_char_p
+            lib.mmf_version.restype = ctypes.c_char_p
+            lib.mmf_output_length.argtypes = [_I64, _I64, _INT]
+            lib.mmf_output_length.restype = _I64
+            lib.mmf_filter1d.argtypes = [_VP, _I64, _I64, _INT, _INT, _VP, _VP, _VP]
+            lib.mmf_filter1d.restype = _INT
+            lib.mmf_filter1d_ex.argtypes = [_VP, _I64, _I64, _INT, _INT, _VP, _VP, _VP, _INT]
+            lib.mmf_filter1d_ex.restype = _INT
+            lib.mmf_device_status.argtypes = [ctypes.POINTER(ctypes.c_uint32), _INT]
+            lib.mmf_device_status.restype = _INT
+            _declare_more(lib)
+            _lib = lib
+    return _lib
+
+
+def _declare_more(lib) -> None:
+    """Signatures of the entry points added beyond the 1D filter."""
+    for name, args in _EXTRA_SIGNATURES.items():
+        if hasattr(lib, name):
+            f = getattr(lib, name)
+            f.argtypes = args[0]
+            f.restype = args[1]
+
+
+_EXTRA_SIGNATURES: dict = {}
+
+
+def check(status: int) -> None:
+    if status != MMF_OK:
+        raise MMFError(status, load().mmf_last_error().decode(errors="replace"))
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _check_tensor(t: torch.Tensor, name: str) -> None:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype not in DTYPES:
+        raise TypeError(f"{name}: unsupported dtype {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def output_length(n: int, w_or_r: int, mode: str = "valid") -> int:
+    return int(load().mmf_output_length(n, w_or_r, MODES[mode]))
+
+
+def filter1d(x: torch.Tensor, w: int, mode: str = "valid", out_max=None, out_min=None,
+             kernel: str = "auto", stream=None, want_max: bool = True, want_min: bool = True):
+    """Running max and min of every window of ``x`` (1D, CUDA tensor).
+
+    ``mode="valid"``: windows [j, j+w), n-w+1 outputs.  ``mode="envelope"``:
+    ``w`` is the radius r and the windows are [i-r, i+r] clipped to the array,
+    n outputs.  Returns ``(max, min)`` (either may be None if not wanted).
+    """
+    _check_tensor(x, "x")
+    lib = load()
+    x = x.reshape(-1)
+    m = int(lib.mmf_output_length(x.numel(), w, MODES[mode]))
+    if m < 0:
+        raise MMFError(1, f"invalid window {w} for mode {mode}")
+    if want_max and out_max is None:
+        out_max = torch.empty(m, dtype=x.dtype, device=x.device)
+    if want_min and out_min is None:
+        out_min = torch.empty(m, dtype=x.dtype, device=x.device)
+    for o, nm in ((out_max, "out_max"), (out_min, "out_min")):
+        if o is not None:
+            _check_tensor(o, nm)
+            if o.dtype != x.dtype or o.numel() < m:
+                raise ValueError(f"{nm} must hold {m} elements of {x.dtype}")
+    with torch.cuda.device(x.device):
+        check(lib.mmf_filter1d_ex(_ptr(x), x.numel(), w, DTYPES[x.dtype], MODES[mode],
+                                  _ptr(out_max), _ptr(out_min), _VP(_stream_handle(stream)),
+                                  KERNELS[kernel]))
+    return out_max, out_min
+
+
+def device_status(reset: bool = True) -> int:
+    """Device status word (bit 0: a bounded wait ran out); syncs the device."""
+    v = ctypes.c_uint32(0)
+    check(load().mmf_device_status(ctypes.byref(v), 1 if reset else 0))
+    return int(v.value)

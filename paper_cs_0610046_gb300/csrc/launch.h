@@ -1,0 +1,31 @@
+// Internal host-side interface between the C ABI and the per-dtype kernel
+// translation units.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "blockscan.cuh"
+
+namespace mmf {
+
+struct LaunchCtx {
+    int device;
+    int sms;
+    uint32_t *status;  // device status word
+    cudaStream_t stream;
+};
+
+// One series, statically split into per-CTA items (no allocation).
+template <typename T>
+cudaError_t blockscan_1d(const LaunchCtx &ctx, const void *in, const SeriesDesc &sd, void *omax, void *omin);
+
+// Table-driven launch (batched plans): items pulled from an atomic ticket.
+template <typename T>
+cudaError_t blockscan_table(const LaunchCtx &ctx, const void *in, void *omax, void *omin,
+                            const SeriesDesc *d_series, const ItemDesc *d_items, int64_t n_items,
+                            int *d_ticket, int grid);
+
+template <typename T> size_t blockscan_smem_bytes();
+int blockscan_tile(int dtype);
+
+}  // namespace mmf

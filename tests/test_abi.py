@@ -1,0 +1,77 @@
+"""CPU-side checks of the C ABI: the library builds, loads, and exports every
+function that include/*.h declares.  No compute call is made (no GPU here)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b(mmf_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_cs_0610046_gb300 import build
+    build.build()
+    return ctypes.CDLL(build.LIB)
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for required in ("mmf_filter1d", "mmf_filter1d_ex", "mmf_last_error", "mmf_device_status"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, f"declared but not exported: {missing}"
+
+
+def test_host_only_calls(lib):
+    lib.mmf_output_length.restype = ctypes.c_int64
+    lib.mmf_output_length.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int]
+    assert lib.mmf_output_length(10, 3, 0) == 8
+    assert lib.mmf_output_length(10, 11, 0) == 0
+    assert lib.mmf_output_length(10, 0, 0) == -1
+    assert lib.mmf_output_length(10, 4, 1) == 10
+    assert lib.mmf_output_length(-1, 4, 1) == -1
+    lib.mmf_version.restype = ctypes.c_char_p
+    assert b"sm_103a" in lib.mmf_version()
+
+
+def test_argument_errors_need_no_gpu(lib):
+    """Invalid arguments are rejected before any CUDA call."""
+    f = lib.mmf_filter1d
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    lib.mmf_last_error.restype = ctypes.c_char_p
+    assert f(None, 10, 3, 0, 0, None, None, None) == 1          # both outputs NULL
+    assert f(None, 10, 3, 0, 0, 16, None, None) == 1            # NULL input, n > 0
+    assert f(16, 10, 0, 0, 0, 16, None, None) == 1              # w < 1
+    assert f(16, -1, 3, 0, 0, 16, None, None) == 1              # n < 0
+    assert f(16, 10, 3, 9, 0, 16, None, None) == 1              # bad dtype
+    assert f(16, 10, 3, 0, 7, 16, None, None) == 1              # bad mode
+    assert f(18, 10, 3, 0, 0, 16, None, None) == 1              # misaligned f32 pointer
+    assert f(16, 2, 3, 0, 0, 16, 32, None) == 0                 # w > n: nothing to do
+    assert f(16, 10 ** 9, 4096 * 2000, 0, 0, 16, None, None) == 7  # window beyond the limit
+    assert len(lib.mmf_last_error()) > 0
+
+
+def test_product_path_fails_loudly_without_library(tmp_path, monkeypatch):
+    import paper_cs_0610046_gb300 as mmf
+    monkeypatch.setattr(mmf, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(mmf, "_lib", None)
+    with pytest.raises(RuntimeError):
+        mmf.load()

@@ -1,0 +1,179 @@
+"""GPU parity of the 1D filter (mmf_filter1d through the C ABI) against the
+CPU oracle: bit-exact for every dtype, since a max or min returns an input."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+NP2T = {np.float32: torch.float32, np.float64: torch.float64, np.int16: torch.int16, np.uint8: torch.uint8}
+DTYPES = [np.float32, np.float64, np.int16, np.uint8]
+
+
+@pytest.fixture(scope="module")
+def mmf():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_cs_0610046_gb300 as m
+    return m
+
+
+def _gpu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _expect(a, w):
+    # The definition for modest sizes, Algorithm 1 (pinned to it) for large w.
+    if a.size * w <= 4e8:
+        return oracle.bf1d(a, w)
+    mx, mn, _ = oracle.wedge(a, w)
+    return mx, mn
+
+
+def _check(mmf, a, w, mode="valid", kernel="auto"):
+    x = _gpu(a)
+    mx, mn = mmf.filter1d(x, w, mode=mode, kernel=kernel)
+    torch.cuda.synchronize()
+    if mode == "valid":
+        emx, emn = _expect(a, w)
+    else:
+        emx, emn = oracle.envelope(a, w)
+    gm, gn = mx.cpu().numpy(), mn.cpu().numpy()
+    assert gm.shape == emx.shape
+    if not np.array_equal(gm, emx):
+        bad = np.nonzero(gm != emx)[0]
+        raise AssertionError(f"max mismatch w={w} n={a.size}: {bad.size} bad, first {bad[:8]}")
+    if not np.array_equal(gn, emn):
+        bad = np.nonzero(gn != emn)[0]
+        raise AssertionError(f"min mismatch w={w} n={a.size}: {bad.size} bad, first {bad[:8]}")
+
+
+WINDOWS = [1, 2, 3, 4, 5, 8, 9, 16, 17, 31, 32, 33, 101, 511, 512, 513, 1001, 1024, 1025,
+           2047, 2048, 2049, 4095, 4096, 4097, 4098, 8193, 12289]
+
+
+@pytest.mark.parametrize("w", WINDOWS)
+def test_f32_windows_random_walk(mmf, w):
+    a = synth.random_walk(61_237, seed=w, dtype=np.float32)
+    _check(mmf, a, w)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("dist", synth.DISTS)
+@pytest.mark.parametrize("w", [3, 31, 1001, 5000])
+def test_dtypes_distributions(mmf, dtype, dist, w):
+    a = synth.by_name(dist, 40_003, seed=7, dtype=dtype)
+    _check(mmf, a, w)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_edge_sizes(mmf, dtype):
+    for n, w in [(1, 1), (2, 1), (2, 2), (3, 2), (7, 7), (4096, 4096), (4097, 4096), (4097, 2),
+                 (8192, 4097), (8193, 8193), (100, 99), (12_345, 12_345), (5, 3)]:
+        a = synth.uniform(n, seed=n + w, dtype=dtype)
+        _check(mmf, a, w)
+
+
+def test_empty_and_oversized_window(mmf):
+    x = torch.zeros(0, device="cuda")
+    mx, mn = mmf.filter1d(x, 3)
+    assert mx.numel() == 0 and mn.numel() == 0
+    x = torch.arange(10, device="cuda", dtype=torch.float32)
+    mx, mn = mmf.filter1d(x, 11)
+    assert mx.numel() == 0
+
+
+def test_monotone_and_constant(mmf):
+    a = synth.monotone(50_000, 3, np.float32)
+    x = _gpu(a)
+    for w in (3, 1000, 5000):
+        mx, mn = mmf.filter1d(x, w)
+        assert np.array_equal(mx.cpu().numpy(), a[w - 1:])
+        assert np.array_equal(mn.cpu().numpy(), a[: a.size - w + 1])
+    c = torch.full((9999,), 2.5, device="cuda")
+    mx, mn = mmf.filter1d(c, 77)
+    assert bool((mx == 2.5).all()) and bool((mn == 2.5).all())
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("off", [1, 3, 5])
+def test_unaligned_input_and_output(mmf, dtype, off):
+    """Sub-tensor views whose start is not 16-byte aligned."""
+    a = synth.random_walk(30_000, seed=off, dtype=dtype)
+    big = _gpu(a)
+    x = big[off:]
+    w = 257
+    m = x.numel() - w + 1
+    obuf = torch.empty(m + 8, dtype=x.dtype, device="cuda")
+    nbuf = torch.empty(m + 8, dtype=x.dtype, device="cuda")
+    mmf.filter1d(x, w, out_max=obuf[off:off + m], out_min=nbuf[off:off + m])
+    torch.cuda.synchronize()
+    emx, emn = oracle.bf1d(a[off:], w)
+    assert np.array_equal(obuf[off:off + m].cpu().numpy(), emx)
+    assert np.array_equal(nbuf[off:off + m].cpu().numpy(), emn)
+
+
+def test_single_side_outputs(mmf):
+    a = synth.uniform(20_000, 4, np.float32)
+    x = _gpu(a)
+    mx, mn = mmf.filter1d(x, 55, want_min=False)
+    assert mn is None
+    emx, emn = oracle.bf1d(a, 55)
+    assert np.array_equal(mx.cpu().numpy(), emx)
+    mx, mn = mmf.filter1d(x, 55, want_max=False)
+    assert mx is None and np.array_equal(mn.cpu().numpy(), emn)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("r", [0, 1, 51, 700, 5000, 100_000])
+def test_envelope(mmf, dtype, r):
+    a = synth.random_walk(9_001, seed=r, dtype=dtype)
+    _check(mmf, a, r, mode="envelope")
+
+
+def test_envelope_unaligned_short_series(mmf):
+    a = synth.znorm_walks(3, 1024, 33)
+    flat = a.reshape(-1)
+    big = _gpu(flat)
+    for s in range(3):
+        x = big[s * 1024 + 1:(s + 1) * 1024]
+        up, lo = mmf.filter1d(x, 51, mode="envelope")
+        eup, elo = oracle.envelope(flat[s * 1024 + 1:(s + 1) * 1024], 51)
+        assert np.array_equal(up.cpu().numpy(), eup) and np.array_equal(lo.cpu().numpy(), elo)
+
+
+def test_sine_wave_paper_input(mmf):
+    a = synth.sine(1_000_000, np.float64)
+    for w in (10, 1000, 30_000):
+        _check(mmf, a, w)
+
+
+def test_device_status_clean(mmf):
+    assert mmf.device_status(reset=True) == 0
+
+
+@pytest.mark.parametrize("w", [3, 31, 1001, 65537])
+def test_full_size_long_stream_sampled(mmf, w):
+    """n = 2^30 fp32 (the long-stream workload), same launch as the bench:
+    sampled windows against the definition, plus the bracketing property
+    max >= min on every output."""
+    n = 1 << 30
+    x = synth.torch_by_name("random_walk", n, seed=22, device="cuda")
+    mx, mn = mmf.filter1d(x, w)
+    torch.cuda.synchronize()
+    m = n - w + 1
+    assert bool((mx >= mn).all())
+    rng = np.random.default_rng(w)
+    starts = np.concatenate([rng.integers(0, m, size=3000), [0, 1, m - 1, m - 2],
+                             np.arange(0, m, 4096 * 152 * 7)[:400]]).astype(np.int64)
+    a = x.cpu().numpy()
+    emx, emn = oracle.bf1d_at(a, w, starts)
+    idx = torch.from_numpy(starts).cuda()
+    assert np.array_equal(mx[idx].cpu().numpy(), emx)
+    assert np.array_equal(mn[idx].cpu().numpy(), emn)
+    del x, mx, mn
+    torch.cuda.empty_cache()
+    assert mmf.device_status(reset=True) == 0
