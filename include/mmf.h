@@ -67,8 +67,9 @@ typedef enum {
                                  Section 4 per chunk with a w-1 halo        */
 } mmf_kernel;
 
-/* Largest window handled (w - 1 < MMF_MAX_WINDOW_TILES * tile; the tile is
- * 4096 elements for f32/i16/u8 and 2048 for f64). */
+/* Largest window handled: (w - 1) / tile <= MMF_MAX_WINDOW_TILES, where the
+ * tile is 2048 elements for f32, 1024 for f64 and 4096 for i16 and u8 (so w up
+ * to about 2.1 M for f32). */
 #define MMF_MAX_WINDOW_TILES 1024
 
 /* ---------------------------------------------------------------- 1D ---- */
@@ -82,8 +83,10 @@ typedef enum {
  *           elements; NULL skips the max side
  *   d_min   same for the min side; NULL skips it (not both NULL)
  * Outputs must not overlap the input.  Allocates nothing.
- * Returns MMF_EINVAL for w < 1, r < 0, n < 0, both outputs NULL, or a NULL
- * input with n > 0; MMF_ENOTIMPL if w exceeds the window limit above. */
+ * Returns MMF_OK without touching memory when there are no outputs (w > n or
+ * n == 0; pointers may then be NULL).  Otherwise returns MMF_EINVAL for
+ * w < 1, r < 0, n < 0, both outputs NULL, a NULL input, or pointers not
+ * aligned to the element size; MMF_ENOTIMPL if w exceeds the window limit. */
 mmf_status mmf_filter1d(const void *d_in, int64_t n, int64_t w_or_r, mmf_dtype dtype,
                         mmf_mode mode, void *d_max, void *d_min, void *stream);
 

@@ -13,19 +13,21 @@
 //   * s >= T: B = T (blocks are tiles); k lies q or q+1 tiles after j
 //     (s = qT + r), and the tiles between contribute tile aggregates kept in a
 //     small ring in shared memory.
-// With the output index j as the thread's own index, S_B lives in registers,
-// and P_B is read from a 3-tile ring in shared memory at offset s.  Each input
-// element is read from HBM once (for s >= T the J-side tile is re-read about
-// w elements later, normally from L2) and each output written once.
+// The thread that owns output j holds S_B[j] in registers; P_B is written to a
+// 3-tile ring of (max, min) pairs in shared memory and read back at offset s.
+// Each input element is read from HBM once (for s >= T the J-side tile is
+// read again about w elements later, normally from L2) and each output is
+// written once.
 //
-// Work decomposition.  A work item is a contiguous range of output tiles of one
-// series.  A CTA owns an item at a time and streams its input tiles in order:
-// one producer warp issues 1D bulk TMA copies into a ring of stages
-// (mbarrier transaction counts), 8 consumer warps read their 16 contiguous
-// elements (64 bytes for f32) per tile, scan, and store.  Items come from a
-// static round-robin (1D launches: one per CTA) or an atomic ticket (batched
-// plans).  Every wait is bounded; a timeout sets a bit in the device status
-// word and the CTA drains its copies and returns.
+// Work decomposition.  A work item is a contiguous range of output tiles of
+// one series.  A CTA (8 warps, two per SM) owns one item at a time and streams
+// its input tiles in order.  Thread 0 issues 1D bulk TMA copies into a ring of
+// stages (mbarrier transaction counts) right after each CTA barrier, into the
+// stages consumed before it, so it never waits.  Outputs of tile c are formed
+// one iteration later, after the barrier that also serves the scans of tile
+// c+1: one barrier per tile.  Items come from a static round-robin (1D
+// launches) or an atomic ticket (batched plans).  Every wait is bounded; a
+// timeout sets a bit in the device status word and the CTA returns.
 #pragma once
 #include <cstdint>
 
@@ -34,30 +36,48 @@
 namespace mmf {
 
 // ------------------------------------------------------------ element types
+// V: elements per thread per tile; PS: log2 of the ring padding period (one
+// padding pair every 2^PS pairs keeps strided ring accesses conflict-free).
 template <typename T> struct Elem;
 template <> struct Elem<float> {
     using R = float;
-    static constexpr int V = 16;
+    using Pair = float2;
+    static constexpr int V = 8, PS = 4;
     __device__ static R lo() { return __int_as_float(0xff800000); }
     __device__ static R hi() { return __int_as_float(0x7f800000); }
+    __device__ static Pair pair(R m, R n) { return make_float2(m, n); }
+    __device__ static R pmax(Pair p) { return p.x; }
+    __device__ static R pmin(Pair p) { return p.y; }
 };
 template <> struct Elem<double> {
     using R = double;
-    static constexpr int V = 8;
+    using Pair = double2;
+    static constexpr int V = 4, PS = 3;
     __device__ static R lo() { return __longlong_as_double(0xfff0000000000000ULL); }
     __device__ static R hi() { return __longlong_as_double(0x7ff0000000000000ULL); }
+    __device__ static Pair pair(R m, R n) { return make_double2(m, n); }
+    __device__ static R pmax(Pair p) { return p.x; }
+    __device__ static R pmin(Pair p) { return p.y; }
 };
 template <> struct Elem<int16_t> {
     using R = int;
-    static constexpr int V = 16;
+    using Pair = short2;
+    static constexpr int V = 16, PS = 4;
     __device__ static R lo() { return -32768; }
     __device__ static R hi() { return 32767; }
+    __device__ static Pair pair(R m, R n) { return make_short2((short)m, (short)n); }
+    __device__ static R pmax(Pair p) { return p.x; }
+    __device__ static R pmin(Pair p) { return p.y; }
 };
 template <> struct Elem<uint8_t> {
     using R = int;
-    static constexpr int V = 16;
+    using Pair = uchar2;
+    static constexpr int V = 16, PS = 4;
     __device__ static R lo() { return 0; }
     __device__ static R hi() { return 255; }
+    __device__ static Pair pair(R m, R n) { return make_uchar2((unsigned char)m, (unsigned char)n); }
+    __device__ static R pmax(Pair p) { return p.x; }
+    __device__ static R pmin(Pair p) { return p.y; }
 };
 
 __device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
@@ -83,7 +103,9 @@ template <> struct WordElem<int16_t> {
     }
 };
 template <> struct WordElem<uint8_t> {
-    template <int B> __device__ static int get(const uint32_t *wd) { return (int)((wd[B >> 2] >> ((B & 3) * 8)) & 0xffu); }
+    template <int B> __device__ static int get(const uint32_t *wd) {
+        return (int)((wd[B >> 2] >> ((B & 3) * 8)) & 0xffu);
+    }
 };
 
 template <typename T, int S, int I, int V> struct ExtractLoop {
@@ -153,49 +175,89 @@ struct BlockScanParams {
 constexpr int kConsumerWarps = 8;
 constexpr int kNT = kConsumerWarps * 32;
 constexpr int kThreads = kNT;  // thread 0 also issues the copies
-constexpr int kStages = 4;
-constexpr int kQCap = 1024 + 8;     // tile-aggregate ring (>= max tiles per window + 2)
+constexpr int kStages = 5;
+constexpr int kQCap = 1024 + 8;  // tile-aggregate ring (>= max tiles per window + 2)
+constexpr int kMaxItemSpan = 1 << 30;  // relative positions of an item fit in int32
+
+// Metadata of one staged tile, written by thread 0 with the copy.
+struct StageMeta {
+    int64_t item;    // item index on the item's first load; -2 otherwise; -1 = end
+    int64_t a;       // first input position of the tile (series-relative)
+    int64_t int_lo;  // positions [int_lo, int_hi) were copied by the TMA engine
+    int64_t int_hi;
+    int32_t shift;   // element offset of position a within its 16-byte chunk
+    int32_t inner;   // 1 if every position of the tile is in [int_lo, int_hi)
+};
+
+// Dynamic shared memory of the block-scan kernel (layout in Geo<T>).
+extern __shared__ __align__(128) uint8_t bs_smem[];
+
+// Copy-issue state of thread 0 (in shared memory: costs other threads nothing).
+struct ProdState {
+    const void *in;
+    int64_t n, p0, item, k, issued;
+    int32_t q, caseB, ok, l, nloads, finished;
+};
 
 template <typename T> struct Geo {
+    using Pair = typename Elem<T>::Pair;
     static constexpr int V = Elem<T>::V;
-    static constexpr int LGV = (V == 16) ? 4 : 3;
+    static constexpr int PS = Elem<T>::PS;
+    static constexpr int LGV = V == 16 ? 4 : (V == 8 ? 3 : 2);
     static constexpr int T_ = kNT * V;  // tile, elements
-    static constexpr int LGT = (T_ == 4096) ? 12 : 11;
+    static constexpr int LGT = LGV + 8;
     static constexpr int NCH = V * (int)sizeof(T) / 16;  // 16-byte chunks per thread
     static constexpr int STAGE_BYTES = ((T_ * (int)sizeof(T) + 16 + 127) / 128) * 128;
-    static constexpr int RING = 3 * T_;                       // logical ring elements
-    static constexpr int RING_PHYS = RING + RING / 16 + 16;   // 1 pad per 16
+    static constexpr int RING = 3 * T_;  // logical ring pairs
+    static constexpr int RING_PHYS = RING + (RING >> PS) + 16;
+    static constexpr size_t rnd(size_t b) { return (b + 127) / 128 * 128; }
     static constexpr size_t off_stage = 0;
-    static constexpr size_t off_ring_max = off_stage + (size_t)kStages * STAGE_BYTES;
-    static constexpr size_t off_ring_min = off_ring_max + ((RING_PHYS * sizeof(T) + 127) / 128) * 128;
-    static constexpr size_t off_ta_max = off_ring_min + ((RING_PHYS * sizeof(T) + 127) / 128) * 128;
-    static constexpr size_t off_ta_min = off_ta_max + ((kQCap * sizeof(T) + 127) / 128) * 128;
-    static constexpr size_t off_misc = off_ta_min + ((kQCap * sizeof(T) + 127) / 128) * 128;
-    // misc: wtot[2][2 dir][2 side][8] R, mid[2][2][2] R, full barriers,
-    // stage items, producer state
-    static constexpr size_t off_wtot = 0;
-    static constexpr size_t off_mid = off_wtot + 2 * 2 * 2 * kConsumerWarps * 8;
-    static constexpr size_t off_bar = off_mid + 2 * 2 * 2 * 8;
-    static constexpr size_t off_sitem = off_bar + kStages * 8;
-    static constexpr size_t off_prod = off_sitem + kStages * 8;
-    static constexpr size_t misc_bytes = off_prod + 64;
+    static constexpr size_t off_ring = off_stage + (size_t)kStages * STAGE_BYTES;
+    static constexpr size_t off_ta = off_ring + rnd(RING_PHYS * sizeof(Pair));
+    static constexpr size_t off_misc = off_ta + rnd(kQCap * sizeof(Pair));
+    static constexpr size_t off_kagg = 0;  // [3 ring slots][8 warps] block aggregates of K tiles
+    static constexpr size_t off_jagg = off_kagg + 3 * kConsumerWarps * sizeof(Pair);  // [2][8] of J tiles
+    static constexpr size_t off_bar = rnd(off_jagg + 2 * kConsumerWarps * sizeof(Pair));
+    static constexpr size_t off_meta = off_bar + kStages * 8;
+    static constexpr size_t off_prod = off_meta + kStages * sizeof(StageMeta);
+    static constexpr size_t off_params = rnd(off_prod + sizeof(ProdState));
+    static constexpr size_t misc_bytes = off_params + sizeof(BlockScanParams);
     static constexpr size_t smem_bytes = off_misc + misc_bytes;
 };
 
-// Per-item quantities, computed identically by producer and consumers.
+// Shared-memory regions (compile-time offsets from the shared window).
+template <typename T> struct Smem {
+    using G = Geo<T>;
+    using Pair = typename Elem<T>::Pair;
+    __device__ static uint8_t *stage(int s) { return bs_smem + G::off_stage + (size_t)s * G::STAGE_BYTES; }
+    __device__ static Pair *ring() { return reinterpret_cast<Pair *>(bs_smem + G::off_ring); }
+    __device__ static Pair *ta() { return reinterpret_cast<Pair *>(bs_smem + G::off_ta); }
+    __device__ static uint8_t *misc() { return bs_smem + G::off_misc; }
+    __device__ static Pair *kagg() { return reinterpret_cast<Pair *>(misc() + G::off_kagg); }
+    __device__ static Pair *jagg() { return reinterpret_cast<Pair *>(misc() + G::off_jagg); }
+    __device__ static uint64_t *bar() { return reinterpret_cast<uint64_t *>(misc() + G::off_bar); }
+    __device__ static StageMeta *meta() { return reinterpret_cast<StageMeta *>(misc() + G::off_meta); }
+    __device__ static ProdState *prod() { return reinterpret_cast<ProdState *>(misc() + G::off_prod); }
+    __device__ static const BlockScanParams &params() {
+        return *reinterpret_cast<const BlockScanParams *>(misc() + G::off_params);
+    }
+};
+
+// Per-item quantities, computed identically by thread 0 and the consumers.
 template <typename T> struct ItemPlan {
     const T *in;
     T *omax;
     T *omin;
     int64_t n;
-    int64_t p0;       // input position of relative position 0 (= o_begin + d)
+    int64_t p0;  // input position of relative position 0 (= o_begin + d)
     int64_t o_begin;
     int64_t o_end;
-    int64_t s;        // w - 1
-    int q;            // s / T
-    int caseB;        // s >= T
-    int lgB;          // block size log2
-    int NC;           // output tiles in the item
+    int s;       // w - 1
+    int q;       // s / T
+    int caseB;   // s >= T
+    int lgB;     // block size log2
+    int mode;    // 0: B < V, 1: V <= B < 32V, 2: B = 32V (one block per warp)
+    int NC;      // output tiles in the item
     int ok;
 };
 
@@ -223,27 +285,30 @@ __device__ __forceinline__ ItemPlan<T> make_plan(const BlockScanParams &P, int64
     ip.o_begin = ob;
     ip.o_end = oe;
     ip.p0 = ob + sd.d;
-    ip.s = sd.w - 1;
-    ip.q = (int)(ip.s >> G::LGT);
-    ip.caseB = ip.s >= G::T_;
-    if (ip.caseB) {
-        ip.lgB = G::LGT;
+    const int64_t s = sd.w - 1;
+    ip.s = (int)s;
+    ip.q = (int)(s >> G::LGT);
+    ip.caseB = s >= G::T_;
+    if (s >= (int64_t)32 * G::V) {
+        ip.lgB = G::LGV + 5;
+        ip.mode = 2;
     } else {
         int lg = 0;
-        while ((2ll << lg) <= ip.s) ++lg;  // floor(log2 s), s >= 1; s == 0 -> 0
+        while ((2ll << lg) <= s) ++lg;  // floor(log2 s) for s >= 1; 0 for s == 0
         ip.lgB = lg;
+        ip.mode = lg >= G::LGV ? 1 : 0;
     }
-    ip.NC = oe > ob ? (int)((oe - ob + G::T_ - 1) >> G::LGT) : 0;
-    ip.ok = (ip.q + 2 <= kQCap) && oe >= ob;
+    const int64_t span = oe - ob;
+    ip.NC = span > 0 ? (int)((span + G::T_ - 1) >> G::LGT) : 0;
+    ip.ok = (s >= 0) && (ip.q + 2 <= kQCap) && span >= 0 && span + s + 2 * (int64_t)G::T_ <= kMaxItemSpan;
     return ip;
 }
 
 // Loads of one item, in order: prologue tiles x = (caseB ? 1 : 0) .. q, then
 // per output tile c: K tile c+q+1 and, when caseB, J tile c.
-template <typename T> __device__ __forceinline__ int item_loads(const ItemPlan<T> &ip) {
-    if (!ip.ok) return 1;  // a rejected item is one empty stage
-    int pro = ip.caseB ? ip.q : 1;
-    return pro + ip.NC * (ip.caseB ? 2 : 1);
+__device__ __forceinline__ int item_loads(int ok, int caseB, int q, int NC) {
+    if (!ok) return 1;  // a rejected item is one empty stage
+    return (caseB ? q : 1) + NC * (caseB ? 2 : 1);
 }
 
 struct StageCursor {
@@ -255,56 +320,6 @@ struct StageCursor {
             phase ^= 1u;
         }
     }
-};
-
-// Byte range of input tile x that the TMA engine copies: the 16-byte aligned
-// interior of [p0 + xT, p0 + xT + T) clipped to [0, n).
-template <typename T> struct TileCopy {
-    uintptr_t g_aligned_base;  // 16B-aligned address that maps to stage byte 0
-    uintptr_t src;             // first copied byte
-    uint32_t bytes;            // copied bytes (multiple of 16, may be 0)
-    int64_t a;                 // first input position of the tile
-    int64_t int_lo, int_hi;    // positions fully covered by the copy
-};
-
-template <typename T> __device__ __forceinline__ TileCopy<T> tile_copy(const ItemPlan<T> &ip, int x) {
-    using G = Geo<T>;
-    TileCopy<T> tc;
-    tc.a = ip.p0 + (int64_t)x * G::T_;
-    const intptr_t base = (intptr_t)ip.in;
-    const intptr_t ga = base + tc.a * (intptr_t)sizeof(T);
-    tc.g_aligned_base = (uintptr_t)(ga & ~(intptr_t)15);
-    int64_t lo = tc.a > 0 ? tc.a : 0;
-    int64_t hi = tc.a + G::T_ < ip.n ? tc.a + G::T_ : ip.n;
-    tc.bytes = 0;
-    tc.src = 0;
-    tc.int_lo = tc.int_hi = lo;
-    if (hi > lo) {
-        intptr_t gb = base + lo * (intptr_t)sizeof(T);
-        intptr_t ge = base + hi * (intptr_t)sizeof(T);
-        intptr_t gbu = (gb + 15) & ~(intptr_t)15;
-        intptr_t geu = ge & ~(intptr_t)15;
-        if (geu > gbu) {
-            tc.bytes = (uint32_t)(geu - gbu);
-            tc.src = (uintptr_t)gbu;
-            tc.int_lo = (gbu - base) / (intptr_t)sizeof(T);
-            tc.int_hi = (geu - base) / (intptr_t)sizeof(T);
-        }
-    }
-    return tc;
-}
-
-// ------------------------------------------------------------------ kernel
-// Copy issue state of thread 0, kept in shared memory so that it costs the
-// other threads no registers.
-struct ProdState {
-    int64_t item;     // current item (valid when l < nloads)
-    int64_t k;        // static round-robin cursor
-    int64_t issued;   // loads issued so far (all items)
-    int32_t l;        // next load within the item
-    int32_t nloads;   // loads of the item
-    int32_t finished; // end marker issued
-    int32_t pad;
 };
 
 template <typename T>
@@ -321,18 +336,20 @@ __device__ __forceinline__ bool next_item(const BlockScanParams &P, ProdState &p
 // Thread 0 only: issue copies until `consumed + kStages` loads are in flight.
 // Stages consumed before the caller's barrier are free, so this never waits.
 template <typename T>
-__device__ void refill(const BlockScanParams &P, uint8_t *smem, int64_t consumed) {
+__device__ __noinline__ void refill(int64_t consumed) {
     using G = Geo<T>;
-    uint8_t *misc = smem + G::off_misc;
-    uint64_t *full_bar = reinterpret_cast<uint64_t *>(misc + G::off_bar);
-    int64_t *stage_item = reinterpret_cast<int64_t *>(misc + G::off_sitem);
-    ProdState &ps = *reinterpret_cast<ProdState *>(misc + G::off_prod);
+    using S = Smem<T>;
+    const BlockScanParams &P = S::params();
+    uint64_t *full_bar = S::bar();
+    StageMeta *meta = S::meta();
+    ProdState &ps = *S::prod();
     while (!ps.finished && ps.issued < consumed + kStages) {
         const int stage = (int)(ps.issued % kStages);
+        StageMeta &m = meta[stage];
         if (ps.l >= ps.nloads) {
             int64_t item;
             if (!next_item<T>(P, ps, item)) {
-                stage_item[stage] = -1;  // end marker: an empty phase
+                m.item = -1;  // end marker: an empty phase
                 mbar_arrive_expect_tx(&full_bar[stage], 0);
                 ps.finished = 1;
                 ps.issued++;
@@ -340,33 +357,58 @@ __device__ void refill(const BlockScanParams &P, uint8_t *smem, int64_t consumed
             }
             ItemPlan<T> ip = make_plan<T>(P, item);
             if (!ip.ok) report_error(P.status, kErrBadItem);
+            ps.in = ip.in;
+            ps.n = ip.n;
+            ps.p0 = ip.p0;
+            ps.q = ip.q;
+            ps.caseB = ip.caseB;
+            ps.ok = ip.ok;
             ps.item = item;
-            ps.nloads = item_loads(ip);
+            ps.nloads = item_loads(ip.ok, ip.caseB, ip.q, ip.NC);
             ps.l = 0;
         }
-        ItemPlan<T> ip = make_plan<T>(P, ps.item);
-        stage_item[stage] = ps.l == 0 ? ps.item : -2;
+        m.item = ps.l == 0 ? ps.item : -2;
         uint32_t bytes = 0;
         void *dst = nullptr;
         const void *src = nullptr;
         bool keep = false;
-        if (ip.ok) {
+        if (ps.ok) {
             int x;
-            const int pro = ip.caseB ? ip.q : 1;
+            const int pro = ps.caseB ? ps.q : 1;
             if (ps.l < pro) {
-                x = ip.caseB ? 1 + ps.l : 0;
-                keep = ip.caseB;
+                x = ps.caseB ? 1 + ps.l : 0;
+                keep = ps.caseB;
             } else {
                 const int r = ps.l - pro;
-                const int c = ip.caseB ? r >> 1 : r;
-                const bool jload = ip.caseB && (r & 1);
-                x = jload ? c : c + ip.q + 1;
-                keep = ip.caseB && !jload;  // re-read later as a J tile
+                const int c = ps.caseB ? r >> 1 : r;
+                const bool jload = ps.caseB && (r & 1);
+                x = jload ? c : c + ps.q + 1;
+                keep = ps.caseB && !jload;  // read again later as a J tile
             }
-            TileCopy<T> tc = tile_copy<T>(ip, x);
-            bytes = tc.bytes;
-            dst = smem + G::off_stage + (size_t)stage * G::STAGE_BYTES + (tc.src - tc.g_aligned_base);
-            src = reinterpret_cast<const void *>(tc.src);
+            // The 16-byte aligned interior of [a, a+T) clipped to [0, n).
+            const int64_t a = ps.p0 + (int64_t)x * G::T_;
+            const intptr_t base = (intptr_t)ps.in;
+            const intptr_t ga = base + a * (intptr_t)sizeof(T);
+            const intptr_t gal = ga & ~(intptr_t)15;
+            const int64_t lo = a > 0 ? a : 0;
+            const int64_t hi = a + G::T_ < ps.n ? a + G::T_ : ps.n;
+            int64_t ilo = lo, ihi = lo;
+            if (hi > lo) {
+                const intptr_t gbu = (base + lo * (intptr_t)sizeof(T) + 15) & ~(intptr_t)15;
+                const intptr_t geu = (base + hi * (intptr_t)sizeof(T)) & ~(intptr_t)15;
+                if (geu > gbu) {
+                    bytes = (uint32_t)(geu - gbu);
+                    src = reinterpret_cast<const void *>(gbu);
+                    dst = S::stage(stage) + (size_t)(gbu - gal);
+                    ilo = (gbu - base) / (intptr_t)sizeof(T);
+                    ihi = (geu - base) / (intptr_t)sizeof(T);
+                }
+            }
+            m.a = a;
+            m.int_lo = ilo;
+            m.int_hi = ihi;
+            m.shift = (int)((ga - gal) / (intptr_t)sizeof(T));
+            m.inner = (ilo <= a && a + G::T_ <= ihi) ? 1 : 0;
         }
         mbar_arrive_expect_tx(&full_bar[stage], bytes);
         if (bytes) tma_load_1d(dst, src, bytes, &full_bar[stage], keep ? policy_evict_last() : policy_evict_first());
@@ -375,71 +417,73 @@ __device__ void refill(const BlockScanParams &P, uint8_t *smem, int64_t consumed
     }
 }
 
-template <typename T, bool FULL>
+// ------------------------------------------------------------ consumer side
+// Block modes of an item (s = w-1, warp span W = 32V):
+//   0: s < V      B = 2^floor(log2 s) < V: blocks inside a thread
+//   1: s < W      B = 2^floor(log2 s) in [V, W/2]: blocks of 2..16 lanes
+//   2: s >= W     B = W: one block per warp; for s >= T also tile aggregates
+template <typename T>
 struct Consumer {
     using R = typename Elem<T>::R;
+    using Pair = typename Elem<T>::Pair;
     using G = Geo<T>;
+    using S = Smem<T>;
     static constexpr int V = G::V;
+    static constexpr int T_ = G::T_;
 
-    const BlockScanParams *P;
-    uint8_t *smem;
-    T *ring_max, *ring_min, *ta_max, *ta_min;
-    R *wtot;  // [2 buf][2 dir][2 side][8 warps]
-    R *mid;   // [2 buf][2 which][2 side]
-    uint64_t *full_bar;
-    uint32_t *status;
     int tid, lane, warp;
-    int wbuf = 0;
     int64_t consumed = 0;
     StageCursor cur;
     bool failed = false;
 
-    __device__ __forceinline__ int ring_phys(int idx) const { return idx + (idx >> 4); }
-
-    // Barrier over the CTA; afterwards thread 0 refills the consumed stages.
+    // CTA barrier; afterwards thread 0 refills the stages consumed before it.
     __device__ __forceinline__ void sync() {
         named_bar_sync(1, kNT);
-        if (tid == 0) refill<T>(*P, smem, consumed);
+        if (tid == 0) refill<T>(consumed);
     }
 
-    // Read input tile x of the item into registers (max-side and min-side
-    // copies differ only where positions fall outside [0, n): padding).
-    __device__ __forceinline__ bool read_tile(const ItemPlan<T> &ip, int x, R (&xm)[V], R (&xn)[V]) {
-        if (!mbar_wait_bounded(&full_bar[cur.stage], cur.phase)) {
-            report_error(status, kErrWaitTimeout);
+    // Read the next staged tile into registers.  Max-side and min-side copies
+    // differ only at positions outside [0, n), which hold identities.
+    __device__ __forceinline__ bool read_tile(const ItemPlan<T> &ip, R (&xm)[V], R (&xn)[V]) {
+        if (!mbar_wait_bounded(&S::bar()[cur.stage], cur.phase)) {
+            report_error(S::params().status, kErrWaitTimeout);
             failed = true;
             return false;
         }
-        TileCopy<T> tc = tile_copy<T>(ip, x);
-        const uint8_t *sb = smem + G::off_stage + (size_t)cur.stage * G::STAGE_BYTES;
-        const int shift_b = (int)((((intptr_t)ip.in + tc.a * (intptr_t)sizeof(T))) & 15);
-        uint32_t wd[4 * (G::NCH + 1)];
-        const uint4 *p4 = reinterpret_cast<const uint4 *>(sb + (size_t)tid * V * sizeof(T));
-#pragma unroll
-        for (int c = 0; c < G::NCH; ++c) {
-            uint4 v = p4[c];
-            wd[4 * c] = v.x; wd[4 * c + 1] = v.y; wd[4 * c + 2] = v.z; wd[4 * c + 3] = v.w;
-        }
-        if (shift_b) {
-            uint4 v = p4[G::NCH];
-            wd[4 * G::NCH] = v.x; wd[4 * G::NCH + 1] = v.y; wd[4 * G::NCH + 2] = v.z; wd[4 * G::NCH + 3] = v.w;
-        } else {
-            wd[4 * G::NCH] = wd[4 * G::NCH + 1] = wd[4 * G::NCH + 2] = wd[4 * G::NCH + 3] = 0;
-        }
+        const StageMeta &m = S::meta()[cur.stage];
+        const int shift = m.shift;
+        const int inner = m.inner;
+        const uint8_t *sb = S::stage(cur.stage);
         R xv[V];
-        extract_shifted<T>(shift_b / (int)sizeof(T), wd, xv);
-        const int64_t pt = tc.a + (int64_t)tid * V;
-        if (pt >= tc.int_lo && pt + V <= tc.int_hi) {
+        if (shift == 0) {
+            // Aligned tile: 16-byte vector reads of the thread's V elements.
+            uint32_t wd[4 * G::NCH];
+            const uint4 *p4 = reinterpret_cast<const uint4 *>(sb + (size_t)tid * V * sizeof(T));
+#pragma unroll
+            for (int c = 0; c < G::NCH; ++c) {
+                uint4 v = p4[c];
+                wd[4 * c] = v.x; wd[4 * c + 1] = v.y; wd[4 * c + 2] = v.z; wd[4 * c + 3] = v.w;
+            }
+            ExtractLoop<T, 0, 0, V>::run(wd, xv);
+        } else {
+            // Tile start not 16-byte aligned (unaligned series): element reads.
+            const T *pe = reinterpret_cast<const T *>(sb) + shift + tid * V;
+#pragma unroll
+            for (int i = 0; i < V; ++i) xv[i] = (R)pe[i];
+        }
+        if (inner) {
 #pragma unroll
             for (int i = 0; i < V; ++i) xm[i] = xn[i] = xv[i];
         } else {
+            const int64_t pt = m.a + (int64_t)tid * V;
+            const int64_t ilo = m.int_lo, ihi = m.int_hi;
 #pragma unroll
             for (int i = 0; i < V; ++i) {
                 const int64_t p = pt + i;
                 if (p < 0 || p >= ip.n) {
                     xm[i] = Elem<T>::lo();
                     xn[i] = Elem<T>::hi();
-                } else if (p < tc.int_lo || p >= tc.int_hi) {
+                } else if (p < ilo || p >= ihi) {
                     R v = (R)ip.in[p];
                     xm[i] = xn[i] = v;
                 } else {
@@ -451,9 +495,10 @@ struct Consumer {
         ++consumed;
         return true;
     }
-    // Thread-local part of the block-segmented prefix (dir 0) scan.
+
+    template <int MODE>
     __device__ __forceinline__ void local_prefix(R (&m)[V], R (&n)[V], int lgB) const {
-        if constexpr (FULL) {
+        if constexpr (MODE > 0) {
 #pragma unroll
             for (int i = 1; i < V; ++i) { m[i] = vmax(m[i - 1], m[i]); n[i] = vmin(n[i - 1], n[i]); }
         } else {
@@ -463,8 +508,9 @@ struct Consumer {
                 if (i & bmask) { m[i] = vmax(m[i - 1], m[i]); n[i] = vmin(n[i - 1], n[i]); }
         }
     }
+    template <int MODE>
     __device__ __forceinline__ void local_suffix(R (&m)[V], R (&n)[V], int lgB) const {
-        if constexpr (FULL) {
+        if constexpr (MODE > 0) {
 #pragma unroll
             for (int i = V - 2; i >= 0; --i) { m[i] = vmax(m[i + 1], m[i]); n[i] = vmin(n[i + 1], n[i]); }
         } else {
@@ -475,14 +521,16 @@ struct Consumer {
         }
     }
 
-    // Cross-thread carries for segments of 2^lgS threads (lgS = lgB - LGV > 0).
-    // dir 0: exclusive prefix carry from lower threads of the segment;
-    // dir 1: exclusive suffix carry from higher threads.  Warp totals are
-    // published in wtot[wbuf][dir] for segments spanning several warps.
-    __device__ __forceinline__ void warp_carry(int dir, R tm, R tn, int lgS, R &cm, R &cn) {
-        const int segl = lgS >= 5 ? 32 : (1 << lgS);
+    // Block-segmented carries across the lanes of a block of 2^lgS lanes
+    // (1 <= lgS <= 5): dir 0 applies the exclusive prefix from lower lanes,
+    // dir 1 the exclusive suffix from higher lanes.  Returns the inclusive
+    // total of the block (valid in the block's last / first lane).
+    __device__ __forceinline__ void lane_carry(int dir, R (&m)[V], R (&n)[V], int lgS, R &tot_m, R &tot_n) const {
+        const int segl = 1 << lgS;
         const int lis = lane & (segl - 1);
         const int pos = dir == 0 ? lis : (segl - 1 - lis);
+        R tm = dir == 0 ? m[V - 1] : m[0];
+        R tn = dir == 0 ? n[V - 1] : n[0];
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             if (d >= segl) break;
@@ -492,188 +540,140 @@ struct Consumer {
         }
         R em = dir == 0 ? __shfl_up_sync(0xffffffffu, tm, 1) : __shfl_down_sync(0xffffffffu, tm, 1);
         R en = dir == 0 ? __shfl_up_sync(0xffffffffu, tn, 1) : __shfl_down_sync(0xffffffffu, tn, 1);
-        if (pos == 0) { em = Elem<T>::lo(); en = Elem<T>::hi(); }
-        cm = em;
-        cn = en;
-        if (lgS > 5) {
-            const bool pub = dir == 0 ? (lane == 31) : (lane == 0);
-            if (pub) {
-                R *wt = wtot + ((wbuf * 2 + dir) * 2) * kConsumerWarps;
-                wt[warp] = tm;
-                wt[kConsumerWarps + warp] = tn;
-            }
-        }
-    }
-    __device__ __forceinline__ void warp_carry_cross(int dir, int lgS, R &cm, R &cn) const {
-        const int segw = 1 << (lgS - 5);
-        const int wfirst = warp & ~(segw - 1);
-        const R *wt = wtot + ((wbuf * 2 + dir) * 2) * kConsumerWarps;
-        if (dir == 0) {
-            for (int k = wfirst; k < warp; ++k) { cm = vmax(cm, wt[k]); cn = vmin(cn, wt[kConsumerWarps + k]); }
-        } else {
-            for (int k = warp + 1; k < wfirst + segw; ++k) { cm = vmax(cm, wt[k]); cn = vmin(cn, wt[kConsumerWarps + k]); }
-        }
-    }
-
-    // Full block-segmented scans: prefix over (pm, pn) and, if do_suf, suffix
-    // over (sm, sn).  One consumer barrier when segments span warps.
-    __device__ __forceinline__ void scans(R (&pm)[V], R (&pn)[V], bool do_suf, R (&sm)[V], R (&sn)[V], int lgB) {
-        local_prefix(pm, pn, lgB);
-        if (do_suf) local_suffix(sm, sn, lgB);
-        if (lgB > G::LGV) {
-            const int lgS = lgB - G::LGV;
-            R pcm, pcn, scm = Elem<T>::lo(), scn = Elem<T>::hi();
-            warp_carry(0, pm[V - 1], pn[V - 1], lgS, pcm, pcn);
-            if (do_suf) warp_carry(1, sm[0], sn[0], lgS, scm, scn);
-            if (lgS > 5) {
-                sync();
-                warp_carry_cross(0, lgS, pcm, pcn);
-                if (do_suf) warp_carry_cross(1, lgS, scm, scn);
-                wbuf ^= 1;
-            }
+        if (pos != 0) {
 #pragma unroll
-            for (int i = 0; i < V; ++i) { pm[i] = vmax(pm[i], pcm); pn[i] = vmin(pn[i], pcn); }
-            if (do_suf) {
-#pragma unroll
-                for (int i = 0; i < V; ++i) { sm[i] = vmax(sm[i], scm); sn[i] = vmin(sn[i], scn); }
-            }
+            for (int i = 0; i < V; ++i) { m[i] = vmax(m[i], em); n[i] = vmin(n[i], en); }
         }
+        tot_m = tm;
+        tot_n = tn;
     }
 
     __device__ __forceinline__ void ring_write(int x, const R (&pm)[V], const R (&pn)[V]) {
-        const int base = (x % 3) * G::T_ + tid * V;
+        const int base = (x % 3) * T_ + tid * V;
+        Pair *r = S::ring() + base + (base >> G::PS);
 #pragma unroll
-        for (int i = 0; i < V; ++i) {
-            const int ph = ring_phys(base + i);
-            ring_max[ph] = (T)pm[i];
-            ring_min[ph] = (T)pn[i];
+        for (int i = 0; i < V; ++i) r[i] = Elem<T>::pair(pm[i], pn[i]);
+    }
+
+    // Ring slot index of relative position p (p >= 0).
+    __device__ __forceinline__ int ring_index(int p) const { return ((p >> G::LGT) % 3) * T_ + (p & (T_ - 1)); }
+    __device__ __forceinline__ Pair ring_at(int idx) const { return S::ring()[idx + (idx >> G::PS)]; }
+
+    // Tile aggregates c+1 .. c+q-1, reduced across the warp.
+    __device__ __forceinline__ void tiles_between(int c, int q, R &m1, R &n1) const {
+        m1 = Elem<T>::lo();
+        n1 = Elem<T>::hi();
+        for (int x = c + 1 + lane; x <= c + q - 1; x += 32) {
+            const Pair pr = S::ta()[x % kQCap];
+            m1 = vmax(m1, Elem<T>::pmax(pr));
+            n1 = vmin(n1, Elem<T>::pmin(pr));
+        }
+#pragma unroll
+        for (int d = 16; d >= 1; d >>= 1) {
+            m1 = vmax(m1, __shfl_xor_sync(0xffffffffu, m1, d));
+            n1 = vmin(n1, __shfl_xor_sync(0xffffffffu, n1, d));
         }
     }
 
-    __device__ __forceinline__ void run_item(const ItemPlan<T> &ip) {
-        R sm[V], sn[V];  // suffix scan of the J tile of the current output tile
-        const int q = ip.q;
-        // ---------------- prologue
-        const int xs = ip.caseB ? 1 : 0;
-        for (int x = xs; x <= q; ++x) {
-            R pm[V], pn[V];
-            if (!read_tile(ip, x, pm, pn)) return;
+    // Outputs of output tile c: max(S_B[j], blocks between, P_B[j+s]).
+    template <int MODE>
+    __device__ __forceinline__ void outputs(const ItemPlan<T> &ip, int c, const R (&sm)[V], const R (&sn)[V]) {
+        const int lgB = ip.lgB;
+        const int jr0 = c * T_ + tid * V;
+        const int kr0 = jr0 + ip.s;
+        // Ring addresses of kr0 .. kr0+V-1: one padding step and at most one
+        // wrap of the 3-tile ring, both at the same 2^PS boundary.
+        const int p = ring_index(kr0);
+        const int phys = p + (p >> G::PS);
+        const int cpad = (1 << G::PS) - (p & ((1 << G::PS) - 1));
+        const int hi_base = (p + cpad == G::RING) ? -cpad : phys + 1;
+        R om[V], on[V];
+        if constexpr (MODE == 2) {
+            // Lane array of block aggregates in window order: case A lanes 0..15
+            // = warp blocks of tiles c, c+1; case B lanes 0..7 = J tile c,
+            // 8..15 = K tile c+q, 16..23 = K tile c+q+1.  Prefix from the block
+            // after j's (lane warp+1); for case B the full tiles c+1..c+q-1
+            // join every lane from 7 on.
+            const int q = ip.q;
+            Pair a;
             if (!ip.caseB) {
-#pragma unroll
-                for (int i = 0; i < V; ++i) { sm[i] = pm[i]; sn[i] = pn[i]; }
-            }
-            scans(pm, pn, !ip.caseB, sm, sn, ip.lgB);
-            if (x == q) ring_write(x, pm, pn);
-            if (ip.caseB && tid == kNT - 1) { ta_max[x % kQCap] = (T)pm[V - 1]; ta_min[x % kQCap] = (T)pn[V - 1]; }
-        }
-        sync();
-        // ---------------- main loop over output tiles
-        const int64_t s = ip.s;
-        for (int c = 0; c < ip.NC; ++c) {
-            if (ip.caseB && warp == 0) {
-                // Mid1 = max over tile aggregates c+1 .. c+q-1; Mid2 adds c+q.
-                R m1 = Elem<T>::lo(), n1 = Elem<T>::hi();
-                for (int x = c + 1 + lane; x <= c + q - 1; x += 32) {
-                    m1 = vmax(m1, (R)ta_max[x % kQCap]);
-                    n1 = vmin(n1, (R)ta_min[x % kQCap]);
-                }
-#pragma unroll
-                for (int d = 16; d >= 1; d >>= 1) {
-                    m1 = vmax(m1, __shfl_xor_sync(0xffffffffu, m1, d));
-                    n1 = vmin(n1, __shfl_xor_sync(0xffffffffu, n1, d));
-                }
-                if (lane == 0) {
-                    R *md = mid + (c & 1) * 4;
-                    const int xl = (c + q) % kQCap;
-                    md[0] = m1;
-                    md[1] = n1;
-                    md[2] = vmax(m1, (R)ta_max[xl]);
-                    md[3] = vmin(n1, (R)ta_min[xl]);
-                }
-            }
-            R pm[V], pn[V], nm[V], nn[V];
-            const int xk = c + q + 1;
-            if (!read_tile(ip, xk, pm, pn)) return;
-            if (!ip.caseB) {
-#pragma unroll
-                for (int i = 0; i < V; ++i) { nm[i] = pm[i]; nn[i] = pn[i]; }
-                scans(pm, pn, true, nm, nn, ip.lgB);
+                a = lane < 8 ? S::kagg()[(c % 3) * 8 + lane]
+                             : (lane < 16 ? S::kagg()[((c + 1) % 3) * 8 + lane - 8] : Elem<T>::pair(Elem<T>::lo(), Elem<T>::hi()));
             } else {
-                if (!read_tile(ip, c, sm, sn)) return;
-                scans(pm, pn, true, sm, sn, ip.lgB);
+                a = lane < 8 ? S::jagg()[(c & 1) * 8 + lane]
+                             : (lane < 16 ? S::kagg()[((c + q) % 3) * 8 + lane - 8]
+                                          : (lane < 24 ? S::kagg()[((c + q + 1) % 3) * 8 + lane - 16]
+                                                       : Elem<T>::pair(Elem<T>::lo(), Elem<T>::hi())));
             }
-            ring_write(xk, pm, pn);
-            if (ip.caseB && tid == kNT - 1) { ta_max[xk % kQCap] = (T)pm[V - 1]; ta_min[xk % kQCap] = (T)pn[V - 1]; }
-            sync();
-
-            // ------------ outputs of tile c
-            R om[V], on[V];
-            const int64_t jr0 = (int64_t)c * G::T_ + (int64_t)tid * V;  // relative J position of element 0
-            const int64_t kr0 = jr0 + s;
-            const int ring_len = G::RING;
-            int ridx = (int)(kr0 % ring_len);
+            R am = lane > warp ? Elem<T>::pmax(a) : Elem<T>::lo();
+            R an = lane > warp ? Elem<T>::pmin(a) : Elem<T>::hi();
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                R um = __shfl_up_sync(0xffffffffu, am, d);
+                R un = __shfl_up_sync(0xffffffffu, an, d);
+                if (lane >= d) { am = vmax(am, um); an = vmin(an, un); }
+            }
             if (ip.caseB) {
-                const R *md = mid + (c & 1) * 4;
-                const R m1 = md[0], n1 = md[1], m2 = md[2], n2 = md[3];
-                const int64_t cross = (int64_t)(c + q + 1) * G::T_ - kr0;  // i >= cross -> k in tile c+q+1
-#pragma unroll
-                for (int i = 0; i < V; ++i) {
-                    int r = ridx + i;
-                    if (r >= ring_len) r -= ring_len;
-                    const int ph = ring_phys(r);
-                    const bool far = i >= cross;
-                    om[i] = vmax(sm[i], vmax((R)ring_max[ph], far ? m2 : m1));
-                    on[i] = vmin(sn[i], vmin((R)ring_min[ph], far ? n2 : n1));
-                }
-            } else if (FULL) {
-                const int lgB = ip.lgB;
-                const int64_t bj = jr0 >> lgB;
-                const int64_t cross = ((bj + 2) << lgB) - kr0;  // i >= cross -> k in block bj+2
-                R mm = Elem<T>::lo(), mn_ = Elem<T>::hi();
-                if (cross < V) {
-                    int r = (int)((((bj + 2) << lgB) - 1) % ring_len);
-                    mm = (R)ring_max[ring_phys(r)];
-                    mn_ = (R)ring_min[ring_phys(r)];
-                }
-#pragma unroll
-                for (int i = 0; i < V; ++i) {
-                    int r = ridx + i;
-                    if (r >= ring_len) r -= ring_len;
-                    const int ph = ring_phys(r);
-                    const bool far = i >= cross;
-                    om[i] = vmax(sm[i], vmax((R)ring_max[ph], far ? mm : Elem<T>::lo()));
-                    on[i] = vmin(sn[i], vmin((R)ring_min[ph], far ? mn_ : Elem<T>::hi()));
-                }
-            } else {
-                const int lgB = ip.lgB;
-#pragma unroll
-                for (int i = 0; i < V; ++i) {
-                    int r = ridx + i;
-                    if (r >= ring_len) r -= ring_len;
-                    const int ph = ring_phys(r);
-                    R vm = vmax(sm[i], (R)ring_max[ph]);
-                    R vn = vmin(sn[i], (R)ring_min[ph]);
-                    const int64_t bj = (jr0 + i) >> lgB, bk = (kr0 + i) >> lgB;
-                    if (bk == bj + 2) {
-                        int rm = (int)(((bk << lgB) - 1) % ring_len);
-                        vm = vmax(vm, (R)ring_max[ring_phys(rm)]);
-                        vn = vmin(vn, (R)ring_min[ring_phys(rm)]);
-                    }
-                    om[i] = vm;
-                    on[i] = vn;
-                }
+                R tm, tn;
+                tiles_between(c, q, tm, tn);
+                if (lane >= 7) { am = vmax(am, tm); an = vmin(an, tn); }
             }
-            // ------------ store
-            const int64_t o0 = ip.o_begin + jr0;
-            if (o0 < ip.o_end) {
-                const bool full = o0 + V <= ip.o_end;
-                if (ip.omax) store(ip.omax + o0, om, full ? V : (int)(ip.o_end - o0));
-                if (ip.omin) store(ip.omin + o0, on, full ? V : (int)(ip.o_end - o0));
-            }
-            if (!ip.caseB) {
+            // Lane of k0's block; outputs i >= cross have k in the next block.
+            const int kb = kr0 >> lgB;
+            const int g0 = ip.caseB ? kb - ((c + q) << 3) + 8 : kb - (c << 3);
+            const int cross = ((kb + 1) << lgB) - kr0;
+            const R c0m = __shfl_sync(0xffffffffu, am, g0 - 1), c0n = __shfl_sync(0xffffffffu, an, g0 - 1);
+            const R c1m = __shfl_sync(0xffffffffu, am, g0), c1n = __shfl_sync(0xffffffffu, an, g0);
 #pragma unroll
-                for (int i = 0; i < V; ++i) { sm[i] = nm[i]; sn[i] = nn[i]; }
+            for (int i = 0; i < V; ++i) {
+                const Pair pr = S::ring()[(i < cpad ? phys : hi_base) + i];
+                const bool far = i >= cross;
+                om[i] = vmax(vmax(sm[i], far ? c1m : c0m), Elem<T>::pmax(pr));
+                on[i] = vmin(vmin(sn[i], far ? c1n : c0n), Elem<T>::pmin(pr));
             }
+        } else if constexpr (MODE == 1) {
+            const int bj = jr0 >> lgB;
+            const int bend = ((bj + 2) << lgB) - 1;  // last position of block bj+1
+            const int cross = bend + 1 - kr0;         // i >= cross: k in block bj+2
+            R mm = Elem<T>::lo(), mn = Elem<T>::hi();
+            if (cross < V) {
+                int idx = p + (bend - kr0);
+                if (idx < 0) idx += G::RING;
+                const Pair pr = ring_at(idx);
+                mm = Elem<T>::pmax(pr);
+                mn = Elem<T>::pmin(pr);
+            }
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const Pair pr = S::ring()[(i < cpad ? phys : hi_base) + i];
+                const bool far = i >= cross;
+                om[i] = vmax(vmax(sm[i], far ? mm : Elem<T>::lo()), Elem<T>::pmax(pr));
+                on[i] = vmin(vmin(sn[i], far ? mn : Elem<T>::hi()), Elem<T>::pmin(pr));
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const Pair pr = S::ring()[(i < cpad ? phys : hi_base) + i];
+                R vm = vmax(sm[i], Elem<T>::pmax(pr));
+                R vn = vmin(sn[i], Elem<T>::pmin(pr));
+                const int bj = (jr0 + i) >> lgB, bk = (kr0 + i) >> lgB;
+                if (bk == bj + 2) {
+                    int idx = p + ((bk << lgB) - 1 - kr0);
+                    if (idx < 0) idx += G::RING;
+                    if (idx >= G::RING) idx -= G::RING;
+                    const Pair pm = ring_at(idx);
+                    vm = vmax(vm, Elem<T>::pmax(pm));
+                    vn = vmin(vn, Elem<T>::pmin(pm));
+                }
+                om[i] = vm;
+                on[i] = vn;
+            }
+        }
+        const int64_t o0 = ip.o_begin + jr0;
+        if (o0 < ip.o_end) {
+            const int cnt = o0 + V <= ip.o_end ? V : (int)(ip.o_end - o0);
+            if (ip.omax) store(ip.omax + o0, om, cnt);
+            if (ip.omin) store(ip.omin + o0, on, cnt);
         }
     }
 
@@ -695,82 +695,142 @@ struct Consumer {
                 if (i < cnt) dst[i] = (T)v[i];
         }
     }
+
+    // Tile aggregate of K tile x from its warp-block aggregates (warp 0).
+    __device__ __forceinline__ void publish_tile_aggregate(int x) const {
+        if (warp != 0) return;
+        Pair a = lane < 8 ? S::kagg()[(x % 3) * 8 + lane] : Elem<T>::pair(Elem<T>::lo(), Elem<T>::hi());
+        R m = Elem<T>::pmax(a), n = Elem<T>::pmin(a);
+#pragma unroll
+        for (int d = 4; d >= 1; d >>= 1) {
+            m = vmax(m, __shfl_xor_sync(0xffffffffu, m, d));
+            n = vmin(n, __shfl_xor_sync(0xffffffffu, n, d));
+        }
+        if (lane == 0) S::ta()[x % kQCap] = Elem<T>::pair(m, n);
+    }
+
+    // Prefix (and optionally suffix) block scans of one tile's registers.
+    // MODE 2 publishes the warp (= block) totals.
+    template <int MODE>
+    __device__ __forceinline__ void scan_tile(const ItemPlan<T> &ip, R (&pm)[V], R (&pn)[V], bool suf, R (&sm)[V],
+                                              R (&sn)[V], int kslot, int jbuf) {
+        const int lgB = ip.lgB;
+        local_prefix<MODE>(pm, pn, lgB);
+        if (suf) local_suffix<MODE>(sm, sn, lgB);
+        if constexpr (MODE > 0) {
+            const int lgS = lgB - G::LGV;
+            if (lgS > 0) {
+                R tm, tn;
+                lane_carry(0, pm, pn, lgS, tm, tn);
+                if (MODE == 2 && lane == 31) S::kagg()[kslot * 8 + warp] = Elem<T>::pair(tm, tn);
+                if (suf) {
+                    lane_carry(1, sm, sn, lgS, tm, tn);
+                    if (MODE == 2 && jbuf >= 0 && lane == 0) S::jagg()[jbuf * 8 + warp] = Elem<T>::pair(tm, tn);
+                }
+            }
+        }
+    }
+
+    template <int MODE>
+    __device__ __forceinline__ void run_item(const ItemPlan<T> &ip) {
+        const int q = ip.q;
+        R Sc_m[V], Sc_n[V];  // case A: suffix scan of input tile c
+
+        // ---------------- prologue: tile 0 (case A) or tiles 1..q (case B)
+        if (!ip.caseB) {
+            R pm[V], pn[V];
+            if (!read_tile(ip, pm, pn)) return;
+#pragma unroll
+            for (int i = 0; i < V; ++i) { Sc_m[i] = pm[i]; Sc_n[i] = pn[i]; }
+            scan_tile<MODE>(ip, pm, pn, true, Sc_m, Sc_n, 0, -1);
+            ring_write(0, pm, pn);
+        } else {
+            for (int x = 1; x <= q; ++x) {
+                R pm[V], pn[V];
+                if (!read_tile(ip, pm, pn)) return;
+                scan_tile<MODE>(ip, pm, pn, false, pm, pn, x % 3, -1);
+                if (x == q) ring_write(x, pm, pn);
+                sync();
+                publish_tile_aggregate(x);
+            }
+        }
+        sync();
+
+        // ---------------- main loop over output tiles
+        for (int c = 0; c < ip.NC; ++c) {
+            R pm[V], pn[V], Sn_m[V], Sn_n[V];
+            const int xk = c + q + 1;
+            if (!read_tile(ip, pm, pn)) return;  // K tile c+q+1
+            if (!ip.caseB) {
+#pragma unroll
+                for (int i = 0; i < V; ++i) { Sn_m[i] = pm[i]; Sn_n[i] = pn[i]; }
+            } else {
+                if (!read_tile(ip, Sn_m, Sn_n)) return;  // J tile c
+            }
+            scan_tile<MODE>(ip, pm, pn, true, Sn_m, Sn_n, xk % 3, ip.caseB ? (c & 1) : -1);
+            ring_write(xk, pm, pn);
+            sync();
+            if (ip.caseB) {
+                publish_tile_aggregate(xk);
+                outputs<MODE>(ip, c, Sn_m, Sn_n);
+            } else {
+                outputs<MODE>(ip, c, Sc_m, Sc_n);
+#pragma unroll
+                for (int i = 0; i < V; ++i) { Sc_m[i] = Sn_m[i]; Sc_n[i] = Sn_n[i]; }
+            }
+        }
+    }
 };
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 1) blockscan_kernel(const BlockScanParams P) {
-    using G = Geo<T>;
-    using R = typename Elem<T>::R;
-    extern __shared__ __align__(128) uint8_t smem[];
-    uint8_t *misc = smem + G::off_misc;
-    R *wtot = reinterpret_cast<R *>(misc + G::off_wtot);
-    R *mid = reinterpret_cast<R *>(misc + G::off_mid);
-    uint64_t *full_bar = reinterpret_cast<uint64_t *>(misc + G::off_bar);
-    int64_t *stage_item = reinterpret_cast<int64_t *>(misc + G::off_sitem);
-
+__global__ void __launch_bounds__(kThreads, Elem<T>::V == 16 ? 1 : 2) blockscan_kernel(const BlockScanParams P) {
+    using S = Smem<T>;
     const int tid = threadIdx.x;
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) mbar_init(&full_bar[s], 1);
+        *reinterpret_cast<BlockScanParams *>(S::misc() + Geo<T>::off_params) = P;
+        for (int s = 0; s < kStages; ++s) mbar_init(&S::bar()[s], 1);
         fence_mbar_init();
-        ProdState &ps = *reinterpret_cast<ProdState *>(misc + G::off_prod);
+        ProdState &ps = *S::prod();
+        ps.in = nullptr;
+        ps.n = ps.p0 = 0;
         ps.item = -1;
         ps.k = 0;
         ps.issued = 0;
+        ps.q = ps.caseB = ps.ok = 0;
         ps.l = 0;
         ps.nloads = 0;
         ps.finished = 0;
-        refill<T>(P, smem, 0);
+        refill<T>(0);
     }
     __syncthreads();
 
-    Consumer<T, true> cf;
-    Consumer<T, false> cg;
-    auto setup = [&](auto &cc) {
-        cc.P = &P;
-        cc.smem = smem;
-        cc.ring_max = reinterpret_cast<T *>(smem + G::off_ring_max);
-        cc.ring_min = reinterpret_cast<T *>(smem + G::off_ring_min);
-        cc.ta_max = reinterpret_cast<T *>(smem + G::off_ta_max);
-        cc.ta_min = reinterpret_cast<T *>(smem + G::off_ta_min);
-        cc.wtot = wtot;
-        cc.mid = mid;
-        cc.full_bar = full_bar;
-        cc.status = P.status;
-        cc.tid = tid;
-        cc.lane = tid & 31;
-        cc.warp = tid >> 5;
-    };
-    setup(cf);
-    setup(cg);
-    StageCursor cur;
-    int wbuf = 0;
-    int64_t consumed = 0;
+    Consumer<T> cs;
+    cs.tid = tid;
+    cs.lane = tid & 31;
+    cs.warp = tid >> 5;
     while (true) {
         // The first stage of each item carries its index (-1 marks the end).
-        if (!mbar_wait_bounded(&full_bar[cur.stage], cur.phase)) {
+        if (!mbar_wait_bounded(&S::bar()[cs.cur.stage], cs.cur.phase)) {
             report_error(P.status, kErrWaitTimeout);
             return;
         }
-        const int64_t item = stage_item[cur.stage];
+        const int64_t item = S::meta()[cs.cur.stage].item;
         if (item < 0) return;
         ItemPlan<T> ip = make_plan<T>(P, item);
         if (!ip.ok) {
-            cur.advance();
-            ++consumed;
-        } else if (ip.caseB || ip.lgB >= Geo<T>::LGV) {
-            cf.cur = cur; cf.wbuf = wbuf; cf.consumed = consumed;
-            cf.run_item(ip);
-            if (cf.failed) return;
-            cur = cf.cur; wbuf = cf.wbuf; consumed = cf.consumed;
+            cs.cur.advance();
+            ++cs.consumed;
+        } else if (ip.mode == 2) {
+            cs.template run_item<2>(ip);
+        } else if (ip.mode == 1) {
+            cs.template run_item<1>(ip);
         } else {
-            cg.cur = cur; cg.wbuf = wbuf; cg.consumed = consumed;
-            cg.run_item(ip);
-            if (cg.failed) return;
-            cur = cg.cur; wbuf = cg.wbuf; consumed = cg.consumed;
+            cs.template run_item<0>(ip);
         }
+        if (cs.failed) return;
         // Item boundary: the ring may be reused and consumed stages refilled.
         named_bar_sync(1, kNT);
-        if (tid == 0) refill<T>(P, smem, consumed);
+        if (tid == 0) refill<T>(cs.consumed);
     }
 }
 

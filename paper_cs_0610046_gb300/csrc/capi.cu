@@ -74,7 +74,13 @@ int elem_size(mmf_dtype dt) {
     return 0;
 }
 
-int tile_of(mmf_dtype dt) { return dt == MMF_F64 ? 2048 : 4096; }
+int tile_of(mmf_dtype dt) {
+    switch (dt) {
+        case MMF_F32: return 2048;
+        case MMF_F64: return 1024;
+        default: return 4096;
+    }
+}
 
 // Translate (n, w_or_r, mode) into the kernel's series description.
 mmf_status make_series(int64_t n, int64_t w_or_r, mmf_mode mode, mmf_dtype dt, SeriesDesc *sd) {
@@ -133,15 +139,15 @@ int64_t mmf_output_length(int64_t n, int64_t w_or_r, mmf_mode mode) {
 mmf_status mmf_filter1d_ex(const void *d_in, int64_t n, int64_t w_or_r, mmf_dtype dtype, mmf_mode mode,
                            void *d_max, void *d_min, void *stream, mmf_kernel kernel) {
     if (elem_size(dtype) == 0) return set_error(MMF_EINVAL, "unknown dtype %d", (int)dtype);
-    if (!d_max && !d_min) return set_error(MMF_EINVAL, "both outputs are NULL");
-    if (n > 0 && !d_in) return set_error(MMF_EINVAL, "NULL input with n = %lld", (long long)n);
     SeriesDesc sd;
     mmf_status st = make_series(n, w_or_r, mode, dtype, &sd);
     if (st != MMF_OK) return st;
+    if (sd.n_out == 0) return MMF_OK;  // nothing to write (empty outputs may be NULL)
+    if (!d_max && !d_min) return set_error(MMF_EINVAL, "both outputs are NULL");
+    if (!d_in) return set_error(MMF_EINVAL, "NULL input with n = %lld", (long long)n);
     const int esz = elem_size(dtype);
     if (((uintptr_t)d_in % esz) || ((uintptr_t)d_max % esz) || ((uintptr_t)d_min % esz))
         return set_error(MMF_EINVAL, "pointers must be aligned to the element size");
-    if (sd.n_out == 0) return MMF_OK;
     LaunchCtx ctx;
     st = get_ctx(stream, &ctx);
     if (st != MMF_OK) return st;

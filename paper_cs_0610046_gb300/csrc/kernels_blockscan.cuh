@@ -6,23 +6,35 @@ namespace mmf {
 
 template <typename T> size_t blockscan_smem_bytes() { return Geo<T>::smem_bytes; }
 
-template <typename T> static cudaError_t prepare_blockscan(int device) {
-    static bool done[64] = {false};
-    if (device >= 0 && device < 64 && done[device]) return cudaSuccess;
+// Sets the shared-memory attribute once per device and returns the number of
+// resident CTAs per SM.
+template <typename T> static cudaError_t prepare_blockscan(int device, int *per_sm) {
+    static int occ[64] = {0};
+    if (device >= 0 && device < 64 && occ[device] > 0) {
+        *per_sm = occ[device];
+        return cudaSuccess;
+    }
     cudaError_t e = cudaFuncSetAttribute(blockscan_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Geo<T>::smem_bytes);
-    if (e == cudaSuccess && device >= 0 && device < 64) done[device] = true;
-    return e;
+    if (e != cudaSuccess) return e;
+    int k = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, blockscan_kernel<T>, kThreads, Geo<T>::smem_bytes);
+    if (e != cudaSuccess) return e;
+    if (k < 1) k = 1;
+    if (device >= 0 && device < 64) occ[device] = k;
+    *per_sm = k;
+    return cudaSuccess;
 }
 
 template <typename T>
 cudaError_t blockscan_1d(const LaunchCtx &ctx, const void *in, const SeriesDesc &sd, void *omax, void *omin) {
     using G = Geo<T>;
     if (sd.n_out <= 0) return cudaSuccess;
-    cudaError_t e = prepare_blockscan<T>(ctx.device);
+    int per_sm = 1;
+    cudaError_t e = prepare_blockscan<T>(ctx.device, &per_sm);
     if (e != cudaSuccess) return e;
     const int64_t tiles = (sd.n_out + G::T_ - 1) / G::T_;
-    const int64_t gmax = ctx.sms > 0 ? ctx.sms : 1;
+    const int64_t gmax = (int64_t)(ctx.sms > 0 ? ctx.sms : 1) * per_sm;
     const int64_t seg_tiles = (tiles + gmax - 1) / gmax;
     const int64_t n_items = (tiles + seg_tiles - 1) / seg_tiles;
     BlockScanParams P{};
@@ -45,8 +57,10 @@ cudaError_t blockscan_table(const LaunchCtx &ctx, const void *in, void *omax, vo
                             const ItemDesc *d_items, int64_t n_items, int *d_ticket, int grid) {
     using G = Geo<T>;
     if (n_items <= 0) return cudaSuccess;
-    cudaError_t e = prepare_blockscan<T>(ctx.device);
+    int per_sm = 1;
+    cudaError_t e = prepare_blockscan<T>(ctx.device, &per_sm);
     if (e != cudaSuccess) return e;
+    if (grid <= 0) grid = (ctx.sms > 0 ? ctx.sms : 1) * per_sm;
     BlockScanParams P{};
     P.in = in;
     P.out_max = omax;

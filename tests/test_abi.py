@@ -57,7 +57,7 @@ def test_argument_errors_need_no_gpu(lib):
                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     f.restype = ctypes.c_int
     lib.mmf_last_error.restype = ctypes.c_char_p
-    assert f(None, 10, 3, 0, 0, None, None, None) == 1          # both outputs NULL
+    assert f(16, 10, 3, 0, 0, None, None, None) == 1            # both outputs NULL
     assert f(None, 10, 3, 0, 0, 16, None, None) == 1            # NULL input, n > 0
     assert f(16, 10, 0, 0, 0, 16, None, None) == 1              # w < 1
     assert f(16, -1, 3, 0, 0, 16, None, None) == 1              # n < 0
@@ -65,7 +65,8 @@ def test_argument_errors_need_no_gpu(lib):
     assert f(16, 10, 3, 0, 7, 16, None, None) == 1              # bad mode
     assert f(18, 10, 3, 0, 0, 16, None, None) == 1              # misaligned f32 pointer
     assert f(16, 2, 3, 0, 0, 16, 32, None) == 0                 # w > n: nothing to do
-    assert f(16, 10 ** 9, 4096 * 2000, 0, 0, 16, None, None) == 7  # window beyond the limit
+    assert f(None, 0, 3, 0, 0, None, None, None) == 0           # empty input
+    assert f(16, 10 ** 9, 2048 * 1100, 0, 0, 16, None, None) == 7  # window beyond the limit
     assert len(lib.mmf_last_error()) > 0
 
 

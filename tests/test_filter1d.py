@@ -51,13 +51,19 @@ def _check(mmf, a, w, mode="valid", kernel="auto"):
         raise AssertionError(f"min mismatch w={w} n={a.size}: {bad.size} bad, first {bad[:8]}")
 
 
-WINDOWS = [1, 2, 3, 4, 5, 8, 9, 16, 17, 31, 32, 33, 101, 511, 512, 513, 1001, 1024, 1025,
+WINDOWS = [1, 2, 3, 4, 5, 8, 9, 16, 17, 31, 32, 33, 101, 255, 256, 257, 258, 511, 512, 513, 1001, 1024, 1025,
            2047, 2048, 2049, 4095, 4096, 4097, 4098, 8193, 12289]
 
 
 @pytest.mark.parametrize("w", WINDOWS)
 def test_f32_windows_random_walk(mmf, w):
     a = synth.random_walk(61_237, seed=w, dtype=np.float32)
+    _check(mmf, a, w)
+
+
+@pytest.mark.parametrize("w", [2, 4, 5, 9, 33, 127, 128, 129, 130, 1023, 1024, 1025, 1026, 2049, 3075])
+def test_f64_windows(mmf, w):
+    a = synth.piecewise_monotone(23_457, seed=w, dtype=np.float64)
     _check(mmf, a, w)
 
 
