@@ -175,7 +175,7 @@ struct BlockScanParams {
 constexpr int kConsumerWarps = 8;
 constexpr int kNT = kConsumerWarps * 32;
 constexpr int kThreads = kNT;  // thread 0 also issues the copies
-constexpr int kStages = 5;
+constexpr int kStages = 4;  // power of two
 constexpr int kQCap = 1024 + 8;  // tile-aggregate ring (>= max tiles per window + 2)
 constexpr int kMaxItemSpan = 1 << 30;  // relative positions of an item fit in int32
 
@@ -194,9 +194,13 @@ extern __shared__ __align__(128) uint8_t bs_smem[];
 
 // Copy-issue state of thread 0 (in shared memory: costs other threads nothing).
 struct ProdState {
-    const void *in;
-    int64_t n, p0, item, k, issued;
+    const void *in;     // series base
+    int64_t n, p0;      // series length; input position of tile 0
+    int64_t item, k;    // current item; static round-robin cursor
+    uintptr_t base0;    // address of position p0
+    int32_t issued;     // loads issued so far (all items)
     int32_t q, caseB, ok, l, nloads, finished;
+    int32_t fast_lo, fast_hi;  // tiles x in [fast_lo, fast_hi) are whole, aligned copies
 };
 
 template <typename T> struct Geo {
@@ -261,8 +265,9 @@ template <typename T> struct ItemPlan {
     int ok;
 };
 
+// `want_mode` >= 0 rejects items of another block mode.
 template <typename T>
-__device__ __forceinline__ ItemPlan<T> make_plan(const BlockScanParams &P, int64_t item) {
+__device__ __forceinline__ ItemPlan<T> make_plan(const BlockScanParams &P, int64_t item, int want_mode) {
     using G = Geo<T>;
     ItemPlan<T> ip;
     SeriesDesc sd;
@@ -300,12 +305,12 @@ __device__ __forceinline__ ItemPlan<T> make_plan(const BlockScanParams &P, int64
     }
     const int64_t span = oe - ob;
     ip.NC = span > 0 ? (int)((span + G::T_ - 1) >> G::LGT) : 0;
-    ip.ok = (s >= 0) && (ip.q + 2 <= kQCap) && span >= 0 && span + s + 2 * (int64_t)G::T_ <= kMaxItemSpan;
+    ip.ok = (s >= 0) && (ip.q + 2 <= kQCap) && span >= 0 && span + s + 2 * (int64_t)G::T_ <= kMaxItemSpan &&
+            (want_mode < 0 || want_mode == ip.mode);
     return ip;
 }
 
-// Loads of one item, in order: prologue tiles x = (caseB ? 1 : 0) .. q, then
-// per output tile c: K tile c+q+1 and, when caseB, J tile c.
+// Number of loads of one item (see load_tile for their order).
 __device__ __forceinline__ int item_loads(int ok, int caseB, int q, int NC) {
     if (!ok) return 1;  // a rejected item is one empty stage
     return (caseB ? q : 1) + NC * (caseB ? 2 : 1);
@@ -333,29 +338,48 @@ __device__ __forceinline__ bool next_item(const BlockScanParams &P, ProdState &p
     return item < P.n_items;
 }
 
+// Tile index of load l of an item: prologue tiles (caseB ? 1 : 0) .. q, then
+// per output tile c the K tile c+q+1 and, for caseB, the J tile c.
+__device__ __forceinline__ int load_tile(int l, int caseB, int q, bool &keep) {
+    const int pro = caseB ? q : 1;
+    if (l < pro) {
+        keep = caseB;
+        return caseB ? 1 + l : 0;
+    }
+    const int r = l - pro;
+    if (!caseB) {
+        keep = false;
+        return r + q + 1;
+    }
+    const int c = r >> 1;
+    keep = !(r & 1);  // a K tile is read again later as a J tile
+    return (r & 1) ? c : c + q + 1;
+}
+
 // Thread 0 only: issue copies until `consumed + kStages` loads are in flight.
 // Stages consumed before the caller's barrier are free, so this never waits.
-template <typename T>
-__device__ __noinline__ void refill(int64_t consumed) {
+template <typename T, int MODE>
+__device__ __noinline__ void refill(int consumed) {
     using G = Geo<T>;
     using S = Smem<T>;
     const BlockScanParams &P = S::params();
     uint64_t *full_bar = S::bar();
     StageMeta *meta = S::meta();
     ProdState &ps = *S::prod();
-    while (!ps.finished && ps.issued < consumed + kStages) {
-        const int stage = (int)(ps.issued % kStages);
+    int issued = ps.issued, l = ps.l, nloads = ps.nloads;
+    while (issued < consumed + kStages && !ps.finished) {
+        const int stage = issued & (kStages - 1);
         StageMeta &m = meta[stage];
-        if (ps.l >= ps.nloads) {
+        if (l >= nloads) {
             int64_t item;
             if (!next_item<T>(P, ps, item)) {
                 m.item = -1;  // end marker: an empty phase
                 mbar_arrive_expect_tx(&full_bar[stage], 0);
                 ps.finished = 1;
-                ps.issued++;
+                issued++;
                 break;
             }
-            ItemPlan<T> ip = make_plan<T>(P, item);
+            ItemPlan<T> ip = make_plan<T>(P, item, MODE);
             if (!ip.ok) report_error(P.status, kErrBadItem);
             ps.in = ip.in;
             ps.n = ip.n;
@@ -364,57 +388,72 @@ __device__ __noinline__ void refill(int64_t consumed) {
             ps.caseB = ip.caseB;
             ps.ok = ip.ok;
             ps.item = item;
-            ps.nloads = item_loads(ip.ok, ip.caseB, ip.q, ip.NC);
-            ps.l = 0;
+            nloads = item_loads(ip.ok, ip.caseB, ip.q, ip.NC);
+            l = 0;
+            // Tiles wholly inside [0, n) with a 16-byte aligned start.
+            const uintptr_t b0 = (uintptr_t)(ip.in + ip.p0);
+            ps.base0 = b0;
+            int flo = 0, fhi = 0;
+            if ((b0 & 15) == 0) {
+                const int64_t lo_t = ip.p0 >= 0 ? 0 : (-ip.p0 + G::T_ - 1) / G::T_;
+                const int64_t hi_t = ip.n - ip.p0 >= G::T_ ? (ip.n - ip.p0) / G::T_ : 0;
+                flo = (int)lo_t;
+                fhi = (int)(hi_t > lo_t ? hi_t : lo_t);
+            }
+            ps.fast_lo = flo;
+            ps.fast_hi = fhi;
         }
-        m.item = ps.l == 0 ? ps.item : -2;
-        uint32_t bytes = 0;
-        void *dst = nullptr;
-        const void *src = nullptr;
+        m.item = l == 0 ? ps.item : -2;
         bool keep = false;
-        if (ps.ok) {
-            int x;
-            const int pro = ps.caseB ? ps.q : 1;
-            if (ps.l < pro) {
-                x = ps.caseB ? 1 + ps.l : 0;
-                keep = ps.caseB;
-            } else {
-                const int r = ps.l - pro;
-                const int c = ps.caseB ? r >> 1 : r;
-                const bool jload = ps.caseB && (r & 1);
-                x = jload ? c : c + ps.q + 1;
-                keep = ps.caseB && !jload;  // read again later as a J tile
-            }
-            // The 16-byte aligned interior of [a, a+T) clipped to [0, n).
-            const int64_t a = ps.p0 + (int64_t)x * G::T_;
-            const intptr_t base = (intptr_t)ps.in;
-            const intptr_t ga = base + a * (intptr_t)sizeof(T);
-            const intptr_t gal = ga & ~(intptr_t)15;
-            const int64_t lo = a > 0 ? a : 0;
-            const int64_t hi = a + G::T_ < ps.n ? a + G::T_ : ps.n;
-            int64_t ilo = lo, ihi = lo;
-            if (hi > lo) {
-                const intptr_t gbu = (base + lo * (intptr_t)sizeof(T) + 15) & ~(intptr_t)15;
-                const intptr_t geu = (base + hi * (intptr_t)sizeof(T)) & ~(intptr_t)15;
-                if (geu > gbu) {
-                    bytes = (uint32_t)(geu - gbu);
-                    src = reinterpret_cast<const void *>(gbu);
-                    dst = S::stage(stage) + (size_t)(gbu - gal);
-                    ilo = (gbu - base) / (intptr_t)sizeof(T);
-                    ihi = (geu - base) / (intptr_t)sizeof(T);
+        const int x = ps.ok ? load_tile(l, ps.caseB, ps.q, keep) : 0;
+        const uint64_t pol = keep ? policy_evict_last() : policy_evict_first();
+        if (ps.ok && x >= ps.fast_lo && x < ps.fast_hi) {
+            // Fast path: a whole, aligned tile.
+            m.shift = 0;
+            m.inner = 1;
+            const uint32_t bytes = (uint32_t)(G::T_ * sizeof(T));
+            mbar_arrive_expect_tx(&full_bar[stage], bytes);
+            tma_load_1d(S::stage(stage), reinterpret_cast<const void *>(ps.base0 + (uintptr_t)x * bytes), bytes,
+                        &full_bar[stage], pol);
+        } else {
+            uint32_t bytes = 0;
+            void *dst = nullptr;
+            const void *src = nullptr;
+            if (ps.ok) {
+                // The 16-byte aligned interior of [a, a+T) clipped to [0, n).
+                const int64_t a = ps.p0 + (int64_t)x * G::T_;
+                const intptr_t base = (intptr_t)ps.in;
+                const intptr_t ga = base + a * (intptr_t)sizeof(T);
+                const intptr_t gal = ga & ~(intptr_t)15;
+                const int64_t lo = a > 0 ? a : 0;
+                const int64_t hi = a + G::T_ < ps.n ? a + G::T_ : ps.n;
+                int64_t ilo = lo, ihi = lo;
+                if (hi > lo) {
+                    const intptr_t gbu = (base + lo * (intptr_t)sizeof(T) + 15) & ~(intptr_t)15;
+                    const intptr_t geu = (base + hi * (intptr_t)sizeof(T)) & ~(intptr_t)15;
+                    if (geu > gbu) {
+                        bytes = (uint32_t)(geu - gbu);
+                        src = reinterpret_cast<const void *>(gbu);
+                        dst = S::stage(stage) + (size_t)(gbu - gal);
+                        ilo = (gbu - base) / (intptr_t)sizeof(T);
+                        ihi = (geu - base) / (intptr_t)sizeof(T);
+                    }
                 }
+                m.a = a;
+                m.int_lo = ilo;
+                m.int_hi = ihi;
+                m.shift = (int)((ga - gal) / (intptr_t)sizeof(T));
+                m.inner = (ilo <= a && a + G::T_ <= ihi) ? 1 : 0;
             }
-            m.a = a;
-            m.int_lo = ilo;
-            m.int_hi = ihi;
-            m.shift = (int)((ga - gal) / (intptr_t)sizeof(T));
-            m.inner = (ilo <= a && a + G::T_ <= ihi) ? 1 : 0;
+            mbar_arrive_expect_tx(&full_bar[stage], bytes);
+            if (bytes) tma_load_1d(dst, src, bytes, &full_bar[stage], pol);
         }
-        mbar_arrive_expect_tx(&full_bar[stage], bytes);
-        if (bytes) tma_load_1d(dst, src, bytes, &full_bar[stage], keep ? policy_evict_last() : policy_evict_first());
-        ps.l++;
-        ps.issued++;
+        l++;
+        issued++;
     }
+    ps.issued = issued;
+    ps.l = l;
+    ps.nloads = nloads;
 }
 
 // ------------------------------------------------------------ consumer side
@@ -422,7 +461,7 @@ __device__ __noinline__ void refill(int64_t consumed) {
 //   0: s < V      B = 2^floor(log2 s) < V: blocks inside a thread
 //   1: s < W      B = 2^floor(log2 s) in [V, W/2]: blocks of 2..16 lanes
 //   2: s >= W     B = W: one block per warp; for s >= T also tile aggregates
-template <typename T>
+template <typename T, int KMODE>
 struct Consumer {
     using R = typename Elem<T>::R;
     using Pair = typename Elem<T>::Pair;
@@ -432,14 +471,14 @@ struct Consumer {
     static constexpr int T_ = G::T_;
 
     int tid, lane, warp;
-    int64_t consumed = 0;
+    int consumed = 0;
     StageCursor cur;
     bool failed = false;
 
     // CTA barrier; afterwards thread 0 refills the stages consumed before it.
     __device__ __forceinline__ void sync() {
         named_bar_sync(1, kNT);
-        if (tid == 0) refill<T>(consumed);
+        if (tid == 0) refill<T, KMODE>(consumed);
     }
 
     // Read the next staged tile into registers.  Max-side and min-side copies
@@ -782,7 +821,9 @@ struct Consumer {
     }
 };
 
-template <typename T>
+// One instantiation per block mode keeps each one within 128 registers (two
+// CTAs per SM); an item whose mode differs is rejected (kErrBadItem).
+template <typename T, int MODE>
 __global__ void __launch_bounds__(kThreads, Elem<T>::V == 16 ? 1 : 2) blockscan_kernel(const BlockScanParams P) {
     using S = Smem<T>;
     const int tid = threadIdx.x;
@@ -795,16 +836,18 @@ __global__ void __launch_bounds__(kThreads, Elem<T>::V == 16 ? 1 : 2) blockscan_
         ps.n = ps.p0 = 0;
         ps.item = -1;
         ps.k = 0;
+        ps.base0 = 0;
         ps.issued = 0;
         ps.q = ps.caseB = ps.ok = 0;
         ps.l = 0;
         ps.nloads = 0;
         ps.finished = 0;
-        refill<T>(0);
+        ps.fast_lo = ps.fast_hi = 0;
+        refill<T, MODE>(0);
     }
     __syncthreads();
 
-    Consumer<T> cs;
+    Consumer<T, MODE> cs;
     cs.tid = tid;
     cs.lane = tid & 31;
     cs.warp = tid >> 5;
@@ -816,21 +859,17 @@ __global__ void __launch_bounds__(kThreads, Elem<T>::V == 16 ? 1 : 2) blockscan_
         }
         const int64_t item = S::meta()[cs.cur.stage].item;
         if (item < 0) return;
-        ItemPlan<T> ip = make_plan<T>(P, item);
+        ItemPlan<T> ip = make_plan<T>(P, item, MODE);
         if (!ip.ok) {
             cs.cur.advance();
             ++cs.consumed;
-        } else if (ip.mode == 2) {
-            cs.template run_item<2>(ip);
-        } else if (ip.mode == 1) {
-            cs.template run_item<1>(ip);
         } else {
-            cs.template run_item<0>(ip);
+            cs.template run_item<MODE>(ip);
         }
         if (cs.failed) return;
         // Item boundary: the ring may be reused and consumed stages refilled.
         named_bar_sync(1, kNT);
-        if (tid == 0) refill<T>(cs.consumed);
+        if (tid == 0) refill<T, MODE>(cs.consumed);
     }
 }
 

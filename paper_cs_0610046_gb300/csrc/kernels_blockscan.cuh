@@ -8,17 +8,17 @@ template <typename T> size_t blockscan_smem_bytes() { return Geo<T>::smem_bytes;
 
 // Sets the shared-memory attribute once per device and returns the number of
 // resident CTAs per SM.
-template <typename T> static cudaError_t prepare_blockscan(int device, int *per_sm) {
+template <typename T, int MODE> static cudaError_t prepare_blockscan(int device, int *per_sm) {
     static int occ[64] = {0};
     if (device >= 0 && device < 64 && occ[device] > 0) {
         *per_sm = occ[device];
         return cudaSuccess;
     }
-    cudaError_t e = cudaFuncSetAttribute(blockscan_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(blockscan_kernel<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Geo<T>::smem_bytes);
     if (e != cudaSuccess) return e;
     int k = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, blockscan_kernel<T>, kThreads, Geo<T>::smem_bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, blockscan_kernel<T, MODE>, kThreads, Geo<T>::smem_bytes);
     if (e != cudaSuccess) return e;
     if (k < 1) k = 1;
     if (device >= 0 && device < 64) occ[device] = k;
@@ -26,12 +26,43 @@ template <typename T> static cudaError_t prepare_blockscan(int device, int *per_
     return cudaSuccess;
 }
 
+// Block mode of window w (see the kernel): 0, 1 or 2.
+template <typename T> int block_mode(int64_t w) {
+    const int64_t s = w - 1;
+    if (s >= 32 * (int64_t)Geo<T>::V) return 2;
+    return s >= Geo<T>::V ? 1 : 0;
+}
+
+template <typename T, int MODE>
+static void launch_bs(const BlockScanParams &P, int grid, cudaStream_t st) {
+    blockscan_kernel<T, MODE><<<(unsigned)grid, kThreads, Geo<T>::smem_bytes, st>>>(P);
+}
+
+template <typename T>
+static cudaError_t prepare_mode(int mode, int device, int *per_sm) {
+    switch (mode) {
+        case 0: return prepare_blockscan<T, 0>(device, per_sm);
+        case 1: return prepare_blockscan<T, 1>(device, per_sm);
+        default: return prepare_blockscan<T, 2>(device, per_sm);
+    }
+}
+
+template <typename T>
+static void launch_mode(int mode, const BlockScanParams &P, int grid, cudaStream_t st) {
+    switch (mode) {
+        case 0: launch_bs<T, 0>(P, grid, st); break;
+        case 1: launch_bs<T, 1>(P, grid, st); break;
+        default: launch_bs<T, 2>(P, grid, st); break;
+    }
+}
+
 template <typename T>
 cudaError_t blockscan_1d(const LaunchCtx &ctx, const void *in, const SeriesDesc &sd, void *omax, void *omin) {
     using G = Geo<T>;
     if (sd.n_out <= 0) return cudaSuccess;
+    const int mode = block_mode<T>(sd.w);
     int per_sm = 1;
-    cudaError_t e = prepare_blockscan<T>(ctx.device, &per_sm);
+    cudaError_t e = prepare_mode<T>(mode, ctx.device, &per_sm);
     if (e != cudaSuccess) return e;
     const int64_t tiles = (sd.n_out + G::T_ - 1) / G::T_;
     const int64_t gmax = (int64_t)(ctx.sms > 0 ? ctx.sms : 1) * per_sm;
@@ -48,17 +79,17 @@ cudaError_t blockscan_1d(const LaunchCtx &ctx, const void *in, const SeriesDesc 
     P.n_items = n_items;
     P.ticket = nullptr;
     P.status = ctx.status;
-    blockscan_kernel<T><<<(unsigned)n_items, kThreads, G::smem_bytes, ctx.stream>>>(P);
+    launch_mode<T>(mode, P, (int)n_items, ctx.stream);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t blockscan_table(const LaunchCtx &ctx, const void *in, void *omax, void *omin, const SeriesDesc *d_series,
-                            const ItemDesc *d_items, int64_t n_items, int *d_ticket, int grid) {
-    using G = Geo<T>;
+cudaError_t blockscan_table(const LaunchCtx &ctx, int mode, const void *in, void *omax, void *omin,
+                            const SeriesDesc *d_series, const ItemDesc *d_items, int64_t n_items, int *d_ticket,
+                            int grid) {
     if (n_items <= 0) return cudaSuccess;
     int per_sm = 1;
-    cudaError_t e = prepare_blockscan<T>(ctx.device, &per_sm);
+    cudaError_t e = prepare_mode<T>(mode, ctx.device, &per_sm);
     if (e != cudaSuccess) return e;
     if (grid <= 0) grid = (ctx.sms > 0 ? ctx.sms : 1) * per_sm;
     BlockScanParams P{};
@@ -71,7 +102,7 @@ cudaError_t blockscan_table(const LaunchCtx &ctx, const void *in, void *omax, vo
     P.n_items = n_items;
     P.ticket = d_ticket;
     P.status = ctx.status;
-    blockscan_kernel<T><<<(unsigned)grid, kThreads, G::smem_bytes, ctx.stream>>>(P);
+    launch_mode<T>(mode, P, grid, ctx.stream);
     return cudaGetLastError();
 }
 
@@ -81,5 +112,6 @@ cudaError_t blockscan_table(const LaunchCtx &ctx, const void *in, void *omax, vo
     template size_t mmf::blockscan_smem_bytes<T>();                                                            \
     template cudaError_t mmf::blockscan_1d<T>(const LaunchCtx &, const void *, const SeriesDesc &, void *,      \
                                                void *);                                                         \
-    template cudaError_t mmf::blockscan_table<T>(const LaunchCtx &, const void *, void *, void *,              \
-                                                  const SeriesDesc *, const ItemDesc *, int64_t, int *, int);
+    template cudaError_t mmf::blockscan_table<T>(const LaunchCtx &, int, const void *, void *, void *,         \
+                                                  const SeriesDesc *, const ItemDesc *, int64_t, int *, int); \
+    template int mmf::block_mode<T>(int64_t);

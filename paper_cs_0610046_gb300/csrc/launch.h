@@ -19,11 +19,16 @@ struct LaunchCtx {
 template <typename T>
 cudaError_t blockscan_1d(const LaunchCtx &ctx, const void *in, const SeriesDesc &sd, void *omax, void *omin);
 
-// Table-driven launch (batched plans): items pulled from an atomic ticket.
+// Table-driven launch (batched plans): items of one block mode, pulled from
+// an atomic ticket (or round-robin if d_ticket is null).  grid <= 0: one
+// persistent wave.
 template <typename T>
-cudaError_t blockscan_table(const LaunchCtx &ctx, const void *in, void *omax, void *omin,
+cudaError_t blockscan_table(const LaunchCtx &ctx, int mode, const void *in, void *omax, void *omin,
                             const SeriesDesc *d_series, const ItemDesc *d_items, int64_t n_items,
                             int *d_ticket, int grid);
+
+// Block mode (0, 1, 2) the kernel uses for window w.
+template <typename T> int block_mode(int64_t w);
 
 template <typename T> size_t blockscan_smem_bytes();
 int blockscan_tile(int dtype);
