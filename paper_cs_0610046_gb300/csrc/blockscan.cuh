@@ -174,33 +174,25 @@ struct BlockScanParams {
 
 constexpr int kConsumerWarps = 8;
 constexpr int kNT = kConsumerWarps * 32;
-constexpr int kThreads = kNT;  // thread 0 also issues the copies
-constexpr int kStages = 4;  // power of two
-constexpr int kQCap = 1024 + 8;  // tile-aggregate ring (>= max tiles per window + 2)
+constexpr int kThreads = kNT;
+constexpr int kStages = 4;             // per-warp slice stages (power of two)
+constexpr int kQCap = 1024 + 8;        // tile-aggregate ring (>= max tiles per window + 2)
+constexpr int kQueue = 16;             // upcoming item ids under dynamic scheduling
 constexpr int kMaxItemSpan = 1 << 30;  // relative positions of an item fit in int32
-
-// Metadata of one staged tile, written by thread 0 with the copy.
-struct StageMeta {
-    int64_t item;    // item index on the item's first load; -2 otherwise; -1 = end
-    int64_t a;       // first input position of the tile (series-relative)
-    int64_t int_lo;  // positions [int_lo, int_hi) were copied by the TMA engine
-    int64_t int_hi;
-    int32_t shift;   // element offset of position a within its 16-byte chunk
-    int32_t inner;   // 1 if every position of the tile is in [int_lo, int_hi)
-};
 
 // Dynamic shared memory of the block-scan kernel (layout in Geo<T>).
 extern __shared__ __align__(128) uint8_t bs_smem[];
 
-// Copy-issue state of thread 0 (in shared memory: costs other threads nothing).
-struct ProdState {
-    const void *in;     // series base
-    int64_t n, p0;      // series length; input position of tile 0
-    int64_t item, k;    // current item; static round-robin cursor
-    uintptr_t base0;    // address of position p0
-    int32_t issued;     // loads issued so far (all items)
-    int32_t q, caseB, ok, l, nloads, finished;
-    int32_t fast_lo, fast_hi;  // tiles x in [fast_lo, fast_hi) are whole, aligned copies
+// Copy-issue state of one warp (its lane 0 issues the warp's slice of every
+// tile load).  Kept in shared memory so that it costs no registers.
+struct WarpIssue {
+    const void *in;  // series base of the item being issued
+    int64_t n, p0;   // its length and the input position of its tile 0
+    int32_t seq;     // its sequence number among this CTA's items
+    int32_t l;       // next load within it
+    int32_t nloads;  // its number of loads; -1 once the sequence has ended
+    int32_t q, caseB, ok;
+    int32_t issued;  // loads issued so far by this warp
 };
 
 template <typename T> struct Geo {
@@ -210,38 +202,42 @@ template <typename T> struct Geo {
     static constexpr int LGV = V == 16 ? 4 : (V == 8 ? 3 : 2);
     static constexpr int T_ = kNT * V;  // tile, elements
     static constexpr int LGT = LGV + 8;
+    static constexpr int SLICE = 32 * V;  // elements of a tile read by one warp
     static constexpr int NCH = V * (int)sizeof(T) / 16;  // 16-byte chunks per thread
-    static constexpr int STAGE_BYTES = ((T_ * (int)sizeof(T) + 16 + 127) / 128) * 128;
+    static constexpr int SLICE_BYTES = SLICE * (int)sizeof(T) + 16;  // + room for a 16-byte shift
     static constexpr int RING = 3 * T_;  // logical ring pairs
     static constexpr int RING_PHYS = RING + (RING >> PS) + 16;
     static constexpr size_t rnd(size_t b) { return (b + 127) / 128 * 128; }
-    static constexpr size_t off_stage = 0;
-    static constexpr size_t off_ring = off_stage + (size_t)kStages * STAGE_BYTES;
+    static constexpr size_t off_stage = 0;  // [warp][stage] slices
+    static constexpr size_t off_ring = rnd((size_t)kConsumerWarps * kStages * SLICE_BYTES);
     static constexpr size_t off_ta = off_ring + rnd(RING_PHYS * sizeof(Pair));
     static constexpr size_t off_misc = off_ta + rnd(kQCap * sizeof(Pair));
     static constexpr size_t off_kagg = 0;  // [3 ring slots][8 warps] block aggregates of K tiles
     static constexpr size_t off_jagg = off_kagg + 3 * kConsumerWarps * sizeof(Pair);  // [2][8] of J tiles
-    static constexpr size_t off_bar = rnd(off_jagg + 2 * kConsumerWarps * sizeof(Pair));
-    static constexpr size_t off_meta = off_bar + kStages * 8;
-    static constexpr size_t off_prod = off_meta + kStages * sizeof(StageMeta);
-    static constexpr size_t off_params = rnd(off_prod + sizeof(ProdState));
-    static constexpr size_t misc_bytes = off_params + sizeof(BlockScanParams);
+    static constexpr size_t off_bar = rnd(off_jagg + 2 * kConsumerWarps * sizeof(Pair));  // [warp][stage]
+    static constexpr size_t off_issue = off_bar + kConsumerWarps * kStages * 8;
+    static constexpr size_t off_queue = rnd(off_issue + kConsumerWarps * sizeof(WarpIssue));
+    static constexpr size_t off_params = rnd(off_queue + kQueue * 8 + 16);
+    static constexpr size_t misc_bytes = off_params + 256;
     static constexpr size_t smem_bytes = off_misc + misc_bytes;
 };
-
 // Shared-memory regions (compile-time offsets from the shared window).
 template <typename T> struct Smem {
     using G = Geo<T>;
     using Pair = typename Elem<T>::Pair;
-    __device__ static uint8_t *stage(int s) { return bs_smem + G::off_stage + (size_t)s * G::STAGE_BYTES; }
+    __device__ static uint8_t *slice(int warp, int s) {
+        return bs_smem + G::off_stage + (size_t)(warp * kStages + s) * G::SLICE_BYTES;
+    }
     __device__ static Pair *ring() { return reinterpret_cast<Pair *>(bs_smem + G::off_ring); }
     __device__ static Pair *ta() { return reinterpret_cast<Pair *>(bs_smem + G::off_ta); }
     __device__ static uint8_t *misc() { return bs_smem + G::off_misc; }
     __device__ static Pair *kagg() { return reinterpret_cast<Pair *>(misc() + G::off_kagg); }
     __device__ static Pair *jagg() { return reinterpret_cast<Pair *>(misc() + G::off_jagg); }
-    __device__ static uint64_t *bar() { return reinterpret_cast<uint64_t *>(misc() + G::off_bar); }
-    __device__ static StageMeta *meta() { return reinterpret_cast<StageMeta *>(misc() + G::off_meta); }
-    __device__ static ProdState *prod() { return reinterpret_cast<ProdState *>(misc() + G::off_prod); }
+    __device__ static uint64_t *bar(int warp, int s) {
+        return reinterpret_cast<uint64_t *>(misc() + G::off_bar) + warp * kStages + s;
+    }
+    __device__ static WarpIssue *issue(int warp) { return reinterpret_cast<WarpIssue *>(misc() + G::off_issue) + warp; }
+    __device__ static int64_t *queue() { return reinterpret_cast<int64_t *>(misc() + G::off_queue); }
     __device__ static const BlockScanParams &params() {
         return *reinterpret_cast<const BlockScanParams *>(misc() + G::off_params);
     }
@@ -327,17 +323,6 @@ struct StageCursor {
     }
 };
 
-template <typename T>
-__device__ __forceinline__ bool next_item(const BlockScanParams &P, ProdState &ps, int64_t &item) {
-    if (P.ticket) {
-        item = atomicAdd(P.ticket, 1);
-    } else {
-        item = (int64_t)blockIdx.x + ps.k * gridDim.x;
-        ++ps.k;
-    }
-    return item < P.n_items;
-}
-
 // Tile index of load l of an item: prologue tiles (caseB ? 1 : 0) .. q, then
 // per output tile c the K tile c+q+1 and, for caseB, the J tile c.
 __device__ __forceinline__ int load_tile(int l, int caseB, int q, bool &keep) {
@@ -356,104 +341,98 @@ __device__ __forceinline__ int load_tile(int l, int caseB, int q, bool &keep) {
     return (r & 1) ? c : c + q + 1;
 }
 
-// Thread 0 only: issue copies until `consumed + kStages` loads are in flight.
-// Stages consumed before the caller's barrier are free, so this never waits.
+// How one warp's slice [a, a + SLICE) of a tile reaches shared memory:
+//   0 (fast)    aligned and inside the series: one bulk copy of the slice;
+//   1 (shifted) unaligned but the 16-byte aligned cover lies inside the series:
+//               one bulk copy of the cover, read back at an element shift;
+//   2 (direct)  touches the series edges: threads load their elements.
+struct SliceCopy {
+    int mode;
+    int shift;       // elements (mode 1)
+    uintptr_t src;   // first copied byte
+    uint32_t bytes;  // copied bytes
+};
+
+template <typename T>
+__device__ __forceinline__ SliceCopy slice_copy(const T *in, int64_t n, int64_t a) {
+    using G = Geo<T>;
+    SliceCopy sc;
+    sc.mode = 2;
+    sc.shift = 0;
+    sc.src = 0;
+    sc.bytes = 0;
+    if (a < 0 || a + G::SLICE > n) return sc;
+    const uintptr_t start = (uintptr_t)(in + a);
+    const int sb = (int)(start & 15);
+    if (sb == 0) {
+        sc.mode = 0;
+        sc.src = start;
+        sc.bytes = (uint32_t)(G::SLICE * sizeof(T));
+        return sc;
+    }
+    const uintptr_t al = start - sb;
+    const uintptr_t end = al + (uintptr_t)G::SLICE * sizeof(T) + 16;
+    if (al >= (uintptr_t)in && end <= (uintptr_t)(in + n)) {
+        sc.mode = 1;
+        sc.shift = sb / (int)sizeof(T);
+        sc.src = al;
+        sc.bytes = (uint32_t)(G::SLICE * sizeof(T) + 16);
+    }
+    return sc;
+}
+
+// The CTA's item with sequence number seq (or >= n_items at the end).
+template <typename T>
+__device__ __forceinline__ int64_t item_of(const BlockScanParams &P, int seq) {
+    if (P.ticket) return Smem<T>::queue()[seq & (kQueue - 1)];
+    return (int64_t)blockIdx.x + (int64_t)seq * gridDim.x;
+}
+
+// Lane 0 of `warp`: issue this warp's slice of its next load, if any.
 template <typename T, int MODE>
-__device__ __noinline__ void refill(int consumed) {
+__device__ __noinline__ void issue_next(int warp) {
     using G = Geo<T>;
     using S = Smem<T>;
     const BlockScanParams &P = S::params();
-    uint64_t *full_bar = S::bar();
-    StageMeta *meta = S::meta();
-    ProdState &ps = *S::prod();
-    int issued = ps.issued, l = ps.l, nloads = ps.nloads;
-    while (issued < consumed + kStages && !ps.finished) {
-        const int stage = issued & (kStages - 1);
-        StageMeta &m = meta[stage];
-        if (l >= nloads) {
-            int64_t item;
-            if (!next_item<T>(P, ps, item)) {
-                m.item = -1;  // end marker: an empty phase
-                mbar_arrive_expect_tx(&full_bar[stage], 0);
-                ps.finished = 1;
-                issued++;
-                break;
-            }
-            ItemPlan<T> ip = make_plan<T>(P, item, MODE);
-            if (!ip.ok) report_error(P.status, kErrBadItem);
-            ps.in = ip.in;
-            ps.n = ip.n;
-            ps.p0 = ip.p0;
-            ps.q = ip.q;
-            ps.caseB = ip.caseB;
-            ps.ok = ip.ok;
-            ps.item = item;
-            nloads = item_loads(ip.ok, ip.caseB, ip.q, ip.NC);
-            l = 0;
-            // Tiles wholly inside [0, n) with a 16-byte aligned start.
-            const uintptr_t b0 = (uintptr_t)(ip.in + ip.p0);
-            ps.base0 = b0;
-            int flo = 0, fhi = 0;
-            if ((b0 & 15) == 0) {
-                const int64_t lo_t = ip.p0 >= 0 ? 0 : (-ip.p0 + G::T_ - 1) / G::T_;
-                const int64_t hi_t = ip.n - ip.p0 >= G::T_ ? (ip.n - ip.p0) / G::T_ : 0;
-                flo = (int)lo_t;
-                fhi = (int)(hi_t > lo_t ? hi_t : lo_t);
-            }
-            ps.fast_lo = flo;
-            ps.fast_hi = fhi;
+    WarpIssue &wi = *S::issue(warp);
+    if (wi.nloads < 0) return;
+    while (wi.l >= wi.nloads) {
+        wi.seq++;
+        const int64_t item = item_of<T>(P, wi.seq);
+        if (item >= P.n_items || item < 0) {
+            wi.nloads = -1;
+            return;
         }
-        m.item = l == 0 ? ps.item : -2;
-        bool keep = false;
-        const int x = ps.ok ? load_tile(l, ps.caseB, ps.q, keep) : 0;
-        const uint64_t pol = keep ? policy_evict_last() : policy_evict_first();
-        if (ps.ok && x >= ps.fast_lo && x < ps.fast_hi) {
-            // Fast path: a whole, aligned tile.
-            m.shift = 0;
-            m.inner = 1;
-            const uint32_t bytes = (uint32_t)(G::T_ * sizeof(T));
-            mbar_arrive_expect_tx(&full_bar[stage], bytes);
-            tma_load_1d(S::stage(stage), reinterpret_cast<const void *>(ps.base0 + (uintptr_t)x * bytes), bytes,
-                        &full_bar[stage], pol);
-        } else {
-            uint32_t bytes = 0;
-            void *dst = nullptr;
-            const void *src = nullptr;
-            if (ps.ok) {
-                // The 16-byte aligned interior of [a, a+T) clipped to [0, n).
-                const int64_t a = ps.p0 + (int64_t)x * G::T_;
-                const intptr_t base = (intptr_t)ps.in;
-                const intptr_t ga = base + a * (intptr_t)sizeof(T);
-                const intptr_t gal = ga & ~(intptr_t)15;
-                const int64_t lo = a > 0 ? a : 0;
-                const int64_t hi = a + G::T_ < ps.n ? a + G::T_ : ps.n;
-                int64_t ilo = lo, ihi = lo;
-                if (hi > lo) {
-                    const intptr_t gbu = (base + lo * (intptr_t)sizeof(T) + 15) & ~(intptr_t)15;
-                    const intptr_t geu = (base + hi * (intptr_t)sizeof(T)) & ~(intptr_t)15;
-                    if (geu > gbu) {
-                        bytes = (uint32_t)(geu - gbu);
-                        src = reinterpret_cast<const void *>(gbu);
-                        dst = S::stage(stage) + (size_t)(gbu - gal);
-                        ilo = (gbu - base) / (intptr_t)sizeof(T);
-                        ihi = (geu - base) / (intptr_t)sizeof(T);
-                    }
-                }
-                m.a = a;
-                m.int_lo = ilo;
-                m.int_hi = ihi;
-                m.shift = (int)((ga - gal) / (intptr_t)sizeof(T));
-                m.inner = (ilo <= a && a + G::T_ <= ihi) ? 1 : 0;
-            }
-            mbar_arrive_expect_tx(&full_bar[stage], bytes);
-            if (bytes) tma_load_1d(dst, src, bytes, &full_bar[stage], pol);
-        }
-        l++;
-        issued++;
+        ItemPlan<T> ip = make_plan<T>(P, item, MODE);
+        if (!ip.ok && warp == 0) report_error(P.status, kErrBadItem);
+        wi.in = ip.in;
+        wi.n = ip.n;
+        wi.p0 = ip.p0;
+        wi.q = ip.q;
+        wi.caseB = ip.caseB;
+        wi.ok = ip.ok;
+        wi.nloads = item_loads(ip.ok, ip.caseB, ip.q, ip.NC);
+        wi.l = 0;
     }
-    ps.issued = issued;
-    ps.l = l;
-    ps.nloads = nloads;
+    const int stage = wi.issued & (kStages - 1);
+    uint64_t *bar = S::bar(warp, stage);
+    uint32_t bytes = 0;
+    if (wi.ok) {
+        bool keep = false;
+        const int x = load_tile(wi.l, wi.caseB, wi.q, keep);
+        const int64_t a = wi.p0 + (int64_t)x * G::T_ + (int64_t)warp * G::SLICE;
+        const SliceCopy sc = slice_copy<T>(reinterpret_cast<const T *>(wi.in), wi.n, a);
+        if (sc.mode != 2) {
+            bytes = sc.bytes;
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(bar, bytes);
+            tma_load_1d(S::slice(warp, stage), reinterpret_cast<const void *>(sc.src), bytes, bar,
+                        keep ? policy_evict_last() : policy_evict_first());
+        }
+    }
+    if (bytes == 0) mbar_arrive_expect_tx(bar, 0);
+    wi.l++;
+    wi.issued++;
 }
 
 // ------------------------------------------------------------ consumer side
@@ -471,67 +450,58 @@ struct Consumer {
     static constexpr int T_ = G::T_;
 
     int tid, lane, warp;
-    int consumed = 0;
     StageCursor cur;
     bool failed = false;
 
-    // CTA barrier; afterwards thread 0 refills the stages consumed before it.
-    __device__ __forceinline__ void sync() {
-        named_bar_sync(1, kNT);
-        if (tid == 0) refill<T, KMODE>(consumed);
-    }
+    // CTA barrier (the P ring and block aggregates are shared by all warps).
+    __device__ __forceinline__ void sync() { named_bar_sync(1, kNT); }
 
-    // Read the next staged tile into registers.  Max-side and min-side copies
-    // differ only at positions outside [0, n), which hold identities.
-    __device__ __forceinline__ bool read_tile(const ItemPlan<T> &ip, R (&xm)[V], R (&xn)[V]) {
-        if (!mbar_wait_bounded(&S::bar()[cur.stage], cur.phase)) {
+    // Read this thread's V elements of input tile x of the item from the
+    // warp's slice stage, then let lane 0 refill the stage with the warp's
+    // next load.  Max-side and min-side copies differ only at positions
+    // outside [0, n), which hold identities.
+    __device__ __forceinline__ bool read_tile(const ItemPlan<T> &ip, int x, R (&xm)[V], R (&xn)[V]) {
+        if (!mbar_wait_bounded(S::bar(warp, cur.stage), cur.phase)) {
             report_error(S::params().status, kErrWaitTimeout);
             failed = true;
             return false;
         }
-        const StageMeta &m = S::meta()[cur.stage];
-        const int shift = m.shift;
-        const int inner = m.inner;
-        const uint8_t *sb = S::stage(cur.stage);
-        R xv[V];
-        if (shift == 0) {
-            // Aligned tile: 16-byte vector reads of the thread's V elements.
+        const int64_t a = ip.p0 + (int64_t)x * T_ + (int64_t)warp * G::SLICE;
+        const SliceCopy sc = slice_copy<T>(ip.in, ip.n, a);
+        const uint8_t *sb = S::slice(warp, cur.stage);
+        if (sc.mode == 0) {
             uint32_t wd[4 * G::NCH];
-            const uint4 *p4 = reinterpret_cast<const uint4 *>(sb + (size_t)tid * V * sizeof(T));
+            const uint4 *p4 = reinterpret_cast<const uint4 *>(sb + (size_t)lane * V * sizeof(T));
 #pragma unroll
             for (int c = 0; c < G::NCH; ++c) {
                 uint4 v = p4[c];
                 wd[4 * c] = v.x; wd[4 * c + 1] = v.y; wd[4 * c + 2] = v.z; wd[4 * c + 3] = v.w;
             }
+            R xv[V];
             ExtractLoop<T, 0, 0, V>::run(wd, xv);
-        } else {
-            // Tile start not 16-byte aligned (unaligned series): element reads.
-            const T *pe = reinterpret_cast<const T *>(sb) + shift + tid * V;
-#pragma unroll
-            for (int i = 0; i < V; ++i) xv[i] = (R)pe[i];
-        }
-        if (inner) {
 #pragma unroll
             for (int i = 0; i < V; ++i) xm[i] = xn[i] = xv[i];
+        } else if (sc.mode == 1) {
+            const T *pe = reinterpret_cast<const T *>(sb) + sc.shift + lane * V;
+#pragma unroll
+            for (int i = 0; i < V; ++i) xm[i] = xn[i] = (R)pe[i];
         } else {
-            const int64_t pt = m.a + (int64_t)tid * V;
-            const int64_t ilo = m.int_lo, ihi = m.int_hi;
+            const int64_t pt = a + (int64_t)lane * V;
 #pragma unroll
             for (int i = 0; i < V; ++i) {
                 const int64_t p = pt + i;
                 if (p < 0 || p >= ip.n) {
                     xm[i] = Elem<T>::lo();
                     xn[i] = Elem<T>::hi();
-                } else if (p < ilo || p >= ihi) {
-                    R v = (R)ip.in[p];
-                    xm[i] = xn[i] = v;
                 } else {
-                    xm[i] = xn[i] = xv[i];
+                    xm[i] = xn[i] = (R)ip.in[p];
                 }
             }
         }
+        __syncwarp();
+        if (lane == 0) issue_next<T, KMODE>(warp);
+        __syncwarp();
         cur.advance();
-        ++consumed;
         return true;
     }
 
@@ -778,7 +748,7 @@ struct Consumer {
         // ---------------- prologue: tile 0 (case A) or tiles 1..q (case B)
         if (!ip.caseB) {
             R pm[V], pn[V];
-            if (!read_tile(ip, pm, pn)) return;
+            if (!read_tile(ip, 0, pm, pn)) return;
 #pragma unroll
             for (int i = 0; i < V; ++i) { Sc_m[i] = pm[i]; Sc_n[i] = pn[i]; }
             scan_tile<MODE>(ip, pm, pn, true, Sc_m, Sc_n, 0, -1);
@@ -786,7 +756,7 @@ struct Consumer {
         } else {
             for (int x = 1; x <= q; ++x) {
                 R pm[V], pn[V];
-                if (!read_tile(ip, pm, pn)) return;
+                if (!read_tile(ip, x, pm, pn)) return;
                 scan_tile<MODE>(ip, pm, pn, false, pm, pn, x % 3, -1);
                 if (x == q) ring_write(x, pm, pn);
                 sync();
@@ -799,12 +769,12 @@ struct Consumer {
         for (int c = 0; c < ip.NC; ++c) {
             R pm[V], pn[V], Sn_m[V], Sn_n[V];
             const int xk = c + q + 1;
-            if (!read_tile(ip, pm, pn)) return;  // K tile c+q+1
+            if (!read_tile(ip, xk, pm, pn)) return;  // K tile c+q+1
             if (!ip.caseB) {
 #pragma unroll
                 for (int i = 0; i < V; ++i) { Sn_m[i] = pm[i]; Sn_n[i] = pn[i]; }
             } else {
-                if (!read_tile(ip, Sn_m, Sn_n)) return;  // J tile c
+                if (!read_tile(ip, c, Sn_m, Sn_n)) return;  // J tile c
             }
             scan_tile<MODE>(ip, pm, pn, true, Sn_m, Sn_n, xk % 3, ip.caseB ? (c & 1) : -1);
             ring_write(xk, pm, pn);
@@ -827,49 +797,62 @@ template <typename T, int MODE>
 __global__ void __launch_bounds__(kThreads, Elem<T>::V == 16 ? 1 : 2) blockscan_kernel(const BlockScanParams P) {
     using S = Smem<T>;
     const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    int fetched = 0;  // thread 0: dynamic tickets fetched
     if (tid == 0) {
         *reinterpret_cast<BlockScanParams *>(S::misc() + Geo<T>::off_params) = P;
-        for (int s = 0; s < kStages; ++s) mbar_init(&S::bar()[s], 1);
+        if (P.ticket) {
+            // Items for sequence numbers 0..kStages: enough for every warp's
+            // prefetch until the first item boundary.
+            for (; fetched <= kStages; ++fetched) S::queue()[fetched & (kQueue - 1)] = atomicAdd(P.ticket, 1);
+        }
+    }
+    if (lane == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(S::bar(warp, s), 1);
+        WarpIssue &wi = *S::issue(warp);
+        wi.in = nullptr;
+        wi.n = wi.p0 = 0;
+        wi.seq = -1;
+        wi.l = wi.nloads = 0;
+        wi.q = wi.caseB = wi.ok = 0;
+        wi.issued = 0;
         fence_mbar_init();
-        ProdState &ps = *S::prod();
-        ps.in = nullptr;
-        ps.n = ps.p0 = 0;
-        ps.item = -1;
-        ps.k = 0;
-        ps.base0 = 0;
-        ps.issued = 0;
-        ps.q = ps.caseB = ps.ok = 0;
-        ps.l = 0;
-        ps.nloads = 0;
-        ps.finished = 0;
-        ps.fast_lo = ps.fast_hi = 0;
-        refill<T, MODE>(0);
     }
     __syncthreads();
+    if (lane == 0)
+        for (int s = 0; s < kStages; ++s) issue_next<T, MODE>(warp);
+    __syncwarp();
 
     Consumer<T, MODE> cs;
     cs.tid = tid;
-    cs.lane = tid & 31;
-    cs.warp = tid >> 5;
-    while (true) {
-        // The first stage of each item carries its index (-1 marks the end).
-        if (!mbar_wait_bounded(&S::bar()[cs.cur.stage], cs.cur.phase)) {
-            report_error(P.status, kErrWaitTimeout);
-            return;
-        }
-        const int64_t item = S::meta()[cs.cur.stage].item;
-        if (item < 0) return;
-        ItemPlan<T> ip = make_plan<T>(P, item, MODE);
+    cs.lane = lane;
+    cs.warp = warp;
+    const BlockScanParams &PS = S::params();
+    for (int seq = 0;; ++seq) {
+        const int64_t item = item_of<T>(PS, seq);
+        if (item >= PS.n_items || item < 0) return;
+        ItemPlan<T> ip = make_plan<T>(PS, item, MODE);
         if (!ip.ok) {
+            // A rejected item occupies one empty stage per warp.
+            if (!mbar_wait_bounded(S::bar(warp, cs.cur.stage), cs.cur.phase)) {
+                report_error(P.status, kErrWaitTimeout);
+                return;
+            }
+            __syncwarp();
+            if (lane == 0) issue_next<T, MODE>(warp);
+            __syncwarp();
             cs.cur.advance();
-            ++cs.consumed;
         } else {
             cs.template run_item<MODE>(ip);
+            if (cs.failed) return;
         }
-        if (cs.failed) return;
-        // Item boundary: the ring may be reused and consumed stages refilled.
+        // Thread 0 fetches the ticket that the prefetch will need next, then
+        // the item boundary frees the ring and publishes the queue.
+        if (tid == 0 && PS.ticket) {
+            S::queue()[fetched & (kQueue - 1)] = atomicAdd(P.ticket, 1);
+            ++fetched;
+        }
         named_bar_sync(1, kNT);
-        if (tid == 0) refill<T, MODE>(cs.consumed);
     }
 }
 
