@@ -186,13 +186,16 @@ extern __shared__ __align__(128) uint8_t bs_smem[];
 // Copy-issue state of one warp (its lane 0 issues the warp's slice of every
 // tile load).  Kept in shared memory so that it costs no registers.
 struct WarpIssue {
-    const void *in;  // series base of the item being issued
+    uintptr_t src0;  // address of this warp's slice of tile 0 of the item being issued
+    const void *in;  // its series base
     int64_t n, p0;   // its length and the input position of its tile 0
+    int32_t fast_lo, fast_hi;  // tiles whose slice is whole and aligned (one plain copy)
     int32_t seq;     // its sequence number among this CTA's items
     int32_t l;       // next load within it
     int32_t nloads;  // its number of loads; -1 once the sequence has ended
     int32_t q, caseB, ok;
     int32_t issued;  // loads issued so far by this warp
+    int32_t smode[kStages];  // per stage: copy mode | shift << 8, for the readers
 };
 
 template <typename T> struct Geo {
@@ -204,22 +207,26 @@ template <typename T> struct Geo {
     static constexpr int LGT = LGV + 8;
     static constexpr int SLICE = 32 * V;  // elements of a tile read by one warp
     static constexpr int NCH = V * (int)sizeof(T) / 16;  // 16-byte chunks per thread
-    static constexpr int SLICE_BYTES = SLICE * (int)sizeof(T) + 16;  // + room for a 16-byte shift
+    // Register-slide halo (elements after the slice; windows up to HALO_MAX+1).
+    static constexpr int HALO_MAX = 8 > 16 / (int)sizeof(T) ? 8 : 16 / (int)sizeof(T);
+    static constexpr int SLICE_BYTES = (SLICE + HALO_MAX) * (int)sizeof(T) + 16;  // + 16-byte shift room
     static constexpr int RING = 3 * T_;  // logical ring pairs
     static constexpr int RING_PHYS = RING + (RING >> PS) + 16;
     static constexpr size_t rnd(size_t b) { return (b + 127) / 128 * 128; }
-    static constexpr size_t off_stage = 0;  // [warp][stage] slices
-    static constexpr size_t off_ring = rnd((size_t)kConsumerWarps * kStages * SLICE_BYTES);
-    static constexpr size_t off_ta = off_ring + rnd(RING_PHYS * sizeof(Pair));
-    static constexpr size_t off_misc = off_ta + rnd(kQCap * sizeof(Pair));
+    static constexpr size_t off_misc = 0;
     static constexpr size_t off_kagg = 0;  // [3 ring slots][8 warps] block aggregates of K tiles
     static constexpr size_t off_jagg = off_kagg + 3 * kConsumerWarps * sizeof(Pair);  // [2][8] of J tiles
     static constexpr size_t off_bar = rnd(off_jagg + 2 * kConsumerWarps * sizeof(Pair));  // [warp][stage]
     static constexpr size_t off_issue = off_bar + kConsumerWarps * kStages * 8;
     static constexpr size_t off_queue = rnd(off_issue + kConsumerWarps * sizeof(WarpIssue));
     static constexpr size_t off_params = rnd(off_queue + kQueue * 8 + 16);
-    static constexpr size_t misc_bytes = off_params + 256;
-    static constexpr size_t smem_bytes = off_misc + misc_bytes;
+    static constexpr size_t misc_bytes = rnd(off_params + 256);
+    static constexpr size_t off_stage = off_misc + misc_bytes;  // [warp][stage] slices
+    static constexpr size_t off_ring = off_stage + rnd((size_t)kConsumerWarps * kStages * SLICE_BYTES);
+    static constexpr size_t off_ta = off_ring + rnd(RING_PHYS * sizeof(Pair));
+    static constexpr size_t smem_bytes = off_ta + rnd(kQCap * sizeof(Pair));
+    // The register slide uses only the misc area and the stages.
+    static constexpr size_t smem_bytes_slide = off_ring;
 };
 // Shared-memory regions (compile-time offsets from the shared window).
 template <typename T> struct Smem {
@@ -256,7 +263,7 @@ template <typename T> struct ItemPlan {
     int q;       // s / T
     int caseB;   // s >= T
     int lgB;     // block size log2
-    int mode;    // 0: B < V, 1: V <= B < 32V, 2: B = 32V (one block per warp)
+    int mode;    // 0: B < V, 1: V <= B < 32V, 2: B = 32V (one block per warp); 3: register slide
     int NC;      // output tiles in the item
     int ok;
 };
@@ -301,14 +308,16 @@ __device__ __forceinline__ ItemPlan<T> make_plan(const BlockScanParams &P, int64
     }
     const int64_t span = oe - ob;
     ip.NC = span > 0 ? (int)((span + G::T_ - 1) >> G::LGT) : 0;
+    if (want_mode == 3 && s <= 8) ip.mode = 3;  // register slide: w <= 9
     ip.ok = (s >= 0) && (ip.q + 2 <= kQCap) && span >= 0 && span + s + 2 * (int64_t)G::T_ <= kMaxItemSpan &&
             (want_mode < 0 || want_mode == ip.mode);
     return ip;
 }
 
 // Number of loads of one item (see load_tile for their order).
-__device__ __forceinline__ int item_loads(int ok, int caseB, int q, int NC) {
+__device__ __forceinline__ int item_loads(int ok, int caseB, int q, int NC, int mode) {
     if (!ok) return 1;  // a rejected item is one empty stage
+    if (mode == 3) return NC;  // register slide: tile c with its halo
     return (caseB ? q : 1) + NC * (caseB ? 2 : 1);
 }
 
@@ -325,7 +334,11 @@ struct StageCursor {
 
 // Tile index of load l of an item: prologue tiles (caseB ? 1 : 0) .. q, then
 // per output tile c the K tile c+q+1 and, for caseB, the J tile c.
-__device__ __forceinline__ int load_tile(int l, int caseB, int q, bool &keep) {
+__device__ __forceinline__ int load_tile(int l, int caseB, int q, bool &keep, int mode) {
+    if (mode == 3) {
+        keep = false;
+        return l;
+    }
     const int pro = caseB ? q : 1;
     if (l < pro) {
         keep = caseB;
@@ -353,30 +366,32 @@ struct SliceCopy {
     uint32_t bytes;  // copied bytes
 };
 
-template <typename T>
+// HALO extra elements after the slice are copied too (register slide).
+template <typename T, int HALO>
 __device__ __forceinline__ SliceCopy slice_copy(const T *in, int64_t n, int64_t a) {
     using G = Geo<T>;
+    constexpr int LEN = G::SLICE + HALO;  // elements; LEN * sizeof(T) is a multiple of 16
     SliceCopy sc;
     sc.mode = 2;
     sc.shift = 0;
     sc.src = 0;
     sc.bytes = 0;
-    if (a < 0 || a + G::SLICE > n) return sc;
+    if (a < 0 || a + LEN > n) return sc;
     const uintptr_t start = (uintptr_t)(in + a);
     const int sb = (int)(start & 15);
     if (sb == 0) {
         sc.mode = 0;
         sc.src = start;
-        sc.bytes = (uint32_t)(G::SLICE * sizeof(T));
+        sc.bytes = (uint32_t)(LEN * sizeof(T));
         return sc;
     }
     const uintptr_t al = start - sb;
-    const uintptr_t end = al + (uintptr_t)G::SLICE * sizeof(T) + 16;
+    const uintptr_t end = al + (uintptr_t)LEN * sizeof(T) + 16;
     if (al >= (uintptr_t)in && end <= (uintptr_t)(in + n)) {
         sc.mode = 1;
         sc.shift = sb / (int)sizeof(T);
         sc.src = al;
-        sc.bytes = (uint32_t)(G::SLICE * sizeof(T) + 16);
+        sc.bytes = (uint32_t)(LEN * sizeof(T) + 16);
     }
     return sc;
 }
@@ -390,47 +405,75 @@ __device__ __forceinline__ int64_t item_of(const BlockScanParams &P, int seq) {
 
 // Lane 0 of `warp`: issue this warp's slice of its next load, if any.
 template <typename T, int MODE>
-__device__ __noinline__ void issue_next(int warp) {
+__device__ __forceinline__ void issue_next(int warp) {
     using G = Geo<T>;
     using S = Smem<T>;
-    const BlockScanParams &P = S::params();
+    constexpr int HALO = MODE == 3 ? G::HALO_MAX : 0;
+    constexpr int LEN = G::SLICE + HALO;
     WarpIssue &wi = *S::issue(warp);
     if (wi.nloads < 0) return;
-    while (wi.l >= wi.nloads) {
-        wi.seq++;
-        const int64_t item = item_of<T>(P, wi.seq);
-        if (item >= P.n_items || item < 0) {
-            wi.nloads = -1;
-            return;
-        }
-        ItemPlan<T> ip = make_plan<T>(P, item, MODE);
-        if (!ip.ok && warp == 0) report_error(P.status, kErrBadItem);
-        wi.in = ip.in;
-        wi.n = ip.n;
-        wi.p0 = ip.p0;
-        wi.q = ip.q;
-        wi.caseB = ip.caseB;
-        wi.ok = ip.ok;
-        wi.nloads = item_loads(ip.ok, ip.caseB, ip.q, ip.NC);
-        wi.l = 0;
+    if (wi.l >= wi.nloads) {
+        const BlockScanParams &P = S::params();
+        do {
+            wi.seq++;
+            const int64_t item = item_of<T>(P, wi.seq);
+            if (item >= P.n_items || item < 0) {
+                wi.nloads = -1;
+                return;
+            }
+            ItemPlan<T> ip = make_plan<T>(P, item, MODE);
+            if (!ip.ok && warp == 0) report_error(P.status, kErrBadItem);
+            const int64_t a0 = ip.p0 + (int64_t)warp * G::SLICE;
+            const uintptr_t src0 = (uintptr_t)(ip.in + a0);
+            int64_t flo = 0, fhi = 0;
+            if ((src0 & 15) == 0) {
+                flo = a0 >= 0 ? 0 : (-a0 + G::T_ - 1) / G::T_;
+                fhi = ip.n - LEN - a0 >= 0 ? (ip.n - LEN - a0) / G::T_ + 1 : 0;
+                if (fhi < flo) fhi = flo;
+            }
+            wi.src0 = src0;
+            wi.fast_lo = (int)flo;
+            wi.fast_hi = (int)(fhi > 0x7fffffff ? 0x7fffffff : fhi);
+            wi.in = ip.in;
+            wi.n = ip.n;
+            wi.p0 = ip.p0;
+            wi.q = ip.q;
+            wi.caseB = ip.caseB;
+            wi.ok = ip.ok;
+            wi.nloads = item_loads(ip.ok, ip.caseB, ip.q, ip.NC, MODE);
+            wi.l = 0;
+        } while (wi.l >= wi.nloads);
     }
     const int stage = wi.issued & (kStages - 1);
     uint64_t *bar = S::bar(warp, stage);
-    uint32_t bytes = 0;
+    int smode = 2;
     if (wi.ok) {
         bool keep = false;
-        const int x = load_tile(wi.l, wi.caseB, wi.q, keep);
-        const int64_t a = wi.p0 + (int64_t)x * G::T_ + (int64_t)warp * G::SLICE;
-        const SliceCopy sc = slice_copy<T>(reinterpret_cast<const T *>(wi.in), wi.n, a);
-        if (sc.mode != 2) {
-            bytes = sc.bytes;
+        const int x = load_tile(wi.l, wi.caseB, wi.q, keep, MODE);
+        const uint64_t pol = keep ? policy_evict_last() : policy_evict_first();
+        if (x >= wi.fast_lo && x < wi.fast_hi) {
+            constexpr uint32_t bytes = (uint32_t)(LEN * sizeof(T));
+            wi.smode[stage] = 0;
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(bar, bytes);
-            tma_load_1d(S::slice(warp, stage), reinterpret_cast<const void *>(sc.src), bytes, bar,
-                        keep ? policy_evict_last() : policy_evict_first());
+            tma_load_1d(S::slice(warp, stage), reinterpret_cast<const void *>(wi.src0 + (uintptr_t)x * G::T_ * sizeof(T)),
+                        bytes, bar, pol);
+            smode = 0;
+        } else {
+            const int64_t a = wi.p0 + (int64_t)x * G::T_ + (int64_t)warp * G::SLICE;
+            const SliceCopy sc = slice_copy<T, HALO>(reinterpret_cast<const T *>(wi.in), wi.n, a);
+            smode = sc.mode | (sc.shift << 8);
+            wi.smode[stage] = smode;
+            if (sc.mode != 2) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(bar, sc.bytes);
+                tma_load_1d(S::slice(warp, stage), reinterpret_cast<const void *>(sc.src), sc.bytes, bar, pol);
+            }
         }
+    } else {
+        wi.smode[stage] = 2;
     }
-    if (bytes == 0) mbar_arrive_expect_tx(bar, 0);
+    if ((smode & 0xff) == 2) mbar_arrive_expect_tx(bar, 0);
     wi.l++;
     wi.issued++;
 }
@@ -466,10 +509,10 @@ struct Consumer {
             failed = true;
             return false;
         }
-        const int64_t a = ip.p0 + (int64_t)x * T_ + (int64_t)warp * G::SLICE;
-        const SliceCopy sc = slice_copy<T>(ip.in, ip.n, a);
+        const int smode = S::issue(warp)->smode[cur.stage];
+        const int mode = smode & 0xff;
         const uint8_t *sb = S::slice(warp, cur.stage);
-        if (sc.mode == 0) {
+        if (mode == 0) {
             uint32_t wd[4 * G::NCH];
             const uint4 *p4 = reinterpret_cast<const uint4 *>(sb + (size_t)lane * V * sizeof(T));
 #pragma unroll
@@ -481,12 +524,12 @@ struct Consumer {
             ExtractLoop<T, 0, 0, V>::run(wd, xv);
 #pragma unroll
             for (int i = 0; i < V; ++i) xm[i] = xn[i] = xv[i];
-        } else if (sc.mode == 1) {
-            const T *pe = reinterpret_cast<const T *>(sb) + sc.shift + lane * V;
+        } else if (mode == 1) {
+            const T *pe = reinterpret_cast<const T *>(sb) + (smode >> 8) + lane * V;
 #pragma unroll
             for (int i = 0; i < V; ++i) xm[i] = xn[i] = (R)pe[i];
         } else {
-            const int64_t pt = a + (int64_t)lane * V;
+            const int64_t pt = ip.p0 + (int64_t)x * T_ + (int64_t)warp * G::SLICE + (int64_t)lane * V;
 #pragma unroll
             for (int i = 0; i < V; ++i) {
                 const int64_t p = pt + i;
@@ -740,6 +783,100 @@ struct Consumer {
         }
     }
 
+    // ------------------------------------------------------ register slide
+    // Read this thread's V elements and the HALO_MAX that follow them.
+    __device__ __forceinline__ bool read_tile_ext(const ItemPlan<T> &ip, int x, R (&xm)[V + G::HALO_MAX],
+                                                  R (&xn)[V + G::HALO_MAX]) {
+        constexpr int NE = V + G::HALO_MAX;
+        if (!mbar_wait_bounded(S::bar(warp, cur.stage), cur.phase)) {
+            report_error(S::params().status, kErrWaitTimeout);
+            failed = true;
+            return false;
+        }
+        const int smode = S::issue(warp)->smode[cur.stage];
+        const int mode = smode & 0xff;
+        const uint8_t *sb = S::slice(warp, cur.stage);
+        if (mode == 0) {
+            constexpr int NW = NE * (int)sizeof(T) / 4;
+            uint32_t wd[NW];
+            const uint4 *p4 = reinterpret_cast<const uint4 *>(sb + (size_t)lane * V * sizeof(T));
+#pragma unroll
+            for (int c = 0; c < NW / 4; ++c) {
+                uint4 v = p4[c];
+                wd[4 * c] = v.x; wd[4 * c + 1] = v.y; wd[4 * c + 2] = v.z; wd[4 * c + 3] = v.w;
+            }
+            R xv[NE];
+            ExtractLoop<T, 0, 0, NE>::run(wd, xv);
+#pragma unroll
+            for (int i = 0; i < NE; ++i) xm[i] = xn[i] = xv[i];
+        } else if (mode == 1) {
+            const T *pe = reinterpret_cast<const T *>(sb) + (smode >> 8) + lane * V;
+#pragma unroll
+            for (int i = 0; i < NE; ++i) xm[i] = xn[i] = (R)pe[i];
+        } else {
+            const int64_t pt = ip.p0 + (int64_t)x * T_ + (int64_t)warp * G::SLICE + (int64_t)lane * V;
+#pragma unroll
+            for (int i = 0; i < NE; ++i) {
+                const int64_t p = pt + i;
+                if (p < 0 || p >= ip.n) {
+                    xm[i] = Elem<T>::lo();
+                    xn[i] = Elem<T>::hi();
+                } else {
+                    xm[i] = xn[i] = (R)ip.in[p];
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) issue_next<T, KMODE>(warp);
+        __syncwarp();
+        cur.advance();
+        return true;
+    }
+
+    // Windows of W elements straight from registers (the naive row of
+    // Table 1), shared by pairwise doubling: after the passes a[i] is the
+    // max over 2^k consecutive elements, and two such ranges cover a window.
+    template <int W>
+    __device__ __forceinline__ void run_slide(const ItemPlan<T> &ip) {
+        constexpr int NE = V + G::HALO_MAX;
+        constexpr int P2 = W >= 8 ? 8 : (W >= 4 ? 4 : (W >= 2 ? 2 : 1));
+        for (int c = 0; c < ip.NC; ++c) {
+            R am[NE], an[NE];
+            if (!read_tile_ext(ip, c, am, an)) return;
+#pragma unroll
+            for (int p = 1; p < P2; p <<= 1) {
+#pragma unroll
+                for (int i = 0; i + p < NE; ++i) { am[i] = vmax(am[i], am[i + p]); an[i] = vmin(an[i], an[i + p]); }
+            }
+            R om[V], on[V];
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                om[i] = W > P2 ? vmax(am[i], am[i + W - P2]) : am[i];
+                on[i] = W > P2 ? vmin(an[i], an[i + W - P2]) : an[i];
+            }
+            const int64_t o0 = ip.o_begin + (int64_t)c * T_ + (int64_t)tid * V;
+            if (o0 < ip.o_end) {
+                const int cnt = o0 + V <= ip.o_end ? V : (int)(ip.o_end - o0);
+                if (ip.omax) store(ip.omax + o0, om, cnt);
+                if (ip.omin) store(ip.omin + o0, on, cnt);
+            }
+        }
+    }
+
+    __device__ __forceinline__ void run_item_slide(const ItemPlan<T> &ip) {
+        switch (ip.s) {
+            case 0: run_slide<1>(ip); break;
+            case 1: run_slide<2>(ip); break;
+            case 2: run_slide<3>(ip); break;
+            case 3: run_slide<4>(ip); break;
+            case 4: run_slide<5>(ip); break;
+            case 5: run_slide<6>(ip); break;
+            case 6: run_slide<7>(ip); break;
+            case 7: run_slide<8>(ip); break;
+            default: run_slide<9>(ip); break;
+        }
+    }
+
     template <int MODE>
     __device__ __forceinline__ void run_item(const ItemPlan<T> &ip) {
         const int q = ip.q;
@@ -794,7 +931,8 @@ struct Consumer {
 // One instantiation per block mode keeps each one within 128 registers (two
 // CTAs per SM); an item whose mode differs is rejected (kErrBadItem).
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kThreads, Elem<T>::V == 16 ? 1 : 2) blockscan_kernel(const BlockScanParams P) {
+__global__ void __launch_bounds__(kThreads, (Elem<T>::V == 16 && MODE != 3) ? 1 : 2)
+    blockscan_kernel(const BlockScanParams P) {
     using S = Smem<T>;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -810,6 +948,8 @@ __global__ void __launch_bounds__(kThreads, Elem<T>::V == 16 ? 1 : 2) blockscan_
     if (lane == 0) {
         for (int s = 0; s < kStages; ++s) mbar_init(S::bar(warp, s), 1);
         WarpIssue &wi = *S::issue(warp);
+        wi.src0 = 0;
+        wi.fast_lo = wi.fast_hi = 0;
         wi.in = nullptr;
         wi.n = wi.p0 = 0;
         wi.seq = -1;
@@ -843,7 +983,10 @@ __global__ void __launch_bounds__(kThreads, Elem<T>::V == 16 ? 1 : 2) blockscan_
             __syncwarp();
             cs.cur.advance();
         } else {
-            cs.template run_item<MODE>(ip);
+            if constexpr (MODE == 3)
+                cs.run_item_slide(ip);
+            else
+                cs.template run_item<MODE>(ip);
             if (cs.failed) return;
         }
         // Thread 0 fetches the ticket that the prefetch will need next, then

@@ -6,6 +6,10 @@ namespace mmf {
 
 template <typename T> size_t blockscan_smem_bytes() { return Geo<T>::smem_bytes; }
 
+template <typename T> constexpr size_t smem_of(int mode) {
+    return mode == 3 ? Geo<T>::smem_bytes_slide : Geo<T>::smem_bytes;
+}
+
 // Sets the shared-memory attribute once per device and returns the number of
 // resident CTAs per SM.
 template <typename T, int MODE> static cudaError_t prepare_blockscan(int device, int *per_sm) {
@@ -14,11 +18,12 @@ template <typename T, int MODE> static cudaError_t prepare_blockscan(int device,
         *per_sm = occ[device];
         return cudaSuccess;
     }
+    const size_t smem = smem_of<T>(MODE);
     cudaError_t e = cudaFuncSetAttribute(blockscan_kernel<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Geo<T>::smem_bytes);
+                                         (int)smem);
     if (e != cudaSuccess) return e;
     int k = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, blockscan_kernel<T, MODE>, kThreads, Geo<T>::smem_bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, blockscan_kernel<T, MODE>, kThreads, smem);
     if (e != cudaSuccess) return e;
     if (k < 1) k = 1;
     if (device >= 0 && device < 64) occ[device] = k;
@@ -26,16 +31,18 @@ template <typename T, int MODE> static cudaError_t prepare_blockscan(int device,
     return cudaSuccess;
 }
 
-// Block mode of window w (see the kernel): 0, 1 or 2.
-template <typename T> int block_mode(int64_t w) {
+// Kernel mode for window w: 3 = register slide (w <= 9, unless a block scan
+// is forced), else the block-scan mode 0, 1 or 2.
+template <typename T> int block_mode(int64_t w, bool allow_slide) {
     const int64_t s = w - 1;
+    if (allow_slide && s <= 8) return 3;
     if (s >= 32 * (int64_t)Geo<T>::V) return 2;
     return s >= Geo<T>::V ? 1 : 0;
 }
 
 template <typename T, int MODE>
 static void launch_bs(const BlockScanParams &P, int grid, cudaStream_t st) {
-    blockscan_kernel<T, MODE><<<(unsigned)grid, kThreads, Geo<T>::smem_bytes, st>>>(P);
+    blockscan_kernel<T, MODE><<<(unsigned)grid, kThreads, smem_of<T>(MODE), st>>>(P);
 }
 
 template <typename T>
@@ -43,7 +50,8 @@ static cudaError_t prepare_mode(int mode, int device, int *per_sm) {
     switch (mode) {
         case 0: return prepare_blockscan<T, 0>(device, per_sm);
         case 1: return prepare_blockscan<T, 1>(device, per_sm);
-        default: return prepare_blockscan<T, 2>(device, per_sm);
+        case 2: return prepare_blockscan<T, 2>(device, per_sm);
+        default: return prepare_blockscan<T, 3>(device, per_sm);
     }
 }
 
@@ -52,15 +60,17 @@ static void launch_mode(int mode, const BlockScanParams &P, int grid, cudaStream
     switch (mode) {
         case 0: launch_bs<T, 0>(P, grid, st); break;
         case 1: launch_bs<T, 1>(P, grid, st); break;
-        default: launch_bs<T, 2>(P, grid, st); break;
+        case 2: launch_bs<T, 2>(P, grid, st); break;
+        default: launch_bs<T, 3>(P, grid, st); break;
     }
 }
 
 template <typename T>
-cudaError_t blockscan_1d(const LaunchCtx &ctx, const void *in, const SeriesDesc &sd, void *omax, void *omin) {
+cudaError_t blockscan_1d(const LaunchCtx &ctx, const void *in, const SeriesDesc &sd, void *omax, void *omin,
+                         bool allow_slide) {
     using G = Geo<T>;
     if (sd.n_out <= 0) return cudaSuccess;
-    const int mode = block_mode<T>(sd.w);
+    const int mode = block_mode<T>(sd.w, allow_slide);
     int per_sm = 1;
     cudaError_t e = prepare_mode<T>(mode, ctx.device, &per_sm);
     if (e != cudaSuccess) return e;
@@ -111,7 +121,7 @@ cudaError_t blockscan_table(const LaunchCtx &ctx, int mode, const void *in, void
 #define MMF_INSTANTIATE_BLOCKSCAN(T)                                                                             \
     template size_t mmf::blockscan_smem_bytes<T>();                                                            \
     template cudaError_t mmf::blockscan_1d<T>(const LaunchCtx &, const void *, const SeriesDesc &, void *,      \
-                                               void *);                                                         \
+                                               void *, bool);                                                   \
     template cudaError_t mmf::blockscan_table<T>(const LaunchCtx &, int, const void *, void *, void *,         \
                                                   const SeriesDesc *, const ItemDesc *, int64_t, int *, int); \
-    template int mmf::block_mode<T>(int64_t);
+    template int mmf::block_mode<T>(int64_t, bool);

@@ -15,9 +15,11 @@ struct LaunchCtx {
     cudaStream_t stream;
 };
 
-// One series, statically split into per-CTA items (no allocation).
+// One series, statically split into per-CTA items (no allocation).  With
+// allow_slide, windows w <= 9 use the register slide instead of block scans.
 template <typename T>
-cudaError_t blockscan_1d(const LaunchCtx &ctx, const void *in, const SeriesDesc &sd, void *omax, void *omin);
+cudaError_t blockscan_1d(const LaunchCtx &ctx, const void *in, const SeriesDesc &sd, void *omax, void *omin,
+                         bool allow_slide);
 
 // Table-driven launch (batched plans): items of one block mode, pulled from
 // an atomic ticket (or round-robin if d_ticket is null).  grid <= 0: one
@@ -27,8 +29,9 @@ cudaError_t blockscan_table(const LaunchCtx &ctx, int mode, const void *in, void
                             const SeriesDesc *d_series, const ItemDesc *d_items, int64_t n_items,
                             int *d_ticket, int grid);
 
-// Block mode (0, 1, 2) the kernel uses for window w.
-template <typename T> int block_mode(int64_t w);
+// Kernel mode for window w: 3 = register slide (if allowed and w <= 9), else
+// the block-scan mode 0, 1 or 2.
+template <typename T> int block_mode(int64_t w, bool allow_slide);
 
 template <typename T> size_t blockscan_smem_bytes();
 int blockscan_tile(int dtype);

@@ -61,6 +61,27 @@ def test_f32_windows_random_walk(mmf, w):
     _check(mmf, a, w)
 
 
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("kernel", ["slide", "blockscan"])
+@pytest.mark.parametrize("w", [1, 2, 3, 4, 5, 6, 7, 8, 9])
+def test_small_windows_each_kernel(mmf, dtype, kernel, w):
+    """Windows up to 9 through the register slide and through the block
+    scan (blocks inside a thread), both bit-exact."""
+    a = synth.random_walk(30_011, seed=w, dtype=dtype)
+    _check(mmf, a, w, kernel=kernel)
+    off = synth.uniform(10_007, seed=w, dtype=dtype)
+    x = _gpu(off)[3:]
+    mx, mn = mmf.filter1d(x, w, kernel=kernel)
+    emx, emn = oracle.bf1d(off[3:], w)
+    assert np.array_equal(mx.cpu().numpy(), emx) and np.array_equal(mn.cpu().numpy(), emn)
+
+
+def test_slide_rejects_large_window(mmf):
+    x = torch.zeros(100, device="cuda")
+    with pytest.raises(mmf.MMFError):
+        mmf.filter1d(x, 10, kernel="slide")
+
+
 @pytest.mark.parametrize("w", [2, 4, 5, 9, 33, 127, 128, 129, 130, 1023, 1024, 1025, 1026, 2049, 3075])
 def test_f64_windows(mmf, w):
     a = synth.piecewise_monotone(23_457, seed=w, dtype=np.float64)
