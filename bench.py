@@ -177,7 +177,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n", type=int, default=N)
     ap.add_argument("--ref-sample", type=int, default=1 << 24)
-    ap.add_argument("--cpu-sample", type=int, default=1 << 24)
+    ap.add_argument("--cpu-sample", type=int, default=1 << 26)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -256,29 +256,49 @@ def main():
     total_elems = per_step_elems * args.steps * ws
     value = total_elems / (elapsed_ms * 1e-3) / 1e9
 
-    # Roofline of the (single) kernel: algorithmic bytes n*4 + 2*(n-w+1)*4.
+    # Roofline of the dominant kernel.  Each window maps to one kernel
+    # instantiation (mode): 3 register slide, 1 sub-warp blocks, 2 warp blocks.
+    # Algorithmic bytes per launch: n*4 read + 2*(n-w+1)*4 written.
     peak, peak_kind = _peaks()
+    def kmode(w):
+        s = w - 1
+        return 3 if s <= 8 else (2 if s >= 256 else 1)
     per_w = {}
-    tot_bytes = 0.0
-    tot_ms = 0.0
+    per_k = {}
     for w, e0, e1 in launch_events:
         ms = e0.elapsed_time(e1)
         b = 4.0 * n + 8.0 * (n - w + 1)
         d = per_w.setdefault(w, {"ms": [], "bytes": b})
         d["ms"].append(ms)
-        tot_bytes += b
-        tot_ms += ms
-    achieved = tot_bytes / (tot_ms * 1e-3) / 1e9
-    traffic = _traffic().get("blockscan_kernel<float>", {}).get("dram_bytes_per_elem")
+        k = per_k.setdefault(kmode(w), {"ms": 0.0, "bytes": 0.0, "launches": 0, "windows": set()})
+        k["ms"] += ms
+        k["bytes"] += b
+        k["launches"] += 1
+        k["windows"].add(w)
+    dom = max(per_k, key=lambda m: per_k[m]["ms"])
+    kd = per_k[dom]
+    kname = f"mmf::blockscan_kernel<float, {dom}>"
+    achieved = kd["bytes"] / (kd["ms"] * 1e-3) / 1e9
+    tr = _traffic().get(kname)
+    traffic = None
+    if tr:
+        per_elem = dict(zip(tr["windows"], tr["dram_bytes_per_elem"]))
+        if all(w in per_elem for w in kd["windows"]):
+            traffic = sum(per_elem[w] for w in kd["windows"]) / len(kd["windows"]) * n
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_kind": peak_kind,
-                "kernel": "mmf::blockscan_kernel<float>",
-                "traffic": (traffic * n) if traffic else None,
-                "algorithmic_bytes_per_launch": tot_bytes / max(1, len(launch_events)),
+                "frac": achieved / peak, "peak_kind": peak_kind, "kernel": kname,
+                "kernel_windows": sorted(kd["windows"]),
+                "traffic": traffic,
+                "algorithmic_bytes_per_launch": kd["bytes"] / kd["launches"],
                 "frac_of_8TBps": achieved / 8000.0}
+    all_bytes = sum(v["bytes"] for v in per_k.values())
+    all_ms = sum(v["ms"] for v in per_k.values())
+    roofline["all_kernels_achieved"] = all_bytes / (all_ms * 1e-3) / 1e9
     breakdown = {str(w): {"ms": statistics.median(v["ms"]),
                           "GBps": v["bytes"] / (statistics.median(v["ms"]) * 1e-3) / 1e9,
-                          "Gelem_s": n / (statistics.median(v["ms"]) * 1e-3) / 1e9}
+                          "Gelem_s": n / (statistics.median(v["ms"]) * 1e-3) / 1e9,
+                          "frac": v["bytes"] / (statistics.median(v["ms"]) * 1e-3) / 1e9 / peak,
+                          "kernel_mode": kmode(w)}
                  for w, v in per_w.items()}
 
     # End to end through the public API with host buffers: H2D of each
