@@ -99,6 +99,58 @@ mmf_status mmf_filter1d_ex(const void *d_in, int64_t n, int64_t w_or_r, mmf_dtyp
 /* Number of outputs of one side for (n, w_or_r, mode); -1 if invalid. */
 int64_t mmf_output_length(int64_t n, int64_t w_or_r, mmf_mode mode);
 
+/* ----------------------------------------------------------- batched ---- */
+
+/* A batch plan describes many independent series in one input buffer (the
+ * batching pattern: thousands of series of uneven length and window in one
+ * persistent launch, captured in a CUDA graph).  Each series s is filtered as
+ * by mmf_filter1d (window h_w[s], clipped to the series length in VALID mode
+ * by the caller; radius in CENTERED_CLIPPED mode).  The plan owns device
+ * tables (series, work items, ticket counters) and a graph cache; it is not
+ * thread-safe.  Outputs are concatenated series by series, at the offsets
+ * reported by mmf_batch_plan_out_offsets. */
+typedef struct mmf_batch_plan mmf_batch_plan;
+
+/* h_in_off: element offset of each series in the input buffer (NULL: the
+ *           series are packed back to back in order)
+ * h_len, h_w: length and window (or radius) of each series
+ * Allocates the plan and its device tables; *out receives it. */
+mmf_status mmf_batch_plan_create(const int64_t *h_in_off, const int64_t *h_len, const int64_t *h_w,
+                                 int64_t nseries, mmf_dtype dtype, mmf_mode mode, mmf_batch_plan **out);
+
+/* Frees the plan (NULL is ignored).  No call may use it afterwards. */
+void mmf_batch_plan_destroy(mmf_batch_plan *plan);
+
+/* h_off[nseries+1]: start of each series' outputs in the output buffers. */
+mmf_status mmf_batch_plan_out_offsets(const mmf_batch_plan *plan, int64_t *h_off);
+
+/* Required input / output buffer lengths (elements) and, in n_items[4] (may
+ * be NULL), the work items per kernel group (0-2 block scans, 3 slide). */
+mmf_status mmf_batch_plan_sizes(const mmf_batch_plan *plan, int64_t *in_len, int64_t *out_len, int64_t *n_items);
+
+/* Output tiles per work item of one kernel group (tuning knob). */
+mmf_status mmf_batch_plan_set_segment(mmf_batch_plan *plan, int group, int seg_tiles);
+mmf_status mmf_batch_plan_get_segment(const mmf_batch_plan *plan, int group, int *seg_tiles);
+
+/* Times candidate segment lengths on the given buffers (synchronises the
+ * stream) and keeps the fastest per group; with $MMF_AUTOTUNE_CACHE set, the
+ * choice is appended to that file, keyed by GPU name and workload shape, and
+ * reused by later plans. */
+mmf_status mmf_batch_plan_autotune(mmf_batch_plan *plan, const void *d_in, void *d_max, void *d_min,
+                                   void *stream);
+
+/* Filters every series: one ticket reset plus one persistent launch per
+ * non-empty kernel group, replayed from a CUDA graph (captured on the first
+ * call for this set of buffers).  d_max/d_min: out_len elements each (either
+ * may be NULL). */
+mmf_status mmf_filter1d_batched(mmf_batch_plan *plan, const void *d_in, void *d_max, void *d_min,
+                                void *stream);
+
+/* The plain form: one mmf_filter1d launch per series on `stream`, same
+ * kernels, no graph (the baseline the batched form is compared with). */
+mmf_status mmf_filter1d_per_series(const mmf_batch_plan *plan, const void *d_in, void *d_max, void *d_min,
+                                   void *stream);
+
 /* --------------------------------------------------------- device status */
 
 /* Reads (and, if reset != 0, clears) the device status word that kernels set

@@ -17,7 +17,7 @@ import threading
 
 import torch
 
-__all__ = ["MMFError", "load", "filter1d", "output_length", "device_status", "DTYPES", "KERNELS"]
+__all__ = ["MMFError", "load", "filter1d", "output_length", "device_status", "BatchPlan", "DTYPES", "KERNELS"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmmf.so")
@@ -76,7 +76,18 @@ def _declare_more(lib) -> None:
             f.restype = args[1]
 
 
-_EXTRA_SIGNATURES: dict = {}
+_P64 = ctypes.POINTER(ctypes.c_int64)
+_EXTRA_SIGNATURES: dict = {
+    "mmf_batch_plan_create": ([_P64, _P64, _P64, _I64, _INT, _INT, ctypes.POINTER(_VP)], _INT),
+    "mmf_batch_plan_destroy": ([_VP], None),
+    "mmf_batch_plan_out_offsets": ([_VP, _P64], _INT),
+    "mmf_batch_plan_sizes": ([_VP, _P64, _P64, _P64], _INT),
+    "mmf_batch_plan_set_segment": ([_VP, _INT, _INT], _INT),
+    "mmf_batch_plan_get_segment": ([_VP, _INT, ctypes.POINTER(_INT)], _INT),
+    "mmf_batch_plan_autotune": ([_VP, _VP, _VP, _VP, _VP], _INT),
+    "mmf_filter1d_batched": ([_VP, _VP, _VP, _VP, _VP], _INT),
+    "mmf_filter1d_per_series": ([_VP, _VP, _VP, _VP, _VP], _INT),
+}
 
 
 def check(status: int) -> None:
@@ -135,6 +146,103 @@ def filter1d(x: torch.Tensor, w: int, mode: str = "valid", out_max=None, out_min
                                   _ptr(out_max), _ptr(out_min), _VP(_stream_handle(stream)),
                                   KERNELS[kernel]))
     return out_max, out_min
+
+
+def _i64_array(xs):
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(xs, dtype=np.int64))
+    return a, a.ctypes.data_as(_P64)
+
+
+class BatchPlan:
+    """Many independent series in one buffer, filtered by one persistent
+    launch per kernel group replayed from a CUDA graph (``mmf_filter1d_batched``).
+
+    ``lengths``/``windows`` per series (windows are radii in envelope mode);
+    ``in_offsets`` (optional) places each series in the input buffer, else
+    the series are packed back to back."""
+
+    def __init__(self, lengths, windows, dtype=torch.float32, mode: str = "valid", in_offsets=None):
+        lib = load()
+        self._lib = lib
+        self.dtype = dtype
+        self.mode = mode
+        self._len, plen = _i64_array(lengths)
+        self._w, pw = _i64_array(windows)
+        if self._len.shape != self._w.shape:
+            raise ValueError("lengths and windows differ in size")
+        poff = None
+        if in_offsets is not None:
+            self._off, poff = _i64_array(in_offsets)
+        self.nseries = int(self._len.size)
+        h = _VP()
+        check(lib.mmf_batch_plan_create(poff, plen, pw, self.nseries, DTYPES[dtype], MODES[mode], ctypes.byref(h)))
+        self._h = h
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        items = (ctypes.c_int64 * 4)()
+        check(lib.mmf_batch_plan_sizes(self._h, ctypes.byref(a), ctypes.byref(b), items))
+        self.in_len, self.out_len = int(a.value), int(b.value)
+        self.items_per_group = list(items)
+
+    def out_offsets(self):
+        import numpy as np
+        off = np.zeros(self.nseries + 1, dtype=np.int64)
+        check(self._lib.mmf_batch_plan_out_offsets(self._h, off.ctypes.data_as(_P64)))
+        return off
+
+    def _outs(self, x, out_max, out_min):
+        if out_max is None:
+            out_max = torch.empty(self.out_len, dtype=x.dtype, device=x.device)
+        if out_min is None:
+            out_min = torch.empty(self.out_len, dtype=x.dtype, device=x.device)
+        return out_max, out_min
+
+    def __call__(self, x, out_max=None, out_min=None, stream=None):
+        _check_tensor(x, "x")
+        if x.dtype != self.dtype or x.numel() < self.in_len:
+            raise ValueError(f"input must hold {self.in_len} elements of {self.dtype}")
+        out_max, out_min = self._outs(x, out_max, out_min)
+        with torch.cuda.device(x.device):
+            check(self._lib.mmf_filter1d_batched(self._h, _ptr(x), _ptr(out_max), _ptr(out_min),
+                                                 _VP(_stream_handle(stream))))
+        return out_max, out_min
+
+    def per_series(self, x, out_max=None, out_min=None, stream=None):
+        """The plain form: one mmf_filter1d launch per series."""
+        out_max, out_min = self._outs(x, out_max, out_min)
+        with torch.cuda.device(x.device):
+            check(self._lib.mmf_filter1d_per_series(self._h, _ptr(x), _ptr(out_max), _ptr(out_min),
+                                                    _VP(_stream_handle(stream))))
+        return out_max, out_min
+
+    def autotune(self, x, out_max=None, out_min=None, stream=None):
+        out_max, out_min = self._outs(x, out_max, out_min)
+        with torch.cuda.device(x.device):
+            check(self._lib.mmf_batch_plan_autotune(self._h, _ptr(x), _ptr(out_max), _ptr(out_min),
+                                                    _VP(_stream_handle(stream))))
+        return self.segments()
+
+    def segments(self):
+        out = []
+        for g in range(4):
+            v = ctypes.c_int()
+            check(self._lib.mmf_batch_plan_get_segment(self._h, g, ctypes.byref(v)))
+            out.append(int(v.value))
+        return out
+
+    def set_segment(self, group: int, tiles: int):
+        check(self._lib.mmf_batch_plan_set_segment(self._h, group, tiles))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mmf_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def device_status(reset: bool = True) -> int:

@@ -1,0 +1,411 @@
+// Batched running max-min filter: thousands of series of uneven length and
+// window in one persistent launch per kernel mode, captured in a CUDA graph.
+//
+// A plan turns the host description of the series into a device table of
+// series and work items.  An item is a contiguous range of output tiles of one
+// series; long series are split into items of `seg_tiles` tiles so that every
+// CTA's share is balanced (items are ordered longest first and pulled from an
+// atomic ticket).  Items are grouped by the kernel mode their window needs
+// (register slide, block scans with blocks inside a thread, across lanes, or
+// one per warp); each group is one persistent launch.  The first call with a
+// given set of buffers captures the ticket resets and the launches into a
+// graph; later calls replay it.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "launch.h"
+#include "mmf.h"
+
+namespace mmf {
+mmf_status set_error(mmf_status st, const char *fmt, ...);
+mmf_status cuda_error(cudaError_t e, const char *what);
+mmf_status get_ctx(void *stream, LaunchCtx *ctx);
+int elem_size(mmf_dtype dt);
+int tile_of(mmf_dtype dt);
+mmf_status make_series(int64_t n, int64_t w_or_r, mmf_mode mode, mmf_dtype dt, SeriesDesc *sd);
+}  // namespace mmf
+
+using namespace mmf;
+
+namespace {
+
+constexpr int kModes = 4;  // 0, 1, 2 block scans; 3 register slide
+
+struct Group {
+    int mode = 0;
+    int seg_tiles = 16;
+    std::vector<ItemDesc> items;
+    ItemDesc *d_items = nullptr;
+};
+
+int kernel_mode(mmf_dtype dt, int64_t w) {
+    switch (dt) {
+        case MMF_F32: return block_mode<float>(w, true);
+        case MMF_F64: return block_mode<double>(w, true);
+        case MMF_I16: return block_mode<int16_t>(w, true);
+        default: return block_mode<uint8_t>(w, true);
+    }
+}
+
+}  // namespace
+
+struct mmf_batch_plan {
+    int device = 0;
+    mmf_dtype dtype = MMF_F32;
+    mmf_mode mode = MMF_VALID;
+    int64_t nseries = 0;
+    int64_t in_len = 0;   // elements the input buffer must hold
+    int64_t out_len = 0;  // elements each output buffer must hold
+    std::vector<SeriesDesc> series;
+    std::vector<int64_t> out_off;  // nseries + 1
+    Group groups[kModes];
+    SeriesDesc *d_series = nullptr;
+    int *d_tickets = nullptr;  // one per group
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const void *g_in = nullptr;
+    void *g_max = nullptr, *g_min = nullptr;
+    int g_launches = 0;
+};
+
+namespace {
+
+void free_items(mmf_batch_plan *p) {
+    for (auto &g : p->groups) {
+        if (g.d_items) cudaFree(g.d_items);
+        g.d_items = nullptr;
+    }
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    p->exec = nullptr;
+}
+
+// Split the series of one group into items of at most seg_tiles output tiles
+// and upload them, longest first.
+mmf_status build_items(mmf_batch_plan *p, int gi) {
+    Group &g = p->groups[gi];
+    g.items.clear();
+    const int64_t T = tile_of(p->dtype);
+    const int64_t seg = (int64_t)std::max(1, g.seg_tiles) * T;
+    for (int64_t s = 0; s < p->nseries; ++s) {
+        const SeriesDesc &sd = p->series[s];
+        if (sd.n_out <= 0 || kernel_mode(p->dtype, sd.w) != g.mode) continue;
+        for (int64_t ob = 0; ob < sd.n_out; ob += seg) g.items.push_back({s, ob, std::min(sd.n_out, ob + seg)});
+    }
+    std::stable_sort(g.items.begin(), g.items.end(), [&](const ItemDesc &a, const ItemDesc &b) {
+        const int64_t ca = a.o_end - a.o_begin + p->series[a.series].w;
+        const int64_t cb = b.o_end - b.o_begin + p->series[b.series].w;
+        return ca > cb;
+    });
+    if (g.d_items) cudaFree(g.d_items);
+    g.d_items = nullptr;
+    if (g.items.empty()) return MMF_OK;
+    cudaError_t e = cudaMalloc(&g.d_items, g.items.size() * sizeof(ItemDesc));
+    if (e != cudaSuccess) return set_error(MMF_ENOMEM, "plan items: %s", cudaGetErrorString(e));
+    e = cudaMemcpy(g.d_items, g.items.data(), g.items.size() * sizeof(ItemDesc), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_error(e, "upload items");
+    return MMF_OK;
+}
+
+mmf_status launch_group(mmf_batch_plan *p, int gi, const LaunchCtx &ctx, const void *in, void *omax, void *omin,
+                        bool ticket) {
+    Group &g = p->groups[gi];
+    if (g.items.empty()) return MMF_OK;
+    int *tk = ticket ? p->d_tickets + gi : nullptr;
+    cudaError_t e = cudaSuccess;
+    const int64_t ni = (int64_t)g.items.size();
+    switch (p->dtype) {
+        case MMF_F32: e = blockscan_table<float>(ctx, g.mode, in, omax, omin, p->d_series, g.d_items, ni, tk, 0); break;
+        case MMF_F64: e = blockscan_table<double>(ctx, g.mode, in, omax, omin, p->d_series, g.d_items, ni, tk, 0); break;
+        case MMF_I16: e = blockscan_table<int16_t>(ctx, g.mode, in, omax, omin, p->d_series, g.d_items, ni, tk, 0); break;
+        case MMF_U8: e = blockscan_table<uint8_t>(ctx, g.mode, in, omax, omin, p->d_series, g.d_items, ni, tk, 0); break;
+    }
+    return e == cudaSuccess ? MMF_OK : cuda_error(e, "batched launch");
+}
+
+// Ticket resets and one persistent launch per non-empty group, on `st`.
+mmf_status enqueue_all(mmf_batch_plan *p, cudaStream_t st, const void *in, void *omax, void *omin) {
+    LaunchCtx ctx;
+    mmf_status s = get_ctx(st, &ctx);
+    if (s != MMF_OK) return s;
+    cudaError_t e = cudaMemsetAsync(p->d_tickets, 0, kModes * sizeof(int), st);
+    if (e != cudaSuccess) return cuda_error(e, "reset tickets");
+    for (int gi = 0; gi < kModes; ++gi) {
+        s = launch_group(p, gi, ctx, in, omax, omin, true);
+        if (s != MMF_OK) return s;
+    }
+    return MMF_OK;
+}
+
+mmf_status capture(mmf_batch_plan *p, const void *in, void *omax, void *omin) {
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    p->exec = nullptr;
+    for (int gi = 0; gi < kModes; ++gi) {
+        if (p->groups[gi].items.empty()) continue;
+        cudaError_t pe = cudaSuccess;
+        switch (p->dtype) {
+            case MMF_F32: pe = blockscan_prepare<float>(p->device, gi); break;
+            case MMF_F64: pe = blockscan_prepare<double>(p->device, gi); break;
+            case MMF_I16: pe = blockscan_prepare<int16_t>(p->device, gi); break;
+            case MMF_U8: pe = blockscan_prepare<uint8_t>(p->device, gi); break;
+        }
+        if (pe != cudaSuccess) return cuda_error(pe, "prepare kernels");
+    }
+    LaunchCtx warm;
+    mmf_status ws = get_ctx(nullptr, &warm);  // device cache filled outside the capture
+    if (ws != MMF_OK) return ws;
+    cudaError_t e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_error(e, "begin capture");
+    mmf_status s = enqueue_all(p, p->cap_stream, in, omax, omin);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(p->cap_stream, &graph);
+    if (s != MMF_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    if (e != cudaSuccess) return cuda_error(e, "end capture");
+    e = cudaGraphInstantiate(&p->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_error(e, "instantiate graph");
+    p->g_in = in;
+    p->g_max = omax;
+    p->g_min = omin;
+    return MMF_OK;
+}
+
+// Autotune cache: one line "key seg_tiles" per entry in $MMF_AUTOTUNE_CACHE.
+std::string cache_key(const mmf_batch_plan *p, int gi) {
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, p->device);
+    int64_t tiles = 0, wsum = 0;
+    for (auto &it : p->groups[gi].items) {
+        tiles += (it.o_end - it.o_begin + tile_of(p->dtype) - 1) / tile_of(p->dtype);
+        wsum += p->series[it.series].w;
+    }
+    char buf[256];
+    int lt = 0;
+    while ((1ll << (lt + 1)) <= std::max<int64_t>(1, tiles)) ++lt;
+    snprintf(buf, sizeof(buf), "%s|dt%d|m%d|g%d|tiles2^%d|series%lld", prop.name, (int)p->dtype, (int)p->mode,
+             p->groups[gi].mode, lt, (long long)p->nseries);
+    std::string k(buf);
+    for (auto &c : k)
+        if (c == ' ') c = '_';
+    return k;
+}
+
+int cache_lookup(const std::string &key) {
+    const char *path = getenv("MMF_AUTOTUNE_CACHE");
+    if (!path) return 0;
+    FILE *f = fopen(path, "r");
+    if (!f) return 0;
+    char k[512];
+    int v = 0, found = 0;
+    while (fscanf(f, "%511s %d", k, &v) == 2)
+        if (key == k) found = v;
+    fclose(f);
+    return found;
+}
+
+void cache_store(const std::string &key, int v) {
+    const char *path = getenv("MMF_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %d\n", key.c_str(), v);
+    fclose(f);
+}
+
+}  // namespace
+
+extern "C" {
+
+mmf_status mmf_batch_plan_create(const int64_t *h_in_off, const int64_t *h_len, const int64_t *h_w, int64_t nseries,
+                                 mmf_dtype dtype, mmf_mode mode, mmf_batch_plan **out) {
+    if (!out) return set_error(MMF_EINVAL, "NULL plan output");
+    *out = nullptr;
+    if (nseries < 0 || (nseries > 0 && (!h_len || !h_w))) return set_error(MMF_EINVAL, "bad series description");
+    if (elem_size(dtype) == 0) return set_error(MMF_EINVAL, "unknown dtype %d", (int)dtype);
+    mmf_batch_plan *p = new (std::nothrow) mmf_batch_plan();
+    if (!p) return set_error(MMF_ENOMEM, "plan");
+    cudaGetDevice(&p->device);
+    p->dtype = dtype;
+    p->mode = mode;
+    p->nseries = nseries;
+    p->series.resize(nseries);
+    p->out_off.assign(nseries + 1, 0);
+    int64_t in_pos = 0;
+    for (int64_t s = 0; s < nseries; ++s) {
+        SeriesDesc sd;
+        mmf_status st = make_series(h_len[s], h_w[s], mode, dtype, &sd);
+        if (st != MMF_OK) {
+            delete p;
+            return st;
+        }
+        sd.in_off = h_in_off ? h_in_off[s] : in_pos;
+        if (sd.in_off < 0) {
+            delete p;
+            return set_error(MMF_EINVAL, "negative input offset for series %lld", (long long)s);
+        }
+        in_pos = sd.in_off + sd.n;
+        p->in_len = std::max(p->in_len, sd.in_off + sd.n);
+        sd.out_off = p->out_off[s];
+        p->out_off[s + 1] = p->out_off[s] + sd.n_out;
+        p->series[s] = sd;
+    }
+    p->out_len = p->out_off[nseries];
+    for (int gi = 0; gi < kModes; ++gi) {
+        p->groups[gi].mode = gi;
+        p->groups[gi].seg_tiles = gi == 2 ? 32 : 16;
+    }
+    cudaError_t e = cudaMalloc(&p->d_tickets, kModes * sizeof(int));
+    if (e == cudaSuccess && nseries > 0) e = cudaMalloc(&p->d_series, nseries * sizeof(SeriesDesc));
+    if (e == cudaSuccess && nseries > 0)
+        e = cudaMemcpy(p->d_series, p->series.data(), nseries * sizeof(SeriesDesc), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        mmf_batch_plan_destroy(p);
+        return set_error(MMF_ENOMEM, "plan device tables: %s", cudaGetErrorString(e));
+    }
+    for (int gi = 0; gi < kModes; ++gi) {
+        mmf_status st = build_items(p, gi);
+        if (st != MMF_OK) {
+            mmf_batch_plan_destroy(p);
+            return st;
+        }
+        const int cached = cache_lookup(cache_key(p, gi));
+        if (cached > 0 && cached != p->groups[gi].seg_tiles) {
+            p->groups[gi].seg_tiles = cached;
+            st = build_items(p, gi);
+            if (st != MMF_OK) {
+                mmf_batch_plan_destroy(p);
+                return st;
+            }
+        }
+    }
+    *out = p;
+    return MMF_OK;
+}
+
+void mmf_batch_plan_destroy(mmf_batch_plan *p) {
+    if (!p) return;
+    free_items(p);
+    if (p->d_series) cudaFree(p->d_series);
+    if (p->d_tickets) cudaFree(p->d_tickets);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    delete p;
+}
+
+mmf_status mmf_batch_plan_out_offsets(const mmf_batch_plan *p, int64_t *h_off) {
+    if (!p || !h_off) return set_error(MMF_EINVAL, "NULL argument");
+    memcpy(h_off, p->out_off.data(), (p->nseries + 1) * sizeof(int64_t));
+    return MMF_OK;
+}
+
+mmf_status mmf_batch_plan_sizes(const mmf_batch_plan *p, int64_t *in_len, int64_t *out_len, int64_t *n_items) {
+    if (!p) return set_error(MMF_EINVAL, "NULL plan");
+    if (in_len) *in_len = p->in_len;
+    if (out_len) *out_len = p->out_len;
+    if (n_items)
+        for (int gi = 0; gi < kModes; ++gi) n_items[gi] = (int64_t)p->groups[gi].items.size();
+    return MMF_OK;
+}
+
+mmf_status mmf_batch_plan_set_segment(mmf_batch_plan *p, int group, int seg_tiles) {
+    if (!p || group < 0 || group >= kModes || seg_tiles < 1) return set_error(MMF_EINVAL, "bad segment request");
+    p->groups[group].seg_tiles = seg_tiles;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    p->exec = nullptr;
+    return build_items(p, group);
+}
+
+mmf_status mmf_filter1d_batched(mmf_batch_plan *p, const void *d_in, void *d_max, void *d_min, void *stream) {
+    if (!p) return set_error(MMF_EINVAL, "NULL plan");
+    if (p->out_len == 0) return MMF_OK;
+    if (!d_in || (!d_max && !d_min)) return set_error(MMF_EINVAL, "NULL buffers");
+    const int esz = elem_size(p->dtype);
+    if (((uintptr_t)d_in % esz) || ((uintptr_t)d_max % esz) || ((uintptr_t)d_min % esz))
+        return set_error(MMF_EINVAL, "pointers must be aligned to the element size");
+    if (!p->exec || p->g_in != d_in || p->g_max != d_max || p->g_min != d_min) {
+        mmf_status s = capture(p, d_in, d_max, d_min);
+        if (s != MMF_OK) return s;
+    }
+    cudaError_t e = cudaGraphLaunch(p->exec, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? MMF_OK : cuda_error(e, "graph launch");
+}
+
+mmf_status mmf_filter1d_per_series(const mmf_batch_plan *p, const void *d_in, void *d_max, void *d_min,
+                                   void *stream) {
+    if (!p) return set_error(MMF_EINVAL, "NULL plan");
+    const int esz = elem_size(p->dtype);
+    for (int64_t s = 0; s < p->nseries; ++s) {
+        const SeriesDesc &sd = p->series[s];
+        if (sd.n_out <= 0) continue;
+        const int64_t w_or_r = p->mode == MMF_VALID ? sd.w : (sd.w - 1) / 2;
+        mmf_status st = mmf_filter1d(static_cast<const char *>(d_in) + sd.in_off * esz, sd.n, w_or_r, p->dtype,
+                                     p->mode, d_max ? static_cast<char *>(d_max) + sd.out_off * esz : nullptr,
+                                     d_min ? static_cast<char *>(d_min) + sd.out_off * esz : nullptr, stream);
+        if (st != MMF_OK) return st;
+    }
+    return MMF_OK;
+}
+
+mmf_status mmf_batch_plan_autotune(mmf_batch_plan *p, const void *d_in, void *d_max, void *d_min, void *stream) {
+    if (!p) return set_error(MMF_EINVAL, "NULL plan");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    LaunchCtx ctx;
+    mmf_status s = get_ctx(stream, &ctx);
+    if (s != MMF_OK) return s;
+    const int cands[] = {1, 2, 4, 8, 16, 32, 64, 128};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int gi = 0; gi < kModes; ++gi) {
+        if (p->groups[gi].items.empty()) continue;
+        int best = p->groups[gi].seg_tiles;
+        float best_ms = 1e30f;
+        for (int c : cands) {
+            p->groups[gi].seg_tiles = c;
+            s = build_items(p, gi);
+            if (s != MMF_OK) break;
+            float ms = 0.f;
+            for (int rep = 0; rep < 3; ++rep) {
+                cudaMemsetAsync(p->d_tickets + gi, 0, sizeof(int), st);
+                cudaEventRecord(e0, st);
+                s = launch_group(p, gi, ctx, d_in, d_max, d_min, true);
+                cudaEventRecord(e1, st);
+                if (s != MMF_OK) break;
+                cudaEventSynchronize(e1);
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e0, e1);
+                if (rep > 0) ms += t;  // first run warms up
+            }
+            if (s != MMF_OK) break;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+        p->groups[gi].seg_tiles = best;
+        mmf_status s2 = build_items(p, gi);
+        if (s == MMF_OK) s = s2;
+        if (s != MMF_OK) break;
+        cache_store(cache_key(p, gi), best);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    p->exec = nullptr;
+    return s;
+}
+
+mmf_status mmf_batch_plan_get_segment(const mmf_batch_plan *p, int group, int *seg_tiles) {
+    if (!p || !seg_tiles || group < 0 || group >= kModes) return set_error(MMF_EINVAL, "bad arguments");
+    *seg_tiles = p->groups[group].seg_tiles;
+    return MMF_OK;
+}
+
+}  // extern "C"

@@ -65,6 +65,11 @@ static void launch_mode(int mode, const BlockScanParams &P, int grid, cudaStream
     }
 }
 
+template <typename T> cudaError_t blockscan_prepare(int device, int mode) {
+    int per_sm = 1;
+    return prepare_mode<T>(mode, device, &per_sm);
+}
+
 template <typename T>
 cudaError_t blockscan_1d(const LaunchCtx &ctx, const void *in, const SeriesDesc &sd, void *omax, void *omin,
                          bool allow_slide) {
@@ -120,6 +125,7 @@ cudaError_t blockscan_table(const LaunchCtx &ctx, int mode, const void *in, void
 
 #define MMF_INSTANTIATE_BLOCKSCAN(T)                                                                             \
     template size_t mmf::blockscan_smem_bytes<T>();                                                            \
+    template cudaError_t mmf::blockscan_prepare<T>(int, int);                                                  \
     template cudaError_t mmf::blockscan_1d<T>(const LaunchCtx &, const void *, const SeriesDesc &, void *,      \
                                                void *, bool);                                                   \
     template cudaError_t mmf::blockscan_table<T>(const LaunchCtx &, int, const void *, void *, void *,         \

@@ -34,6 +34,10 @@ cudaError_t blockscan_table(const LaunchCtx &ctx, int mode, const void *in, void
 template <typename T> int block_mode(int64_t w, bool allow_slide);
 
 template <typename T> size_t blockscan_smem_bytes();
+
+// Sets the kernel attributes of one mode on the current device (outside any
+// stream capture).
+template <typename T> cudaError_t blockscan_prepare(int device, int mode);
 int blockscan_tile(int dtype);
 
 }  // namespace mmf
