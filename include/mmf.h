@@ -151,6 +151,35 @@ mmf_status mmf_filter1d_batched(mmf_batch_plan *plan, const void *d_in, void *d_
 mmf_status mmf_filter1d_per_series(const mmf_batch_plan *plan, const void *d_in, void *d_max, void *d_min,
                                    void *stream);
 
+/* ------------------------------------------- batched, no allocation ---- */
+
+/* Limits of mmf_filter1d_batched_noalloc. */
+#define MMF_NOALLOC_MAX_SERIES 512
+#define MMF_NOALLOC_MAX_ITEMS 2048
+
+/* The batched filter for callers that must not allocate device memory (a
+ * process that reserved a fixed device-memory pool up front, a real-time path
+ * where an allocation may block or fail, a host callback where allocation
+ * APIs are not allowed).  The paper has no counterpart to this entry point;
+ * it is an interface convenience.
+ *
+ * Same results as a batch plan over the same series (inputs packed back to
+ * back in d_in, outputs concatenated in d_max/d_min in series order), but it
+ * calls no cudaMalloc/cudaFree: its work tables live in one fixed device array
+ * of about 70 KB that every GPU which loads the library keeps until the
+ * process exits.  At most MMF_NOALLOC_MAX_SERIES series; long series are
+ * split into at most MMF_NOALLOC_MAX_ITEMS work items.  Larger requests
+ * return MMF_EINVAL.
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call reuses the same array and clears its counters itself;
+ * calls that overlap on the GPU (two host threads, or two unordered streams)
+ * race on it and give wrong results. */
+mmf_status mmf_filter1d_batched_noalloc(const void *d_in, const int64_t *h_len, const int64_t *h_w,
+                                        int64_t nseries, mmf_dtype dtype, mmf_mode mode, void *d_max,
+                                        void *d_min, void *stream);
+
 /* --------------------------------------------------------- device status */
 
 /* Reads (and, if reset != 0, clears) the device status word that kernels set
