@@ -169,6 +169,80 @@ def cpu_baseline(sample: int):
                       f"Algorithm 1 wedge (single thread), {dt:.1f} s"}
 
 
+def _events_ms(fn, reps, stream):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def batched_extras(dev, stream, peak, reps=5, envelope_series=1_000_000):
+    """Uneven batch (4096 series, f32 and f64) and envelope batch (1M series
+    of 1024, r=51): one persistent launch per kernel group (graph replay)
+    against one mmf_filter1d launch per series, both event-timed."""
+    import torch
+    import paper_cs_0610046_gb300 as mmf
+    import synth
+    out = {}
+    lens, ws, dists, seeds = synth.uneven_batch(4096, seed=31)
+    total = int(lens.sum())
+    starts = np.concatenate([[0], np.cumsum(lens)[:-1]])
+    for tname, tdt in (("f32", torch.float32), ("f64", torch.float64)):
+        src = [synth.torch_by_name(d, total, 31 + i, dev, tdt) for i, d in enumerate(synth.DISTS)]
+        # each series takes its distribution's values at its own offset
+        x = src[0]
+        for i in range(lens.size):
+            if dists[i]:
+                a, b = int(starts[i]), int(starts[i] + lens[i])
+                x[a:b] = src[dists[i]][a:b]
+        del src
+        plan = mmf.BatchPlan(lens, ws, tdt)
+        om = torch.empty(plan.out_len, dtype=tdt, device=dev)
+        on = torch.empty(plan.out_len, dtype=tdt, device=dev)
+        plan.autotune(x, om, on, stream)
+        for _ in range(2):
+            plan(x, om, on, stream)
+        bms = _events_ms(lambda: plan(x, om, on, stream), reps, stream)
+        plan.per_series(x, om, on, stream)
+        pms = _events_ms(lambda: plan.per_series(x, om, on, stream), 2, stream)
+        sz = 4 if tdt == torch.float32 else 8
+        byts = (total + 2 * plan.out_len) * sz
+        out[f"uneven_{tname}"] = {
+            "series": 4096, "elements": total, "batched_ms": bms, "per_series_ms": pms,
+            "batched_over_per_series": pms / bms, "batched_Gelem_s": total / bms / 1e6,
+            "batched_GBps": byts / bms / 1e6, "frac": byts / bms / 1e6 / peak,
+            "segments": plan.segments(), "items_per_group": plan.items_per_group}
+        plan.close()
+        del x, om, on
+    torch.cuda.empty_cache()
+    # Envelope: z-normalised random walks, 1024 each, centred windows r = 51.
+    ns, L, r = envelope_series, 1024, 51
+    g = torch.Generator(device=dev)
+    g.manual_seed(33)
+    z = torch.cumsum(torch.randn(ns, L, generator=g, device=dev, dtype=torch.float64), 1)
+    z = ((z - z.mean(1, keepdim=True)) / z.std(1, unbiased=False, keepdim=True)).float().reshape(-1) + 0.0
+    plan = mmf.BatchPlan(np.full(ns, L), np.full(ns, r), torch.float32, "envelope")
+    om = torch.empty(plan.out_len, dtype=torch.float32, device=dev)
+    on = torch.empty(plan.out_len, dtype=torch.float32, device=dev)
+    plan.autotune(z, om, on, stream)
+    for _ in range(2):
+        plan(z, om, on, stream)
+    bms = _events_ms(lambda: plan(z, om, on, stream), reps, stream)
+    pms = _events_ms(lambda: plan.per_series(z, om, on, stream), 1, stream)
+    byts = 3 * ns * L * 4
+    out["envelope_f32"] = {
+        "series": ns, "length": L, "radius": r, "batched_ms": bms, "per_series_ms": pms,
+        "batched_over_per_series": pms / bms, "batched_Gelem_s": ns * L / bms / 1e6,
+        "batched_GBps": byts / bms / 1e6, "frac": byts / bms / 1e6 / peak, "segments": plan.segments()}
+    plan.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -181,6 +255,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched/2D/serving measurements")
     args = ap.parse_args()
 
     if args.impl == "reference":
@@ -337,6 +412,12 @@ def main():
                "steps": args.e2e_steps}
         del hx, hmax, hmin, dx
 
+    extras = {}
+    if not args.no_extras and rank == 0:
+        del xs
+        torch.cuda.empty_cache()
+        extras["batched"] = batched_extras(dev, stream, peak)
+
     status = mmf.device_status(reset=True)
     cpu = None
     if not args.no_cpu and rank == 0 and ws == 1:
@@ -353,6 +434,7 @@ def main():
                        "parallelism": f"{ws} independent streams per distribution (one per GPU)"},
             "roofline": roofline, "per_window": breakdown, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": len(launch_events), "clocks": clocks, "device_status": status,
+            **extras,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
