@@ -67,6 +67,8 @@ struct mmf_batch_plan {
     SeriesDesc *d_series = nullptr;
     int *d_tickets = nullptr;  // one per group
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t branch[kModes] = {};   // capture branches: groups run concurrently
+    cudaEvent_t fork = nullptr, join[kModes] = {};
     cudaGraphExec_t exec = nullptr;
     const void *g_in = nullptr;
     void *g_max = nullptr, *g_min = nullptr;
@@ -127,16 +129,28 @@ mmf_status launch_group(mmf_batch_plan *p, int gi, const LaunchCtx &ctx, const v
     return e == cudaSuccess ? MMF_OK : cuda_error(e, "batched launch");
 }
 
-// Ticket resets and one persistent launch per non-empty group, on `st`.
+// Ticket resets on `st`, then one persistent launch per non-empty group, each
+// on its own branch stream (fork/join by events) so that a group's tail
+// overlaps the next group's work.
 mmf_status enqueue_all(mmf_batch_plan *p, cudaStream_t st, const void *in, void *omax, void *omin) {
     LaunchCtx ctx;
     mmf_status s = get_ctx(st, &ctx);
     if (s != MMF_OK) return s;
     cudaError_t e = cudaMemsetAsync(p->d_tickets, 0, kModes * sizeof(int), st);
     if (e != cudaSuccess) return cuda_error(e, "reset tickets");
+    e = cudaEventRecord(p->fork, st);
+    if (e != cudaSuccess) return cuda_error(e, "fork");
     for (int gi = 0; gi < kModes; ++gi) {
-        s = launch_group(p, gi, ctx, in, omax, omin, true);
+        if (p->groups[gi].items.empty()) continue;
+        e = cudaStreamWaitEvent(p->branch[gi], p->fork, 0);
+        if (e != cudaSuccess) return cuda_error(e, "branch wait");
+        LaunchCtx bctx = ctx;
+        bctx.stream = p->branch[gi];
+        s = launch_group(p, gi, bctx, in, omax, omin, true);
         if (s != MMF_OK) return s;
+        e = cudaEventRecord(p->join[gi], p->branch[gi]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, p->join[gi], 0);
+        if (e != cudaSuccess) return cuda_error(e, "join");
     }
     return MMF_OK;
 }
@@ -266,6 +280,11 @@ mmf_status mmf_batch_plan_create(const int64_t *h_in_off, const int64_t *h_len, 
     if (e == cudaSuccess && nseries > 0)
         e = cudaMemcpy(p->d_series, p->series.data(), nseries * sizeof(SeriesDesc), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+    for (int gi = 0; gi < kModes && e == cudaSuccess; ++gi) {
+        e = cudaStreamCreateWithFlags(&p->branch[gi], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->join[gi], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         mmf_batch_plan_destroy(p);
         return set_error(MMF_ENOMEM, "plan device tables: %s", cudaGetErrorString(e));
@@ -296,6 +315,11 @@ void mmf_batch_plan_destroy(mmf_batch_plan *p) {
     if (p->d_series) cudaFree(p->d_series);
     if (p->d_tickets) cudaFree(p->d_tickets);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    for (int gi = 0; gi < kModes; ++gi) {
+        if (p->branch[gi]) cudaStreamDestroy(p->branch[gi]);
+        if (p->join[gi]) cudaEventDestroy(p->join[gi]);
+    }
+    if (p->fork) cudaEventDestroy(p->fork);
     delete p;
 }
 

@@ -48,16 +48,25 @@ template <> struct Elem<float> {
     __device__ static Pair pair(R m, R n) { return make_float2(m, n); }
     __device__ static R pmax(Pair p) { return p.x; }
     __device__ static R pmin(Pair p) { return p.y; }
+    __device__ static R load(float x) { return x; }
+    __device__ static float store(R x) { return x; }
 };
+// Doubles are compared as order-preserving 64-bit integer keys (sign bit kept,
+// magnitude bits flipped for negatives): for non-NaN values the integer order
+// is the floating-point order, and GB300's integer pipes are far faster than
+// its FP64 pipe.  Keys are converted back on store, so results are exact.
 template <> struct Elem<double> {
-    using R = double;
-    using Pair = double2;
+    using R = long long;
+    using Pair = longlong2;
     static constexpr int V = 4, PS = 3;
-    __device__ static R lo() { return __longlong_as_double(0xfff0000000000000ULL); }
-    __device__ static R hi() { return __longlong_as_double(0x7ff0000000000000ULL); }
-    __device__ static Pair pair(R m, R n) { return make_double2(m, n); }
+    __device__ static R key(long long b) { return b ^ ((b >> 63) & 0x7fffffffffffffffLL); }
+    __device__ static R lo() { return key((long long)0xfff0000000000000ULL); }  // -inf
+    __device__ static R hi() { return key(0x7ff0000000000000LL); }              // +inf
+    __device__ static Pair pair(R m, R n) { return make_longlong2(m, n); }
     __device__ static R pmax(Pair p) { return p.x; }
     __device__ static R pmin(Pair p) { return p.y; }
+    __device__ static R load(double x) { return key(__double_as_longlong(x)); }
+    __device__ static double store(R k) { return __longlong_as_double(key(k)); }
 };
 template <> struct Elem<int16_t> {
     using R = int;
@@ -68,6 +77,8 @@ template <> struct Elem<int16_t> {
     __device__ static Pair pair(R m, R n) { return make_short2((short)m, (short)n); }
     __device__ static R pmax(Pair p) { return p.x; }
     __device__ static R pmin(Pair p) { return p.y; }
+    __device__ static R load(int16_t x) { return x; }
+    __device__ static int16_t store(R x) { return (int16_t)x; }
 };
 template <> struct Elem<uint8_t> {
     using R = int;
@@ -78,12 +89,14 @@ template <> struct Elem<uint8_t> {
     __device__ static Pair pair(R m, R n) { return make_uchar2((unsigned char)m, (unsigned char)n); }
     __device__ static R pmax(Pair p) { return p.x; }
     __device__ static R pmin(Pair p) { return p.y; }
+    __device__ static R load(uint8_t x) { return x; }
+    __device__ static uint8_t store(R x) { return (uint8_t)x; }
 };
 
 __device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
-__device__ __forceinline__ double vmax(double a, double b) { return fmax(a, b); }
-__device__ __forceinline__ double vmin(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ long long vmax(long long a, long long b) { return a > b ? a : b; }
+__device__ __forceinline__ long long vmin(long long a, long long b) { return a < b ? a : b; }
 __device__ __forceinline__ int vmax(int a, int b) { return max(a, b); }
 __device__ __forceinline__ int vmin(int a, int b) { return min(a, b); }
 
@@ -93,8 +106,8 @@ template <> struct WordElem<float> {
     template <int B> __device__ static float get(const uint32_t *wd) { return __uint_as_float(wd[B >> 2]); }
 };
 template <> struct WordElem<double> {
-    template <int B> __device__ static double get(const uint32_t *wd) {
-        return __hiloint2double((int)wd[(B >> 2) + 1], (int)wd[B >> 2]);
+    template <int B> __device__ static long long get(const uint32_t *wd) {
+        return Elem<double>::key((long long)(((unsigned long long)wd[(B >> 2) + 1] << 32) | wd[B >> 2]));
     }
 };
 template <> struct WordElem<int16_t> {
@@ -132,8 +145,9 @@ __device__ __forceinline__ void extract_shifted(int s, const uint32_t *wd, typen
 
 template <typename T> __device__ __forceinline__ uint32_t pack_word(const typename Elem<T>::R *x, int w);
 template <> __device__ __forceinline__ uint32_t pack_word<float>(const float *x, int w) { return __float_as_uint(x[w]); }
-template <> __device__ __forceinline__ uint32_t pack_word<double>(const double *x, int w) {
-    return (w & 1) ? (uint32_t)__double2hiint(x[w >> 1]) : (uint32_t)__double2loint(x[w >> 1]);
+template <> __device__ __forceinline__ uint32_t pack_word<double>(const long long *x, int w) {
+    const unsigned long long b = (unsigned long long)Elem<double>::key(x[w >> 1]);
+    return (w & 1) ? (uint32_t)(b >> 32) : (uint32_t)b;
 }
 template <> __device__ __forceinline__ uint32_t pack_word<int16_t>(const int *x, int w) {
     return ((uint32_t)(uint16_t)x[2 * w]) | ((uint32_t)(uint16_t)x[2 * w + 1] << 16);
@@ -527,7 +541,7 @@ struct Consumer {
         } else if (mode == 1) {
             const T *pe = reinterpret_cast<const T *>(sb) + (smode >> 8) + lane * V;
 #pragma unroll
-            for (int i = 0; i < V; ++i) xm[i] = xn[i] = (R)pe[i];
+            for (int i = 0; i < V; ++i) xm[i] = xn[i] = Elem<T>::load(pe[i]);
         } else {
             const int64_t pt = ip.p0 + (int64_t)x * T_ + (int64_t)warp * G::SLICE + (int64_t)lane * V;
 #pragma unroll
@@ -537,7 +551,7 @@ struct Consumer {
                     xm[i] = Elem<T>::lo();
                     xn[i] = Elem<T>::hi();
                 } else {
-                    xm[i] = xn[i] = (R)ip.in[p];
+                    xm[i] = xn[i] = Elem<T>::load(ip.in[p]);
                 }
             }
         }
@@ -744,7 +758,7 @@ struct Consumer {
         } else {
 #pragma unroll
             for (int i = 0; i < V; ++i)
-                if (i < cnt) dst[i] = (T)v[i];
+                if (i < cnt) dst[i] = Elem<T>::store(v[i]);
         }
     }
 
@@ -812,7 +826,7 @@ struct Consumer {
         } else if (mode == 1) {
             const T *pe = reinterpret_cast<const T *>(sb) + (smode >> 8) + lane * V;
 #pragma unroll
-            for (int i = 0; i < NE; ++i) xm[i] = xn[i] = (R)pe[i];
+            for (int i = 0; i < NE; ++i) xm[i] = xn[i] = Elem<T>::load(pe[i]);
         } else {
             const int64_t pt = ip.p0 + (int64_t)x * T_ + (int64_t)warp * G::SLICE + (int64_t)lane * V;
 #pragma unroll
@@ -822,7 +836,7 @@ struct Consumer {
                     xm[i] = Elem<T>::lo();
                     xn[i] = Elem<T>::hi();
                 } else {
-                    xm[i] = xn[i] = (R)ip.in[p];
+                    xm[i] = xn[i] = Elem<T>::load(ip.in[p]);
                 }
             }
         }
