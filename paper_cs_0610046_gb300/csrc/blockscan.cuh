@@ -207,7 +207,7 @@ struct WarpIssue {
     int32_t seq;     // its sequence number among this CTA's items
     int32_t l;       // next load within it
     int32_t nloads;  // its number of loads; -1 once the sequence has ended
-    int32_t q, caseB, ok;
+    int32_t q, caseB, ok, NC, klast;
     int32_t issued;  // loads issued so far by this warp
     int32_t smode[kStages];  // per stage: copy mode | shift << 8, for the readers
 };
@@ -279,6 +279,7 @@ template <typename T> struct ItemPlan {
     int lgB;     // block size log2
     int mode;    // 0: B < V, 1: V <= B < 32V, 2: B = 32V (one block per warp); 3: register slide
     int NC;      // output tiles in the item
+    int klast;   // 1 if some window of the last output tile reaches K tile NC+q
     int ok;
 };
 
@@ -322,6 +323,7 @@ __device__ __forceinline__ ItemPlan<T> make_plan(const BlockScanParams &P, int64
     }
     const int64_t span = oe - ob;
     ip.NC = span > 0 ? (int)((span + G::T_ - 1) >> G::LGT) : 0;
+    ip.klast = span > 0 ? (int)((((span - 1) + s) >> G::LGT) >= ip.NC + ip.q) : 0;
     if (want_mode == 3 && s <= 8) ip.mode = 3;  // register slide: w <= 9
     ip.ok = (s >= 0) && (ip.q + 2 <= kQCap) && span >= 0 && span + s + 2 * (int64_t)G::T_ <= kMaxItemSpan &&
             (want_mode < 0 || want_mode == ip.mode);
@@ -329,10 +331,10 @@ __device__ __forceinline__ ItemPlan<T> make_plan(const BlockScanParams &P, int64
 }
 
 // Number of loads of one item (see load_tile for their order).
-__device__ __forceinline__ int item_loads(int ok, int caseB, int q, int NC, int mode) {
+__device__ __forceinline__ int item_loads(int ok, int caseB, int q, int NC, int mode, int klast) {
     if (!ok) return 1;  // a rejected item is one empty stage
     if (mode == 3) return NC;  // register slide: tile c with its halo
-    return (caseB ? q : 1) + NC * (caseB ? 2 : 1);
+    return (caseB ? q : 1) + NC * (caseB ? 2 : 1) - ((NC > 0 && !klast) ? 1 : 0);
 }
 
 struct StageCursor {
@@ -348,7 +350,8 @@ struct StageCursor {
 
 // Tile index of load l of an item: prologue tiles (caseB ? 1 : 0) .. q, then
 // per output tile c the K tile c+q+1 and, for caseB, the J tile c.
-__device__ __forceinline__ int load_tile(int l, int caseB, int q, bool &keep, int mode) {
+// (The last K tile is skipped when no window reaches it: !klast.)
+__device__ __forceinline__ int load_tile(int l, int caseB, int q, bool &keep, int mode, int NC, int klast) {
     if (mode == 3) {
         keep = false;
         return l;
@@ -362,6 +365,10 @@ __device__ __forceinline__ int load_tile(int l, int caseB, int q, bool &keep, in
     if (!caseB) {
         keep = false;
         return r + q + 1;
+    }
+    if (!klast && r == 2 * (NC - 1)) {  // last iteration: J tile only
+        keep = false;
+        return NC - 1;
     }
     const int c = r >> 1;
     keep = !(r & 1);  // a K tile is read again later as a J tile
@@ -454,7 +461,9 @@ __device__ __forceinline__ void issue_next(int warp) {
             wi.q = ip.q;
             wi.caseB = ip.caseB;
             wi.ok = ip.ok;
-            wi.nloads = item_loads(ip.ok, ip.caseB, ip.q, ip.NC, MODE);
+            wi.NC = ip.NC;
+            wi.klast = ip.klast;
+            wi.nloads = item_loads(ip.ok, ip.caseB, ip.q, ip.NC, MODE, ip.klast);
             wi.l = 0;
         } while (wi.l >= wi.nloads);
     }
@@ -463,7 +472,7 @@ __device__ __forceinline__ void issue_next(int warp) {
     int smode = 2;
     if (wi.ok) {
         bool keep = false;
-        const int x = load_tile(wi.l, wi.caseB, wi.q, keep, MODE);
+        const int x = load_tile(wi.l, wi.caseB, wi.q, keep, MODE, wi.NC, wi.klast);
         const uint64_t pol = keep ? policy_evict_last() : policy_evict_first();
         if (x >= wi.fast_lo && x < wi.fast_hi) {
             constexpr uint32_t bytes = (uint32_t)(LEN * sizeof(T));
@@ -779,16 +788,18 @@ struct Consumer {
     // MODE 2 publishes the warp (= block) totals.
     template <int MODE>
     __device__ __forceinline__ void scan_tile(const ItemPlan<T> &ip, R (&pm)[V], R (&pn)[V], bool suf, R (&sm)[V],
-                                              R (&sn)[V], int kslot, int jbuf) {
+                                              R (&sn)[V], int kslot, int jbuf, bool pre = true) {
         const int lgB = ip.lgB;
-        local_prefix<MODE>(pm, pn, lgB);
+        if (pre) local_prefix<MODE>(pm, pn, lgB);
         if (suf) local_suffix<MODE>(sm, sn, lgB);
         if constexpr (MODE > 0) {
             const int lgS = lgB - G::LGV;
             if (lgS > 0) {
                 R tm, tn;
-                lane_carry(0, pm, pn, lgS, tm, tn);
-                if (MODE == 2 && lane == 31) S::kagg()[kslot * 8 + warp] = Elem<T>::pair(tm, tn);
+                if (pre) {
+                    lane_carry(0, pm, pn, lgS, tm, tn);
+                    if (MODE == 2 && lane == 31) S::kagg()[kslot * 8 + warp] = Elem<T>::pair(tm, tn);
+                }
                 if (suf) {
                     lane_carry(1, sm, sn, lgS, tm, tn);
                     if (MODE == 2 && jbuf >= 0 && lane == 0) S::jagg()[jbuf * 8 + warp] = Elem<T>::pair(tm, tn);
@@ -920,23 +931,29 @@ struct Consumer {
         for (int c = 0; c < ip.NC; ++c) {
             R pm[V], pn[V], Sn_m[V], Sn_n[V];
             const int xk = c + q + 1;
-            if (!read_tile(ip, xk, pm, pn)) return;  // K tile c+q+1
+            const bool kload = c + 1 < ip.NC || ip.klast;  // else no window reaches K tile xk
             if (!ip.caseB) {
+                if (kload) {
+                    if (!read_tile(ip, xk, pm, pn)) return;  // K tile c+1 (also J tile of c+1)
 #pragma unroll
-                for (int i = 0; i < V; ++i) { Sn_m[i] = pm[i]; Sn_n[i] = pn[i]; }
-            } else {
-                if (!read_tile(ip, c, Sn_m, Sn_n)) return;  // J tile c
-            }
-            scan_tile<MODE>(ip, pm, pn, true, Sn_m, Sn_n, xk % 3, ip.caseB ? (c & 1) : -1);
-            ring_write(xk, pm, pn);
-            sync();
-            if (ip.caseB) {
-                publish_tile_aggregate(xk);
-                outputs<MODE>(ip, c, Sn_m, Sn_n);
-            } else {
+                    for (int i = 0; i < V; ++i) { Sn_m[i] = pm[i]; Sn_n[i] = pn[i]; }
+                    scan_tile<MODE>(ip, pm, pn, true, Sn_m, Sn_n, xk % 3, -1);
+                    ring_write(xk, pm, pn);
+                }
+                sync();
                 outputs<MODE>(ip, c, Sc_m, Sc_n);
+                if (kload) {
 #pragma unroll
-                for (int i = 0; i < V; ++i) { Sc_m[i] = Sn_m[i]; Sc_n[i] = Sn_n[i]; }
+                    for (int i = 0; i < V; ++i) { Sc_m[i] = Sn_m[i]; Sc_n[i] = Sn_n[i]; }
+                }
+            } else {
+                if (kload && !read_tile(ip, xk, pm, pn)) return;  // K tile c+q+1
+                if (!read_tile(ip, c, Sn_m, Sn_n)) return;        // J tile c
+                scan_tile<MODE>(ip, pm, pn, true, Sn_m, Sn_n, xk % 3, c & 1, kload);
+                if (kload) ring_write(xk, pm, pn);
+                sync();
+                if (kload) publish_tile_aggregate(xk);
+                outputs<MODE>(ip, c, Sn_m, Sn_n);
             }
         }
     }
@@ -968,7 +985,7 @@ __global__ void __launch_bounds__(kThreads, (Elem<T>::V == 16 && MODE != 3) ? 1 
         wi.n = wi.p0 = 0;
         wi.seq = -1;
         wi.l = wi.nloads = 0;
-        wi.q = wi.caseB = wi.ok = 0;
+        wi.q = wi.caseB = wi.ok = wi.NC = wi.klast = 0;
         wi.issued = 0;
         fence_mbar_init();
     }
