@@ -99,6 +99,27 @@ mmf_status mmf_filter1d_ex(const void *d_in, int64_t n, int64_t w_or_r, mmf_dtyp
 /* Number of outputs of one side for (n, w_or_r, mode); -1 if invalid. */
 int64_t mmf_output_length(int64_t n, int64_t w_or_r, mmf_mode mode);
 
+/* ---------------------------------------------------------------- 2D ---- */
+
+/* Separable 2D filter (Section 1: the 1D filter on rows, then on columns),
+ * valid windows: for each of nimg images of H rows x W columns (row pitch
+ * `pitch` >= W elements; image k starts at d_in + k*H*pitch),
+ *     max[y][x] = max over rows y..y+wy-1, columns x..x+wx-1   (min likewise)
+ * for y = 0..H-wy, x = 0..W-wx.  Outputs are packed: image k, row y starts at
+ * d_max + (k*(H-wy+1) + y)*(W-wx+1).  Both windows >= 1; a window of 1 skips
+ * that pass.  The row pass writes its two intermediates to `d_work` (16-byte
+ * aligned, size from mmf_filter2d_workspace; none needed when wy or wx is 1).
+ * fuse: -1 automatic, 0 row pass then column pass; 1 (a fused kernel) returns
+ * MMF_ENOTIMPL.  For 1- and 2-byte types the output width W-wx+1 and the
+ * output pointers must be even (and, when wx is 1, the pitch and input).
+ * Column windows are limited by the column pass's shared memory: up to about
+ * 760 rows for f32, 320 for f64 and 1700 for i16/u8 (MMF_ENOTIMPL beyond). */
+mmf_status mmf_filter2d_workspace(int64_t nimg, int64_t H, int64_t W, int64_t wy, int64_t wx, mmf_dtype dtype,
+                                  int fuse, size_t *bytes);
+mmf_status mmf_filter2d_separable(const void *d_in, int64_t nimg, int64_t H, int64_t W, int64_t pitch,
+                                  int64_t wy, int64_t wx, mmf_dtype dtype, int fuse, void *d_max, void *d_min,
+                                  void *d_work, size_t work_bytes, void *stream);
+
 /* ----------------------------------------------------------- batched ---- */
 
 /* A batch plan describes many independent series in one input buffer (the

@@ -17,7 +17,7 @@ import threading
 
 import torch
 
-__all__ = ["MMFError", "load", "filter1d", "output_length", "device_status", "BatchPlan", "DTYPES", "KERNELS"]
+__all__ = ["MMFError", "load", "filter1d", "output_length", "device_status", "BatchPlan", "filter2d", "DTYPES", "KERNELS"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmmf.so")
@@ -87,6 +87,9 @@ _EXTRA_SIGNATURES: dict = {
     "mmf_batch_plan_autotune": ([_VP, _VP, _VP, _VP, _VP], _INT),
     "mmf_filter1d_batched": ([_VP, _VP, _VP, _VP, _VP], _INT),
     "mmf_filter1d_per_series": ([_VP, _VP, _VP, _VP, _VP], _INT),
+    "mmf_filter2d_workspace": ([_I64, _I64, _I64, _I64, _I64, _INT, _INT, ctypes.POINTER(ctypes.c_size_t)], _INT),
+    "mmf_filter2d_separable": ([_VP, _I64, _I64, _I64, _I64, _I64, _I64, _INT, _INT, _VP, _VP, _VP,
+                                ctypes.c_size_t, _VP], _INT),
 }
 
 
@@ -243,6 +246,36 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+def filter2d(x: torch.Tensor, wy: int, wx: int, fuse: int = -1, out_max=None, out_min=None,
+             workspace=None, stream=None):
+    """Separable 2D max/min filter, valid windows wy x wx, of images
+    ``x`` shaped (H, W) or (N, H, W) (last dim contiguous; rows may be
+    padded).  Returns ``(max, min)`` shaped (N, H-wy+1, W-wx+1)."""
+    if x.dim() == 2:
+        x = x.unsqueeze(0)
+    if x.dim() != 3 or not x.is_cuda or x.dtype not in DTYPES or x.stride(2) != 1:
+        raise TypeError("x must be a CUDA tensor (N, H, W) with unit column stride")
+    n, H, W = x.shape
+    pitch = x.stride(1)
+    if n > 1 and x.stride(0) != H * pitch:
+        raise ValueError("images must be stacked at H * pitch")
+    lib = load()
+    Ho, Wo = max(0, H - wy + 1), max(0, W - wx + 1)
+    if out_max is None:
+        out_max = torch.empty((n, Ho, Wo), dtype=x.dtype, device=x.device)
+    if out_min is None:
+        out_min = torch.empty((n, Ho, Wo), dtype=x.dtype, device=x.device)
+    need = ctypes.c_size_t(0)
+    check(lib.mmf_filter2d_workspace(n, H, W, wy, wx, DTYPES[x.dtype], fuse, ctypes.byref(need)))
+    if need.value and (workspace is None or workspace.numel() * workspace.element_size() < need.value):
+        workspace = torch.empty(need.value, dtype=torch.uint8, device=x.device)
+    with torch.cuda.device(x.device):
+        check(lib.mmf_filter2d_separable(_ptr(x), n, H, W, pitch, wy, wx, DTYPES[x.dtype], fuse,
+                                         _ptr(out_max), _ptr(out_min), _ptr(workspace),
+                                         need.value, _VP(_stream_handle(stream))))
+    return out_max, out_min
 
 
 def device_status(reset: bool = True) -> int:

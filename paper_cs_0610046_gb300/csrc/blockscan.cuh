@@ -179,9 +179,12 @@ struct BlockScanParams {
     void *out_min;
     const SeriesDesc *series;  // table (batched) or nullptr (use `one`)
     const ItemDesc *items;     // table (batched) or nullptr (arithmetic)
-    SeriesDesc one;            // the single series of a 1D launch
+    SeriesDesc one;            // the single series of a 1D launch (or every row)
     int64_t seg_outputs;       // 1D: outputs per item (multiple of the tile)
     int64_t n_items;
+    int64_t row_items;         // > 0: rows mode, `one` repeated per row, row_items items a row
+    int64_t in_pitch;          // rows mode: element stride between rows (input)
+    int64_t out_pitch;         // rows mode: element stride between rows (outputs)
     int *ticket;               // nullptr: static round-robin; else atomic ticket
     uint32_t *status;          // device status word
 };
@@ -295,6 +298,15 @@ __device__ __forceinline__ ItemPlan<T> make_plan(const BlockScanParams &P, int64
         sd = P.series[it.series];
         ob = it.o_begin;
         oe = it.o_end;
+    } else if (P.row_items > 0) {
+        const int64_t row = item / P.row_items;
+        const int64_t seg = item - row * P.row_items;
+        sd = P.one;
+        sd.in_off += row * P.in_pitch;
+        sd.out_off += row * P.out_pitch;
+        ob = seg * P.seg_outputs;
+        oe = ob + P.seg_outputs;
+        if (oe > sd.n_out) oe = sd.n_out;
     } else {
         sd = P.one;
         ob = item * P.seg_outputs;

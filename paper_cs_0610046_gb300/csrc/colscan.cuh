@@ -1,0 +1,273 @@
+// Column pass of the separable 2D filter (Section 1: the 2D filter is the 1D
+// filter on rows, then on columns).  Each thread streams CPT adjacent columns
+// of one image down the rows in tiles of 8 rows, so consecutive threads touch
+// consecutive columns (coalesced rows) and no two threads share state: no CTA
+// barrier at all.
+//
+//   wy <= 9  (slide): outputs of rows 8c..8c+7 are the window max over the
+//            current and the next 8-row tile held in registers (pairwise
+//            doubling, the naive row of Table 1).
+//   wy >= 10 (blocks of 8 rows, van Herk / Gil-Werman, Section 2): with
+//            s = wy-1 = 8q + r, row j = 8c+i has k = j+s in tile c+q or
+//            c+q+1, and max[j] = max(S_c[i], tiles c+1 .. c+q-1 (or c+q),
+//            P(k)), where S is the suffix max inside tile c (the J tile, read
+//            again from memory), P the prefix max inside k's tile (a 2-slot
+//            per-thread ring in shared memory) and the tiles between come from
+//            a per-thread ring of tile aggregates.
+// The max side reads `src_max` and the min side `src_min` (the row-pass
+// outputs, or the image itself when the row window is 1).
+#pragma once
+#include <cstdint>
+
+#include "blockscan.cuh"
+
+namespace mmf {
+
+struct ColParams {
+    const void *src_max;
+    const void *src_min;
+    void *out_max;
+    void *out_min;
+    int64_t nimg, H, Wc;          // images, rows, columns of the column pass
+    int64_t in_pitch, in_img;     // element strides (row, image) of the sources
+    int64_t out_pitch, out_img;   // element strides of the outputs
+    int32_t wy;                   // column window
+    int32_t strips;               // column strips per image
+    int32_t qcap;                 // tile-aggregate ring entries per thread (>= q+2)
+    uint32_t *status;
+};
+
+constexpr int kColThreads = 256;
+constexpr int kColRows = 8;  // rows per tile
+
+template <typename T> struct ColGeo {
+    static constexpr int CPT = sizeof(T) >= 4 ? 1 : 2;  // columns per thread
+    static constexpr int STRIP = kColThreads * CPT;
+};
+
+// Vector of CPT elements of one row (one load / store per row and thread).
+template <typename T, int CPT> struct RowVec;
+template <typename T> struct RowVec<T, 1> {
+    using R = typename Elem<T>::R;
+    __device__ static void load(const T *p, R (&v)[1]) { v[0] = Elem<T>::load(__ldg(p)); }
+    __device__ static void store(T *p, const R (&v)[1]) { __stcs(p, Elem<T>::store(v[0])); }
+};
+template <> struct RowVec<uint8_t, 2> {
+    using R = int;
+    __device__ static void load(const uint8_t *p, R (&v)[2]) {
+        const uint32_t u = __ldg(reinterpret_cast<const unsigned short *>(p));
+        v[0] = u & 0xff;
+        v[1] = (u >> 8) & 0xff;
+    }
+    __device__ static void store(uint8_t *p, const R (&v)[2]) {
+        const unsigned short u = (unsigned short)((v[0] & 0xff) | ((v[1] & 0xff) << 8));
+        *reinterpret_cast<unsigned short *>(p) = u;
+    }
+};
+template <> struct RowVec<int16_t, 2> {
+    using R = int;
+    __device__ static void load(const int16_t *p, R (&v)[2]) {
+        const uint32_t u = __ldg(reinterpret_cast<const unsigned int *>(p));
+        v[0] = (int16_t)(u & 0xffff);
+        v[1] = (int16_t)(u >> 16);
+    }
+    __device__ static void store(int16_t *p, const R (&v)[2]) {
+        const uint32_t u = (uint32_t)(uint16_t)v[0] | ((uint32_t)(uint16_t)v[1] << 16);
+        __stcs(reinterpret_cast<unsigned int *>(p), u);
+    }
+};
+
+template <typename T> struct ColSmem {
+    using Pair = typename Elem<T>::Pair;
+    static constexpr int CPT = ColGeo<T>::CPT;
+    // P ring [2 slots][8 rows][CPT][threads] and aggregates [qcap][CPT][threads].
+    static size_t bytes(int qcap) {
+        return (size_t)(2 * kColRows + qcap) * CPT * kColThreads * sizeof(Pair);
+    }
+};
+
+extern __shared__ __align__(16) uint8_t col_smem[];
+
+// Loads one 8-row tile (rows y..y+7 of this thread's columns) of one source;
+// rows outside [0, H) read as the identity `pad`.
+template <typename T, int CPT>
+__device__ __forceinline__ void col_tile(const T *col, int64_t pitch, int64_t y, int64_t H,
+                                         typename Elem<T>::R pad,
+                                         typename Elem<T>::R (&v)[kColRows][CPT]) {
+#pragma unroll
+    for (int r = 0; r < kColRows; ++r) {
+        if (y + r >= 0 && y + r < H) {
+            RowVec<T, CPT>::load(col + (y + r) * pitch, v[r]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) v[r][c] = pad;
+        }
+    }
+}
+
+template <typename T, int CPT>
+__device__ __forceinline__ void col_store(T *col, int64_t pitch, int64_t y, int64_t Ho,
+                                          const typename Elem<T>::R (&v)[kColRows][CPT]) {
+#pragma unroll
+    for (int r = 0; r < kColRows; ++r)
+        if (y + r < Ho) RowVec<T, CPT>::store(col + (y + r) * pitch, v[r]);
+}
+
+template <typename T, int W>
+__device__ __forceinline__ void col_slide(const ColParams &P, const T *smax, const T *smin, T *omax, T *omin,
+                                          int64_t Ho) {
+    using R = typename Elem<T>::R;
+    constexpr int CPT = ColGeo<T>::CPT;
+    constexpr int P2 = W >= 8 ? 8 : (W >= 4 ? 4 : (W >= 2 ? 2 : 1));
+    R cm[kColRows][CPT], cn[kColRows][CPT];  // current tile
+    col_tile<T, CPT>(smax, P.in_pitch, 0, P.H, Elem<T>::lo(), cm);
+    col_tile<T, CPT>(smin, P.in_pitch, 0, P.H, Elem<T>::hi(), cn);
+    for (int64_t y = 0; y < Ho; y += kColRows) {
+        R nm[kColRows][CPT], nn[kColRows][CPT];  // next tile
+        col_tile<T, CPT>(smax, P.in_pitch, y + kColRows, P.H, Elem<T>::lo(), nm);
+        col_tile<T, CPT>(smin, P.in_pitch, y + kColRows, P.H, Elem<T>::hi(), nn);
+        R om[kColRows][CPT], on[kColRows][CPT];
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+            R am[2 * kColRows], an[2 * kColRows];
+#pragma unroll
+            for (int r = 0; r < kColRows; ++r) {
+                am[r] = cm[r][c]; am[r + kColRows] = nm[r][c];
+                an[r] = cn[r][c]; an[r + kColRows] = nn[r][c];
+            }
+#pragma unroll
+            for (int p = 1; p < P2; p <<= 1) {
+#pragma unroll
+                for (int i = 0; i + p < 2 * kColRows; ++i) { am[i] = vmax(am[i], am[i + p]); an[i] = vmin(an[i], an[i + p]); }
+            }
+#pragma unroll
+            for (int r = 0; r < kColRows; ++r) {
+                om[r][c] = W > P2 ? vmax(am[r], am[r + W - P2]) : am[r];
+                on[r][c] = W > P2 ? vmin(an[r], an[r + W - P2]) : an[r];
+            }
+        }
+        if (omax) col_store<T, CPT>(omax, P.out_pitch, y, Ho, om);
+        if (omin) col_store<T, CPT>(omin, P.out_pitch, y, Ho, on);
+#pragma unroll
+        for (int r = 0; r < kColRows; ++r)
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) { cm[r][c] = nm[r][c]; cn[r][c] = nn[r][c]; }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void col_blocks(const ColParams &P, const T *smax, const T *smin, T *omax, T *omin,
+                                           int64_t Ho) {
+    using R = typename Elem<T>::R;
+    using Pair = typename Elem<T>::Pair;
+    constexpr int CPT = ColGeo<T>::CPT;
+    const int tid = threadIdx.x;
+    const int s = P.wy - 1;
+    const int q = s >> 3, rr = s & 7;
+    const int qcap = P.qcap;
+    Pair *ring = reinterpret_cast<Pair *>(col_smem);                      // [2][8][CPT][NT]
+    Pair *ta = ring + 2 * kColRows * CPT * kColThreads;                   // [qcap][CPT][NT]
+    auto RP = [&](int slot, int r, int c) -> Pair & { return ring[((slot * kColRows + r) * CPT + c) * kColThreads + tid]; };
+    auto TA = [&](int x, int c) -> Pair & { return ta[((x % qcap) * CPT + c) * kColThreads + tid]; };
+
+    // Prefix scan inside a tile; P to ring slot, aggregate to the ring of tile aggregates.
+    auto k_tile = [&](int x, R (&km)[kColRows][CPT], R (&kn)[kColRows][CPT]) {
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+#pragma unroll
+            for (int r = 1; r < kColRows; ++r) {
+                km[r][c] = vmax(km[r - 1][c], km[r][c]);
+                kn[r][c] = vmin(kn[r - 1][c], kn[r][c]);
+            }
+#pragma unroll
+            for (int r = 0; r < kColRows; ++r) RP(x & 1, r, c) = Elem<T>::pair(km[r][c], kn[r][c]);
+            TA(x, c) = Elem<T>::pair(km[kColRows - 1][c], kn[kColRows - 1][c]);
+        }
+    };
+
+    // Prologue: tiles 1 .. q (P of tile q stays in the ring).
+    for (int x = 1; x <= q; ++x) {
+        R km[kColRows][CPT], kn[kColRows][CPT];
+        col_tile<T, CPT>(smax, P.in_pitch, (int64_t)x * kColRows, P.H, Elem<T>::lo(), km);
+        col_tile<T, CPT>(smin, P.in_pitch, (int64_t)x * kColRows, P.H, Elem<T>::hi(), kn);
+        k_tile(x, km, kn);
+    }
+    const int NC = (int)((Ho + kColRows - 1) / kColRows);
+    // Prefetched K tile (c+q+1) and J tile (c) of the next iteration.
+    R km[kColRows][CPT], kn[kColRows][CPT], jm[kColRows][CPT], jn[kColRows][CPT];
+    col_tile<T, CPT>(smax, P.in_pitch, (int64_t)(q + 1) * kColRows, P.H, Elem<T>::lo(), km);
+    col_tile<T, CPT>(smin, P.in_pitch, (int64_t)(q + 1) * kColRows, P.H, Elem<T>::hi(), kn);
+    col_tile<T, CPT>(smax, P.in_pitch, 0, P.H, Elem<T>::lo(), jm);
+    col_tile<T, CPT>(smin, P.in_pitch, 0, P.H, Elem<T>::hi(), jn);
+    for (int c = 0; c < NC; ++c) {
+        R cjm[kColRows][CPT], cjn[kColRows][CPT];
+#pragma unroll
+        for (int r = 0; r < kColRows; ++r)
+#pragma unroll
+            for (int cc = 0; cc < CPT; ++cc) { cjm[r][cc] = jm[r][cc]; cjn[r][cc] = jn[r][cc]; }
+        k_tile(c + q + 1, km, kn);
+        if (c + 1 < NC) {  // prefetch the next iteration's tiles
+            col_tile<T, CPT>(smax, P.in_pitch, (int64_t)(c + q + 2) * kColRows, P.H, Elem<T>::lo(), km);
+            col_tile<T, CPT>(smin, P.in_pitch, (int64_t)(c + q + 2) * kColRows, P.H, Elem<T>::hi(), kn);
+            col_tile<T, CPT>(smax, P.in_pitch, (int64_t)(c + 1) * kColRows, P.H, Elem<T>::lo(), jm);
+            col_tile<T, CPT>(smin, P.in_pitch, (int64_t)(c + 1) * kColRows, P.H, Elem<T>::hi(), jn);
+        }
+        R om[kColRows][CPT], on[kColRows][CPT];
+#pragma unroll
+        for (int cc = 0; cc < CPT; ++cc) {
+            // suffix inside the J tile
+#pragma unroll
+            for (int r = kColRows - 2; r >= 0; --r) {
+                cjm[r][cc] = vmax(cjm[r + 1][cc], cjm[r][cc]);
+                cjn[r][cc] = vmin(cjn[r + 1][cc], cjn[r][cc]);
+            }
+            // tiles strictly between: c+1 .. c+q-1 (near), .. c+q (far)
+            R m1 = Elem<T>::lo(), n1 = Elem<T>::hi();
+            for (int x = c + 1; x <= c + q - 1; ++x) {
+                const Pair a = TA(x, cc);
+                m1 = vmax(m1, Elem<T>::pmax(a));
+                n1 = vmin(n1, Elem<T>::pmin(a));
+            }
+            const Pair lastp = TA(c + q, cc);
+            const R m2 = vmax(m1, Elem<T>::pmax(lastp)), n2 = vmin(n1, Elem<T>::pmin(lastp));
+#pragma unroll
+            for (int i = 0; i < kColRows; ++i) {
+                const int kr = i + rr;  // row of k within tiles c+q, c+q+1
+                const bool far = kr >= kColRows;
+                const Pair pk = RP((c + q + (far ? 1 : 0)) & 1, kr & 7, cc);
+                om[i][cc] = vmax(vmax(cjm[i][cc], far ? m2 : m1), Elem<T>::pmax(pk));
+                on[i][cc] = vmin(vmin(cjn[i][cc], far ? n2 : n1), Elem<T>::pmin(pk));
+            }
+        }
+        if (omax) col_store<T, CPT>(omax, P.out_pitch, (int64_t)c * kColRows, Ho, om);
+        if (omin) col_store<T, CPT>(omin, P.out_pitch, (int64_t)c * kColRows, Ho, on);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kColThreads) colscan_kernel(const ColParams P) {
+    constexpr int CPT = ColGeo<T>::CPT;
+    const int64_t img = blockIdx.x / P.strips;
+    const int64_t strip = blockIdx.x % P.strips;
+    const int64_t x = strip * ColGeo<T>::STRIP + (int64_t)threadIdx.x * CPT;
+    const int64_t Ho = P.H - P.wy + 1;
+    if (x >= P.Wc || Ho <= 0 || img >= P.nimg) return;  // no barriers below
+    const T *smax = reinterpret_cast<const T *>(P.src_max) + img * P.in_img + x;
+    const T *smin = reinterpret_cast<const T *>(P.src_min) + img * P.in_img + x;
+    T *omax = P.out_max ? reinterpret_cast<T *>(P.out_max) + img * P.out_img + x : nullptr;
+    T *omin = P.out_min ? reinterpret_cast<T *>(P.out_min) + img * P.out_img + x : nullptr;
+    switch (P.wy) {
+        case 1: col_slide<T, 1>(P, smax, smin, omax, omin, Ho); break;
+        case 2: col_slide<T, 2>(P, smax, smin, omax, omin, Ho); break;
+        case 3: col_slide<T, 3>(P, smax, smin, omax, omin, Ho); break;
+        case 4: col_slide<T, 4>(P, smax, smin, omax, omin, Ho); break;
+        case 5: col_slide<T, 5>(P, smax, smin, omax, omin, Ho); break;
+        case 6: col_slide<T, 6>(P, smax, smin, omax, omin, Ho); break;
+        case 7: col_slide<T, 7>(P, smax, smin, omax, omin, Ho); break;
+        case 8: col_slide<T, 8>(P, smax, smin, omax, omin, Ho); break;
+        case 9: col_slide<T, 9>(P, smax, smin, omax, omin, Ho); break;
+        default: col_blocks<T>(P, smax, smin, omax, omin, Ho); break;
+    }
+}
+
+}  // namespace mmf

@@ -1,0 +1,151 @@
+// Separable 2D running max-min filter (Section 1: the 1D filter on rows, then
+// on columns), valid windows: out[y][x] = max over rows y..y+wy-1 and columns
+// x..x+wx-1.  Row pass: the 1D block-scan kernel over strided rows.  Column
+// pass: colscan_kernel (one thread per column).  The row-pass intermediates go
+// to a caller-provided workspace.
+#include <cstring>
+
+#include "colscan.cuh"
+#include "launch.h"
+#include "mmf.h"
+
+namespace mmf {
+mmf_status set_error(mmf_status st, const char *fmt, ...);
+mmf_status cuda_error(cudaError_t e, const char *what);
+mmf_status get_ctx(void *stream, LaunchCtx *ctx);
+int elem_size(mmf_dtype dt);
+
+template <typename T> static int col_qcap(int64_t wy) { return wy >= 10 ? (int)((wy - 1) / 8) + 2 : 0; }
+
+template <typename T> static size_t col_smem_bytes(int64_t wy) { return ColSmem<T>::bytes(col_qcap<T>(wy)); }
+
+template <typename T> static cudaError_t col_launch(const LaunchCtx &ctx, const ColParams &P0) {
+    ColParams P = P0;
+    P.strips = (int)((P.Wc + ColGeo<T>::STRIP - 1) / ColGeo<T>::STRIP);
+    P.qcap = col_qcap<T>(P.wy);
+    P.status = ctx.status;
+    const size_t smem = col_smem_bytes<T>(P.wy);
+    static size_t set[64] = {0};
+    if (smem > set[ctx.device]) {
+        cudaError_t e = cudaFuncSetAttribute(colscan_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        set[ctx.device] = smem;
+    }
+    const int64_t grid = P.nimg * P.strips;
+    if (grid <= 0) return cudaSuccess;
+    colscan_kernel<T><<<(unsigned)grid, kColThreads, smem, ctx.stream>>>(P);
+    return cudaGetLastError();
+}
+
+// Row pitch of the intermediates: Wo rounded up to 16 elements, so every
+// row starts 16-byte aligned.
+static int64_t mid_pitch(int64_t Wo) { return (Wo + 15) / 16 * 16; }
+
+template <typename T>
+static mmf_status filter2d(const LaunchCtx &ctx, const T *in, int64_t nimg, int64_t H, int64_t W, int64_t pitch,
+                           int64_t wy, int64_t wx, T *omax, T *omin, void *work) {
+    const int64_t Ho = H - wy + 1, Wo = W - wx + 1;
+    cudaError_t e = cudaSuccess;
+    if (wy == 1) {  // rows only, straight into the outputs
+        SeriesDesc sd{0, W, 0, wx, 0, Wo};
+        e = blockscan_rows<T>(ctx, in, sd, nimg * H, pitch, Wo, omax, omin);
+        return e == cudaSuccess ? MMF_OK : cuda_error(e, "row pass");
+    }
+    ColParams P{};
+    P.out_max = omax;
+    P.out_min = omin;
+    P.nimg = nimg;
+    P.H = H;
+    P.Wc = Wo;
+    P.out_pitch = Wo;
+    P.out_img = Ho * Wo;
+    P.wy = (int)wy;
+    if (wx == 1) {  // columns only, on the image
+        P.src_max = in;
+        P.src_min = in;
+        P.in_pitch = pitch;
+        P.in_img = H * pitch;
+    } else {
+        const int64_t wp = mid_pitch(Wo);
+        T *rmax = static_cast<T *>(work);
+        T *rmin = rmax + nimg * H * wp;
+        SeriesDesc sd{0, W, 0, wx, 0, Wo};
+        // Each image row is a row of the input; rows of consecutive images are
+        // `pitch` apart as well (images are stacked).
+        e = blockscan_rows<T>(ctx, in, sd, nimg * H, pitch, wp, rmax, rmin);
+        if (e != cudaSuccess) return cuda_error(e, "row pass");
+        P.src_max = rmax;
+        P.src_min = rmin;
+        P.in_pitch = wp;
+        P.in_img = H * wp;
+    }
+    e = col_launch<T>(ctx, P);
+    return e == cudaSuccess ? MMF_OK : cuda_error(e, "column pass");
+}
+
+static mmf_status check2d(int64_t nimg, int64_t H, int64_t W, int64_t pitch, int64_t wy, int64_t wx, mmf_dtype dt,
+                          int fuse) {
+    if (elem_size(dt) == 0) return set_error(MMF_EINVAL, "unknown dtype %d", (int)dt);
+    if (nimg < 0 || H < 0 || W < 0 || pitch < W) return set_error(MMF_EINVAL, "bad image geometry");
+    if (wy < 1 || wx < 1) return set_error(MMF_EINVAL, "windows must be >= 1");
+    if (fuse == 1) return set_error(MMF_ENOTIMPL, "the fused 2D kernel is not available for this request");
+    // Column-pass shared memory: P ring plus the tile-aggregate ring.
+    size_t smem = 0;
+    switch (dt) {
+        case MMF_F32: smem = col_smem_bytes<float>(wy); break;
+        case MMF_F64: smem = col_smem_bytes<double>(wy); break;
+        case MMF_I16: smem = col_smem_bytes<int16_t>(wy); break;
+        case MMF_U8: smem = col_smem_bytes<uint8_t>(wy); break;
+    }
+    if (smem > 227 * 1024) return set_error(MMF_ENOTIMPL, "column window %lld too large", (long long)wy);
+    return MMF_OK;
+}
+
+}  // namespace mmf
+
+using namespace mmf;
+
+extern "C" {
+
+mmf_status mmf_filter2d_workspace(int64_t nimg, int64_t H, int64_t W, int64_t wy, int64_t wx, mmf_dtype dtype,
+                                  int fuse, size_t *bytes) {
+    if (!bytes) return set_error(MMF_EINVAL, "NULL output");
+    mmf_status st = check2d(nimg, H, W, W, wy, wx, dtype, fuse);
+    if (st != MMF_OK) return st;
+    const int64_t Wo = W - wx + 1;
+    *bytes = (wy > 1 && wx > 1 && Wo > 0 && H >= wy) ? (size_t)(2 * nimg * H * mid_pitch(Wo) * elem_size(dtype)) : 0;
+    return MMF_OK;
+}
+
+mmf_status mmf_filter2d_separable(const void *d_in, int64_t nimg, int64_t H, int64_t W, int64_t pitch, int64_t wy,
+                                  int64_t wx, mmf_dtype dtype, int fuse, void *d_max, void *d_min, void *d_work,
+                                  size_t work_bytes, void *stream) {
+    mmf_status st = check2d(nimg, H, W, pitch, wy, wx, dtype, fuse);
+    if (st != MMF_OK) return st;
+    const int64_t Ho = H - wy + 1, Wo = W - wx + 1;
+    if (nimg == 0 || Ho <= 0 || Wo <= 0) return MMF_OK;
+    if (!d_in || (!d_max && !d_min)) return set_error(MMF_EINVAL, "NULL buffers");
+    size_t need = 0;
+    mmf_filter2d_workspace(nimg, H, W, wy, wx, dtype, fuse, &need);
+    if (work_bytes < need || (need && !d_work))
+        return set_error(MMF_EINVAL, "workspace of %zu bytes needed", need);
+    const int esz = elem_size(dtype);
+    if (((uintptr_t)d_in % esz) || ((uintptr_t)d_max % esz) || ((uintptr_t)d_min % esz) || ((uintptr_t)d_work % 16))
+        return set_error(MMF_EINVAL, "misaligned pointer (workspace needs 16 bytes)");
+    const int64_t cpt = esz >= 4 ? 1 : 2;
+    if (wy > 1 && (Wo % cpt || (wx == 1 && (pitch % cpt || (uintptr_t)d_in % (cpt * esz))) ||
+                   (uintptr_t)d_max % (cpt * esz) || (uintptr_t)d_min % (cpt * esz)))
+        return set_error(MMF_EINVAL, "for 1- and 2-byte types the output width and pointers must be even");
+    LaunchCtx ctx;
+    st = get_ctx(stream, &ctx);
+    if (st != MMF_OK) return st;
+    switch (dtype) {
+        case MMF_F32: return filter2d<float>(ctx, (const float *)d_in, nimg, H, W, pitch, wy, wx, (float *)d_max, (float *)d_min, d_work);
+        case MMF_F64: return filter2d<double>(ctx, (const double *)d_in, nimg, H, W, pitch, wy, wx, (double *)d_max, (double *)d_min, d_work);
+        case MMF_I16: return filter2d<int16_t>(ctx, (const int16_t *)d_in, nimg, H, W, pitch, wy, wx, (int16_t *)d_max, (int16_t *)d_min, d_work);
+        case MMF_U8: return filter2d<uint8_t>(ctx, (const uint8_t *)d_in, nimg, H, W, pitch, wy, wx, (uint8_t *)d_max, (uint8_t *)d_min, d_work);
+    }
+    return set_error(MMF_EINVAL, "unknown dtype");
+}
+
+}  // extern "C"

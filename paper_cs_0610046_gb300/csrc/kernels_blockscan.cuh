@@ -99,6 +99,34 @@ cudaError_t blockscan_1d(const LaunchCtx &ctx, const void *in, const SeriesDesc 
 }
 
 template <typename T>
+cudaError_t blockscan_rows(const LaunchCtx &ctx, const void *in, const SeriesDesc &sd, int64_t rows, int64_t in_pitch,
+                           int64_t out_pitch, void *omax, void *omin) {
+    using G = Geo<T>;
+    if (sd.n_out <= 0 || rows <= 0) return cudaSuccess;
+    const int mode = block_mode<T>(sd.w, true);
+    int per_sm = 1;
+    cudaError_t e = prepare_mode<T>(mode, ctx.device, &per_sm);
+    if (e != cudaSuccess) return e;
+    const int64_t tiles = (sd.n_out + G::T_ - 1) / G::T_;
+    const int64_t seg_tiles = tiles < 64 ? tiles : 64;
+    const int64_t row_items = (tiles + seg_tiles - 1) / seg_tiles;
+    BlockScanParams P{};
+    P.in = in;
+    P.out_max = omax;
+    P.out_min = omin;
+    P.one = sd;
+    P.seg_outputs = seg_tiles * G::T_;
+    P.row_items = row_items;
+    P.in_pitch = in_pitch;
+    P.out_pitch = out_pitch;
+    P.n_items = rows * row_items;
+    P.status = ctx.status;
+    const int64_t gmax = (int64_t)(ctx.sms > 0 ? ctx.sms : 1) * per_sm;
+    launch_mode<T>(mode, P, (int)(P.n_items < gmax ? P.n_items : gmax), ctx.stream);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t blockscan_table(const LaunchCtx &ctx, int mode, const void *in, void *omax, void *omin,
                             const SeriesDesc *d_series, const ItemDesc *d_items, int64_t n_items, int *d_ticket,
                             int grid) {
@@ -126,6 +154,8 @@ cudaError_t blockscan_table(const LaunchCtx &ctx, int mode, const void *in, void
 #define MMF_INSTANTIATE_BLOCKSCAN(T)                                                                             \
     template size_t mmf::blockscan_smem_bytes<T>();                                                            \
     template cudaError_t mmf::blockscan_prepare<T>(int, int);                                                  \
+    template cudaError_t mmf::blockscan_rows<T>(const LaunchCtx &, const void *, const SeriesDesc &, int64_t,   \
+                                                int64_t, int64_t, void *, void *);                            \
     template cudaError_t mmf::blockscan_1d<T>(const LaunchCtx &, const void *, const SeriesDesc &, void *,      \
                                                void *, bool);                                                   \
     template cudaError_t mmf::blockscan_table<T>(const LaunchCtx &, int, const void *, void *, void *,         \

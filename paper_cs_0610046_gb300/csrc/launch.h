@@ -21,6 +21,12 @@ template <typename T>
 cudaError_t blockscan_1d(const LaunchCtx &ctx, const void *in, const SeriesDesc &sd, void *omax, void *omin,
                          bool allow_slide);
 
+// The same series description applied to `rows` rows at the given element
+// pitches (row pass of the 2D filter); items are generated arithmetically.
+template <typename T>
+cudaError_t blockscan_rows(const LaunchCtx &ctx, const void *in, const SeriesDesc &sd, int64_t rows,
+                           int64_t in_pitch, int64_t out_pitch, void *omax, void *omin);
+
 // Table-driven launch (batched plans): items of one block mode, pulled from
 // an atomic ticket (or round-robin if d_ticket is null).  grid <= 0: one
 // persistent wave.
