@@ -110,10 +110,9 @@ int64_t mmf_output_length(int64_t n, int64_t w_or_r, mmf_mode mode);
  * that pass.  The row pass writes its two intermediates to `d_work` (16-byte
  * aligned, size from mmf_filter2d_workspace; none needed when wy or wx is 1).
  * fuse: -1 automatic, 0 row pass then column pass; 1 (a fused kernel) returns
- * MMF_ENOTIMPL.  For 1- and 2-byte types the output width W-wx+1 and the
- * output pointers must be even (and, when wx is 1, the pitch and input).
- * Column windows are limited by the column pass's shared memory: up to about
- * 760 rows for f32, 320 for f64 and 1700 for i16/u8 (MMF_ENOTIMPL beyond). */
+ * MMF_ENOTIMPL.  Column windows are limited by the column pass's shared
+ * memory: up to about 760 rows for f32, 320 for f64 and 1700 for i16/u8
+ * (MMF_ENOTIMPL beyond). */
 mmf_status mmf_filter2d_workspace(int64_t nimg, int64_t H, int64_t W, int64_t wy, int64_t wx, mmf_dtype dtype,
                                   int fuse, size_t *bytes);
 mmf_status mmf_filter2d_separable(const void *d_in, int64_t nimg, int64_t H, int64_t W, int64_t pitch,

@@ -40,10 +40,9 @@ struct ColParams {
 constexpr int kColThreads = 256;
 constexpr int kColRows = 8;  // rows per tile
 
-template <typename T> struct ColGeo {
-    static constexpr int CPT = sizeof(T) >= 4 ? 1 : 2;  // columns per thread
-    static constexpr int STRIP = kColThreads * CPT;
-};
+// Columns per thread: 2 for 1- and 2-byte types when widths and pointers
+// allow paired accesses (wider coalesced rows), else 1.
+template <typename T> constexpr int col_cpt_max() { return sizeof(T) >= 4 ? 1 : 2; }
 
 // Vector of CPT elements of one row (one load / store per row and thread).
 template <typename T, int CPT> struct RowVec;
@@ -79,10 +78,9 @@ template <> struct RowVec<int16_t, 2> {
 
 template <typename T> struct ColSmem {
     using Pair = typename Elem<T>::Pair;
-    static constexpr int CPT = ColGeo<T>::CPT;
     // P ring [2 slots][8 rows][CPT][threads] and aggregates [qcap][CPT][threads].
-    static size_t bytes(int qcap) {
-        return (size_t)(2 * kColRows + qcap) * CPT * kColThreads * sizeof(Pair);
+    static size_t bytes(int qcap, int cpt) {
+        return (size_t)(2 * kColRows + qcap) * cpt * kColThreads * sizeof(Pair);
     }
 };
 
@@ -113,11 +111,10 @@ __device__ __forceinline__ void col_store(T *col, int64_t pitch, int64_t y, int6
         if (y + r < Ho) RowVec<T, CPT>::store(col + (y + r) * pitch, v[r]);
 }
 
-template <typename T, int W>
+template <typename T, int CPT, int W>
 __device__ __forceinline__ void col_slide(const ColParams &P, const T *smax, const T *smin, T *omax, T *omin,
                                           int64_t Ho) {
     using R = typename Elem<T>::R;
-    constexpr int CPT = ColGeo<T>::CPT;
     constexpr int P2 = W >= 8 ? 8 : (W >= 4 ? 4 : (W >= 2 ? 2 : 1));
     R cm[kColRows][CPT], cn[kColRows][CPT];  // current tile
     col_tile<T, CPT>(smax, P.in_pitch, 0, P.H, Elem<T>::lo(), cm);
@@ -155,12 +152,11 @@ __device__ __forceinline__ void col_slide(const ColParams &P, const T *smax, con
     }
 }
 
-template <typename T>
+template <typename T, int CPT>
 __device__ __forceinline__ void col_blocks(const ColParams &P, const T *smax, const T *smin, T *omax, T *omin,
                                            int64_t Ho) {
     using R = typename Elem<T>::R;
     using Pair = typename Elem<T>::Pair;
-    constexpr int CPT = ColGeo<T>::CPT;
     const int tid = threadIdx.x;
     const int s = P.wy - 1;
     const int q = s >> 3, rr = s & 7;
@@ -244,12 +240,11 @@ __device__ __forceinline__ void col_blocks(const ColParams &P, const T *smax, co
     }
 }
 
-template <typename T>
+template <typename T, int CPT>
 __global__ void __launch_bounds__(kColThreads) colscan_kernel(const ColParams P) {
-    constexpr int CPT = ColGeo<T>::CPT;
     const int64_t img = blockIdx.x / P.strips;
     const int64_t strip = blockIdx.x % P.strips;
-    const int64_t x = strip * ColGeo<T>::STRIP + (int64_t)threadIdx.x * CPT;
+    const int64_t x = strip * (kColThreads * CPT) + (int64_t)threadIdx.x * CPT;
     const int64_t Ho = P.H - P.wy + 1;
     if (x >= P.Wc || Ho <= 0 || img >= P.nimg) return;  // no barriers below
     const T *smax = reinterpret_cast<const T *>(P.src_max) + img * P.in_img + x;
@@ -257,16 +252,16 @@ __global__ void __launch_bounds__(kColThreads) colscan_kernel(const ColParams P)
     T *omax = P.out_max ? reinterpret_cast<T *>(P.out_max) + img * P.out_img + x : nullptr;
     T *omin = P.out_min ? reinterpret_cast<T *>(P.out_min) + img * P.out_img + x : nullptr;
     switch (P.wy) {
-        case 1: col_slide<T, 1>(P, smax, smin, omax, omin, Ho); break;
-        case 2: col_slide<T, 2>(P, smax, smin, omax, omin, Ho); break;
-        case 3: col_slide<T, 3>(P, smax, smin, omax, omin, Ho); break;
-        case 4: col_slide<T, 4>(P, smax, smin, omax, omin, Ho); break;
-        case 5: col_slide<T, 5>(P, smax, smin, omax, omin, Ho); break;
-        case 6: col_slide<T, 6>(P, smax, smin, omax, omin, Ho); break;
-        case 7: col_slide<T, 7>(P, smax, smin, omax, omin, Ho); break;
-        case 8: col_slide<T, 8>(P, smax, smin, omax, omin, Ho); break;
-        case 9: col_slide<T, 9>(P, smax, smin, omax, omin, Ho); break;
-        default: col_blocks<T>(P, smax, smin, omax, omin, Ho); break;
+        case 1: col_slide<T, CPT, 1>(P, smax, smin, omax, omin, Ho); break;
+        case 2: col_slide<T, CPT, 2>(P, smax, smin, omax, omin, Ho); break;
+        case 3: col_slide<T, CPT, 3>(P, smax, smin, omax, omin, Ho); break;
+        case 4: col_slide<T, CPT, 4>(P, smax, smin, omax, omin, Ho); break;
+        case 5: col_slide<T, CPT, 5>(P, smax, smin, omax, omin, Ho); break;
+        case 6: col_slide<T, CPT, 6>(P, smax, smin, omax, omin, Ho); break;
+        case 7: col_slide<T, CPT, 7>(P, smax, smin, omax, omin, Ho); break;
+        case 8: col_slide<T, CPT, 8>(P, smax, smin, omax, omin, Ho); break;
+        case 9: col_slide<T, CPT, 9>(P, smax, smin, omax, omin, Ho); break;
+        default: col_blocks<T, CPT>(P, smax, smin, omax, omin, Ho); break;
     }
 }
 

@@ -17,24 +17,38 @@ int elem_size(mmf_dtype dt);
 
 template <typename T> static int col_qcap(int64_t wy) { return wy >= 10 ? (int)((wy - 1) / 8) + 2 : 0; }
 
-template <typename T> static size_t col_smem_bytes(int64_t wy) { return ColSmem<T>::bytes(col_qcap<T>(wy)); }
+template <typename T> static size_t col_smem_bytes(int64_t wy, int cpt = col_cpt_max<T>()) {
+    return ColSmem<T>::bytes(col_qcap<T>(wy), cpt);
+}
 
-template <typename T> static cudaError_t col_launch(const LaunchCtx &ctx, const ColParams &P0) {
-    ColParams P = P0;
-    P.strips = (int)((P.Wc + ColGeo<T>::STRIP - 1) / ColGeo<T>::STRIP);
+template <typename T, int CPT> static cudaError_t col_launch_cpt(const LaunchCtx &ctx, ColParams P) {
+    P.strips = (int)((P.Wc + kColThreads * CPT - 1) / (kColThreads * CPT));
     P.qcap = col_qcap<T>(P.wy);
     P.status = ctx.status;
-    const size_t smem = col_smem_bytes<T>(P.wy);
+    const size_t smem = col_smem_bytes<T>(P.wy, CPT);
     static size_t set[64] = {0};
     if (smem > set[ctx.device]) {
-        cudaError_t e = cudaFuncSetAttribute(colscan_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(colscan_kernel<T, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         set[ctx.device] = smem;
     }
     const int64_t grid = P.nimg * P.strips;
     if (grid <= 0) return cudaSuccess;
-    colscan_kernel<T><<<(unsigned)grid, kColThreads, smem, ctx.stream>>>(P);
+    colscan_kernel<T, CPT><<<(unsigned)grid, kColThreads, smem, ctx.stream>>>(P);
     return cudaGetLastError();
+}
+
+// Paired columns when every row start and the width allow it.
+template <typename T> static cudaError_t col_launch(const LaunchCtx &ctx, const ColParams &P) {
+    if constexpr (col_cpt_max<T>() == 2) {
+        const uintptr_t a = 2 * sizeof(T) - 1;
+        const bool paired = P.Wc % 2 == 0 && P.in_pitch % 2 == 0 && P.in_img % 2 == 0 && P.out_pitch % 2 == 0 &&
+                            P.out_img % 2 == 0 && ((uintptr_t)P.src_max & a) == 0 && ((uintptr_t)P.src_min & a) == 0 &&
+                            ((uintptr_t)P.out_max & a) == 0 && ((uintptr_t)P.out_min & a) == 0;
+        if (paired) return col_launch_cpt<T, 2>(ctx, P);
+    }
+    return col_launch_cpt<T, 1>(ctx, P);
 }
 
 // Row pitch of the intermediates: Wo rounded up to 16 elements, so every
@@ -94,8 +108,8 @@ static mmf_status check2d(int64_t nimg, int64_t H, int64_t W, int64_t pitch, int
     switch (dt) {
         case MMF_F32: smem = col_smem_bytes<float>(wy); break;
         case MMF_F64: smem = col_smem_bytes<double>(wy); break;
-        case MMF_I16: smem = col_smem_bytes<int16_t>(wy); break;
-        case MMF_U8: smem = col_smem_bytes<uint8_t>(wy); break;
+        case MMF_I16: smem = col_smem_bytes<int16_t>(wy, 1); break;
+        case MMF_U8: smem = col_smem_bytes<uint8_t>(wy, 1); break;
     }
     if (smem > 227 * 1024) return set_error(MMF_ENOTIMPL, "column window %lld too large", (long long)wy);
     return MMF_OK;
@@ -132,10 +146,6 @@ mmf_status mmf_filter2d_separable(const void *d_in, int64_t nimg, int64_t H, int
     const int esz = elem_size(dtype);
     if (((uintptr_t)d_in % esz) || ((uintptr_t)d_max % esz) || ((uintptr_t)d_min % esz) || ((uintptr_t)d_work % 16))
         return set_error(MMF_EINVAL, "misaligned pointer (workspace needs 16 bytes)");
-    const int64_t cpt = esz >= 4 ? 1 : 2;
-    if (wy > 1 && (Wo % cpt || (wx == 1 && (pitch % cpt || (uintptr_t)d_in % (cpt * esz))) ||
-                   (uintptr_t)d_max % (cpt * esz) || (uintptr_t)d_min % (cpt * esz)))
-        return set_error(MMF_EINVAL, "for 1- and 2-byte types the output width and pointers must be even");
     LaunchCtx ctx;
     st = get_ctx(stream, &ctx);
     if (st != MMF_OK) return st;
