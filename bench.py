@@ -243,6 +243,58 @@ def batched_extras(dev, stream, peak, reps=5, envelope_series=1_000_000):
     return out
 
 
+def blobs_torch(nimg, H, W, seed, dev, nblobs=200):
+    """The 2D recipe (sum of Gaussian blobs + 10 % uniform noise) drawn on the
+    device: each image is an outer-product sum, one GEMM."""
+    import torch
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    out = torch.empty((nimg, H, W), dtype=torch.float32, device=dev)
+    ys = torch.arange(H, device=dev, dtype=torch.float32)
+    xs = torch.arange(W, device=dev, dtype=torch.float32)
+    for k in range(nimg):
+        cy = torch.rand(nblobs, generator=g, device=dev) * H
+        cx = torch.rand(nblobs, generator=g, device=dev) * W
+        sig = 5 + torch.rand(nblobs, generator=g, device=dev) * 195
+        amp = torch.rand(nblobs, generator=g, device=dev)
+        gy = torch.exp(-0.5 * ((ys[None, :] - cy[:, None]) / sig[:, None]) ** 2) * amp[:, None]
+        gx = torch.exp(-0.5 * ((xs[None, :] - cx[:, None]) / sig[:, None]) ** 2)
+        img = gy.T @ gx
+        rng = (img.max() - img.min()).clamp_min(1e-6)
+        img += torch.rand((H, W), generator=g, device=dev) * 0.1 * rng
+        out[k] = img
+    return out
+
+
+def filter2d_extras(dev, stream, peak, nimg=64, H=4096, W=4096, reps=3):
+    """64 images of 4096 x 4096, uint8 and fp32, five windows; row pass then
+    column pass.  Algorithmic bytes: the image once plus both outputs."""
+    import torch
+    import paper_cs_0610046_gb300 as mmf
+    f = blobs_torch(nimg, H, W, 41, dev)
+    lo, hi = f.amin(dim=(1, 2), keepdim=True), f.amax(dim=(1, 2), keepdim=True)
+    u8 = torch.round((f - lo) / (hi - lo) * 255).clamp(0, 255).to(torch.uint8)
+    res = {}
+    for name, x in (("u8", u8), ("f32", f)):
+        sz = x.element_size()
+        for wy, wx in ((3, 3), (15, 15), (63, 63), (255, 1), (1, 255)):
+            Ho, Wo = H - wy + 1, W - wx + 1
+            om = torch.empty((nimg, Ho, Wo), dtype=x.dtype, device=dev)
+            on = torch.empty((nimg, Ho, Wo), dtype=x.dtype, device=dev)
+            ws = torch.empty(2 * nimg * H * ((Wo + 15) // 16 * 16) * sz if wy > 1 and wx > 1 else 16,
+                             dtype=torch.uint8, device=dev)
+            mmf.filter2d(x, wy, wx, out_max=om, out_min=on, workspace=ws, stream=stream)
+            ms = _events_ms(lambda: mmf.filter2d(x, wy, wx, out_max=om, out_min=on, workspace=ws,
+                                                 stream=stream), reps, stream)
+            byts = (nimg * H * W + 2 * nimg * Ho * Wo) * sz
+            res[f"{name}_{wy}x{wx}"] = {"ms": ms, "Gpix_s": nimg * H * W / ms / 1e6,
+                                        "GBps": byts / ms / 1e6, "frac": byts / ms / 1e6 / peak}
+            del om, on, ws
+    del f, u8
+    torch.cuda.empty_cache()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -417,6 +469,7 @@ def main():
         del xs
         torch.cuda.empty_cache()
         extras["batched"] = batched_extras(dev, stream, peak)
+        extras["filter2d"] = filter2d_extras(dev, stream, peak)
 
     status = mmf.device_status(reset=True)
     cpu = None
