@@ -171,6 +171,66 @@ mmf_status mmf_filter1d_batched(mmf_batch_plan *plan, const void *d_in, void *d_
 mmf_status mmf_filter1d_per_series(const mmf_batch_plan *plan, const void *d_in, void *d_max, void *d_min,
                                    void *stream);
 
+/* ---------------------------------------------------------- serving ---- */
+
+/* A streaming service: many concurrent streams, each filtered with zero
+ * stream latency (Section 1: a window's outputs are emitted as soon as its
+ * last element has arrived).  Each stream's last w-1 samples and its int64
+ * sample count stay on the device, so the outputs of the chunks pushed to a
+ * stream are exactly the whole-array filter of their concatenation (VALID
+ * windows).  Chunks are admitted FIFO while the device-memory budget allows,
+ * at most one chunk per stream in flight, and batched across streams into one
+ * launch per kernel group (continuous batching: a chunk that arrives while a
+ * batch runs joins a later batch as soon as memory and its stream allow).  The
+ * server owns a worker thread, its device budget and a few CUDA streams; all
+ * its functions are thread-safe. */
+typedef struct mmf_server mmf_server;
+
+typedef struct {
+    int64_t chunks;             /* chunks completed (since the last reset) */
+    int64_t elements;           /* their input samples */
+    int64_t batches;            /* batches launched */
+    double p50_ms, p99_ms;      /* push-to-completion latency percentiles */
+    double max_ms;
+    int64_t queued;             /* chunks waiting for admission now */
+    int64_t device_bytes_used;  /* budget in use now */
+} mmf_server_stats_t;
+
+/* device_budget_bytes: one device allocation shared by stream state, chunk
+ * staging and outputs (>= 1 MiB); max_batch: chunks per launch. */
+mmf_status mmf_server_create(size_t device_budget_bytes, int max_batch, mmf_dtype dtype, mmf_server **out);
+
+/* Stops the worker after the batches already on the GPU, frees everything. */
+void mmf_server_destroy(mmf_server *server);
+
+/* Opens a stream with window w >= 1 (state: w-1 samples of the budget;
+ * MMF_ENOMEM if the budget is exhausted). */
+mmf_status mmf_stream_open(mmf_server *server, int64_t w, uint64_t *stream_id);
+
+/* Queues len samples (HOST pointer; pinned memory is faster) for the stream
+ * and returns at once.  *n_out receives the number of outputs of this chunk,
+ * max(0, N+len-w+1) - max(0, N-w+1) for N samples pushed before it; they are
+ * written to the HOST buffers h_max/h_min (either may be NULL, not both when
+ * *n_out > 0).  h_chunk, h_max and h_min must stay valid until the ticket
+ * completes.  MMF_ECLOSED for a closed or unknown stream, MMF_ENOMEM for a
+ * chunk that can never fit the budget, MMF_EDEVICE after a device failure. */
+mmf_status mmf_stream_push(mmf_server *server, uint64_t stream_id, const void *h_chunk, int64_t len, void *h_max,
+                           void *h_min, int64_t *n_out, uint64_t *ticket);
+
+/* Waits up to timeout_ms for a ticket (MMF_ETIMEOUT if not done; the ticket
+ * stays valid).  A completed ticket is consumed. */
+mmf_status mmf_ticket_wait(mmf_server *server, uint64_t ticket, int timeout_ms);
+
+/* Refuses further pushes, waits up to timeout_ms for the stream's chunks,
+ * frees its state (MMF_ETIMEOUT leaves it closed but not yet freed). */
+mmf_status mmf_stream_close(mmf_server *server, uint64_t stream_id, int timeout_ms);
+
+/* Stops (1) or resumes (0) admissions: for tests of stalled service. */
+mmf_status mmf_server_pause(mmf_server *server, int paused);
+
+/* Latency percentiles and counters; reset != 0 clears them. */
+mmf_status mmf_server_stats(mmf_server *server, int reset, mmf_server_stats_t *out);
+
 /* ------------------------------------------- batched, no allocation ---- */
 
 /* Limits of mmf_filter1d_batched_noalloc. */

@@ -17,7 +17,7 @@ import threading
 
 import torch
 
-__all__ = ["MMFError", "load", "filter1d", "output_length", "device_status", "BatchPlan", "filter2d", "DTYPES", "KERNELS"]
+__all__ = ["MMFError", "load", "filter1d", "output_length", "device_status", "BatchPlan", "filter2d", "Server", "n_outputs", "DTYPES", "KERNELS"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmmf.so")
@@ -87,6 +87,13 @@ _EXTRA_SIGNATURES: dict = {
     "mmf_batch_plan_autotune": ([_VP, _VP, _VP, _VP, _VP], _INT),
     "mmf_filter1d_batched": ([_VP, _VP, _VP, _VP, _VP], _INT),
     "mmf_filter1d_per_series": ([_VP, _VP, _VP, _VP, _VP], _INT),
+    "mmf_server_create": ([ctypes.c_size_t, _INT, _INT, ctypes.POINTER(_VP)], _INT),
+    "mmf_server_destroy": ([_VP], None),
+    "mmf_stream_open": ([_VP, _I64, ctypes.POINTER(ctypes.c_uint64)], _INT),
+    "mmf_stream_push": ([_VP, ctypes.c_uint64, _VP, _I64, _VP, _VP, _P64, ctypes.POINTER(ctypes.c_uint64)], _INT),
+    "mmf_ticket_wait": ([_VP, ctypes.c_uint64, _INT], _INT),
+    "mmf_stream_close": ([_VP, ctypes.c_uint64, _INT], _INT),
+    "mmf_server_pause": ([_VP, _INT], _INT),
     "mmf_filter2d_workspace": ([_I64, _I64, _I64, _I64, _I64, _INT, _INT, ctypes.POINTER(ctypes.c_size_t)], _INT),
     "mmf_filter2d_separable": ([_VP, _I64, _I64, _I64, _I64, _I64, _I64, _INT, _INT, _VP, _VP, _VP,
                                 ctypes.c_size_t, _VP], _INT),
@@ -276,6 +283,86 @@ def filter2d(x: torch.Tensor, wy: int, wx: int, fuse: int = -1, out_max=None, ou
                                          _ptr(out_max), _ptr(out_min), _ptr(workspace),
                                          need.value, _VP(_stream_handle(stream))))
     return out_max, out_min
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("chunks", ctypes.c_int64), ("elements", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("queued", ctypes.c_int64), ("device_bytes_used", ctypes.c_int64)]
+
+
+_NP_DTYPES = {"float32": 0, "float64": 1, "int16": 2, "uint8": 3}
+
+
+class Server:
+    """Streaming service (``mmf_server_*``): zero-latency running max-min of
+    many concurrent streams with continuous batching on the device.
+
+    Chunks and outputs are numpy arrays in host memory (pinned arrays, e.g.
+    from ``torch.empty(..., pin_memory=True).numpy()``, copy faster); they must
+    stay alive until their ticket is waited for."""
+
+    def __init__(self, budget_bytes: int = 1 << 30, max_batch: int = 256, dtype: str = "float32"):
+        lib = load()
+        self._lib = lib
+        self.dtype = dtype
+        h = _VP()
+        check(lib.mmf_server_create(budget_bytes, max_batch, _NP_DTYPES[dtype], ctypes.byref(h)))
+        self._h = h
+        self._keep = {}
+        lib.mmf_server_stats.argtypes = [_VP, _INT, ctypes.POINTER(ServerStats)]
+        lib.mmf_server_stats.restype = _INT
+
+    def open(self, w: int) -> int:
+        sid = ctypes.c_uint64(0)
+        check(self._lib.mmf_stream_open(self._h, w, ctypes.byref(sid)))
+        return int(sid.value)
+
+    def push(self, sid: int, chunk, out_max=None, out_min=None):
+        """Queue ``chunk`` (1D numpy array); returns ``(ticket, n_out)``.
+        ``out_max``/``out_min`` must hold n_out elements (see n_outputs)."""
+        import numpy as np
+        assert chunk.dtype == np.dtype(self.dtype) and chunk.flags["C_CONTIGUOUS"]
+        n_out = ctypes.c_int64(0)
+        t = ctypes.c_uint64(0)
+        p = lambda a: None if a is None else ctypes.c_void_p(a.ctypes.data)
+        check(self._lib.mmf_stream_push(self._h, sid, p(chunk), chunk.size, p(out_max), p(out_min),
+                                        ctypes.byref(n_out), ctypes.byref(t)))
+        self._keep[int(t.value)] = (chunk, out_max, out_min)
+        return int(t.value), int(n_out.value)
+
+    def wait(self, ticket: int, timeout_ms: int = 60_000) -> None:
+        check(self._lib.mmf_ticket_wait(self._h, ticket, timeout_ms))
+        self._keep.pop(ticket, None)
+
+    def close_stream(self, sid: int, timeout_ms: int = 60_000) -> None:
+        check(self._lib.mmf_stream_close(self._h, sid, timeout_ms))
+
+    def pause(self, paused: bool = True) -> None:
+        check(self._lib.mmf_server_pause(self._h, 1 if paused else 0))
+
+    def stats(self, reset: bool = False) -> dict:
+        st = ServerStats()
+        check(self._lib.mmf_server_stats(self._h, 1 if reset else 0, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mmf_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def n_outputs(count_before: int, chunk_len: int, w: int) -> int:
+    """Outputs of a chunk of chunk_len samples pushed after count_before
+    samples to a stream with window w (windows ending inside the chunk)."""
+    return max(0, count_before + chunk_len - w + 1) - max(0, count_before - w + 1)
 
 
 def device_status(reset: bool = True) -> int:

@@ -1,0 +1,574 @@
+// Streaming service: many concurrent streams, each filtered with zero stream
+// latency (Section 1: an output is emitted as soon as the last element of its
+// window has arrived).  Each stream keeps its last w-1 samples (the halo) and
+// its sample count (int64, as the paper advises for streams) on the device, so
+// the outputs of a chunk are exactly those of the whole-array filter for the
+// windows that end inside the chunk.
+//
+// Continuous batching: push() queues a chunk and returns a ticket.  A worker
+// thread repeatedly admits queued chunks (FIFO, at most one chunk per stream
+// in flight, while the device-memory budget allows), and runs each admitted
+// batch as: host-to-device copies of the chunks behind their streams' halos,
+// one batched filter launch per kernel group over all of them, one
+// halo-update launch, and device-to-host copies of the outputs.  Batches
+// rotate over a few CUDA streams so that copies and kernels of consecutive
+// batches overlap; chunks that arrive while a batch runs join the next batch
+// as soon as memory and their stream allow.  Completion is observed through
+// events; the release-to-completion latency of every chunk is recorded.
+//
+// Device memory: the budget is split into a staging pool (halos and chunk
+// inputs) and an output pool whose max and min halves mirror each other (a
+// chunk's min outputs sit at the same offset in the min half).
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "launch.h"
+#include "mmf.h"
+
+namespace mmf {
+mmf_status set_error(mmf_status st, const char *fmt, ...);
+mmf_status cuda_error(cudaError_t e, const char *what);
+mmf_status get_ctx(void *stream, LaunchCtx *ctx);
+int elem_size(mmf_dtype dt);
+
+// Copies the new halo of each stream of a batch: the last h_new elements of
+// its staging block [halo | chunk].
+template <typename T>
+__global__ void halo_update_kernel(const SeriesDesc *series, const int64_t *halo_off, const int64_t *h_new,
+                                   T *base, int n) {
+    const int i = blockIdx.x;
+    if (i >= n) return;
+    const SeriesDesc sd = series[i];
+    const int64_t h = h_new[i];
+    const T *src = base + sd.in_off + sd.n - h;
+    T *dst = base + halo_off[i];
+    for (int64_t k = threadIdx.x; k < h; k += blockDim.x) dst[k] = src[k];
+}
+}  // namespace mmf
+
+using namespace mmf;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+// First-fit allocator over [0, size) with coalescing; offsets 256-aligned.
+class Arena {
+  public:
+    void init(size_t size) {
+        size_ = size;
+        free_.clear();
+        if (size) free_[0] = size;
+    }
+    int64_t alloc(size_t bytes) {
+        bytes = round(bytes);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                const size_t off = it->first, sz = it->second;
+                free_.erase(it);
+                if (sz > bytes) free_[off + bytes] = sz - bytes;
+                used_ += bytes;
+                return (int64_t)off;
+            }
+        }
+        return -1;
+    }
+    void release(int64_t off, size_t bytes) {
+        bytes = round(bytes);
+        used_ -= bytes;
+        auto it = free_.emplace((size_t)off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    size_t size() const { return size_; }
+    size_t used() const { return used_; }
+    static size_t round(size_t b) { return (std::max<size_t>(b, 1) + 255) & ~size_t(255); }
+
+  private:
+    size_t size_ = 0, used_ = 0;
+    std::map<size_t, size_t> free_;
+};
+
+struct Request {
+    uint64_t ticket;
+    uint64_t stream;
+    const void *h_in;
+    int64_t len;
+    void *h_max, *h_min;
+    int64_t n_out;
+    Clock::time_point released;
+};
+
+struct StreamState {
+    int64_t w = 0;
+    int64_t count = 0;      // samples pushed so far (int64: unbounded streams)
+    int64_t halo_off = -1;  // staging-arena block of w-1 elements
+    int64_t halo_len = 0;   // min(count, w-1) once the pushes so far are done
+    bool in_flight = false;
+    bool closed = false;
+    int64_t pending = 0;    // queued or in flight
+};
+
+struct Batch {
+    std::vector<Request> reqs;
+    std::vector<std::pair<int64_t, size_t>> stage_blocks, out_blocks;
+    std::vector<int64_t> halo_after;
+    cudaEvent_t done = nullptr;
+};
+
+constexpr int kSlots = 3;  // CUDA streams that batches rotate over
+constexpr int64_t kTicketDone = 1, kTicketFailed = 2;
+
+}  // namespace
+
+struct mmf_server {
+    int device = 0;
+    mmf_dtype dtype = MMF_F32;
+    int64_t esz = 4;
+    int max_batch = 256;
+    char *dev_base = nullptr;  // one allocation: staging arena, then output halves
+    size_t stage_size = 0, out_half = 0;
+    Arena stage, out;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::unordered_map<uint64_t, StreamState> streams;
+    std::deque<Request> queue;
+    std::deque<Batch> inflight;
+    std::unordered_map<uint64_t, int64_t> tickets;  // 0 pending, 1 done, 2 failed
+    uint64_t next_stream = 1, next_ticket = 1;
+    bool stop = false, paused = false;
+    mmf_status failed = MMF_OK;
+    std::thread worker;
+    cudaStream_t slots[kSlots] = {};
+    cudaEvent_t slot_free[kSlots] = {};
+    SeriesDesc *d_series[kSlots] = {};
+    ItemDesc *d_items[kSlots] = {};
+    int64_t *d_halo[kSlots] = {};  // [2][max_batch]: halo offsets, new halo lengths
+    int *d_tick[kSlots] = {};
+    SeriesDesc *h_series[kSlots] = {};  // pinned staging of the tables
+    ItemDesc *h_items[kSlots] = {};
+    int64_t *h_halo[kSlots] = {};
+    uint64_t nbatches = 0;
+    std::vector<double> lat_ms;
+    int64_t done_chunks = 0, done_elems = 0;
+};
+
+namespace {
+
+int mode_for(mmf_dtype dt, int64_t w) {
+    switch (dt) {
+        case MMF_F32: return block_mode<float>(w, true);
+        case MMF_F64: return block_mode<double>(w, true);
+        case MMF_I16: return block_mode<int16_t>(w, true);
+        default: return block_mode<uint8_t>(w, true);
+    }
+}
+
+cudaError_t launch_group(mmf_server *S, const LaunchCtx &ctx, int g, int slot, const ItemDesc *items, int64_t ni) {
+    char *base = S->dev_base;
+    char *omax = base + S->stage_size, *omin = omax + S->out_half;
+    switch (S->dtype) {
+        case MMF_F32: return blockscan_table<float>(ctx, g, base, omax, omin, S->d_series[slot], items, ni, S->d_tick[slot] + g, 0);
+        case MMF_F64: return blockscan_table<double>(ctx, g, base, omax, omin, S->d_series[slot], items, ni, S->d_tick[slot] + g, 0);
+        case MMF_I16: return blockscan_table<int16_t>(ctx, g, base, omax, omin, S->d_series[slot], items, ni, S->d_tick[slot] + g, 0);
+        default: return blockscan_table<uint8_t>(ctx, g, base, omax, omin, S->d_series[slot], items, ni, S->d_tick[slot] + g, 0);
+    }
+}
+
+cudaError_t launch_halo(mmf_server *S, int slot, int n, cudaStream_t st) {
+    const int64_t *hoff = S->d_halo[slot];
+    const int64_t *hnew = hoff + S->max_batch;
+    switch (S->dtype) {
+        case MMF_F32: halo_update_kernel<float><<<n, 256, 0, st>>>(S->d_series[slot], hoff, hnew, (float *)S->dev_base, n); break;
+        case MMF_F64: halo_update_kernel<double><<<n, 256, 0, st>>>(S->d_series[slot], hoff, hnew, (double *)S->dev_base, n); break;
+        case MMF_I16: halo_update_kernel<int16_t><<<n, 256, 0, st>>>(S->d_series[slot], hoff, hnew, (int16_t *)S->dev_base, n); break;
+        default: halo_update_kernel<uint8_t><<<n, 256, 0, st>>>(S->d_series[slot], hoff, hnew, (uint8_t *)S->dev_base, n); break;
+    }
+    return cudaGetLastError();
+}
+
+// With S->mu held: admit one batch and enqueue its work (the lock is dropped
+// around the CUDA calls).  Returns false if nothing could be admitted.
+bool run_batch(mmf_server *S, std::unique_lock<std::mutex> &lk) {
+    const int slot = (int)(S->nbatches % kSlots);
+    // The slot's pinned tables and device tables are reused: wait for the
+    // batch that last used this slot to have finished its uploads.
+    if (cudaEventQuery(S->slot_free[slot]) == cudaErrorNotReady) return false;
+    Batch b;
+    std::vector<int64_t> stage_off, out_off, halo_before;
+    const int64_t esz = S->esz;
+    for (auto it = S->queue.begin(); it != S->queue.end() && (int)b.reqs.size() < S->max_batch;) {
+        StreamState &ss = S->streams[it->stream];
+        if (ss.in_flight) {
+            ++it;
+            continue;
+        }
+        const int64_t h = ss.halo_len;
+        const size_t in_bytes = (size_t)(h + it->len) * esz;
+        const size_t out_bytes = (size_t)it->n_out * esz;
+        const int64_t ib = S->stage.alloc(in_bytes);
+        if (ib < 0) break;  // no room: wait for completions (FIFO admission)
+        const int64_t ob = S->out.alloc(out_bytes);
+        if (ob < 0) {
+            S->stage.release(ib, in_bytes);
+            break;
+        }
+        ss.in_flight = true;
+        b.reqs.push_back(*it);
+        b.stage_blocks.push_back({ib, in_bytes});
+        b.out_blocks.push_back({ob, out_bytes});
+        stage_off.push_back(ib);
+        out_off.push_back(ob);
+        halo_before.push_back(h);
+        // State after this chunk (used by the next chunk of the stream, which
+        // cannot be admitted before this one completes).
+        ss.count += it->len;
+        ss.halo_len = std::min<int64_t>(ss.count, ss.w - 1);
+        b.halo_after.push_back(ss.halo_len);
+        it = S->queue.erase(it);
+    }
+    if (b.reqs.empty()) return false;
+    S->nbatches++;
+    const int n = (int)b.reqs.size();
+    int64_t counts[4] = {0, 0, 0, 0};
+    std::vector<int> modes(n);
+    std::vector<int64_t> hoffs(n);
+    for (int i = 0; i < n; ++i) {
+        const Request &r = b.reqs[i];
+        const StreamState &ss = S->streams[r.stream];
+        SeriesDesc &sd = S->h_series[slot][i];
+        sd.in_off = stage_off[i] / esz;
+        sd.n = halo_before[i] + r.len;
+        sd.out_off = out_off[i] / esz;
+        sd.w = ss.w;
+        sd.d = 0;
+        sd.n_out = r.n_out;
+        modes[i] = mode_for(S->dtype, ss.w);
+        if (r.n_out > 0) counts[modes[i]]++;  // chunks without outputs only move the halo
+        hoffs[i] = ss.halo_off;
+        S->h_halo[slot][i] = ss.halo_off / esz;
+        S->h_halo[slot][S->max_batch + i] = b.halo_after[i];
+    }
+    int64_t pos[4], acc = 0;
+    for (int g = 0; g < 4; ++g) {
+        pos[g] = acc;
+        acc += counts[g];
+    }
+    for (int i = 0; i < n; ++i)
+        if (b.reqs[i].n_out > 0) S->h_items[slot][pos[modes[i]]++] = {i, 0, b.reqs[i].n_out};
+    lk.unlock();
+
+    cudaStream_t st = S->slots[slot];
+    char *base = S->dev_base;
+    char *omax = base + S->stage_size, *omin = omax + S->out_half;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        const Request &r = b.reqs[i];
+        char *stage = base + stage_off[i];
+        if (halo_before[i] > 0)
+            e = cudaMemcpyAsync(stage, base + hoffs[i], halo_before[i] * esz, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess && r.len > 0)
+            e = cudaMemcpyAsync(stage + halo_before[i] * esz, r.h_in, r.len * esz, cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(S->d_series[slot], S->h_series[slot], n * sizeof(SeriesDesc), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(S->d_items[slot], S->h_items[slot], n * sizeof(ItemDesc), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(S->d_halo[slot], S->h_halo[slot], 2 * S->max_batch * sizeof(int64_t),
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(S->slot_free[slot], st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S->d_tick[slot], 0, 4 * sizeof(int), st);
+    LaunchCtx ctx;
+    if (e == cudaSuccess && get_ctx(st, &ctx) != MMF_OK) e = cudaErrorUnknown;
+    int64_t first = 0;
+    for (int g = 0; g < 4 && e == cudaSuccess; ++g) {
+        if (counts[g]) e = launch_group(S, ctx, g, slot, S->d_items[slot] + first, counts[g]);
+        first += counts[g];
+    }
+    if (e == cudaSuccess) e = launch_halo(S, slot, n, st);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        const Request &r = b.reqs[i];
+        if (r.n_out == 0) continue;
+        if (r.h_max) e = cudaMemcpyAsync(r.h_max, omax + out_off[i], r.n_out * esz, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && r.h_min)
+            e = cudaMemcpyAsync(r.h_min, omin + out_off[i], r.n_out * esz, cudaMemcpyDeviceToHost, st);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(b.done, st);
+    lk.lock();
+    if (e != cudaSuccess) {
+        S->failed = MMF_ECUDA;
+        set_error(MMF_ECUDA, "serving batch: %s", cudaGetErrorString(e));
+    }
+    S->inflight.push_back(std::move(b));
+    return true;
+}
+
+// With S->mu held: retire finished batches in order.
+void retire(mmf_server *S) {
+    while (!S->inflight.empty()) {
+        Batch &b = S->inflight.front();
+        cudaError_t q = b.done ? cudaEventQuery(b.done) : cudaErrorUnknown;
+        if (q == cudaErrorNotReady) break;
+        const auto now = Clock::now();
+        for (size_t i = 0; i < b.reqs.size(); ++i) {
+            const Request &r = b.reqs[i];
+            S->stage.release(b.stage_blocks[i].first, b.stage_blocks[i].second);
+            S->out.release(b.out_blocks[i].first, b.out_blocks[i].second);
+            auto sit = S->streams.find(r.stream);
+            if (sit != S->streams.end()) {
+                sit->second.in_flight = false;
+                sit->second.pending--;
+            }
+            S->tickets[r.ticket] = q == cudaSuccess ? kTicketDone : kTicketFailed;
+            S->lat_ms.push_back(std::chrono::duration<double, std::milli>(now - r.released).count());
+            S->done_chunks++;
+            S->done_elems += r.len;
+        }
+        if (q != cudaSuccess) S->failed = MMF_ECUDA;
+        if (b.done) cudaEventDestroy(b.done);
+        S->inflight.pop_front();
+        S->cv_done.notify_all();
+    }
+}
+
+void worker_main(mmf_server *S) {
+    cudaSetDevice(S->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (!S->stop) {
+        retire(S);
+        bool launched = false;
+        if (!S->paused && !S->queue.empty() && S->inflight.size() < (size_t)kSlots) launched = run_batch(S, lk);
+        if (launched) continue;
+        if (!S->inflight.empty()) {
+            // Poll completions without holding the lock for long.
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+            lk.lock();
+        } else {
+            S->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+        }
+    }
+    // Drain whatever is still on the GPU before the buffers go away.
+    while (!S->inflight.empty()) {
+        lk.unlock();
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+        lk.lock();
+        retire(S);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+mmf_status mmf_server_create(size_t device_budget_bytes, int max_batch, mmf_dtype dtype, mmf_server **out) {
+    if (!out) return set_error(MMF_EINVAL, "NULL server output");
+    *out = nullptr;
+    if (elem_size(dtype) == 0) return set_error(MMF_EINVAL, "unknown dtype %d", (int)dtype);
+    if (max_batch < 1 || max_batch > 65536) return set_error(MMF_EINVAL, "max_batch out of range");
+    if (device_budget_bytes < (1u << 20)) return set_error(MMF_EINVAL, "budget below 1 MiB");
+    mmf_server *S = new (std::nothrow) mmf_server();
+    if (!S) return set_error(MMF_ENOMEM, "server");
+    cudaGetDevice(&S->device);
+    S->dtype = dtype;
+    S->esz = elem_size(dtype);
+    S->max_batch = max_batch;
+    // Budget: half for staging (halos + chunk inputs), half for the outputs
+    // (two mirrored quarters: max and min).
+    S->out_half = (device_budget_bytes / 4) & ~size_t(255);
+    S->stage_size = (device_budget_bytes - 2 * S->out_half) & ~size_t(255);
+    cudaError_t e = cudaMalloc(&S->dev_base, S->stage_size + 2 * S->out_half);
+    for (int k = 0; k < kSlots && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&S->slots[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->slot_free[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMalloc(&S->d_series[k], max_batch * sizeof(SeriesDesc));
+        if (e == cudaSuccess) e = cudaMalloc(&S->d_items[k], max_batch * sizeof(ItemDesc));
+        if (e == cudaSuccess) e = cudaMalloc(&S->d_halo[k], 2 * max_batch * sizeof(int64_t));
+        if (e == cudaSuccess) e = cudaMalloc(&S->d_tick[k], 4 * sizeof(int));
+        if (e == cudaSuccess) e = cudaMallocHost(&S->h_series[k], max_batch * sizeof(SeriesDesc));
+        if (e == cudaSuccess) e = cudaMallocHost(&S->h_items[k], max_batch * sizeof(ItemDesc));
+        if (e == cudaSuccess) e = cudaMallocHost(&S->h_halo[k], 2 * max_batch * sizeof(int64_t));
+    }
+    if (e != cudaSuccess) {
+        set_error(MMF_ENOMEM, "server resources: %s", cudaGetErrorString(e));
+        mmf_server_destroy(S);
+        return MMF_ENOMEM;
+    }
+    S->stage.init(S->stage_size);
+    S->out.init(S->out_half);
+    // Kernel attributes are set here, outside any capture or worker race.
+    for (int g = 0; g < 4; ++g) {
+        switch (dtype) {
+            case MMF_F32: blockscan_prepare<float>(S->device, g); break;
+            case MMF_F64: blockscan_prepare<double>(S->device, g); break;
+            case MMF_I16: blockscan_prepare<int16_t>(S->device, g); break;
+            case MMF_U8: blockscan_prepare<uint8_t>(S->device, g); break;
+        }
+    }
+    S->worker = std::thread(worker_main, S);
+    *out = S;
+    return MMF_OK;
+}
+
+void mmf_server_destroy(mmf_server *S) {
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+        S->paused = false;
+    }
+    S->cv_work.notify_all();
+    if (S->worker.joinable()) S->worker.join();
+    for (int k = 0; k < kSlots; ++k) {
+        if (S->slots[k]) cudaStreamSynchronize(S->slots[k]);
+        if (S->slots[k]) cudaStreamDestroy(S->slots[k]);
+        if (S->slot_free[k]) cudaEventDestroy(S->slot_free[k]);
+        if (S->d_series[k]) cudaFree(S->d_series[k]);
+        if (S->d_items[k]) cudaFree(S->d_items[k]);
+        if (S->d_halo[k]) cudaFree(S->d_halo[k]);
+        if (S->d_tick[k]) cudaFree(S->d_tick[k]);
+        if (S->h_series[k]) cudaFreeHost(S->h_series[k]);
+        if (S->h_items[k]) cudaFreeHost(S->h_items[k]);
+        if (S->h_halo[k]) cudaFreeHost(S->h_halo[k]);
+    }
+    if (S->dev_base) cudaFree(S->dev_base);
+    delete S;
+}
+
+mmf_status mmf_stream_open(mmf_server *S, int64_t w, uint64_t *stream_id) {
+    if (!S || !stream_id) return set_error(MMF_EINVAL, "NULL argument");
+    if (w < 1) return set_error(MMF_EINVAL, "window w = %lld < 1", (long long)w);
+    std::lock_guard<std::mutex> lk(S->mu);
+    StreamState ss;
+    ss.w = w;
+    if (w > 1) {
+        ss.halo_off = S->stage.alloc((size_t)(w - 1) * S->esz);
+        if (ss.halo_off < 0) return set_error(MMF_ENOMEM, "no device memory left for the stream state");
+    }
+    const uint64_t id = S->next_stream++;
+    S->streams[id] = ss;
+    *stream_id = id;
+    return MMF_OK;
+}
+
+mmf_status mmf_stream_push(mmf_server *S, uint64_t stream_id, const void *h_chunk, int64_t len, void *h_max,
+                           void *h_min, int64_t *n_out, uint64_t *ticket) {
+    if (!S || !ticket) return set_error(MMF_EINVAL, "NULL argument");
+    if (len < 0 || (len > 0 && !h_chunk)) return set_error(MMF_EINVAL, "bad chunk");
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->failed != MMF_OK) return set_error(MMF_EDEVICE, "the server failed earlier");
+    auto it = S->streams.find(stream_id);
+    if (it == S->streams.end() || it->second.closed) return set_error(MMF_ECLOSED, "stream %llu is not open", (unsigned long long)stream_id);
+    StreamState &ss = it->second;
+    // Outputs of this chunk: windows that end inside it (zero latency).
+    int64_t before = ss.count;
+    for (const Request &r : S->queue)
+        if (r.stream == stream_id) before += r.len;  // queued chunks of this stream come first
+    const int64_t done_before = std::max<int64_t>(0, before - ss.w + 1);
+    const int64_t done_after = std::max<int64_t>(0, before + len - ss.w + 1);
+    const int64_t m = done_after - done_before;
+    if (m > 0 && !h_max && !h_min) return set_error(MMF_EINVAL, "both outputs are NULL");
+    const size_t in_need = Arena::round((size_t)(std::min<int64_t>(before, ss.w - 1) + len) * S->esz);
+    if (in_need > S->stage.size() || Arena::round((size_t)m * S->esz) > S->out.size())
+        return set_error(MMF_ENOMEM, "chunk larger than the device budget allows");
+    Request r;
+    r.ticket = S->next_ticket++;
+    r.stream = stream_id;
+    r.h_in = h_chunk;
+    r.len = len;
+    r.h_max = h_max;
+    r.h_min = h_min;
+    r.n_out = m;
+    r.released = Clock::now();
+    S->queue.push_back(r);
+    S->tickets[r.ticket] = 0;
+    ss.pending++;
+    if (n_out) *n_out = m;
+    *ticket = r.ticket;
+    S->cv_work.notify_one();
+    return MMF_OK;
+}
+
+mmf_status mmf_ticket_wait(mmf_server *S, uint64_t ticket, int timeout_ms) {
+    if (!S) return set_error(MMF_EINVAL, "NULL server");
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->tickets.find(ticket);
+    if (it == S->tickets.end()) return set_error(MMF_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+    const auto deadline = Clock::now() + std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms);
+    while (S->tickets[ticket] == 0) {
+        if (S->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && S->tickets[ticket] == 0)
+            return set_error(MMF_ETIMEOUT, "ticket %llu not done after %d ms", (unsigned long long)ticket, timeout_ms);
+    }
+    const int64_t st = S->tickets[ticket];
+    S->tickets.erase(ticket);
+    return st == kTicketDone ? MMF_OK : set_error(MMF_EDEVICE, "the batch of ticket %llu failed", (unsigned long long)ticket);
+}
+
+mmf_status mmf_stream_close(mmf_server *S, uint64_t stream_id, int timeout_ms) {
+    if (!S) return set_error(MMF_EINVAL, "NULL server");
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->streams.find(stream_id);
+    if (it == S->streams.end() || it->second.closed) return set_error(MMF_ECLOSED, "stream %llu is not open", (unsigned long long)stream_id);
+    it->second.closed = true;  // no new pushes
+    const auto deadline = Clock::now() + std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms);
+    while (S->streams[stream_id].pending > 0) {
+        if (S->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && S->streams[stream_id].pending > 0)
+            return set_error(MMF_ETIMEOUT, "stream %llu still has chunks after %d ms", (unsigned long long)stream_id, timeout_ms);
+    }
+    StreamState ss = S->streams[stream_id];
+    if (ss.halo_off >= 0) S->stage.release(ss.halo_off, (size_t)(ss.w - 1) * S->esz);
+    S->streams.erase(stream_id);
+    return MMF_OK;
+}
+
+mmf_status mmf_server_pause(mmf_server *S, int paused) {
+    if (!S) return set_error(MMF_EINVAL, "NULL server");
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->paused = paused != 0;
+    S->cv_work.notify_all();
+    return MMF_OK;
+}
+
+mmf_status mmf_server_stats(mmf_server *S, int reset, mmf_server_stats_t *out) {
+    if (!S || !out) return set_error(MMF_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    std::vector<double> v = S->lat_ms;
+    std::sort(v.begin(), v.end());
+    auto pct = [&](double p) { return v.empty() ? 0.0 : v[std::min(v.size() - 1, (size_t)(p * (v.size() - 1) + 0.5))]; };
+    out->chunks = S->done_chunks;
+    out->elements = S->done_elems;
+    out->batches = (int64_t)S->nbatches;
+    out->p50_ms = pct(0.50);
+    out->p99_ms = pct(0.99);
+    out->max_ms = v.empty() ? 0.0 : v.back();
+    out->queued = (int64_t)S->queue.size();
+    out->device_bytes_used = (int64_t)(S->stage.used() + 2 * S->out.used());
+    if (reset) {
+        S->lat_ms.clear();
+        S->done_chunks = S->done_elems = 0;
+        S->nbatches = 0;
+    }
+    return MMF_OK;
+}
+
+}  // extern "C"

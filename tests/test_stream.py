@@ -1,0 +1,140 @@
+"""GPU tests of the streaming service: chunked outputs equal the whole-array
+oracle exactly, a stream gives the same outputs alone and in the mix, and
+host-side failures (closed streams, stalls, oversize chunks) return errors
+without touching the GPU's health."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mmf():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_cs_0610046_gb300 as m
+    return m
+
+
+def _split(n, rng, lo=1, hi=5000):
+    cuts = []
+    pos = 0
+    while pos < n:
+        c = int(rng.integers(lo, hi))
+        cuts.append(min(c, n - pos))
+        pos += c
+    return cuts
+
+
+def _serve(mmf, streams, budget=1 << 28, max_batch=64, interleave=True, seed=0):
+    """streams: list of (data, w, chunk lengths).  Returns per-stream outputs."""
+    srv = mmf.Server(budget, max_batch, "float32")
+    ids = [srv.open(w) for _, w, _ in streams]
+    pos = [0] * len(streams)
+    ci = [0] * len(streams)
+    outs = [([], []) for _ in streams]
+    pend = []
+    order = np.random.default_rng(seed)
+    live = list(range(len(streams)))
+    while live:
+        k = int(order.choice(live)) if interleave else live[0]
+        data, w, cl = streams[k]
+        L = cl[ci[k]]
+        chunk = np.ascontiguousarray(data[pos[k]:pos[k] + L])
+        m = mmf.n_outputs(pos[k], L, w)
+        omax = np.empty(m, np.float32)
+        omin = np.empty(m, np.float32)
+        t, n_out = srv.push(ids[k], chunk, omax, omin)
+        assert n_out == m
+        pend.append(t)
+        outs[k][0].append(omax)
+        outs[k][1].append(omin)
+        pos[k] += L
+        ci[k] += 1
+        if ci[k] == len(cl):
+            live.remove(k)
+    for t in pend:
+        srv.wait(t)
+    st = srv.stats()
+    for sid in ids:
+        srv.close_stream(sid)
+    srv.close()
+    return [(np.concatenate(a) if a else np.empty(0, np.float32),
+             np.concatenate(b) if b else np.empty(0, np.float32)) for a, b in outs], st
+
+
+def test_chunked_equals_whole_array(mmf):
+    rng = np.random.default_rng(5)
+    streams = []
+    for k in range(24):
+        n = int(rng.integers(1, 40_000))
+        w = int(rng.choice([1, 2, 3, 8, 9, 31, 257, 1001, 4096, 5000]))
+        data = synth.random_walk(n, 100 + k, np.float32)
+        streams.append((data, w, _split(n, rng, 1, 7000)))
+    outs, st = _serve(mmf, streams)
+    for (data, w, cl), (gm, gn) in zip(streams, outs):
+        em, en = oracle.stream_reference(np.split(data, np.cumsum(cl)[:-1]), w)
+        assert np.array_equal(gm, em) and np.array_equal(gn, en), (len(data), w)
+    assert st["chunks"] == sum(len(c) for _, _, c in streams)
+    assert st["p99_ms"] >= st["p50_ms"] > 0
+
+
+def test_alone_equals_in_the_mix(mmf):
+    rng = np.random.default_rng(9)
+    target = (synth.piecewise_monotone(30_000, 3, np.float32), 777, _split(30_000, rng, 100, 4000))
+    others = [(synth.uniform(20_000, 50 + k, np.float32), int(rng.choice([5, 64, 2000])),
+               _split(20_000, rng, 10, 3000)) for k in range(16)]
+    alone, _ = _serve(mmf, [target])
+    mixed, _ = _serve(mmf, [target] + others, max_batch=8, seed=3)
+    assert np.array_equal(alone[0][0], mixed[0][0]) and np.array_equal(alone[0][1], mixed[0][1])
+    em, en = oracle.bf1d(target[0], target[1])
+    assert np.array_equal(alone[0][0], em) and np.array_equal(alone[0][1], en)
+
+
+def test_tight_budget_admission(mmf):
+    """A budget that holds only a few chunks at a time: admission waits for
+    completions and every result is still exact."""
+    rng = np.random.default_rng(12)
+    streams = [(synth.random_walk(60_000, 7 + k, np.float32), 513, _split(60_000, rng, 4000, 16_000))
+               for k in range(6)]
+    outs, _ = _serve(mmf, streams, budget=1 << 20, max_batch=4)
+    for (data, w, _), (gm, gn) in zip(streams, outs):
+        em, en = oracle.bf1d(data, w)
+        assert np.array_equal(gm, em) and np.array_equal(gn, en)
+
+
+def test_host_side_faults(mmf):
+    srv = mmf.Server(1 << 20, 8, "float32")
+    sid = srv.open(16)
+    x = synth.uniform(100_000, 1, np.float32)
+    # a chunk that can never fit the budget
+    big = np.ascontiguousarray(x)
+    with pytest.raises(mmf.MMFError) as e:
+        srv.push(sid, big, np.empty(100_000, np.float32), None)
+    assert e.value.status == 2  # MMF_ENOMEM
+    # a stalled service: the wait times out, then completes after resuming
+    srv.pause(True)
+    chunk = np.ascontiguousarray(x[:1000])
+    om = np.empty(985, np.float32)
+    t, m = srv.push(sid, chunk, om, None)
+    with pytest.raises(mmf.MMFError) as e:
+        srv.wait(t, timeout_ms=50)
+    assert e.value.status == 5  # MMF_ETIMEOUT
+    with pytest.raises(mmf.MMFError) as e:
+        srv.close_stream(sid, timeout_ms=20)  # still pending
+    assert e.value.status == 5
+    srv.pause(False)
+    srv.wait(t)
+    assert np.array_equal(om, oracle.bf1d(chunk, 16)[0])
+    # the stream was closed by the timed-out close: pushes are refused
+    with pytest.raises(mmf.MMFError) as e:
+        srv.push(sid, chunk, om, None)
+    assert e.value.status == 6  # MMF_ECLOSED
+    with pytest.raises(mmf.MMFError) as e:
+        srv.push(12345, chunk, om, None)
+    assert e.value.status == 6
+    srv.close()
+    assert mmf.device_status() == 0
