@@ -52,6 +52,41 @@ __global__ void halo_update_kernel(const SeriesDesc *series, const int64_t *halo
     T *dst = base + halo_off[i];
     for (int64_t k = threadIdx.x; k < h; k += blockDim.x) dst[k] = src[k];
 }
+// Per-chunk copy descriptor of a batch (offsets in elements).
+struct ChunkCopy {
+    const void *h_in;  // host chunk (device-accessible)
+    void *h_max;       // host outputs (device-accessible, may be null)
+    void *h_min;
+    int64_t len, stage_off, halo_off, halo_len, out_off, n_out;
+};
+
+// Builds every staging block [halo | chunk] of a batch: the halo from the
+// stream's device state, the chunk straight from host memory (over the
+// CPU-GPU link).  blockIdx.y strides over the chunk.
+template <typename T>
+__global__ void gather_kernel(const ChunkCopy *cc, int n, T *base) {
+    const int i = blockIdx.x;
+    if (i >= n) return;
+    const ChunkCopy c = cc[i];
+    T *stage = base + c.stage_off;
+    const int64_t tot = c.halo_len + c.len;
+    const int64_t stride = (int64_t)gridDim.y * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; k < tot; k += stride)
+        stage[k] = k < c.halo_len ? base[c.halo_off + k] : static_cast<const T *>(c.h_in)[k - c.halo_len];
+}
+
+// Writes every chunk's outputs straight to its host buffers.
+template <typename T>
+__global__ void scatter_kernel(const ChunkCopy *cc, int n, const T *omax, const T *omin) {
+    const int i = blockIdx.x;
+    if (i >= n) return;
+    const ChunkCopy c = cc[i];
+    const int64_t stride = (int64_t)gridDim.y * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; k < c.n_out; k += stride) {
+        if (c.h_max) static_cast<T *>(c.h_max)[k] = omax[c.out_off + k];
+        if (c.h_min) static_cast<T *>(c.h_min)[k] = omin[c.out_off + k];
+    }
+}
 }  // namespace mmf
 
 using namespace mmf;
@@ -114,6 +149,7 @@ struct Request {
     int64_t len;
     void *h_max, *h_min;
     int64_t n_out;
+    bool direct;  // the GPU can read/write these host buffers itself
     Clock::time_point released;
 };
 
@@ -166,6 +202,9 @@ struct mmf_server {
     SeriesDesc *h_series[kSlots] = {};  // pinned staging of the tables
     ItemDesc *h_items[kSlots] = {};
     int64_t *h_halo[kSlots] = {};
+    ChunkCopy *d_copy[kSlots] = {};
+    ChunkCopy *h_copy[kSlots] = {};
+    bool pageable_ok = false;  // the device can access pageable host memory
     uint64_t nbatches = 0;
     std::vector<double> lat_ms;
     int64_t done_chunks = 0, done_elems = 0;
@@ -280,13 +319,46 @@ bool run_batch(mmf_server *S, std::unique_lock<std::mutex> &lk) {
     char *base = S->dev_base;
     char *omax = base + S->stage_size, *omin = omax + S->out_half;
     cudaError_t e = cudaSuccess;
+    // Copy descriptors: direct chunks go through the gather/scatter kernels,
+    // the others through one copy call per buffer.
+    int nd = 0;
+    int64_t maxlen = 1, maxout = 1;
+    for (int i = 0; i < n; ++i) {
+        const Request &r = b.reqs[i];
+        if (!r.direct) continue;
+        ChunkCopy &c = S->h_copy[slot][nd++];
+        c.h_in = r.h_in;
+        c.h_max = r.h_max;
+        c.h_min = r.h_min;
+        c.len = r.len;
+        c.stage_off = stage_off[i] / esz;
+        c.halo_off = hoffs[i] / esz;
+        c.halo_len = halo_before[i];
+        c.out_off = out_off[i] / esz;
+        c.n_out = r.n_out;
+        maxlen = std::max(maxlen, halo_before[i] + r.len);
+        maxout = std::max(maxout, r.n_out);
+    }
     for (int i = 0; i < n && e == cudaSuccess; ++i) {
         const Request &r = b.reqs[i];
+        if (r.direct) continue;
         char *stage = base + stage_off[i];
         if (halo_before[i] > 0)
             e = cudaMemcpyAsync(stage, base + hoffs[i], halo_before[i] * esz, cudaMemcpyDeviceToDevice, st);
         if (e == cudaSuccess && r.len > 0)
             e = cudaMemcpyAsync(stage + halo_before[i] * esz, r.h_in, r.len * esz, cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess && nd > 0)
+        e = cudaMemcpyAsync(S->d_copy[slot], S->h_copy[slot], nd * sizeof(ChunkCopy), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && nd > 0) {
+        const dim3 g(nd, (unsigned)std::min<int64_t>(32, (maxlen + 2047) / 2048));
+        switch (S->dtype) {
+            case MMF_F32: gather_kernel<float><<<g, 256, 0, st>>>(S->d_copy[slot], nd, (float *)base); break;
+            case MMF_F64: gather_kernel<double><<<g, 256, 0, st>>>(S->d_copy[slot], nd, (double *)base); break;
+            case MMF_I16: gather_kernel<int16_t><<<g, 256, 0, st>>>(S->d_copy[slot], nd, (int16_t *)base); break;
+            default: gather_kernel<uint8_t><<<g, 256, 0, st>>>(S->d_copy[slot], nd, (uint8_t *)base); break;
+        }
+        e = cudaGetLastError();
     }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(S->d_series[slot], S->h_series[slot], n * sizeof(SeriesDesc), cudaMemcpyHostToDevice, st);
@@ -305,9 +377,19 @@ bool run_batch(mmf_server *S, std::unique_lock<std::mutex> &lk) {
         first += counts[g];
     }
     if (e == cudaSuccess) e = launch_halo(S, slot, n, st);
+    if (e == cudaSuccess && nd > 0) {
+        const dim3 g(nd, (unsigned)std::min<int64_t>(32, (maxout + 2047) / 2048));
+        switch (S->dtype) {
+            case MMF_F32: scatter_kernel<float><<<g, 256, 0, st>>>(S->d_copy[slot], nd, (const float *)omax, (const float *)omin); break;
+            case MMF_F64: scatter_kernel<double><<<g, 256, 0, st>>>(S->d_copy[slot], nd, (const double *)omax, (const double *)omin); break;
+            case MMF_I16: scatter_kernel<int16_t><<<g, 256, 0, st>>>(S->d_copy[slot], nd, (const int16_t *)omax, (const int16_t *)omin); break;
+            default: scatter_kernel<uint8_t><<<g, 256, 0, st>>>(S->d_copy[slot], nd, (const uint8_t *)omax, (const uint8_t *)omin); break;
+        }
+        e = cudaGetLastError();
+    }
     for (int i = 0; i < n && e == cudaSuccess; ++i) {
         const Request &r = b.reqs[i];
-        if (r.n_out == 0) continue;
+        if (r.direct || r.n_out == 0) continue;
         if (r.h_max) e = cudaMemcpyAsync(r.h_max, omax + out_off[i], r.n_out * esz, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess && r.h_min)
             e = cudaMemcpyAsync(r.h_min, omin + out_off[i], r.n_out * esz, cudaMemcpyDeviceToHost, st);
@@ -379,6 +461,18 @@ void worker_main(mmf_server *S) {
 
 }  // namespace
 
+// Pinned (page-locked) host memory is accessible from kernels; so is any host
+// memory where the device supports pageable access.
+bool device_accessible(const void *p) {
+    if (!p) return true;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeManaged || a.type == cudaMemoryTypeDevice;
+}
+
 extern "C" {
 
 mmf_status mmf_server_create(size_t device_budget_bytes, int max_batch, mmf_dtype dtype, mmf_server **out) {
@@ -408,7 +502,12 @@ mmf_status mmf_server_create(size_t device_budget_bytes, int max_batch, mmf_dtyp
         if (e == cudaSuccess) e = cudaMallocHost(&S->h_series[k], max_batch * sizeof(SeriesDesc));
         if (e == cudaSuccess) e = cudaMallocHost(&S->h_items[k], max_batch * sizeof(ItemDesc));
         if (e == cudaSuccess) e = cudaMallocHost(&S->h_halo[k], 2 * max_batch * sizeof(int64_t));
+        if (e == cudaSuccess) e = cudaMalloc(&S->d_copy[k], max_batch * sizeof(ChunkCopy));
+        if (e == cudaSuccess) e = cudaMallocHost(&S->h_copy[k], max_batch * sizeof(ChunkCopy));
     }
+    int pageable = 0;
+    if (e == cudaSuccess) cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, S->device);
+    S->pageable_ok = pageable != 0;
     if (e != cudaSuccess) {
         set_error(MMF_ENOMEM, "server resources: %s", cudaGetErrorString(e));
         mmf_server_destroy(S);
@@ -450,6 +549,8 @@ void mmf_server_destroy(mmf_server *S) {
         if (S->h_series[k]) cudaFreeHost(S->h_series[k]);
         if (S->h_items[k]) cudaFreeHost(S->h_items[k]);
         if (S->h_halo[k]) cudaFreeHost(S->h_halo[k]);
+        if (S->d_copy[k]) cudaFree(S->d_copy[k]);
+        if (S->h_copy[k]) cudaFreeHost(S->h_copy[k]);
     }
     if (S->dev_base) cudaFree(S->dev_base);
     delete S;
@@ -492,6 +593,7 @@ mmf_status mmf_stream_push(mmf_server *S, uint64_t stream_id, const void *h_chun
     if (in_need > S->stage.size() || Arena::round((size_t)m * S->esz) > S->out.size())
         return set_error(MMF_ENOMEM, "chunk larger than the device budget allows");
     Request r;
+    r.direct = S->pageable_ok || (device_accessible(h_chunk) && device_accessible(h_max) && device_accessible(h_min));
     r.ticket = S->next_ticket++;
     r.stream = stream_id;
     r.h_in = h_chunk;
