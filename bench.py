@@ -243,6 +243,36 @@ def batched_extras(dev, stream, peak, reps=5, envelope_series=1_000_000):
     return out
 
 
+def wedge_extras(dev, stream, peak, n=1 << 30, windows=(3, 31, 101, 496), reps=3):
+    """The chunked-wedge kernel (Algorithm 1 per thread chunk) beside the
+    library's default kernel choice (register slide or block scan) on the same
+    n = 2^30 f32 streams, each event-timed."""
+    import torch
+    import paper_cs_0610046_gb300 as mmf
+    import synth
+    out = {}
+    om = torch.empty(n, dtype=torch.float32, device=dev)
+    on = torch.empty(n, dtype=torch.float32, device=dev)
+    for d in DISTS:
+        x = synth.torch_by_name(d, n, 91, dev)
+        for w in windows:
+            m = n - w + 1
+            row = {}
+            for k in ("wedge", "auto"):
+                def f():
+                    mmf.filter1d(x, w, out_max=om[:m], out_min=on[:m], kernel=k, stream=stream)
+                f()
+                ms = _events_ms(f, reps, stream)
+                gbs = (n + 2 * m) * 4 / ms / 1e6
+                row[k] = {"ms": ms, "Gelem_s": n / ms / 1e6, "GBps": gbs, "frac": gbs / peak}
+            row["wedge_over_auto"] = row["auto"]["ms"] / row["wedge"]["ms"]
+            out[f"{d}_w{w}"] = row
+        del x
+    del om, on
+    torch.cuda.empty_cache()
+    return out
+
+
 def blobs_torch(nimg, H, W, seed, dev, nblobs=200):
     """The 2D recipe (sum of Gaussian blobs + 10 % uniform noise) drawn on the
     device: each image is an outer-product sum, one GEMM."""
@@ -531,6 +561,7 @@ def main():
     if not args.no_extras and rank == 0:
         del xs
         torch.cuda.empty_cache()
+        extras["wedge"] = wedge_extras(dev, stream, peak)
         extras["batched"] = batched_extras(dev, stream, peak)
         extras["filter2d"] = filter2d_extras(dev, stream, peak)
         extras["serving"] = serving_extras(dev)

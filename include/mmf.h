@@ -90,8 +90,14 @@ typedef enum {
 mmf_status mmf_filter1d(const void *d_in, int64_t n, int64_t w_or_r, mmf_dtype dtype,
                         mmf_mode mode, void *d_max, void *d_min, void *stream);
 
+/* Largest window of the chunked-wedge kernel: its per-thread rings (the
+ * window of inputs and the deques U and L, Section 4) must fit shared memory. */
+#define MMF_WEDGE_MAX_WINDOW 496
+
 /* Same as mmf_filter1d with an explicit kernel choice (for tests and the
- * autotuner).  MMF_KERNEL_SLIDE requires w <= 32. */
+ * autotuner).  MMF_KERNEL_SLIDE requires w <= 9; MMF_KERNEL_WEDGE computes
+ * MMF_VALID windows with w <= MMF_WEDGE_MAX_WINDOW (MMF_EINVAL /
+ * MMF_ENOTIMPL otherwise). */
 mmf_status mmf_filter1d_ex(const void *d_in, int64_t n, int64_t w_or_r, mmf_dtype dtype,
                            mmf_mode mode, void *d_max, void *d_min, void *stream,
                            mmf_kernel kernel);

@@ -153,6 +153,16 @@ mmf_status mmf_filter1d_ex(const void *d_in, int64_t n, int64_t w_or_r, mmf_dtyp
     if (st != MMF_OK) return st;
     if (kernel == MMF_KERNEL_SLIDE && sd.w > 9)
         return set_error(MMF_EINVAL, "the register slide handles windows up to 9 (w = %lld)", (long long)sd.w);
+    if (kernel == MMF_KERNEL_WEDGE) {
+        if (mode != MMF_VALID) return set_error(MMF_ENOTIMPL, "the wedge kernel computes valid windows only");
+        if (sd.w > MMF_WEDGE_MAX_WINDOW)
+            return set_error(MMF_EINVAL, "the wedge kernel handles windows up to %d", MMF_WEDGE_MAX_WINDOW);
+        return dispatch_dtype(dtype, [&](auto tag) -> mmf_status {
+            using T = decltype(tag);
+            cudaError_t e = wedge_1d<T>(ctx, d_in, n, sd.w, d_max, d_min);
+            return e == cudaSuccess ? MMF_OK : cuda_error(e, "wedge launch");
+        });
+    }
     if (kernel != MMF_KERNEL_AUTO && kernel != MMF_KERNEL_BLOCKSCAN && kernel != MMF_KERNEL_SLIDE)
         return set_error(MMF_ENOTIMPL, "kernel %d not available", (int)kernel);
     const bool allow_slide = kernel != MMF_KERNEL_BLOCKSCAN;

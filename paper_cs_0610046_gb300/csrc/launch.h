@@ -35,6 +35,11 @@ cudaError_t blockscan_table(const LaunchCtx &ctx, int mode, const void *in, void
                             const SeriesDesc *d_series, const ItemDesc *d_items, int64_t n_items,
                             int *d_ticket, int grid);
 
+// Chunked monotonic wedge (Algorithm 1 per thread chunk), valid windows,
+// w <= MMF_WEDGE_MAX_WINDOW.
+template <typename T>
+cudaError_t wedge_1d(const LaunchCtx &ctx, const void *in, int64_t n, int64_t w, void *omax, void *omin);
+
 // Kernel mode for window w: 3 = register slide (if allowed and w <= 9), else
 // the block-scan mode 0, 1 or 2.
 template <typename T> int block_mode(int64_t w, bool allow_slide);
