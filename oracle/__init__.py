@@ -134,6 +134,35 @@ def wedge(a: np.ndarray, w: int):
                     "stale_fronts": st.stale_fronts, "steps": st.steps}
 
 
+def wedge_mt(a: np.ndarray, w: int, threads: int | None = None):
+    """Algorithm 1 on ``threads`` host threads: the outputs are split into
+    contiguous ranges and each range runs the single-thread wedge over its
+    inputs plus the w-1 that follow (each output depends only on its own
+    window, Section 1, so the split is exact).  ctypes releases the GIL
+    around each call.  Returns (max, min, threads used)."""
+    from concurrent.futures import ThreadPoolExecutor
+    a = np.ascontiguousarray(a)
+    m = n_out(a.size, w)
+    mx = np.empty(m, a.dtype)
+    mn = np.empty(m, a.dtype)
+    t = max(1, min(threads or os.cpu_count() or 1, m))
+    bounds = [m * k // t for k in range(t + 1)]
+    fn = _fn("wedge", a.dtype)
+
+    def run(k):
+        j0, j1 = bounds[k], bounds[k + 1]
+        if j1 <= j0:
+            return 0
+        seg = a[j0:j1 + w - 1]
+        return fn(_ptr(seg), seg.size, w, _ptr(mx[j0:j1]), _ptr(mn[j0:j1]), None)
+
+    if m > 0:
+        with ThreadPoolExecutor(max_workers=t) as ex:
+            for rc in ex.map(run, range(t)):
+                _check(rc, "wedge_mt")
+    return mx, mn, t
+
+
 def envelope(a: np.ndarray, r: int):
     """Centred end-clipped envelope of radius r: (upper, lower), n each."""
     a = np.ascontiguousarray(a)

@@ -42,7 +42,7 @@ template <typename T> struct Elem;
 template <> struct Elem<float> {
     using R = float;
     using Pair = float2;
-    static constexpr int V = 8, PS = 4;
+    static constexpr int V = 16, PS = 4, NW = 4;
     __device__ static R lo() { return __int_as_float(0xff800000); }
     __device__ static R hi() { return __int_as_float(0x7f800000); }
     __device__ static Pair pair(R m, R n) { return make_float2(m, n); }
@@ -58,7 +58,7 @@ template <> struct Elem<float> {
 template <> struct Elem<double> {
     using R = long long;
     using Pair = longlong2;
-    static constexpr int V = 4, PS = 3;
+    static constexpr int V = 4, PS = 3, NW = 8;
     __device__ static R key(long long b) { return b ^ ((b >> 63) & 0x7fffffffffffffffLL); }
     __device__ static R lo() { return key((long long)0xfff0000000000000ULL); }  // -inf
     __device__ static R hi() { return key(0x7ff0000000000000LL); }              // +inf
@@ -71,7 +71,7 @@ template <> struct Elem<double> {
 template <> struct Elem<int16_t> {
     using R = int;
     using Pair = short2;
-    static constexpr int V = 16, PS = 4;
+    static constexpr int V = 16, PS = 4, NW = 8;
     __device__ static R lo() { return -32768; }
     __device__ static R hi() { return 32767; }
     __device__ static Pair pair(R m, R n) { return make_short2((short)m, (short)n); }
@@ -83,7 +83,7 @@ template <> struct Elem<int16_t> {
 template <> struct Elem<uint8_t> {
     using R = int;
     using Pair = uchar2;
-    static constexpr int V = 16, PS = 4;
+    static constexpr int V = 16, PS = 4, NW = 8;
     __device__ static R lo() { return 0; }
     __device__ static R hi() { return 255; }
     __device__ static Pair pair(R m, R n) { return make_uchar2((unsigned char)m, (unsigned char)n); }
@@ -99,6 +99,19 @@ __device__ __forceinline__ long long vmax(long long a, long long b) { return a >
 __device__ __forceinline__ long long vmin(long long a, long long b) { return a < b ? a : b; }
 __device__ __forceinline__ int vmax(int a, int b) { return max(a, b); }
 __device__ __forceinline__ int vmin(int a, int b) { return min(a, b); }
+// Three-operand forms: one instruction for f32 on sm_100-family GPUs.
+__device__ __forceinline__ float vmax3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float vmin3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+template <typename X> __device__ __forceinline__ X vmax3(X a, X b, X c) { return vmax(vmax(a, b), c); }
+template <typename X> __device__ __forceinline__ X vmin3(X a, X b, X c) { return vmin(vmin(a, b), c); }
 
 // Element at compile-time byte offset B of a little-endian word array.
 template <typename T> struct WordElem;
@@ -189,9 +202,6 @@ struct BlockScanParams {
     uint32_t *status;          // device status word
 };
 
-constexpr int kConsumerWarps = 8;
-constexpr int kNT = kConsumerWarps * 32;
-constexpr int kThreads = kNT;
 constexpr int kStages = 4;             // per-warp slice stages (power of two)
 constexpr int kQCap = 1024 + 8;        // tile-aggregate ring (>= max tiles per window + 2)
 constexpr int kQueue = 16;             // upcoming item ids under dynamic scheduling
@@ -212,36 +222,62 @@ struct WarpIssue {
     int32_t nloads;  // its number of loads; -1 once the sequence has ended
     int32_t q, caseB, ok, NC, klast;
     int32_t issued;  // loads issued so far by this warp
+    int32_t linear;  // load l of the item is tile l (every mode but case B)
     int32_t smode[kStages];  // per stage: copy mode | shift << 8, for the readers
 };
+
+// Lane carries of one thread's V-element block inside its scan block (modes
+// 1 and 2): e = maximum/minimum of the threads before it in the block
+// (exclusive), g = including its own elements.
+template <typename T> struct __align__(2 * sizeof(typename Elem<T>::Pair)) CarryRec {
+    typename Elem<T>::Pair e, g;
+};
+
+// Modes 1 and 2 use thread-local scans with lane carries kept per thread (the
+// carry ring) for every type but f64, whose larger pairs would leave room for
+// only one CTA per SM; f64 applies the lane carries to every element instead.
+template <typename T> constexpr bool kCarryRing = sizeof(T) != 8;
 
 template <typename T> struct Geo {
     using Pair = typename Elem<T>::Pair;
     static constexpr int V = Elem<T>::V;
     static constexpr int PS = Elem<T>::PS;
     static constexpr int LGV = V == 16 ? 4 : (V == 8 ? 3 : 2);
-    static constexpr int T_ = kNT * V;  // tile, elements
-    static constexpr int LGT = LGV + 8;
+    static constexpr int NW = Elem<T>::NW;  // warps per CTA
+    static constexpr int NT = NW * 32;      // threads per CTA
+    static constexpr int LGNT = NW == 8 ? 8 : 7;
+    static constexpr int T_ = NT * V;  // tile, elements
+    static constexpr int LGT = LGV + LGNT;
     static constexpr int SLICE = 32 * V;  // elements of a tile read by one warp
     static constexpr int NCH = V * (int)sizeof(T) / 16;  // 16-byte chunks per thread
     // Register-slide halo (elements after the slice; windows up to HALO_MAX+1).
     static constexpr int HALO_MAX = 8 > 16 / (int)sizeof(T) ? 8 : 16 / (int)sizeof(T);
-    static constexpr int SLICE_BYTES = (SLICE + HALO_MAX) * (int)sizeof(T) + 16;  // + 16-byte shift room
+    // A warp's slice arrives in PIECES copies of PLANES lanes' elements each,
+    // placed PSTRIDE bytes apart (PSTRIDE/16 odd): lanes reading 16-byte words
+    // of their own V elements then fall on distinct bank groups.  Each piece
+    // holds room for the register-slide halo and a 16-byte shift.
+    static constexpr int PIECES = V * (int)sizeof(T) / 16;  // 16-byte words per lane
+    static constexpr int PLANES = 32 / PIECES;
+    static constexpr int PIECE = PLANES * V;  // elements
+    static constexpr int PSTRIDE0 = (PIECE + HALO_MAX) * (int)sizeof(T) + 16;
+    static constexpr int PSTRIDE = (PSTRIDE0 / 16) % 2 ? PSTRIDE0 : PSTRIDE0 + 16;
+    static constexpr int SLICE_BYTES = PIECES * PSTRIDE;
     static constexpr int RING = 3 * T_;  // logical ring pairs
     static constexpr int RING_PHYS = RING + (RING >> PS) + 16;
     static constexpr size_t rnd(size_t b) { return (b + 127) / 128 * 128; }
     static constexpr size_t off_misc = 0;
-    static constexpr size_t off_kagg = 0;  // [3 ring slots][8 warps] block aggregates of K tiles
-    static constexpr size_t off_jagg = off_kagg + 3 * kConsumerWarps * sizeof(Pair);  // [2][8] of J tiles
-    static constexpr size_t off_bar = rnd(off_jagg + 2 * kConsumerWarps * sizeof(Pair));  // [warp][stage]
-    static constexpr size_t off_issue = off_bar + kConsumerWarps * kStages * 8;
-    static constexpr size_t off_queue = rnd(off_issue + kConsumerWarps * sizeof(WarpIssue));
+    static constexpr size_t off_kagg = 0;  // [3 ring slots][NW warps] block aggregates of K tiles
+    static constexpr size_t off_jagg = off_kagg + 3 * NW * sizeof(Pair);  // [2][NW] of J tiles
+    static constexpr size_t off_bar = rnd(off_jagg + 2 * NW * sizeof(Pair));  // [warp][stage]
+    static constexpr size_t off_issue = off_bar + NW * kStages * 8;
+    static constexpr size_t off_queue = rnd(off_issue + NW * sizeof(WarpIssue));
     static constexpr size_t off_params = rnd(off_queue + kQueue * 8 + 16);
     static constexpr size_t misc_bytes = rnd(off_params + 256);
     static constexpr size_t off_stage = off_misc + misc_bytes;  // [warp][stage] slices
-    static constexpr size_t off_ring = off_stage + rnd((size_t)kConsumerWarps * kStages * SLICE_BYTES);
+    static constexpr size_t off_ring = off_stage + rnd((size_t)NW * kStages * SLICE_BYTES);
     static constexpr size_t off_ta = off_ring + rnd(RING_PHYS * sizeof(Pair));
-    static constexpr size_t smem_bytes = off_ta + rnd(kQCap * sizeof(Pair));
+    static constexpr size_t off_cr = off_ta + rnd(kQCap * sizeof(Pair));  // [3 tiles][NT] carry records
+    static constexpr size_t smem_bytes = off_cr + (kCarryRing<T> ? rnd(3 * NT * sizeof(CarryRec<T>)) : 0);
     // The register slide uses only the misc area and the stages.
     static constexpr size_t smem_bytes_slide = off_ring;
 };
@@ -252,8 +288,13 @@ template <typename T> struct Smem {
     __device__ static uint8_t *slice(int warp, int s) {
         return bs_smem + G::off_stage + (size_t)(warp * kStages + s) * G::SLICE_BYTES;
     }
+    // First byte of `lane`'s elements in a slice stage.
+    __device__ static const uint8_t *lane_base(const uint8_t *slice, int lane) {
+        return slice + (lane / G::PLANES) * G::PSTRIDE + (lane % G::PLANES) * G::V * (int)sizeof(T);
+    }
     __device__ static Pair *ring() { return reinterpret_cast<Pair *>(bs_smem + G::off_ring); }
     __device__ static Pair *ta() { return reinterpret_cast<Pair *>(bs_smem + G::off_ta); }
+    __device__ static CarryRec<T> *cr() { return reinterpret_cast<CarryRec<T> *>(bs_smem + G::off_cr); }
     __device__ static uint8_t *misc() { return bs_smem + G::off_misc; }
     __device__ static Pair *kagg() { return reinterpret_cast<Pair *>(misc() + G::off_kagg); }
     __device__ static Pair *jagg() { return reinterpret_cast<Pair *>(misc() + G::off_jagg); }
@@ -436,6 +477,20 @@ __device__ __forceinline__ int64_t item_of(const BlockScanParams &P, int seq) {
     return (int64_t)blockIdx.x + (int64_t)seq * gridDim.x;
 }
 
+// Copy a warp's slice (plus HALO elements and `extra` bytes) starting at
+// global address src into the pieces of stage `dst`, completing on bar.
+template <typename T, int HALO>
+__device__ __forceinline__ void copy_pieces(uint8_t *dst, uintptr_t src, uint32_t extra, uint64_t *bar,
+                                            uint64_t pol) {
+    using G = Geo<T>;
+    const uint32_t bytes = (uint32_t)((G::PIECE + HALO) * sizeof(T)) + extra;
+    mbar_arrive_expect_tx(bar, bytes * G::PIECES);
+#pragma unroll
+    for (int g = 0; g < G::PIECES; ++g)
+        tma_load_1d(dst + g * G::PSTRIDE, reinterpret_cast<const void *>(src + (uintptr_t)g * G::PIECE * sizeof(T)),
+                    bytes, bar, pol);
+}
+
 // Lane 0 of `warp`: issue this warp's slice of its next load, if any.
 template <typename T, int MODE>
 __device__ __forceinline__ void issue_next(int warp) {
@@ -444,6 +499,21 @@ __device__ __forceinline__ void issue_next(int warp) {
     constexpr int HALO = MODE == 3 ? G::HALO_MAX : 0;
     constexpr int LEN = G::SLICE + HALO;
     WarpIssue &wi = *S::issue(warp);
+    {
+        // Steady state: the next tile of a linear item, whole and aligned.
+        const int l = wi.l;
+        if (l < wi.nloads && wi.linear && l >= wi.fast_lo && l < wi.fast_hi) {
+            const int stage = wi.issued & (kStages - 1);
+            uint64_t *bar = S::bar(warp, stage);
+            wi.smode[stage] = 0;
+            fence_proxy_async_smem();
+            copy_pieces<T, HALO>(S::slice(warp, stage), wi.src0 + (uintptr_t)l * G::T_ * sizeof(T), 0, bar,
+                                 policy_evict_first());
+            wi.l = l + 1;
+            wi.issued++;
+            return;
+        }
+    }
     if (wi.nloads < 0) return;
     if (wi.l >= wi.nloads) {
         const BlockScanParams &P = S::params();
@@ -476,6 +546,7 @@ __device__ __forceinline__ void issue_next(int warp) {
             wi.NC = ip.NC;
             wi.klast = ip.klast;
             wi.nloads = item_loads(ip.ok, ip.caseB, ip.q, ip.NC, MODE, ip.klast);
+            wi.linear = ip.ok && (MODE == 3 || !ip.caseB);
             wi.l = 0;
         } while (wi.l >= wi.nloads);
     }
@@ -487,12 +558,9 @@ __device__ __forceinline__ void issue_next(int warp) {
         const int x = load_tile(wi.l, wi.caseB, wi.q, keep, MODE, wi.NC, wi.klast);
         const uint64_t pol = keep ? policy_evict_last() : policy_evict_first();
         if (x >= wi.fast_lo && x < wi.fast_hi) {
-            constexpr uint32_t bytes = (uint32_t)(LEN * sizeof(T));
             wi.smode[stage] = 0;
             fence_proxy_async_smem();
-            mbar_arrive_expect_tx(bar, bytes);
-            tma_load_1d(S::slice(warp, stage), reinterpret_cast<const void *>(wi.src0 + (uintptr_t)x * G::T_ * sizeof(T)),
-                        bytes, bar, pol);
+            copy_pieces<T, HALO>(S::slice(warp, stage), wi.src0 + (uintptr_t)x * G::T_ * sizeof(T), 0, bar, pol);
             smode = 0;
         } else {
             const int64_t a = wi.p0 + (int64_t)x * G::T_ + (int64_t)warp * G::SLICE;
@@ -501,8 +569,7 @@ __device__ __forceinline__ void issue_next(int warp) {
             wi.smode[stage] = smode;
             if (sc.mode != 2) {
                 fence_proxy_async_smem();
-                mbar_arrive_expect_tx(bar, sc.bytes);
-                tma_load_1d(S::slice(warp, stage), reinterpret_cast<const void *>(sc.src), sc.bytes, bar, pol);
+                copy_pieces<T, HALO>(S::slice(warp, stage), sc.src, sc.mode == 1 ? 16 : 0, bar, pol);
             }
         }
     } else {
@@ -526,13 +593,14 @@ struct Consumer {
     using S = Smem<T>;
     static constexpr int V = G::V;
     static constexpr int T_ = G::T_;
+    static constexpr int NW = G::NW;
 
     int tid, lane, warp;
     StageCursor cur;
     bool failed = false;
 
     // CTA barrier (the P ring and block aggregates are shared by all warps).
-    __device__ __forceinline__ void sync() { named_bar_sync(1, kNT); }
+    __device__ __forceinline__ void sync() { named_bar_sync(1, G::NT); }
 
     // Read this thread's V elements of input tile x of the item from the
     // warp's slice stage, then let lane 0 refill the stage with the warp's
@@ -549,7 +617,7 @@ struct Consumer {
         const uint8_t *sb = S::slice(warp, cur.stage);
         if (mode == 0) {
             uint32_t wd[4 * G::NCH];
-            const uint4 *p4 = reinterpret_cast<const uint4 *>(sb + (size_t)lane * V * sizeof(T));
+            const uint4 *p4 = reinterpret_cast<const uint4 *>(S::lane_base(sb, lane));
 #pragma unroll
             for (int c = 0; c < G::NCH; ++c) {
                 uint4 v = p4[c];
@@ -560,7 +628,7 @@ struct Consumer {
 #pragma unroll
             for (int i = 0; i < V; ++i) xm[i] = xn[i] = xv[i];
         } else if (mode == 1) {
-            const T *pe = reinterpret_cast<const T *>(sb) + (smode >> 8) + lane * V;
+            const T *pe = reinterpret_cast<const T *>(S::lane_base(sb, lane)) + (smode >> 8);
 #pragma unroll
             for (int i = 0; i < V; ++i) xm[i] = xn[i] = Elem<T>::load(pe[i]);
         } else {
@@ -684,13 +752,14 @@ struct Consumer {
             const int q = ip.q;
             Pair a;
             if (!ip.caseB) {
-                a = lane < 8 ? S::kagg()[(c % 3) * 8 + lane]
-                             : (lane < 16 ? S::kagg()[((c + 1) % 3) * 8 + lane - 8] : Elem<T>::pair(Elem<T>::lo(), Elem<T>::hi()));
+                a = lane < NW ? S::kagg()[(c % 3) * NW + lane]
+                              : (lane < 2 * NW ? S::kagg()[((c + 1) % 3) * NW + lane - NW]
+                                               : Elem<T>::pair(Elem<T>::lo(), Elem<T>::hi()));
             } else {
-                a = lane < 8 ? S::jagg()[(c & 1) * 8 + lane]
-                             : (lane < 16 ? S::kagg()[((c + q) % 3) * 8 + lane - 8]
-                                          : (lane < 24 ? S::kagg()[((c + q + 1) % 3) * 8 + lane - 16]
-                                                       : Elem<T>::pair(Elem<T>::lo(), Elem<T>::hi())));
+                a = lane < NW ? S::jagg()[(c & 1) * NW + lane]
+                              : (lane < 2 * NW ? S::kagg()[((c + q) % 3) * NW + lane - NW]
+                                               : (lane < 3 * NW ? S::kagg()[((c + q + 1) % 3) * NW + lane - 2 * NW]
+                                                                : Elem<T>::pair(Elem<T>::lo(), Elem<T>::hi())));
             }
             R am = lane > warp ? Elem<T>::pmax(a) : Elem<T>::lo();
             R an = lane > warp ? Elem<T>::pmin(a) : Elem<T>::hi();
@@ -703,11 +772,11 @@ struct Consumer {
             if (ip.caseB) {
                 R tm, tn;
                 tiles_between(c, q, tm, tn);
-                if (lane >= 7) { am = vmax(am, tm); an = vmin(an, tn); }
+                if (lane >= NW - 1) { am = vmax(am, tm); an = vmin(an, tn); }
             }
             // Lane of k0's block; outputs i >= cross have k in the next block.
             const int kb = kr0 >> lgB;
-            const int g0 = ip.caseB ? kb - ((c + q) << 3) + 8 : kb - (c << 3);
+            const int g0 = ip.caseB ? kb - (c + q) * NW + NW : kb - c * NW;
             const int cross = ((kb + 1) << lgB) - kr0;
             const R c0m = __shfl_sync(0xffffffffu, am, g0 - 1), c0n = __shfl_sync(0xffffffffu, an, g0 - 1);
             const R c1m = __shfl_sync(0xffffffffu, am, g0), c1n = __shfl_sync(0xffffffffu, an, g0);
@@ -765,6 +834,12 @@ struct Consumer {
     }
 
     __device__ __forceinline__ void store(T *dst, const R (&v)[V], int cnt) const {
+        if constexpr (G::NCH % 2 == 0) {
+            if (cnt == V && (((uintptr_t)dst) & 31) == 0) {
+                store_v8(dst, v);
+                return;
+            }
+        }
         if (cnt == V && (((uintptr_t)dst) & 15) == 0) {
             uint4 *d4 = reinterpret_cast<uint4 *>(dst);
 #pragma unroll
@@ -786,10 +861,10 @@ struct Consumer {
     // Tile aggregate of K tile x from its warp-block aggregates (warp 0).
     __device__ __forceinline__ void publish_tile_aggregate(int x) const {
         if (warp != 0) return;
-        Pair a = lane < 8 ? S::kagg()[(x % 3) * 8 + lane] : Elem<T>::pair(Elem<T>::lo(), Elem<T>::hi());
+        Pair a = lane < NW ? S::kagg()[(x % 3) * NW + lane] : Elem<T>::pair(Elem<T>::lo(), Elem<T>::hi());
         R m = Elem<T>::pmax(a), n = Elem<T>::pmin(a);
 #pragma unroll
-        for (int d = 4; d >= 1; d >>= 1) {
+        for (int d = NW / 2; d >= 1; d >>= 1) {
             m = vmax(m, __shfl_xor_sync(0xffffffffu, m, d));
             n = vmin(n, __shfl_xor_sync(0xffffffffu, n, d));
         }
@@ -810,12 +885,361 @@ struct Consumer {
                 R tm, tn;
                 if (pre) {
                     lane_carry(0, pm, pn, lgS, tm, tn);
-                    if (MODE == 2 && lane == 31) S::kagg()[kslot * 8 + warp] = Elem<T>::pair(tm, tn);
+                    if (MODE == 2 && lane == 31) S::kagg()[kslot * NW + warp] = Elem<T>::pair(tm, tn);
                 }
                 if (suf) {
                     lane_carry(1, sm, sn, lgS, tm, tn);
-                    if (MODE == 2 && jbuf >= 0 && lane == 0) S::jagg()[jbuf * 8 + warp] = Elem<T>::pair(tm, tn);
+                    if (MODE == 2 && jbuf >= 0 && lane == 0) S::jagg()[jbuf * NW + warp] = Elem<T>::pair(tm, tn);
                 }
+            }
+        }
+    }
+
+    // ------------------------------------- modes 1 and 2: thread-local scans
+    // The window [j, j+s] splits into (a) the rest of j's V-element thread
+    // block, (b) the later thread blocks of j's scan block, (c) the whole scan
+    // blocks in between, (d) the earlier thread blocks of k's scan block and
+    // (e) the start of k's thread block up to k = j+s.  (a) and (e) are scans
+    // local to one thread; (b) and (d) are one lane carry per thread (f and e
+    // below), (c) one aggregate per thread and side of k.  So every output is
+    // max(local suffix, per-thread constant, local prefix from the ring).
+
+    // K role: local prefix of the thread's elements; lane carries within the
+    // scan block of 2^lgS lanes: e (exclusive) and g (inclusive).
+    __device__ __forceinline__ void scan_k(int lgS, const R (&xm)[V], const R (&xn)[V], R (&pm)[V], R (&pn)[V],
+                                           R &em, R &en, R &gm, R &gn) const {
+        pm[0] = xm[0];
+        pn[0] = xn[0];
+#pragma unroll
+        for (int i = 1; i < V; ++i) { pm[i] = vmax(pm[i - 1], xm[i]); pn[i] = vmin(pn[i - 1], xn[i]); }
+        const int segl = 1 << lgS;
+        const int pos = lane & (segl - 1);
+        R tm = pm[V - 1], tn = pn[V - 1];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            if (d >= segl) break;
+            const R um = __shfl_up_sync(0xffffffffu, tm, d);
+            const R un = __shfl_up_sync(0xffffffffu, tn, d);
+            if (pos >= d) { tm = vmax(tm, um); tn = vmin(tn, un); }
+        }
+        gm = tm;
+        gn = tn;
+        const R xm1 = __shfl_up_sync(0xffffffffu, tm, 1);
+        const R xn1 = __shfl_up_sync(0xffffffffu, tn, 1);
+        em = pos ? xm1 : Elem<T>::lo();
+        en = pos ? xn1 : Elem<T>::hi();
+    }
+
+    // J role: local suffix; lane carry f (exclusive suffix within the scan
+    // block) and h (inclusive: at the block's first lane, the block aggregate).
+    __device__ __forceinline__ void scan_j(int lgS, const R (&xm)[V], const R (&xn)[V], R (&sm)[V], R (&sn)[V],
+                                           R &fm, R &fn, R &hm, R &hn) const {
+        sm[V - 1] = xm[V - 1];
+        sn[V - 1] = xn[V - 1];
+#pragma unroll
+        for (int i = V - 2; i >= 0; --i) { sm[i] = vmax(sm[i + 1], xm[i]); sn[i] = vmin(sn[i + 1], xn[i]); }
+        const int segl = 1 << lgS;
+        const int pos = (segl - 1) - (lane & (segl - 1));
+        R tm = sm[0], tn = sn[0];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            if (d >= segl) break;
+            const R um = __shfl_down_sync(0xffffffffu, tm, d);
+            const R un = __shfl_down_sync(0xffffffffu, tn, d);
+            if (pos >= d) { tm = vmax(tm, um); tn = vmin(tn, un); }
+        }
+        hm = tm;
+        hn = tn;
+        const R xm1 = __shfl_down_sync(0xffffffffu, tm, 1);
+        const R xn1 = __shfl_down_sync(0xffffffffu, tn, 1);
+        fm = pos ? xm1 : Elem<T>::lo();
+        fn = pos ? xn1 : Elem<T>::hi();
+    }
+
+    // Both roles at once (independent chains interleave): K role on km/kn,
+    // J role on jm/jn (the same tile in case A).
+    __device__ __forceinline__ void scan_kj(int lgS, const R (&km)[V], const R (&kn)[V], const R (&jm)[V],
+                                            const R (&jn)[V], R (&pm)[V], R (&pn)[V], R &em, R &en, R &gm, R &gn,
+                                            R (&sm)[V], R (&sn)[V], R &fm, R &fn, R &hm, R &hn) const {
+        pm[0] = km[0];
+        pn[0] = kn[0];
+        sm[V - 1] = jm[V - 1];
+        sn[V - 1] = jn[V - 1];
+#pragma unroll
+        for (int i = 1; i < V; ++i) {
+            pm[i] = vmax(pm[i - 1], km[i]);
+            pn[i] = vmin(pn[i - 1], kn[i]);
+            sm[V - 1 - i] = vmax(sm[V - i], jm[V - 1 - i]);
+            sn[V - 1 - i] = vmin(sn[V - i], jn[V - 1 - i]);
+        }
+        const int segl = 1 << lgS;
+        const int posk = lane & (segl - 1), posj = (segl - 1) - posk;
+        R am = pm[V - 1], an = pn[V - 1], bm = sm[0], bn = sn[0];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            if (d >= segl) break;
+            const R uam = __shfl_up_sync(0xffffffffu, am, d);
+            const R uan = __shfl_up_sync(0xffffffffu, an, d);
+            const R ubm = __shfl_down_sync(0xffffffffu, bm, d);
+            const R ubn = __shfl_down_sync(0xffffffffu, bn, d);
+            if (posk >= d) { am = vmax(am, uam); an = vmin(an, uan); }
+            if (posj >= d) { bm = vmax(bm, ubm); bn = vmin(bn, ubn); }
+        }
+        gm = am;
+        gn = an;
+        hm = bm;
+        hn = bn;
+        const R xam = __shfl_up_sync(0xffffffffu, am, 1);
+        const R xan = __shfl_up_sync(0xffffffffu, an, 1);
+        const R xbm = __shfl_down_sync(0xffffffffu, bm, 1);
+        const R xbn = __shfl_down_sync(0xffffffffu, bn, 1);
+        em = posk ? xam : Elem<T>::lo();
+        en = posk ? xan : Elem<T>::hi();
+        fm = posj ? xbm : Elem<T>::lo();
+        fn = posj ? xbn : Elem<T>::hi();
+    }
+
+    // Carry record of item-relative thread block u (its tile is in the ring).
+    __device__ __forceinline__ const CarryRec<T> &cr_at(int u) const {
+        return S::cr()[((u >> G::LGNT) % 3) * G::NT + (u & (G::NT - 1))];
+    }
+
+    // K-side bookkeeping of tile x: local prefixes into the P ring, carries
+    // into the carry ring, and (mode 2) the warp's block aggregate.
+    template <int MODE>
+    __device__ __forceinline__ void k_publish(int x, const R (&pm)[V], const R (&pn)[V], R em, R en, R gm, R gn) {
+        ring_write(x, pm, pn);
+        CarryRec<T> rec;
+        rec.e = Elem<T>::pair(em, en);
+        rec.g = Elem<T>::pair(gm, gn);
+        S::cr()[(x % 3) * G::NT + tid] = rec;
+        if (MODE == 2 && lane == 31) S::kagg()[(x % 3) * NW + warp] = rec.g;
+    }
+
+    // Outputs of output tile c (modes 1, 2): sm/sn the local suffixes of the
+    // J tile, fm/fn its lane carry.  vec: the item's outputs start 16-byte
+    // aligned (full groups of V are stored as vectors).
+    template <int MODE>
+    __device__ __forceinline__ void outputs12(const ItemPlan<T> &ip, int c, const R (&sm)[V], const R (&sn)[V], R fm,
+                                              R fn, int vec) {
+        const int lgB = ip.lgB;
+        const int jr0 = c * T_ + tid * V;
+        const int kr0 = jr0 + ip.s;
+        const int p = ring_index(kr0);
+        const int phys = p + (p >> G::PS);
+        const int cpad = (1 << G::PS) - (p & ((1 << G::PS) - 1));
+        const int hi_base = (p + cpad == G::RING) ? -cpad : phys + 1;
+        // k = kr0 + i lies in thread block tk0 for i < crossT, else tk0 + 1.
+        const int o = kr0 & (V - 1);  // the same for every thread of the item
+        const int crossT = o ? V - o : V;
+        const int tk0 = kr0 >> G::LGV;
+        const CarryRec<T> r0 = cr_at(tk0);
+        R e1m = Elem<T>::lo(), e1n = Elem<T>::hi();
+        if (o) {
+            const CarryRec<T> r1 = cr_at(tk0 + 1);
+            e1m = Elem<T>::pmax(r1.e);
+            e1n = Elem<T>::pmin(r1.e);
+        }
+        const int Bj = jr0 >> lgB;
+        const int Bk0 = kr0 >> lgB;
+        const int Bk1 = (kr0 + crossT) >> lgB;  // scan block of k for i >= crossT (if any)
+        R mid0m, mid0n, mid1m, mid1n;
+        if (MODE == 1 || !ip.caseB) {
+            // k's scan block is Bj+q2 or Bj+q2+1 (q2 = s >> lgB), the same two
+            // for the whole warp: Ma = blocks Bj+1 .. Bj+q2-1, Mb adds Bj+q2.
+            // Mode 1 has q2 = 1 (Ma empty); mode 2 case A reads the warp-block
+            // aggregates of tiles c and c+1.
+            const int q2 = ip.s >> lgB;
+            R Mam = Elem<T>::lo(), Man = Elem<T>::hi(), Mbm, Mbn;
+            if constexpr (MODE == 1) {
+                const CarryRec<T> rb = cr_at(((Bj + 2) << (lgB - G::LGV)) - 1);
+                Mbm = Elem<T>::pmax(rb.g);
+                Mbn = Elem<T>::pmin(rb.g);
+            } else {
+                const int s0 = c % 3, s1 = s0 == 2 ? 0 : s0 + 1;
+#pragma unroll
+                for (int u = 1; u < NW; ++u) {
+                    if (u < q2) {
+                        const int g = warp + u;  // warp block of tile c (< NW) or c+1
+                        const Pair a = S::kagg()[(g < NW ? s0 : s1) * NW + (g & (NW - 1))];
+                        Mam = vmax(Mam, Elem<T>::pmax(a));
+                        Man = vmin(Man, Elem<T>::pmin(a));
+                    }
+                }
+                const int g = warp + q2;
+                const Pair a = S::kagg()[(g < NW ? s0 : s1) * NW + (g & (NW - 1))];
+                Mbm = vmax(Mam, Elem<T>::pmax(a));
+                Mbn = vmin(Man, Elem<T>::pmin(a));
+            }
+            const bool a0 = Bk0 == Bj + q2, a1 = Bk1 == Bj + q2;
+            mid0m = a0 ? Mam : Mbm;
+            mid0n = a0 ? Man : Mbn;
+            mid1m = a1 ? Mam : Mbm;
+            mid1n = a1 ? Man : Mbn;
+        } else {
+            // Case B lane array of warp-block aggregates in window order: lanes
+            // 0..NW-1 = J tile c, then K tiles c+q and c+q+1; prefix from the
+            // block after j's (lane warp+1); the whole tiles c+1..c+q-1 join
+            // every lane from NW-1 on.
+            const int q = ip.q;
+            const Pair a = lane < NW ? S::jagg()[(c & 1) * NW + lane]
+                                     : (lane < 2 * NW ? S::kagg()[((c + q) % 3) * NW + lane - NW]
+                                                      : (lane < 3 * NW ? S::kagg()[((c + q + 1) % 3) * NW + lane - 2 * NW]
+                                                                       : Elem<T>::pair(Elem<T>::lo(), Elem<T>::hi())));
+            R am = lane > warp ? Elem<T>::pmax(a) : Elem<T>::lo();
+            R an = lane > warp ? Elem<T>::pmin(a) : Elem<T>::hi();
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const R um = __shfl_up_sync(0xffffffffu, am, d);
+                const R un = __shfl_up_sync(0xffffffffu, an, d);
+                if (lane >= d) { am = vmax(am, um); an = vmin(an, un); }
+            }
+            R tm, tn;
+            tiles_between(c, q, tm, tn);
+            if (lane >= NW - 1) { am = vmax(am, tm); an = vmin(an, tn); }
+            const int base = (c + q) * NW - NW;
+            const int g0 = Bk0 - base, g1 = Bk1 - base;
+            mid0m = __shfl_sync(0xffffffffu, am, g0 - 1);
+            mid0n = __shfl_sync(0xffffffffu, an, g0 - 1);
+            mid1m = __shfl_sync(0xffffffffu, am, (g1 - 1) & 31);
+            mid1n = __shfl_sync(0xffffffffu, an, (g1 - 1) & 31);
+        }
+        const R c0m = vmax3(fm, mid0m, Elem<T>::pmax(r0.e)), c0n = vmin3(fn, mid0n, Elem<T>::pmin(r0.e));
+        const R c1m = vmax3(fm, mid1m, e1m), c1n = vmin3(fn, mid1n, e1n);
+        R om[V], on[V];
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            const Pair pr = S::ring()[(i < cpad ? phys : hi_base) + i];
+            const bool far = i >= crossT;
+            om[i] = vmax3(sm[i], far ? c1m : c0m, Elem<T>::pmax(pr));
+            on[i] = vmin3(sn[i], far ? c1n : c0n, Elem<T>::pmin(pr));
+        }
+        const int64_t o0 = ip.o_begin + jr0;
+        if (vec && o0 + V <= ip.o_end) {
+            if constexpr (G::NCH % 2 == 0) {
+                if (vec == 2) {
+                    if (ip.omax) store_v8(ip.omax + o0, om);
+                    if (ip.omin) store_v8(ip.omin + o0, on);
+                    return;
+                }
+            }
+            if (ip.omax) store_vec(ip.omax + o0, om);
+            if (ip.omin) store_vec(ip.omin + o0, on);
+        } else if (o0 < ip.o_end) {
+            const int cnt = o0 + V <= ip.o_end ? V : (int)(ip.o_end - o0);
+            if (ip.omax) store(ip.omax + o0, om, cnt);
+            if (ip.omin) store(ip.omin + o0, on, cnt);
+        }
+    }
+
+    // 32-byte streaming stores (full sectors): V * sizeof(T) a multiple of 32,
+    // dst 32-byte aligned.
+    __device__ __forceinline__ void store_v8(T *dst, const R (&v)[V]) const {
+#pragma unroll
+        for (int c = 0; c < G::NCH / 2; ++c) {
+            asm volatile("st.global.cs.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(
+                             reinterpret_cast<uint8_t *>(dst) + 32 * c),
+                         "r"(pack_word<T>(v, 8 * c)), "r"(pack_word<T>(v, 8 * c + 1)), "r"(pack_word<T>(v, 8 * c + 2)),
+                         "r"(pack_word<T>(v, 8 * c + 3)), "r"(pack_word<T>(v, 8 * c + 4)),
+                         "r"(pack_word<T>(v, 8 * c + 5)), "r"(pack_word<T>(v, 8 * c + 6)),
+                         "r"(pack_word<T>(v, 8 * c + 7))
+                         : "memory");
+        }
+    }
+
+    __device__ __forceinline__ void store_vec(T *dst, const R (&v)[V]) const {
+        uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+#pragma unroll
+        for (int c = 0; c < G::NCH; ++c) {
+            uint4 u;
+            u.x = pack_word<T>(v, 4 * c);
+            u.y = pack_word<T>(v, 4 * c + 1);
+            u.z = pack_word<T>(v, 4 * c + 2);
+            u.w = pack_word<T>(v, 4 * c + 3);
+            __stcs(d4 + c, u);
+        }
+    }
+
+    // J-side state of one output tile: local suffixes and lane carry.
+    struct JState {
+        R sm[V], sn[V];
+        R fm, fn;
+    };
+
+    // Case A iteration c: read tile c+1 (K role now, J role of the next
+    // output tile, into nx), then the outputs of tile c from cur.
+    template <int MODE>
+    __device__ __forceinline__ bool step_a(const ItemPlan<T> &ip, int c, int lgS, int vec, const JState &cur,
+                                           JState &nx) {
+        const bool kload = c + 1 < ip.NC || ip.klast;  // else no window reaches tile c+1
+        if (kload) {
+            R xm[V], xn[V];
+            if (!read_tile(ip, c + 1, xm, xn)) return false;
+            R pm[V], pn[V], em, en, gm, gn, hm, hn;
+            scan_kj(lgS, xm, xn, xm, xn, pm, pn, em, en, gm, gn, nx.sm, nx.sn, nx.fm, nx.fn, hm, hn);
+            k_publish<MODE>(c + 1, pm, pn, em, en, gm, gn);
+        }
+        sync();
+        outputs12<MODE>(ip, c, cur.sm, cur.sn, cur.fm, cur.fn, vec);
+        return true;
+    }
+
+    template <int MODE>
+    __device__ __forceinline__ void run_item12(const ItemPlan<T> &ip) {
+        const int q = ip.q;
+        const int lgS = ip.lgB - G::LGV;
+        // Output alignment of the item (outputs of a thread start V elements
+        // apart): 2 = 32-byte, 1 = 16-byte, 0 = neither.
+        const uintptr_t oa = ((uintptr_t)(ip.omax + ip.o_begin)) | ((uintptr_t)(ip.omin + ip.o_begin));
+        const int vec = (oa & 31) == 0 ? 2 : ((oa & 15) == 0 ? 1 : 0);
+        if (!ip.caseB) {
+            // Tile c is the J tile of output tile c and a K tile of c-1 and c.
+            // The loop is unrolled by two so that the J states alternate.
+            JState ja, jb;
+            {
+                R xm[V], xn[V];
+                if (!read_tile(ip, 0, xm, xn)) return;
+                R pm[V], pn[V], em, en, gm, gn, hm, hn;
+                scan_kj(lgS, xm, xn, xm, xn, pm, pn, em, en, gm, gn, ja.sm, ja.sn, ja.fm, ja.fn, hm, hn);
+                k_publish<MODE>(0, pm, pn, em, en, gm, gn);
+            }
+            for (int c = 0; c < ip.NC; c += 2) {
+                if (!step_a<MODE>(ip, c, lgS, vec, ja, jb)) return;
+                if (c + 1 < ip.NC && !step_a<MODE>(ip, c + 1, lgS, vec, jb, ja)) return;
+            }
+        } else {
+            // w - 1 >= T: K tiles c+q, c+q+1; the J tile c is read again.
+            for (int x = 1; x <= q; ++x) {
+                R xm[V], xn[V];
+                if (!read_tile(ip, x, xm, xn)) return;
+                R pm[V], pn[V], em, en, gm, gn;
+                scan_k(lgS, xm, xn, pm, pn, em, en, gm, gn);
+                k_publish<MODE>(x, pm, pn, em, en, gm, gn);
+                sync();
+                publish_tile_aggregate(x);
+            }
+            sync();
+            for (int c = 0; c < ip.NC; ++c) {
+                const int xk = c + q + 1;
+                const bool kload = c + 1 < ip.NC || ip.klast;
+                JState js;
+                R hm, hn;
+                if (kload) {
+                    R km[V], kn[V], jm[V], jn[V];
+                    if (!read_tile(ip, xk, km, kn)) return;  // K tile c+q+1
+                    if (!read_tile(ip, c, jm, jn)) return;   // J tile c
+                    R pm[V], pn[V], em, en, gm, gn;
+                    scan_kj(lgS, km, kn, jm, jn, pm, pn, em, en, gm, gn, js.sm, js.sn, js.fm, js.fn, hm, hn);
+                    k_publish<MODE>(xk, pm, pn, em, en, gm, gn);
+                } else {
+                    R jm[V], jn[V];
+                    if (!read_tile(ip, c, jm, jn)) return;
+                    scan_j(lgS, jm, jn, js.sm, js.sn, js.fm, js.fn, hm, hn);
+                }
+                if (lane == 0) S::jagg()[(c & 1) * NW + warp] = Elem<T>::pair(hm, hn);
+                sync();
+                if (kload) publish_tile_aggregate(xk);
+                outputs12<MODE>(ip, c, js.sm, js.sn, js.fm, js.fn, vec);
             }
         }
     }
@@ -836,7 +1260,7 @@ struct Consumer {
         if (mode == 0) {
             constexpr int NW = NE * (int)sizeof(T) / 4;
             uint32_t wd[NW];
-            const uint4 *p4 = reinterpret_cast<const uint4 *>(sb + (size_t)lane * V * sizeof(T));
+            const uint4 *p4 = reinterpret_cast<const uint4 *>(S::lane_base(sb, lane));
 #pragma unroll
             for (int c = 0; c < NW / 4; ++c) {
                 uint4 v = p4[c];
@@ -847,7 +1271,7 @@ struct Consumer {
 #pragma unroll
             for (int i = 0; i < NE; ++i) xm[i] = xn[i] = xv[i];
         } else if (mode == 1) {
-            const T *pe = reinterpret_cast<const T *>(sb) + (smode >> 8) + lane * V;
+            const T *pe = reinterpret_cast<const T *>(S::lane_base(sb, lane)) + (smode >> 8);
 #pragma unroll
             for (int i = 0; i < NE; ++i) xm[i] = xn[i] = Elem<T>::load(pe[i]);
         } else {
@@ -974,7 +1398,7 @@ struct Consumer {
 // One instantiation per block mode keeps each one within 128 registers (two
 // CTAs per SM); an item whose mode differs is rejected (kErrBadItem).
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kThreads, (Elem<T>::V == 16 && MODE != 3) ? 1 : 2)
+__global__ void __launch_bounds__(Geo<T>::NT, (Geo<T>::NT * Elem<T>::V == 4096 && MODE != 3) ? 1 : 2)
     blockscan_kernel(const BlockScanParams P) {
     using S = Smem<T>;
     const int tid = threadIdx.x;
@@ -998,6 +1422,7 @@ __global__ void __launch_bounds__(kThreads, (Elem<T>::V == 16 && MODE != 3) ? 1 
         wi.seq = -1;
         wi.l = wi.nloads = 0;
         wi.q = wi.caseB = wi.ok = wi.NC = wi.klast = 0;
+        wi.linear = 0;
         wi.issued = 0;
         fence_mbar_init();
     }
@@ -1028,8 +1453,10 @@ __global__ void __launch_bounds__(kThreads, (Elem<T>::V == 16 && MODE != 3) ? 1 
         } else {
             if constexpr (MODE == 3)
                 cs.run_item_slide(ip);
-            else
+            else if constexpr (MODE == 0 || !kCarryRing<T>)
                 cs.template run_item<MODE>(ip);
+            else
+                cs.template run_item12<MODE>(ip);
             if (cs.failed) return;
         }
         // Thread 0 fetches the ticket that the prefetch will need next, then
@@ -1038,7 +1465,7 @@ __global__ void __launch_bounds__(kThreads, (Elem<T>::V == 16 && MODE != 3) ? 1 
             S::queue()[fetched & (kQueue - 1)] = atomicAdd(P.ticket, 1);
             ++fetched;
         }
-        named_bar_sync(1, kNT);
+        named_bar_sync(1, Geo<T>::NT);
     }
 }
 

@@ -23,7 +23,7 @@ template <typename T, int MODE> static cudaError_t prepare_blockscan(int device,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     int k = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, blockscan_kernel<T, MODE>, kThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, blockscan_kernel<T, MODE>, Geo<T>::NT, smem);
     if (e != cudaSuccess) return e;
     if (k < 1) k = 1;
     if (device >= 0 && device < 64) occ[device] = k;
@@ -42,7 +42,7 @@ template <typename T> int block_mode(int64_t w, bool allow_slide) {
 
 template <typename T, int MODE>
 static void launch_bs(const BlockScanParams &P, int grid, cudaStream_t st) {
-    blockscan_kernel<T, MODE><<<(unsigned)grid, kThreads, smem_of<T>(MODE), st>>>(P);
+    blockscan_kernel<T, MODE><<<(unsigned)grid, Geo<T>::NT, smem_of<T>(MODE), st>>>(P);
 }
 
 template <typename T>

@@ -196,6 +196,19 @@ def test_chunk_invariance(dtype):
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("threads", [1, 2, 3, 7, 64])
+def test_wedge_mt_equals_definition(dtype, threads):
+    """The threaded chunk+halo wedge (the timed CPU baseline) against the
+    definition, with thread counts that leave ragged and empty ranges."""
+    for n, w in ((20011, 1), (20011, 2), (20011, 101), (300, 250), (50, 50), (10, 20)):
+        a = synth.random_walk(n, n + w, dtype)
+        mx, mn = oracle.bf1d(a, w)
+        tmx, tmn, used = oracle.wedge_mt(a, w, threads)
+        assert used >= 1
+        assert np.array_equal(tmx, mx) and np.array_equal(tmn, mn)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
 def test_sampled_equals_full(dtype):
     a = synth.random_walk(10000, 23, dtype)
     w = 777
