@@ -226,12 +226,6 @@ struct WarpIssue {
     int32_t smode[kStages];  // per stage: copy mode | shift << 8, for the readers
 };
 
-// Lane carries of one thread's V-element block inside its scan block (modes
-// 1 and 2): e = maximum/minimum of the threads before it in the block
-// (exclusive), g = including its own elements.
-template <typename T> struct __align__(2 * sizeof(typename Elem<T>::Pair)) CarryRec {
-    typename Elem<T>::Pair e, g;
-};
 
 // Modes 1 and 2 use thread-local scans with lane carries kept per thread (the
 // carry ring) for every type but f64, whose larger pairs would leave room for
@@ -253,10 +247,11 @@ template <typename T> struct Geo {
     // Register-slide halo (elements after the slice; windows up to HALO_MAX+1).
     static constexpr int HALO_MAX = 8 > 16 / (int)sizeof(T) ? 8 : 16 / (int)sizeof(T);
     // A warp's slice arrives in PIECES copies of PLANES lanes' elements each,
-    // placed PSTRIDE bytes apart (PSTRIDE/16 odd): lanes reading 16-byte words
-    // of their own V elements then fall on distinct bank groups.  Each piece
-    // holds room for the register-slide halo and a 16-byte shift.
-    static constexpr int PIECES = V * (int)sizeof(T) / 16;  // 16-byte words per lane
+    // placed PSTRIDE bytes apart; each piece holds room for the
+    // register-slide halo and a 16-byte shift.  One piece: the bank spread of
+    // the readers comes from the order in which lanes read their words
+    // (see read_tile).
+    static constexpr int PIECES = 1;
     static constexpr int PLANES = 32 / PIECES;
     static constexpr int PIECE = PLANES * V;  // elements
     static constexpr int PSTRIDE0 = (PIECE + HALO_MAX) * (int)sizeof(T) + 16;
@@ -277,7 +272,10 @@ template <typename T> struct Geo {
     static constexpr size_t off_ring = off_stage + rnd((size_t)NW * kStages * SLICE_BYTES);
     static constexpr size_t off_ta = off_ring + rnd(RING_PHYS * sizeof(Pair));
     static constexpr size_t off_cr = off_ta + rnd(kQCap * sizeof(Pair));  // [3 tiles][NT] carry records
-    static constexpr size_t smem_bytes = off_cr + (kCarryRing<T> ? rnd(3 * NT * sizeof(CarryRec<T>)) : 0);
+    // Carry ring (modes 1, 2): per thread block of the last three tiles, the
+    // lane carries inside its scan block: e = threads before it (exclusive),
+    // g = including its own elements; [2][3 NT] pairs.
+    static constexpr size_t smem_bytes = off_cr + (kCarryRing<T> ? rnd(2 * 3 * NT * sizeof(Pair)) : 0);
     // The register slide uses only the misc area and the stages.
     static constexpr size_t smem_bytes_slide = off_ring;
 };
@@ -294,7 +292,8 @@ template <typename T> struct Smem {
     }
     __device__ static Pair *ring() { return reinterpret_cast<Pair *>(bs_smem + G::off_ring); }
     __device__ static Pair *ta() { return reinterpret_cast<Pair *>(bs_smem + G::off_ta); }
-    __device__ static CarryRec<T> *cr() { return reinterpret_cast<CarryRec<T> *>(bs_smem + G::off_cr); }
+    __device__ static Pair *cre() { return reinterpret_cast<Pair *>(bs_smem + G::off_cr); }
+    __device__ static Pair *crg() { return cre() + 3 * G::NT; }
     __device__ static uint8_t *misc() { return bs_smem + G::off_misc; }
     __device__ static Pair *kagg() { return reinterpret_cast<Pair *>(misc() + G::off_kagg); }
     __device__ static Pair *jagg() { return reinterpret_cast<Pair *>(misc() + G::off_jagg); }
@@ -618,10 +617,38 @@ struct Consumer {
         if (mode == 0) {
             uint32_t wd[4 * G::NCH];
             const uint4 *p4 = reinterpret_cast<const uint4 *>(S::lane_base(sb, lane));
+            if constexpr (G::NCH == 2 || G::NCH == 4) {
+                // 16-byte reads are served eight lanes at a time; lanes V*sz
+                // bytes apart reading the same word index would share banks.
+                // Lane l reads its words starting at rot = (l / (8/NCH)) mod
+                // NCH, which spreads each group of eight over all banks, then
+                // a barrel shift restores the order.
+                constexpr int NC = G::NCH;
+                const int rot = (lane / (8 / NC)) & (NC - 1);
+                uint4 u[NC];
 #pragma unroll
-            for (int c = 0; c < G::NCH; ++c) {
-                uint4 v = p4[c];
-                wd[4 * c] = v.x; wd[4 * c + 1] = v.y; wd[4 * c + 2] = v.z; wd[4 * c + 3] = v.w;
+                for (int c = 0; c < NC; ++c) u[c] = p4[(c + rot) & (NC - 1)];
+                // u[c] holds word (c + rot) mod NC: rotate right by rot.
+#pragma unroll
+                for (int b = 1; b < NC; b <<= 1) {
+                    if (rot & b) {
+                        uint4 t[NC];
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) t[c] = u[(c - b + NC) & (NC - 1)];
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) u[c] = t[c];
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    wd[4 * c] = u[c].x; wd[4 * c + 1] = u[c].y; wd[4 * c + 2] = u[c].z; wd[4 * c + 3] = u[c].w;
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < G::NCH; ++c) {
+                    uint4 v = p4[c];
+                    wd[4 * c] = v.x; wd[4 * c + 1] = v.y; wd[4 * c + 2] = v.z; wd[4 * c + 3] = v.w;
+                }
             }
             R xv[V];
             ExtractLoop<T, 0, 0, V>::run(wd, xv);
@@ -999,21 +1026,24 @@ struct Consumer {
         fn = posj ? xbn : Elem<T>::hi();
     }
 
-    // Carry record of item-relative thread block u (its tile is in the ring).
-    __device__ __forceinline__ const CarryRec<T> &cr_at(int u) const {
-        return S::cr()[((u >> G::LGNT) % 3) * G::NT + (u & (G::NT - 1))];
-    }
+    // Column of item-relative thread block u in the rings of modes 1 and 2
+    // (its tile is one of the last three).
+    __device__ __forceinline__ int col_of(int u) const { return ((u >> G::LGNT) % 3) * G::NT + (u & (G::NT - 1)); }
 
-    // K-side bookkeeping of tile x: local prefixes into the P ring, carries
-    // into the carry ring, and (mode 2) the warp's block aggregate.
+    // K-side bookkeeping of tile x: local prefixes into the P ring, stored
+    // element-major (element i of thread block u at row i, column u, so
+    // that a warp reading one element of consecutive blocks touches
+    // consecutive words), carries into the carry ring, and (mode 2) the
+    // warp's block aggregate.
     template <int MODE>
     __device__ __forceinline__ void k_publish(int x, const R (&pm)[V], const R (&pn)[V], R em, R en, R gm, R gn) {
-        ring_write(x, pm, pn);
-        CarryRec<T> rec;
-        rec.e = Elem<T>::pair(em, en);
-        rec.g = Elem<T>::pair(gm, gn);
-        S::cr()[(x % 3) * G::NT + tid] = rec;
-        if (MODE == 2 && lane == 31) S::kagg()[(x % 3) * NW + warp] = rec.g;
+        const int col = (x % 3) * G::NT + tid;
+        Pair *r = S::ring() + col;
+#pragma unroll
+        for (int i = 0; i < V; ++i) r[i * 3 * G::NT] = Elem<T>::pair(pm[i], pn[i]);
+        S::cre()[col] = Elem<T>::pair(em, en);
+        S::crg()[col] = Elem<T>::pair(gm, gn);
+        if (MODE == 2 && lane == 31) S::kagg()[(x % 3) * NW + warp] = Elem<T>::pair(gm, gn);
     }
 
     // Outputs of output tile c (modes 1, 2): sm/sn the local suffixes of the
@@ -1025,20 +1055,19 @@ struct Consumer {
         const int lgB = ip.lgB;
         const int jr0 = c * T_ + tid * V;
         const int kr0 = jr0 + ip.s;
-        const int p = ring_index(kr0);
-        const int phys = p + (p >> G::PS);
-        const int cpad = (1 << G::PS) - (p & ((1 << G::PS) - 1));
-        const int hi_base = (p + cpad == G::RING) ? -cpad : phys + 1;
-        // k = kr0 + i lies in thread block tk0 for i < crossT, else tk0 + 1.
+        // k = kr0 + i lies in thread block tk0 for i < crossT (as its element
+        // o + i), else in tk0 + 1 (element o + i - V).
         const int o = kr0 & (V - 1);  // the same for every thread of the item
         const int crossT = o ? V - o : V;
         const int tk0 = kr0 >> G::LGV;
-        const CarryRec<T> r0 = cr_at(tk0);
+        const int col0 = col_of(tk0), col1 = col_of(tk0 + 1);
+        const int base0 = o * 3 * G::NT + col0, base1 = (o - V) * 3 * G::NT + col1;
+        const Pair e0 = S::cre()[col0];
         R e1m = Elem<T>::lo(), e1n = Elem<T>::hi();
         if (o) {
-            const CarryRec<T> r1 = cr_at(tk0 + 1);
-            e1m = Elem<T>::pmax(r1.e);
-            e1n = Elem<T>::pmin(r1.e);
+            const Pair e1 = S::cre()[col1];
+            e1m = Elem<T>::pmax(e1);
+            e1n = Elem<T>::pmin(e1);
         }
         const int Bj = jr0 >> lgB;
         const int Bk0 = kr0 >> lgB;
@@ -1052,9 +1081,9 @@ struct Consumer {
             const int q2 = ip.s >> lgB;
             R Mam = Elem<T>::lo(), Man = Elem<T>::hi(), Mbm, Mbn;
             if constexpr (MODE == 1) {
-                const CarryRec<T> rb = cr_at(((Bj + 2) << (lgB - G::LGV)) - 1);
-                Mbm = Elem<T>::pmax(rb.g);
-                Mbn = Elem<T>::pmin(rb.g);
+                const Pair gb = S::crg()[col_of(((Bj + 2) << (lgB - G::LGV)) - 1)];
+                Mbm = Elem<T>::pmax(gb);
+                Mbn = Elem<T>::pmin(gb);
             } else {
                 const int s0 = c % 3, s1 = s0 == 2 ? 0 : s0 + 1;
 #pragma unroll
@@ -1104,12 +1133,12 @@ struct Consumer {
             mid1m = __shfl_sync(0xffffffffu, am, (g1 - 1) & 31);
             mid1n = __shfl_sync(0xffffffffu, an, (g1 - 1) & 31);
         }
-        const R c0m = vmax3(fm, mid0m, Elem<T>::pmax(r0.e)), c0n = vmin3(fn, mid0n, Elem<T>::pmin(r0.e));
+        const R c0m = vmax3(fm, mid0m, Elem<T>::pmax(e0)), c0n = vmin3(fn, mid0n, Elem<T>::pmin(e0));
         const R c1m = vmax3(fm, mid1m, e1m), c1n = vmin3(fn, mid1n, e1n);
         R om[V], on[V];
 #pragma unroll
         for (int i = 0; i < V; ++i) {
-            const Pair pr = S::ring()[(i < cpad ? phys : hi_base) + i];
+            const Pair pr = S::ring()[(i < crossT ? base0 : base1) + i * 3 * G::NT];
             const bool far = i >= crossT;
             om[i] = vmax3(sm[i], far ? c1m : c0m, Elem<T>::pmax(pr));
             on[i] = vmin3(sn[i], far ? c1n : c0n, Elem<T>::pmin(pr));
