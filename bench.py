@@ -313,7 +313,8 @@ def blobs_torch(nimg, H, W, seed, dev, nblobs=200):
 
 def filter2d_extras(dev, stream, peak, nimg=64, H=4096, W=4096, reps=3):
     """64 images of 4096 x 4096, uint8 and fp32, five windows; row pass then
-    column pass.  Algorithmic bytes: the image once plus both outputs."""
+    column pass (unfused) and, where the row window allows, the fused kernel.
+    Algorithmic bytes: the image once plus both outputs."""
     import torch
     import paper_cs_0610046_gb300 as mmf
     f = blobs_torch(nimg, H, W, 41, dev)
@@ -328,12 +329,18 @@ def filter2d_extras(dev, stream, peak, nimg=64, H=4096, W=4096, reps=3):
             on = torch.empty((nimg, Ho, Wo), dtype=x.dtype, device=dev)
             ws = torch.empty(2 * nimg * H * ((Wo + 15) // 16 * 16) * sz if wy > 1 and wx > 1 else 16,
                              dtype=torch.uint8, device=dev)
-            mmf.filter2d(x, wy, wx, out_max=om, out_min=on, workspace=ws, stream=stream)
-            ms = _events_ms(lambda: mmf.filter2d(x, wy, wx, out_max=om, out_min=on, workspace=ws,
-                                                 stream=stream), reps, stream)
             byts = (nimg * H * W + 2 * nimg * Ho * Wo) * sz
-            res[f"{name}_{wy}x{wx}"] = {"ms": ms, "Gpix_s": nimg * H * W / ms / 1e6,
-                                        "GBps": byts / ms / 1e6, "frac": byts / ms / 1e6 / peak}
+            row = {}
+            for tag, fuse in (("unfused", 0), ("fused", 1)):
+                if fuse and (wy == 1 or wx == 1 or wx > 17):
+                    continue
+                mmf.filter2d(x, wy, wx, fuse=fuse, out_max=om, out_min=on, workspace=ws, stream=stream)
+                ms = _events_ms(lambda: mmf.filter2d(x, wy, wx, fuse=fuse, out_max=om, out_min=on, workspace=ws,
+                                                     stream=stream), reps, stream)
+                row[tag] = {"ms": ms, "Gpix_s": nimg * H * W / ms / 1e6,
+                            "GBps": byts / ms / 1e6, "frac": byts / ms / 1e6 / peak}
+            best = min(row.values(), key=lambda r: r["ms"])
+            res[f"{name}_{wy}x{wx}"] = {**best, **({k: v for k, v in row.items()} if len(row) > 1 else {})}
             del om, on, ws
     del f, u8
     torch.cuda.empty_cache()

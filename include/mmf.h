@@ -114,11 +114,15 @@ int64_t mmf_output_length(int64_t n, int64_t w_or_r, mmf_mode mode);
  * for y = 0..H-wy, x = 0..W-wx.  Outputs are packed: image k, row y starts at
  * d_max + (k*(H-wy+1) + y)*(W-wx+1).  Both windows >= 1; a window of 1 skips
  * that pass.  The row pass writes its two intermediates to `d_work` (16-byte
- * aligned, size from mmf_filter2d_workspace; none needed when wy or wx is 1).
- * fuse: -1 automatic, 0 row pass then column pass; 1 (a fused kernel) returns
- * MMF_ENOTIMPL.  Column windows are limited by the column pass's shared
- * memory: up to about 760 rows for f32, 320 for f64 and 1700 for i16/u8
- * (MMF_ENOTIMPL beyond). */
+ * aligned, size from mmf_filter2d_workspace; none needed when wy or wx is 1
+ * or when the fused kernel runs).
+ * fuse: 0 row pass then column pass; 1 the fused kernel (the column pass
+ * computes the row maxima and minima of each tile in registers, no
+ * intermediates in memory; wx <= MMF_FUSED_MAX_WX, else MMF_ENOTIMPL);
+ * -1 automatic (currently the two passes).  Column windows are limited by the column
+ * pass's shared memory: up to about 760 rows for f32, 320 for f64 and 1700 for
+ * i16/u8 (MMF_ENOTIMPL beyond). */
+#define MMF_FUSED_MAX_WX 64
 mmf_status mmf_filter2d_workspace(int64_t nimg, int64_t H, int64_t W, int64_t wy, int64_t wx, mmf_dtype dtype,
                                   int fuse, size_t *bytes);
 mmf_status mmf_filter2d_separable(const void *d_in, int64_t nimg, int64_t H, int64_t W, int64_t pitch,

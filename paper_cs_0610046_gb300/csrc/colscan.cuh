@@ -15,7 +15,11 @@
 //            per-thread ring in shared memory) and the tiles between come from
 //            a per-thread ring of tile aggregates.
 // The max side reads `src_max` and the min side `src_min` (the row-pass
-// outputs, or the image itself when the row window is 1).
+// outputs, or the image itself when the row window is 1).  The fused form
+// (FUSED = true) reads the image only: each 8-row tile of row-pass values is
+// computed in registers as the maximum and minimum over wx consecutive image
+// elements of each row (neighbouring threads read overlapping elements, which
+// the L1 cache serves), so no intermediate reaches memory.
 #pragma once
 #include <cstdint>
 
@@ -32,6 +36,7 @@ struct ColParams {
     int64_t in_pitch, in_img;     // element strides (row, image) of the sources
     int64_t out_pitch, out_img;   // element strides of the outputs
     int32_t wy;                   // column window
+    int32_t wx;                   // fused: row window (the sources are the image)
     int32_t strips;               // column strips per image
     int32_t qcap;                 // tile-aggregate ring entries per thread (>= q+2)
     uint32_t *status;
@@ -103,6 +108,49 @@ __device__ __forceinline__ void col_tile(const T *col, int64_t pitch, int64_t y,
     }
 }
 
+// Tile sources: the row-pass intermediates, or the image itself (fused).
+template <typename T, int CPT> struct SepSrc {
+    using R = typename Elem<T>::R;
+    const T *smax, *smin;
+    int64_t pitch, H;
+    __device__ __forceinline__ void tile(int64_t y, R (&vm)[kColRows][CPT], R (&vn)[kColRows][CPT]) const {
+        col_tile<T, CPT>(smax, pitch, y, H, Elem<T>::lo(), vm);
+        col_tile<T, CPT>(smin, pitch, y, H, Elem<T>::hi(), vn);
+    }
+};
+
+template <typename T, int CPT> struct FusedSrc {
+    using R = typename Elem<T>::R;
+    const T *img;  // this thread's first column of the image
+    int64_t pitch, H;
+    int wx;
+    __device__ __forceinline__ void tile(int64_t y, R (&vm)[kColRows][CPT], R (&vn)[kColRows][CPT]) const {
+#pragma unroll
+        for (int r = 0; r < kColRows; ++r) {
+            if (y + r >= 0 && y + r < H) {
+                const T *row = img + (y + r) * pitch;
+                R m[CPT], n[CPT];
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) m[c] = n[c] = Elem<T>::load(__ldg(row + c));
+                // Elements c+1 .. c+wx-1 of column c; element j serves
+                // every column c with c < j <= c + wx - 1.
+#pragma unroll 4
+                for (int j = 1; j < wx + CPT - 1; ++j) {
+                    const R v = Elem<T>::load(__ldg(row + j));
+#pragma unroll
+                    for (int c = 0; c < CPT; ++c)
+                        if (j >= c + 1 && j <= c + wx - 1) { m[c] = vmax(m[c], v); n[c] = vmin(n[c], v); }
+                }
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) { vm[r][c] = m[c]; vn[r][c] = n[c]; }
+            } else {
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) { vm[r][c] = Elem<T>::lo(); vn[r][c] = Elem<T>::hi(); }
+            }
+        }
+    }
+};
+
 template <typename T, int CPT>
 __device__ __forceinline__ void col_store(T *col, int64_t pitch, int64_t y, int64_t Ho,
                                           const typename Elem<T>::R (&v)[kColRows][CPT]) {
@@ -111,18 +159,15 @@ __device__ __forceinline__ void col_store(T *col, int64_t pitch, int64_t y, int6
         if (y + r < Ho) RowVec<T, CPT>::store(col + (y + r) * pitch, v[r]);
 }
 
-template <typename T, int CPT, int W>
-__device__ __forceinline__ void col_slide(const ColParams &P, const T *smax, const T *smin, T *omax, T *omin,
-                                          int64_t Ho) {
+template <typename T, int CPT, int W, typename Src>
+__device__ __forceinline__ void col_slide(const ColParams &P, const Src &src, T *omax, T *omin, int64_t Ho) {
     using R = typename Elem<T>::R;
     constexpr int P2 = W >= 8 ? 8 : (W >= 4 ? 4 : (W >= 2 ? 2 : 1));
     R cm[kColRows][CPT], cn[kColRows][CPT];  // current tile
-    col_tile<T, CPT>(smax, P.in_pitch, 0, P.H, Elem<T>::lo(), cm);
-    col_tile<T, CPT>(smin, P.in_pitch, 0, P.H, Elem<T>::hi(), cn);
+    src.tile(0, cm, cn);
     for (int64_t y = 0; y < Ho; y += kColRows) {
         R nm[kColRows][CPT], nn[kColRows][CPT];  // next tile
-        col_tile<T, CPT>(smax, P.in_pitch, y + kColRows, P.H, Elem<T>::lo(), nm);
-        col_tile<T, CPT>(smin, P.in_pitch, y + kColRows, P.H, Elem<T>::hi(), nn);
+        src.tile(y + kColRows, nm, nn);
         R om[kColRows][CPT], on[kColRows][CPT];
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {
@@ -152,9 +197,8 @@ __device__ __forceinline__ void col_slide(const ColParams &P, const T *smax, con
     }
 }
 
-template <typename T, int CPT>
-__device__ __forceinline__ void col_blocks(const ColParams &P, const T *smax, const T *smin, T *omax, T *omin,
-                                           int64_t Ho) {
+template <typename T, int CPT, typename Src>
+__device__ __forceinline__ void col_blocks(const ColParams &P, const Src &src, T *omax, T *omin, int64_t Ho) {
     using R = typename Elem<T>::R;
     using Pair = typename Elem<T>::Pair;
     const int tid = threadIdx.x;
@@ -184,17 +228,14 @@ __device__ __forceinline__ void col_blocks(const ColParams &P, const T *smax, co
     // Prologue: tiles 1 .. q (P of tile q stays in the ring).
     for (int x = 1; x <= q; ++x) {
         R km[kColRows][CPT], kn[kColRows][CPT];
-        col_tile<T, CPT>(smax, P.in_pitch, (int64_t)x * kColRows, P.H, Elem<T>::lo(), km);
-        col_tile<T, CPT>(smin, P.in_pitch, (int64_t)x * kColRows, P.H, Elem<T>::hi(), kn);
+        src.tile((int64_t)x * kColRows, km, kn);
         k_tile(x, km, kn);
     }
     const int NC = (int)((Ho + kColRows - 1) / kColRows);
     // Prefetched K tile (c+q+1) and J tile (c) of the next iteration.
     R km[kColRows][CPT], kn[kColRows][CPT], jm[kColRows][CPT], jn[kColRows][CPT];
-    col_tile<T, CPT>(smax, P.in_pitch, (int64_t)(q + 1) * kColRows, P.H, Elem<T>::lo(), km);
-    col_tile<T, CPT>(smin, P.in_pitch, (int64_t)(q + 1) * kColRows, P.H, Elem<T>::hi(), kn);
-    col_tile<T, CPT>(smax, P.in_pitch, 0, P.H, Elem<T>::lo(), jm);
-    col_tile<T, CPT>(smin, P.in_pitch, 0, P.H, Elem<T>::hi(), jn);
+    src.tile((int64_t)(q + 1) * kColRows, km, kn);
+    src.tile(0, jm, jn);
     for (int c = 0; c < NC; ++c) {
         R cjm[kColRows][CPT], cjn[kColRows][CPT];
 #pragma unroll
@@ -203,10 +244,8 @@ __device__ __forceinline__ void col_blocks(const ColParams &P, const T *smax, co
             for (int cc = 0; cc < CPT; ++cc) { cjm[r][cc] = jm[r][cc]; cjn[r][cc] = jn[r][cc]; }
         k_tile(c + q + 1, km, kn);
         if (c + 1 < NC) {  // prefetch the next iteration's tiles
-            col_tile<T, CPT>(smax, P.in_pitch, (int64_t)(c + q + 2) * kColRows, P.H, Elem<T>::lo(), km);
-            col_tile<T, CPT>(smin, P.in_pitch, (int64_t)(c + q + 2) * kColRows, P.H, Elem<T>::hi(), kn);
-            col_tile<T, CPT>(smax, P.in_pitch, (int64_t)(c + 1) * kColRows, P.H, Elem<T>::lo(), jm);
-            col_tile<T, CPT>(smin, P.in_pitch, (int64_t)(c + 1) * kColRows, P.H, Elem<T>::hi(), jn);
+            src.tile((int64_t)(c + q + 2) * kColRows, km, kn);
+            src.tile((int64_t)(c + 1) * kColRows, jm, jn);
         }
         R om[kColRows][CPT], on[kColRows][CPT];
 #pragma unroll
@@ -240,28 +279,39 @@ __device__ __forceinline__ void col_blocks(const ColParams &P, const T *smax, co
     }
 }
 
-template <typename T, int CPT>
+template <typename T, int CPT, typename Src>
+__device__ __forceinline__ void col_dispatch(const ColParams &P, const Src &src, T *omax, T *omin, int64_t Ho) {
+    switch (P.wy) {
+        case 1: col_slide<T, CPT, 1>(P, src, omax, omin, Ho); break;
+        case 2: col_slide<T, CPT, 2>(P, src, omax, omin, Ho); break;
+        case 3: col_slide<T, CPT, 3>(P, src, omax, omin, Ho); break;
+        case 4: col_slide<T, CPT, 4>(P, src, omax, omin, Ho); break;
+        case 5: col_slide<T, CPT, 5>(P, src, omax, omin, Ho); break;
+        case 6: col_slide<T, CPT, 6>(P, src, omax, omin, Ho); break;
+        case 7: col_slide<T, CPT, 7>(P, src, omax, omin, Ho); break;
+        case 8: col_slide<T, CPT, 8>(P, src, omax, omin, Ho); break;
+        case 9: col_slide<T, CPT, 9>(P, src, omax, omin, Ho); break;
+        default: col_blocks<T, CPT>(P, src, omax, omin, Ho); break;
+    }
+}
+
+template <typename T, int CPT, bool FUSED>
 __global__ void __launch_bounds__(kColThreads) colscan_kernel(const ColParams P) {
     const int64_t img = blockIdx.x / P.strips;
     const int64_t strip = blockIdx.x % P.strips;
     const int64_t x = strip * (kColThreads * CPT) + (int64_t)threadIdx.x * CPT;
     const int64_t Ho = P.H - P.wy + 1;
     if (x >= P.Wc || Ho <= 0 || img >= P.nimg) return;  // no barriers below
-    const T *smax = reinterpret_cast<const T *>(P.src_max) + img * P.in_img + x;
-    const T *smin = reinterpret_cast<const T *>(P.src_min) + img * P.in_img + x;
     T *omax = P.out_max ? reinterpret_cast<T *>(P.out_max) + img * P.out_img + x : nullptr;
     T *omin = P.out_min ? reinterpret_cast<T *>(P.out_min) + img * P.out_img + x : nullptr;
-    switch (P.wy) {
-        case 1: col_slide<T, CPT, 1>(P, smax, smin, omax, omin, Ho); break;
-        case 2: col_slide<T, CPT, 2>(P, smax, smin, omax, omin, Ho); break;
-        case 3: col_slide<T, CPT, 3>(P, smax, smin, omax, omin, Ho); break;
-        case 4: col_slide<T, CPT, 4>(P, smax, smin, omax, omin, Ho); break;
-        case 5: col_slide<T, CPT, 5>(P, smax, smin, omax, omin, Ho); break;
-        case 6: col_slide<T, CPT, 6>(P, smax, smin, omax, omin, Ho); break;
-        case 7: col_slide<T, CPT, 7>(P, smax, smin, omax, omin, Ho); break;
-        case 8: col_slide<T, CPT, 8>(P, smax, smin, omax, omin, Ho); break;
-        case 9: col_slide<T, CPT, 9>(P, smax, smin, omax, omin, Ho); break;
-        default: col_blocks<T, CPT>(P, smax, smin, omax, omin, Ho); break;
+    if constexpr (FUSED) {
+        const FusedSrc<T, CPT> src{reinterpret_cast<const T *>(P.src_max) + img * P.in_img + x, P.in_pitch, P.H,
+                                   P.wx};
+        col_dispatch<T, CPT>(P, src, omax, omin, Ho);
+    } else {
+        const SepSrc<T, CPT> src{reinterpret_cast<const T *>(P.src_max) + img * P.in_img + x,
+                                 reinterpret_cast<const T *>(P.src_min) + img * P.in_img + x, P.in_pitch, P.H};
+        col_dispatch<T, CPT>(P, src, omax, omin, Ho);
     }
 }
 

@@ -2,7 +2,8 @@
 // on columns), valid windows: out[y][x] = max over rows y..y+wy-1 and columns
 // x..x+wx-1.  Row pass: the 1D block-scan kernel over strided rows.  Column
 // pass: colscan_kernel (one thread per column).  The row-pass intermediates go
-// to a caller-provided workspace.
+// to a caller-provided workspace; the fused form computes them in registers
+// inside the column pass (no workspace).
 #include <cstring>
 
 #include "colscan.cuh"
@@ -21,34 +22,46 @@ template <typename T> static size_t col_smem_bytes(int64_t wy, int cpt = col_cpt
     return ColSmem<T>::bytes(col_qcap<T>(wy), cpt);
 }
 
-template <typename T, int CPT> static cudaError_t col_launch_cpt(const LaunchCtx &ctx, ColParams P) {
+template <typename T, int CPT, bool FUSED> static cudaError_t col_launch_cpt(const LaunchCtx &ctx, ColParams P) {
     P.strips = (int)((P.Wc + kColThreads * CPT - 1) / (kColThreads * CPT));
     P.qcap = col_qcap<T>(P.wy);
     P.status = ctx.status;
     const size_t smem = col_smem_bytes<T>(P.wy, CPT);
     static size_t set[64] = {0};
     if (smem > set[ctx.device]) {
-        cudaError_t e =
-            cudaFuncSetAttribute(colscan_kernel<T, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(colscan_kernel<T, CPT, FUSED>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         set[ctx.device] = smem;
     }
     const int64_t grid = P.nimg * P.strips;
     if (grid <= 0) return cudaSuccess;
-    colscan_kernel<T, CPT><<<(unsigned)grid, kColThreads, smem, ctx.stream>>>(P);
+    colscan_kernel<T, CPT, FUSED><<<(unsigned)grid, kColThreads, smem, ctx.stream>>>(P);
     return cudaGetLastError();
 }
 
-// Paired columns when every row start and the width allow it.
-template <typename T> static cudaError_t col_launch(const LaunchCtx &ctx, const ColParams &P) {
+// Paired columns when every row start and the width allow it (the fused
+// form reads single elements, so only its outputs need pairing).
+template <typename T> static cudaError_t col_launch(const LaunchCtx &ctx, const ColParams &P, bool fused) {
     if constexpr (col_cpt_max<T>() == 2) {
         const uintptr_t a = 2 * sizeof(T) - 1;
-        const bool paired = P.Wc % 2 == 0 && P.in_pitch % 2 == 0 && P.in_img % 2 == 0 && P.out_pitch % 2 == 0 &&
-                            P.out_img % 2 == 0 && ((uintptr_t)P.src_max & a) == 0 && ((uintptr_t)P.src_min & a) == 0 &&
+        const bool out_ok = P.Wc % 2 == 0 && P.out_pitch % 2 == 0 && P.out_img % 2 == 0 &&
                             ((uintptr_t)P.out_max & a) == 0 && ((uintptr_t)P.out_min & a) == 0;
-        if (paired) return col_launch_cpt<T, 2>(ctx, P);
+        const bool in_ok = P.in_pitch % 2 == 0 && P.in_img % 2 == 0 && ((uintptr_t)P.src_max & a) == 0 &&
+                           ((uintptr_t)P.src_min & a) == 0;
+        if (fused && out_ok) return col_launch_cpt<T, 2, true>(ctx, P);
+        if (!fused && out_ok && in_ok) return col_launch_cpt<T, 2, false>(ctx, P);
     }
-    return col_launch_cpt<T, 1>(ctx, P);
+    return fused ? col_launch_cpt<T, 1, true>(ctx, P) : col_launch_cpt<T, 1, false>(ctx, P);
+}
+
+// The fused kernel reads wx image elements per row and thread (scalar loads
+// served by L1); measured slower than the two passes on the 4096 x 4096
+// workload at every window, so the automatic choice is the two passes and the
+// fused form runs when requested (wx <= MMF_FUSED_MAX_WX).
+static bool use_fused(int64_t wy, int64_t wx, int fuse) {
+    if (wy == 1 || wx == 1) return false;  // a single pass already
+    return fuse == 1;
 }
 
 // Row pitch of the intermediates: Wo rounded up to 16 elements, so every
@@ -57,7 +70,7 @@ static int64_t mid_pitch(int64_t Wo) { return (Wo + 15) / 16 * 16; }
 
 template <typename T>
 static mmf_status filter2d(const LaunchCtx &ctx, const T *in, int64_t nimg, int64_t H, int64_t W, int64_t pitch,
-                           int64_t wy, int64_t wx, T *omax, T *omin, void *work) {
+                           int64_t wy, int64_t wx, int fuse, T *omax, T *omin, void *work) {
     const int64_t Ho = H - wy + 1, Wo = W - wx + 1;
     cudaError_t e = cudaSuccess;
     if (wy == 1) {  // rows only, straight into the outputs
@@ -74,7 +87,9 @@ static mmf_status filter2d(const LaunchCtx &ctx, const T *in, int64_t nimg, int6
     P.out_pitch = Wo;
     P.out_img = Ho * Wo;
     P.wy = (int)wy;
-    if (wx == 1) {  // columns only, on the image
+    P.wx = (int)wx;
+    const bool fused = use_fused(wy, wx, fuse);
+    if (wx == 1 || fused) {  // columns only (or fused), on the image
         P.src_max = in;
         P.src_min = in;
         P.in_pitch = pitch;
@@ -93,7 +108,7 @@ static mmf_status filter2d(const LaunchCtx &ctx, const T *in, int64_t nimg, int6
         P.in_pitch = wp;
         P.in_img = H * wp;
     }
-    e = col_launch<T>(ctx, P);
+    e = col_launch<T>(ctx, P, fused);
     return e == cudaSuccess ? MMF_OK : cuda_error(e, "column pass");
 }
 
@@ -102,7 +117,8 @@ static mmf_status check2d(int64_t nimg, int64_t H, int64_t W, int64_t pitch, int
     if (elem_size(dt) == 0) return set_error(MMF_EINVAL, "unknown dtype %d", (int)dt);
     if (nimg < 0 || H < 0 || W < 0 || pitch < W) return set_error(MMF_EINVAL, "bad image geometry");
     if (wy < 1 || wx < 1) return set_error(MMF_EINVAL, "windows must be >= 1");
-    if (fuse == 1) return set_error(MMF_ENOTIMPL, "the fused 2D kernel is not available for this request");
+    if (fuse == 1 && wy > 1 && wx > MMF_FUSED_MAX_WX)
+        return set_error(MMF_ENOTIMPL, "the fused 2D kernel handles row windows up to %d", MMF_FUSED_MAX_WX);
     // Column-pass shared memory: P ring plus the tile-aggregate ring.
     size_t smem = 0;
     switch (dt) {
@@ -127,7 +143,9 @@ mmf_status mmf_filter2d_workspace(int64_t nimg, int64_t H, int64_t W, int64_t wy
     mmf_status st = check2d(nimg, H, W, W, wy, wx, dtype, fuse);
     if (st != MMF_OK) return st;
     const int64_t Wo = W - wx + 1;
-    *bytes = (wy > 1 && wx > 1 && Wo > 0 && H >= wy) ? (size_t)(2 * nimg * H * mid_pitch(Wo) * elem_size(dtype)) : 0;
+    *bytes = (wy > 1 && wx > 1 && Wo > 0 && H >= wy && !use_fused(wy, wx, fuse))
+                 ? (size_t)(2 * nimg * H * mid_pitch(Wo) * elem_size(dtype))
+                 : 0;
     return MMF_OK;
 }
 
@@ -150,10 +168,10 @@ mmf_status mmf_filter2d_separable(const void *d_in, int64_t nimg, int64_t H, int
     st = get_ctx(stream, &ctx);
     if (st != MMF_OK) return st;
     switch (dtype) {
-        case MMF_F32: return filter2d<float>(ctx, (const float *)d_in, nimg, H, W, pitch, wy, wx, (float *)d_max, (float *)d_min, d_work);
-        case MMF_F64: return filter2d<double>(ctx, (const double *)d_in, nimg, H, W, pitch, wy, wx, (double *)d_max, (double *)d_min, d_work);
-        case MMF_I16: return filter2d<int16_t>(ctx, (const int16_t *)d_in, nimg, H, W, pitch, wy, wx, (int16_t *)d_max, (int16_t *)d_min, d_work);
-        case MMF_U8: return filter2d<uint8_t>(ctx, (const uint8_t *)d_in, nimg, H, W, pitch, wy, wx, (uint8_t *)d_max, (uint8_t *)d_min, d_work);
+        case MMF_F32: return filter2d<float>(ctx, (const float *)d_in, nimg, H, W, pitch, wy, wx, fuse, (float *)d_max, (float *)d_min, d_work);
+        case MMF_F64: return filter2d<double>(ctx, (const double *)d_in, nimg, H, W, pitch, wy, wx, fuse, (double *)d_max, (double *)d_min, d_work);
+        case MMF_I16: return filter2d<int16_t>(ctx, (const int16_t *)d_in, nimg, H, W, pitch, wy, wx, fuse, (int16_t *)d_max, (int16_t *)d_min, d_work);
+        case MMF_U8: return filter2d<uint8_t>(ctx, (const uint8_t *)d_in, nimg, H, W, pitch, wy, wx, fuse, (uint8_t *)d_max, (uint8_t *)d_min, d_work);
     }
     return set_error(MMF_EINVAL, "unknown dtype");
 }

@@ -25,14 +25,21 @@ def _expect(img, wy, wx):
     return oracle.bf2d(img, wy, wx)
 
 
+@pytest.mark.parametrize("fuse", [0, 1])
 @pytest.mark.parametrize("dtype", [np.float32, np.uint8, np.float64, np.int16])
 @pytest.mark.parametrize("wy,wx", WINDOWS)
-def test_2d_windows(mmf, dtype, wy, wx):
+def test_2d_windows(mmf, dtype, wy, wx, fuse):
+    """Unfused (row pass to a workspace, then columns) and fused (row maxima
+    computed inside the column pass) against the literal rectangle."""
     imgs = synth.blobs2d(2, 300, 262, seed=wy * 7 + wx, dtype=dtype, nblobs=20)
     if dtype == np.int16:
         imgs = (imgs.astype(np.int32) - 16000).astype(np.int16)
     x = torch.from_numpy(imgs).cuda()
-    mx, mn = mmf.filter2d(x, wy, wx)
+    if fuse == 1 and wx > 64 and wy > 1:
+        with pytest.raises(mmf.MMFError):
+            mmf.filter2d(x, wy, wx, fuse=1)
+        return
+    mx, mn = mmf.filter2d(x, wy, wx, fuse=fuse)
     torch.cuda.synchronize()
     for k in range(imgs.shape[0]):
         em, en = _expect(imgs[k], wy, wx)
@@ -45,11 +52,26 @@ def test_2d_pitched_rows_and_ragged(mmf):
     full = synth.blobs2d(3, 131, 517, seed=3, dtype=np.float32, nblobs=9)
     base = torch.from_numpy(full).cuda()
     x = base[:, :, :501]  # pitch 517, width 501
-    for wy, wx in ((5, 6), (40, 1), (1, 40), (33, 71)):
-        mx, mn = mmf.filter2d(x, wy, wx)
+    for wy, wx, fuse in ((5, 6, 0), (5, 6, 1), (40, 1, -1), (1, 40, -1), (33, 71, 0), (33, 17, 1), (12, 3, 1)):
+        mx, mn = mmf.filter2d(x, wy, wx, fuse=fuse)
         torch.cuda.synchronize()
         for k in range(3):
             em, en = _expect(full[k, :, :501], wy, wx)
+            assert np.array_equal(mx[k].cpu().numpy(), em) and np.array_equal(mn[k].cpu().numpy(), en)
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.int16])
+def test_2d_fused_odd_width_unpaired(mmf, dtype):
+    """Odd output widths and offset views take the one-column-per-thread
+    forms of the fused kernel."""
+    full = synth.blobs2d(2, 77, 300, seed=8, dtype=dtype, nblobs=5)
+    base = torch.from_numpy(full).cuda()
+    for off, wx in ((0, 4), (1, 3), (3, 8)):
+        x = base[:, :, off:off + 251]
+        mx, mn = mmf.filter2d(x, 6, wx, fuse=1)
+        torch.cuda.synchronize()
+        for k in range(2):
+            em, en = _expect(full[k, :, off:off + 251], 6, wx)
             assert np.array_equal(mx[k].cpu().numpy(), em) and np.array_equal(mn[k].cpu().numpy(), en)
 
 
@@ -61,10 +83,17 @@ def test_2d_window_larger_than_image(mmf):
     assert torch.equal(mx.reshape(-1), x.amax(dim=(1, 2))) and torch.equal(mn.reshape(-1), x.amin(dim=(1, 2)))
 
 
-def test_2d_fused_request_is_refused(mmf):
-    x = torch.rand(1, 64, 64, device="cuda")
+def test_2d_fused_limits(mmf):
+    """A forced fused request beyond the fused kernel's row window is refused;
+    within it no workspace is needed."""
+    x = torch.rand(1, 128, 128, device="cuda")
     with pytest.raises(mmf.MMFError):
-        mmf.filter2d(x, 3, 3, fuse=1)
+        mmf.filter2d(x, 3, 65, fuse=1)
+    lib = mmf.load()
+    import ctypes
+    need = ctypes.c_size_t(1)
+    assert lib.mmf_filter2d_workspace(1, 128, 128, 3, 3, 0, 1, ctypes.byref(need)) == 0 and need.value == 0
+    assert lib.mmf_filter2d_workspace(1, 128, 128, 3, 3, 0, 0, ctypes.byref(need)) == 0 and need.value > 0
 
 
 def test_2d_full_size_sampled(mmf):
@@ -73,8 +102,8 @@ def test_2d_full_size_sampled(mmf):
     img = synth.blobs2d(1, 4096, 4096, seed=41, dtype=np.uint8, nblobs=200)
     x = torch.from_numpy(img).cuda()
     rng = np.random.default_rng(4)
-    for wy, wx in ((3, 3), (15, 15), (63, 63), (255, 1), (1, 255)):
-        mx, mn = mmf.filter2d(x, wy, wx)
+    for wy, wx, fuse in ((3, 3, 0), (3, 3, 1), (15, 15, 0), (15, 15, 1), (63, 63, -1), (255, 1, -1), (1, 255, -1)):
+        mx, mn = mmf.filter2d(x, wy, wx, fuse=fuse)
         torch.cuda.synchronize()
         ys = rng.integers(0, 4096 - wy + 1, 2000)
         xs = rng.integers(0, 4096 - wx + 1, 2000)
