@@ -410,6 +410,27 @@ def serving_extras(dev, nstreams=10_000, seed=51, duration=0.5,
                          "p99_ms": head["p99_ms"], "note": "load nearest to half of saturation"}}
 
 
+def run_only(args):
+    """One extra measurement on its own (the commands of the profiles/ summaries)."""
+    import torch
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    from paper_cs_0610046_gb300 import build
+    build.build()
+    stream = torch.cuda.current_stream()
+    peak = _peaks()[0]
+    if args.only == "wedge":
+        r = wedge_extras(dev, stream, peak, n=(1 << 26) if args.small else (1 << 30))
+    elif args.only == "batched":
+        r = batched_extras(dev, stream, peak, envelope_series=100_000 if args.small else 1_000_000)
+    elif args.only == "filter2d":
+        r = filter2d_extras(dev, stream, peak, nimg=4 if args.small else 64)
+    else:
+        r = serving_extras(dev, duration=0.2 if args.small else 0.5)
+    print(json.dumps({args.only: r}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -423,10 +444,16 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched/2D/serving measurements")
+    ap.add_argument("--only", choices=["wedge", "batched", "filter2d", "serving"],
+                    help="run one extra measurement alone and print its JSON (profiling)")
+    ap.add_argument("--small", action="store_true",
+                    help="with --only: a smaller instance of that workload (profiling captures)")
     args = ap.parse_args()
 
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        return run_only(args)
 
     import torch
     import torch.distributed as dist

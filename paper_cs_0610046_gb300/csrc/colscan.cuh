@@ -13,7 +13,11 @@
 //            P(k)), where S is the suffix max inside tile c (the J tile, read
 //            again from memory), P the prefix max inside k's tile (a 2-slot
 //            per-thread ring in shared memory) and the tiles between come from
-//            a per-thread ring of tile aggregates.
+//            a per-thread ring of tile aggregates.  That range slides by one
+//            tile per step; it is kept as a two-stack queue inside the ring:
+//            the older part holds suffix maxima (rebuilt in place when it runs
+//            empty), the newer part raw aggregates with a running max, so each
+//            step costs O(1) amortised whatever wy.
 // The max side reads `src_max` and the min side `src_min` (the row-pass
 // outputs, or the image itself when the row window is 1).  The fused form
 // (FUSED = true) reads the image only: each 8-row tile of row-pass values is
@@ -236,7 +240,45 @@ __device__ __forceinline__ void col_blocks(const ColParams &P, const Src &src, T
     R km[kColRows][CPT], kn[kColRows][CPT], jm[kColRows][CPT], jn[kColRows][CPT];
     src.tile((int64_t)(q + 1) * kColRows, km, kn);
     src.tile(0, jm, jn);
+    // Two-stack queue over tile aggregates for the range [c+1, c+q-1] (empty
+    // when q < 2): ring slots [fs, fe) hold suffix maxima up to fe-1, slots
+    // [fe, be) raw aggregates whose running max is (bm, bn).
+    int fs = 1, fe = 1, be = 1;
+    R bm[CPT], bn[CPT];
+#pragma unroll
+    for (int cc = 0; cc < CPT; ++cc) { bm[cc] = Elem<T>::lo(); bn[cc] = Elem<T>::hi(); }
+    auto push = [&](int x) {  // tile x joins the newer part
+#pragma unroll
+        for (int cc = 0; cc < CPT; ++cc) {
+            const Pair a = TA(x, cc);
+            bm[cc] = vmax(bm[cc], Elem<T>::pmax(a));
+            bn[cc] = vmin(bn[cc], Elem<T>::pmin(a));
+        }
+        be = x + 1;
+    };
+    if (q >= 2)
+        for (int x = 1; x <= q - 1; ++x) push(x);
     for (int c = 0; c < NC; ++c) {
+        if (c > 0 && q >= 2) {
+            ++fs;             // tile c leaves the range
+            push(c + q - 1);  // tile c+q-1 joins it
+            if (fs >= fe) {
+                // Older part empty: the newer part becomes suffix maxima in place.
+#pragma unroll
+                for (int cc = 0; cc < CPT; ++cc) {
+                    R m = Elem<T>::lo(), n = Elem<T>::hi();
+                    for (int x = be - 1; x >= fs; --x) {
+                        Pair &a = TA(x, cc);
+                        m = vmax(m, Elem<T>::pmax(a));
+                        n = vmin(n, Elem<T>::pmin(a));
+                        a = Elem<T>::pair(m, n);
+                    }
+                    bm[cc] = Elem<T>::lo();
+                    bn[cc] = Elem<T>::hi();
+                }
+                fe = be;
+            }
+        }
         R cjm[kColRows][CPT], cjn[kColRows][CPT];
 #pragma unroll
         for (int r = 0; r < kColRows; ++r)
@@ -257,11 +299,11 @@ __device__ __forceinline__ void col_blocks(const ColParams &P, const Src &src, T
                 cjn[r][cc] = vmin(cjn[r + 1][cc], cjn[r][cc]);
             }
             // tiles strictly between: c+1 .. c+q-1 (near), .. c+q (far)
-            R m1 = Elem<T>::lo(), n1 = Elem<T>::hi();
-            for (int x = c + 1; x <= c + q - 1; ++x) {
-                const Pair a = TA(x, cc);
-                m1 = vmax(m1, Elem<T>::pmax(a));
-                n1 = vmin(n1, Elem<T>::pmin(a));
+            R m1 = bm[cc], n1 = bn[cc];
+            if (fs < fe) {
+                const Pair f = TA(fs, cc);
+                m1 = vmax(m1, Elem<T>::pmax(f));
+                n1 = vmin(n1, Elem<T>::pmin(f));
             }
             const Pair lastp = TA(c + q, cc);
             const R m2 = vmax(m1, Elem<T>::pmax(lastp)), n2 = vmin(n1, Elem<T>::pmin(lastp));
