@@ -263,7 +263,8 @@ template <typename T> struct Geo {
     static constexpr size_t off_misc = 0;
     static constexpr size_t off_kagg = 0;  // [3 ring slots][NW warps] block aggregates of K tiles
     static constexpr size_t off_jagg = off_kagg + 3 * NW * sizeof(Pair);  // [2][NW] of J tiles
-    static constexpr size_t off_bar = rnd(off_jagg + 2 * NW * sizeof(Pair));  // [warp][stage]
+    static constexpr size_t off_tb = off_jagg + 2 * NW * sizeof(Pair);  // [2] whole tiles between (case B)
+    static constexpr size_t off_bar = rnd(off_tb + 2 * sizeof(Pair));  // [warp][stage]
     static constexpr size_t off_issue = off_bar + NW * kStages * 8;
     static constexpr size_t off_queue = rnd(off_issue + NW * sizeof(WarpIssue));
     static constexpr size_t off_params = rnd(off_queue + kQueue * 8 + 16);
@@ -297,6 +298,7 @@ template <typename T> struct Smem {
     __device__ static uint8_t *misc() { return bs_smem + G::off_misc; }
     __device__ static Pair *kagg() { return reinterpret_cast<Pair *>(misc() + G::off_kagg); }
     __device__ static Pair *jagg() { return reinterpret_cast<Pair *>(misc() + G::off_jagg); }
+    __device__ static Pair *tb() { return reinterpret_cast<Pair *>(misc() + G::off_tb); }
     __device__ static uint64_t *bar(int warp, int s) {
         return reinterpret_cast<uint64_t *>(misc() + G::off_bar) + warp * kStages + s;
     }
@@ -578,6 +580,52 @@ __device__ __forceinline__ void issue_next(int warp) {
     wi.l++;
     wi.issued++;
 }
+
+// Sliding maximum/minimum of the tile aggregates of tiles [c+1, c+q-1] (case
+// B), kept by warp 0 as a two-stack queue inside the tile-aggregate ring:
+// slots [fs, fe) hold suffix maxima up to fe-1, slots [fe, be) raw aggregates
+// whose running max is (bm, bn).  Each step costs O(1) amortised.  Every
+// lane of warp 0 runs it; lanes write identical values.
+template <typename T> struct TileQueue {
+    using R = typename Elem<T>::R;
+    using Pair = typename Elem<T>::Pair;
+    int fs = 1, fe = 1, be = 1;
+    R bm = Elem<T>::lo(), bn = Elem<T>::hi();
+    __device__ static Pair &ta(int x) { return Smem<T>::ta()[x % kQCap]; }
+    __device__ void push(int x) {
+        const Pair a = ta(x);
+        bm = vmax(bm, Elem<T>::pmax(a));
+        bn = vmin(bn, Elem<T>::pmin(a));
+        be = x + 1;
+    }
+    // Drop the oldest tile, add tile x; rebuild the older part (in place, as
+    // suffix maxima of what the newer part holds) when it runs empty.
+    __device__ void slide(int x) {
+        ++fs;
+        push(x);
+        if (fs >= fe) {
+            R m = Elem<T>::lo(), n = Elem<T>::hi();
+            for (int x = be - 1; x >= fs; --x) {
+                Pair &a = ta(x);
+                m = vmax(m, Elem<T>::pmax(a));
+                n = vmin(n, Elem<T>::pmin(a));
+                a = Elem<T>::pair(m, n);
+            }
+            bm = Elem<T>::lo();
+            bn = Elem<T>::hi();
+            fe = be;
+        }
+    }
+    __device__ Pair query() const {
+        R m = bm, n = bn;
+        if (fs < fe) {
+            const Pair f = ta(fs);
+            m = vmax(m, Elem<T>::pmax(f));
+            n = vmin(n, Elem<T>::pmin(f));
+        }
+        return Elem<T>::pair(m, n);
+    }
+};
 
 // ------------------------------------------------------------ consumer side
 // Block modes of an item (s = w-1, warp span W = 32V):
@@ -1106,32 +1154,45 @@ struct Consumer {
             mid1m = a1 ? Mam : Mbm;
             mid1n = a1 ? Man : Mbn;
         } else {
-            // Case B lane array of warp-block aggregates in window order: lanes
-            // 0..NW-1 = J tile c, then K tiles c+q and c+q+1; prefix from the
-            // block after j's (lane warp+1); the whole tiles c+1..c+q-1 join
-            // every lane from NW-1 on.
+            // Case B: the warp blocks Bj+1 .. Bj+q2-1 are the rest of tile c
+            // (J-tile block aggregates), the whole tiles c+1 .. c+q-1 (one
+            // value per output tile, kept by warp 0), and the first warp
+            // blocks of K tile c+q (or all of it and the first of c+q+1).
+            // Mb adds block Bj+q2.  All of it is the same for the warp.
             const int q = ip.q;
-            const Pair a = lane < NW ? S::jagg()[(c & 1) * NW + lane]
-                                     : (lane < 2 * NW ? S::kagg()[((c + q) % 3) * NW + lane - NW]
-                                                      : (lane < 3 * NW ? S::kagg()[((c + q + 1) % 3) * NW + lane - 2 * NW]
-                                                                       : Elem<T>::pair(Elem<T>::lo(), Elem<T>::hi())));
-            R am = lane > warp ? Elem<T>::pmax(a) : Elem<T>::lo();
-            R an = lane > warp ? Elem<T>::pmin(a) : Elem<T>::hi();
+            const int q2 = ip.s >> lgB;
+            const Pair tbv = S::tb()[c & 1];
+            R Mam = Elem<T>::pmax(tbv), Man = Elem<T>::pmin(tbv), Mbm, Mbn;
 #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const R um = __shfl_up_sync(0xffffffffu, am, d);
-                const R un = __shfl_up_sync(0xffffffffu, an, d);
-                if (lane >= d) { am = vmax(am, um); an = vmin(an, un); }
+            for (int w = 1; w < NW; ++w) {
+                if (warp + w < NW) {
+                    const Pair a = S::jagg()[(c & 1) * NW + warp + w];
+                    Mam = vmax(Mam, Elem<T>::pmax(a));
+                    Man = vmin(Man, Elem<T>::pmin(a));
+                }
             }
-            R tm, tn;
-            tiles_between(c, q, tm, tn);
-            if (lane >= NW - 1) { am = vmax(am, tm); an = vmin(an, tn); }
-            const int base = (c + q) * NW - NW;
-            const int g0 = Bk0 - base, g1 = Bk1 - base;
-            mid0m = __shfl_sync(0xffffffffu, am, g0 - 1);
-            mid0n = __shfl_sync(0xffffffffu, an, g0 - 1);
-            mid1m = __shfl_sync(0xffffffffu, am, (g1 - 1) & 31);
-            mid1n = __shfl_sync(0xffffffffu, an, (g1 - 1) & 31);
+            // Last block of the range, in warp blocks from the start of tile c+q.
+            const int last = warp + (q2 - q * NW) - 1;  // in [-1, 2NW-2]
+            const int s0 = (c + q) % 3, s1 = (c + q + 1) % 3;
+#pragma unroll
+            for (int g = 0; g < 2 * NW - 1; ++g) {
+                if (g <= last) {
+                    const Pair a = S::kagg()[(g < NW ? s0 : s1) * NW + (g & (NW - 1))];
+                    Mam = vmax(Mam, Elem<T>::pmax(a));
+                    Man = vmin(Man, Elem<T>::pmin(a));
+                }
+            }
+            {
+                const int g = last + 1;  // block Bj+q2
+                const Pair a = S::kagg()[(g < NW ? s0 : s1) * NW + (g & (NW - 1))];
+                Mbm = vmax(Mam, Elem<T>::pmax(a));
+                Mbn = vmin(Man, Elem<T>::pmin(a));
+            }
+            const bool a0 = Bk0 == Bj + q2, a1 = Bk1 == Bj + q2;
+            mid0m = a0 ? Mam : Mbm;
+            mid0n = a0 ? Man : Mbn;
+            mid1m = a1 ? Mam : Mbm;
+            mid1n = a1 ? Man : Mbn;
         }
         const R c0m = vmax3(fm, mid0m, Elem<T>::pmax(e0)), c0n = vmin3(fn, mid0n, Elem<T>::pmin(e0));
         const R c1m = vmax3(fm, mid1m, e1m), c1n = vmin3(fn, mid1n, e1n);
@@ -1247,6 +1308,12 @@ struct Consumer {
                 sync();
                 publish_tile_aggregate(x);
             }
+            TileQueue<T> tq;  // warp 0: tiles [c+1, c+q-1]
+            if (warp == 0) {
+                for (int x = 1; x <= q - 1; ++x) tq.push(x);
+                const Pair v = tq.query();
+                if (lane == 0) S::tb()[0] = v;
+            }
             sync();
             for (int c = 0; c < ip.NC; ++c) {
                 const int xk = c + q + 1;
@@ -1268,6 +1335,13 @@ struct Consumer {
                 if (lane == 0) S::jagg()[(c & 1) * NW + warp] = Elem<T>::pair(hm, hn);
                 sync();
                 if (kload) publish_tile_aggregate(xk);
+                if (warp == 0 && c + 1 < ip.NC) {
+                    // The range of output tile c+1: drop tile c+1, add tile c+q
+                    // (published in the previous step).
+                    if (q >= 2) tq.slide(c + q);
+                    const Pair v = tq.query();
+                    if (lane == 0) S::tb()[(c + 1) & 1] = v;
+                }
                 outputs12<MODE>(ip, c, js.sm, js.sn, js.fm, js.fn, vec);
             }
         }

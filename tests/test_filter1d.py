@@ -204,3 +204,14 @@ def test_full_size_long_stream_sampled(mmf, w):
     del x, mx, mn
     torch.cuda.empty_cache()
     assert mmf.device_status(reset=True) == 0
+
+
+@pytest.mark.parametrize("w", [2049, 4097, 4200, 6145, 8193])
+def test_long_items_large_windows(mmf, w):
+    """Windows of 1-4 whole tiles with items of many tiles (few CTAs per
+    series): the sliding range of whole tiles between j and k advances
+    across many output tiles of one item."""
+    a = synth.random_walk(8_000_000, seed=w, dtype=np.float32)
+    _check(mmf, a, w)
+    b = synth.piecewise_monotone(700_001, seed=w, dtype=np.float32)
+    _check(mmf, b, w)
