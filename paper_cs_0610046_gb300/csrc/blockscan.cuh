@@ -244,8 +244,9 @@ template <typename T> struct Geo {
     static constexpr int LGT = LGV + LGNT;
     static constexpr int SLICE = 32 * V;  // elements of a tile read by one warp
     static constexpr int NCH = V * (int)sizeof(T) / 16;  // 16-byte chunks per thread
-    // Register-slide halo (elements after the slice; windows up to HALO_MAX+1).
-    static constexpr int HALO_MAX = 8 > 16 / (int)sizeof(T) ? 8 : 16 / (int)sizeof(T);
+    // Register-slide halo (elements after the slice; windows up to HALO_MAX+1):
+    // one more thread's elements for the 16-element types, 8 for f64.
+    static constexpr int HALO_MAX = V == 16 ? 16 : 8;
     // A warp's slice arrives in PIECES copies of PLANES lanes' elements each,
     // placed PSTRIDE bytes apart; each piece holds room for the
     // register-slide halo and a 16-byte shift.  One piece: the bank spread of
@@ -378,7 +379,7 @@ __device__ __forceinline__ ItemPlan<T> make_plan(const BlockScanParams &P, int64
     const int64_t span = oe - ob;
     ip.NC = span > 0 ? (int)((span + G::T_ - 1) >> G::LGT) : 0;
     ip.klast = span > 0 ? (int)((((span - 1) + s) >> G::LGT) >= ip.NC + ip.q) : 0;
-    if (want_mode == 3 && s <= 8) ip.mode = 3;  // register slide: w <= 9
+    if (want_mode == 3 && s <= G::HALO_MAX) ip.mode = 3;  // register slide: w <= HALO_MAX + 1
     ip.ok = (s >= 0) && (ip.q + 2 <= kQCap) && span >= 0 && span + s + 2 * (int64_t)G::T_ <= kMaxItemSpan &&
             (want_mode < 0 || want_mode == ip.mode);
     return ip;
@@ -1364,10 +1365,38 @@ struct Consumer {
             constexpr int NW = NE * (int)sizeof(T) / 4;
             uint32_t wd[NW];
             const uint4 *p4 = reinterpret_cast<const uint4 *>(S::lane_base(sb, lane));
+            if constexpr ((G::NCH == 2 || G::NCH == 4) && (NW / 4) % G::NCH == 0) {
+                // Group g of NCH words is lane+g's own elements, read with
+                // lane+g's rotation (see read_tile): no bank conflicts.
+                constexpr int NC = G::NCH;
 #pragma unroll
-            for (int c = 0; c < NW / 4; ++c) {
-                uint4 v = p4[c];
-                wd[4 * c] = v.x; wd[4 * c + 1] = v.y; wd[4 * c + 2] = v.z; wd[4 * c + 3] = v.w;
+                for (int g = 0; g < NW / 4 / NC; ++g) {
+                    const int rot = ((lane + g) / (8 / NC)) & (NC - 1);
+                    uint4 u[NC];
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) u[c] = p4[g * NC + ((c + rot) & (NC - 1))];
+#pragma unroll
+                    for (int b = 1; b < NC; b <<= 1) {
+                        if (rot & b) {
+                            uint4 t[NC];
+#pragma unroll
+                            for (int c = 0; c < NC; ++c) t[c] = u[(c - b + NC) & (NC - 1)];
+#pragma unroll
+                            for (int c = 0; c < NC; ++c) u[c] = t[c];
+                        }
+                    }
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        const int k = g * NC + c;
+                        wd[4 * k] = u[c].x; wd[4 * k + 1] = u[c].y; wd[4 * k + 2] = u[c].z; wd[4 * k + 3] = u[c].w;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < NW / 4; ++c) {
+                    uint4 v = p4[c];
+                    wd[4 * c] = v.x; wd[4 * c + 1] = v.y; wd[4 * c + 2] = v.z; wd[4 * c + 3] = v.w;
+                }
             }
             R xv[NE];
             ExtractLoop<T, 0, 0, NE>::run(wd, xv);
@@ -1403,7 +1432,7 @@ struct Consumer {
     template <int W>
     __device__ __forceinline__ void run_slide(const ItemPlan<T> &ip) {
         constexpr int NE = V + G::HALO_MAX;
-        constexpr int P2 = W >= 8 ? 8 : (W >= 4 ? 4 : (W >= 2 ? 2 : 1));
+        constexpr int P2 = W >= 16 ? 16 : (W >= 8 ? 8 : (W >= 4 ? 4 : (W >= 2 ? 2 : 1)));
         for (int c = 0; c < ip.NC; ++c) {
             R am[NE], an[NE];
             if (!read_tile_ext(ip, c, am, an)) return;
@@ -1437,7 +1466,21 @@ struct Consumer {
             case 5: run_slide<6>(ip); break;
             case 6: run_slide<7>(ip); break;
             case 7: run_slide<8>(ip); break;
-            default: run_slide<9>(ip); break;
+            case 8: run_slide<9>(ip); break;
+            default:
+                if constexpr (G::HALO_MAX >= 16) {
+                    switch (ip.s) {
+                        case 9: run_slide<10>(ip); break;
+                        case 10: run_slide<11>(ip); break;
+                        case 11: run_slide<12>(ip); break;
+                        case 12: run_slide<13>(ip); break;
+                        case 13: run_slide<14>(ip); break;
+                        case 14: run_slide<15>(ip); break;
+                        case 15: run_slide<16>(ip); break;
+                        default: run_slide<17>(ip); break;
+                    }
+                }
+                break;
         }
     }
 

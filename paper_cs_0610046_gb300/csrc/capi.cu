@@ -151,8 +151,10 @@ mmf_status mmf_filter1d_ex(const void *d_in, int64_t n, int64_t w_or_r, mmf_dtyp
     LaunchCtx ctx;
     st = get_ctx(stream, &ctx);
     if (st != MMF_OK) return st;
-    if (kernel == MMF_KERNEL_SLIDE && sd.w > 9)
-        return set_error(MMF_EINVAL, "the register slide handles windows up to 9 (w = %lld)", (long long)sd.w);
+    const int slide_max = dtype == MMF_F64 ? 9 : 17;
+    if (kernel == MMF_KERNEL_SLIDE && sd.w > slide_max)
+        return set_error(MMF_EINVAL, "the register slide handles windows up to %d (w = %lld)", slide_max,
+                         (long long)sd.w);
     if (kernel == MMF_KERNEL_WEDGE) {
         if (mode != MMF_VALID) return set_error(MMF_ENOTIMPL, "the wedge kernel computes valid windows only");
         if (sd.w > MMF_WEDGE_MAX_WINDOW)

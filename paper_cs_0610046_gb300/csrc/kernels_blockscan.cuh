@@ -31,11 +31,12 @@ template <typename T, int MODE> static cudaError_t prepare_blockscan(int device,
     return cudaSuccess;
 }
 
-// Kernel mode for window w: 3 = register slide (w <= 9, unless a block scan
-// is forced), else the block-scan mode 0, 1 or 2.
+// Kernel mode for window w: 3 = register slide (w <= 17 for the 16-element
+// types, 9 for f64, unless a block scan is forced), else the block-scan mode
+// 0, 1 or 2.
 template <typename T> int block_mode(int64_t w, bool allow_slide) {
     const int64_t s = w - 1;
-    if (allow_slide && s <= 8) return 3;
+    if (allow_slide && s <= Geo<T>::HALO_MAX) return 3;
     if (s >= 32 * (int64_t)Geo<T>::V) return 2;
     return s >= Geo<T>::V ? 1 : 0;
 }

@@ -16,7 +16,8 @@ struct LaunchCtx {
 };
 
 // One series, statically split into per-CTA items (no allocation).  With
-// allow_slide, windows w <= 9 use the register slide instead of block scans.
+// allow_slide, small windows (w <= 17; 9 for f64) use the register slide
+// instead of block scans.
 template <typename T>
 cudaError_t blockscan_1d(const LaunchCtx &ctx, const void *in, const SeriesDesc &sd, void *omax, void *omin,
                          bool allow_slide);
@@ -40,7 +41,8 @@ cudaError_t blockscan_table(const LaunchCtx &ctx, int mode, const void *in, void
 template <typename T>
 cudaError_t wedge_1d(const LaunchCtx &ctx, const void *in, int64_t n, int64_t w, void *omax, void *omin);
 
-// Kernel mode for window w: 3 = register slide (if allowed and w <= 9), else
+// Kernel mode for window w: 3 = register slide (if allowed and w <= 17; 9 for
+// f64), else
 // the block-scan mode 0, 1 or 2.
 template <typename T> int block_mode(int64_t w, bool allow_slide);
 
