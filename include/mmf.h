@@ -232,6 +232,21 @@ mmf_status mmf_stream_push(mmf_server *server, uint64_t stream_id, const void *h
  * stays valid).  A completed ticket is consumed. */
 mmf_status mmf_ticket_wait(mmf_server *server, uint64_t ticket, int timeout_ms);
 
+/* Many pushes under one lock, in order: the same as calling mmf_stream_push
+ * for i = 0..count-1 with stream_ids[i], h_chunks[i], lens[i], h_max[i] and
+ * h_min[i] (h_max or h_min may be NULL arrays: no such outputs), writing
+ * n_out[i] (may be NULL) and tickets[i].  Stops at the first failing push and
+ * returns its status; *n_done (may be NULL) receives the number queued.  For
+ * feed handlers that receive many streams' chunks at once. */
+mmf_status mmf_stream_push_batch(mmf_server *server, int64_t count, const uint64_t *stream_ids,
+                                 const void *const *h_chunks, const int64_t *lens, void *const *h_max,
+                                 void *const *h_min, int64_t *n_out, uint64_t *tickets, int64_t *n_done);
+
+/* Waits for every ticket of the array (consuming each), up to timeout_ms in
+ * total.  MMF_ETIMEOUT leaves the tickets not yet reached valid; MMF_EDEVICE
+ * if a batch of any of them failed. */
+mmf_status mmf_ticket_wait_batch(mmf_server *server, int64_t count, const uint64_t *tickets, int timeout_ms);
+
 /* Refuses further pushes, waits up to timeout_ms for the stream's chunks,
  * frees its state (MMF_ETIMEOUT leaves it closed but not yet freed). */
 mmf_status mmf_stream_close(mmf_server *server, uint64_t stream_id, int timeout_ms);

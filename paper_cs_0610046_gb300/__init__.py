@@ -92,6 +92,8 @@ _EXTRA_SIGNATURES: dict = {
     "mmf_stream_open": ([_VP, _I64, ctypes.POINTER(ctypes.c_uint64)], _INT),
     "mmf_stream_push": ([_VP, ctypes.c_uint64, _VP, _I64, _VP, _VP, _P64, ctypes.POINTER(ctypes.c_uint64)], _INT),
     "mmf_ticket_wait": ([_VP, ctypes.c_uint64, _INT], _INT),
+    "mmf_stream_push_batch": ([_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _P64], _INT),
+    "mmf_ticket_wait_batch": ([_VP, _I64, _VP, _INT], _INT),
     "mmf_stream_close": ([_VP, ctypes.c_uint64, _INT], _INT),
     "mmf_server_pause": ([_VP, _INT], _INT),
     "mmf_filter2d_workspace": ([_I64, _I64, _I64, _I64, _I64, _INT, _INT, ctypes.POINTER(ctypes.c_size_t)], _INT),
@@ -334,6 +336,36 @@ class Server:
     def wait(self, ticket: int, timeout_ms: int = 60_000) -> None:
         check(self._lib.mmf_ticket_wait(self._h, ticket, timeout_ms))
         self._keep.pop(ticket, None)
+
+    def push_batch(self, sids, chunk_ptrs, lens, max_ptrs=None, min_ptrs=None):
+        """Queue many chunks in one call (``mmf_stream_push_batch``).  All
+        arguments are equal-length numpy arrays: stream ids (uint64), host
+        addresses of the chunks and of their outputs (uint64, e.g.
+        ``arr.ctypes.data`` plus byte offsets) and lengths (int64).  The
+        caller keeps the memory alive until the tickets are waited for.
+        Returns ``(tickets, n_out)`` as numpy arrays."""
+        import numpy as np
+        sids = np.ascontiguousarray(sids, dtype=np.uint64)
+        chunk_ptrs = np.ascontiguousarray(chunk_ptrs, dtype=np.uint64)
+        lens = np.ascontiguousarray(lens, dtype=np.int64)
+        k = sids.size
+        tickets = np.empty(k, dtype=np.uint64)
+        n_out = np.empty(k, dtype=np.int64)
+        done = ctypes.c_int64(0)
+        p = lambda a: None if a is None else ctypes.c_void_p(np.ascontiguousarray(a, dtype=np.uint64).ctypes.data)
+        mp, np_ = (None if max_ptrs is None else np.ascontiguousarray(max_ptrs, dtype=np.uint64),
+                   None if min_ptrs is None else np.ascontiguousarray(min_ptrs, dtype=np.uint64))
+        check(self._lib.mmf_stream_push_batch(self._h, k, p(sids), p(chunk_ptrs), ctypes.c_void_p(lens.ctypes.data),
+                                              p(mp), p(np_), ctypes.c_void_p(n_out.ctypes.data),
+                                              ctypes.c_void_p(tickets.ctypes.data), ctypes.byref(done)))
+        return tickets, n_out
+
+    def wait_batch(self, tickets, timeout_ms: int = 60_000) -> None:
+        import numpy as np
+        t = np.ascontiguousarray(tickets, dtype=np.uint64)
+        check(self._lib.mmf_ticket_wait_batch(self._h, t.size, ctypes.c_void_p(t.ctypes.data), timeout_ms))
+        for x in t.tolist():
+            self._keep.pop(int(x), None)
 
     def close_stream(self, sid: int, timeout_ms: int = 60_000) -> None:
         check(self._lib.mmf_stream_close(self._h, sid, timeout_ms))

@@ -24,6 +24,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <list>
 #include <map>
 #include <mutex>
 #include <thread>
@@ -161,6 +162,7 @@ struct StreamState {
     bool in_flight = false;
     bool closed = false;
     int64_t pending = 0;    // queued or in flight
+    int64_t queued = 0;     // samples of this stream's chunks still in the queue
 };
 
 struct Batch {
@@ -186,7 +188,7 @@ struct mmf_server {
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::unordered_map<uint64_t, StreamState> streams;
-    std::deque<Request> queue;
+    std::list<Request> queue;  // admission order; admitted chunks leave from anywhere
     std::deque<Batch> inflight;
     std::unordered_map<uint64_t, int64_t> tickets;  // 0 pending, 1 done, 2 failed
     uint64_t next_stream = 1, next_ticket = 1;
@@ -271,6 +273,7 @@ bool run_batch(mmf_server *S, std::unique_lock<std::mutex> &lk) {
             break;
         }
         ss.in_flight = true;
+        ss.queued -= it->len;
         b.reqs.push_back(*it);
         b.stage_blocks.push_back({ib, in_bytes});
         b.out_blocks.push_back({ob, out_bytes});
@@ -572,19 +575,21 @@ mmf_status mmf_stream_open(mmf_server *S, int64_t w, uint64_t *stream_id) {
     return MMF_OK;
 }
 
-mmf_status mmf_stream_push(mmf_server *S, uint64_t stream_id, const void *h_chunk, int64_t len, void *h_max,
-                           void *h_min, int64_t *n_out, uint64_t *ticket) {
-    if (!S || !ticket) return set_error(MMF_EINVAL, "NULL argument");
+}  // extern "C"
+
+namespace {
+// With S->mu held: queue one chunk (see mmf_stream_push).
+mmf_status push_locked(mmf_server *S, uint64_t stream_id, const void *h_chunk, int64_t len, void *h_max,
+                       void *h_min, int64_t *n_out, uint64_t *ticket) {
     if (len < 0 || (len > 0 && !h_chunk)) return set_error(MMF_EINVAL, "bad chunk");
-    std::lock_guard<std::mutex> lk(S->mu);
     if (S->failed != MMF_OK) return set_error(MMF_EDEVICE, "the server failed earlier");
     auto it = S->streams.find(stream_id);
-    if (it == S->streams.end() || it->second.closed) return set_error(MMF_ECLOSED, "stream %llu is not open", (unsigned long long)stream_id);
+    if (it == S->streams.end() || it->second.closed)
+        return set_error(MMF_ECLOSED, "stream %llu is not open", (unsigned long long)stream_id);
     StreamState &ss = it->second;
-    // Outputs of this chunk: windows that end inside it (zero latency).
-    int64_t before = ss.count;
-    for (const Request &r : S->queue)
-        if (r.stream == stream_id) before += r.len;  // queued chunks of this stream come first
+    // Outputs of this chunk: windows that end inside it (zero latency).  The
+    // stream's queued chunks come first.
+    const int64_t before = ss.count + ss.queued;
     const int64_t done_before = std::max<int64_t>(0, before - ss.w + 1);
     const int64_t done_after = std::max<int64_t>(0, before + len - ss.w + 1);
     const int64_t m = done_after - done_before;
@@ -605,10 +610,45 @@ mmf_status mmf_stream_push(mmf_server *S, uint64_t stream_id, const void *h_chun
     S->queue.push_back(r);
     S->tickets[r.ticket] = 0;
     ss.pending++;
+    ss.queued += len;
     if (n_out) *n_out = m;
     *ticket = r.ticket;
-    S->cv_work.notify_one();
     return MMF_OK;
+}
+}  // namespace
+
+extern "C" {
+
+mmf_status mmf_stream_push(mmf_server *S, uint64_t stream_id, const void *h_chunk, int64_t len, void *h_max,
+                           void *h_min, int64_t *n_out, uint64_t *ticket) {
+    if (!S || !ticket) return set_error(MMF_EINVAL, "NULL argument");
+    mmf_status st;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        st = push_locked(S, stream_id, h_chunk, len, h_max, h_min, n_out, ticket);
+    }
+    if (st == MMF_OK) S->cv_work.notify_one();
+    return st;
+}
+
+mmf_status mmf_stream_push_batch(mmf_server *S, int64_t count, const uint64_t *stream_ids,
+                                 const void *const *h_chunks, const int64_t *lens, void *const *h_max,
+                                 void *const *h_min, int64_t *n_out, uint64_t *tickets, int64_t *n_done) {
+    if (!S || count < 0 || (count > 0 && (!stream_ids || !h_chunks || !lens || !tickets)))
+        return set_error(MMF_EINVAL, "NULL argument");
+    mmf_status st = MMF_OK;
+    int64_t i = 0;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        for (; i < count; ++i) {
+            st = push_locked(S, stream_ids[i], h_chunks[i], lens[i], h_max ? h_max[i] : nullptr,
+                             h_min ? h_min[i] : nullptr, n_out ? n_out + i : nullptr, tickets + i);
+            if (st != MMF_OK) break;
+        }
+    }
+    if (n_done) *n_done = i;
+    if (i > 0) S->cv_work.notify_one();
+    return st;
 }
 
 mmf_status mmf_ticket_wait(mmf_server *S, uint64_t ticket, int timeout_ms) {
@@ -624,6 +664,25 @@ mmf_status mmf_ticket_wait(mmf_server *S, uint64_t ticket, int timeout_ms) {
     const int64_t st = S->tickets[ticket];
     S->tickets.erase(ticket);
     return st == kTicketDone ? MMF_OK : set_error(MMF_EDEVICE, "the batch of ticket %llu failed", (unsigned long long)ticket);
+}
+
+mmf_status mmf_ticket_wait_batch(mmf_server *S, int64_t count, const uint64_t *tickets, int timeout_ms) {
+    if (!S || count < 0 || (count > 0 && !tickets)) return set_error(MMF_EINVAL, "NULL argument");
+    std::unique_lock<std::mutex> lk(S->mu);
+    const auto deadline = Clock::now() + std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms);
+    bool failed = false;
+    for (int64_t i = 0; i < count; ++i) {
+        auto it = S->tickets.find(tickets[i]);
+        if (it == S->tickets.end()) return set_error(MMF_EINVAL, "unknown ticket %llu", (unsigned long long)tickets[i]);
+        while (it->second == 0) {
+            if (S->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && it->second == 0)
+                return set_error(MMF_ETIMEOUT, "ticket %llu not done after %d ms (%lld of %lld done)",
+                                 (unsigned long long)tickets[i], timeout_ms, (long long)i, (long long)count);
+        }
+        failed |= it->second != kTicketDone;
+        S->tickets.erase(it);
+    }
+    return failed ? set_error(MMF_EDEVICE, "a batch of these tickets failed") : MMF_OK;
 }
 
 mmf_status mmf_stream_close(mmf_server *S, uint64_t stream_id, int timeout_ms) {

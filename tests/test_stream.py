@@ -138,3 +138,58 @@ def test_host_side_faults(mmf):
     assert e.value.status == 6
     srv.close()
     assert mmf.device_status() == 0
+
+
+def test_push_batch_equals_whole_array(mmf):
+    """Chunks of many streams queued with mmf_stream_push_batch (several of a
+    stream in one call, in order) and waited with mmf_ticket_wait_batch give
+    the filter of each stream's concatenation."""
+    rng = np.random.default_rng(17)
+    ns = 40
+    ws = rng.integers(1, 700, ns)
+    data = [synth.random_walk(int(rng.integers(2000, 30000)), seed=100 + k, dtype=np.float32) for k in range(ns)]
+    cuts = [_split(d.size, rng, 1, 3000) for d in data]
+    srv = mmf.Server(1 << 28, 128, "float32")
+    ids = np.array([srv.open(int(w)) for w in ws], dtype=np.uint64)
+    # One flat host buffer per side for every output, laid out per chunk.
+    events = []
+    for k in range(ns):
+        pos = 0
+        for L in cuts[k]:
+            events.append((k, pos, L))
+            pos += L
+    # A random interleaving of the streams that keeps each stream's chunks in order.
+    per = {k: [e for e in events if e[0] == k] for k in range(ns)}
+    seq = []
+    nxt = {k: 0 for k in range(ns)}
+    for _ in range(len(events)):
+        live = [k for k in range(ns) if nxt[k] < len(per[k])]
+        k = live[int(rng.integers(0, len(live)))]
+        seq.append(per[k][nxt[k]])
+        nxt[k] += 1
+    m_of = [mmf.n_outputs(p, L, int(ws[k])) for k, p, L in seq]
+    out_off = np.concatenate([[0], np.cumsum(m_of)])
+    hmax = np.empty(max(1, int(out_off[-1])), np.float32)
+    hmin = np.empty_like(hmax)
+    chunks = [np.ascontiguousarray(data[k][p:p + L]) for k, p, L in seq]
+    sids = np.array([ids[k] for k, _, _ in seq], dtype=np.uint64)
+    cptr = np.array([c.ctypes.data for c in chunks], dtype=np.uint64)
+    lens = np.array([L for _, _, L in seq], dtype=np.int64)
+    mptr = np.array([hmax.ctypes.data + 4 * int(o) for o in out_off[:-1]], dtype=np.uint64)
+    nptr = np.array([hmin.ctypes.data + 4 * int(o) for o in out_off[:-1]], dtype=np.uint64)
+    tickets = []
+    for a in range(0, len(seq), 97):  # groups of up to 97 chunks per call
+        b = min(len(seq), a + 97)
+        t, n_out = srv.push_batch(sids[a:b], cptr[a:b], lens[a:b], mptr[a:b], nptr[a:b])
+        assert list(n_out) == m_of[a:b]
+        tickets.append(t)
+    srv.wait_batch(np.concatenate(tickets))
+    srv.close()
+    got = {k: ([], []) for k in range(ns)}
+    for (k, p, L), o0, o1 in zip(seq, out_off[:-1], out_off[1:]):
+        got[k][0].append(hmax[o0:o1])
+        got[k][1].append(hmin[o0:o1])
+    for k in range(ns):
+        emx, emn = oracle.bf1d(data[k], int(ws[k]))
+        assert np.array_equal(np.concatenate(got[k][0]), emx), k
+        assert np.array_equal(np.concatenate(got[k][1]), emn), k
