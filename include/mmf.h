@@ -95,7 +95,7 @@ mmf_status mmf_filter1d(const void *d_in, int64_t n, int64_t w_or_r, mmf_dtype d
 #define MMF_WEDGE_MAX_WINDOW 496
 
 /* Same as mmf_filter1d with an explicit kernel choice (for tests and the
- * autotuner).  MMF_KERNEL_SLIDE requires w <= 17 (w <= 9 for f64);
+ * autotuner).  MMF_KERNEL_SLIDE requires w <= 17 for f32, w <= 9 otherwise;
  * MMF_KERNEL_WEDGE computes
  * MMF_VALID windows with w <= MMF_WEDGE_MAX_WINDOW (MMF_EINVAL /
  * MMF_ENOTIMPL otherwise). */

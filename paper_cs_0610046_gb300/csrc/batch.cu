@@ -121,10 +121,10 @@ mmf_status launch_group(mmf_batch_plan *p, int gi, const LaunchCtx &ctx, const v
     cudaError_t e = cudaSuccess;
     const int64_t ni = (int64_t)g.items.size();
     switch (p->dtype) {
-        case MMF_F32: e = blockscan_table<float>(ctx, g.mode, in, omax, omin, p->d_series, g.d_items, ni, tk, 0); break;
-        case MMF_F64: e = blockscan_table<double>(ctx, g.mode, in, omax, omin, p->d_series, g.d_items, ni, tk, 0); break;
-        case MMF_I16: e = blockscan_table<int16_t>(ctx, g.mode, in, omax, omin, p->d_series, g.d_items, ni, tk, 0); break;
-        case MMF_U8: e = blockscan_table<uint8_t>(ctx, g.mode, in, omax, omin, p->d_series, g.d_items, ni, tk, 0); break;
+        case MMF_F32: e = blockscan_table<float>(ctx, g.mode, in, p->in_len, omax, omin, p->d_series, g.d_items, ni, tk, 0); break;
+        case MMF_F64: e = blockscan_table<double>(ctx, g.mode, in, p->in_len, omax, omin, p->d_series, g.d_items, ni, tk, 0); break;
+        case MMF_I16: e = blockscan_table<int16_t>(ctx, g.mode, in, p->in_len, omax, omin, p->d_series, g.d_items, ni, tk, 0); break;
+        case MMF_U8: e = blockscan_table<uint8_t>(ctx, g.mode, in, p->in_len, omax, omin, p->d_series, g.d_items, ni, tk, 0); break;
     }
     return e == cudaSuccess ? MMF_OK : cuda_error(e, "batched launch");
 }

@@ -200,6 +200,7 @@ struct BlockScanParams {
     int64_t out_pitch;         // rows mode: element stride between rows (outputs)
     int *ticket;               // nullptr: static round-robin; else atomic ticket
     uint32_t *status;          // device status word
+    int64_t in_elems;          // elements of `in` that may be read (copies past a series end stay inside)
 };
 
 constexpr int kStages = 4;             // per-warp slice stages (power of two)
@@ -244,9 +245,11 @@ template <typename T> struct Geo {
     static constexpr int LGT = LGV + LGNT;
     static constexpr int SLICE = 32 * V;  // elements of a tile read by one warp
     static constexpr int NCH = V * (int)sizeof(T) / 16;  // 16-byte chunks per thread
-    // Register-slide halo (elements after the slice; windows up to HALO_MAX+1):
-    // one more thread's elements for the 16-element types, 8 for f64.
-    static constexpr int HALO_MAX = V == 16 ? 16 : 8;
+    // Register-slide halo (elements after the slice, a multiple of 16 bytes)
+    // and the largest w-1 the slide takes: 16 for f32 (one more thread's
+    // elements), 8 for the others (their 256-thread CTAs leave 128 registers).
+    static constexpr int HALO_MAX = sizeof(T) == 4 ? 16 : (8 > 16 / (int)sizeof(T) ? 8 : 16 / (int)sizeof(T));
+    static constexpr int SLIDE_S = sizeof(T) == 4 ? 16 : 8;
     // A warp's slice arrives in PIECES copies of PLANES lanes' elements each,
     // placed PSTRIDE bytes apart; each piece holds room for the
     // register-slide halo and a 16-byte shift.  One piece: the bank spread of
@@ -379,7 +382,7 @@ __device__ __forceinline__ ItemPlan<T> make_plan(const BlockScanParams &P, int64
     const int64_t span = oe - ob;
     ip.NC = span > 0 ? (int)((span + G::T_ - 1) >> G::LGT) : 0;
     ip.klast = span > 0 ? (int)((((span - 1) + s) >> G::LGT) >= ip.NC + ip.q) : 0;
-    if (want_mode == 3 && s <= G::HALO_MAX) ip.mode = 3;  // register slide: w <= HALO_MAX + 1
+    if (want_mode == 3 && s <= G::SLIDE_S) ip.mode = 3;  // register slide: w <= SLIDE_S + 1
     ip.ok = (s >= 0) && (ip.q + 2 <= kQCap) && span >= 0 && span + s + 2 * (int64_t)G::T_ <= kMaxItemSpan &&
             (want_mode < 0 || want_mode == ip.mode);
     return ip;
@@ -432,9 +435,13 @@ __device__ __forceinline__ int load_tile(int l, int caseB, int q, bool &keep, in
 
 // How one warp's slice [a, a + SLICE) of a tile reaches shared memory:
 //   0 (fast)    aligned and inside the series: one bulk copy of the slice;
-//   1 (shifted) unaligned but the 16-byte aligned cover lies inside the series:
-//               one bulk copy of the cover, read back at an element shift;
-//   2 (direct)  touches the series edges: threads load their elements.
+//   1 (shifted) inside the series, unaligned: one bulk copy of the 16-byte
+//               aligned cover (inside the readable buffer), read back at an
+//               element shift;
+//   2 (direct)  threads load their elements (the cover would leave the buffer);
+//   3 (empty)   wholly outside the series: identities, nothing is read;
+//   4 (clipped) partly outside the series, cover inside the buffer: as 1, and
+//               the readers put identities at positions outside the series.
 struct SliceCopy {
     int mode;
     int shift;       // elements (mode 1)
@@ -443,8 +450,9 @@ struct SliceCopy {
 };
 
 // HALO extra elements after the slice are copied too (register slide).
+// `buf`, `buf_n`: the readable buffer that holds the series.
 template <typename T, int HALO>
-__device__ __forceinline__ SliceCopy slice_copy(const T *in, int64_t n, int64_t a) {
+__device__ __forceinline__ SliceCopy slice_copy(const T *in, int64_t n, int64_t a, const T *buf, int64_t buf_n) {
     using G = Geo<T>;
     constexpr int LEN = G::SLICE + HALO;  // elements; LEN * sizeof(T) is a multiple of 16
     SliceCopy sc;
@@ -452,10 +460,14 @@ __device__ __forceinline__ SliceCopy slice_copy(const T *in, int64_t n, int64_t 
     sc.shift = 0;
     sc.src = 0;
     sc.bytes = 0;
-    if (a < 0 || a + LEN > n) return sc;
-    const uintptr_t start = (uintptr_t)(in + a);
+    if (a >= n || a + LEN <= 0) {
+        sc.mode = 3;
+        return sc;
+    }
+    const bool inside = a >= 0 && a + LEN <= n;
+    const uintptr_t start = (uintptr_t)in + (uintptr_t)(a * (int64_t)sizeof(T));
     const int sb = (int)(start & 15);
-    if (sb == 0) {
+    if (inside && sb == 0) {
         sc.mode = 0;
         sc.src = start;
         sc.bytes = (uint32_t)(LEN * sizeof(T));
@@ -463,8 +475,8 @@ __device__ __forceinline__ SliceCopy slice_copy(const T *in, int64_t n, int64_t 
     }
     const uintptr_t al = start - sb;
     const uintptr_t end = al + (uintptr_t)LEN * sizeof(T) + 16;
-    if (al >= (uintptr_t)in && end <= (uintptr_t)(in + n)) {
-        sc.mode = 1;
+    if (al >= (uintptr_t)buf && end <= (uintptr_t)(buf + buf_n)) {
+        sc.mode = inside ? 1 : 4;
         sc.shift = sb / (int)sizeof(T);
         sc.src = al;
         sc.bytes = (uint32_t)(LEN * sizeof(T) + 16);
@@ -566,18 +578,20 @@ __device__ __forceinline__ void issue_next(int warp) {
             smode = 0;
         } else {
             const int64_t a = wi.p0 + (int64_t)x * G::T_ + (int64_t)warp * G::SLICE;
-            const SliceCopy sc = slice_copy<T, HALO>(reinterpret_cast<const T *>(wi.in), wi.n, a);
+            const BlockScanParams &PP = S::params();
+            const SliceCopy sc = slice_copy<T, HALO>(reinterpret_cast<const T *>(wi.in), wi.n, a,
+                                                     reinterpret_cast<const T *>(PP.in), PP.in_elems);
             smode = sc.mode | (sc.shift << 8);
             wi.smode[stage] = smode;
-            if (sc.mode != 2) {
+            if (sc.mode != 2 && sc.mode != 3) {
                 fence_proxy_async_smem();
-                copy_pieces<T, HALO>(S::slice(warp, stage), sc.src, sc.mode == 1 ? 16 : 0, bar, pol);
+                copy_pieces<T, HALO>(S::slice(warp, stage), sc.src, 16, bar, pol);
             }
         }
     } else {
         wi.smode[stage] = 2;
     }
-    if ((smode & 0xff) == 2) mbar_arrive_expect_tx(bar, 0);
+    if ((smode & 0xff) == 2 || (smode & 0xff) == 3) mbar_arrive_expect_tx(bar, 0);
     wi.l++;
     wi.issued++;
 }
@@ -650,6 +664,21 @@ struct Consumer {
     // CTA barrier (the P ring and block aggregates are shared by all warps).
     __device__ __forceinline__ void sync() { named_bar_sync(1, G::NT); }
 
+    // Identities at this thread's positions of tile x that lie outside the
+    // series [0, n) (clipped copies).
+    template <int NE>
+    __device__ __forceinline__ void clip(const ItemPlan<T> &ip, int x, int, R (&xm)[NE], R (&xn)[NE]) const {
+        const int64_t pt = ip.p0 + (int64_t)x * T_ + (int64_t)warp * G::SLICE + (int64_t)lane * V;
+        const int64_t lo = -pt, hi = ip.n - pt;  // valid element indices: [lo, hi)
+#pragma unroll
+        for (int i = 0; i < NE; ++i) {
+            if (i < lo || i >= hi) {
+                xm[i] = Elem<T>::lo();
+                xn[i] = Elem<T>::hi();
+            }
+        }
+    }
+
     // Read this thread's V elements of input tile x of the item from the
     // warp's slice stage, then let lane 0 refill the stage with the warp's
     // next load.  Max-side and min-side copies differ only at positions
@@ -703,10 +732,17 @@ struct Consumer {
             ExtractLoop<T, 0, 0, V>::run(wd, xv);
 #pragma unroll
             for (int i = 0; i < V; ++i) xm[i] = xn[i] = xv[i];
-        } else if (mode == 1) {
+        } else if (mode == 1 || mode == 4) {
             const T *pe = reinterpret_cast<const T *>(S::lane_base(sb, lane)) + (smode >> 8);
 #pragma unroll
             for (int i = 0; i < V; ++i) xm[i] = xn[i] = Elem<T>::load(pe[i]);
+            if (mode == 4) clip(ip, x, V, xm, xn);
+        } else if (mode == 3) {
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                xm[i] = Elem<T>::lo();
+                xn[i] = Elem<T>::hi();
+            }
         } else {
             const int64_t pt = ip.p0 + (int64_t)x * T_ + (int64_t)warp * G::SLICE + (int64_t)lane * V;
 #pragma unroll
@@ -1402,10 +1438,17 @@ struct Consumer {
             ExtractLoop<T, 0, 0, NE>::run(wd, xv);
 #pragma unroll
             for (int i = 0; i < NE; ++i) xm[i] = xn[i] = xv[i];
-        } else if (mode == 1) {
+        } else if (mode == 1 || mode == 4) {
             const T *pe = reinterpret_cast<const T *>(S::lane_base(sb, lane)) + (smode >> 8);
 #pragma unroll
             for (int i = 0; i < NE; ++i) xm[i] = xn[i] = Elem<T>::load(pe[i]);
+            if (mode == 4) clip(ip, x, NE, xm, xn);
+        } else if (mode == 3) {
+#pragma unroll
+            for (int i = 0; i < NE; ++i) {
+                xm[i] = Elem<T>::lo();
+                xn[i] = Elem<T>::hi();
+            }
         } else {
             const int64_t pt = ip.p0 + (int64_t)x * T_ + (int64_t)warp * G::SLICE + (int64_t)lane * V;
 #pragma unroll
@@ -1468,7 +1511,7 @@ struct Consumer {
             case 7: run_slide<8>(ip); break;
             case 8: run_slide<9>(ip); break;
             default:
-                if constexpr (G::HALO_MAX >= 16) {
+                if constexpr (G::SLIDE_S >= 16) {
                     switch (ip.s) {
                         case 9: run_slide<10>(ip); break;
                         case 10: run_slide<11>(ip); break;
@@ -1585,6 +1628,14 @@ __global__ void __launch_bounds__(Geo<T>::NT, (Geo<T>::NT * Elem<T>::V == 4096 &
     for (int seq = 0;; ++seq) {
         const int64_t item = item_of<T>(PS, seq);
         if (item >= PS.n_items || item < 0) return;
+        // The ticket for the prefetch is requested now and stored at the
+        // item's end; the next item's table entries are brought to L1 while
+        // this item runs (its item entry now, its series entry at the end).
+        int tk = 0;
+        if (tid == 0 && PS.ticket) tk = atomicAdd(P.ticket, 1);
+        const int64_t next = item_of<T>(PS, seq + 1);
+        int64_t nser = -1;
+        if (PS.items && next < PS.n_items && next >= 0) nser = __ldg(&PS.items[next].series);
         ItemPlan<T> ip = make_plan<T>(PS, item, MODE);
         if (!ip.ok) {
             // A rejected item occupies one empty stage per warp.
@@ -1605,10 +1656,10 @@ __global__ void __launch_bounds__(Geo<T>::NT, (Geo<T>::NT * Elem<T>::V == 4096 &
                 cs.template run_item12<MODE>(ip);
             if (cs.failed) return;
         }
-        // Thread 0 fetches the ticket that the prefetch will need next, then
-        // the item boundary frees the ring and publishes the queue.
+        if (nser >= 0) prefetch_l1(PS.series + nser);
+        // The item boundary frees the ring and publishes the queue.
         if (tid == 0 && PS.ticket) {
-            S::queue()[fetched & (kQueue - 1)] = atomicAdd(P.ticket, 1);
+            S::queue()[fetched & (kQueue - 1)] = tk;
             ++fetched;
         }
         named_bar_sync(1, Geo<T>::NT);

@@ -151,7 +151,7 @@ mmf_status mmf_filter1d_ex(const void *d_in, int64_t n, int64_t w_or_r, mmf_dtyp
     LaunchCtx ctx;
     st = get_ctx(stream, &ctx);
     if (st != MMF_OK) return st;
-    const int slide_max = dtype == MMF_F64 ? 9 : 17;
+    const int slide_max = dtype == MMF_F32 ? 17 : 9;
     if (kernel == MMF_KERNEL_SLIDE && sd.w > slide_max)
         return set_error(MMF_EINVAL, "the register slide handles windows up to %d (w = %lld)", slide_max,
                          (long long)sd.w);

@@ -31,12 +31,12 @@ template <typename T, int MODE> static cudaError_t prepare_blockscan(int device,
     return cudaSuccess;
 }
 
-// Kernel mode for window w: 3 = register slide (w <= 17 for the 16-element
-// types, 9 for f64, unless a block scan is forced), else the block-scan mode
-// 0, 1 or 2.
+// Kernel mode for window w: 3 = register slide (w <= 17 for f32, 9 for the
+// other types, unless a block scan is forced), else the block-scan mode 0, 1
+// or 2.
 template <typename T> int block_mode(int64_t w, bool allow_slide) {
     const int64_t s = w - 1;
-    if (allow_slide && s <= Geo<T>::HALO_MAX) return 3;
+    if (allow_slide && s <= Geo<T>::SLIDE_S) return 3;
     if (s >= 32 * (int64_t)Geo<T>::V) return 2;
     return s >= Geo<T>::V ? 1 : 0;
 }
@@ -95,6 +95,7 @@ cudaError_t blockscan_1d(const LaunchCtx &ctx, const void *in, const SeriesDesc 
     P.n_items = n_items;
     P.ticket = nullptr;
     P.status = ctx.status;
+    P.in_elems = sd.in_off + sd.n;
     launch_mode<T>(mode, P, (int)n_items, ctx.stream);
     return cudaGetLastError();
 }
@@ -122,15 +123,16 @@ cudaError_t blockscan_rows(const LaunchCtx &ctx, const void *in, const SeriesDes
     P.out_pitch = out_pitch;
     P.n_items = rows * row_items;
     P.status = ctx.status;
+    P.in_elems = (rows - 1) * in_pitch + sd.in_off + sd.n;
     const int64_t gmax = (int64_t)(ctx.sms > 0 ? ctx.sms : 1) * per_sm;
     launch_mode<T>(mode, P, (int)(P.n_items < gmax ? P.n_items : gmax), ctx.stream);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t blockscan_table(const LaunchCtx &ctx, int mode, const void *in, void *omax, void *omin,
-                            const SeriesDesc *d_series, const ItemDesc *d_items, int64_t n_items, int *d_ticket,
-                            int grid) {
+cudaError_t blockscan_table(const LaunchCtx &ctx, int mode, const void *in, int64_t in_elems, void *omax,
+                            void *omin, const SeriesDesc *d_series, const ItemDesc *d_items, int64_t n_items,
+                            int *d_ticket, int grid) {
     if (n_items <= 0) return cudaSuccess;
     int per_sm = 1;
     cudaError_t e = prepare_mode<T>(mode, ctx.device, &per_sm);
@@ -146,6 +148,7 @@ cudaError_t blockscan_table(const LaunchCtx &ctx, int mode, const void *in, void
     P.n_items = n_items;
     P.ticket = d_ticket;
     P.status = ctx.status;
+    P.in_elems = in_elems;
     launch_mode<T>(mode, P, grid, ctx.stream);
     return cudaGetLastError();
 }
@@ -159,6 +162,6 @@ cudaError_t blockscan_table(const LaunchCtx &ctx, int mode, const void *in, void
                                                 int64_t, int64_t, void *, void *);                            \
     template cudaError_t mmf::blockscan_1d<T>(const LaunchCtx &, const void *, const SeriesDesc &, void *,      \
                                                void *, bool);                                                   \
-    template cudaError_t mmf::blockscan_table<T>(const LaunchCtx &, int, const void *, void *, void *,         \
+    template cudaError_t mmf::blockscan_table<T>(const LaunchCtx &, int, const void *, int64_t, void *, void *, \
                                                   const SeriesDesc *, const ItemDesc *, int64_t, int *, int); \
     template int mmf::block_mode<T>(int64_t, bool);

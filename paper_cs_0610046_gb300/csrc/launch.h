@@ -16,7 +16,7 @@ struct LaunchCtx {
 };
 
 // One series, statically split into per-CTA items (no allocation).  With
-// allow_slide, small windows (w <= 17; 9 for f64) use the register slide
+// allow_slide, small windows (w <= 17 for f32, 9 otherwise) use the register slide
 // instead of block scans.
 template <typename T>
 cudaError_t blockscan_1d(const LaunchCtx &ctx, const void *in, const SeriesDesc &sd, void *omax, void *omin,
@@ -31,9 +31,11 @@ cudaError_t blockscan_rows(const LaunchCtx &ctx, const void *in, const SeriesDes
 // Table-driven launch (batched plans): items of one block mode, pulled from
 // an atomic ticket (or round-robin if d_ticket is null).  grid <= 0: one
 // persistent wave.
+// in_elems: elements of `in` that may be read (the whole input buffer; copies
+// that cross a series end stay inside it).
 template <typename T>
-cudaError_t blockscan_table(const LaunchCtx &ctx, int mode, const void *in, void *omax, void *omin,
-                            const SeriesDesc *d_series, const ItemDesc *d_items, int64_t n_items,
+cudaError_t blockscan_table(const LaunchCtx &ctx, int mode, const void *in, int64_t in_elems, void *omax,
+                            void *omin, const SeriesDesc *d_series, const ItemDesc *d_items, int64_t n_items,
                             int *d_ticket, int grid);
 
 // Chunked monotonic wedge (Algorithm 1 per thread chunk), valid windows,
@@ -41,8 +43,8 @@ cudaError_t blockscan_table(const LaunchCtx &ctx, int mode, const void *in, void
 template <typename T>
 cudaError_t wedge_1d(const LaunchCtx &ctx, const void *in, int64_t n, int64_t w, void *omax, void *omin);
 
-// Kernel mode for window w: 3 = register slide (if allowed and w <= 17; 9 for
-// f64), else
+// Kernel mode for window w: 3 = register slide (if allowed and w <= 17 for
+// f32, 9 otherwise), else
 // the block-scan mode 0, 1 or 2.
 template <typename T> int block_mode(int64_t w, bool allow_slide);
 

@@ -141,10 +141,10 @@ extern "C" mmf_status mmf_filter1d_batched_noalloc(const void *d_in, const int64
         const ItemDesc *d_items = tab->items + group_begin[g];
         int *tk = tab->tickets + g;
         switch (dtype) {
-            case MMF_F32: e = blockscan_table<float>(ctx, g, d_in, d_max, d_min, tab->series, d_items, n_items, tk, 0); break;
-            case MMF_F64: e = blockscan_table<double>(ctx, g, d_in, d_max, d_min, tab->series, d_items, n_items, tk, 0); break;
-            case MMF_I16: e = blockscan_table<int16_t>(ctx, g, d_in, d_max, d_min, tab->series, d_items, n_items, tk, 0); break;
-            case MMF_U8: e = blockscan_table<uint8_t>(ctx, g, d_in, d_max, d_min, tab->series, d_items, n_items, tk, 0); break;
+            case MMF_F32: e = blockscan_table<float>(ctx, g, d_in, in_pos, d_max, d_min, tab->series, d_items, n_items, tk, 0); break;
+            case MMF_F64: e = blockscan_table<double>(ctx, g, d_in, in_pos, d_max, d_min, tab->series, d_items, n_items, tk, 0); break;
+            case MMF_I16: e = blockscan_table<int16_t>(ctx, g, d_in, in_pos, d_max, d_min, tab->series, d_items, n_items, tk, 0); break;
+            case MMF_U8: e = blockscan_table<uint8_t>(ctx, g, d_in, in_pos, d_max, d_min, tab->series, d_items, n_items, tk, 0); break;
         }
         if (e != cudaSuccess) return cuda_error(e, "no-allocation batched launch");
     }

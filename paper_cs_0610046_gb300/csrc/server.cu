@@ -226,11 +226,12 @@ int mode_for(mmf_dtype dt, int64_t w) {
 cudaError_t launch_group(mmf_server *S, const LaunchCtx &ctx, int g, int slot, const ItemDesc *items, int64_t ni) {
     char *base = S->dev_base;
     char *omax = base + S->stage_size, *omin = omax + S->out_half;
+    const int64_t stage_elems = (int64_t)(S->stage_size / S->esz);
     switch (S->dtype) {
-        case MMF_F32: return blockscan_table<float>(ctx, g, base, omax, omin, S->d_series[slot], items, ni, S->d_tick[slot] + g, 0);
-        case MMF_F64: return blockscan_table<double>(ctx, g, base, omax, omin, S->d_series[slot], items, ni, S->d_tick[slot] + g, 0);
-        case MMF_I16: return blockscan_table<int16_t>(ctx, g, base, omax, omin, S->d_series[slot], items, ni, S->d_tick[slot] + g, 0);
-        default: return blockscan_table<uint8_t>(ctx, g, base, omax, omin, S->d_series[slot], items, ni, S->d_tick[slot] + g, 0);
+        case MMF_F32: return blockscan_table<float>(ctx, g, base, stage_elems, omax, omin, S->d_series[slot], items, ni, S->d_tick[slot] + g, 0);
+        case MMF_F64: return blockscan_table<double>(ctx, g, base, stage_elems, omax, omin, S->d_series[slot], items, ni, S->d_tick[slot] + g, 0);
+        case MMF_I16: return blockscan_table<int16_t>(ctx, g, base, stage_elems, omax, omin, S->d_series[slot], items, ni, S->d_tick[slot] + g, 0);
+        default: return blockscan_table<uint8_t>(ctx, g, base, stage_elems, omax, omin, S->d_series[slot], items, ni, S->d_tick[slot] + g, 0);
     }
 }
 

@@ -65,10 +65,10 @@ def test_f32_windows_random_walk(mmf, w):
 @pytest.mark.parametrize("kernel", ["slide", "blockscan"])
 @pytest.mark.parametrize("w", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 13, 15, 16, 17])
 def test_small_windows_each_kernel(mmf, dtype, kernel, w):
-    """Windows up to 17 (9 for f64) through the register slide and through
-    the block scan (blocks inside a thread), both bit-exact."""
-    if kernel == "slide" and dtype == np.float64 and w > 9:
-        pytest.skip("the f64 register slide covers w <= 9")
+    """Windows up to 17 (9 for types other than f32) through the register
+    slide and through the block scan (blocks inside a thread), bit-exact."""
+    if kernel == "slide" and dtype != np.float32 and w > 9:
+        pytest.skip("the register slide covers w <= 9 for this type")
     a = synth.random_walk(30_011, seed=w, dtype=dtype)
     _check(mmf, a, w, kernel=kernel)
     off = synth.uniform(10_007, seed=w, dtype=dtype)
@@ -84,6 +84,8 @@ def test_slide_rejects_large_window(mmf):
         mmf.filter1d(x, 18, kernel="slide")
     with pytest.raises(mmf.MMFError):
         mmf.filter1d(x.double(), 10, kernel="slide")
+    with pytest.raises(mmf.MMFError):
+        mmf.filter1d(x.to(torch.int16), 10, kernel="slide")
 
 
 @pytest.mark.parametrize("w", [2, 4, 5, 9, 33, 127, 128, 129, 130, 1023, 1024, 1025, 1026, 2049, 3075])
