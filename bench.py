@@ -332,7 +332,7 @@ def filter2d_extras(dev, stream, peak, nimg=64, H=4096, W=4096, reps=3):
             byts = (nimg * H * W + 2 * nimg * Ho * Wo) * sz
             row = {}
             for tag, fuse in (("unfused", 0), ("fused", 1)):
-                if fuse and (wy == 1 or wx == 1 or wx > 17):
+                if fuse and (wy == 1 or wx == 1 or wx > 31 or wy > 31):
                     continue
                 mmf.filter2d(x, wy, wx, fuse=fuse, out_max=om, out_min=on, workspace=ws, stream=stream)
                 ms = _events_ms(lambda: mmf.filter2d(x, wy, wx, fuse=fuse, out_max=om, out_min=on, workspace=ws,

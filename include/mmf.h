@@ -117,10 +117,12 @@ int64_t mmf_output_length(int64_t n, int64_t w_or_r, mmf_mode mode);
  * that pass.  The row pass writes its two intermediates to `d_work` (16-byte
  * aligned, size from mmf_filter2d_workspace; none needed when wy or wx is 1
  * or when the fused kernel runs).
- * fuse: 0 row pass then column pass; 1 the fused kernel (the column pass
- * computes the row maxima and minima of each tile in registers, no
- * intermediates in memory; wx <= MMF_FUSED_MAX_WX, else MMF_ENOTIMPL);
- * -1 automatic (currently the two passes).  Column windows are limited by the column
+ * fuse: 0 row pass then column pass; 1 a fused kernel, no intermediates in
+ * memory: for wy, wx <= 31 a tile with its halo in shared memory, rows then
+ * columns; otherwise the column pass computing each tile's row maxima and
+ * minima in registers (wx <= MMF_FUSED_MAX_WX, else MMF_ENOTIMPL); -1
+ * automatic (the tile kernel when wy, wx <= 31, else the two passes).
+ * Column windows are limited by the column
  * pass's shared memory: up to about 760 rows for f32, 320 for f64 and 1700 for
  * i16/u8 (MMF_ENOTIMPL beyond). */
 #define MMF_FUSED_MAX_WX 64

@@ -7,6 +7,7 @@
 #include <cstring>
 
 #include "colscan.cuh"
+#include "tile2d.cuh"
 #include "launch.h"
 #include "mmf.h"
 
@@ -55,13 +56,60 @@ template <typename T> static cudaError_t col_launch(const LaunchCtx &ctx, const 
     return fused ? col_launch_cpt<T, 1, true>(ctx, P) : col_launch_cpt<T, 1, false>(ctx, P);
 }
 
-// The fused kernel reads wx image elements per row and thread (scalar loads
-// served by L1); measured slower than the two passes on the 4096 x 4096
-// workload at every window, so the automatic choice is the two passes and the
-// fused form runs when requested (wx <= MMF_FUSED_MAX_WX).
+// Fused forms: the tile kernel (halo tile in shared memory) for windows up to
+// kTileMaxW in both directions, automatically and on request; beyond that, on
+// request (fuse = 1, wx <= MMF_FUSED_MAX_WX), the column pass with row
+// maxima computed per row in registers.
+static bool tile_fits(int64_t wy, int64_t wx) { return wy <= kTileMaxW && wx <= kTileMaxW; }
 static bool use_fused(int64_t wy, int64_t wx, int fuse) {
     if (wy == 1 || wx == 1) return false;  // a single pass already
-    return fuse == 1;
+    return fuse == 1 || (fuse < 0 && tile_fits(wy, wx));
+}
+
+template <typename T>
+static cudaError_t tile_launch(const LaunchCtx &ctx, const T *in, int64_t nimg, int64_t H, int64_t W, int64_t pitch,
+                               int64_t wy, int64_t wx, T *omax, T *omin) {
+    Tile2DParams P{};
+    P.in = in;
+    P.out_max = omax;
+    P.out_min = omin;
+    P.nimg = nimg;
+    P.H = H;
+    P.W = W;
+    P.pitch = pitch;
+    P.img_stride = H * pitch;
+    P.Ho = H - wy + 1;
+    P.Wo = W - wx + 1;
+    P.wy = (int)wy;
+    P.wx = (int)wx;
+    P.tiles_x = (int)((P.Wo + kTC - 1) / kTC);
+    P.tiles_y = (int)((P.Ho + kTR - 1) / kTR);
+    const int64_t grid = nimg * P.tiles_x * P.tiles_y;
+    if (grid <= 0) return cudaSuccess;
+    if (grid > 0x7fffffff) return cudaErrorInvalidValue;
+    P.xs = Tile2DSmem<T>::xs((int)wx);
+    P.x_bytes = (int)Tile2DSmem<T>::x_bytes((int)wy, (int)wx);
+    P.r_bytes = (int)Tile2DSmem<T>::r_bytes((int)wy);
+    const size_t smem = Tile2DSmem<T>::bytes((int)wy, (int)wx);
+    const int pmax = pow2_floor((int)(wx > wy ? wx : wy));
+    auto go = [&](auto kernel, int slot) -> cudaError_t {
+        static size_t set[64][5] = {};
+        size_t &have = set[ctx.device & 63][slot];
+        if (smem > have) {
+            cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            have = smem;
+        }
+        kernel<<<(unsigned)grid, kTThreads, smem, ctx.stream>>>(P);
+        return cudaGetLastError();
+    };
+    switch (pmax) {
+        case 1:
+        case 2: return go(tile2d_kernel<T, 2>, 0);
+        case 4: return go(tile2d_kernel<T, 4>, 1);
+        case 8: return go(tile2d_kernel<T, 8>, 2);
+        default: return go(tile2d_kernel<T, 16>, 3);
+    }
 }
 
 // Row pitch of the intermediates: Wo rounded up to 16 elements, so every
@@ -89,6 +137,10 @@ static mmf_status filter2d(const LaunchCtx &ctx, const T *in, int64_t nimg, int6
     P.wy = (int)wy;
     P.wx = (int)wx;
     const bool fused = use_fused(wy, wx, fuse);
+    if (fused && tile_fits(wy, wx)) {
+        e = tile_launch<T>(ctx, in, nimg, H, W, pitch, wy, wx, omax, omin);
+        return e == cudaSuccess ? MMF_OK : cuda_error(e, "fused 2D tile");
+    }
     if (wx == 1 || fused) {  // columns only (or fused), on the image
         P.src_max = in;
         P.src_min = in;

@@ -25,12 +25,13 @@ def _expect(img, wy, wx):
     return oracle.bf2d(img, wy, wx)
 
 
-@pytest.mark.parametrize("fuse", [0, 1])
+@pytest.mark.parametrize("fuse", [0, 1, -1])
 @pytest.mark.parametrize("dtype", [np.float32, np.uint8, np.float64, np.int16])
 @pytest.mark.parametrize("wy,wx", WINDOWS)
 def test_2d_windows(mmf, dtype, wy, wx, fuse):
-    """Unfused (row pass to a workspace, then columns) and fused (row maxima
-    computed inside the column pass) against the literal rectangle."""
+    """Unfused (row pass to a workspace, then columns), fused (the shared
+    memory tile kernel up to 31 x 31, else row maxima computed inside the
+    column pass) and the automatic choice against the literal rectangle."""
     imgs = synth.blobs2d(2, 300, 262, seed=wy * 7 + wx, dtype=dtype, nblobs=20)
     if dtype == np.int16:
         imgs = (imgs.astype(np.int32) - 16000).astype(np.int16)
@@ -52,7 +53,8 @@ def test_2d_pitched_rows_and_ragged(mmf):
     full = synth.blobs2d(3, 131, 517, seed=3, dtype=np.float32, nblobs=9)
     base = torch.from_numpy(full).cuda()
     x = base[:, :, :501]  # pitch 517, width 501
-    for wy, wx, fuse in ((5, 6, 0), (5, 6, 1), (40, 1, -1), (1, 40, -1), (33, 71, 0), (33, 17, 1), (12, 3, 1)):
+    for wy, wx, fuse in ((5, 6, 0), (5, 6, 1), (40, 1, -1), (1, 40, -1), (33, 71, 0), (33, 17, 1), (12, 3, 1),
+                         (31, 31, -1), (2, 30, 1), (31, 2, 1), (16, 16, -1)):
         mx, mn = mmf.filter2d(x, wy, wx, fuse=fuse)
         torch.cuda.synchronize()
         for k in range(3):
