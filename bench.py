@@ -226,7 +226,8 @@ def batched_extras(dev, stream, peak, reps=5, envelope_series=1_000_000):
         plan.per_series(x, om, on, stream)
         pms = _events_ms(lambda: plan.per_series(x, om, on, stream), 2, stream)
         sz = 4 if tdt == torch.float32 else 8
-        byts = (total + 2 * plan.out_len) * sz
+        n_out = int(np.maximum(lens - ws + 1, 0).sum())  # padding between series excluded
+        byts = (total + 2 * n_out) * sz
         out[f"uneven_{tname}"] = {
             "series": 4096, "elements": total, "batched_ms": bms, "per_series_ms": pms,
             "batched_over_per_series": pms / bms, "batched_Gelem_s": total / bms / 1e6,

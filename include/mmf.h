@@ -140,8 +140,11 @@ mmf_status mmf_filter2d_separable(const void *d_in, int64_t nimg, int64_t H, int
  * by mmf_filter1d (window h_w[s], clipped to the series length in VALID mode
  * by the caller; radius in CENTERED_CLIPPED mode).  The plan owns device
  * tables (series, work items, ticket counters) and a graph cache; it is not
- * thread-safe.  Outputs are concatenated series by series, at the offsets
- * reported by mmf_batch_plan_out_offsets. */
+ * thread-safe.  Outputs follow series by series, at the offsets reported by
+ * mmf_batch_plan_out_offsets: each series' outputs start on a 32-byte
+ * boundary of the output buffers (whole-sector vector stores), after the
+ * previous series' outputs and at most 31 bytes of padding that no call
+ * writes. */
 typedef struct mmf_batch_plan mmf_batch_plan;
 
 /* h_in_off: element offset of each series in the input buffer (NULL: the
@@ -154,7 +157,10 @@ mmf_status mmf_batch_plan_create(const int64_t *h_in_off, const int64_t *h_len, 
 /* Frees the plan (NULL is ignored).  No call may use it afterwards. */
 void mmf_batch_plan_destroy(mmf_batch_plan *plan);
 
-/* h_off[nseries+1]: start of each series' outputs in the output buffers. */
+/* h_off[nseries+1]: start of each series' outputs in the output buffers
+ * (elements); series s has n_out outputs from h_off[s] (VALID: len - w + 1,
+ * CENTERED_CLIPPED: len), followed by padding up to h_off[s+1];
+ * h_off[nseries] = out_len, the end of the last series' outputs. */
 mmf_status mmf_batch_plan_out_offsets(const mmf_batch_plan *plan, int64_t *h_off);
 
 /* Required input / output buffer lengths (elements) and, in n_items[4] (may
@@ -272,7 +278,8 @@ mmf_status mmf_server_stats(mmf_server *server, int reset, mmf_server_stats_t *o
  * it is an interface convenience.
  *
  * Same results as a batch plan over the same series (inputs packed back to
- * back in d_in, outputs concatenated in d_max/d_min in series order), but it
+ * back in d_in, outputs in d_max/d_min in series order at the offsets a plan
+ * reports, each series on a 32-byte boundary), but it
  * calls no cudaMalloc/cudaFree: its work tables live in one fixed device array
  * of about 70 KB that every GPU which loads the library keeps until the
  * process exits.  At most MMF_NOALLOC_MAX_SERIES series; long series are

@@ -197,16 +197,20 @@ class BatchPlan:
         self.items_per_group = list(items)
 
     def out_offsets(self):
+        """Start of each series' outputs, then out_len: series s has its
+        n_out outputs from off[s] (on a 32-byte boundary), then padding."""
         import numpy as np
         off = np.zeros(self.nseries + 1, dtype=np.int64)
         check(self._lib.mmf_batch_plan_out_offsets(self._h, off.ctypes.data_as(_P64)))
         return off
 
     def _outs(self, x, out_max, out_min):
+        # Zero-filled: the padding between series (outputs start on 32-byte
+        # boundaries) is never written and reads as 0.
         if out_max is None:
-            out_max = torch.empty(self.out_len, dtype=x.dtype, device=x.device)
+            out_max = torch.zeros(self.out_len, dtype=x.dtype, device=x.device)
         if out_min is None:
-            out_min = torch.empty(self.out_len, dtype=x.dtype, device=x.device)
+            out_min = torch.zeros(self.out_len, dtype=x.dtype, device=x.device)
         return out_max, out_min
 
     def __call__(self, x, out_max=None, out_min=None, stream=None):

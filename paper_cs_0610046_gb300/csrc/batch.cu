@@ -251,7 +251,8 @@ mmf_status mmf_batch_plan_create(const int64_t *h_in_off, const int64_t *h_len, 
     p->nseries = nseries;
     p->series.resize(nseries);
     p->out_off.assign(nseries + 1, 0);
-    int64_t in_pos = 0;
+    int64_t in_pos = 0, out_pos = 0;
+    const int esz = elem_size(dtype);
     for (int64_t s = 0; s < nseries; ++s) {
         SeriesDesc sd;
         mmf_status st = make_series(h_len[s], h_w[s], mode, dtype, &sd);
@@ -266,11 +267,13 @@ mmf_status mmf_batch_plan_create(const int64_t *h_in_off, const int64_t *h_len, 
         }
         in_pos = sd.in_off + sd.n;
         p->in_len = std::max(p->in_len, sd.in_off + sd.n);
-        sd.out_off = p->out_off[s];
-        p->out_off[s + 1] = p->out_off[s] + sd.n_out;
+        sd.out_off = batch_out_start(out_pos, esz);
+        p->out_off[s] = sd.out_off;
+        out_pos = sd.out_off + sd.n_out;
         p->series[s] = sd;
     }
-    p->out_len = p->out_off[nseries];
+    p->out_off[nseries] = out_pos;
+    p->out_len = out_pos;
     for (int gi = 0; gi < kModes; ++gi) {
         p->groups[gi].mode = gi;
         p->groups[gi].seg_tiles = gi == 2 ? 32 : 16;

@@ -144,15 +144,24 @@ template <typename T, int S, int V> struct ExtractLoop<T, S, V, V> {
     __device__ static void run(const uint32_t *, typename Elem<T>::R *) {}
 };
 
-// Dispatch the (warp-uniform) element shift to a compile-time extraction.
-template <typename T, int S = 0>
-__device__ __forceinline__ void extract_shifted(int s, const uint32_t *wd, typename Elem<T>::R *x) {
-    if constexpr (S < 16 / (int)sizeof(T)) {
-        if (s == S) {
-            ExtractLoop<T, S, 0, Elem<T>::V>::run(wd, x);
-            return;
+// Moves a little-endian byte sequence of N + 4 words down by sb bytes
+// (0 <= sb < 16, the same for the whole warp): afterwards word k holds bytes
+// [4k + sb, 4k + sb + 4) of the original sequence, for k < N.  A two-stage
+// barrel shift by whole words, then a funnel shift for the rest.
+template <int N>
+__device__ __forceinline__ void shift_bytes(uint32_t (&wd)[N + 4], int sb) {
+    const int sw = sb >> 2;
+#pragma unroll
+    for (int b = 1; b < 4; b <<= 1) {
+        if (sw & b) {
+#pragma unroll
+            for (int k = 0; k + b < N + 4; ++k) wd[k] = wd[k + b];
         }
-        extract_shifted<T, S + 1>(s, wd, x);
+    }
+    const int br = (sb & 3) * 8;
+    if (br) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) wd[k] = __funnelshift_r(wd[k], wd[k + 1], br);
     }
 }
 
@@ -214,10 +223,12 @@ extern __shared__ __align__(128) uint8_t bs_smem[];
 // Copy-issue state of one warp (its lane 0 issues the warp's slice of every
 // tile load).  Kept in shared memory so that it costs no registers.
 struct WarpIssue {
-    uintptr_t src0;  // address of this warp's slice of tile 0 of the item being issued
+    uintptr_t src0;  // this warp's slice of tile 0 of the item being issued, rounded down to 16 bytes
     const void *in;  // its series base
     int64_t n, p0;   // its length and the input position of its tile 0
-    int32_t fast_lo, fast_hi;  // tiles whose slice is whole and aligned (one plain copy)
+    int32_t fast_lo, fast_hi;  // tiles whose slice lies inside the series (one copy, no checks)
+    int32_t fast_smode;        // their copy mode: 0 (aligned) or 1 | shift << 8
+    int32_t fast_extra;        // bytes copied past the slice for the shift (0 or 16)
     int32_t seq;     // its sequence number among this CTA's items
     int32_t l;       // next load within it
     int32_t nloads;  // its number of loads; -1 once the sequence has ended
@@ -519,10 +530,10 @@ __device__ __forceinline__ void issue_next(int warp) {
         if (l < wi.nloads && wi.linear && l >= wi.fast_lo && l < wi.fast_hi) {
             const int stage = wi.issued & (kStages - 1);
             uint64_t *bar = S::bar(warp, stage);
-            wi.smode[stage] = 0;
+            wi.smode[stage] = wi.fast_smode;
             fence_proxy_async_smem();
-            copy_pieces<T, HALO>(S::slice(warp, stage), wi.src0 + (uintptr_t)l * G::T_ * sizeof(T), 0, bar,
-                                 policy_evict_first());
+            copy_pieces<T, HALO>(S::slice(warp, stage), wi.src0 + (uintptr_t)l * G::T_ * sizeof(T), wi.fast_extra,
+                                 bar, policy_evict_first());
             wi.l = l + 1;
             wi.issued++;
             return;
@@ -542,13 +553,20 @@ __device__ __forceinline__ void issue_next(int warp) {
             if (!ip.ok && warp == 0) report_error(P.status, kErrBadItem);
             const int64_t a0 = ip.p0 + (int64_t)warp * G::SLICE;
             const uintptr_t src0 = (uintptr_t)(ip.in + a0);
-            int64_t flo = 0, fhi = 0;
-            if ((src0 & 15) == 0) {
-                flo = a0 >= 0 ? 0 : (-a0 + G::T_ - 1) / G::T_;
-                fhi = ip.n - LEN - a0 >= 0 ? (ip.n - LEN - a0) / G::T_ + 1 : 0;
-                if (fhi < flo) fhi = flo;
-            }
-            wi.src0 = src0;
+            // Tiles whose slice [a, a + LEN) lies inside the series take one
+            // copy without checks: from the slice itself if it is 16-byte
+            // aligned, else (the same shift for every tile of the item) from
+            // 16 bytes below, with 16 bytes more, which stays inside the
+            // series when a >= 16 bytes and a + LEN + 16 bytes <= n.
+            const int sb = (int)(src0 & 15);
+            const int64_t lead = sb ? 16 / (int)sizeof(T) : 0;
+            const int64_t lo_a = lead, hi_a = ip.n - LEN - lead;  // range of a
+            int64_t flo = a0 >= lo_a ? 0 : (lo_a - a0 + G::T_ - 1) / G::T_;
+            int64_t fhi = hi_a - a0 >= 0 ? (hi_a - a0) / G::T_ + 1 : 0;
+            if (fhi < flo) fhi = flo;
+            wi.src0 = src0 - sb;
+            wi.fast_smode = sb ? 1 | ((sb / (int)sizeof(T)) << 8) : 0;
+            wi.fast_extra = sb ? 16 : 0;
             wi.fast_lo = (int)flo;
             wi.fast_hi = (int)(fhi > 0x7fffffff ? 0x7fffffff : fhi);
             wi.in = ip.in;
@@ -572,10 +590,11 @@ __device__ __forceinline__ void issue_next(int warp) {
         const int x = load_tile(wi.l, wi.caseB, wi.q, keep, MODE, wi.NC, wi.klast);
         const uint64_t pol = keep ? policy_evict_last() : policy_evict_first();
         if (x >= wi.fast_lo && x < wi.fast_hi) {
-            wi.smode[stage] = 0;
+            smode = wi.fast_smode;
+            wi.smode[stage] = smode;
             fence_proxy_async_smem();
-            copy_pieces<T, HALO>(S::slice(warp, stage), wi.src0 + (uintptr_t)x * G::T_ * sizeof(T), 0, bar, pol);
-            smode = 0;
+            copy_pieces<T, HALO>(S::slice(warp, stage), wi.src0 + (uintptr_t)x * G::T_ * sizeof(T), wi.fast_extra,
+                                 bar, pol);
         } else {
             const int64_t a = wi.p0 + (int64_t)x * G::T_ + (int64_t)warp * G::SLICE;
             const BlockScanParams &PP = S::params();
@@ -679,6 +698,56 @@ struct Consumer {
         }
     }
 
+    // This lane's first NWD words (16-byte chunks from its element base) of
+    // a slice stage.  16-byte reads are served eight lanes at a time; lanes
+    // V*sz bytes apart reading the same chunk index would share banks, so
+    // each group of NCH chunks (lane+g's elements) is read starting at chunk
+    // rot = ((lane+g) / (8/NCH)) mod NCH, which spreads each group of eight
+    // lanes over all banks, and a barrel shift restores the order.
+    template <int NWD>
+    __device__ __forceinline__ void read_words(const uint8_t *sb, uint32_t *wd) const {
+        const uint4 *p4 = reinterpret_cast<const uint4 *>(S::lane_base(sb, lane));
+        if constexpr ((G::NCH == 2 || G::NCH == 4) && (NWD / 4) % G::NCH == 0) {
+            constexpr int NC = G::NCH;
+#pragma unroll
+            for (int g = 0; g < NWD / 4 / NC; ++g) {
+                const int rot = ((lane + g) / (8 / NC)) & (NC - 1);
+                uint4 u[NC];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) u[c] = p4[g * NC + ((c + rot) & (NC - 1))];
+                // u[c] holds chunk (c + rot) mod NC: rotate right by rot.
+#pragma unroll
+                for (int b = 1; b < NC; b <<= 1) {
+                    if (rot & b) {
+                        uint4 t[NC];
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) t[c] = u[(c - b + NC) & (NC - 1)];
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) u[c] = t[c];
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const int k = g * NC + c;
+                    wd[4 * k] = u[c].x; wd[4 * k + 1] = u[c].y; wd[4 * k + 2] = u[c].z; wd[4 * k + 3] = u[c].w;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < NWD / 4; ++c) {
+                const uint4 v = p4[c];
+                wd[4 * c] = v.x; wd[4 * c + 1] = v.y; wd[4 * c + 2] = v.z; wd[4 * c + 3] = v.w;
+            }
+        }
+    }
+    // The 16 bytes that follow this lane's first NWD words (inside the stage:
+    // shifted copies carry 16 bytes past the slice and its halo).
+    __device__ __forceinline__ void read_tail(const uint8_t *sb, int nwd, uint32_t *wd) const {
+        static_assert(G::PIECES == 1, "one piece per slice: lane data is contiguous");
+        const uint4 v = reinterpret_cast<const uint4 *>(S::lane_base(sb, lane))[nwd / 4];
+        wd[0] = v.x; wd[1] = v.y; wd[2] = v.z; wd[3] = v.w;
+    }
+
     // Read this thread's V elements of input tile x of the item from the
     // warp's slice stage, then let lane 0 refill the stage with the warp's
     // next load.  Max-side and min-side copies differ only at positions
@@ -694,48 +763,22 @@ struct Consumer {
         const uint8_t *sb = S::slice(warp, cur.stage);
         if (mode == 0) {
             uint32_t wd[4 * G::NCH];
-            const uint4 *p4 = reinterpret_cast<const uint4 *>(S::lane_base(sb, lane));
-            if constexpr (G::NCH == 2 || G::NCH == 4) {
-                // 16-byte reads are served eight lanes at a time; lanes V*sz
-                // bytes apart reading the same word index would share banks.
-                // Lane l reads its words starting at rot = (l / (8/NCH)) mod
-                // NCH, which spreads each group of eight over all banks, then
-                // a barrel shift restores the order.
-                constexpr int NC = G::NCH;
-                const int rot = (lane / (8 / NC)) & (NC - 1);
-                uint4 u[NC];
-#pragma unroll
-                for (int c = 0; c < NC; ++c) u[c] = p4[(c + rot) & (NC - 1)];
-                // u[c] holds word (c + rot) mod NC: rotate right by rot.
-#pragma unroll
-                for (int b = 1; b < NC; b <<= 1) {
-                    if (rot & b) {
-                        uint4 t[NC];
-#pragma unroll
-                        for (int c = 0; c < NC; ++c) t[c] = u[(c - b + NC) & (NC - 1)];
-#pragma unroll
-                        for (int c = 0; c < NC; ++c) u[c] = t[c];
-                    }
-                }
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    wd[4 * c] = u[c].x; wd[4 * c + 1] = u[c].y; wd[4 * c + 2] = u[c].z; wd[4 * c + 3] = u[c].w;
-                }
-            } else {
-#pragma unroll
-                for (int c = 0; c < G::NCH; ++c) {
-                    uint4 v = p4[c];
-                    wd[4 * c] = v.x; wd[4 * c + 1] = v.y; wd[4 * c + 2] = v.z; wd[4 * c + 3] = v.w;
-                }
-            }
+            read_words<4 * G::NCH>(sb, wd);
             R xv[V];
             ExtractLoop<T, 0, 0, V>::run(wd, xv);
 #pragma unroll
             for (int i = 0; i < V; ++i) xm[i] = xn[i] = xv[i];
         } else if (mode == 1 || mode == 4) {
-            const T *pe = reinterpret_cast<const T *>(S::lane_base(sb, lane)) + (smode >> 8);
+            // The slice starts smode >> 8 elements (under 16 bytes) into the
+            // stage: this lane's words, then the next 16 bytes, shifted.
+            uint32_t wd[4 * G::NCH + 4];
+            read_words<4 * G::NCH>(sb, wd);
+            read_tail(sb, 4 * G::NCH, wd + 4 * G::NCH);
+            shift_bytes<4 * G::NCH>(wd, (smode >> 8) * (int)sizeof(T));
+            R xv[V];
+            ExtractLoop<T, 0, 0, V>::run(wd, xv);
 #pragma unroll
-            for (int i = 0; i < V; ++i) xm[i] = xn[i] = Elem<T>::load(pe[i]);
+            for (int i = 0; i < V; ++i) xm[i] = xn[i] = xv[i];
             if (mode == 4) clip(ip, x, V, xm, xn);
         } else if (mode == 3) {
 #pragma unroll
@@ -937,11 +980,73 @@ struct Consumer {
                 on[i] = vn;
             }
         }
-        const int64_t o0 = ip.o_begin + jr0;
-        if (o0 < ip.o_end) {
-            const int cnt = o0 + V <= ip.o_end ? V : (int)(ip.o_end - o0);
+        store_out(ip, ip.o_begin + jr0, om, on, out_vec(ip));
+    }
+
+    // Output alignment of the item (outputs of a thread start V elements
+    // apart): 2 = 32-byte, 1 = 16-byte, 0 = neither (same for every thread).
+    __device__ __forceinline__ int out_vec(const ItemPlan<T> &ip) const {
+        const uintptr_t oa = (ip.omax ? (uintptr_t)(ip.omax + ip.o_begin) : 0) |
+                             (ip.omin ? (uintptr_t)(ip.omin + ip.o_begin) : 0);
+        return (oa & 31) == 0 ? 2 : ((oa & 15) == 0 ? 1 : 0);
+    }
+
+    // Stores this thread's outputs o0 .. o0+V-1 of the item (those before
+    // o_end).  Every lane of the warp calls it (vec from out_vec).
+    __device__ __forceinline__ void store_out(const ItemPlan<T> &ip, int64_t o0, const R (&om)[V], const R (&on)[V],
+                                              int vec) const {
+        const bool full = o0 + V <= ip.o_end;
+        const bool wfull = __all_sync(0xffffffffu, full);
+        if (vec && full) {
+            if constexpr (G::NCH % 2 == 0) {
+                if (vec == 2) {
+                    if (ip.omax) store_v8(ip.omax + o0, om);
+                    if (ip.omin) store_v8(ip.omin + o0, on);
+                    return;
+                }
+            }
+            if (ip.omax) store_vec(ip.omax + o0, om);
+            if (ip.omin) store_vec(ip.omin + o0, on);
+        } else if (!vec && wfull) {
+            if (ip.omax) store_shifted(ip.omax + o0, om);
+            if (ip.omin) store_shifted(ip.omin + o0, on);
+        } else if (o0 < ip.o_end) {
+            const int cnt = full ? V : (int)(ip.o_end - o0);
             if (ip.omax) store(ip.omax + o0, om, cnt);
             if (ip.omin) store(ip.omin + o0, on, cnt);
+        }
+    }
+
+    // A whole warp span of outputs (every lane V values at dst, lanes V
+    // elements apart) whose start is not 16-byte aligned: the warp moves its
+    // values down by d elements (d: from dst to the next 16-byte boundary,
+    // the same for every lane), so that each lane stores whole aligned
+    // 16-byte chunks; lane 0 stores its first d values singly and lane 31
+    // its last A - d (its last chunk would reach into the next warp's span).
+    __device__ __forceinline__ void store_shifted(T *dst, const R (&v)[V]) const {
+        constexpr int A = 16 / (int)sizeof(T);  // elements per chunk
+        constexpr int NWD = 4 * G::NCH;
+        const int d = (int)((16 - ((uintptr_t)dst & 15)) & 15) / (int)sizeof(T);
+        uint32_t wd[NWD + 4];
+#pragma unroll
+        for (int k = 0; k < NWD; ++k) wd[k] = pack_word<T>(v, k);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) wd[NWD + k] = __shfl_down_sync(0xffffffffu, wd[k], 1);
+        shift_bytes<NWD>(wd, d * (int)sizeof(T));
+        uint4 *p = reinterpret_cast<uint4 *>(dst + d);
+#pragma unroll
+        for (int c = 0; c < G::NCH; ++c)
+            if (c < G::NCH - 1 || lane != 31 || d == 0)
+                __stcs(p + c, make_uint4(wd[4 * c], wd[4 * c + 1], wd[4 * c + 2], wd[4 * c + 3]));
+        if (lane == 0) {
+#pragma unroll
+            for (int i = 0; i < A - 1; ++i)
+                if (i < d) dst[i] = Elem<T>::store(v[i]);
+        }
+        if (lane == 31 && d) {
+#pragma unroll
+            for (int i = V - A + 1; i < V; ++i)
+                if (i >= V - A + d) dst[i] = Elem<T>::store(v[i]);
         }
     }
 
@@ -1137,7 +1242,7 @@ struct Consumer {
     template <int MODE>
     __device__ __forceinline__ void outputs12(const ItemPlan<T> &ip, int c, const R (&sm)[V], const R (&sn)[V], R fm,
                                               R fn, int vec) {
-        const int lgB = ip.lgB;
+        const int lgB = MODE == 2 ? G::LGV + 5 : ip.lgB;
         const int jr0 = c * T_ + tid * V;
         const int kr0 = jr0 + ip.s;
         // k = kr0 + i lies in thread block tk0 for i < crossT (as its element
@@ -1241,22 +1346,7 @@ struct Consumer {
             om[i] = vmax3(sm[i], far ? c1m : c0m, Elem<T>::pmax(pr));
             on[i] = vmin3(sn[i], far ? c1n : c0n, Elem<T>::pmin(pr));
         }
-        const int64_t o0 = ip.o_begin + jr0;
-        if (vec && o0 + V <= ip.o_end) {
-            if constexpr (G::NCH % 2 == 0) {
-                if (vec == 2) {
-                    if (ip.omax) store_v8(ip.omax + o0, om);
-                    if (ip.omin) store_v8(ip.omin + o0, on);
-                    return;
-                }
-            }
-            if (ip.omax) store_vec(ip.omax + o0, om);
-            if (ip.omin) store_vec(ip.omin + o0, on);
-        } else if (o0 < ip.o_end) {
-            const int cnt = o0 + V <= ip.o_end ? V : (int)(ip.o_end - o0);
-            if (ip.omax) store(ip.omax + o0, om, cnt);
-            if (ip.omin) store(ip.omin + o0, on, cnt);
-        }
+        store_out(ip, ip.o_begin + jr0, om, on, vec);
     }
 
     // 32-byte streaming stores (full sectors): V * sizeof(T) a multiple of 32,
@@ -1314,11 +1404,10 @@ struct Consumer {
     template <int MODE>
     __device__ __forceinline__ void run_item12(const ItemPlan<T> &ip) {
         const int q = ip.q;
-        const int lgS = ip.lgB - G::LGV;
-        // Output alignment of the item (outputs of a thread start V elements
-        // apart): 2 = 32-byte, 1 = 16-byte, 0 = neither.
-        const uintptr_t oa = ((uintptr_t)(ip.omax + ip.o_begin)) | ((uintptr_t)(ip.omin + ip.o_begin));
-        const int vec = (oa & 31) == 0 ? 2 : ((oa & 15) == 0 ? 1 : 0);
+        // Mode 2 scan blocks span one warp (2^5 lanes): a compile-time width
+        // keeps the lane scans free of branches.
+        const int lgS = MODE == 2 ? 5 : ip.lgB - G::LGV;
+        const int vec = out_vec(ip);
         if (!ip.caseB) {
             // Tile c is the J tile of output tile c and a K tile of c-1 and c.
             // The loop is unrolled by two so that the J states alternate.
@@ -1397,51 +1486,23 @@ struct Consumer {
         const int smode = S::issue(warp)->smode[cur.stage];
         const int mode = smode & 0xff;
         const uint8_t *sb = S::slice(warp, cur.stage);
+        constexpr int NWE = NE * (int)sizeof(T) / 4;
         if (mode == 0) {
-            constexpr int NW = NE * (int)sizeof(T) / 4;
-            uint32_t wd[NW];
-            const uint4 *p4 = reinterpret_cast<const uint4 *>(S::lane_base(sb, lane));
-            if constexpr ((G::NCH == 2 || G::NCH == 4) && (NW / 4) % G::NCH == 0) {
-                // Group g of NCH words is lane+g's own elements, read with
-                // lane+g's rotation (see read_tile): no bank conflicts.
-                constexpr int NC = G::NCH;
-#pragma unroll
-                for (int g = 0; g < NW / 4 / NC; ++g) {
-                    const int rot = ((lane + g) / (8 / NC)) & (NC - 1);
-                    uint4 u[NC];
-#pragma unroll
-                    for (int c = 0; c < NC; ++c) u[c] = p4[g * NC + ((c + rot) & (NC - 1))];
-#pragma unroll
-                    for (int b = 1; b < NC; b <<= 1) {
-                        if (rot & b) {
-                            uint4 t[NC];
-#pragma unroll
-                            for (int c = 0; c < NC; ++c) t[c] = u[(c - b + NC) & (NC - 1)];
-#pragma unroll
-                            for (int c = 0; c < NC; ++c) u[c] = t[c];
-                        }
-                    }
-#pragma unroll
-                    for (int c = 0; c < NC; ++c) {
-                        const int k = g * NC + c;
-                        wd[4 * k] = u[c].x; wd[4 * k + 1] = u[c].y; wd[4 * k + 2] = u[c].z; wd[4 * k + 3] = u[c].w;
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int c = 0; c < NW / 4; ++c) {
-                    uint4 v = p4[c];
-                    wd[4 * c] = v.x; wd[4 * c + 1] = v.y; wd[4 * c + 2] = v.z; wd[4 * c + 3] = v.w;
-                }
-            }
+            uint32_t wd[NWE];
+            read_words<NWE>(sb, wd);
             R xv[NE];
             ExtractLoop<T, 0, 0, NE>::run(wd, xv);
 #pragma unroll
             for (int i = 0; i < NE; ++i) xm[i] = xn[i] = xv[i];
         } else if (mode == 1 || mode == 4) {
-            const T *pe = reinterpret_cast<const T *>(S::lane_base(sb, lane)) + (smode >> 8);
+            uint32_t wd[NWE + 4];
+            read_words<NWE>(sb, wd);
+            read_tail(sb, NWE, wd + NWE);
+            shift_bytes<NWE>(wd, (smode >> 8) * (int)sizeof(T));
+            R xv[NE];
+            ExtractLoop<T, 0, 0, NE>::run(wd, xv);
 #pragma unroll
-            for (int i = 0; i < NE; ++i) xm[i] = xn[i] = Elem<T>::load(pe[i]);
+            for (int i = 0; i < NE; ++i) xm[i] = xn[i] = xv[i];
             if (mode == 4) clip(ip, x, NE, xm, xn);
         } else if (mode == 3) {
 #pragma unroll
@@ -1476,6 +1537,7 @@ struct Consumer {
     __device__ __forceinline__ void run_slide(const ItemPlan<T> &ip) {
         constexpr int NE = V + G::HALO_MAX;
         constexpr int P2 = W >= 16 ? 16 : (W >= 8 ? 8 : (W >= 4 ? 4 : (W >= 2 ? 2 : 1)));
+        const int vec = out_vec(ip);
         for (int c = 0; c < ip.NC; ++c) {
             R am[NE], an[NE];
             if (!read_tile_ext(ip, c, am, an)) return;
@@ -1490,12 +1552,7 @@ struct Consumer {
                 om[i] = W > P2 ? vmax(am[i], am[i + W - P2]) : am[i];
                 on[i] = W > P2 ? vmin(an[i], an[i + W - P2]) : an[i];
             }
-            const int64_t o0 = ip.o_begin + (int64_t)c * T_ + (int64_t)tid * V;
-            if (o0 < ip.o_end) {
-                const int cnt = o0 + V <= ip.o_end ? V : (int)(ip.o_end - o0);
-                if (ip.omax) store(ip.omax + o0, om, cnt);
-                if (ip.omin) store(ip.omin + o0, on, cnt);
-            }
+            store_out(ip, ip.o_begin + (int64_t)c * T_ + (int64_t)tid * V, om, on, vec);
         }
     }
 
@@ -1606,6 +1663,7 @@ __global__ void __launch_bounds__(Geo<T>::NT, (Geo<T>::NT * Elem<T>::V == 4096 &
         WarpIssue &wi = *S::issue(warp);
         wi.src0 = 0;
         wi.fast_lo = wi.fast_hi = 0;
+        wi.fast_smode = wi.fast_extra = 0;
         wi.in = nullptr;
         wi.n = wi.p0 = 0;
         wi.seq = -1;

@@ -28,6 +28,14 @@ template <typename T>
 cudaError_t blockscan_rows(const LaunchCtx &ctx, const void *in, const SeriesDesc &sd, int64_t rows,
                            int64_t in_pitch, int64_t out_pitch, void *omax, void *omin);
 
+// Batched outputs: each series' outputs start on a 32-byte boundary of the
+// output buffers (whole-sector vector stores); the start after a run of
+// outputs that ends at element `end`.
+inline int64_t batch_out_start(int64_t end, int esz) {
+    const int64_t a = 32 / esz;
+    return (end + a - 1) / a * a;
+}
+
 // Table-driven launch (batched plans): items of one block mode, pulled from
 // an atomic ticket (or round-robin if d_ticket is null).  grid <= 0: one
 // persistent wave.

@@ -75,7 +75,8 @@ extern "C" mmf_status mmf_filter1d_batched_noalloc(const void *d_in, const int64
     const int esz = elem_size(dtype);
     if (esz == 0) return set_error(MMF_EINVAL, "unknown dtype %d", (int)dtype);
 
-    // Series table (packed input and output, in order) and output length.
+    // Series table (inputs packed in order; outputs in order, each series
+    // starting on a 32-byte boundary as in a batch plan) and output length.
     SeriesDesc series[MMF_NOALLOC_MAX_SERIES];
     int64_t in_pos = 0, out_pos = 0, tiles = 0;
     const int64_t T = tile_of(dtype);
@@ -84,9 +85,9 @@ extern "C" mmf_status mmf_filter1d_batched_noalloc(const void *d_in, const int64
         mmf_status st = make_series(h_len[s], h_w[s], mode, dtype, &sd);
         if (st != MMF_OK) return st;
         sd.in_off = in_pos;
-        sd.out_off = out_pos;
+        sd.out_off = batch_out_start(out_pos, esz);
         in_pos += sd.n;
-        out_pos += sd.n_out;
+        out_pos = sd.out_off + sd.n_out;
         tiles += (sd.n_out + T - 1) / T;
         series[s] = sd;
     }

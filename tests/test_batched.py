@@ -31,8 +31,10 @@ def _check_batch(mmf, data, lens, ws, mode="valid", in_offsets=None, dtype=np.fl
     for s in range(len(lens)):
         a = data[starts[s]:starts[s] + lens[s]]
         em, en = oracle.bf1d(a, ws[s]) if mode == "valid" else oracle.envelope(a, ws[s])
-        assert np.array_equal(gm[off[s]:off[s + 1]], em), f"series {s} max (len {lens[s]}, w {ws[s]})"
-        assert np.array_equal(gn[off[s]:off[s + 1]], en), f"series {s} min"
+        # Series s's outputs start on a 32-byte boundary; padding follows.
+        assert off[s] * data.itemsize % 32 == 0 and off[s] + em.size <= off[s + 1]
+        assert np.array_equal(gm[off[s]:off[s] + em.size], em), f"series {s} max (len {lens[s]}, w {ws[s]})"
+        assert np.array_equal(gn[off[s]:off[s] + en.size], en), f"series {s} min"
     # Replay from the cached graph and the plain per-series form agree.
     mx2, mn2 = plan(x)
     pm, pn = plan.per_series(x)

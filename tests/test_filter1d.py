@@ -132,21 +132,43 @@ def test_monotone_and_constant(mmf):
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
-@pytest.mark.parametrize("off", [1, 3, 5])
-def test_unaligned_input_and_output(mmf, dtype, off):
-    """Sub-tensor views whose start is not 16-byte aligned."""
-    a = synth.random_walk(30_000, seed=off, dtype=dtype)
+@pytest.mark.parametrize("off", [1, 2, 3, 5, 7, 13])
+@pytest.mark.parametrize("w,kernel", [(3, "auto"), (3, "blockscan"), (257, "auto"), (1001, "auto"),
+                                      (5000, "auto")])
+def test_unaligned_input_and_output(mmf, dtype, off, w, kernel):
+    """Sub-tensor views whose start is not 16-byte aligned, through each
+    kernel path (register slide, blocks in a thread, across lanes, per warp,
+    tile aggregates): inputs are realigned after the copy and outputs are
+    moved across lanes to whole 16-byte stores.  The offsets reach every
+    distance to the next 16-byte boundary for each type; the elements around
+    the output view stay untouched."""
+    a = synth.random_walk(30_000, seed=off + w, dtype=dtype)
     big = _gpu(a)
     x = big[off:]
-    w = 257
     m = x.numel() - w + 1
-    obuf = torch.empty(m + 8, dtype=x.dtype, device="cuda")
-    nbuf = torch.empty(m + 8, dtype=x.dtype, device="cuda")
-    mmf.filter1d(x, w, out_max=obuf[off:off + m], out_min=nbuf[off:off + m])
+    obuf = torch.zeros(m + 2 * off, dtype=x.dtype, device="cuda")
+    nbuf = torch.zeros(m + 2 * off, dtype=x.dtype, device="cuda")
+    mmf.filter1d(x, w, out_max=obuf[off:off + m], out_min=nbuf[off:off + m], kernel=kernel)
     torch.cuda.synchronize()
     emx, emn = oracle.bf1d(a[off:], w)
-    assert np.array_equal(obuf[off:off + m].cpu().numpy(), emx)
-    assert np.array_equal(nbuf[off:off + m].cpu().numpy(), emn)
+    ob, nb = obuf.cpu().numpy(), nbuf.cpu().numpy()
+    assert np.array_equal(ob[off:off + m], emx)
+    assert np.array_equal(nb[off:off + m], emn)
+    assert not ob[:off].any() and not ob[off + m:].any()
+    assert not nb[:off].any() and not nb[off + m:].any()
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_unaligned_max_only(mmf, dtype):
+    """One output side, not 16-byte aligned."""
+    a = synth.uniform(20_011, seed=3, dtype=dtype)
+    x = _gpu(a)
+    m = x.numel() - 1001 + 1
+    obuf = torch.zeros(m + 1, dtype=x.dtype, device="cuda")
+    mmf.filter1d(x, 1001, out_max=obuf[1:], want_min=False)
+    emx, _ = oracle.bf1d(a, 1001)
+    ob = obuf.cpu().numpy()
+    assert np.array_equal(ob[1:], emx) and ob[0] == 0
 
 
 def test_single_side_outputs(mmf):

@@ -33,8 +33,10 @@ def _noalloc(lib, x, lens, ws, mode, out_len):
     f.restype = ctypes.c_int
     lens = np.ascontiguousarray(lens, dtype=np.int64)
     ws = np.ascontiguousarray(ws, dtype=np.int64)
-    mx = torch.empty(out_len, dtype=x.dtype, device=x.device)
-    mn = torch.empty(out_len, dtype=x.dtype, device=x.device)
+    # Zero-filled like the plan's own buffers: the padding between series
+    # is never written, so both keep zeros there.
+    mx = torch.zeros(out_len, dtype=x.dtype, device=x.device)
+    mn = torch.zeros(out_len, dtype=x.dtype, device=x.device)
     st = f(x.data_ptr(), lens.ctypes.data_as(P64), ws.ctypes.data_as(P64), lens.size,
            {torch.float32: 0, torch.float64: 1}[x.dtype], {"valid": 0, "envelope": 1}[mode],
            mx.data_ptr(), mn.data_ptr(), torch.cuda.current_stream().cuda_stream)
