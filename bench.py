@@ -255,6 +255,21 @@ def batched_extras(dev, stream, peak, reps=5, envelope_series=1_000_000):
         "series": ns, "length": L, "radius": r, "batched_ms": bms, "per_series_ms": pms,
         "batched_over_per_series": pms / bms, "batched_Gelem_s": ns * L / bms / 1e6,
         "batched_GBps": byts / bms / 1e6, "frac": byts / bms / 1e6 / peak, "segments": plan.segments()}
+    # The envelope lower bound of the time-warping distance against one query
+    # (same series and radius): the envelope feeds a per-series sum in the
+    # kernel and is never stored.  Bytes: the series once, the query, one
+    # double per series.
+    qz = torch.cumsum(torch.randn(L, generator=g, device=dev, dtype=torch.float64), 0)
+    qz = ((qz - qz.mean()) / qz.std(unbiased=False)).float()
+    lb = torch.empty(ns, dtype=torch.float64, device=dev)
+    for _ in range(2):
+        plan.lb_keogh(z, qz, out=lb, stream=stream)
+    lms = _events_ms(lambda: plan.lb_keogh(z, qz, out=lb, stream=stream), reps, stream)
+    lbyts = ns * L * 4 + L * 4 + ns * 8
+    out["lb_keogh_f32"] = {
+        "series": ns, "length": L, "radius": r, "ms": lms, "Gelem_s": ns * L / lms / 1e6,
+        "GBps": lbyts / lms / 1e6, "frac": lbyts / lms / 1e6 / peak,
+        "envelope_batch_ms": bms, "envelope_over_lb": bms / lms}
     plan.close()
     return out
 

@@ -185,6 +185,24 @@ mmf_status mmf_batch_plan_autotune(mmf_batch_plan *plan, const void *d_in, void 
 mmf_status mmf_filter1d_batched(mmf_batch_plan *plan, const void *d_in, void *d_max, void *d_min,
                                 void *stream);
 
+/* Lower bound of the dynamic-time-warping distance from a precomputed
+ * max-min envelope (the application the paper's Section 1 cites): for a
+ * plan in MMF_CENTERED_CLIPPED mode whose series all have n_query elements,
+ * with U, L the envelope of radius h_w[s] of series s,
+ *     d_lb[s] = sqrt( sum_i (q_i - U_i)^2 [q_i > U_i] + (L_i - q_i)^2 [q_i < L_i] )
+ * for the query q = d_query (same dtype, device memory).  It is a lower bound
+ * of the time-warping distance of q and series s with warping limited to
+ * |i - j| <= r.  The envelope is never written: each tile's envelope feeds
+ * the sum directly, so the call reads the series once (about a third of the
+ * bytes of the envelope filter followed by a separate reduction).
+ * d_lb: nseries doubles (8-byte aligned).  Arithmetic: f32 series in f32
+ * with a per-warp sum (relative error below 2e-6 of the bound), f64 in
+ * double, i16/u8 exactly in integers; sums over the tiles of one series are
+ * added atomically in double.  MMF_EINVAL for a VALID plan or series of
+ * another length.  Launches directly on `stream` (no graph). */
+mmf_status mmf_lb_keogh_batched(mmf_batch_plan *plan, const void *d_in, const void *d_query, int64_t n_query,
+                                double *d_lb, void *stream);
+
 /* The plain form: one mmf_filter1d launch per series on `stream`, same
  * kernels, no graph (the baseline the batched form is compared with). */
 mmf_status mmf_filter1d_per_series(const mmf_batch_plan *plan, const void *d_in, void *d_max, void *d_min,

@@ -17,6 +17,11 @@ The arithmetic lives in ``mmf_oracle.c`` (plain C, compiled by :func:`build`):
   valid mode (the 2D filter of Section 1, written without separation).
 * :func:`stream_reference` -- the served outputs of a chunked stream are, by
   the definition, the whole-array filter over the concatenated chunks.
+* :func:`lb_keogh` -- the lower bound of the time-warping distance from a
+  precomputed envelope (the application Section 1 cites): a query against
+  a series' centred, end-clipped envelope of radius ``r``, in double.
+* :func:`dtw_band` -- the banded time-warping distance that ``lb_keogh``
+  bounds (a pin for it), by dynamic programming in double.
 
 Python here does marshalling only; no arithmetic of the method is in it.
 """
@@ -53,7 +58,7 @@ def build(force: bool = False) -> str:
             os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC",
-                               "-Wall", "-Wextra", "-o", tmp, _SRC])
+                               "-Wall", "-Wextra", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -73,7 +78,10 @@ def _load():
                 getattr(lib, f"oracle_bf2d_{suf}").argtypes = [_VP, _I64, _I64, _I64, _I64, _I64, _VP, _VP]
                 getattr(lib, f"oracle_bf2d_at_{suf}").argtypes = [_VP, _I64, _I64, _I64, _I64, _I64,
                                                                  _VP, _VP, _I64, _VP, _VP]
-                for name in ("bf1d", "bf1d_at", "wedge", "envelope", "bf2d", "bf2d_at"):
+                getattr(lib, f"oracle_lb_keogh_{suf}").argtypes = [_VP, _VP, _I64, _I64, _VP]
+                getattr(lib, f"oracle_dtw_band_{suf}").argtypes = [_VP, _VP, _I64, _I64, _VP]
+                for name in ("bf1d", "bf1d_at", "wedge", "envelope", "bf2d", "bf2d_at", "lb_keogh",
+                             "dtw_band"):
                     getattr(lib, f"oracle_{name}_{suf}").restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -201,3 +209,26 @@ def stream_reference(chunks, w: int):
     the filter of the concatenation (each output depends only on its
     window, Section 1)."""
     return bf1d(np.concatenate([np.asarray(c) for c in chunks]), w)
+
+
+def lb_keogh(c: np.ndarray, q: np.ndarray, r: int) -> float:
+    """Lower bound of the banded time-warping distance of q and c from the
+    envelope of radius r of c (sqrt of the squared excursions of q outside
+    it), in double."""
+    c = np.ascontiguousarray(c)
+    q = np.ascontiguousarray(q, dtype=c.dtype)
+    if q.size != c.size:
+        raise ValueError("query and series lengths differ")
+    out = ctypes.c_double()
+    _check(_fn("lb_keogh", c.dtype)(_ptr(c), _ptr(q), c.size, r, ctypes.byref(out)), "lb_keogh")
+    return out.value
+
+
+def dtw_band(q: np.ndarray, c: np.ndarray, r: int) -> float:
+    """Time-warping distance of q and c with |i - j| <= r (small n only:
+    n x n doubles)."""
+    q = np.ascontiguousarray(q)
+    c = np.ascontiguousarray(c, dtype=q.dtype)
+    out = ctypes.c_double()
+    _check(_fn("dtw_band", q.dtype)(_ptr(q), _ptr(c), q.size, r, ctypes.byref(out)), "dtw_band")
+    return out.value

@@ -28,6 +28,17 @@
  *             written as the literal maximum/minimum over each wy x wx
  *             rectangle (valid mode), with no separation.
  *   bf2d_at   the same at caller-chosen output pixels.
+ *   lb_keogh  the lower bound of the dynamic-time-warping distance built on a
+ *             precomputed max-min envelope (the application cited in
+ *             Section 1): with U, L the centred, end-clipped envelope of
+ *             radius r of a series c (as in `envelope`) and a query q of
+ *             the same length, sqrt of the sum over i of (q_i - U_i)^2 where
+ *             q_i > U_i and (L_i - q_i)^2 where q_i < L_i, in double.
+ *   dtw_band  the dynamic-time-warping distance of q and c with warping
+ *             restricted to |i - j| <= r: sqrt of the least sum of
+ *             (q_i - c_j)^2 along a monotone path from (0,0) to (n-1,n-1)
+ *             with unit steps, by dynamic programming, in double.  It is the
+ *             quantity lb_keogh bounds from below (used to pin lb_keogh).
  *
  * Every result is one of the input elements, so there is no rounding: all
  * comparisons are the plain C operators on the element type.
@@ -42,6 +53,7 @@
  *     older index is in exactly one of U, L).  The oracle counts the steps
  *     where both fronts were stale and reports it; it must stay zero.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -246,3 +258,55 @@ ORC_DEFINE(f32, float)
 ORC_DEFINE(f64, double)
 ORC_DEFINE(i16, int16_t)
 ORC_DEFINE(u8, uint8_t)
+
+/* The envelope bound and the banded warping distance, in double. */
+#define ORC_DEFINE_LB(SUF, T)                                                     \
+int oracle_lb_keogh_##SUF(const T *c, const T *q, int64_t n, int64_t r,           \
+                          double *out) {                                          \
+    if (n < 0 || r < 0 || !out || (n > 0 && (!c || !q))) return ORC_EINVAL;       \
+    double sum = 0.0;                                                             \
+    for (int64_t i = 0; i < n; ++i) {                                             \
+        int64_t b = i - r < 0 ? 0 : i - r;                                        \
+        int64_t e = i + r > n - 1 ? n - 1 : i + r;                                \
+        T hi = c[b], lw = c[b];                                                   \
+        for (int64_t k = b + 1; k <= e; ++k) {                                    \
+            if (c[k] > hi) hi = c[k];                                             \
+            if (c[k] < lw) lw = c[k];                                             \
+        }                                                                         \
+        double qi = (double)q[i];                                                 \
+        if (qi > (double)hi) sum += (qi - (double)hi) * (qi - (double)hi);        \
+        else if (qi < (double)lw) sum += ((double)lw - qi) * ((double)lw - qi);   \
+    }                                                                             \
+    *out = sqrt(sum);                                                             \
+    return ORC_OK;                                                                \
+}                                                                                 \
+                                                                                  \
+int oracle_dtw_band_##SUF(const T *q, const T *c, int64_t n, int64_t r,           \
+                          double *out) {                                          \
+    if (n < 1 || r < 0 || !out || !q || !c) return ORC_EINVAL;                    \
+    double *D = (double *)malloc((size_t)(n * n) * sizeof(double));               \
+    if (!D) return ORC_ENOMEM;                                                    \
+    for (int64_t i = 0; i < n; ++i)                                               \
+        for (int64_t j = 0; j < n; ++j) {                                         \
+            if (i - j > r || j - i > r) { D[i * n + j] = INFINITY; continue; }    \
+            double d = (double)q[i] - (double)c[j];                               \
+            double best;                                                          \
+            if (i == 0 && j == 0) best = 0.0;                                     \
+            else {                                                                \
+                best = INFINITY;                                                  \
+                if (i > 0 && D[(i - 1) * n + j] < best) best = D[(i - 1) * n + j];\
+                if (j > 0 && D[i * n + j - 1] < best) best = D[i * n + j - 1];    \
+                if (i > 0 && j > 0 && D[(i - 1) * n + j - 1] < best)              \
+                    best = D[(i - 1) * n + j - 1];                                \
+            }                                                                     \
+            D[i * n + j] = best + d * d;                                          \
+        }                                                                         \
+    *out = sqrt(D[n * n - 1]);                                                    \
+    free(D);                                                                      \
+    return ORC_OK;                                                                \
+}
+
+ORC_DEFINE_LB(f32, float)
+ORC_DEFINE_LB(f64, double)
+ORC_DEFINE_LB(i16, int16_t)
+ORC_DEFINE_LB(u8, uint8_t)

@@ -87,6 +87,7 @@ _EXTRA_SIGNATURES: dict = {
     "mmf_batch_plan_autotune": ([_VP, _VP, _VP, _VP, _VP], _INT),
     "mmf_filter1d_batched": ([_VP, _VP, _VP, _VP, _VP], _INT),
     "mmf_filter1d_per_series": ([_VP, _VP, _VP, _VP, _VP], _INT),
+    "mmf_lb_keogh_batched": ([_VP, _VP, _VP, _I64, _VP, _VP], _INT),
     "mmf_server_create": ([ctypes.c_size_t, _INT, _INT, ctypes.POINTER(_VP)], _INT),
     "mmf_server_destroy": ([_VP], None),
     "mmf_stream_open": ([_VP, _I64, ctypes.POINTER(ctypes.c_uint64)], _INT),
@@ -230,6 +231,23 @@ class BatchPlan:
             check(self._lib.mmf_filter1d_per_series(self._h, _ptr(x), _ptr(out_max), _ptr(out_min),
                                                     _VP(_stream_handle(stream))))
         return out_max, out_min
+
+    def lb_keogh(self, x, query, out=None, stream=None):
+        """Lower bound of the time-warping distance of ``query`` and every
+        series from the series' envelope (an envelope plan whose series all
+        have the query's length): float64 tensor of nseries."""
+        _check_tensor(x, "x")
+        _check_tensor(query, "query")
+        if query.dtype != self.dtype or x.dtype != self.dtype:
+            raise ValueError(f"x and query must be {self.dtype}")
+        if out is None:
+            out = torch.empty(self.nseries, dtype=torch.float64, device=x.device)
+        elif out.dtype != torch.float64 or out.numel() < self.nseries:
+            raise ValueError(f"out must hold {self.nseries} float64 values")
+        with torch.cuda.device(x.device):
+            check(self._lib.mmf_lb_keogh_batched(self._h, _ptr(x), _ptr(query), query.numel(), _ptr(out),
+                                                 _VP(_stream_handle(stream))))
+        return out
 
     def autotune(self, x, out_max=None, out_min=None, stream=None):
         out_max, out_min = self._outs(x, out_max, out_min)

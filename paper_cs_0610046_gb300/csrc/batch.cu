@@ -61,9 +61,14 @@ struct mmf_batch_plan {
     int64_t nseries = 0;
     int64_t in_len = 0;   // elements the input buffer must hold
     int64_t out_len = 0;  // elements each output buffer must hold
+    int64_t common_len = -1;  // the length every series has (-1 if they differ)
     std::vector<SeriesDesc> series;
     std::vector<int64_t> out_off;  // nseries + 1
     Group groups[kModes];
+    std::vector<int64_t> short_ids;  // series taken by the warp-per-series kernel
+    int64_t *d_short = nullptr;
+    cudaStream_t short_branch = nullptr;
+    cudaEvent_t short_join = nullptr;
     SeriesDesc *d_series = nullptr;
     int *d_tickets = nullptr;  // one per group
     cudaStream_t cap_stream = nullptr;
@@ -76,6 +81,10 @@ struct mmf_batch_plan {
 };
 
 namespace {
+
+bool is_short(const mmf_batch_plan *p, const SeriesDesc &sd) {
+    return sd.n_out > 0 && sd.n <= short_max_len(elem_size(p->dtype));
+}
 
 void free_items(mmf_batch_plan *p) {
     for (auto &g : p->groups) {
@@ -95,7 +104,7 @@ mmf_status build_items(mmf_batch_plan *p, int gi) {
     const int64_t seg = (int64_t)std::max(1, g.seg_tiles) * T;
     for (int64_t s = 0; s < p->nseries; ++s) {
         const SeriesDesc &sd = p->series[s];
-        if (sd.n_out <= 0 || kernel_mode(p->dtype, sd.w) != g.mode) continue;
+        if (sd.n_out <= 0 || is_short(p, sd) || kernel_mode(p->dtype, sd.w) != g.mode) continue;
         for (int64_t ob = 0; ob < sd.n_out; ob += seg) g.items.push_back({s, ob, std::min(sd.n_out, ob + seg)});
     }
     std::stable_sort(g.items.begin(), g.items.end(), [&](const ItemDesc &a, const ItemDesc &b) {
@@ -114,17 +123,17 @@ mmf_status build_items(mmf_batch_plan *p, int gi) {
 }
 
 mmf_status launch_group(mmf_batch_plan *p, int gi, const LaunchCtx &ctx, const void *in, void *omax, void *omin,
-                        bool ticket) {
+                        bool ticket, const void *lb_query = nullptr, double *lb_acc = nullptr) {
     Group &g = p->groups[gi];
     if (g.items.empty()) return MMF_OK;
     int *tk = ticket ? p->d_tickets + gi : nullptr;
     cudaError_t e = cudaSuccess;
     const int64_t ni = (int64_t)g.items.size();
     switch (p->dtype) {
-        case MMF_F32: e = blockscan_table<float>(ctx, g.mode, in, p->in_len, omax, omin, p->d_series, g.d_items, ni, tk, 0); break;
-        case MMF_F64: e = blockscan_table<double>(ctx, g.mode, in, p->in_len, omax, omin, p->d_series, g.d_items, ni, tk, 0); break;
-        case MMF_I16: e = blockscan_table<int16_t>(ctx, g.mode, in, p->in_len, omax, omin, p->d_series, g.d_items, ni, tk, 0); break;
-        case MMF_U8: e = blockscan_table<uint8_t>(ctx, g.mode, in, p->in_len, omax, omin, p->d_series, g.d_items, ni, tk, 0); break;
+        case MMF_F32: e = blockscan_table<float>(ctx, g.mode, in, p->in_len, omax, omin, p->d_series, g.d_items, ni, tk, 0, lb_query, lb_acc); break;
+        case MMF_F64: e = blockscan_table<double>(ctx, g.mode, in, p->in_len, omax, omin, p->d_series, g.d_items, ni, tk, 0, lb_query, lb_acc); break;
+        case MMF_I16: e = blockscan_table<int16_t>(ctx, g.mode, in, p->in_len, omax, omin, p->d_series, g.d_items, ni, tk, 0, lb_query, lb_acc); break;
+        case MMF_U8: e = blockscan_table<uint8_t>(ctx, g.mode, in, p->in_len, omax, omin, p->d_series, g.d_items, ni, tk, 0, lb_query, lb_acc); break;
     }
     return e == cudaSuccess ? MMF_OK : cuda_error(e, "batched launch");
 }
@@ -132,7 +141,8 @@ mmf_status launch_group(mmf_batch_plan *p, int gi, const LaunchCtx &ctx, const v
 // Ticket resets on `st`, then one persistent launch per non-empty group, each
 // on its own branch stream (fork/join by events) so that a group's tail
 // overlaps the next group's work.
-mmf_status enqueue_all(mmf_batch_plan *p, cudaStream_t st, const void *in, void *omax, void *omin) {
+mmf_status enqueue_all(mmf_batch_plan *p, cudaStream_t st, const void *in, void *omax, void *omin,
+                       const void *lb_query = nullptr, double *lb_acc = nullptr) {
     LaunchCtx ctx;
     mmf_status s = get_ctx(st, &ctx);
     if (s != MMF_OK) return s;
@@ -146,10 +156,27 @@ mmf_status enqueue_all(mmf_batch_plan *p, cudaStream_t st, const void *in, void 
         if (e != cudaSuccess) return cuda_error(e, "branch wait");
         LaunchCtx bctx = ctx;
         bctx.stream = p->branch[gi];
-        s = launch_group(p, gi, bctx, in, omax, omin, true);
+        s = launch_group(p, gi, bctx, in, omax, omin, true, lb_query, lb_acc);
         if (s != MMF_OK) return s;
         e = cudaEventRecord(p->join[gi], p->branch[gi]);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, p->join[gi], 0);
+        if (e != cudaSuccess) return cuda_error(e, "join");
+    }
+    if (!p->short_ids.empty()) {
+        e = cudaStreamWaitEvent(p->short_branch, p->fork, 0);
+        if (e != cudaSuccess) return cuda_error(e, "branch wait");
+        LaunchCtx bctx = ctx;
+        bctx.stream = p->short_branch;
+        const int64_t cnt = (int64_t)p->short_ids.size();
+        switch (p->dtype) {
+            case MMF_F32: e = short_table<float>(bctx, in, p->in_len, omax, omin, p->d_series, p->d_short, cnt, lb_query, lb_acc); break;
+            case MMF_F64: e = short_table<double>(bctx, in, p->in_len, omax, omin, p->d_series, p->d_short, cnt, lb_query, lb_acc); break;
+            case MMF_I16: e = short_table<int16_t>(bctx, in, p->in_len, omax, omin, p->d_series, p->d_short, cnt, lb_query, lb_acc); break;
+            case MMF_U8: e = short_table<uint8_t>(bctx, in, p->in_len, omax, omin, p->d_series, p->d_short, cnt, lb_query, lb_acc); break;
+        }
+        if (e != cudaSuccess) return cuda_error(e, "short-series launch");
+        e = cudaEventRecord(p->short_join, p->short_branch);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, p->short_join, 0);
         if (e != cudaSuccess) return cuda_error(e, "join");
     }
     return MMF_OK;
@@ -166,6 +193,17 @@ mmf_status capture(mmf_batch_plan *p, const void *in, void *omax, void *omin) {
             case MMF_F64: pe = blockscan_prepare<double>(p->device, gi); break;
             case MMF_I16: pe = blockscan_prepare<int16_t>(p->device, gi); break;
             case MMF_U8: pe = blockscan_prepare<uint8_t>(p->device, gi); break;
+        }
+        if (pe != cudaSuccess) return cuda_error(pe, "prepare kernels");
+    }
+    if (!p->short_ids.empty()) {
+        int k = 0;
+        cudaError_t pe = cudaSuccess;
+        switch (p->dtype) {
+            case MMF_F32: pe = short_prepare<float>(p->device, false, &k); break;
+            case MMF_F64: pe = short_prepare<double>(p->device, false, &k); break;
+            case MMF_I16: pe = short_prepare<int16_t>(p->device, false, &k); break;
+            case MMF_U8: pe = short_prepare<uint8_t>(p->device, false, &k); break;
         }
         if (pe != cudaSuccess) return cuda_error(pe, "prepare kernels");
     }
@@ -189,6 +227,17 @@ mmf_status capture(mmf_batch_plan *p, const void *in, void *omax, void *omin) {
     p->g_max = omax;
     p->g_min = omin;
     return MMF_OK;
+}
+
+// Envelope lower bound: accumulators cleared before the launches, square
+// roots taken after them.
+__global__ void lb_clear_kernel(double *acc, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc[i] = 0.0;
+}
+__global__ void lb_sqrt_kernel(double *acc, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc[i] = sqrt(acc[i]);
 }
 
 // Autotune cache: one line "key seg_tiles" per entry in $MMF_AUTOTUNE_CACHE.
@@ -274,6 +323,9 @@ mmf_status mmf_batch_plan_create(const int64_t *h_in_off, const int64_t *h_len, 
     }
     p->out_off[nseries] = out_pos;
     p->out_len = out_pos;
+    p->common_len = nseries > 0 ? p->series[0].n : 0;
+    for (int64_t s = 1; s < nseries; ++s)
+        if (p->series[s].n != p->common_len) p->common_len = -1;
     for (int gi = 0; gi < kModes; ++gi) {
         p->groups[gi].mode = gi;
         p->groups[gi].seg_tiles = gi == 2 ? 32 : 16;
@@ -288,6 +340,16 @@ mmf_status mmf_batch_plan_create(const int64_t *h_in_off, const int64_t *h_len, 
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->join[gi], cudaEventDisableTiming);
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->short_branch, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->short_join, cudaEventDisableTiming);
+    for (int64_t s = 0; s < nseries; ++s)
+        if (is_short(p, p->series[s])) p->short_ids.push_back(s);
+    if (e == cudaSuccess && !p->short_ids.empty()) {
+        e = cudaMalloc(&p->d_short, p->short_ids.size() * sizeof(int64_t));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(p->d_short, p->short_ids.data(), p->short_ids.size() * sizeof(int64_t),
+                           cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         mmf_batch_plan_destroy(p);
         return set_error(MMF_ENOMEM, "plan device tables: %s", cudaGetErrorString(e));
@@ -323,6 +385,9 @@ void mmf_batch_plan_destroy(mmf_batch_plan *p) {
         if (p->join[gi]) cudaEventDestroy(p->join[gi]);
     }
     if (p->fork) cudaEventDestroy(p->fork);
+    if (p->d_short) cudaFree(p->d_short);
+    if (p->short_branch) cudaStreamDestroy(p->short_branch);
+    if (p->short_join) cudaEventDestroy(p->short_join);
     delete p;
 }
 
@@ -362,6 +427,43 @@ mmf_status mmf_filter1d_batched(mmf_batch_plan *p, const void *d_in, void *d_max
     }
     cudaError_t e = cudaGraphLaunch(p->exec, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? MMF_OK : cuda_error(e, "graph launch");
+}
+
+mmf_status mmf_lb_keogh_batched(mmf_batch_plan *p, const void *d_in, const void *d_query, int64_t n_query,
+                                double *d_lb, void *stream) {
+    if (!p) return set_error(MMF_EINVAL, "NULL plan");
+    if (p->mode != MMF_CENTERED_CLIPPED) return set_error(MMF_EINVAL, "the lower bound needs an envelope plan");
+    if (p->nseries == 0) return MMF_OK;
+    if (p->common_len < 0 || p->common_len != n_query)
+        return set_error(MMF_EINVAL, "every series must be as long as the query (%lld)", (long long)n_query);
+    const int esz = elem_size(p->dtype);
+    if (!d_lb || (n_query > 0 && (!d_in || !d_query))) return set_error(MMF_EINVAL, "NULL buffers");
+    if (((uintptr_t)d_in % esz) || ((uintptr_t)d_query % esz) || ((uintptr_t)d_lb % 8))
+        return set_error(MMF_EINVAL, "misaligned pointer");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    LaunchCtx ctx;
+    mmf_status s = get_ctx(stream, &ctx);
+    if (s != MMF_OK) return s;
+    const int nb = (int)std::min<int64_t>((p->nseries + 255) / 256, 4 * std::max(1, ctx.sms));
+    lb_clear_kernel<<<nb, 256, 0, st>>>(d_lb, p->nseries);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "clear bounds");
+    for (int gi = 0; gi < kModes; ++gi) {
+        if (p->groups[gi].items.empty()) continue;
+        cudaError_t pe = cudaSuccess;
+        switch (p->dtype) {
+            case MMF_F32: pe = blockscan_prepare<float>(p->device, gi); break;
+            case MMF_F64: pe = blockscan_prepare<double>(p->device, gi); break;
+            case MMF_I16: pe = blockscan_prepare<int16_t>(p->device, gi); break;
+            case MMF_U8: pe = blockscan_prepare<uint8_t>(p->device, gi); break;
+        }
+        if (pe != cudaSuccess) return cuda_error(pe, "prepare kernels");
+    }
+    s = enqueue_all(p, st, d_in, nullptr, nullptr, d_query, d_lb);
+    if (s != MMF_OK) return s;
+    lb_sqrt_kernel<<<nb, 256, 0, st>>>(d_lb, p->nseries);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? MMF_OK : cuda_error(e, "square roots");
 }
 
 mmf_status mmf_filter1d_per_series(const mmf_batch_plan *p, const void *d_in, void *d_max, void *d_min,

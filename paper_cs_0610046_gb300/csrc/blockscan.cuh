@@ -93,6 +93,14 @@ template <> struct Elem<uint8_t> {
     __device__ static uint8_t store(R x) { return (uint8_t)x; }
 };
 
+// Arithmetic of the envelope lower bound per element type: f32 in float
+// (rounding bounded in the design notes), f64 in double, the integer types
+// exactly in 64-bit integers.
+template <typename T> struct LbAcc { using A = float; };
+template <> struct LbAcc<double> { using A = double; };
+template <> struct LbAcc<int16_t> { using A = long long; };
+template <> struct LbAcc<uint8_t> { using A = long long; };
+
 __device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
 __device__ __forceinline__ long long vmax(long long a, long long b) { return a > b ? a : b; }
@@ -210,7 +218,13 @@ struct BlockScanParams {
     int *ticket;               // nullptr: static round-robin; else atomic ticket
     uint32_t *status;          // device status word
     int64_t in_elems;          // elements of `in` that may be read (copies past a series end stay inside)
+    // Envelope lower bound (batched, centred windows): when lb_acc is set, no
+    // outputs are stored; each output i of series s instead adds the squared
+    // excursion of lb_query[i] outside [min, max] to lb_acc[s].
+    const void *lb_query;
+    double *lb_acc;
 };
+static_assert(sizeof(BlockScanParams) <= 256, "parameters are copied to a 256-byte shared slot");
 
 constexpr int kStages = 4;             // per-warp slice stages (power of two)
 constexpr int kQCap = 1024 + 8;        // tile-aggregate ring (>= max tiles per window + 2)
@@ -326,6 +340,7 @@ template <typename T> struct Smem {
 
 // Per-item quantities, computed identically by thread 0 and the consumers.
 template <typename T> struct ItemPlan {
+    int64_t series;  // index in the series table (0 without one)
     const T *in;
     T *omax;
     T *omin;
@@ -350,8 +365,10 @@ __device__ __forceinline__ ItemPlan<T> make_plan(const BlockScanParams &P, int64
     ItemPlan<T> ip;
     SeriesDesc sd;
     int64_t ob, oe;
+    ip.series = 0;
     if (P.items) {
         ItemDesc it = P.items[item];
+        ip.series = it.series;
         sd = P.series[it.series];
         ob = it.o_begin;
         oe = it.o_end;
@@ -995,6 +1012,10 @@ struct Consumer {
     // o_end).  Every lane of the warp calls it (vec from out_vec).
     __device__ __forceinline__ void store_out(const ItemPlan<T> &ip, int64_t o0, const R (&om)[V], const R (&on)[V],
                                               int vec) const {
+        if (S::params().lb_acc) {
+            lb_out(ip, o0, om, on);
+            return;
+        }
         const bool full = o0 + V <= ip.o_end;
         const bool wfull = __all_sync(0xffffffffu, full);
         if (vec && full) {
@@ -1015,6 +1036,44 @@ struct Consumer {
             if (ip.omax) store(ip.omax + o0, om, cnt);
             if (ip.omin) store(ip.omin + o0, on, cnt);
         }
+    }
+
+    // Envelope lower bound: this thread's outputs o0 .. o0+V-1 (before o_end)
+    // are the upper and lower envelope at series positions o0 + i; the
+    // squared excursions of the query there are summed over the warp and
+    // added to the series' accumulator (one atomic per warp and tile).
+    __device__ __forceinline__ void lb_out(const ItemPlan<T> &ip, int64_t o0, const R (&om)[V],
+                                           const R (&on)[V]) const {
+        using A = typename LbAcc<T>::A;
+        const T *q = reinterpret_cast<const T *>(S::params().lb_query) + o0;
+        A part = A(0);
+        if (o0 + V <= ip.o_end && (((uintptr_t)q) & 15) == 0) {
+            // A whole run with an aligned query: 16-byte loads.
+            T qv[V];
+#pragma unroll
+            for (int c = 0; c < V * (int)sizeof(T) / 16; ++c)
+                reinterpret_cast<uint4 *>(qv)[c] = __ldg(reinterpret_cast<const uint4 *>(q) + c);
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const A qi = (A)qv[i];
+                const A u = (A)Elem<T>::store(om[i]), l = (A)Elem<T>::store(on[i]);
+                const A d = qi > u ? qi - u : (qi < l ? l - qi : A(0));
+                part += d * d;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                if (o0 + i < ip.o_end) {
+                    const A qi = (A)__ldg(q + i);
+                    const A u = (A)Elem<T>::store(om[i]), l = (A)Elem<T>::store(on[i]);
+                    const A d = qi > u ? qi - u : (qi < l ? l - qi : A(0));
+                    part += d * d;
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 16; k >= 1; k >>= 1) part += __shfl_xor_sync(0xffffffffu, part, k);
+        if (lane == 0 && part != A(0)) atomicAdd(S::params().lb_acc + ip.series, (double)part);
     }
 
     // A whole warp span of outputs (every lane V values at dst, lanes V

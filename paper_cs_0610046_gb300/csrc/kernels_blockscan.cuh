@@ -1,6 +1,7 @@
 // Host launchers of the block-scan kernel, instantiated once per dtype.
 #pragma once
 #include "launch.h"
+#include "short.cuh"
 
 namespace mmf {
 
@@ -132,7 +133,7 @@ cudaError_t blockscan_rows(const LaunchCtx &ctx, const void *in, const SeriesDes
 template <typename T>
 cudaError_t blockscan_table(const LaunchCtx &ctx, int mode, const void *in, int64_t in_elems, void *omax,
                             void *omin, const SeriesDesc *d_series, const ItemDesc *d_items, int64_t n_items,
-                            int *d_ticket, int grid) {
+                            int *d_ticket, int grid, const void *lb_query, double *lb_acc) {
     if (n_items <= 0) return cudaSuccess;
     int per_sm = 1;
     cudaError_t e = prepare_mode<T>(mode, ctx.device, &per_sm);
@@ -149,6 +150,8 @@ cudaError_t blockscan_table(const LaunchCtx &ctx, int mode, const void *in, int6
     P.ticket = d_ticket;
     P.status = ctx.status;
     P.in_elems = in_elems;
+    P.lb_query = lb_query;
+    P.lb_acc = lb_acc;
     launch_mode<T>(mode, P, grid, ctx.stream);
     return cudaGetLastError();
 }
@@ -163,5 +166,9 @@ cudaError_t blockscan_table(const LaunchCtx &ctx, int mode, const void *in, int6
     template cudaError_t mmf::blockscan_1d<T>(const LaunchCtx &, const void *, const SeriesDesc &, void *,      \
                                                void *, bool);                                                   \
     template cudaError_t mmf::blockscan_table<T>(const LaunchCtx &, int, const void *, int64_t, void *, void *, \
-                                                  const SeriesDesc *, const ItemDesc *, int64_t, int *, int); \
-    template int mmf::block_mode<T>(int64_t, bool);
+                                                  const SeriesDesc *, const ItemDesc *, int64_t, int *, int,    \
+                                                  const void *, double *);                                      \
+    template int mmf::block_mode<T>(int64_t, bool);                                                            \
+    template cudaError_t mmf::short_table<T>(const LaunchCtx &, const void *, int64_t, void *, void *,         \
+                                              const SeriesDesc *, const int64_t *, int64_t, const void *, double *); \
+    template cudaError_t mmf::short_prepare<T>(int, bool, int *);

@@ -28,6 +28,20 @@ template <typename T>
 cudaError_t blockscan_rows(const LaunchCtx &ctx, const void *in, const SeriesDesc &sd, int64_t rows,
                            int64_t in_pitch, int64_t out_pitch, void *omax, void *omin);
 
+// Short series (batched plans): at most this many elements take the
+// warp-per-series kernel (32 lanes x 32 elements; 16 for 8-byte types).
+constexpr int64_t short_max_len(int esz) { return esz == 8 ? 512 : 1024; }
+
+// Warp-per-series launch over the series d_ids[0..count) of the table;
+// lb_acc (with lb_query): the envelope lower bound instead of outputs (each
+// series' sum is written, not added).
+template <typename T>
+cudaError_t short_table(const LaunchCtx &ctx, const void *in, int64_t in_elems, void *omax, void *omin,
+                        const SeriesDesc *d_series, const int64_t *d_ids, int64_t count, const void *lb_query,
+                        double *lb_acc);
+// Kernel attributes of the short-series kernel (outside any stream capture).
+template <typename T> cudaError_t short_prepare(int device, bool lb, int *per_sm);
+
 // Batched outputs: each series' outputs start on a 32-byte boundary of the
 // output buffers (whole-sector vector stores); the start after a run of
 // outputs that ends at element `end`.
@@ -40,11 +54,13 @@ inline int64_t batch_out_start(int64_t end, int esz) {
 // an atomic ticket (or round-robin if d_ticket is null).  grid <= 0: one
 // persistent wave.
 // in_elems: elements of `in` that may be read (the whole input buffer; copies
-// that cross a series end stay inside it).
+// that cross a series end stay inside it).  lb_acc (with lb_query): instead of
+// storing outputs, add each series' squared query excursions outside its
+// envelope to lb_acc[series].
 template <typename T>
 cudaError_t blockscan_table(const LaunchCtx &ctx, int mode, const void *in, int64_t in_elems, void *omax,
                             void *omin, const SeriesDesc *d_series, const ItemDesc *d_items, int64_t n_items,
-                            int *d_ticket, int grid);
+                            int *d_ticket, int grid, const void *lb_query = nullptr, double *lb_acc = nullptr);
 
 // Chunked monotonic wedge (Algorithm 1 per thread chunk), valid windows,
 // w <= MMF_WEDGE_MAX_WINDOW.

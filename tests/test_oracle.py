@@ -288,3 +288,62 @@ def test_stream_reference_is_concatenation():
     mx, mn = oracle.stream_reference(chunks, 64)
     bmx, bmn = oracle.bf1d(a, 64)
     assert np.array_equal(mx, bmx) and np.array_equal(mn, bmn)
+
+
+# ------------------------------------------------ envelope lower bound (DTW)
+
+def test_lb_keogh_worked_example():
+    """Hand-computed: series c = (1, 1, 1), query q = (0, 5, 0), r = 1.  The
+    envelope of c is U = L = (1, 1, 1); q leaves it by 1, 4 and 1, so the
+    bound is sqrt(1 + 16 + 1).  With the roles swapped (the envelope of q,
+    U = (5, 5, 5), L = (0, 0, 0)) every c_i lies inside and the bound is 0:
+    the envelope belongs to the series, the excursions to the query."""
+    c = np.array([1, 1, 1], np.float64)
+    q = np.array([0, 5, 0], np.float64)
+    assert oracle.lb_keogh(c, q, 1) == np.sqrt(18.0)
+    assert oracle.lb_keogh(q, c, 1) == 0.0
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64, np.int16, np.uint8])
+def test_lb_keogh_radius_zero_is_euclidean(dtype):
+    """r = 0: the envelope is the series itself, so the bound is the plain
+    Euclidean distance (a textbook formula, computed here with numpy)."""
+    for n in (1, 2, 17, 300):
+        c = synth.uniform(n, seed=n, dtype=dtype)
+        q = synth.uniform(n, seed=n + 1, dtype=dtype)
+        e = np.sqrt(((q.astype(np.float64) - c.astype(np.float64)) ** 2).sum())
+        assert abs(oracle.lb_keogh(c, q, 0) - e) <= 1e-12 * max(1.0, e)
+        assert abs(oracle.dtw_band(q, c, 0) - e) <= 1e-12 * max(1.0, e)
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64, np.int16])
+def test_lb_keogh_below_banded_dtw(dtype):
+    """The bound never exceeds the time-warping distance with the same band
+    (brute-force dynamic programming on small series), for any radius; the
+    banded distance only falls as the band widens, and a query inside the
+    envelope (the series itself, or halfway between U and L) gives 0."""
+    for seed in range(12):
+        n = 5 + 7 * seed
+        c = synth.random_walk(n, seed=seed, dtype=dtype)
+        q = synth.random_walk(n, seed=100 + seed, dtype=dtype)
+        prev = None
+        for r in (0, 1, 2, 4, n):
+            lb = oracle.lb_keogh(c, q, r)
+            d = oracle.dtw_band(q, c, r)
+            assert lb <= d * (1 + 1e-12) + 1e-12
+            if prev is not None:
+                assert d <= prev * (1 + 1e-12) + 1e-12
+            prev = d
+            assert oracle.lb_keogh(c, c, r) == 0.0
+            up, lo = oracle.envelope(c, r)
+            mid = ((up.astype(np.float64) + lo.astype(np.float64)) / 2).astype(dtype)
+            assert oracle.lb_keogh(c, mid, r) == 0.0
+
+
+def test_lb_keogh_is_monotone_in_radius():
+    """A wider radius widens the envelope, so the bound can only fall."""
+    c = synth.random_walk(400, seed=5, dtype=np.float64)
+    q = synth.random_walk(400, seed=6, dtype=np.float64)
+    vals = [oracle.lb_keogh(c, q, r) for r in (0, 1, 3, 10, 50, 399)]
+    assert all(b <= a for a, b in zip(vals, vals[1:]))
+    assert vals[0] > vals[-1] >= 0.0
