@@ -103,6 +103,17 @@ mmf_status mmf_filter1d_ex(const void *d_in, int64_t n, int64_t w_or_r, mmf_dtyp
                            mmf_mode mode, void *d_max, void *d_min, void *stream,
                            mmf_kernel kernel);
 
+/* Arg-max / arg-min filter (Section 5: the streaming algorithm stores the
+ * locations of the extremes, so their positions come at no extra cost):
+ * for every valid window [j, j+w), d_argmax[j] / d_argmin[j] is the position
+ * in the array (int64) of its maximum / minimum, the leftmost among equal
+ * values, and d_max / d_min the values; any output may be NULL (not all).
+ * n-w+1 outputs each, computed by the chunked-wedge kernel with ties kept in
+ * the deques, so w <= MMF_WEDGE_MAX_WINDOW (MMF_ENOTIMPL beyond).  Pointers:
+ * element-aligned values, 8-byte aligned positions. */
+mmf_status mmf_argfilter1d(const void *d_in, int64_t n, int64_t w, mmf_dtype dtype, void *d_max, void *d_min,
+                           int64_t *d_argmax, int64_t *d_argmin, void *stream);
+
 /* Number of outputs of one side for (n, w_or_r, mode); -1 if invalid. */
 int64_t mmf_output_length(int64_t n, int64_t w_or_r, mmf_mode mode);
 
@@ -276,6 +287,28 @@ mmf_status mmf_ticket_wait_batch(mmf_server *server, int64_t count, const uint64
 /* Refuses further pushes, waits up to timeout_ms for the stream's chunks,
  * frees its state (MMF_ETIMEOUT leaves it closed but not yet freed). */
 mmf_status mmf_stream_close(mmf_server *server, uint64_t stream_id, int timeout_ms);
+
+/* Stream state snapshot, a checkpoint of one stream: its window, its 64-bit
+ * sample count (streams are unbounded; positions are 64-bit as Section 5
+ * recommends for streams) and its last min(count, w-1) samples, which are all
+ * that later outputs depend on (each output depends on its window only,
+ * Section 1).  Waits up to timeout_ms for the stream's queued and in-flight
+ * chunks (MMF_ETIMEOUT otherwise); the caller must not push to the stream
+ * during the call.  Layout, little-endian: uint32 magic 0x53464d4d ("MMFS"),
+ * uint32 version 1, int32 dtype, int32 0, int64 w, int64 count, int64 halo
+ * length h, then h samples of the dtype (oldest first).  *size receives the
+ * bytes of the snapshot; with h_buf NULL only the size is reported, else
+ * buf_bytes must hold it (MMF_EINVAL). */
+#define MMF_SNAPSHOT_MAGIC 0x53464d4du
+#define MMF_SNAPSHOT_HEADER_BYTES 40
+mmf_status mmf_stream_snapshot(mmf_server *server, uint64_t stream_id, void *h_buf, size_t buf_bytes, size_t *size,
+                               int timeout_ms);
+
+/* Opens a new stream in the state of a snapshot (from this server or another
+ * of the same dtype): its later pushes give exactly the outputs the original
+ * stream would have given.  MMF_EINVAL for another dtype, a bad header or a
+ * short buffer; MMF_ENOMEM if the budget has no room for its state. */
+mmf_status mmf_stream_restore(mmf_server *server, const void *h_buf, size_t buf_bytes, uint64_t *stream_id);
 
 /* Stops (1) or resumes (0) admissions: for tests of stalled service. */
 mmf_status mmf_server_pause(mmf_server *server, int paused);

@@ -22,6 +22,11 @@ The arithmetic lives in ``mmf_oracle.c`` (plain C, compiled by :func:`build`):
   a series' centred, end-clipped envelope of radius ``r``, in double.
 * :func:`dtw_band` -- the banded time-warping distance that ``lb_keogh``
   bounds (a pin for it), by dynamic programming in double.
+* :func:`argbf1d` -- the locations of every window's maximum and minimum
+  (leftmost among equals), by scanning each window (Section 5's
+  arg-max/arg-min filter).
+* :func:`w3` -- the window-3 filter of the proposition following Section 3's
+  lower bound, in at most 2 comparisons per element (counted).
 
 Python here does marshalling only; no arithmetic of the method is in it.
 """
@@ -80,8 +85,10 @@ def _load():
                                                                  _VP, _VP, _I64, _VP, _VP]
                 getattr(lib, f"oracle_lb_keogh_{suf}").argtypes = [_VP, _VP, _I64, _I64, _VP]
                 getattr(lib, f"oracle_dtw_band_{suf}").argtypes = [_VP, _VP, _I64, _I64, _VP]
+                getattr(lib, f"oracle_w3_{suf}").argtypes = [_VP, _I64, _VP, _VP, _VP]
+                getattr(lib, f"oracle_argbf1d_{suf}").argtypes = [_VP, _I64, _I64, _VP, _VP]
                 for name in ("bf1d", "bf1d_at", "wedge", "envelope", "bf2d", "bf2d_at", "lb_keogh",
-                             "dtw_band"):
+                             "dtw_band", "w3", "argbf1d"):
                     getattr(lib, f"oracle_{name}_{suf}").restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -232,3 +239,26 @@ def dtw_band(q: np.ndarray, c: np.ndarray, r: int) -> float:
     out = ctypes.c_double()
     _check(_fn("dtw_band", q.dtype)(_ptr(q), _ptr(c), q.size, r, ctypes.byref(out)), "dtw_band")
     return out.value
+
+
+def w3(a: np.ndarray):
+    """Window-3 max and min in at most 2 comparisons per element: returns
+    (max, min, comparisons)."""
+    a = np.ascontiguousarray(a)
+    m = n_out(a.size, 3)
+    mx = np.empty(m, a.dtype)
+    mn = np.empty(m, a.dtype)
+    c = ctypes.c_int64()
+    _check(_fn("w3", a.dtype)(_ptr(a), a.size, _ptr(mx), _ptr(mn), ctypes.byref(c)), "w3")
+    return mx, mn, c.value
+
+
+def argbf1d(a: np.ndarray, w: int):
+    """Positions of the maximum and minimum of every window [j, j+w), the
+    leftmost among equal values (int64 arrays of n-w+1)."""
+    a = np.ascontiguousarray(a)
+    m = n_out(a.size, w)
+    imx = np.empty(m, np.int64)
+    imn = np.empty(m, np.int64)
+    _check(_fn("argbf1d", a.dtype)(_ptr(a), a.size, w, _ptr(imx), _ptr(imn)), "argbf1d")
+    return imx, imn

@@ -34,6 +34,18 @@
  *             radius r of a series c (as in `envelope`) and a query q of
  *             the same length, sqrt of the sum over i of (q_i - U_i)^2 where
  *             q_i > U_i and (L_i - q_i)^2 where q_i < L_i, in double.
+ *   argbf1d   the locations of the maximum and the minimum of every window
+ *             [j, j+w) (the arg-max/arg-min filter that stored locations give
+ *             at no cost, Section 5): the leftmost position among equal
+ *             extremes, found by scanning the window left to right and
+ *             replacing the candidate only on a strictly larger (smaller)
+ *             value.
+ *   w3        the window-3 filter of the proposition after the lower
+ *             bound in Section 3 (at most 2 comparisons per element, zero
+ *             latency): the order of the last two elements is known from
+ *             the previous step, so comparing the new element with each of
+ *             them fixes the maximum, the minimum and the next order.  One
+ *             comparison starts the first pair; 2 per later element.
  *   dtw_band  the dynamic-time-warping distance of q and c with warping
  *             restricted to |i - j| <= r: sqrt of the least sum of
  *             (q_i - c_j)^2 along a monotone path from (0,0) to (n-1,n-1)
@@ -305,6 +317,62 @@ int oracle_dtw_band_##SUF(const T *q, const T *c, int64_t n, int64_t r,         
     free(D);                                                                      \
     return ORC_OK;                                                                \
 }
+
+/* Leftmost arg-max / arg-min of every window [j, j+w), by scanning it. */
+#define ORC_DEFINE_ARG(SUF, T)                                                    \
+int oracle_argbf1d_##SUF(const T *a, int64_t n, int64_t w, int64_t *imx,          \
+                         int64_t *imn) {                                          \
+    if (n < 0 || w < 1 || (n > 0 && !a)) return ORC_EINVAL;                       \
+    for (int64_t j = 0; j + w <= n; ++j) {                                        \
+        int64_t bx = j, bn = j;                                                   \
+        for (int64_t k = j + 1; k < j + w; ++k) {                                 \
+            if (a[k] > a[bx]) bx = k;                                             \
+            if (a[k] < a[bn]) bn = k;                                             \
+        }                                                                         \
+        if (imx) imx[j] = bx;                                                     \
+        if (imn) imn[j] = bn;                                                     \
+    }                                                                             \
+    return ORC_OK;                                                                \
+}
+
+ORC_DEFINE_ARG(f32, float)
+ORC_DEFINE_ARG(f64, double)
+ORC_DEFINE_ARG(i16, int16_t)
+ORC_DEFINE_ARG(u8, uint8_t)
+
+/* Window 3 in two comparisons per element; *ncmp counts them. */
+#define ORC_DEFINE_W3(SUF, T)                                                     \
+int oracle_w3_##SUF(const T *a, int64_t n, T *mx, T *mn, int64_t *ncmp) {         \
+    if (n < 0 || (n > 0 && !a)) return ORC_EINVAL;                                \
+    int64_t c = 0;                                                                \
+    if (n >= 3) {                                                                 \
+        int older_greater = a[0] > a[1]; /* order of the last two */             \
+        c = 1;                                                                    \
+        for (int64_t i = 2; i < n; ++i) {                                         \
+            int prev_gt = a[i - 1] > a[i];   /* comparison 1 */                   \
+            int older_gt = a[i - 2] > a[i];  /* comparison 2 */                   \
+            c += 2;                                                               \
+            T hi, lw;                                                             \
+            if (older_greater) {   /* a[i-2] > a[i-1] */                          \
+                hi = older_gt ? a[i - 2] : a[i];                                  \
+                lw = prev_gt ? a[i] : a[i - 1];                                   \
+            } else {               /* a[i-1] >= a[i-2] */                         \
+                hi = prev_gt ? a[i - 1] : a[i];                                   \
+                lw = older_gt ? a[i] : a[i - 2];                                  \
+            }                                                                     \
+            mx[i - 2] = hi;                                                       \
+            mn[i - 2] = lw;                                                       \
+            older_greater = prev_gt;                                              \
+        }                                                                         \
+    }                                                                             \
+    if (ncmp) *ncmp = c;                                                          \
+    return ORC_OK;                                                                \
+}
+
+ORC_DEFINE_W3(f32, float)
+ORC_DEFINE_W3(f64, double)
+ORC_DEFINE_W3(i16, int16_t)
+ORC_DEFINE_W3(u8, uint8_t)
 
 ORC_DEFINE_LB(f32, float)
 ORC_DEFINE_LB(f64, double)

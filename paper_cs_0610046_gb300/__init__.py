@@ -96,6 +96,9 @@ _EXTRA_SIGNATURES: dict = {
     "mmf_stream_push_batch": ([_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _P64], _INT),
     "mmf_ticket_wait_batch": ([_VP, _I64, _VP, _INT], _INT),
     "mmf_stream_close": ([_VP, ctypes.c_uint64, _INT], _INT),
+    "mmf_argfilter1d": ([_VP, _I64, _I64, _INT, _VP, _VP, _VP, _VP, _VP], _INT),
+    "mmf_stream_snapshot": ([_VP, ctypes.c_uint64, _VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), _INT], _INT),
+    "mmf_stream_restore": ([_VP, _VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint64)], _INT),
     "mmf_server_pause": ([_VP, _INT], _INT),
     "mmf_filter2d_workspace": ([_I64, _I64, _I64, _I64, _I64, _INT, _INT, ctypes.POINTER(ctypes.c_size_t)], _INT),
     "mmf_filter2d_separable": ([_VP, _I64, _I64, _I64, _I64, _I64, _I64, _INT, _INT, _VP, _VP, _VP,
@@ -159,6 +162,26 @@ def filter1d(x: torch.Tensor, w: int, mode: str = "valid", out_max=None, out_min
                                   _ptr(out_max), _ptr(out_min), _VP(_stream_handle(stream)),
                                   KERNELS[kernel]))
     return out_max, out_min
+
+
+def argfilter1d(x: torch.Tensor, w: int, stream=None):
+    """Positions (int64) of the maximum and minimum of every window
+    [j, j+w) of ``x``, leftmost among equal values, and the values:
+    returns ``(argmax, argmin, max, min)``; w <= 496."""
+    _check_tensor(x, "x")
+    lib = load()
+    x = x.reshape(-1)
+    m = int(lib.mmf_output_length(x.numel(), w, MODES["valid"]))
+    if m < 0:
+        raise MMFError(1, f"invalid window {w}")
+    am = torch.empty(m, dtype=torch.int64, device=x.device)
+    an = torch.empty(m, dtype=torch.int64, device=x.device)
+    vm = torch.empty(m, dtype=x.dtype, device=x.device)
+    vn = torch.empty(m, dtype=x.dtype, device=x.device)
+    with torch.cuda.device(x.device):
+        check(lib.mmf_argfilter1d(_ptr(x), x.numel(), w, DTYPES[x.dtype], _ptr(vm), _ptr(vn), _ptr(am), _ptr(an),
+                                  _VP(_stream_handle(stream))))
+    return am, an, vm, vn
 
 
 def _i64_array(xs):
@@ -391,6 +414,21 @@ class Server:
 
     def close_stream(self, sid: int, timeout_ms: int = 60_000) -> None:
         check(self._lib.mmf_stream_close(self._h, sid, timeout_ms))
+
+    def snapshot(self, sid: int, timeout_ms: int = 60_000) -> bytes:
+        """The stream's state (window, 64-bit count, last w-1 samples) as bytes."""
+        n = ctypes.c_size_t()
+        check(self._lib.mmf_stream_snapshot(self._h, sid, None, 0, ctypes.byref(n), timeout_ms))
+        buf = ctypes.create_string_buffer(n.value)
+        check(self._lib.mmf_stream_snapshot(self._h, sid, buf, n.value, ctypes.byref(n), timeout_ms))
+        return buf.raw[:n.value]
+
+    def restore(self, state: bytes) -> int:
+        """A new stream in the state of a snapshot; returns its id."""
+        sid = ctypes.c_uint64()
+        buf = ctypes.create_string_buffer(bytes(state), len(state))
+        check(self._lib.mmf_stream_restore(self._h, buf, len(state), ctypes.byref(sid)))
+        return int(sid.value)
 
     def pause(self, paused: bool = True) -> None:
         check(self._lib.mmf_server_pause(self._h, 1 if paused else 0))

@@ -129,6 +129,31 @@ const char *mmf_last_error(void) { return g_err; }
 
 const char *mmf_version(void) { return "mmf-gb300 0.1 (sm_103a)"; }
 
+mmf_status mmf_argfilter1d(const void *d_in, int64_t n, int64_t w, mmf_dtype dtype, void *d_max, void *d_min,
+                           int64_t *d_argmax, int64_t *d_argmin, void *stream) {
+    if (elem_size(dtype) == 0) return set_error(MMF_EINVAL, "unknown dtype %d", (int)dtype);
+    SeriesDesc sd;
+    mmf_status st = make_series(n, w, MMF_VALID, dtype, &sd);
+    if (st != MMF_OK) return st;
+    if (w > MMF_WEDGE_MAX_WINDOW)
+        return set_error(MMF_ENOTIMPL, "locations are computed for windows up to %d", MMF_WEDGE_MAX_WINDOW);
+    if (sd.n_out == 0) return MMF_OK;
+    if (!d_max && !d_min && !d_argmax && !d_argmin) return set_error(MMF_EINVAL, "every output is NULL");
+    if (!d_in) return set_error(MMF_EINVAL, "NULL input with n = %lld", (long long)n);
+    const int esz = elem_size(dtype);
+    if (((uintptr_t)d_in % esz) || ((uintptr_t)d_max % esz) || ((uintptr_t)d_min % esz) ||
+        ((uintptr_t)d_argmax % 8) || ((uintptr_t)d_argmin % 8))
+        return set_error(MMF_EINVAL, "misaligned pointer");
+    LaunchCtx ctx;
+    st = get_ctx(stream, &ctx);
+    if (st != MMF_OK) return st;
+    return dispatch_dtype(dtype, [&](auto tag) -> mmf_status {
+        using T = decltype(tag);
+        cudaError_t e = wedge_arg_1d<T>(ctx, d_in, n, w, d_max, d_min, d_argmax, d_argmin);
+        return e == cudaSuccess ? MMF_OK : cuda_error(e, "argfilter launch");
+    });
+}
+
 int64_t mmf_output_length(int64_t n, int64_t w_or_r, mmf_mode mode) {
     if (n < 0) return -1;
     if (mode == MMF_VALID) return w_or_r < 1 ? -1 : (n >= w_or_r ? n - w_or_r + 1 : 0);

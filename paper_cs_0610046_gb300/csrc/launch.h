@@ -66,6 +66,10 @@ cudaError_t blockscan_table(const LaunchCtx &ctx, int mode, const void *in, int6
 // w <= MMF_WEDGE_MAX_WINDOW.
 template <typename T>
 cudaError_t wedge_1d(const LaunchCtx &ctx, const void *in, int64_t n, int64_t w, void *omax, void *omin);
+// The same with the locations of the extremes (leftmost among equals), int64.
+template <typename T>
+cudaError_t wedge_arg_1d(const LaunchCtx &ctx, const void *in, int64_t n, int64_t w, void *omax, void *omin,
+                         int64_t *amax, int64_t *amin);
 
 // Kernel mode for window w: 3 = register slide (if allowed and w <= 17 for
 // f32, 9 otherwise), else

@@ -703,6 +703,82 @@ mmf_status mmf_stream_close(mmf_server *S, uint64_t stream_id, int timeout_ms) {
     return MMF_OK;
 }
 
+namespace {
+struct SnapshotHeader {
+    uint32_t magic;
+    uint32_t version;
+    int32_t dtype;
+    int32_t zero;
+    int64_t w;
+    int64_t count;
+    int64_t halo_len;
+};
+static_assert(sizeof(SnapshotHeader) == MMF_SNAPSHOT_HEADER_BYTES, "snapshot header layout");
+}  // namespace
+
+mmf_status mmf_stream_snapshot(mmf_server *S, uint64_t stream_id, void *h_buf, size_t buf_bytes, size_t *size,
+                               int timeout_ms) {
+    if (!S || !size) return set_error(MMF_EINVAL, "NULL argument");
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->streams.find(stream_id);
+    if (it == S->streams.end() || it->second.closed)
+        return set_error(MMF_ECLOSED, "stream %llu is not open", (unsigned long long)stream_id);
+    const auto deadline = Clock::now() + std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms);
+    while (S->streams[stream_id].pending > 0) {
+        if (S->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && S->streams[stream_id].pending > 0)
+            return set_error(MMF_ETIMEOUT, "stream %llu still has chunks after %d ms", (unsigned long long)stream_id,
+                             timeout_ms);
+    }
+    if (S->failed != MMF_OK) return set_error(MMF_EDEVICE, "the server failed earlier");
+    const StreamState ss = S->streams[stream_id];
+    const size_t need = sizeof(SnapshotHeader) + (size_t)ss.halo_len * S->esz;
+    *size = need;
+    if (!h_buf) return MMF_OK;
+    if (buf_bytes < need) return set_error(MMF_EINVAL, "snapshot needs %zu bytes", need);
+    SnapshotHeader hd{MMF_SNAPSHOT_MAGIC, 1u, (int32_t)S->dtype, 0, ss.w, ss.count, ss.halo_len};
+    memcpy(h_buf, &hd, sizeof(hd));
+    if (ss.halo_len > 0) {
+        cudaSetDevice(S->device);
+        // No chunk of this stream is pending, so no batch touches its halo.
+        cudaError_t e = cudaMemcpy(static_cast<char *>(h_buf) + sizeof(hd), S->dev_base + ss.halo_off,
+                                   (size_t)ss.halo_len * S->esz, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_error(e, "snapshot copy");
+    }
+    return MMF_OK;
+}
+
+mmf_status mmf_stream_restore(mmf_server *S, const void *h_buf, size_t buf_bytes, uint64_t *stream_id) {
+    if (!S || !h_buf || !stream_id) return set_error(MMF_EINVAL, "NULL argument");
+    if (buf_bytes < sizeof(SnapshotHeader)) return set_error(MMF_EINVAL, "snapshot shorter than its header");
+    SnapshotHeader hd;
+    memcpy(&hd, h_buf, sizeof(hd));
+    if (hd.magic != MMF_SNAPSHOT_MAGIC || hd.version != 1u || hd.zero != 0)
+        return set_error(MMF_EINVAL, "not a stream snapshot");
+    if (hd.dtype != (int32_t)S->dtype) return set_error(MMF_EINVAL, "snapshot of another dtype");
+    if (hd.w < 1 || hd.count < 0 || hd.halo_len != std::min<int64_t>(hd.count, hd.w - 1))
+        return set_error(MMF_EINVAL, "inconsistent snapshot header");
+    if (buf_bytes < sizeof(hd) + (size_t)hd.halo_len * S->esz) return set_error(MMF_EINVAL, "truncated snapshot");
+    uint64_t id = 0;
+    mmf_status st = mmf_stream_open(S, hd.w, &id);
+    if (st != MMF_OK) return st;
+    std::lock_guard<std::mutex> lk(S->mu);
+    StreamState &ss = S->streams[id];
+    if (hd.halo_len > 0) {
+        cudaSetDevice(S->device);
+        cudaError_t e = cudaMemcpy(S->dev_base + ss.halo_off, static_cast<const char *>(h_buf) + sizeof(hd),
+                                   (size_t)hd.halo_len * S->esz, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            if (ss.halo_off >= 0) S->stage.release(ss.halo_off, (size_t)(ss.w - 1) * S->esz);
+            S->streams.erase(id);
+            return cuda_error(e, "restore copy");
+        }
+    }
+    ss.count = hd.count;
+    ss.halo_len = hd.halo_len;
+    *stream_id = id;
+    return MMF_OK;
+}
+
 mmf_status mmf_server_pause(mmf_server *S, int paused) {
     if (!S) return set_error(MMF_EINVAL, "NULL server");
     std::lock_guard<std::mutex> lk(S->mu);

@@ -113,6 +113,19 @@ template <typename T> struct WedgeIO {
     }
 };
 
+// Eight int64 positions (the first cnt of them) at dst; whole 16-byte pairs
+// when dst is 16-byte aligned.
+__device__ __forceinline__ void store_index(int64_t *dst, int64_t cnt, const int64_t (&v)[8]) {
+    if (cnt >= 8 && (((uintptr_t)dst) & 15) == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) __stcs(reinterpret_cast<longlong2 *>(dst) + k, make_longlong2(v[2 * k], v[2 * k + 1]));
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (k < cnt) dst[k] = v[k];
+    }
+}
+
 template <typename T> struct Wedge {
     using R = typename Elem<T>::R;
     using S = WedgeS<T>;
@@ -135,9 +148,18 @@ template <typename T> struct Wedge {
     }
 
     // One iteration of Algorithm 1 for input i >= 1: afterwards the fronts are
-    // the maximum and minimum of the window that ends at i.
+    // the maximum and minimum of the window that ends at i.  ARG (locations
+    // wanted, leftmost among equal extremes): an input equal to the previous
+    // one joins both deques behind it, so equal earlier indices stay in front,
+    // and both fronts may leave the window at once.
+    template <bool ARG = false>
     __device__ __forceinline__ void step(uint32_t i, R ai) {
-        if (ai > prev) {
+        if (ARG && ai == prev) {
+            U.at((uh + us) & imask) = (uint16_t)i;
+            ++us;
+            L.at((lh + ls) & imask) = (uint16_t)i;
+            ++ls;
+        } else if (ai > prev) {
             --us;  // i-1 is dominated on the U side
             while (us > 0) {
                 const uint32_t b = U.at((uh + us - 1) & imask);
@@ -166,14 +188,20 @@ template <typename T> struct Wedge {
             U.at((uh + us) & imask) = (uint16_t)i;
             ++us;
         }
-        // At most one front can hold the index that just left the window.
+        // Without ties at most one front can hold the index that just left
+        // the window (every older index is in exactly one deque).
         const uint32_t gone = (i - w) & 0xffffu;
         if (uf == gone) {
             ++uh;
             --us;
             uf = U.at(uh & imask);
             ufv = val(uf);
-        } else if (lf == gone) {
+            if (!ARG) {
+                prev = ai;
+                return;
+            }
+        }
+        if (lf == gone) {
             ++lh;
             --ls;
             lf = L.at(lh & imask);
@@ -183,10 +211,13 @@ template <typename T> struct Wedge {
     }
 };
 
-template <typename T>
+// ARG: also the locations of the extremes (leftmost among equals) in amax /
+// amin (int64 positions in the array; either may be null).
+template <typename T, bool ARG>
 __global__ void __launch_bounds__(256) wedge_kernel(const T *__restrict__ a, int64_t n, int32_t w, int64_t chunk,
                                                     int vlog2, int ilog2, int vec_in, int vec_out,
-                                                    T *__restrict__ omax, T *__restrict__ omin) {
+                                                    T *__restrict__ omax, T *__restrict__ omin,
+                                                    int64_t *__restrict__ amax, int64_t *__restrict__ amin) {
     using IO = WedgeIO<T>;
     using R = typename Elem<T>::R;
     using S = WedgeS<T>;
@@ -202,6 +233,8 @@ __global__ void __launch_bounds__(256) wedge_kernel(const T *__restrict__ a, int
             const T v = x[o];
             if (omax) omax[j0 + o] = v;
             if (omin) omin[j0 + o] = v;
+            if (ARG && amax) amax[j0 + o] = j0 + o;
+            if (ARG && amin) amin[j0 + o] = j0 + o;
         }
         return;
     }
@@ -230,21 +263,33 @@ __global__ void __launch_bounds__(256) wedge_kernel(const T *__restrict__ a, int
     q.start(q.val(0));
     for (uint32_t i = 1; i < h; ++i) {  // warm-up on the halo: no output yet
         if (i >= staged) stage();
-        q.step(i, q.val(i));
+        q.template step<ARG>(i, q.val(i));
     }
     for (uint32_t o = 0; o < (uint32_t)cnt; o += 8) {
         const uint32_t ib = o + h;
         while (staged < ib + 8 && staged < span) stage();
         R om[8], on[8];
+        int64_t im[8], in_[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            if (o + k < (uint32_t)cnt) q.step(ib + k, q.val(ib + k));
+            const uint32_t i = ib + k;
+            if (o + k < (uint32_t)cnt) q.template step<ARG>(i, q.val(i));
             om[k] = q.ufv;
             on[k] = q.lfv;
+            if (ARG) {
+                // The fronts keep the low 16 bits of their indices; each lies
+                // within the window, less than 2^16 back.
+                im[k] = j0 + (int64_t)(i - ((i - q.uf) & 0xffffu));
+                in_[k] = j0 + (int64_t)(i - ((i - q.lf) & 0xffffu));
+            }
         }
         const int64_t left = cnt - o;
         if (omax) IO::store(omax + j0 + o, left, vec_out != 0, om);
         if (omin) IO::store(omin + j0 + o, left, vec_out != 0, on);
+        if (ARG) {
+            if (amax) store_index(amax + j0 + o, left, im);
+            if (amin) store_index(amin + j0 + o, left, in_);
+        }
     }
 }
 
@@ -256,8 +301,9 @@ int ceil_log2(int64_t v) {
 }
 }  // namespace
 
-template <typename T>
-cudaError_t wedge_1d(const LaunchCtx &ctx, const void *in, int64_t n, int64_t w, void *omax, void *omin) {
+template <typename T, bool ARG>
+static cudaError_t wedge_launch(const LaunchCtx &ctx, const void *in, int64_t n, int64_t w, void *omax, void *omin,
+                                int64_t *amax, int64_t *amin) {
     using S = WedgeS<T>;
     const int64_t n_out = n - w + 1;
     if (n_out <= 0) return cudaSuccess;
@@ -273,12 +319,13 @@ cudaError_t wedge_1d(const LaunchCtx &ctx, const void *in, int64_t n, int64_t w,
     const int slot = sizeof(T) == 1 ? 0 : sizeof(T) == 2 ? 1 : sizeof(T) == 4 ? 2 : 3;
     int &have = cached_smem[ctx.device & 63][slot];
     if ((int)smem > have) {
-        cudaError_t e = cudaFuncSetAttribute(wedge_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(wedge_kernel<T, ARG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         have = (int)smem;
     }
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wedge_kernel<T>, tpb, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wedge_kernel<T, ARG>, tpb, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     // One wave of threads, each with at least 8w outputs (the warm-up of w-1
@@ -293,15 +340,34 @@ cudaError_t wedge_1d(const LaunchCtx &ctx, const void *in, int64_t n, int64_t w,
     const size_t align = 8 * sizeof(T) < 16 ? 8 * sizeof(T) : 16;
     const int vec_in = ((uintptr_t)in % align) == 0;
     const int vec_out = ((uintptr_t)omax % align) == 0 && ((uintptr_t)omin % align) == 0;
-    wedge_kernel<T><<<(unsigned)blocks, tpb, smem, ctx.stream>>>(static_cast<const T *>(in), n, (int32_t)w, chunk,
-                                                                 vlog2, ilog2, vec_in, vec_out, static_cast<T *>(omax),
-                                                                 static_cast<T *>(omin));
+    wedge_kernel<T, ARG><<<(unsigned)blocks, tpb, smem, ctx.stream>>>(
+        static_cast<const T *>(in), n, (int32_t)w, chunk, vlog2, ilog2, vec_in, vec_out, static_cast<T *>(omax),
+        static_cast<T *>(omin), amax, amin);
     return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t wedge_1d(const LaunchCtx &ctx, const void *in, int64_t n, int64_t w, void *omax, void *omin) {
+    return wedge_launch<T, false>(ctx, in, n, w, omax, omin, nullptr, nullptr);
+}
+
+template <typename T>
+cudaError_t wedge_arg_1d(const LaunchCtx &ctx, const void *in, int64_t n, int64_t w, void *omax, void *omin,
+                         int64_t *amax, int64_t *amin) {
+    return wedge_launch<T, true>(ctx, in, n, w, omax, omin, amax, amin);
 }
 
 template cudaError_t wedge_1d<float>(const LaunchCtx &, const void *, int64_t, int64_t, void *, void *);
 template cudaError_t wedge_1d<double>(const LaunchCtx &, const void *, int64_t, int64_t, void *, void *);
 template cudaError_t wedge_1d<int16_t>(const LaunchCtx &, const void *, int64_t, int64_t, void *, void *);
 template cudaError_t wedge_1d<uint8_t>(const LaunchCtx &, const void *, int64_t, int64_t, void *, void *);
+template cudaError_t wedge_arg_1d<float>(const LaunchCtx &, const void *, int64_t, int64_t, void *, void *, int64_t *,
+                                         int64_t *);
+template cudaError_t wedge_arg_1d<double>(const LaunchCtx &, const void *, int64_t, int64_t, void *, void *, int64_t *,
+                                          int64_t *);
+template cudaError_t wedge_arg_1d<int16_t>(const LaunchCtx &, const void *, int64_t, int64_t, void *, void *,
+                                           int64_t *, int64_t *);
+template cudaError_t wedge_arg_1d<uint8_t>(const LaunchCtx &, const void *, int64_t, int64_t, void *, void *,
+                                           int64_t *, int64_t *);
 
 }  // namespace mmf

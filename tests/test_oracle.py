@@ -347,3 +347,51 @@ def test_lb_keogh_is_monotone_in_radius():
     vals = [oracle.lb_keogh(c, q, r) for r in (0, 1, 3, 10, 50, 399)]
     assert all(b <= a for a, b in zip(vals, vals[1:]))
     assert vals[0] > vals[-1] >= 0.0
+
+
+# ------------------------------------------------ window 3, 2 comparisons
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64, np.int16, np.uint8])
+def test_w3_two_comparisons_per_element(dtype):
+    """The proposition after Section 3's lower bound: w = 3 needs at most 2
+    comparisons per element with zero latency.  The oracle's version agrees
+    with the definition on every input (uint8 data is full of ties, and the
+    exhaustive part covers every order of up to 6 elements over 3 values),
+    and its count is exactly 2n - 3 <= 2n."""
+    for n in (0, 1, 2, 3, 4, 17, 10_000):
+        a = synth.uniform(n, seed=n, dtype=dtype) if n else np.zeros(0, dtype)
+        mx, mn, c = oracle.w3(a)
+        emx, emn = oracle.bf1d(a, 3)
+        assert np.array_equal(mx, emx) and np.array_equal(mn, emn)
+        assert c == (2 * n - 3 if n >= 3 else 0) and c <= 2 * n
+    for n in range(3, 7):
+        for t in itertools.product(range(3), repeat=n):
+            a = np.array(t, dtype)
+            mx, mn, _ = oracle.w3(a)
+            emx, emn = oracle.bf1d(a, 3)
+            assert np.array_equal(mx, emx) and np.array_equal(mn, emn)
+
+
+# --------------------------------------------------- arg-max / arg-min
+
+@pytest.mark.parametrize("dtype", [np.float32, np.int16, np.uint8])
+def test_argbf1d_leftmost_extreme(dtype):
+    """Every location holds the window's extreme value (the definition's max
+    and min), lies inside the window, and no earlier position of the window
+    holds the same value (leftmost rule), checked with numpy independently
+    of the oracle's loop; a constant array gives the window starts."""
+    a = synth.uniform(3000, seed=8, dtype=dtype)
+    if dtype == np.uint8:
+        a = (a // 16).astype(np.uint8)  # long runs of ties
+    for w in (1, 2, 3, 7, 64):
+        imx, imn = oracle.argbf1d(a, w)
+        mx, mn = oracle.bf1d(a, w)
+        j = np.arange(imx.size)
+        assert ((imx >= j) & (imx < j + w)).all() and ((imn >= j) & (imn < j + w)).all()
+        assert np.array_equal(a[imx], mx) and np.array_equal(a[imn], mn)
+        for k in range(0, imx.size, 97):
+            win = a[k:k + w]
+            assert imx[k] == k + int(np.argmax(win)) and imn[k] == k + int(np.argmin(win))
+    c = np.full(50, 7, dtype)
+    imx, imn = oracle.argbf1d(c, 5)
+    assert np.array_equal(imx, np.arange(46)) and np.array_equal(imn, np.arange(46))

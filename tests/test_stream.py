@@ -193,3 +193,81 @@ def test_push_batch_equals_whole_array(mmf):
         emx, emn = oracle.bf1d(data[k], int(ws[k]))
         assert np.array_equal(np.concatenate(got[k][0]), emx), k
         assert np.array_equal(np.concatenate(got[k][1]), emn), k
+
+
+def _push_all(mmf, srv, sid, data, start, cuts, w, dtype=np.float32):
+    """Pushes data[start:] in chunks of `cuts`; returns the concatenated
+    outputs (max, min)."""
+    mx, mn, ts = [], [], []
+    pos = start
+    for L in cuts:
+        chunk = np.ascontiguousarray(data[pos:pos + L])
+        m = mmf.n_outputs(pos, L, w)
+        a = np.empty(m, dtype)
+        b = np.empty(m, dtype)
+        t, n_out = srv.push(sid, chunk, a, b)
+        assert n_out == m
+        ts.append(t)
+        mx.append(a)
+        mn.append(b)
+        pos += L
+    for t in ts:
+        srv.wait(t)
+    return np.concatenate(mx), np.concatenate(mn)
+
+
+@pytest.mark.parametrize("w,cut_at", [(1, 5000), (2, 1), (5, 3), (257, 100), (257, 40_000), (9001, 20_000)])
+def test_snapshot_restore_continues_exactly(mmf, w, cut_at):
+    """A stream snapshotted after `cut_at` samples and restored as a new
+    stream (on another server) gives, for the rest of the data, the outputs
+    the original stream gives, and both equal the whole-array filter of the
+    concatenation; snapshots before w-1 samples carry a shorter state."""
+    rng = np.random.default_rng(w + cut_at)
+    data = synth.random_walk(60_000, seed=w, dtype=np.float32)
+    first = _split(cut_at, rng, 1, 3000)
+    rest = _split(data.size - cut_at, rng, 1, 7000)
+    srv = mmf.Server(1 << 26, 32, "float32")
+    sid = srv.open(w)
+    m0, n0 = _push_all(mmf, srv, sid, data, 0, first, w)
+    state = srv.snapshot(sid)
+    assert len(state) == 40 + 4 * min(cut_at, w - 1)
+    m1, n1 = _push_all(mmf, srv, sid, data, cut_at, rest, w)
+    srv2 = mmf.Server(1 << 26, 32, "float32")
+    sid2 = srv2.restore(state)
+    m2, n2 = _push_all(mmf, srv2, sid2, data, cut_at, rest, w)
+    assert np.array_equal(m1, m2) and np.array_equal(n1, n2)
+    emx, emn = oracle.bf1d(data, w)
+    assert np.array_equal(np.concatenate([m0, m1]), emx) and np.array_equal(np.concatenate([n0, n1]), emn)
+    srv.close()
+    srv2.close()
+    assert mmf.device_status() == 0
+
+
+def test_snapshot_64bit_count_and_rejects(mmf):
+    """A snapshot written by hand in the documented layout with a count past
+    2^32 (an unbounded stream): the restored stream's outputs follow from its
+    halo and the new samples alone.  Bad snapshots are refused on the host."""
+    import struct
+    w = 33
+    halo = synth.uniform(w - 1, seed=1, dtype=np.float32)
+    count = (1 << 40) + 12345
+    state = struct.pack("<IIiiqqq", 0x53464D4D, 1, 0, 0, w, count, w - 1) + halo.tobytes()
+    srv = mmf.Server(1 << 24, 8, "float32")
+    sid = srv.restore(state)
+    more = synth.uniform(5000, seed=2, dtype=np.float32)
+    m = mmf.n_outputs(count, more.size, w)
+    assert m == more.size
+    a = np.empty(m, np.float32)
+    b = np.empty(m, np.float32)
+    t, n_out = srv.push(sid, more, a, b)
+    srv.wait(t)
+    emx, emn = oracle.bf1d(np.concatenate([halo, more]), w)
+    assert np.array_equal(a, emx) and np.array_equal(b, emn)
+    assert srv.snapshot(sid)[:40] == struct.pack("<IIiiqqq", 0x53464D4D, 1, 0, 0, w, count + more.size, w - 1)
+    for bad in (state[:39], state[:-4], b"XXXX" + state[4:],
+                struct.pack("<IIiiqqq", 0x53464D4D, 1, 1, 0, w, count, w - 1) + halo.tobytes(),
+                struct.pack("<IIiiqqq", 0x53464D4D, 1, 0, 0, w, 3, w - 1) + halo.tobytes()):
+        with pytest.raises(mmf.MMFError):
+            srv.restore(bad)
+    srv.close()
+    assert mmf.device_status() == 0
