@@ -284,6 +284,8 @@ def wedge_extras(dev, stream, peak, n=1 << 30, windows=(3, 31, 101, 496), reps=3
     out = {}
     om = torch.empty(n, dtype=torch.float32, device=dev)
     on = torch.empty(n, dtype=torch.float32, device=dev)
+    am = torch.empty(n, dtype=torch.int64, device=dev)
+    an = torch.empty(n, dtype=torch.int64, device=dev)
     for d in DISTS:
         x = synth.torch_by_name(d, n, 91, dev)
         for w in windows:
@@ -297,9 +299,18 @@ def wedge_extras(dev, stream, peak, n=1 << 30, windows=(3, 31, 101, 496), reps=3
                 gbs = (n + 2 * m) * 4 / ms / 1e6
                 row[k] = {"ms": ms, "Gelem_s": n / ms / 1e6, "GBps": gbs, "frac": gbs / peak}
             row["wedge_over_auto"] = row["auto"]["ms"] / row["wedge"]["ms"]
+            # Values and int64 positions of the extremes (the arg filter):
+            # 4 + 2 x (4 + 8) bytes per element.
+            def g():
+                mmf.argfilter1d(x, w, stream=stream, out=(am[:m], an[:m], om[:m], on[:m]))
+            g()
+            ms = _events_ms(g, reps, stream)
+            gbs = (n * 4 + 2 * m * 12) / ms / 1e6
+            row["arg"] = {"ms": ms, "Gelem_s": n / ms / 1e6, "GBps": gbs, "frac": gbs / peak,
+                          "arg_over_wedge_time": ms / row["wedge"]["ms"]}
             out[f"{d}_w{w}"] = row
         del x
-    del om, on
+    del om, on, am, an
     torch.cuda.empty_cache()
     return out
 

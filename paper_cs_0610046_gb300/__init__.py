@@ -164,20 +164,27 @@ def filter1d(x: torch.Tensor, w: int, mode: str = "valid", out_max=None, out_min
     return out_max, out_min
 
 
-def argfilter1d(x: torch.Tensor, w: int, stream=None):
+def argfilter1d(x: torch.Tensor, w: int, stream=None, out=None):
     """Positions (int64) of the maximum and minimum of every window
     [j, j+w) of ``x``, leftmost among equal values, and the values:
-    returns ``(argmax, argmin, max, min)``; w <= 496."""
+    returns ``(argmax, argmin, max, min)``; w <= 496.  ``out``: optional
+    tuple of the four output tensors (at least n-w+1 elements each)."""
     _check_tensor(x, "x")
     lib = load()
     x = x.reshape(-1)
     m = int(lib.mmf_output_length(x.numel(), w, MODES["valid"]))
     if m < 0:
         raise MMFError(1, f"invalid window {w}")
-    am = torch.empty(m, dtype=torch.int64, device=x.device)
-    an = torch.empty(m, dtype=torch.int64, device=x.device)
-    vm = torch.empty(m, dtype=x.dtype, device=x.device)
-    vn = torch.empty(m, dtype=x.dtype, device=x.device)
+    if out is not None:
+        am, an, vm, vn = out
+        for t, dt in ((am, torch.int64), (an, torch.int64), (vm, x.dtype), (vn, x.dtype)):
+            if not (t.is_cuda and t.is_contiguous()) or t.dtype != dt or t.numel() < m:
+                raise ValueError(f"outputs must be contiguous CUDA tensors of {m} elements ({dt})")
+    else:
+        am = torch.empty(m, dtype=torch.int64, device=x.device)
+        an = torch.empty(m, dtype=torch.int64, device=x.device)
+        vm = torch.empty(m, dtype=x.dtype, device=x.device)
+        vn = torch.empty(m, dtype=x.dtype, device=x.device)
     with torch.cuda.device(x.device):
         check(lib.mmf_argfilter1d(_ptr(x), x.numel(), w, DTYPES[x.dtype], _ptr(vm), _ptr(vn), _ptr(am), _ptr(an),
                                   _VP(_stream_handle(stream))))

@@ -341,6 +341,7 @@ template <typename T> struct Smem {
 // Per-item quantities, computed identically by thread 0 and the consumers.
 template <typename T> struct ItemPlan {
     int64_t series;  // index in the series table (0 without one)
+    double *lb_acc;  // envelope lower bound accumulators (null: store outputs)
     const T *in;
     T *omax;
     T *omin;
@@ -366,6 +367,7 @@ __device__ __forceinline__ ItemPlan<T> make_plan(const BlockScanParams &P, int64
     SeriesDesc sd;
     int64_t ob, oe;
     ip.series = 0;
+    ip.lb_acc = P.lb_acc;
     if (P.items) {
         ItemDesc it = P.items[item];
         ip.series = it.series;
@@ -1012,7 +1014,7 @@ struct Consumer {
     // o_end).  Every lane of the warp calls it (vec from out_vec).
     __device__ __forceinline__ void store_out(const ItemPlan<T> &ip, int64_t o0, const R (&om)[V], const R (&on)[V],
                                               int vec) const {
-        if (S::params().lb_acc) {
+        if (ip.lb_acc) {
             lb_out(ip, o0, om, on);
             return;
         }
@@ -1073,7 +1075,7 @@ struct Consumer {
         }
 #pragma unroll
         for (int k = 16; k >= 1; k >>= 1) part += __shfl_xor_sync(0xffffffffu, part, k);
-        if (lane == 0 && part != A(0)) atomicAdd(S::params().lb_acc + ip.series, (double)part);
+        if (lane == 0 && part != A(0)) atomicAdd(ip.lb_acc + ip.series, (double)part);
     }
 
     // A whole warp span of outputs (every lane V values at dst, lanes V
