@@ -90,6 +90,19 @@ typedef enum {
 mmf_status mmf_filter1d(const void *d_in, int64_t n, int64_t w_or_r, mmf_dtype dtype,
                         mmf_mode mode, void *d_max, void *d_min, void *stream);
 
+/* The same filter on arrays in HOST memory (pinned memory is fastest): the
+ * outputs are cut into chunks of `chunk` elements (<= 0: 2^26) whose inputs
+ * (the chunk plus its windows' reach) are uploaded, filtered and downloaded
+ * through device staging on three internal CUDA streams, so uploads, kernels
+ * and downloads of successive chunks overlap; the result equals mmf_filter1d
+ * on the whole array.  Work starts after the work already queued on `stream`
+ * and `stream` waits for the last download, so synchronising `stream` makes
+ * h_max/h_min ready.  The library keeps per-device staging of three chunks
+ * (grown on demand; growing it synchronises the device).  Calls are
+ * serialised per device. */
+mmf_status mmf_filter1d_host(const void *h_in, int64_t n, int64_t w_or_r, mmf_dtype dtype, mmf_mode mode,
+                             void *h_max, void *h_min, int64_t chunk, void *stream);
+
 /* Largest window of the chunked-wedge kernel: its per-thread rings (the
  * window of inputs and the deques U and L, Section 4) must fit shared memory. */
 #define MMF_WEDGE_MAX_WINDOW 496

@@ -96,6 +96,7 @@ _EXTRA_SIGNATURES: dict = {
     "mmf_stream_push_batch": ([_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _P64], _INT),
     "mmf_ticket_wait_batch": ([_VP, _I64, _VP, _INT], _INT),
     "mmf_stream_close": ([_VP, ctypes.c_uint64, _INT], _INT),
+    "mmf_filter1d_host": ([_VP, _I64, _I64, _INT, _INT, _VP, _VP, _I64, _VP], _INT),
     "mmf_argfilter1d": ([_VP, _I64, _I64, _INT, _VP, _VP, _VP, _VP, _VP], _INT),
     "mmf_stream_snapshot": ([_VP, ctypes.c_uint64, _VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), _INT], _INT),
     "mmf_stream_restore": ([_VP, _VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint64)], _INT),
@@ -161,6 +162,36 @@ def filter1d(x: torch.Tensor, w: int, mode: str = "valid", out_max=None, out_min
         check(lib.mmf_filter1d_ex(_ptr(x), x.numel(), w, DTYPES[x.dtype], MODES[mode],
                                   _ptr(out_max), _ptr(out_min), _VP(_stream_handle(stream)),
                                   KERNELS[kernel]))
+    return out_max, out_min
+
+
+def filter1d_host(x: torch.Tensor, w: int, mode: str = "valid", out_max=None, out_min=None, chunk: int = 0,
+                  stream=None, device=None):
+    """The filter of a HOST (CPU) tensor through the chunked upload / filter /
+    download pipeline on ``device`` (default: the current CUDA device).
+    Outputs are CPU tensors (pinned memory is fastest); returns (max, min).
+    Synchronise ``stream`` (default: the current stream) before reading."""
+    if not isinstance(x, torch.Tensor) or x.is_cuda or x.dtype not in DTYPES:
+        raise TypeError("x must be a CPU tensor of a supported dtype")
+    x = x.reshape(-1)
+    if not x.is_contiguous():
+        raise ValueError("x must be contiguous")
+    lib = load()
+    m = int(lib.mmf_output_length(x.numel(), w, MODES[mode]))
+    if m < 0:
+        raise MMFError(1, f"invalid window {w} for mode {mode}")
+    if out_max is None:
+        out_max = torch.empty(m, dtype=x.dtype, pin_memory=True)
+    if out_min is None:
+        out_min = torch.empty(m, dtype=x.dtype, pin_memory=True)
+    for o in (out_max, out_min):
+        if o.is_cuda or o.dtype != x.dtype or o.numel() < m or not o.is_contiguous():
+            raise ValueError(f"outputs must be contiguous CPU tensors of {m} elements")
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    with torch.cuda.device(dev):
+        check(lib.mmf_filter1d_host(ctypes.c_void_p(x.data_ptr()), x.numel(), w, DTYPES[x.dtype], MODES[mode],
+                                    ctypes.c_void_p(out_max.data_ptr()), ctypes.c_void_p(out_min.data_ptr()), chunk,
+                                    _VP(_stream_handle(stream))))
     return out_max, out_min
 
 

@@ -448,17 +448,8 @@ mmf_status mmf_lb_keogh_batched(mmf_batch_plan *p, const void *d_in, const void 
     lb_clear_kernel<<<nb, 256, 0, st>>>(d_lb, p->nseries);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "clear bounds");
-    for (int gi = 0; gi < kModes; ++gi) {
-        if (p->groups[gi].items.empty()) continue;
-        cudaError_t pe = cudaSuccess;
-        switch (p->dtype) {
-            case MMF_F32: pe = blockscan_prepare<float>(p->device, gi); break;
-            case MMF_F64: pe = blockscan_prepare<double>(p->device, gi); break;
-            case MMF_I16: pe = blockscan_prepare<int16_t>(p->device, gi); break;
-            case MMF_U8: pe = blockscan_prepare<uint8_t>(p->device, gi); break;
-        }
-        if (pe != cudaSuccess) return cuda_error(pe, "prepare kernels");
-    }
+    // The lower-bound launches set their kernels' attributes themselves (no
+    // graph is captured here).
     s = enqueue_all(p, st, d_in, nullptr, nullptr, d_query, d_lb);
     if (s != MMF_OK) return s;
     lb_sqrt_kernel<<<nb, 256, 0, st>>>(d_lb, p->nseries);

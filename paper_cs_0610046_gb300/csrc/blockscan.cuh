@@ -685,7 +685,9 @@ template <typename T> struct TileQueue {
 //   0: s < V      B = 2^floor(log2 s) < V: blocks inside a thread
 //   1: s < W      B = 2^floor(log2 s) in [V, W/2]: blocks of 2..16 lanes
 //   2: s >= W     B = W: one block per warp; for s >= T also tile aggregates
-template <typename T, int KMODE>
+// LB: the output stage feeds the envelope lower bound instead of storing
+// (a separate instantiation, so the storing kernels carry none of it).
+template <typename T, int KMODE, bool LB = false>
 struct Consumer {
     using R = typename Elem<T>::R;
     using Pair = typename Elem<T>::Pair;
@@ -1014,7 +1016,7 @@ struct Consumer {
     // o_end).  Every lane of the warp calls it (vec from out_vec).
     __device__ __forceinline__ void store_out(const ItemPlan<T> &ip, int64_t o0, const R (&om)[V], const R (&on)[V],
                                               int vec) const {
-        if (ip.lb_acc) {
+        if constexpr (LB) {
             lb_out(ip, o0, om, on);
             return;
         }
@@ -1704,7 +1706,7 @@ struct Consumer {
 
 // One instantiation per block mode keeps each one within 128 registers (two
 // CTAs per SM); an item whose mode differs is rejected (kErrBadItem).
-template <typename T, int MODE>
+template <typename T, int MODE, bool LB = false>
 __global__ void __launch_bounds__(Geo<T>::NT, (Geo<T>::NT * Elem<T>::V == 4096 && MODE != 3) ? 1 : 2)
     blockscan_kernel(const BlockScanParams P) {
     using S = Smem<T>;
@@ -1739,7 +1741,7 @@ __global__ void __launch_bounds__(Geo<T>::NT, (Geo<T>::NT * Elem<T>::V == 4096 &
         for (int s = 0; s < kStages; ++s) issue_next<T, MODE>(warp);
     __syncwarp();
 
-    Consumer<T, MODE> cs;
+    Consumer<T, MODE, LB> cs;
     cs.tid = tid;
     cs.lane = lane;
     cs.warp = warp;

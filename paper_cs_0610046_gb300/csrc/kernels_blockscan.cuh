@@ -13,18 +13,18 @@ template <typename T> constexpr size_t smem_of(int mode) {
 
 // Sets the shared-memory attribute once per device and returns the number of
 // resident CTAs per SM.
-template <typename T, int MODE> static cudaError_t prepare_blockscan(int device, int *per_sm) {
+template <typename T, int MODE, bool LB = false> static cudaError_t prepare_blockscan(int device, int *per_sm) {
     static int occ[64] = {0};
     if (device >= 0 && device < 64 && occ[device] > 0) {
         *per_sm = occ[device];
         return cudaSuccess;
     }
     const size_t smem = smem_of<T>(MODE);
-    cudaError_t e = cudaFuncSetAttribute(blockscan_kernel<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(blockscan_kernel<T, MODE, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     int k = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, blockscan_kernel<T, MODE>, Geo<T>::NT, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, blockscan_kernel<T, MODE, LB>, Geo<T>::NT, smem);
     if (e != cudaSuccess) return e;
     if (k < 1) k = 1;
     if (device >= 0 && device < 64) occ[device] = k;
@@ -42,28 +42,28 @@ template <typename T> int block_mode(int64_t w, bool allow_slide) {
     return s >= Geo<T>::V ? 1 : 0;
 }
 
-template <typename T, int MODE>
+template <typename T, int MODE, bool LB = false>
 static void launch_bs(const BlockScanParams &P, int grid, cudaStream_t st) {
-    blockscan_kernel<T, MODE><<<(unsigned)grid, Geo<T>::NT, smem_of<T>(MODE), st>>>(P);
+    blockscan_kernel<T, MODE, LB><<<(unsigned)grid, Geo<T>::NT, smem_of<T>(MODE), st>>>(P);
 }
 
-template <typename T>
+template <typename T, bool LB = false>
 static cudaError_t prepare_mode(int mode, int device, int *per_sm) {
     switch (mode) {
-        case 0: return prepare_blockscan<T, 0>(device, per_sm);
-        case 1: return prepare_blockscan<T, 1>(device, per_sm);
-        case 2: return prepare_blockscan<T, 2>(device, per_sm);
-        default: return prepare_blockscan<T, 3>(device, per_sm);
+        case 0: return prepare_blockscan<T, 0, LB>(device, per_sm);
+        case 1: return prepare_blockscan<T, 1, LB>(device, per_sm);
+        case 2: return prepare_blockscan<T, 2, LB>(device, per_sm);
+        default: return prepare_blockscan<T, 3, LB>(device, per_sm);
     }
 }
 
-template <typename T>
+template <typename T, bool LB = false>
 static void launch_mode(int mode, const BlockScanParams &P, int grid, cudaStream_t st) {
     switch (mode) {
-        case 0: launch_bs<T, 0>(P, grid, st); break;
-        case 1: launch_bs<T, 1>(P, grid, st); break;
-        case 2: launch_bs<T, 2>(P, grid, st); break;
-        default: launch_bs<T, 3>(P, grid, st); break;
+        case 0: launch_bs<T, 0, LB>(P, grid, st); break;
+        case 1: launch_bs<T, 1, LB>(P, grid, st); break;
+        case 2: launch_bs<T, 2, LB>(P, grid, st); break;
+        default: launch_bs<T, 3, LB>(P, grid, st); break;
     }
 }
 
@@ -135,6 +135,9 @@ cudaError_t blockscan_table(const LaunchCtx &ctx, int mode, const void *in, int6
                             void *omin, const SeriesDesc *d_series, const ItemDesc *d_items, int64_t n_items,
                             int *d_ticket, int grid, const void *lb_query, double *lb_acc) {
     if (n_items <= 0) return cudaSuccess;
+    if (lb_acc)  // the lower-bound kernels live in their own translation units
+        return blockscan_table_lb<T>(ctx, mode, in, in_elems, d_series, d_items, n_items, d_ticket, grid, lb_query,
+                                     lb_acc);
     int per_sm = 1;
     cudaError_t e = prepare_mode<T>(mode, ctx.device, &per_sm);
     if (e != cudaSuccess) return e;

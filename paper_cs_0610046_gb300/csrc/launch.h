@@ -62,6 +62,12 @@ cudaError_t blockscan_table(const LaunchCtx &ctx, int mode, const void *in, int6
                             void *omin, const SeriesDesc *d_series, const ItemDesc *d_items, int64_t n_items,
                             int *d_ticket, int grid, const void *lb_query = nullptr, double *lb_acc = nullptr);
 
+// The table launch in its lower-bound form (no outputs; see above).
+template <typename T>
+cudaError_t blockscan_table_lb(const LaunchCtx &ctx, int mode, const void *in, int64_t in_elems,
+                               const SeriesDesc *d_series, const ItemDesc *d_items, int64_t n_items, int *d_ticket,
+                               int grid, const void *lb_query, double *lb_acc);
+
 // Chunked monotonic wedge (Algorithm 1 per thread chunk), valid windows,
 // w <= MMF_WEDGE_MAX_WINDOW.
 template <typename T>

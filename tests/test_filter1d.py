@@ -243,3 +243,28 @@ def test_long_items_large_windows(mmf, w):
     _check(mmf, a, w)
     b = synth.piecewise_monotone(700_001, seed=w, dtype=np.float32)
     _check(mmf, b, w)
+
+
+@pytest.mark.parametrize("mode,w", [("valid", 3), ("valid", 1001), ("valid", 70_001), ("envelope", 0),
+                                    ("envelope", 51), ("envelope", 40_000)])
+def test_host_pipeline_equals_oracle(mmf, mode, w):
+    """Host arrays through the chunked pipeline (small chunks, so many of
+    them, with windows shorter and longer than a chunk) equal the oracle."""
+    a = synth.random_walk(300_007, seed=w + 1, dtype=np.float32)
+    x = torch.from_numpy(a)
+    mx, mn = mmf.filter1d_host(x, w, mode=mode, chunk=20_000)
+    torch.cuda.current_stream().synchronize()
+    emx, emn = oracle.bf1d(a, w) if mode == "valid" else oracle.envelope(a, w)
+    assert np.array_equal(mx.numpy(), emx) and np.array_equal(mn.numpy(), emn)
+
+
+def test_host_pipeline_types_and_calls_in_a_row(mmf):
+    for dtype in DTYPES:
+        a = synth.uniform(50_001, seed=9, dtype=dtype)
+        x = torch.from_numpy(a)
+        outs = [mmf.filter1d_host(x, w, chunk=4096) for w in (2, 257)]
+        torch.cuda.current_stream().synchronize()
+        for (mx, mn), w in zip(outs, (2, 257)):
+            emx, emn = oracle.bf1d(a, w)
+            assert np.array_equal(mx.numpy(), emx) and np.array_equal(mn.numpy(), emn)
+    assert mmf.device_status() == 0
