@@ -169,10 +169,10 @@ mmf_status enqueue_all(mmf_batch_plan *p, cudaStream_t st, const void *in, void 
         bctx.stream = p->short_branch;
         const int64_t cnt = (int64_t)p->short_ids.size();
         switch (p->dtype) {
-            case MMF_F32: e = short_table<float>(bctx, in, p->in_len, omax, omin, p->d_series, p->d_short, cnt, lb_query, lb_acc); break;
-            case MMF_F64: e = short_table<double>(bctx, in, p->in_len, omax, omin, p->d_series, p->d_short, cnt, lb_query, lb_acc); break;
-            case MMF_I16: e = short_table<int16_t>(bctx, in, p->in_len, omax, omin, p->d_series, p->d_short, cnt, lb_query, lb_acc); break;
-            case MMF_U8: e = short_table<uint8_t>(bctx, in, p->in_len, omax, omin, p->d_series, p->d_short, cnt, lb_query, lb_acc); break;
+            case MMF_F32: e = short_table<float>(bctx, in, p->in_len, omax, omin, p->d_series, p->d_short, cnt, lb_query, lb_acc, p->common_len); break;
+            case MMF_F64: e = short_table<double>(bctx, in, p->in_len, omax, omin, p->d_series, p->d_short, cnt, lb_query, lb_acc, p->common_len); break;
+            case MMF_I16: e = short_table<int16_t>(bctx, in, p->in_len, omax, omin, p->d_series, p->d_short, cnt, lb_query, lb_acc, p->common_len); break;
+            case MMF_U8: e = short_table<uint8_t>(bctx, in, p->in_len, omax, omin, p->d_series, p->d_short, cnt, lb_query, lb_acc, p->common_len); break;
         }
         if (e != cudaSuccess) return cuda_error(e, "short-series launch");
         e = cudaEventRecord(p->short_join, p->short_branch);

@@ -173,5 +173,6 @@ cudaError_t blockscan_table(const LaunchCtx &ctx, int mode, const void *in, int6
                                                   const void *, double *);                                      \
     template int mmf::block_mode<T>(int64_t, bool);                                                            \
     template cudaError_t mmf::short_table<T>(const LaunchCtx &, const void *, int64_t, void *, void *,         \
-                                              const SeriesDesc *, const int64_t *, int64_t, const void *, double *); \
+                                              const SeriesDesc *, const int64_t *, int64_t, const void *, double *, \
+                                              int64_t);                                                          \
     template cudaError_t mmf::short_prepare<T>(int, bool, int *);

@@ -33,12 +33,12 @@ cudaError_t blockscan_rows(const LaunchCtx &ctx, const void *in, const SeriesDes
 constexpr int64_t short_max_len(int esz) { return esz == 8 ? 512 : 1024; }
 
 // Warp-per-series launch over the series d_ids[0..count) of the table;
-// lb_acc (with lb_query): the envelope lower bound instead of outputs (each
-// series' sum is written, not added).
+// lb_acc (with lb_query of lb_n elements, every series' length): the envelope
+// lower bound instead of outputs (each series' sum is written, not added).
 template <typename T>
 cudaError_t short_table(const LaunchCtx &ctx, const void *in, int64_t in_elems, void *omax, void *omin,
                         const SeriesDesc *d_series, const int64_t *d_ids, int64_t count, const void *lb_query,
-                        double *lb_acc);
+                        double *lb_acc, int64_t lb_n = 0);
 // Kernel attributes of the short-series kernel (outside any stream capture).
 template <typename T> cudaError_t short_prepare(int device, bool lb, int *per_sm);
 

@@ -3,20 +3,15 @@
 // barriers on every item; a series of a thousand elements would fill half a
 // tile, so short series take this kernel instead.
 //
-// Per series, lane l holds elements [l·E, l·E + E) in registers.  With blocks
-// of B = the largest power of two <= w (Section 2's van Herk/Gil-Werman
-// decomposition with blocks no longer than the window, Table 1), every window
-// [lo, hi] spans at most three blocks, so
-//     out = op(suffix_B[lo], aggregate of the middle block, prefix_B[hi]),
-// and a window inside one block starts at the block's start (prefix_B[hi]) or
-// ends at the series' end, past which every element is the identity
-// (suffix_B[lo]).  Windows clipped to the series (centred mode) are plain
-// [max(lo, 0), min(hi, n-1)].  The block scans are thread-local when B <= E,
-// else carried across the B/E lanes of a block by shuffles.  Both scans go to
-// a warp-private shared array stored element-major (row = position mod E,
-// column = lane), so a warp reading one position per lane touches 32
-// consecutive words; each output reads two or three of them.  Max and min are
-// done one after the other in the same arrays.
+// Per series, lane l holds elements [l·E, l·E + E) in registers.  Blocks are
+// exactly w elements long, from position 0: the decomposition of Section 2's
+// van Herk/Gil-Werman algorithm (Table 1), so every full window is the suffix
+// of one block and the prefix of the next, one operation per output.  The
+// block scans restart at block boundaries inside a lane and are carried
+// across lanes by a segmented shuffle scan.  Both scans go to a warp-private
+// shared array stored element-major (row = position mod E, column = lane), so
+// a warp reading one position per lane touches 32 consecutive words.  Max and
+// min are done one after the other in the same arrays.
 #pragma once
 #include <cstdint>
 
@@ -34,6 +29,7 @@ template <typename T> struct ShortGeo {
     static constexpr int ROW = 33;                       // shared row stride (values)
     static constexpr size_t warp_bytes = 2 * (size_t)E * ROW * sizeof(R);
     static constexpr size_t smem_bytes = WARPS * warp_bytes;
+    static constexpr size_t smem_bytes_lb = smem_bytes + (size_t)NMAX * sizeof(T);  // + the query
 };
 
 struct ShortParams {
@@ -46,6 +42,7 @@ struct ShortParams {
     int64_t in_elems;    // elements of `in` that may be read
     const void *lb_query;  // envelope lower bound (see BlockScanParams)
     double *lb_acc;
+    int32_t lb_n;          // query length (every series has it)
     uint32_t *status;
 };
 
@@ -86,147 +83,165 @@ __device__ __forceinline__ void short_load(const T *src, int n, int lane, const 
 
 template <bool MAX, typename R> __device__ __forceinline__ R sop(R a, R b) { return MAX ? vmax(a, b) : vmin(a, b); }
 
-// One side (max or min) of one series: block scans into the warp's arrays,
-// then the outputs of this lane's positions into res.  Positions past the
-// series' end in v are set to the side's identity first.
+// One side (max or min) of one series with blocks of exactly w elements
+// from position 0 (van Herk/Gil-Werman's own decomposition): a full window
+// [lo, lo+w-1] then spans exactly two blocks (or is one block), so its
+// extreme is op(suffix_w[lo], prefix_w[lo+w-1]).  A window clipped at the
+// start lies in block 0, which starts at position 0: prefix_w[hi].  A window
+// clipped at the end whose start shares a block with the last element:
+// suffix_w[lo] (identities follow the series).  Positions past the series'
+// end in v are set to the side's identity first.  q0: position lane·E modulo
+// w (the lane's offset in its block); u1: position lane·E + E - 1 modulo w.
+// The scans hold positions lane·E + e (contiguous per lane); the outputs are
+// formed for positions 32k + lane (row k of the series), so every shared read
+// is a per-lane base plus a constant and a warp stores whole rows.  res[k]:
+// the output at position 32k + lane.
 template <typename T, bool MAX>
 __device__ __forceinline__ void short_side(typename Elem<T>::R (&v)[ShortGeo<T>::E], int n, int w, int d,
-                                           int n_out, int lgB, int lane, typename Elem<T>::R *PA,
+                                           int n_out, int q0, int u1, int lane, typename Elem<T>::R *PA,
                                            typename Elem<T>::R *SA, typename Elem<T>::R (&res)[ShortGeo<T>::E]) {
     using G = ShortGeo<T>;
     using R = typename Elem<T>::R;
     constexpr int E = G::E;
+    constexpr int CS = 32 / E;  // columns per row of 32 positions
     const R id = MAX ? Elem<T>::lo() : Elem<T>::hi();
-    const int B = 1 << lgB;
 #pragma unroll
     for (int e = 0; e < E; ++e)
         if (lane * E + e >= n) v[e] = id;
+    const int fs = q0 == 0 ? 0 : w - q0;  // this lane's first block start (>= E: none)
+    const int le = E - 2 - (u1 + 1 == w ? -1 : u1);  // its last block end (< 0: none)
     {
-        // Prefix within blocks.
+        // Prefix, restarting at every block start.
         R pre[E];
         pre[0] = v[0];
+        if (w >= E) {  // at most one start in the lane
 #pragma unroll
-        for (int e = 1; e < E; ++e) pre[e] = (e & (B - 1)) ? sop<MAX>(pre[e - 1], v[e]) : v[e];
-        if (lgB > G::LGE) {
-            // A block spans 2^(lgB - LGE) lanes: exclusive carry from the
-            // earlier lanes of the block.
-            const int seg = 1 << (lgB - G::LGE);
-            const int pos = lane & (seg - 1);
-            R t = pre[E - 1];
+            for (int e = 1; e < E; ++e) pre[e] = e == fs ? v[e] : sop<MAX>(pre[e - 1], v[e]);
+        } else {
+            int t = q0;
 #pragma unroll
-            for (int k = 1; k < 32; k <<= 1) {
-                const R u = __shfl_up_sync(0xffffffffu, t, k);
-                if (k < seg && pos >= k) t = sop<MAX>(t, u);
+            for (int e = 1; e < E; ++e) {
+                t = t + 1 == w ? 0 : t + 1;
+                pre[e] = t == 0 ? v[e] : sop<MAX>(pre[e - 1], v[e]);
             }
-            const R ex = __shfl_up_sync(0xffffffffu, t, 1);
-            if (pos) {
+        }
+        // Elements before the lane's first block start continue the block of
+        // earlier lanes: segmented scan of (lane total since its last start,
+        // lane holds a start) over the lanes.
+        R tt = pre[E - 1];
+        bool f = fs < E;
 #pragma unroll
-                for (int e = 0; e < E; ++e) pre[e] = sop<MAX>(pre[e], ex);
+        for (int k = 1; k < 32; k <<= 1) {
+            const R a = __shfl_up_sync(0xffffffffu, tt, k);
+            const bool fa = __shfl_up_sync(0xffffffffu, (int)f, k) != 0;
+            if (lane >= k) {
+                if (!f) tt = sop<MAX>(a, tt);
+                f = f || fa;
             }
+        }
+        const R carry = __shfl_up_sync(0xffffffffu, tt, 1);
+        if (lane > 0) {
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                if (e < fs) pre[e] = sop<MAX>(pre[e], carry);
         }
 #pragma unroll
         for (int e = 0; e < E; ++e) PA[e * G::ROW + lane] = pre[e];
     }
     {
-        // Suffix within blocks.
+        // Suffix, restarting at every block end.
         R suf[E];
         suf[E - 1] = v[E - 1];
+        if (w >= E) {  // at most one end in the lane
 #pragma unroll
-        for (int e = E - 2; e >= 0; --e) suf[e] = ((e + 1) & (B - 1)) ? sop<MAX>(suf[e + 1], v[e]) : v[e];
-        if (lgB > G::LGE) {
-            const int seg = 1 << (lgB - G::LGE);
-            const int pos = (seg - 1) - (lane & (seg - 1));
-            R t = suf[0];
+            for (int e = E - 2; e >= 0; --e) suf[e] = e == le ? v[e] : sop<MAX>(suf[e + 1], v[e]);
+        } else {
+            int t = u1;
 #pragma unroll
-            for (int k = 1; k < 32; k <<= 1) {
-                const R u = __shfl_down_sync(0xffffffffu, t, k);
-                if (k < seg && pos >= k) t = sop<MAX>(t, u);
+            for (int e = E - 2; e >= 0; --e) {
+                t = t == 0 ? w - 1 : t - 1;
+                suf[e] = t == w - 1 ? v[e] : sop<MAX>(suf[e + 1], v[e]);
             }
-            const R ex = __shfl_down_sync(0xffffffffu, t, 1);
-            if (pos) {
+        }
+        R tt = suf[0];
+        bool f = le >= 0;
 #pragma unroll
-                for (int e = 0; e < E; ++e) suf[e] = sop<MAX>(suf[e], ex);
+        for (int k = 1; k < 32; k <<= 1) {
+            const R a = __shfl_down_sync(0xffffffffu, tt, k);
+            const bool fa = __shfl_down_sync(0xffffffffu, (int)f, k) != 0;
+            if (lane + k < 32) {
+                if (!f) tt = sop<MAX>(tt, a);
+                f = f || fa;
             }
+        }
+        const R carry = __shfl_down_sync(0xffffffffu, tt, 1);
+        if (lane < 31) {
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                if (e > le) suf[e] = sop<MAX>(suf[e], carry);
         }
 #pragma unroll
         for (int e = 0; e < E; ++e) SA[e * G::ROW + lane] = suf[e];
     }
     __syncwarp();
-    // Position p lives at row p mod E, column p / E.
+    // Position p lives at row p mod E, column p / E; for p = 32k + c the row
+    // is c mod E and the column CS·k + c / E, so lo = 32k + (lane + d) and
+    // hi = lo + w - 1 read at a per-lane base plus CS·k.
+    const int a = lane + d, b = a + w - 1;
+    const R *sb = SA + (a & (E - 1)) * G::ROW + (a >> G::LGE);
+    const R *pb = PA + (b & (E - 1)) * G::ROW + (b >> G::LGE);
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int o = lane * E + e;
-        R r = id;
-        if (o < n_out) {
-            int lo = o + d;
-            int hi = lo + w - 1;
-            if (lo < 0) lo = 0;
-            if (hi > n - 1) hi = n - 1;
-            const int bl = lo >> lgB, bh = hi >> lgB;
-            const R P = PA[(hi & (E - 1)) * G::ROW + (hi >> G::LGE)];
-            const R S = SA[(lo & (E - 1)) * G::ROW + (lo >> G::LGE)];
-            if (bl == bh) {
-                r = (lo & (B - 1)) == 0 ? P : S;
-            } else {
-                r = sop<MAX>(S, P);
-                if (bh - bl == 2) {
-                    const int m = (bl + 1) << lgB;
-                    r = sop<MAX>(r, SA[(m & (E - 1)) * G::ROW + (m >> G::LGE)]);
+    for (int k = 0; k < E; ++k) {
+        const int r0 = 32 * k;  // first position of row k
+        if (r0 + d >= 0 && r0 + 31 + d + w - 1 <= n - 1 && r0 + 31 < n_out) {
+            res[k] = sop<MAX>(sb[CS * k], pb[CS * k]);  // no window of the row is clipped
+        } else {
+            const int o = r0 + lane;
+            R r = id;
+            if (o < n_out) {
+                const int lo = o + d;
+                int hi = lo + w - 1;
+                if (hi > n - 1) hi = n - 1;
+                const R P = PA[(hi & (E - 1)) * G::ROW + (hi >> G::LGE)];
+                if (lo <= 0) {
+                    r = P;  // clipped at the start: block 0 from position 0
+                } else {
+                    const R S = SA[(lo & (E - 1)) * G::ROW + (lo >> G::LGE)];
+                    r = lo / w == hi / w ? S : sop<MAX>(S, P);
                 }
             }
+            res[k] = r;
         }
-        res[e] = r;
     }
     __syncwarp();
 }
 
+// Outputs of positions 32k + lane (row k) of one side to dst: every row is
+// one coalesced 32-element store.
 template <typename T>
-__device__ __forceinline__ void short_store(T *dst, int lane, int n_out, const typename Elem<T>::R (&r)[ShortGeo<T>::E]) {
-    constexpr int E = ShortGeo<T>::E;
-    T *p = dst + lane * E;
-    if (lane * E + E <= n_out && (((uintptr_t)p) & 15) == 0) {
-        uint4 *d4 = reinterpret_cast<uint4 *>(p);
+__device__ __forceinline__ void short_store_rows(T *dst, int lane, int n_out,
+                                                 const typename Elem<T>::R (&r)[ShortGeo<T>::E]) {
 #pragma unroll
-        for (int c = 0; c < E * (int)sizeof(T) / 16; ++c)
-            __stcs(d4 + c, make_uint4(pack_word<T>(r, 4 * c), pack_word<T>(r, 4 * c + 1), pack_word<T>(r, 4 * c + 2),
-                                      pack_word<T>(r, 4 * c + 3)));
-    } else {
-#pragma unroll
-        for (int e = 0; e < E; ++e)
-            if (lane * E + e < n_out) p[e] = Elem<T>::store(r[e]);
-    }
+    for (int k = 0; k < ShortGeo<T>::E; ++k)
+        if (32 * k + lane < n_out) __stcs(dst + 32 * k + lane, Elem<T>::store(r[k]));
 }
 
 // One side of the envelope lower bound for this lane's positions: the
 // squared excursions of the query above the upper envelope (MAX) or below
 // the lower one.  The two never both occur at a position (U >= L), so the
 // sides add up to the bound's terms.
+// query: the CTA's shared copy.
 template <typename T, bool MAX>
 __device__ __forceinline__ typename LbAcc<T>::A short_lb_side(const T *query, int lane, int n_out,
                                                               const typename Elem<T>::R (&r)[ShortGeo<T>::E]) {
     using A = typename LbAcc<T>::A;
-    constexpr int E = ShortGeo<T>::E;
-    const T *q = query + lane * E;
     A part = A(0);
-    if (lane * E + E <= n_out && (((uintptr_t)q) & 15) == 0) {
-        T qv[E];
 #pragma unroll
-        for (int c = 0; c < E * (int)sizeof(T) / 16; ++c)
-            reinterpret_cast<uint4 *>(qv)[c] = __ldg(reinterpret_cast<const uint4 *>(q) + c);
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const A qi = (A)qv[e];
-            const A v = (A)Elem<T>::store(r[e]);
-            const A dd = MAX ? (qi > v ? qi - v : A(0)) : (qi < v ? v - qi : A(0));
-            part += dd * dd;
-        }
-        return part;
-    }
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        if (lane * E + e < n_out) {
-            const A qi = (A)__ldg(q + e);
-            const A v = (A)Elem<T>::store(r[e]);
+    for (int k = 0; k < ShortGeo<T>::E; ++k) {
+        const int o = 32 * k + lane;
+        if (o < n_out) {
+            const A qi = (A)query[o];
+            const A v = (A)Elem<T>::store(r[k]);
             const A dd = MAX ? (qi > v ? qi - v : A(0)) : (qi < v ? v - qi : A(0));
             part += dd * dd;
         }
@@ -245,6 +260,12 @@ __global__ void __launch_bounds__(ShortGeo<T>::WARPS * 32, 2) short_kernel(const
     R *SA = PA + E * G::ROW;
     const T *buf = reinterpret_cast<const T *>(P.in);
     const int64_t nwarps = (int64_t)gridDim.x * G::WARPS;
+    T *qs = reinterpret_cast<T *>(short_smem + G::smem_bytes);  // LB: the query, once per CTA
+    if constexpr (LB) {
+        const T *q = reinterpret_cast<const T *>(P.lb_query);
+        for (int i = threadIdx.x; i < P.lb_n && i < G::NMAX; i += blockDim.x) qs[i] = __ldg(q + i);
+        __syncthreads();
+    }
     for (int64_t k = (int64_t)blockIdx.x * G::WARPS + wib; k < P.count; k += nwarps) {
         const int64_t sid = P.ids[k];
         const SeriesDesc sd = P.series[sid];
@@ -262,8 +283,7 @@ __global__ void __launch_bounds__(ShortGeo<T>::WARPS * 32, 2) short_kernel(const
         // Windows longer than twice the longest series act like 2·NMAX
         // (every one of them is clipped to the series): 32-bit positions.
         const int wi = (int)(w < 2 * G::NMAX ? w : 2 * G::NMAX);
-        int lgB = 0;
-        while ((2 << lgB) <= (wi < G::NMAX ? wi : G::NMAX)) ++lgB;
+        const int q0 = (lane * E) % wi, u1 = (lane * E + E - 1) % wi;
         // Each side loads the series again (L2-resident): the values of one
         // side need not stay in registers through the other.
         using A = typename LbAcc<T>::A;
@@ -271,21 +291,21 @@ __global__ void __launch_bounds__(ShortGeo<T>::WARPS * 32, 2) short_kernel(const
         {
             R x[E], r[E];
             short_load<T>(buf + sd.in_off, n, lane, buf, P.in_elems, x);
-            short_side<T, true>(x, n, wi, d, n_out, lgB, lane, PA, SA, r);
+            short_side<T, true>(x, n, wi, d, n_out, q0, u1, lane, PA, SA, r);
             if constexpr (LB)
-                part += short_lb_side<T, true>(reinterpret_cast<const T *>(P.lb_query), lane, n_out, r);
+                part += short_lb_side<T, true>(qs, lane, n_out, r);
             else if (P.out_max)
-                short_store<T>(reinterpret_cast<T *>(P.out_max) + sd.out_off, lane, n_out, r);
+                short_store_rows<T>(reinterpret_cast<T *>(P.out_max) + sd.out_off, lane, n_out, r);
         }
         __syncwarp();  // keeps the next side's loads after this side's stores (register pressure)
         {
             R x[E], r[E];
             short_load<T>(buf + sd.in_off, n, lane, buf, P.in_elems, x);
-            short_side<T, false>(x, n, wi, d, n_out, lgB, lane, PA, SA, r);
+            short_side<T, false>(x, n, wi, d, n_out, q0, u1, lane, PA, SA, r);
             if constexpr (LB)
-                part += short_lb_side<T, false>(reinterpret_cast<const T *>(P.lb_query), lane, n_out, r);
+                part += short_lb_side<T, false>(qs, lane, n_out, r);
             else if (P.out_min)
-                short_store<T>(reinterpret_cast<T *>(P.out_min) + sd.out_off, lane, n_out, r);
+                short_store_rows<T>(reinterpret_cast<T *>(P.out_min) + sd.out_off, lane, n_out, r);
         }
         if constexpr (LB) {
             // This warp owns the series: the sum needs no atomics (the
@@ -305,11 +325,11 @@ template <typename T> cudaError_t short_prepare(int device, bool lb, int *per_sm
     int &k = occ[lb][device & 63];
     if (k == 0) {
         cudaError_t e = lb ? cudaFuncSetAttribute(short_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)G::smem_bytes)
+                                                  (int)G::smem_bytes_lb)
                            : cudaFuncSetAttribute(short_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   (int)G::smem_bytes);
         if (e != cudaSuccess) return e;
-        e = lb ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, short_kernel<T, true>, G::WARPS * 32, G::smem_bytes)
+        e = lb ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, short_kernel<T, true>, G::WARPS * 32, G::smem_bytes_lb)
                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, short_kernel<T, false>, G::WARPS * 32, G::smem_bytes);
         if (e != cudaSuccess) return e;
         if (k < 1) k = 1;
@@ -322,7 +342,7 @@ template <typename T> cudaError_t short_prepare(int device, bool lb, int *per_sm
 template <typename T>
 cudaError_t short_table(const LaunchCtx &ctx, const void *in, int64_t in_elems, void *omax, void *omin,
                         const SeriesDesc *d_series, const int64_t *d_ids, int64_t count, const void *lb_query,
-                        double *lb_acc) {
+                        double *lb_acc, int64_t lb_n) {
     using G = ShortGeo<T>;
     static_assert(G::NMAX == short_max_len(sizeof(T)), "host and kernel agree on short series");
     if (count <= 0) return cudaSuccess;
@@ -340,12 +360,13 @@ cudaError_t short_table(const LaunchCtx &ctx, const void *in, int64_t in_elems, 
     P.in_elems = in_elems;
     P.lb_query = lb_query;
     P.lb_acc = lb_acc;
+    P.lb_n = (int32_t)(lb_n < G::NMAX ? lb_n : G::NMAX);
     P.status = ctx.status;
     const int64_t need = (count + G::WARPS - 1) / G::WARPS;
     const int64_t wave = (int64_t)(ctx.sms > 0 ? ctx.sms : 1) * k;
     const unsigned grid = (unsigned)(need < wave ? need : wave);
     if (lb)
-        short_kernel<T, true><<<grid, G::WARPS * 32, G::smem_bytes, ctx.stream>>>(P);
+        short_kernel<T, true><<<grid, G::WARPS * 32, G::smem_bytes_lb, ctx.stream>>>(P);
     else
         short_kernel<T, false><<<grid, G::WARPS * 32, G::smem_bytes, ctx.stream>>>(P);
     return cudaGetLastError();
