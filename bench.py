@@ -117,6 +117,21 @@ def _dist_env():
     return ws, rank, local
 
 
+def job_time(elapsed_ms, per_rank_elems, ws, device="cpu"):
+    """Whole-job timing across ranks: the slowest rank's elapsed time (max
+    over ranks, all_reduce on the process group when ws > 1) and the elements
+    all ranks processed (each rank filters its own streams: weak scaling, no
+    data exchange).  Returns (elapsed_ms, total_elements, Gelem/s)."""
+    import torch
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([float(elapsed_ms)], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    total = per_rank_elems * ws
+    return elapsed_ms, total, total / (elapsed_ms * 1e-3) / 1e9
+
+
 def run_reference(args):
     """CPU oracle (Algorithm 1 on all host cores, chunks with a w-1 halo) on a
     bounded sample per step."""
@@ -555,15 +570,8 @@ def main():
     if ws > 1:
         dist.barrier()
     clocks = sampler.stop()
-    elapsed_ms = t_start.elapsed_time(t_end)
-    if ws > 1:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-
     per_step_elems = len(DISTS) * len(WINDOWS) * n
-    total_elems = per_step_elems * args.steps * ws
-    value = total_elems / (elapsed_ms * 1e-3) / 1e9
+    elapsed_ms, total_elems, value = job_time(t_start.elapsed_time(t_end), per_step_elems * args.steps, ws, dev)
 
     # Roofline of the dominant kernel.  Each window maps to one kernel
     # instantiation (mode): 3 register slide, 1 sub-warp blocks, 2 warp blocks.
