@@ -251,7 +251,16 @@ def batched_extras(dev, stream, peak, reps=5, envelope_series=1_000_000):
         plan.close()
         del x, om, on
     torch.cuda.empty_cache()
-    # Envelope: z-normalised random walks, 1024 each, centred windows r = 51.
+    out.update(envelope_extras(dev, stream, peak, reps=reps, envelope_series=envelope_series))
+    return out
+
+
+def envelope_extras(dev, stream, peak, reps=5, envelope_series=1_000_000):
+    """Envelope batch (z-normalised random walks of 1024, r = 51) batched and
+    per series, and the LB_Keogh bound of one query against the same series."""
+    import torch
+    import paper_cs_0610046_gb300 as mmf
+    out = {}
     ns, L, r = envelope_series, 1024, 51
     g = torch.Generator(device=dev)
     g.manual_seed(33)
@@ -478,6 +487,8 @@ def run_only(args):
         r = wedge_extras(dev, stream, peak, n=(1 << 26) if args.small else (1 << 30))
     elif args.only == "batched":
         r = batched_extras(dev, stream, peak, envelope_series=100_000 if args.small else 1_000_000)
+    elif args.only == "envelope":
+        r = envelope_extras(dev, stream, peak, envelope_series=100_000 if args.small else 1_000_000)
     elif args.only == "filter2d":
         r = filter2d_extras(dev, stream, peak, nimg=4 if args.small else 64)
     else:
@@ -499,7 +510,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched/2D/serving measurements")
-    ap.add_argument("--only", choices=["wedge", "batched", "filter2d", "serving"],
+    ap.add_argument("--only", choices=["wedge", "batched", "envelope", "filter2d", "serving"],
                     help="run one extra measurement alone and print its JSON (profiling)")
     ap.add_argument("--small", action="store_true",
                     help="with --only: a smaller instance of that workload (profiling captures)")
