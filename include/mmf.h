@@ -317,6 +317,20 @@ mmf_status mmf_stream_close(mmf_server *server, uint64_t stream_id, int timeout_
 mmf_status mmf_stream_snapshot(mmf_server *server, uint64_t stream_id, void *h_buf, size_t buf_bytes, size_t *size,
                                int timeout_ms);
 
+/* The same state as the stream's monotonic wedge (Section 4): the samples
+ * that can still be a window maximum (strictly above every later sample: the
+ * deque U of Algorithm 1) or minimum (strictly below every later one: L).  No
+ * other sample can decide a later output (a later, larger and a later,
+ * smaller sample lie in every later window that holds it), so this state
+ * restores the same outputs; it holds about 2 ln(w) samples on i.i.d. noise
+ * and on the order of sqrt(w) on a random walk, where the halo holds w-1
+ * (monotone data: one side is the whole window).  Layout: the header as above with version 2
+ * (halo length h as before), then int64 nU, int64 nL, then nU entries and nL
+ * entries, each an int64 distance back from the count (1..h) followed by the
+ * sample.  Same waiting, sizing and errors as mmf_stream_snapshot. */
+mmf_status mmf_stream_snapshot_wedge(mmf_server *server, uint64_t stream_id, void *h_buf, size_t buf_bytes,
+                                     size_t *size, int timeout_ms);
+
 /* Opens a new stream in the state of a snapshot (from this server or another
  * of the same dtype): its later pushes give exactly the outputs the original
  * stream would have given.  MMF_EINVAL for another dtype, a bad header or a

@@ -99,6 +99,8 @@ _EXTRA_SIGNATURES: dict = {
     "mmf_filter1d_host": ([_VP, _I64, _I64, _INT, _INT, _VP, _VP, _I64, _VP], _INT),
     "mmf_argfilter1d": ([_VP, _I64, _I64, _INT, _VP, _VP, _VP, _VP, _VP], _INT),
     "mmf_stream_snapshot": ([_VP, ctypes.c_uint64, _VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), _INT], _INT),
+    "mmf_stream_snapshot_wedge": ([_VP, ctypes.c_uint64, _VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), _INT],
+                                  _INT),
     "mmf_stream_restore": ([_VP, _VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint64)], _INT),
     "mmf_server_pause": ([_VP, _INT], _INT),
     "mmf_filter2d_workspace": ([_I64, _I64, _I64, _I64, _I64, _INT, _INT, ctypes.POINTER(ctypes.c_size_t)], _INT),
@@ -453,12 +455,14 @@ class Server:
     def close_stream(self, sid: int, timeout_ms: int = 60_000) -> None:
         check(self._lib.mmf_stream_close(self._h, sid, timeout_ms))
 
-    def snapshot(self, sid: int, timeout_ms: int = 60_000) -> bytes:
-        """The stream's state (window, 64-bit count, last w-1 samples) as bytes."""
+    def snapshot(self, sid: int, timeout_ms: int = 60_000, wedge: bool = False) -> bytes:
+        """The stream's state as bytes: window, 64-bit count and the last w-1
+        samples, or (wedge=True) only the samples of its monotonic wedge."""
+        fn = self._lib.mmf_stream_snapshot_wedge if wedge else self._lib.mmf_stream_snapshot
         n = ctypes.c_size_t()
-        check(self._lib.mmf_stream_snapshot(self._h, sid, None, 0, ctypes.byref(n), timeout_ms))
+        check(fn(self._h, sid, None, 0, ctypes.byref(n), timeout_ms))
         buf = ctypes.create_string_buffer(n.value)
-        check(self._lib.mmf_stream_snapshot(self._h, sid, buf, n.value, ctypes.byref(n), timeout_ms))
+        check(fn(self._h, sid, buf, n.value, ctypes.byref(n), timeout_ms))
         return buf.raw[:n.value]
 
     def restore(self, state: bytes) -> int:

@@ -747,17 +747,158 @@ mmf_status mmf_stream_snapshot(mmf_server *S, uint64_t stream_id, void *h_buf, s
     return MMF_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// The halo of a stream: its last h samples as host bytes, after its pending
+// chunks complete (snapshot helpers; S->mu held by the caller).
+mmf_status snapshot_halo(mmf_server *S, uint64_t stream_id, int timeout_ms, std::unique_lock<std::mutex> &lk,
+                         StreamState *out, std::vector<char> *halo) {
+    auto it = S->streams.find(stream_id);
+    if (it == S->streams.end() || it->second.closed)
+        return set_error(MMF_ECLOSED, "stream %llu is not open", (unsigned long long)stream_id);
+    const auto deadline = Clock::now() + std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms);
+    while (S->streams[stream_id].pending > 0) {
+        if (S->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && S->streams[stream_id].pending > 0)
+            return set_error(MMF_ETIMEOUT, "stream %llu still has chunks after %d ms", (unsigned long long)stream_id,
+                             timeout_ms);
+    }
+    if (S->failed != MMF_OK) return set_error(MMF_EDEVICE, "the server failed earlier");
+    *out = S->streams[stream_id];
+    halo->assign((size_t)out->halo_len * S->esz, 0);
+    if (out->halo_len > 0) {
+        cudaSetDevice(S->device);
+        cudaError_t e = cudaMemcpy(halo->data(), S->dev_base + out->halo_off, halo->size(), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_error(e, "snapshot copy");
+    }
+    return MMF_OK;
+}
+
+// Positions (0..h-1) of the samples strictly above (MAX) or below every later
+// one, oldest first: the monotonic wedge's deque of that side.
+template <typename T, bool MAX> void wedge_side(const T *a, int64_t h, std::vector<int64_t> *out) {
+    out->clear();
+    for (int64_t k = 0; k < h; ++k) {
+        while (!out->empty() && (MAX ? !(a[out->back()] > a[k]) : !(a[out->back()] < a[k]))) out->pop_back();
+        out->push_back(k);
+    }
+}
+
+template <typename T>
+void wedge_sides(const char *halo, int64_t h, std::vector<int64_t> *u, std::vector<int64_t> *l) {
+    const T *a = reinterpret_cast<const T *>(halo);
+    wedge_side<T, true>(a, h, u);
+    wedge_side<T, false>(a, h, l);
+}
+
+// A halo with the same later outputs as the wedge: samples of U or L keep
+// their values, every other one takes the value of the nearest later sample
+// of U (within every later window that holds it, and at least as large).
+template <typename T>
+void halo_from_wedge(const char *entries, int64_t nu, int64_t nl, int64_t h, char *halo) {
+    T *a = reinterpret_cast<T *>(halo);
+    std::vector<char> set(h, 0);
+    std::vector<T> uval(h);
+    const size_t rec = 8 + sizeof(T);
+    for (int64_t j = 0; j < nu + nl; ++j) {
+        int64_t back;
+        T v;
+        memcpy(&back, entries + j * rec, 8);
+        memcpy(&v, entries + j * rec + 8, sizeof(T));
+        const int64_t k = h - back;
+        a[k] = v;
+        set[k] = 1;
+        if (j < nu) set[k] = 2;  // in U
+    }
+    T last = a[h - 1];  // the newest sample is in both deques
+    for (int64_t k = h - 1; k >= 0; --k) {
+        if (set[k] == 2) last = a[k];
+        else if (set[k] == 0) a[k] = last;
+    }
+}
+}  // namespace
+
+extern "C" {
+
+mmf_status mmf_stream_snapshot_wedge(mmf_server *S, uint64_t stream_id, void *h_buf, size_t buf_bytes, size_t *size,
+                                     int timeout_ms) {
+    if (!S || !size) return set_error(MMF_EINVAL, "NULL argument");
+    std::unique_lock<std::mutex> lk(S->mu);
+    StreamState ss;
+    std::vector<char> halo;
+    mmf_status st = snapshot_halo(S, stream_id, timeout_ms, lk, &ss, &halo);
+    if (st != MMF_OK) return st;
+    std::vector<int64_t> u, l;
+    switch (S->dtype) {
+        case MMF_F32: wedge_sides<float>(halo.data(), ss.halo_len, &u, &l); break;
+        case MMF_F64: wedge_sides<double>(halo.data(), ss.halo_len, &u, &l); break;
+        case MMF_I16: wedge_sides<int16_t>(halo.data(), ss.halo_len, &u, &l); break;
+        default: wedge_sides<uint8_t>(halo.data(), ss.halo_len, &u, &l); break;
+    }
+    const size_t rec = 8 + (size_t)S->esz;
+    const size_t need = sizeof(SnapshotHeader) + 16 + (u.size() + l.size()) * rec;
+    *size = need;
+    if (!h_buf) return MMF_OK;
+    if (buf_bytes < need) return set_error(MMF_EINVAL, "snapshot needs %zu bytes", need);
+    char *p = static_cast<char *>(h_buf);
+    SnapshotHeader hd{MMF_SNAPSHOT_MAGIC, 2u, (int32_t)S->dtype, 0, ss.w, ss.count, ss.halo_len};
+    memcpy(p, &hd, sizeof(hd));
+    p += sizeof(hd);
+    const int64_t nu = (int64_t)u.size(), nl = (int64_t)l.size();
+    memcpy(p, &nu, 8);
+    memcpy(p + 8, &nl, 8);
+    p += 16;
+    for (const auto *side : {&u, &l}) {
+        for (int64_t k : *side) {
+            const int64_t back = ss.halo_len - k;
+            memcpy(p, &back, 8);
+            memcpy(p + 8, halo.data() + k * S->esz, S->esz);
+            p += rec;
+        }
+    }
+    return MMF_OK;
+}
+
 mmf_status mmf_stream_restore(mmf_server *S, const void *h_buf, size_t buf_bytes, uint64_t *stream_id) {
     if (!S || !h_buf || !stream_id) return set_error(MMF_EINVAL, "NULL argument");
     if (buf_bytes < sizeof(SnapshotHeader)) return set_error(MMF_EINVAL, "snapshot shorter than its header");
     SnapshotHeader hd;
     memcpy(&hd, h_buf, sizeof(hd));
-    if (hd.magic != MMF_SNAPSHOT_MAGIC || hd.version != 1u || hd.zero != 0)
+    if (hd.magic != MMF_SNAPSHOT_MAGIC || (hd.version != 1u && hd.version != 2u) || hd.zero != 0)
         return set_error(MMF_EINVAL, "not a stream snapshot");
     if (hd.dtype != (int32_t)S->dtype) return set_error(MMF_EINVAL, "snapshot of another dtype");
     if (hd.w < 1 || hd.count < 0 || hd.halo_len != std::min<int64_t>(hd.count, hd.w - 1))
         return set_error(MMF_EINVAL, "inconsistent snapshot header");
-    if (buf_bytes < sizeof(hd) + (size_t)hd.halo_len * S->esz) return set_error(MMF_EINVAL, "truncated snapshot");
+    std::vector<char> rebuilt;
+    const char *halo_bytes = static_cast<const char *>(h_buf) + sizeof(hd);
+    if (hd.version == 2u) {
+        // A wedge: rebuild an equivalent halo.
+        if (buf_bytes < sizeof(hd) + 16) return set_error(MMF_EINVAL, "truncated snapshot");
+        int64_t nu, nl;
+        memcpy(&nu, halo_bytes, 8);
+        memcpy(&nl, halo_bytes + 8, 8);
+        const size_t rec = 8 + (size_t)S->esz;
+        if (nu < 0 || nl < 0 || nu > hd.halo_len || nl > hd.halo_len || (hd.halo_len > 0 && (nu < 1 || nl < 1)) ||
+            buf_bytes < sizeof(hd) + 16 + (size_t)(nu + nl) * rec)
+            return set_error(MMF_EINVAL, "truncated or inconsistent wedge snapshot");
+        for (int64_t j = 0; j < nu + nl; ++j) {
+            int64_t back;
+            memcpy(&back, halo_bytes + 16 + j * rec, 8);
+            if (back < 1 || back > hd.halo_len) return set_error(MMF_EINVAL, "wedge entry outside the halo");
+        }
+        rebuilt.assign((size_t)hd.halo_len * S->esz, 0);
+        if (hd.halo_len > 0) {
+            switch (S->dtype) {
+                case MMF_F32: halo_from_wedge<float>(halo_bytes + 16, nu, nl, hd.halo_len, rebuilt.data()); break;
+                case MMF_F64: halo_from_wedge<double>(halo_bytes + 16, nu, nl, hd.halo_len, rebuilt.data()); break;
+                case MMF_I16: halo_from_wedge<int16_t>(halo_bytes + 16, nu, nl, hd.halo_len, rebuilt.data()); break;
+                default: halo_from_wedge<uint8_t>(halo_bytes + 16, nu, nl, hd.halo_len, rebuilt.data()); break;
+            }
+        }
+        halo_bytes = rebuilt.data();
+    } else if (buf_bytes < sizeof(hd) + (size_t)hd.halo_len * S->esz) {
+        return set_error(MMF_EINVAL, "truncated snapshot");
+    }
     uint64_t id = 0;
     mmf_status st = mmf_stream_open(S, hd.w, &id);
     if (st != MMF_OK) return st;
@@ -765,8 +906,8 @@ mmf_status mmf_stream_restore(mmf_server *S, const void *h_buf, size_t buf_bytes
     StreamState &ss = S->streams[id];
     if (hd.halo_len > 0) {
         cudaSetDevice(S->device);
-        cudaError_t e = cudaMemcpy(S->dev_base + ss.halo_off, static_cast<const char *>(h_buf) + sizeof(hd),
-                                   (size_t)hd.halo_len * S->esz, cudaMemcpyHostToDevice);
+        cudaError_t e = cudaMemcpy(S->dev_base + ss.halo_off, halo_bytes, (size_t)hd.halo_len * S->esz,
+                                   cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
             if (ss.halo_off >= 0) S->stage.release(ss.halo_off, (size_t)(ss.w - 1) * S->esz);
             S->streams.erase(id);

@@ -271,3 +271,58 @@ def test_snapshot_64bit_count_and_rejects(mmf):
             srv.restore(bad)
     srv.close()
     assert mmf.device_status() == 0
+
+
+@pytest.mark.parametrize("kind", ["random_walk", "uniform", "increasing", "decreasing", "constant", "steps"])
+@pytest.mark.parametrize("w", [2, 33, 9001])
+def test_wedge_snapshot_continues_exactly(mmf, kind, w):
+    """A stream restored from its monotonic wedge (Section 4) continues with
+    the outputs of the original: samples outside the wedge never decide a
+    later window's extreme.  Ties (constant data, steps) included."""
+    n, cut = 40_000, 23_456
+    if kind == "increasing":
+        data = np.arange(n, dtype=np.float32)
+    elif kind == "decreasing":
+        data = np.arange(n, 0, -1).astype(np.float32)
+    elif kind == "constant":
+        data = np.full(n, 2.5, np.float32)
+    elif kind == "steps":
+        data = np.repeat(synth.uniform(n // 100, seed=w, dtype=np.float32), 100)
+    else:
+        data = synth.by_name(kind, n, seed=w, dtype=np.float32)
+    rng = np.random.default_rng(w)
+    first = _split(cut, rng, 1, 3000)
+    rest = _split(n - cut, rng, 1, 5000)
+    srv = mmf.Server(1 << 26, 32, "float32")
+    sid = srv.open(w)
+    _push_all(mmf, srv, sid, data, 0, first, w)
+    full = srv.snapshot(sid)
+    wedge = srv.snapshot(sid, wedge=True)
+    m1, n1 = _push_all(mmf, srv, sid, data, cut, rest, w)
+    sid2 = srv.restore(wedge)
+    m2, n2 = _push_all(mmf, srv, sid2, data, cut, rest, w)
+    assert np.array_equal(m1, m2) and np.array_equal(n1, n2)
+    if w == 9001:
+        # i.i.d. noise: about ln(w) records per side; a random walk: on the
+        # order of sqrt(w); monotone data: one side holds the whole window.
+        if kind == "uniform":
+            assert len(wedge) < len(full) // 50
+        if kind == "random_walk":
+            assert len(wedge) < len(full) // 5
+    srv.close()
+    assert mmf.device_status() == 0
+
+
+def test_wedge_snapshot_rejects_bad_entries(mmf):
+    import struct
+    srv = mmf.Server(1 << 24, 8, "float32")
+    hdr = struct.pack("<IIiiqqq", 0x53464D4D, 2, 0, 0, 5, 100, 4)
+    good = hdr + struct.pack("<qq", 1, 1) + struct.pack("<qf", 1, 1.0) + struct.pack("<qf", 1, 1.0)
+    sid = srv.restore(good)
+    assert sid > 0
+    for bad in (hdr + struct.pack("<qq", 1, 1) + struct.pack("<qf", 5, 1.0) + struct.pack("<qf", 1, 1.0),
+                hdr + struct.pack("<qq", 0, 1) + struct.pack("<qf", 1, 1.0),
+                hdr + struct.pack("<qq", 1, 1) + struct.pack("<qf", 1, 1.0)):
+        with pytest.raises(mmf.MMFError):
+            srv.restore(bad)
+    srv.close()
