@@ -103,6 +103,33 @@ static cudaError_t tile_launch(const LaunchCtx &ctx, const T *in, int64_t nimg, 
         kernel<<<(unsigned)grid, kTThreads, smem, ctx.stream>>>(P);
         return cudaGetLastError();
     };
+    // Windows up to 7 (f32): the persistent form, one wave of CTAs.
+    auto go_pf = [&](auto kernel, int slot) -> cudaError_t {
+        static size_t set[64][2] = {};
+        static int occ[64][2] = {};
+        size_t &have = set[ctx.device & 63][slot];
+        int &k = occ[ctx.device & 63][slot];
+        if (smem > have) {
+            cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            have = smem;
+            k = 0;
+        }
+        if (k == 0) {
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, kernel, kTThreads, smem);
+            if (e != cudaSuccess) return e;
+            if (k < 1) k = 1;
+        }
+        const int64_t wave = (int64_t)(ctx.sms > 0 ? ctx.sms : 1) * k;
+        kernel<<<(unsigned)(grid < wave ? grid : wave), kTThreads, smem, ctx.stream>>>(P);
+        return cudaGetLastError();
+    };
+    // f32 windows up to 3: the 1-2 byte types are bound by instructions (the
+    // one-tile kernel keeps 4 CTAs per SM to the persistent form's 2), f64
+    // and the depth-4 form spill.
+    if constexpr (sizeof(T) == 4) {
+        if (pmax <= 2) return go_pf(tile2d_pf_kernel<T, 2>, 0);
+    }
     switch (pmax) {
         case 1:
         case 2: return go(tile2d_kernel<T, 2>, 0);

@@ -716,37 +716,6 @@ struct SnapshotHeader {
 static_assert(sizeof(SnapshotHeader) == MMF_SNAPSHOT_HEADER_BYTES, "snapshot header layout");
 }  // namespace
 
-mmf_status mmf_stream_snapshot(mmf_server *S, uint64_t stream_id, void *h_buf, size_t buf_bytes, size_t *size,
-                               int timeout_ms) {
-    if (!S || !size) return set_error(MMF_EINVAL, "NULL argument");
-    std::unique_lock<std::mutex> lk(S->mu);
-    auto it = S->streams.find(stream_id);
-    if (it == S->streams.end() || it->second.closed)
-        return set_error(MMF_ECLOSED, "stream %llu is not open", (unsigned long long)stream_id);
-    const auto deadline = Clock::now() + std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms);
-    while (S->streams[stream_id].pending > 0) {
-        if (S->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && S->streams[stream_id].pending > 0)
-            return set_error(MMF_ETIMEOUT, "stream %llu still has chunks after %d ms", (unsigned long long)stream_id,
-                             timeout_ms);
-    }
-    if (S->failed != MMF_OK) return set_error(MMF_EDEVICE, "the server failed earlier");
-    const StreamState ss = S->streams[stream_id];
-    const size_t need = sizeof(SnapshotHeader) + (size_t)ss.halo_len * S->esz;
-    *size = need;
-    if (!h_buf) return MMF_OK;
-    if (buf_bytes < need) return set_error(MMF_EINVAL, "snapshot needs %zu bytes", need);
-    SnapshotHeader hd{MMF_SNAPSHOT_MAGIC, 1u, (int32_t)S->dtype, 0, ss.w, ss.count, ss.halo_len};
-    memcpy(h_buf, &hd, sizeof(hd));
-    if (ss.halo_len > 0) {
-        cudaSetDevice(S->device);
-        // No chunk of this stream is pending, so no batch touches its halo.
-        cudaError_t e = cudaMemcpy(static_cast<char *>(h_buf) + sizeof(hd), S->dev_base + ss.halo_off,
-                                   (size_t)ss.halo_len * S->esz, cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) return cuda_error(e, "snapshot copy");
-    }
-    return MMF_OK;
-}
-
 }  // extern "C"
 
 namespace {
@@ -819,6 +788,24 @@ void halo_from_wedge(const char *entries, int64_t nu, int64_t nl, int64_t h, cha
 }  // namespace
 
 extern "C" {
+
+mmf_status mmf_stream_snapshot(mmf_server *S, uint64_t stream_id, void *h_buf, size_t buf_bytes, size_t *size,
+                               int timeout_ms) {
+    if (!S || !size) return set_error(MMF_EINVAL, "NULL argument");
+    std::unique_lock<std::mutex> lk(S->mu);
+    StreamState ss;
+    std::vector<char> halo;
+    mmf_status st = snapshot_halo(S, stream_id, timeout_ms, lk, &ss, &halo);
+    if (st != MMF_OK) return st;
+    const size_t need = sizeof(SnapshotHeader) + halo.size();
+    *size = need;
+    if (!h_buf) return MMF_OK;
+    if (buf_bytes < need) return set_error(MMF_EINVAL, "snapshot needs %zu bytes", need);
+    SnapshotHeader hd{MMF_SNAPSHOT_MAGIC, 1u, (int32_t)S->dtype, 0, ss.w, ss.count, ss.halo_len};
+    memcpy(h_buf, &hd, sizeof(hd));
+    if (!halo.empty()) memcpy(static_cast<char *>(h_buf) + sizeof(hd), halo.data(), halo.size());
+    return MMF_OK;
+}
 
 mmf_status mmf_stream_snapshot_wedge(mmf_server *S, uint64_t stream_id, void *h_buf, size_t buf_bytes, size_t *size,
                                      int timeout_ms) {

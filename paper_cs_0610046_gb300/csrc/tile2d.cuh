@@ -188,4 +188,92 @@ __global__ void __launch_bounds__(kTThreads, (tile_min_blocks<T, PMAX>())) tile2
     }
 }
 
+// Persistent form for small windows (doubling depth PMAX, used for f32
+// windows up to 3): each thread keeps its share of the next tile's input in
+// registers (rows warp + 8i, columns lane + 32j), so the loads of the next
+// tile are in flight while this one is filtered; the one-tile kernel above
+// waits for its loads with nothing else to do (ncu on f32 3x3: the global-load
+// wait was the largest stall).
+template <int PMAX> struct TilePf {
+    static constexpr int ROWS = kTR + 2 * PMAX - 1;  // rows_in for windows below 2·PMAX
+    static constexpr int COLS = kTC + 2 * PMAX - 1;
+    static constexpr int RPW = (ROWS + 7) / 8;       // rows per warp (8 warps)
+    static constexpr int CPL = (COLS + 31) / 32;     // columns per lane
+};
+
+// Image, first output row and first output column of tile `tile`.
+__device__ __forceinline__ void tile_origin(const Tile2DParams &P, int64_t tile, int64_t &img, int64_t &y0,
+                                            int64_t &x0) {
+    const int64_t per_img = (int64_t)P.tiles_x * P.tiles_y;
+    img = tile / per_img;
+    const int64_t t = tile - img * per_img;
+    y0 = (t / P.tiles_x) * kTR;
+    x0 = (t % P.tiles_x) * kTC;
+}
+
+template <typename T, int PMAX>
+__device__ __forceinline__ void tile_pf_load(const Tile2DParams &P, int64_t tile, int rows_in, int cols_in, int warp,
+                                             int lane, T (&v)[TilePf<PMAX>::RPW][TilePf<PMAX>::CPL]) {
+    int64_t img, y0, x0;
+    tile_origin(P, tile, img, y0, x0);
+    const T *src = reinterpret_cast<const T *>(P.in) + img * P.img_stride;
+#pragma unroll
+    for (int i = 0; i < TilePf<PMAX>::RPW; ++i) {
+        const int r = warp + 8 * i;
+        const int64_t y = y0 + r;
+        const T *row = src + y * P.pitch + x0;
+#pragma unroll
+        for (int j = 0; j < TilePf<PMAX>::CPL; ++j) {
+            const int c = lane + 32 * j;
+            v[i][j] = (r < rows_in && c < cols_in && y < P.H && x0 + c < P.W) ? __ldg(row + c) : T(0);
+        }
+    }
+}
+
+template <typename T, int PMAX>
+__global__ void __launch_bounds__(kTThreads, 2) tile2d_pf_kernel(const Tile2DParams P) {
+    using F = TilePf<PMAX>;
+    T *X = reinterpret_cast<T *>(tile2d_smem);
+    T *RM = reinterpret_cast<T *>(tile2d_smem + P.x_bytes);
+    T *RN = reinterpret_cast<T *>(tile2d_smem + P.x_bytes + P.r_bytes);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wy = P.wy, wx = P.wx, xs = P.xs;
+    const int rows_in = kTR + wy - 1, cols_in = kTC + wx - 1;
+    const int64_t total = P.nimg * P.tiles_x * P.tiles_y;
+    const int px = pow2_floor(wx), py = pow2_floor(wy);
+    T v[F::RPW][F::CPL];
+    int64_t tile = blockIdx.x;
+    if (tile < total) tile_pf_load<T, PMAX>(P, tile, rows_in, cols_in, warp, lane, v);
+    for (; tile < total; tile += gridDim.x) {
+#pragma unroll
+        for (int i = 0; i < F::RPW; ++i) {
+            const int r = warp + 8 * i;
+#pragma unroll
+            for (int j = 0; j < F::CPL; ++j) {
+                const int c = lane + 32 * j;
+                if (r < rows_in && c < cols_in) X[r * xs + c] = v[i][j];
+            }
+        }
+        __syncthreads();
+        const int64_t next = tile + gridDim.x;
+        if (next < total) tile_pf_load<T, PMAX>(P, next, rows_in, cols_in, warp, lane, v);
+        switch (px) {
+            case 1: tile_rows<T, 1>(X, xs, RM, RN, rows_in, cols_in, wx - 1); break;
+            case 2: tile_rows<T, 2>(X, xs, RM, RN, rows_in, cols_in, wx - 2); break;
+            default: if constexpr (PMAX >= 4) tile_rows<T, 4>(X, xs, RM, RN, rows_in, cols_in, wx - 4); break;
+        }
+        __syncthreads();
+        int64_t img, y0, x0;
+        tile_origin(P, tile, img, y0, x0);
+        T *omax = P.out_max ? reinterpret_cast<T *>(P.out_max) + img * P.Ho * P.Wo : nullptr;
+        T *omin = P.out_min ? reinterpret_cast<T *>(P.out_min) + img * P.Ho * P.Wo : nullptr;
+        switch (py) {
+            case 1: tile_cols<T, 1>(RM, RN, rows_in, wy - 1, P, omax, omin, y0, x0); break;
+            case 2: tile_cols<T, 2>(RM, RN, rows_in, wy - 2, P, omax, omin, y0, x0); break;
+            default: if constexpr (PMAX >= 4) tile_cols<T, 4>(RM, RN, rows_in, wy - 4, P, omax, omin, y0, x0); break;
+        }
+        __syncthreads();  // X, RM and RN are rewritten for the next tile
+    }
+}
+
 }  // namespace mmf
