@@ -308,8 +308,6 @@ def wedge_extras(dev, stream, peak, n=1 << 30, windows=(3, 31, 101, 496), reps=3
     out = {}
     om = torch.empty(n, dtype=torch.float32, device=dev)
     on = torch.empty(n, dtype=torch.float32, device=dev)
-    am = torch.empty(n, dtype=torch.int64, device=dev)
-    an = torch.empty(n, dtype=torch.int64, device=dev)
     for d in DISTS:
         x = synth.torch_by_name(d, n, 91, dev)
         for w in windows:
@@ -323,15 +321,42 @@ def wedge_extras(dev, stream, peak, n=1 << 30, windows=(3, 31, 101, 496), reps=3
                 gbs = (n + 2 * m) * 4 / ms / 1e6
                 row[k] = {"ms": ms, "Gelem_s": n / ms / 1e6, "GBps": gbs, "frac": gbs / peak}
             row["wedge_over_auto"] = row["auto"]["ms"] / row["wedge"]["ms"]
-            # Values and int64 positions of the extremes (the arg filter):
-            # 4 + 2 x (4 + 8) bytes per element.
-            def g():
-                mmf.argfilter1d(x, w, stream=stream, out=(am[:m], an[:m], om[:m], on[:m]))
-            g()
-            ms = _events_ms(g, reps, stream)
-            gbs = (n * 4 + 2 * m * 12) / ms / 1e6
-            row["arg"] = {"ms": ms, "Gelem_s": n / ms / 1e6, "GBps": gbs, "frac": gbs / peak,
-                          "arg_over_wedge_time": ms / row["wedge"]["ms"]}
+            out[f"{d}_w{w}"] = row
+        del x
+    del om, on
+    torch.cuda.empty_cache()
+    return out
+
+
+def arg_extras(dev, stream, peak, n=1 << 30, windows=(3, 31, 496, 1001, 65537), reps=3):
+    """The arg-max / arg-min filter (values and int64 positions of both
+    extremes) on the n = 2^30 f32 streams: block scans over (value, position)
+    pairs, and the chunked wedge where its window limit allows.  Algorithmic
+    bytes: 4 + 2 x (4 + 8) per element."""
+    import torch
+    import paper_cs_0610046_gb300 as mmf
+    import synth
+    out = {}
+    om = torch.empty(n, dtype=torch.float32, device=dev)
+    on = torch.empty(n, dtype=torch.float32, device=dev)
+    am = torch.empty(n, dtype=torch.int64, device=dev)
+    an = torch.empty(n, dtype=torch.int64, device=dev)
+    for d in DISTS:
+        x = synth.torch_by_name(d, n, 91, dev)
+        for w in windows:
+            m = n - w + 1
+            row = {}
+            for k in ("blockscan", "wedge"):
+                if k == "wedge" and w > 496:
+                    continue
+                def g():
+                    mmf.argfilter1d(x, w, stream=stream, out=(am[:m], an[:m], om[:m], on[:m]), kernel=k)
+                g()
+                ms = _events_ms(g, reps, stream)
+                gbs = (n * 4 + 2 * m * 12) / ms / 1e6
+                row[k] = {"ms": ms, "Gelem_s": n / ms / 1e6, "GBps": gbs, "frac": gbs / peak}
+            if "wedge" in row:
+                row["blockscan_over_wedge_time"] = row["blockscan"]["ms"] / row["wedge"]["ms"]
             out[f"{d}_w{w}"] = row
         del x
     del om, on, am, an
@@ -485,6 +510,8 @@ def run_only(args):
     peak = _peaks()[0]
     if args.only == "wedge":
         r = wedge_extras(dev, stream, peak, n=(1 << 26) if args.small else (1 << 30))
+    elif args.only == "arg":
+        r = arg_extras(dev, stream, peak, n=(1 << 26) if args.small else (1 << 30))
     elif args.only == "batched":
         r = batched_extras(dev, stream, peak, envelope_series=100_000 if args.small else 1_000_000)
     elif args.only == "envelope":
@@ -510,7 +537,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched/2D/serving measurements")
-    ap.add_argument("--only", choices=["wedge", "batched", "envelope", "filter2d", "serving"],
+    ap.add_argument("--only", choices=["wedge", "arg", "batched", "envelope", "filter2d", "serving"],
                     help="run one extra measurement alone and print its JSON (profiling)")
     ap.add_argument("--small", action="store_true",
                     help="with --only: a smaller instance of that workload (profiling captures)")
@@ -667,6 +694,7 @@ def main():
         del xs
         torch.cuda.empty_cache()
         extras["wedge"] = wedge_extras(dev, stream, peak)
+        extras["arg"] = arg_extras(dev, stream, peak)
         extras["batched"] = batched_extras(dev, stream, peak)
         extras["filter2d"] = filter2d_extras(dev, stream, peak)
         extras["serving"] = serving_extras(dev)

@@ -121,11 +121,24 @@ mmf_status mmf_filter1d_ex(const void *d_in, int64_t n, int64_t w_or_r, mmf_dtyp
  * for every valid window [j, j+w), d_argmax[j] / d_argmin[j] is the position
  * in the array (int64) of its maximum / minimum, the leftmost among equal
  * values, and d_max / d_min the values; any output may be NULL (not all).
- * n-w+1 outputs each, computed by the chunked-wedge kernel with ties kept in
- * the deques, so w <= MMF_WEDGE_MAX_WINDOW (MMF_ENOTIMPL beyond).  Pointers:
- * element-aligned values, 8-byte aligned positions. */
+ * n-w+1 outputs each, any w >= 1, computed by van Herk/Gil-Werman block
+ * scans (Section 2) over (value, position) pairs: the suffix of a block is
+ * left of the next block's prefix, so keeping the suffix's candidate on equal
+ * values keeps the leftmost position.  For w > 2048 the call takes a
+ * workspace of per-tile aggregates (about 72 bytes per 2048 inputs for f32)
+ * from the stream-ordered allocator and returns it on `stream`.  Pointers:
+ * element-aligned values, 8-byte aligned positions.  Errors: MMF_EINVAL for
+ * w < 1, n < 0, NULL or misaligned buffers; MMF_ENOMEM / MMF_ECUDA from the
+ * workspace allocation or the launches. */
 mmf_status mmf_argfilter1d(const void *d_in, int64_t n, int64_t w, mmf_dtype dtype, void *d_max, void *d_min,
                            int64_t *d_argmax, int64_t *d_argmin, void *stream);
+
+/* The same with an explicit kernel: MMF_KERNEL_AUTO or MMF_KERNEL_BLOCKSCAN
+ * (the block scans above), or MMF_KERNEL_WEDGE (the chunked monotonic wedge of
+ * Algorithm 1 with ties kept in the deques, w <= MMF_WEDGE_MAX_WINDOW, else
+ * MMF_ENOTIMPL); other kernels give MMF_ENOTIMPL. */
+mmf_status mmf_argfilter1d_ex(const void *d_in, int64_t n, int64_t w, mmf_dtype dtype, void *d_max, void *d_min,
+                              int64_t *d_argmax, int64_t *d_argmin, void *stream, mmf_kernel kernel);
 
 /* Number of outputs of one side for (n, w_or_r, mode); -1 if invalid. */
 int64_t mmf_output_length(int64_t n, int64_t w_or_r, mmf_mode mode);

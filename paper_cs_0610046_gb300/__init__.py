@@ -98,6 +98,7 @@ _EXTRA_SIGNATURES: dict = {
     "mmf_stream_close": ([_VP, ctypes.c_uint64, _INT], _INT),
     "mmf_filter1d_host": ([_VP, _I64, _I64, _INT, _INT, _VP, _VP, _I64, _VP], _INT),
     "mmf_argfilter1d": ([_VP, _I64, _I64, _INT, _VP, _VP, _VP, _VP, _VP], _INT),
+    "mmf_argfilter1d_ex": ([_VP, _I64, _I64, _INT, _VP, _VP, _VP, _VP, _VP, _INT], _INT),
     "mmf_stream_snapshot": ([_VP, ctypes.c_uint64, _VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), _INT], _INT),
     "mmf_stream_snapshot_wedge": ([_VP, ctypes.c_uint64, _VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), _INT],
                                   _INT),
@@ -197,11 +198,12 @@ def filter1d_host(x: torch.Tensor, w: int, mode: str = "valid", out_max=None, ou
     return out_max, out_min
 
 
-def argfilter1d(x: torch.Tensor, w: int, stream=None, out=None):
+def argfilter1d(x: torch.Tensor, w: int, stream=None, out=None, kernel: str = "auto"):
     """Positions (int64) of the maximum and minimum of every window
     [j, j+w) of ``x``, leftmost among equal values, and the values:
-    returns ``(argmax, argmin, max, min)``; w <= 496.  ``out``: optional
-    tuple of the four output tensors (at least n-w+1 elements each)."""
+    returns ``(argmax, argmin, max, min)``.  ``kernel``: "auto"/"blockscan"
+    (any w) or "wedge" (w <= 496).  ``out``: optional tuple of the four
+    output tensors (at least n-w+1 elements each)."""
     _check_tensor(x, "x")
     lib = load()
     x = x.reshape(-1)
@@ -219,8 +221,8 @@ def argfilter1d(x: torch.Tensor, w: int, stream=None, out=None):
         vm = torch.empty(m, dtype=x.dtype, device=x.device)
         vn = torch.empty(m, dtype=x.dtype, device=x.device)
     with torch.cuda.device(x.device):
-        check(lib.mmf_argfilter1d(_ptr(x), x.numel(), w, DTYPES[x.dtype], _ptr(vm), _ptr(vn), _ptr(am), _ptr(an),
-                                  _VP(_stream_handle(stream))))
+        check(lib.mmf_argfilter1d_ex(_ptr(x), x.numel(), w, DTYPES[x.dtype], _ptr(vm), _ptr(vn), _ptr(am), _ptr(an),
+                                     _VP(_stream_handle(stream)), KERNELS[kernel]))
     return am, an, vm, vn
 
 

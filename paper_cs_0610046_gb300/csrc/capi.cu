@@ -129,14 +129,17 @@ const char *mmf_last_error(void) { return g_err; }
 
 const char *mmf_version(void) { return "mmf-gb300 0.1 (sm_103a)"; }
 
-mmf_status mmf_argfilter1d(const void *d_in, int64_t n, int64_t w, mmf_dtype dtype, void *d_max, void *d_min,
-                           int64_t *d_argmax, int64_t *d_argmin, void *stream) {
+mmf_status mmf_argfilter1d_ex(const void *d_in, int64_t n, int64_t w, mmf_dtype dtype, void *d_max, void *d_min,
+                              int64_t *d_argmax, int64_t *d_argmin, void *stream, mmf_kernel kernel) {
     if (elem_size(dtype) == 0) return set_error(MMF_EINVAL, "unknown dtype %d", (int)dtype);
+    if (kernel != MMF_KERNEL_AUTO && kernel != MMF_KERNEL_BLOCKSCAN && kernel != MMF_KERNEL_WEDGE)
+        return set_error(MMF_ENOTIMPL, "kernel %d does not compute locations", (int)kernel);
     SeriesDesc sd;
     mmf_status st = make_series(n, w, MMF_VALID, dtype, &sd);
     if (st != MMF_OK) return st;
-    if (w > MMF_WEDGE_MAX_WINDOW)
-        return set_error(MMF_ENOTIMPL, "locations are computed for windows up to %d", MMF_WEDGE_MAX_WINDOW);
+    if (kernel == MMF_KERNEL_WEDGE && w > MMF_WEDGE_MAX_WINDOW)
+        return set_error(MMF_ENOTIMPL, "the wedge kernel computes locations for windows up to %d",
+                         MMF_WEDGE_MAX_WINDOW);
     if (sd.n_out == 0) return MMF_OK;
     if (!d_max && !d_min && !d_argmax && !d_argmin) return set_error(MMF_EINVAL, "every output is NULL");
     if (!d_in) return set_error(MMF_EINVAL, "NULL input with n = %lld", (long long)n);
@@ -149,9 +152,16 @@ mmf_status mmf_argfilter1d(const void *d_in, int64_t n, int64_t w, mmf_dtype dty
     if (st != MMF_OK) return st;
     return dispatch_dtype(dtype, [&](auto tag) -> mmf_status {
         using T = decltype(tag);
-        cudaError_t e = wedge_arg_1d<T>(ctx, d_in, n, w, d_max, d_min, d_argmax, d_argmin);
+        const cudaError_t e = kernel == MMF_KERNEL_WEDGE
+                                  ? wedge_arg_1d<T>(ctx, d_in, n, w, d_max, d_min, d_argmax, d_argmin)
+                                  : argscan_1d<T>(ctx, d_in, n, w, d_max, d_min, d_argmax, d_argmin);
         return e == cudaSuccess ? MMF_OK : cuda_error(e, "argfilter launch");
     });
+}
+
+mmf_status mmf_argfilter1d(const void *d_in, int64_t n, int64_t w, mmf_dtype dtype, void *d_max, void *d_min,
+                           int64_t *d_argmax, int64_t *d_argmin, void *stream) {
+    return mmf_argfilter1d_ex(d_in, n, w, dtype, d_max, d_min, d_argmax, d_argmin, stream, MMF_KERNEL_AUTO);
 }
 
 int64_t mmf_output_length(int64_t n, int64_t w_or_r, mmf_mode mode) {

@@ -76,6 +76,11 @@ cudaError_t wedge_1d(const LaunchCtx &ctx, const void *in, int64_t n, int64_t w,
 template <typename T>
 cudaError_t wedge_arg_1d(const LaunchCtx &ctx, const void *in, int64_t n, int64_t w, void *omax, void *omin,
                          int64_t *amax, int64_t *amin);
+// Locations by block scans over (value, position) pairs, any window; windows
+// above 2048 take a stream-ordered workspace of per-tile aggregates.
+template <typename T>
+cudaError_t argscan_1d(const LaunchCtx &ctx, const void *in, int64_t n, int64_t w, void *omax, void *omin,
+                       int64_t *amax, int64_t *amin);
 
 // Kernel mode for window w: 3 = register slide (if allowed and w <= 17 for
 // f32, 9 otherwise), else
