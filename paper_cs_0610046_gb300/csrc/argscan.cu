@@ -14,18 +14,24 @@
 //
 // One CTA covers a tile of positions [base, base+len):
 //   * w <= kArgTile: whole blocks (len = floor(kArgTile/w)*w), nothing
-//     crosses the tile;
+//     crosses the tile; x and y are one staged range [base, base+len+w);
 //   * w > kArgTile: tile t of block b (positions t*kArgTile.. of the block).
 //     The part of S right of the tile and the part of Q left of it are
 //     per-tile aggregates scanned within each block (argagg_kernel and
 //     argblock_scan_kernel below), read as the CTA's two carries.
-// Each thread holds E consecutive positions.  A local sweep in each direction
-// gives its summary (the aggregate up to its first / last segment boundary
-// and whether it has one), a segmented scan of the summaries across the CTA
-// (warp shuffles, then warp totals) gives the carry into the thread, and the
-// final sweeps form the outputs, which leave through shared memory in
-// coalesced stores.  The max and min sides run one after the other on the
-// same staged inputs.
+// Each thread holds E consecutive positions and both sides (max, min) at
+// once.  One forward sweep forms the local exclusive Q (staged in shared
+// memory) and the thread's two summaries (Q from its last segment start, S up
+// to its first segment end); a segmented scan of the summaries across the CTA
+// (warp shuffles, then warp totals) gives the carries into the thread; one
+// backward sweep forms S, completes Q with its carry and joins them.  Outputs
+// leave through shared memory in 16-byte stores.
+//
+// Positions are offsets from base (x: p, y: w+p, carries inside [0, w+len)),
+// 32-bit unless w is near 2^31.  f32, i16 and u8 compare as float keys (exact
+// for 8- and 16-bit integers), so a NaN marks staged positions outside the
+// array: every comparison with it is false, so no sweep takes it.  f64 keys
+// are order-preserving 64-bit integers, with explicit limits.
 #include <climits>
 #include <cstdint>
 
@@ -36,51 +42,65 @@ namespace mmf {
 namespace {
 
 constexpr int kArgThreads = 256, kArgE = 8, kArgTile = kArgThreads * kArgE, kArgWarps = kArgThreads / 32;
-// Position codes while scanning: 0..kArgTile-1 an x position of the tile,
-// kArgTile + p the y position p, and the carries and the empty aggregate.
-constexpr int kCodeSC = -1, kCodeQC = -2, kCodeNone = -3;
 
-template <typename K> struct VI {
-    K v;
-    int i;
+template <typename T> struct AKey;
+template <> struct AKey<float> {
+    using K = float;
+    static constexpr bool kNanPad = true;
+    __device__ static K load(float v) { return v; }
+    __device__ static float store(K k) { return k; }
+};
+template <> struct AKey<int16_t> {
+    using K = float;
+    static constexpr bool kNanPad = true;
+    __device__ static K load(int16_t v) { return (float)v; }
+    __device__ static int16_t store(K k) { return (int16_t)(int)k; }
+};
+template <> struct AKey<uint8_t> {
+    using K = float;
+    static constexpr bool kNanPad = true;
+    __device__ static K load(uint8_t v) { return (float)v; }
+    __device__ static uint8_t store(K k) { return (uint8_t)(int)k; }
+};
+template <> struct AKey<double> {
+    using K = long long;
+    static constexpr bool kNanPad = false;
+    __device__ static K load(double v) { return Elem<double>::load(v); }
+    __device__ static double store(K k) { return Elem<double>::store(k); }
 };
 
-// Aggregate of a range for both sides; empty ranges hold the identities and
-// position INT64_MAX.
+// Identities: -inf/+inf for float keys (which an equal value in the data
+// only ties: a tied identity is never preferred to a real position in S, and
+// Q is taken only when strictly better than S), the 64-bit limits (outside
+// every key of a non-NaN double) for f64.
+template <typename K> struct KeyLim;
+template <> struct KeyLim<float> {
+    __device__ static float lo() { return __int_as_float(0xff800000); }
+    __device__ static float hi() { return __int_as_float(0x7f800000); }
+    __device__ static float pad() { return __int_as_float(0x7fffffff); }
+};
+template <> struct KeyLim<long long> {
+    __device__ static long long lo() { return LLONG_MIN; }
+    __device__ static long long hi() { return LLONG_MAX; }
+    __device__ static long long pad() { return 0; }
+};
+
+template <typename K, typename P> struct VI {
+    K v;
+    P i;
+};
+
+// Aggregate of a range for both sides (global positions); empty ranges hold
+// the identities and position INT64_MAX.
 template <typename K> struct Agg {
     K vmax, vmin;
     long long imax, imin;
 };
 
-// Identities strictly outside the keys of real values where the key type has
-// room (doubles are order-preserving 64-bit keys, 8/16-bit values are ints);
-// f32 uses -inf/+inf, which equal values in the data only lose ties (the
-// proof is in the sweeps: an identity never beats a real position).
-template <typename K> struct KeyLim;
-template <> struct KeyLim<float> {
-    __device__ static float lo() { return __int_as_float(0xff800000); }
-    __device__ static float hi() { return __int_as_float(0x7f800000); }
-};
-template <> struct KeyLim<long long> {
-    __device__ static long long lo() { return LLONG_MIN; }
-    __device__ static long long hi() { return LLONG_MAX; }
-};
-template <> struct KeyLim<int> {
-    __device__ static int lo() { return INT_MIN; }
-    __device__ static int hi() { return INT_MAX; }
-};
-
-template <typename K, bool MAX> struct Side {
-    __device__ static K id() { return MAX ? KeyLim<K>::lo() : KeyLim<K>::hi(); }
-    __device__ static bool better(K a, K b) { return MAX ? a > b : a < b; }
-    // a left of b: b only when strictly better.
-    __device__ static VI<K> join(VI<K> a, VI<K> b) { return better(b.v, a.v) ? b : a; }
-};
-
 // Shared-memory index with one padding slot per 128 bytes, so E consecutive
 // elements per thread spread over the banks.
 template <typename K> __device__ __forceinline__ int padk(int p) { return p + p / (128 / (int)sizeof(K)); }
-template <typename K> __host__ __device__ constexpr int padded_len() { return kArgTile + kArgTile / (128 / (int)sizeof(K)); }
+template <typename K> __host__ __device__ constexpr int padded_len(int n) { return n + n / (128 / (int)sizeof(K)); }
 
 template <typename T> struct ArgParams {
     const T *x;
@@ -89,232 +109,300 @@ template <typename T> struct ArgParams {
     long long *amax, *amin;
     long long ntiles;  // tiles per block (w > kArgTile), 0 for whole blocks per CTA
     int len_small;     // positions per CTA for whole blocks
-    const Agg<typename Elem<T>::R> *pg, *sg;  // per-tile prefix / suffix aggregates
+    const Agg<typename AKey<T>::K> *pg, *sg;  // per-tile prefix / suffix aggregates
 };
 
-template <typename K> struct ArgScanSmem {
-    VI<K> ft[kArgWarps], bt[kArgWarps];
-    int ff[kArgWarps], bf[kArgWarps];
+template <typename K, typename P> struct ArgScanSmem {
+    VI<K, P> qmx[kArgWarps], qmn[kArgWarps], smx[kArgWarps], smn[kArgWarps];
+    int qf[kArgWarps], sf[kArgWarps];
 };
 
-template <typename K> __device__ __forceinline__ VI<K> shfl_up_vi(VI<K> a, int d) {
-    return VI<K>{__shfl_up_sync(0xffffffffu, a.v, d), __shfl_up_sync(0xffffffffu, a.i, d)};
+template <typename K, typename P> __device__ __forceinline__ VI<K, P> shfl_up_vi(VI<K, P> a, int d) {
+    return VI<K, P>{__shfl_up_sync(0xffffffffu, a.v, d), __shfl_up_sync(0xffffffffu, a.i, d)};
 }
-template <typename K> __device__ __forceinline__ VI<K> shfl_down_vi(VI<K> a, int d) {
-    return VI<K>{__shfl_down_sync(0xffffffffu, a.v, d), __shfl_down_sync(0xffffffffu, a.i, d)};
+template <typename K, typename P> __device__ __forceinline__ VI<K, P> shfl_down_vi(VI<K, P> a, int d) {
+    return VI<K, P>{__shfl_down_sync(0xffffffffu, a.v, d), __shfl_down_sync(0xffffffffu, a.i, d)};
 }
-
-template <typename T, bool MAX>
-__device__ __forceinline__ void arg_side(const ArgParams<T> &P, long long base, int len, int xlim, int ylim,
-                                         unsigned smask, unsigned emask, const typename Elem<T>::R *xs,
-                                         const typename Elem<T>::R *ys, typename Elem<T>::R *vo, long long *io,
-                                         VI<typename Elem<T>::R> qc, long long qci, VI<typename Elem<T>::R> sc,
-                                         long long sci, ArgScanSmem<typename Elem<T>::R> &sm) {
-    using K = typename Elem<T>::R;
-    using S = Side<K, MAX>;
-    const K ID = S::id();
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, p0 = tid * kArgE;
-    const VI<K> none{ID, kCodeNone};
-
-    // 1. Summaries: forward over y (Q), backward over x (S).
-    VI<K> fs = none, bs = none;
-    int ff = 0, bf = 0;
-#pragma unroll
-    for (int k = 0; k < kArgE; ++k) {
-        const int p = p0 + k;
-        if ((smask >> k) & 1u) {
-            fs = none;
-            ff = 1;
-        }
-        const K y = p < ylim ? ys[padk<K>(p)] : ID;
-        if (S::better(y, fs.v)) fs = VI<K>{y, kArgTile + p};
-    }
-#pragma unroll
-    for (int k = kArgE - 1; k >= 0; --k) {
-        const int p = p0 + k;
-        if ((emask >> k) & 1u) {
-            bs = none;
-            bf = 1;
-        }
-        const K x = p < xlim ? xs[padk<K>(p)] : ID;
-        if (!S::better(bs.v, x)) bs = VI<K>{x, p};
-    }
-
-    // 2. Segmented scans of the summaries: inclusive within the warp...
-    VI<K> fi = fs, bi = bs;
-    int fif = ff, bif = bf;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const VI<K> l = shfl_up_vi(fi, d);
-        const int lf = __shfl_up_sync(0xffffffffu, fif, d);
-        if (lane >= d) {
-            if (!fif) fi = S::join(l, fi);
-            fif |= lf;
-        }
-        const VI<K> r = shfl_down_vi(bi, d);
-        const int rf = __shfl_down_sync(0xffffffffu, bif, d);
-        if (lane + d < 32) {
-            if (!bif) bi = S::join(bi, r);
-            bif |= rf;
-        }
-    }
-    if (lane == 31) {
-        sm.ft[warp] = fi;
-        sm.ff[warp] = fif;
-    }
-    if (lane == 0) {
-        sm.bt[warp] = bi;
-        sm.bf[warp] = bif;
-    }
-    // ... exclusive within the warp ...
-    VI<K> fe = shfl_up_vi(fi, 1), be = shfl_down_vi(bi, 1);
-    int fef = __shfl_up_sync(0xffffffffu, fif, 1), bef = __shfl_down_sync(0xffffffffu, bif, 1);
-    if (lane == 0) {
-        fe = none;
-        fef = 0;
-    }
-    if (lane == 31) {
-        be = none;
-        bef = 0;
-    }
-    __syncthreads();
-    // ... then across warps, with the tile's carries at the two ends.
-    VI<K> cf = qc;
-    for (int u = 0; u < warp; ++u) cf = sm.ff[u] ? sm.ft[u] : S::join(cf, sm.ft[u]);
-    cf = fef ? fe : S::join(cf, fe);
-    VI<K> cb = sc;
-    for (int u = kArgWarps - 1; u > warp; --u) cb = sm.bf[u] ? sm.bt[u] : S::join(sm.bt[u], cb);
-    cb = bef ? be : S::join(be, cb);
-
-    // 3. Final sweeps: Q forward into registers, then S backward joined with Q.
-    K qv[kArgE];
-    int qi[kArgE];
-    VI<K> acc = cf;
-#pragma unroll
-    for (int k = 0; k < kArgE; ++k) {
-        const int p = p0 + k;
-        if ((smask >> k) & 1u) acc = none;
-        qv[k] = acc.v;
-        qi[k] = acc.i;
-        const K y = p < ylim ? ys[padk<K>(p)] : ID;
-        if (S::better(y, acc.v)) acc = VI<K>{y, kArgTile + p};
-    }
-    acc = cb;
-#pragma unroll
-    for (int k = kArgE - 1; k >= 0; --k) {
-        const int p = p0 + k;
-        if ((emask >> k) & 1u) acc = none;
-        const K x = p < xlim ? xs[padk<K>(p)] : ID;
-        if (!S::better(acc.v, x)) acc = VI<K>{x, p};
-        const bool useq = S::better(qv[k], acc.v);
-        const int c = useq ? qi[k] : acc.i;
-        // An output of the tile always has its own x in S, so the empty code
-        // never reaches a stored output (the last case only fills the slot).
-        const long long g = c >= kArgTile ? base + P.w + (c - kArgTile)
-                            : c >= 0      ? base + c
-                            : c == kCodeSC ? sci
-                            : c == kCodeQC ? qci
-                                           : base + p;
-        vo[padk<K>(p)] = useq ? qv[k] : acc.v;
-        io[padk<long long>(p)] = g;
-    }
-    __syncthreads();
-    T *oval = MAX ? P.omax : P.omin;
-    long long *oidx = MAX ? P.amax : P.amin;
-    const int nv = (int)min((long long)len, P.n_out - base);
-    for (int i = tid; i < nv; i += kArgThreads) {
-        if (oval) oval[base + i] = Elem<T>::store(vo[padk<K>(i)]);
-        if (oidx) oidx[base + i] = io[padk<long long>(i)];
-    }
+// a left of b: b only when strictly better.
+template <typename K, typename P> __device__ __forceinline__ VI<K, P> jmax(VI<K, P> a, VI<K, P> b) {
+    return b.v > a.v ? b : a;
+}
+template <typename K, typename P> __device__ __forceinline__ VI<K, P> jmin(VI<K, P> a, VI<K, P> b) {
+    return b.v < a.v ? b : a;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kArgThreads) argscan_kernel(const ArgParams<T> P) {
-    using K = typename Elem<T>::R;
-    extern __shared__ __align__(16) unsigned char arg_smem[];
-    __shared__ ArgScanSmem<K> sm;
-    constexpr int PK = padded_len<K>();
-    K *xs = reinterpret_cast<K *>(arg_smem);
-    K *ys = xs + PK;
-    K *vo = ys + PK;
-    long long *io = reinterpret_cast<long long *>(vo + PK);
-
+template <typename T, typename P>
+__device__ __forceinline__ void store_side(T *oval, long long *oidx, long long base, int nv,
+                                           const typename AKey<T>::K *vs, const P *ps) {
+    using A = AKey<T>;
+    using K = typename A::K;
     const int tid = threadIdx.x;
+    if (oval) {
+        constexpr int VW = 16 / (int)sizeof(T);
+        T *o = oval + base;
+        const int h = min(nv, (int)(((16 - ((uintptr_t)o & 15)) & 15) / sizeof(T)));
+        const int nvec = (nv - h) / VW;
+        for (int q = tid; q < nvec; q += kArgThreads) {
+            const int j = h + q * VW;
+            union {
+                uint4 u;
+                T e[VW];
+            } pk;
+#pragma unroll
+            for (int e = 0; e < VW; ++e) pk.e[e] = A::store(vs[padk<K>(j + e)]);
+            *reinterpret_cast<uint4 *>(o + j) = pk.u;
+        }
+        for (int j = tid; j < h; j += kArgThreads) o[j] = A::store(vs[padk<K>(j)]);
+        for (int j = h + nvec * VW + tid; j < nv; j += kArgThreads) o[j] = A::store(vs[padk<K>(j)]);
+    }
+    if (oidx) {
+        long long *o = oidx + base;
+        const int h = min(nv, (int)(((uintptr_t)o >> 3) & 1));
+        const int nvec = (nv - h) / 2;
+        for (int q = tid; q < nvec; q += kArgThreads) {
+            const int j = h + 2 * q;
+            longlong2 v;
+            v.x = base + (long long)ps[padk<P>(j)];
+            v.y = base + (long long)ps[padk<P>(j + 1)];
+            *reinterpret_cast<longlong2 *>(o + j) = v;
+        }
+        if (tid == 0 && h) o[0] = base + (long long)ps[padk<P>(0)];
+        const int tail = h + 2 * nvec;
+        if (tid == 0 && tail < nv) o[tail] = base + (long long)ps[padk<P>(tail)];
+    }
+}
+
+template <typename T, typename P>
+__global__ void __launch_bounds__(kArgThreads) argscan_kernel(const ArgParams<T> prm) {
+    using A = AKey<T>;
+    using K = typename A::K;
+    using V = VI<K, P>;
+    extern __shared__ __align__(16) unsigned char arg_smem[];
+    __shared__ ArgScanSmem<K, P> sm;
+    constexpr int PX = padded_len<K>(2 * kArgTile), PK = padded_len<K>(kArgTile), PP = padded_len<P>(kArgTile);
+    K *xs = reinterpret_cast<K *>(arg_smem);  // staged keys: x at p, y at yoff + p
+    K *vmx = xs + PX;
+    K *vmn = vmx + PK;
+    P *pmx = reinterpret_cast<P *>(vmn + PK);
+    P *pmn = pmx + PP;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     long long base, r0, b = 0, t = 0;
-    int len;
-    if (P.ntiles == 0) {
-        len = P.len_small;
+    int len, yoff;
+    if (prm.ntiles == 0) {
+        len = prm.len_small;
         base = (long long)blockIdx.x * len;
         r0 = 0;
+        yoff = (int)prm.w;
     } else {
-        b = (long long)blockIdx.x / P.ntiles;
-        t = (long long)blockIdx.x % P.ntiles;
+        b = (long long)blockIdx.x / prm.ntiles;
+        t = (long long)blockIdx.x % prm.ntiles;
         r0 = t * kArgTile;
-        base = b * P.w + r0;
-        len = (int)min((long long)kArgTile, P.w - r0);
+        base = b * prm.w + r0;
+        len = (int)min((long long)kArgTile, prm.w - r0);
+        yoff = kArgTile;
     }
-    if (base >= P.n_out) return;  // uniform per CTA, before any barrier
-    const int xlim = (int)max(0LL, min((long long)len, P.n - base));
-    const int ylim = (int)max(0LL, min((long long)len, P.n - base - P.w));
+    if (base >= prm.n_out) return;  // uniform per CTA, before any barrier
+    const int xlim = (int)max(0LL, min((long long)len, prm.n - base));
+    const int ylim = (int)max(0LL, min((long long)len, prm.n - base - prm.w));
 
-    // Stage x[base..) and y[base..) = x[base+w..) as keys (coalesced loads,
-    // all issued before the first shared-memory store).
-    T xv[kArgE], yv[kArgE];
+    // Stage the inputs (all 2*kArgTile slots, loads issued before the stores).
+    {
+        K kv[2 * kArgE];
+        if (prm.ntiles == 0) {
+            const long long lim = min((long long)len + prm.w, prm.n - base);
 #pragma unroll
-    for (int k = 0; k < kArgE; ++k) {
-        const int i = tid + k * kArgThreads;
-        xv[k] = i < xlim ? __ldg(P.x + base + i) : T(0);
-        yv[k] = i < ylim ? __ldg(P.x + base + P.w + i) : T(0);
-    }
+            for (int k = 0; k < 2 * kArgE; ++k) {
+                const int i = tid + k * kArgThreads;
+                kv[k] = i < lim ? A::load(__ldg(prm.x + base + i)) : KeyLim<K>::pad();
+            }
+        } else {
 #pragma unroll
-    for (int k = 0; k < kArgE; ++k) {
-        const int i = tid + k * kArgThreads;
-        xs[padk<K>(i)] = Elem<T>::load(xv[k]);
-        ys[padk<K>(i)] = Elem<T>::load(yv[k]);
+            for (int k = 0; k < 2 * kArgE; ++k) {
+                const int i = tid + k * kArgThreads;
+                const int off = k < kArgE ? i : i - kArgTile;
+                const int lim = k < kArgE ? xlim : ylim;
+                const long long src = k < kArgE ? base : base + prm.w;
+                kv[k] = off < lim ? A::load(__ldg(prm.x + src + off)) : KeyLim<K>::pad();
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 2 * kArgE; ++k) xs[padk<K>(tid + k * kArgThreads)] = kv[k];
     }
 
     // Segment starts (phase 0) and ends (phase w-1) among the thread's positions.
     const int p0 = tid * kArgE;
     unsigned smask = 0, emask = 0;
     {
-        long long r = P.ntiles == 0 ? (long long)(p0 % (int)P.w) : r0 + p0;
+        long long r = prm.ntiles == 0 ? (long long)(p0 % (int)prm.w) : r0 + p0;
 #pragma unroll
         for (int k = 0; k < kArgE; ++k) {
             if (r == 0) smask |= 1u << k;
-            if (r == P.w - 1) emask |= 1u << k;
-            if (++r == P.w) r = 0;
+            if (r == prm.w - 1) emask |= 1u << k;
+            if (++r == prm.w) r = 0;
         }
     }
+    const K LO = KeyLim<K>::lo(), HI = KeyLim<K>::hi();
+    const V nmx{LO, 0}, nmn{HI, 0};
+    const P yrel = (P)prm.w;  // offset of y position 0 from base
+    // Without NaN padding (f64), positions outside the array read as the
+    // identity of each side.
+    auto xmx = [&](int p) { return A::kNanPad || p < xlim ? xs[padk<K>(p)] : LO; };
+    auto xmn = [&](int p) { return A::kNanPad || p < xlim ? xs[padk<K>(p)] : HI; };
+    auto ymx = [&](int p) { return A::kNanPad || p < ylim ? xs[padk<K>(yoff + p)] : LO; };
+    auto ymn = [&](int p) { return A::kNanPad || p < ylim ? xs[padk<K>(yoff + p)] : HI; };
+    __syncthreads();
 
-    // Carries of a tile inside a long block: Q's part left of the tile (the
-    // start of block b+1 up to tile t) and S's part right of it (the rest of
-    // block b after tile t).
-    VI<K> qmx{KeyLim<K>::lo(), kCodeNone}, qmn{KeyLim<K>::hi(), kCodeNone};
-    VI<K> smx{KeyLim<K>::lo(), kCodeNone}, smn{KeyLim<K>::hi(), kCodeNone};
-    long long qmxi = 0, qmni = 0, smxi = 0, smni = 0;
-    if (P.ntiles != 0) {
-        if (t > 0) {
-            const Agg<K> a = P.pg[(b + 1) * P.ntiles + t - 1];
-            qmx = VI<K>{a.vmax, kCodeQC};
-            qmn = VI<K>{a.vmin, kCodeQC};
-            qmxi = a.imax;
-            qmni = a.imin;
+    // 1. Forward sweep: local exclusive Q staged; summaries.
+    V qmx = nmx, qmn = nmn, smx = nmx, smn = nmn;
+    bool done = false;
+#pragma unroll
+    for (int k = 0; k < kArgE; ++k) {
+        const int p = p0 + k;
+        if ((smask >> k) & 1u) {
+            qmx = nmx;
+            qmn = nmn;
         }
-        if (t + 1 < P.ntiles) {
-            const Agg<K> a = P.sg[b * P.ntiles + t + 1];
-            smx = VI<K>{a.vmax, kCodeSC};
-            smn = VI<K>{a.vmin, kCodeSC};
-            smxi = a.imax;
-            smni = a.imin;
+        vmx[padk<K>(p)] = qmx.v;
+        vmn[padk<K>(p)] = qmn.v;
+        pmx[padk<P>(p)] = qmx.i;
+        pmn[padk<P>(p)] = qmn.i;
+        const K ya = ymx(p), yb = ymn(p);
+        if (ya > qmx.v) qmx = V{ya, (P)(yrel + p)};
+        if (yb < qmn.v) qmn = V{yb, (P)(yrel + p)};
+        if (!done) {
+            const K xa = xmx(p), xb = xmn(p);
+            if (xa > smx.v) smx = V{xa, (P)p};
+            if (xb < smn.v) smn = V{xb, (P)p};
+            done = (emask >> k) & 1u;
+        }
+    }
+    int qf = smask != 0, sf = emask != 0;
+
+    // 2. Segmented scans of the summaries: inclusive within the warp ...
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const V la = shfl_up_vi(qmx, d), lb = shfl_up_vi(qmn, d);
+        const int lf = __shfl_up_sync(0xffffffffu, qf, d);
+        if (lane >= d) {
+            if (!qf) {
+                qmx = jmax(la, qmx);
+                qmn = jmin(lb, qmn);
+            }
+            qf |= lf;
+        }
+        const V ra = shfl_down_vi(smx, d), rb = shfl_down_vi(smn, d);
+        const int rf = __shfl_down_sync(0xffffffffu, sf, d);
+        if (lane + d < 32) {
+            if (!sf) {
+                smx = jmax(smx, ra);
+                smn = jmin(smn, rb);
+            }
+            sf |= rf;
+        }
+    }
+    if (lane == 31) {
+        sm.qmx[warp] = qmx;
+        sm.qmn[warp] = qmn;
+        sm.qf[warp] = qf;
+    }
+    if (lane == 0) {
+        sm.smx[warp] = smx;
+        sm.smn[warp] = smn;
+        sm.sf[warp] = sf;
+    }
+    // ... exclusive within the warp ...
+    V eqa = shfl_up_vi(qmx, 1), eqb = shfl_up_vi(qmn, 1), esa = shfl_down_vi(smx, 1), esb = shfl_down_vi(smn, 1);
+    int eqf = __shfl_up_sync(0xffffffffu, qf, 1), esf = __shfl_down_sync(0xffffffffu, sf, 1);
+    if (lane == 0) {
+        eqa = nmx;
+        eqb = nmn;
+        eqf = 0;
+    }
+    if (lane == 31) {
+        esa = nmx;
+        esb = nmn;
+        esf = 0;
+    }
+    // ... then across warps, with the tile's carries at the two ends: Q's part
+    // left of the tile (block b+1 up to tile t) and S's part right of it (the
+    // rest of block b after tile t).
+    V cqa = nmx, cqb = nmn, csa = nmx, csb = nmn;
+    if (prm.ntiles != 0) {
+        if (t > 0) {
+            const Agg<K> a = prm.pg[(b + 1) * prm.ntiles + t - 1];
+            cqa = V{a.vmax, (P)(a.imax - base)};
+            cqb = V{a.vmin, (P)(a.imin - base)};
+        }
+        if (t + 1 < prm.ntiles) {
+            const Agg<K> a = prm.sg[b * prm.ntiles + t + 1];
+            csa = V{a.vmax, (P)(a.imax - base)};
+            csb = V{a.vmin, (P)(a.imin - base)};
         }
     }
     __syncthreads();
-    if (P.omax || P.amax)
-        arg_side<T, true>(P, base, len, xlim, ylim, smask, emask, xs, ys, vo, io, qmx, qmxi, smx, smxi, sm);
-    if (P.omin || P.amin) {
-        __syncthreads();  // the staging of the max side has been stored
-        arg_side<T, false>(P, base, len, xlim, ylim, smask, emask, xs, ys, vo, io, qmn, qmni, smn, smni, sm);
+    for (int u = 0; u < warp; ++u) {
+        if (sm.qf[u]) {
+            cqa = sm.qmx[u];
+            cqb = sm.qmn[u];
+        } else {
+            cqa = jmax(cqa, sm.qmx[u]);
+            cqb = jmin(cqb, sm.qmn[u]);
+        }
     }
+    if (eqf) {
+        cqa = eqa;
+        cqb = eqb;
+    } else {
+        cqa = jmax(cqa, eqa);
+        cqb = jmin(cqb, eqb);
+    }
+    for (int u = kArgWarps - 1; u > warp; --u) {
+        if (sm.sf[u]) {
+            csa = sm.smx[u];
+            csb = sm.smn[u];
+        } else {
+            csa = jmax(sm.smx[u], csa);
+            csb = jmin(sm.smn[u], csb);
+        }
+    }
+    if (esf) {
+        csa = esa;
+        csb = esb;
+    } else {
+        csa = jmax(esa, csa);
+        csb = jmin(esb, csb);
+    }
+
+    // 3. Backward sweep: S with its carry, Q completed with its carry before
+    // the thread's first segment start, the join, staged in place.
+    const int fs = smask ? __ffs(smask) - 1 : kArgE;
+    V sa = csa, sb = csb;
+#pragma unroll
+    for (int k = kArgE - 1; k >= 0; --k) {
+        const int p = p0 + k;
+        if ((emask >> k) & 1u) {
+            sa = nmx;
+            sb = nmn;
+        }
+        const K xa = xmx(p), xb = xmn(p);
+        if (xa >= sa.v) sa = V{xa, (P)p};
+        if (xb <= sb.v) sb = V{xb, (P)p};
+        V qa{vmx[padk<K>(p)], pmx[padk<P>(p)]}, qb{vmn[padk<K>(p)], pmn[padk<P>(p)]};
+        if (k < fs) {
+            qa = jmax(cqa, qa);
+            qb = jmin(cqb, qb);
+        }
+        const V ra = qa.v > sa.v ? qa : sa, rb = qb.v < sb.v ? qb : sb;
+        vmx[padk<K>(p)] = ra.v;
+        pmx[padk<P>(p)] = ra.i;
+        vmn[padk<K>(p)] = rb.v;
+        pmn[padk<P>(p)] = rb.i;
+    }
+    __syncthreads();
+    const int nv = (int)min((long long)len, prm.n_out - base);
+    store_side<T, P>(prm.omax, prm.amax, base, nv, vmx, pmx);
+    store_side<T, P>(prm.omin, prm.amin, base, nv, vmn, pmn);
 }
 
 // Both sides of a range, any order of positions: larger (smaller) value,
@@ -346,6 +434,14 @@ template <typename K> __device__ __forceinline__ Agg<K> agg_shfl_up(const Agg<K>
     r.imin = __shfl_up_sync(0xffffffffu, a.imin, d);
     return r;
 }
+template <typename K> __device__ __forceinline__ Agg<K> agg_bcast(const Agg<K> &a, int lane) {
+    Agg<K> r;
+    r.vmax = __shfl_sync(0xffffffffu, a.vmax, lane);
+    r.vmin = __shfl_sync(0xffffffffu, a.vmin, lane);
+    r.imax = __shfl_sync(0xffffffffu, a.imax, lane);
+    r.imin = __shfl_sync(0xffffffffu, a.imin, lane);
+    return r;
+}
 
 template <typename K> __device__ __forceinline__ Agg<K> agg_empty() {
     return Agg<K>{KeyLim<K>::lo(), KeyLim<K>::hi(), LLONG_MAX, LLONG_MAX};
@@ -355,8 +451,9 @@ template <typename K> __device__ __forceinline__ Agg<K> agg_empty() {
 // block and to the array), for blocks 0..nb-1; grid-stride over tiles.
 template <typename T>
 __global__ void __launch_bounds__(kArgThreads) argagg_kernel(const T *x, long long n, long long w, long long ntiles,
-                                                            long long nb, Agg<typename Elem<T>::R> *g) {
-    using K = typename Elem<T>::R;
+                                                            long long nb, Agg<typename AKey<T>::K> *g) {
+    using A = AKey<T>;
+    using K = typename A::K;
     __shared__ Agg<K> part[kArgWarps];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (long long u = blockIdx.x; u < nb * ntiles; u += gridDim.x) {
@@ -374,7 +471,7 @@ __global__ void __launch_bounds__(kArgThreads) argagg_kernel(const T *x, long lo
         for (int k = 0; k < kArgE; ++k) {
             const long long i = lo + tid + k * kArgThreads;
             if (i < hi) {
-                const K key = Elem<T>::load(v[k]);
+                const K key = A::load(v[k]);
                 if (key > a.vmax || a.imax == LLONG_MAX) {
                     a.vmax = key;
                     a.imax = i;
@@ -422,11 +519,7 @@ __global__ void __launch_bounds__(kArgThreads) argblock_scan_kernel(const Agg<K>
         Agg<K> m = carry;
         agg_join(m, a);
         if (t < ntiles) pg[b * ntiles + t] = m;
-        carry = m;
-        carry.vmax = __shfl_sync(0xffffffffu, m.vmax, 31);
-        carry.vmin = __shfl_sync(0xffffffffu, m.vmin, 31);
-        carry.imax = __shfl_sync(0xffffffffu, m.imax, 31);
-        carry.imin = __shfl_sync(0xffffffffu, m.imin, 31);
+        carry = agg_bcast(m, 31);
     }
     carry = agg_empty<K>();
     for (long long t1 = ntiles; t1 > 0; t1 -= 32) {
@@ -439,11 +532,27 @@ __global__ void __launch_bounds__(kArgThreads) argblock_scan_kernel(const Agg<K>
         }
         agg_join(a, carry);
         if (t >= 0) sg[b * ntiles + t] = a;
-        carry.vmax = __shfl_sync(0xffffffffu, a.vmax, 0);
-        carry.vmin = __shfl_sync(0xffffffffu, a.vmin, 0);
-        carry.imax = __shfl_sync(0xffffffffu, a.imax, 0);
-        carry.imin = __shfl_sync(0xffffffffu, a.imin, 0);
+        carry = agg_bcast(a, 0);
     }
+}
+
+template <typename T, typename P> constexpr size_t arg_smem_bytes() {
+    using K = typename AKey<T>::K;
+    return (size_t)padded_len<K>(2 * kArgTile) * sizeof(K) + 2 * (size_t)padded_len<K>(kArgTile) * sizeof(K) +
+           2 * (size_t)padded_len<P>(kArgTile) * sizeof(P);
+}
+
+template <typename T, typename P> cudaError_t arg_launch(const LaunchCtx &ctx, const ArgParams<T> &prm, int64_t grid) {
+    constexpr size_t smem = arg_smem_bytes<T, P>();
+    static int attr_set[64] = {};
+    if (smem > 48 * 1024 && !attr_set[ctx.device & 63]) {
+        cudaError_t e =
+            cudaFuncSetAttribute(argscan_kernel<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set[ctx.device & 63] = 1;
+    }
+    argscan_kernel<T, P><<<(unsigned)grid, kArgThreads, smem, ctx.stream>>>(prm);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -451,24 +560,18 @@ __global__ void __launch_bounds__(kArgThreads) argblock_scan_kernel(const Agg<K>
 template <typename T>
 cudaError_t argscan_1d(const LaunchCtx &ctx, const void *in, int64_t n, int64_t w, void *omax, void *omin,
                        int64_t *amax, int64_t *amin) {
-    using K = typename Elem<T>::R;
+    using K = typename AKey<T>::K;
     const int64_t n_out = n - w + 1;
     if (n_out <= 0) return cudaSuccess;
-    constexpr size_t smem = 3 * (size_t)padded_len<K>() * sizeof(K) + (size_t)padded_len<long long>() * 8;
-    static int attr_set[64] = {};
-    if (smem > 48 * 1024 && !attr_set[ctx.device & 63]) {
-        cudaError_t e = cudaFuncSetAttribute(argscan_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set[ctx.device & 63] = 1;
-    }
-    ArgParams<T> P{static_cast<const T *>(in), n, w, n_out, static_cast<T *>(omax), static_cast<T *>(omin),
-                   reinterpret_cast<long long *>(amax), reinterpret_cast<long long *>(amin), 0, 0, nullptr,
-                   nullptr};
+    ArgParams<T> prm{static_cast<const T *>(in), n, w, n_out, static_cast<T *>(omax), static_cast<T *>(omin),
+                     reinterpret_cast<long long *>(amax), reinterpret_cast<long long *>(amin), 0, 0, nullptr,
+                     nullptr};
+    // Offsets from a tile's base stay below w + kArgTile: 32-bit up to 2^30.
+    const bool wide = w >= (int64_t(1) << 30);
     if (w <= kArgTile) {
-        P.len_small = (int)((kArgTile / w) * w);
-        const int64_t grid = (n_out + P.len_small - 1) / P.len_small;
-        argscan_kernel<T><<<(unsigned)grid, kArgThreads, smem, ctx.stream>>>(P);
-        return cudaGetLastError();
+        prm.len_small = (int)((kArgTile / w) * w);
+        const int64_t grid = (n_out + prm.len_small - 1) / prm.len_small;
+        return arg_launch<T, int>(ctx, prm, grid);
     }
     const int64_t ntiles = (w + kArgTile - 1) / kArgTile;
     const int64_t nbo = (n_out + w - 1) / w;  // blocks holding outputs
@@ -489,11 +592,10 @@ cudaError_t argscan_1d(const LaunchCtx &ctx, const void *in, int64_t n, int64_t 
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-        P.ntiles = ntiles;
-        P.pg = pg;
-        P.sg = sg;
-        argscan_kernel<T><<<(unsigned)(nbo * ntiles), kArgThreads, smem, ctx.stream>>>(P);
-        e = cudaGetLastError();
+        prm.ntiles = ntiles;
+        prm.pg = pg;
+        prm.sg = sg;
+        e = wide ? arg_launch<T, long long>(ctx, prm, nbo * ntiles) : arg_launch<T, int>(ctx, prm, nbo * ntiles);
     }
     const cudaError_t ef = cudaFreeAsync(ws, ctx.stream);
     return e != cudaSuccess ? e : ef;
