@@ -28,7 +28,7 @@
 // leave through shared memory in 16-byte stores.
 //
 // Positions are offsets from base (x: p, y: w+p, carries inside [0, w+len)),
-// 32-bit unless w is near 2^31.  f32, i16 and u8 compare as float keys (exact
+// unsigned 32-bit unless w is near 2^31.  f32, i16 and u8 compare as float keys (exact
 // for 8- and 16-bit integers), so a NaN marks staged positions outside the
 // array: every comparison with it is false, so no sweep takes it.  f64 keys
 // are order-preserving 64-bit integers, with explicit limits.
@@ -41,7 +41,10 @@
 namespace mmf {
 namespace {
 
-constexpr int kArgThreads = 256, kArgE = 8, kArgTile = kArgThreads * kArgE, kArgWarps = kArgThreads / 32;
+// 128 threads x 16 positions: the per-thread costs (summary scans, carries)
+// spread over 16 elements; E = 16 keeps a thread's positions inside one
+// padding group, so its staged addresses are a base plus constants.
+constexpr int kArgThreads = 128, kArgE = 16, kArgTile = kArgThreads * kArgE, kArgWarps = kArgThreads / 32;
 
 template <typename T> struct AKey;
 template <> struct AKey<float> {
@@ -234,12 +237,22 @@ __global__ void __launch_bounds__(kArgThreads) argscan_kernel(const ArgParams<T>
     const int p0 = tid * kArgE;
     unsigned smask = 0, emask = 0;
     {
-        long long r = prm.ntiles == 0 ? (long long)(p0 % (int)prm.w) : r0 + p0;
+        const long long r = prm.ntiles == 0 ? (long long)(p0 % (int)prm.w) : r0 + p0;  // phase of p0
+        if (r >= prm.w) {
+            // past the last tile of a block: no position of this thread is
+            // in the tile, and the tile's last position ends its segment
+        } else if (prm.w >= kArgE) {  // at most one start and one end
+            const long long ks = r == 0 ? 0 : prm.w - r, ke = prm.w - 1 - r;
+            if (ks < kArgE) smask = 1u << ks;
+            if (ke < kArgE) emask = 1u << ke;
+        } else {
+            int q = (int)r;
 #pragma unroll
-        for (int k = 0; k < kArgE; ++k) {
-            if (r == 0) smask |= 1u << k;
-            if (r == prm.w - 1) emask |= 1u << k;
-            if (++r == prm.w) r = 0;
+            for (int k = 0; k < kArgE; ++k) {
+                if (q == 0) smask |= 1u << k;
+                if (q == (int)prm.w - 1) emask |= 1u << k;
+                if (++q == (int)prm.w) q = 0;
+            }
         }
     }
     const K LO = KeyLim<K>::lo(), HI = KeyLim<K>::hi();
@@ -247,8 +260,10 @@ __global__ void __launch_bounds__(kArgThreads) argscan_kernel(const ArgParams<T>
     const P yrel = (P)prm.w;  // offset of y position 0 from base
     // Without NaN padding (f64), positions outside the array read as the
     // identity of each side.
-    auto xmx = [&](int p) { return A::kNanPad || p < xlim ? xs[padk<K>(p)] : LO; };
-    auto xmn = [&](int p) { return A::kNanPad || p < xlim ? xs[padk<K>(p)] : HI; };
+    // A thread's positions p0..p0+E-1 share one padding group.
+    const int sx = padk<K>(p0), sp = padk<P>(p0);
+    auto xmx = [&](int k) { return A::kNanPad || p0 + k < xlim ? xs[sx + k] : LO; };
+    auto xmn = [&](int k) { return A::kNanPad || p0 + k < xlim ? xs[sx + k] : HI; };
     auto ymx = [&](int p) { return A::kNanPad || p < ylim ? xs[padk<K>(yoff + p)] : LO; };
     auto ymn = [&](int p) { return A::kNanPad || p < ylim ? xs[padk<K>(yoff + p)] : HI; };
     __syncthreads();
@@ -263,15 +278,15 @@ __global__ void __launch_bounds__(kArgThreads) argscan_kernel(const ArgParams<T>
             qmx = nmx;
             qmn = nmn;
         }
-        vmx[padk<K>(p)] = qmx.v;
-        vmn[padk<K>(p)] = qmn.v;
-        pmx[padk<P>(p)] = qmx.i;
-        pmn[padk<P>(p)] = qmn.i;
+        vmx[sx + k] = qmx.v;
+        vmn[sx + k] = qmn.v;
+        pmx[sp + k] = qmx.i;
+        pmn[sp + k] = qmn.i;
         const K ya = ymx(p), yb = ymn(p);
         if (ya > qmx.v) qmx = V{ya, (P)(yrel + p)};
         if (yb < qmn.v) qmn = V{yb, (P)(yrel + p)};
         if (!done) {
-            const K xa = xmx(p), xb = xmn(p);
+            const K xa = xmx(k), xb = xmn(k);
             if (xa > smx.v) smx = V{xa, (P)p};
             if (xb < smn.v) smn = V{xb, (P)p};
             done = (emask >> k) & 1u;
@@ -385,19 +400,19 @@ __global__ void __launch_bounds__(kArgThreads) argscan_kernel(const ArgParams<T>
             sa = nmx;
             sb = nmn;
         }
-        const K xa = xmx(p), xb = xmn(p);
+        const K xa = xmx(k), xb = xmn(k);
         if (xa >= sa.v) sa = V{xa, (P)p};
         if (xb <= sb.v) sb = V{xb, (P)p};
-        V qa{vmx[padk<K>(p)], pmx[padk<P>(p)]}, qb{vmn[padk<K>(p)], pmn[padk<P>(p)]};
+        V qa{vmx[sx + k], pmx[sp + k]}, qb{vmn[sx + k], pmn[sp + k]};
         if (k < fs) {
             qa = jmax(cqa, qa);
             qb = jmin(cqb, qb);
         }
         const V ra = qa.v > sa.v ? qa : sa, rb = qb.v < sb.v ? qb : sb;
-        vmx[padk<K>(p)] = ra.v;
-        pmx[padk<P>(p)] = ra.i;
-        vmn[padk<K>(p)] = rb.v;
-        pmn[padk<P>(p)] = rb.i;
+        vmx[sx + k] = ra.v;
+        pmx[sp + k] = ra.i;
+        vmn[sx + k] = rb.v;
+        pmn[sp + k] = rb.i;
     }
     __syncthreads();
     const int nv = (int)min((long long)len, prm.n_out - base);
@@ -571,7 +586,7 @@ cudaError_t argscan_1d(const LaunchCtx &ctx, const void *in, int64_t n, int64_t 
     if (w <= kArgTile) {
         prm.len_small = (int)((kArgTile / w) * w);
         const int64_t grid = (n_out + prm.len_small - 1) / prm.len_small;
-        return arg_launch<T, int>(ctx, prm, grid);
+        return arg_launch<T, unsigned>(ctx, prm, grid);
     }
     const int64_t ntiles = (w + kArgTile - 1) / kArgTile;
     const int64_t nbo = (n_out + w - 1) / w;  // blocks holding outputs
@@ -595,7 +610,8 @@ cudaError_t argscan_1d(const LaunchCtx &ctx, const void *in, int64_t n, int64_t 
         prm.ntiles = ntiles;
         prm.pg = pg;
         prm.sg = sg;
-        e = wide ? arg_launch<T, long long>(ctx, prm, nbo * ntiles) : arg_launch<T, int>(ctx, prm, nbo * ntiles);
+        e = wide ? arg_launch<T, unsigned long long>(ctx, prm, nbo * ntiles)
+                 : arg_launch<T, unsigned>(ctx, prm, nbo * ntiles);
     }
     const cudaError_t ef = cudaFreeAsync(ws, ctx.stream);
     return e != cudaSuccess ? e : ef;
