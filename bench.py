@@ -321,6 +321,19 @@ def wedge_extras(dev, stream, peak, n=1 << 30, windows=(3, 31, 101, 496), reps=3
                 gbs = (n + 2 * m) * 4 / ms / 1e6
                 row[k] = {"ms": ms, "Gelem_s": n / ms / 1e6, "GBps": gbs, "frac": gbs / peak}
             row["wedge_over_auto"] = row["auto"]["ms"] / row["wedge"]["ms"]
+            if w == 3:
+                # The two-comparison scheme of Section 3 with its comparisons
+                # counted on the device.
+                cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+                def h():
+                    mmf.filter1d_w3(x, out_max=om[:m], out_min=on[:m], stream=stream)
+                h()
+                ms = _events_ms(h, reps, stream)
+                gbs = (n + 2 * m) * 4 / ms / 1e6
+                _, _, cnt = mmf.filter1d_w3(x, out_max=om[:m], out_min=on[:m], count=True, stream=stream)
+                torch.cuda.synchronize()
+                row["w3_two_comparisons"] = {"ms": ms, "Gelem_s": n / ms / 1e6, "GBps": gbs, "frac": gbs / peak,
+                                             "comparisons_per_element": int(cnt.item()) / m}
             out[f"{d}_w{w}"] = row
         del x
     del om, on

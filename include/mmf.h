@@ -140,6 +140,22 @@ mmf_status mmf_argfilter1d(const void *d_in, int64_t n, int64_t w, mmf_dtype dty
 mmf_status mmf_argfilter1d_ex(const void *d_in, int64_t n, int64_t w, mmf_dtype dtype, void *d_max, void *d_min,
                               int64_t *d_argmax, int64_t *d_argmin, void *stream, mmf_kernel kernel);
 
+/* The window-3 filter by the two-comparison scheme of Section 3 (the
+ * proposition after the lower bound): knowing the order of the last two
+ * elements from the previous step, two comparisons of the new element (with
+ * the newer and with the older of the two) give the window's maximum and
+ * minimum and the order of the next pair.  Same outputs as mmf_filter1d with
+ * w = 3, MMF_VALID (n-2 each; n < 3 gives none).  Each GPU thread takes 16
+ * consecutive outputs and starts its pair with one comparison, so a chunk of
+ * c outputs makes 1 + 2c comparisons: ceil((n-2)/16) + 2(n-2) in all, which
+ * are ADDED to *d_ncmp when it is not NULL (the caller zeroes it).  Any of
+ * d_max, d_min, d_ncmp may be NULL (not all).  Pointers element-aligned,
+ * d_ncmp 8-byte aligned; MMF_EINVAL otherwise.  The default kernels take
+ * w = 3 in a register slide; this entry point shows the scheme's comparison
+ * count on the GPU. */
+mmf_status mmf_filter1d_w3(const void *d_in, int64_t n, mmf_dtype dtype, void *d_max, void *d_min,
+                           unsigned long long *d_ncmp, void *stream);
+
 /* Number of outputs of one side for (n, w_or_r, mode); -1 if invalid. */
 int64_t mmf_output_length(int64_t n, int64_t w_or_r, mmf_mode mode);
 

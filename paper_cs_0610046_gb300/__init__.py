@@ -17,7 +17,8 @@ import threading
 
 import torch
 
-__all__ = ["MMFError", "load", "filter1d", "output_length", "device_status", "BatchPlan", "filter2d", "Server", "n_outputs", "DTYPES", "KERNELS"]
+__all__ = ["MMFError", "load", "filter1d", "filter1d_host", "filter1d_w3", "argfilter1d", "output_length",
+           "device_status", "BatchPlan", "filter2d", "Server", "n_outputs", "DTYPES", "KERNELS"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmmf.so")
@@ -99,6 +100,7 @@ _EXTRA_SIGNATURES: dict = {
     "mmf_filter1d_host": ([_VP, _I64, _I64, _INT, _INT, _VP, _VP, _I64, _VP], _INT),
     "mmf_argfilter1d": ([_VP, _I64, _I64, _INT, _VP, _VP, _VP, _VP, _VP], _INT),
     "mmf_argfilter1d_ex": ([_VP, _I64, _I64, _INT, _VP, _VP, _VP, _VP, _VP, _INT], _INT),
+    "mmf_filter1d_w3": ([_VP, _I64, _INT, _VP, _VP, _VP, _VP], _INT),
     "mmf_stream_snapshot": ([_VP, ctypes.c_uint64, _VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), _INT], _INT),
     "mmf_stream_snapshot_wedge": ([_VP, ctypes.c_uint64, _VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), _INT],
                                   _INT),
@@ -224,6 +226,26 @@ def argfilter1d(x: torch.Tensor, w: int, stream=None, out=None, kernel: str = "a
         check(lib.mmf_argfilter1d_ex(_ptr(x), x.numel(), w, DTYPES[x.dtype], _ptr(vm), _ptr(vn), _ptr(am), _ptr(an),
                                      _VP(_stream_handle(stream)), KERNELS[kernel]))
     return am, an, vm, vn
+
+
+def filter1d_w3(x: torch.Tensor, out_max=None, out_min=None, count: bool = False, stream=None):
+    """Window-3 max and min by the two-comparison scheme (``mmf_filter1d_w3``):
+    returns ``(max, min)``, or ``(max, min, comparisons)`` with ``count``."""
+    _check_tensor(x, "x")
+    lib = load()
+    x = x.reshape(-1)
+    m = max(0, x.numel() - 2)
+    mx = out_max if out_max is not None else torch.empty(m, dtype=x.dtype, device=x.device)
+    mn = out_min if out_min is not None else torch.empty(m, dtype=x.dtype, device=x.device)
+    for t in (mx, mn):
+        _check_tensor(t, "output")
+        if t.dtype != x.dtype or t.numel() < m:
+            raise ValueError(f"outputs must be {x.dtype} tensors of at least {m} elements")
+    cnt = torch.zeros(1, dtype=torch.int64, device=x.device) if count else None
+    with torch.cuda.device(x.device):
+        check(lib.mmf_filter1d_w3(_ptr(x), x.numel(), DTYPES[x.dtype], _ptr(mx), _ptr(mn),
+                                  _ptr(cnt) if count else None, _VP(_stream_handle(stream))))
+    return (mx, mn, cnt) if count else (mx, mn)
 
 
 def _i64_array(xs):

@@ -164,6 +164,27 @@ mmf_status mmf_argfilter1d(const void *d_in, int64_t n, int64_t w, mmf_dtype dty
     return mmf_argfilter1d_ex(d_in, n, w, dtype, d_max, d_min, d_argmax, d_argmin, stream, MMF_KERNEL_AUTO);
 }
 
+mmf_status mmf_filter1d_w3(const void *d_in, int64_t n, mmf_dtype dtype, void *d_max, void *d_min,
+                           unsigned long long *d_ncmp, void *stream) {
+    const int esz = elem_size(dtype);
+    if (esz == 0) return set_error(MMF_EINVAL, "unknown dtype %d", (int)dtype);
+    if (n < 0) return set_error(MMF_EINVAL, "n = %lld", (long long)n);
+    if (n < 3) return MMF_OK;  // no window of 3
+    if (!d_max && !d_min && !d_ncmp) return set_error(MMF_EINVAL, "every output is NULL");
+    if (!d_in) return set_error(MMF_EINVAL, "NULL input with n = %lld", (long long)n);
+    if (((uintptr_t)d_in % esz) || ((uintptr_t)d_max % esz) || ((uintptr_t)d_min % esz) ||
+        ((uintptr_t)d_ncmp % 8))
+        return set_error(MMF_EINVAL, "misaligned pointer");
+    LaunchCtx ctx;
+    mmf_status st = get_ctx(stream, &ctx);
+    if (st != MMF_OK) return st;
+    return dispatch_dtype(dtype, [&](auto tag) -> mmf_status {
+        using T = decltype(tag);
+        const cudaError_t e = w3_1d<T>(ctx, d_in, n, d_max, d_min, d_ncmp);
+        return e == cudaSuccess ? MMF_OK : cuda_error(e, "w3 launch");
+    });
+}
+
 int64_t mmf_output_length(int64_t n, int64_t w_or_r, mmf_mode mode) {
     if (n < 0) return -1;
     if (mode == MMF_VALID) return w_or_r < 1 ? -1 : (n >= w_or_r ? n - w_or_r + 1 : 0);

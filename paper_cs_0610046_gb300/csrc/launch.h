@@ -76,6 +76,11 @@ cudaError_t wedge_1d(const LaunchCtx &ctx, const void *in, int64_t n, int64_t w,
 template <typename T>
 cudaError_t wedge_arg_1d(const LaunchCtx &ctx, const void *in, int64_t n, int64_t w, void *omax, void *omin,
                          int64_t *amax, int64_t *amin);
+// The window-3 filter in at most two comparisons per element (Section 3);
+// ncmp (nullable) accumulates the comparisons made.
+template <typename T>
+cudaError_t w3_1d(const LaunchCtx &ctx, const void *in, int64_t n, void *omax, void *omin,
+                  unsigned long long *ncmp);
 // Locations by block scans over (value, position) pairs, any window; windows
 // above 2048 take a stream-ordered workspace of per-tile aggregates.
 template <typename T>
