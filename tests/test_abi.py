@@ -70,6 +70,31 @@ def test_argument_errors_need_no_gpu(lib):
     assert len(lib.mmf_last_error()) > 0
 
 
+def test_argfilter_and_w3_argument_errors_need_no_gpu(lib):
+    """The arg filter and the window-3 entry points reject bad arguments (and
+    kernels that compute no locations) before any CUDA call."""
+    a = lib.mmf_argfilter1d_ex
+    a.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int] + [ctypes.c_void_p] * 5 + \
+        [ctypes.c_int]
+    a.restype = ctypes.c_int
+    assert a(16, 10, 3, 0, None, None, None, None, None, 0) == 1      # every output NULL
+    assert a(16, 10, 0, 0, 16, None, None, None, None, 0) == 1        # w < 1
+    assert a(16, 10, 3, 9, 16, None, None, None, None, 0) == 1        # bad dtype
+    assert a(16, 10, 3, 0, 16, None, 20, None, None, 0) == 1          # misaligned positions
+    assert a(16, 10, 3, 0, 16, None, None, None, None, 2) == 7        # the slide has no locations
+    assert a(16, 1000, 497, 0, 16, None, None, None, None, 3) == 7    # wedge window limit
+    assert a(16, 2, 3, 0, 16, None, None, None, None, 0) == 0         # w > n: nothing to do
+    f = lib.mmf_filter1d_w3
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int] + [ctypes.c_void_p] * 4
+    f.restype = ctypes.c_int
+    assert f(16, 10, 0, None, None, None, None) == 1                  # every output NULL
+    assert f(None, 10, 0, 16, None, None, None) == 1                  # NULL input
+    assert f(16, -1, 0, 16, None, None, None) == 1                    # n < 0
+    assert f(16, 10, 9, 16, None, None, None) == 1                    # bad dtype
+    assert f(16, 10, 0, 16, None, 12, None) == 1                      # misaligned counter
+    assert f(16, 2, 0, 16, None, None, None) == 0                     # no window of 3
+
+
 def test_product_path_fails_loudly_without_library(tmp_path, monkeypatch):
     import paper_cs_0610046_gb300 as mmf
     monkeypatch.setattr(mmf, "LIB_PATH", str(tmp_path / "missing.so"))
