@@ -463,49 +463,53 @@ template <typename K> __device__ __forceinline__ Agg<K> agg_empty() {
 }
 
 // g[b*ntiles + t] = aggregate of x over tile t of block b (clipped to the
-// block and to the array), for blocks 0..nb-1; grid-stride over tiles.
+// block and to the array), for blocks 0..nb-1: one warp per tile (64
+// coalesced loads per lane, 16 in flight), no barriers; warps stride over the
+// tiles.
 template <typename T>
-__global__ void __launch_bounds__(kArgThreads) argagg_kernel(const T *x, long long n, long long w, long long ntiles,
-                                                            long long nb, Agg<typename AKey<T>::K> *g) {
+__global__ void __launch_bounds__(256) argagg_kernel(const T *x, long long n, long long w, long long ntiles,
+                                                    long long nb, Agg<typename AKey<T>::K> *g) {
     using A = AKey<T>;
     using K = typename A::K;
-    __shared__ Agg<K> part[kArgWarps];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (long long u = blockIdx.x; u < nb * ntiles; u += gridDim.x) {
+    constexpr int PER_LANE = kArgTile / 32, BATCH = 16;
+    const int lane = threadIdx.x & 31;
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long u = wid; u < nb * ntiles; u += nwarps) {
         const long long b = u / ntiles, t = u % ntiles;
         const long long lo = b * w + t * kArgTile;
-        const long long hi = min(min(lo + kArgTile, (b + 1) * w), n);
-        Agg<K> a = agg_empty<K>();
-        T v[kArgE];
+        const int lim = (int)max(0LL, min(min((long long)kArgTile, (b + 1) * w - lo), n - lo));
+        const T *xt = x + lo;
+        // Per lane: extremes and their offsets in the tile (-1: none yet).
+        K vmax = KeyLim<K>::lo(), vmin = KeyLim<K>::hi();
+        int omax = -1, omin = -1;
+        for (int k0 = 0; k0 < PER_LANE; k0 += BATCH) {
+            T v[BATCH];
 #pragma unroll
-        for (int k = 0; k < kArgE; ++k) {
-            const long long i = lo + tid + k * kArgThreads;
-            v[k] = i < hi ? __ldg(x + i) : T(0);
-        }
+            for (int k = 0; k < BATCH; ++k) {
+                const int off = lane + (k0 + k) * 32;
+                v[k] = off < lim ? __ldg(xt + off) : T(0);
+            }
 #pragma unroll
-        for (int k = 0; k < kArgE; ++k) {
-            const long long i = lo + tid + k * kArgThreads;
-            if (i < hi) {
-                const K key = A::load(v[k]);
-                if (key > a.vmax || a.imax == LLONG_MAX) {
-                    a.vmax = key;
-                    a.imax = i;
-                }
-                if (key < a.vmin || a.imin == LLONG_MAX) {
-                    a.vmin = key;
-                    a.imin = i;
+            for (int k = 0; k < BATCH; ++k) {
+                const int off = lane + (k0 + k) * 32;
+                if (off < lim) {  // a lane's offsets increase: strict keeps the earliest
+                    const K key = A::load(v[k]);
+                    if (key > vmax || omax < 0) {
+                        vmax = key;
+                        omax = off;
+                    }
+                    if (key < vmin || omin < 0) {
+                        vmin = key;
+                        omin = off;
+                    }
                 }
             }
         }
+        Agg<K> a{vmax, vmin, omax < 0 ? LLONG_MAX : lo + omax, omin < 0 ? LLONG_MAX : lo + omin};
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) agg_join(a, agg_shfl_down(a, d));
-        if (lane == 0) part[warp] = a;
-        __syncthreads();
-        if (tid == 0) {
-            for (int q = 1; q < kArgWarps; ++q) agg_join(a, part[q]);
-            g[u] = a;
-        }
-        __syncthreads();
+        if (lane == 0) g[u] = a;
     }
 }
 
@@ -597,9 +601,9 @@ cudaError_t argscan_1d(const LaunchCtx &ctx, const void *in, int64_t n, int64_t 
     if (e != cudaSuccess) return e;
     Agg<K> *g = ws, *pg = ws + ng, *sg = ws + 2 * ng;
     const int64_t sms = ctx.sms > 0 ? ctx.sms : 1;
-    const int64_t agg_grid = (int64_t)ng < sms * 8 ? (int64_t)ng : sms * 8;
-    argagg_kernel<T><<<(unsigned)agg_grid, kArgThreads, 0, ctx.stream>>>(static_cast<const T *>(in), n, w, ntiles,
-                                                                       nb, g);
+    const int64_t agg_warps = (int64_t)ng < sms * 64 ? (int64_t)ng : sms * 64;  // 8 CTAs of 8 warps per SM
+    argagg_kernel<T><<<(unsigned)((agg_warps + 7) / 8), 256, 0, ctx.stream>>>(static_cast<const T *>(in), n, w,
+                                                                             ntiles, nb, g);
     e = cudaGetLastError();
     if (e == cudaSuccess) {
         argblock_scan_kernel<K><<<(unsigned)((nb + kArgWarps - 1) / kArgWarps), kArgThreads, 0, ctx.stream>>>(
