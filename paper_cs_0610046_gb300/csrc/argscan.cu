@@ -45,6 +45,7 @@ namespace {
 // spread over 16 elements; E = 16 keeps a thread's positions inside one
 // padding group, so its staged addresses are a base plus constants.
 constexpr int kArgThreads = 128, kArgE = 16, kArgTile = kArgThreads * kArgE, kArgWarps = kArgThreads / 32;
+constexpr int kArgSpanSmall = kArgTile + 512;
 
 template <typename T> struct AKey;
 template <> struct AKey<float> {
@@ -104,6 +105,11 @@ template <typename K> struct Agg {
 // elements per thread spread over the banks.
 template <typename K> __device__ __forceinline__ int padk(int p) { return p + p / (128 / (int)sizeof(K)); }
 template <typename K> __host__ __device__ constexpr int padded_len(int n) { return n + n / (128 / (int)sizeof(K)); }
+
+// Staged-input slots for a span, padded and kept a multiple of 16 bytes.
+template <typename K> __host__ __device__ constexpr int arg_span_slots(int span) {
+    return (padded_len<K>(span) + 3) & ~3;
+}
 
 template <typename T> struct ArgParams {
     const T *x;
@@ -175,16 +181,19 @@ __device__ __forceinline__ void store_side(T *oval, long long *oidx, long long b
     }
 }
 
-template <typename T, typename P>
+// SPAN: staged input slots, 2 * kArgTile, or kArgSpanSmall for whole blocks
+// of w <= kArgSpanSmall - kArgTile (one more CTA per SM).  Compile-time
+// offsets keep the staged inputs and the output staging provably apart.
+template <typename T, typename P, int SPAN>
 __global__ void __launch_bounds__(kArgThreads) argscan_kernel(const ArgParams<T> prm) {
     using A = AKey<T>;
     using K = typename A::K;
     using V = VI<K, P>;
     extern __shared__ __align__(16) unsigned char arg_smem[];
     __shared__ ArgScanSmem<K, P> sm;
-    constexpr int PX = padded_len<K>(2 * kArgTile), PK = padded_len<K>(kArgTile), PP = padded_len<P>(kArgTile);
+    constexpr int PK = padded_len<K>(kArgTile), PP = padded_len<P>(kArgTile);
     K *xs = reinterpret_cast<K *>(arg_smem);  // staged keys: x at p, y at yoff + p
-    K *vmx = xs + PX;
+    K *vmx = xs + arg_span_slots<K>(SPAN);
     K *vmn = vmx + PK;
     P *pmx = reinterpret_cast<P *>(vmn + PK);
     P *pmn = pmx + PP;
@@ -209,7 +218,8 @@ __global__ void __launch_bounds__(kArgThreads) argscan_kernel(const ArgParams<T>
     const int xlim = (int)max(0LL, min((long long)len, prm.n - base));
     const int ylim = (int)max(0LL, min((long long)len, prm.n - base - prm.w));
 
-    // Stage the inputs (all 2*kArgTile slots, loads issued before the stores).
+    // Stage the inputs (span slots: every x position and y position p <
+    // kArgTile; loads issued before the stores).
     {
         K kv[2 * kArgE];
         if (prm.ntiles == 0) {
@@ -230,7 +240,8 @@ __global__ void __launch_bounds__(kArgThreads) argscan_kernel(const ArgParams<T>
             }
         }
 #pragma unroll
-        for (int k = 0; k < 2 * kArgE; ++k) xs[padk<K>(tid + k * kArgThreads)] = kv[k];
+        for (int k = 0; k < 2 * kArgE; ++k)
+            if (tid + k * kArgThreads < SPAN) xs[padk<K>(tid + k * kArgThreads)] = kv[k];
     }
 
     // Segment starts (phase 0) and ends (phase w-1) among the thread's positions.
@@ -555,22 +566,23 @@ __global__ void __launch_bounds__(kArgThreads) argblock_scan_kernel(const Agg<K>
     }
 }
 
-template <typename T, typename P> constexpr size_t arg_smem_bytes() {
+template <typename T, typename P, int SPAN> constexpr size_t arg_smem_bytes() {
     using K = typename AKey<T>::K;
-    return (size_t)padded_len<K>(2 * kArgTile) * sizeof(K) + 2 * (size_t)padded_len<K>(kArgTile) * sizeof(K) +
+    return (size_t)arg_span_slots<K>(SPAN) * sizeof(K) + 2 * (size_t)padded_len<K>(kArgTile) * sizeof(K) +
            2 * (size_t)padded_len<P>(kArgTile) * sizeof(P);
 }
 
-template <typename T, typename P> cudaError_t arg_launch(const LaunchCtx &ctx, const ArgParams<T> &prm, int64_t grid) {
-    constexpr size_t smem = arg_smem_bytes<T, P>();
+template <typename T, typename P, int SPAN>
+cudaError_t arg_launch(const LaunchCtx &ctx, const ArgParams<T> &prm, int64_t grid) {
+    constexpr size_t smem = arg_smem_bytes<T, P, SPAN>();
     static int attr_set[64] = {};
     if (smem > 48 * 1024 && !attr_set[ctx.device & 63]) {
         cudaError_t e =
-            cudaFuncSetAttribute(argscan_kernel<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(argscan_kernel<T, P, SPAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_set[ctx.device & 63] = 1;
     }
-    argscan_kernel<T, P><<<(unsigned)grid, kArgThreads, smem, ctx.stream>>>(prm);
+    argscan_kernel<T, P, SPAN><<<(unsigned)grid, kArgThreads, smem, ctx.stream>>>(prm);
     return cudaGetLastError();
 }
 
@@ -590,7 +602,10 @@ cudaError_t argscan_1d(const LaunchCtx &ctx, const void *in, int64_t n, int64_t 
     if (w <= kArgTile) {
         prm.len_small = (int)((kArgTile / w) * w);
         const int64_t grid = (n_out + prm.len_small - 1) / prm.len_small;
-        return arg_launch<T, unsigned>(ctx, prm, grid);
+        // Windows up to 512 stage kArgTile + w <= kArgSpanSmall inputs: one
+        // more CTA per SM (f32: 5 instead of 4).
+        return w <= kArgSpanSmall - kArgTile ? arg_launch<T, unsigned, kArgSpanSmall>(ctx, prm, grid)
+                                             : arg_launch<T, unsigned, 2 * kArgTile>(ctx, prm, grid);
     }
     const int64_t ntiles = (w + kArgTile - 1) / kArgTile;
     const int64_t nbo = (n_out + w - 1) / w;  // blocks holding outputs
@@ -614,8 +629,8 @@ cudaError_t argscan_1d(const LaunchCtx &ctx, const void *in, int64_t n, int64_t 
         prm.ntiles = ntiles;
         prm.pg = pg;
         prm.sg = sg;
-        e = wide ? arg_launch<T, unsigned long long>(ctx, prm, nbo * ntiles)
-                 : arg_launch<T, unsigned>(ctx, prm, nbo * ntiles);
+        e = wide ? arg_launch<T, unsigned long long, 2 * kArgTile>(ctx, prm, nbo * ntiles)
+                 : arg_launch<T, unsigned, 2 * kArgTile>(ctx, prm, nbo * ntiles);
     }
     const cudaError_t ef = cudaFreeAsync(ws, ctx.stream);
     return e != cudaSuccess ? e : ef;
