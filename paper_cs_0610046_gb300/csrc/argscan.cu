@@ -27,11 +27,12 @@
 // backward sweep forms S, completes Q with its carry and joins them.  Outputs
 // leave through shared memory in 16-byte stores.
 //
-// Positions are offsets from base (x: p, y: w+p, carries inside [0, w+len)),
-// unsigned 32-bit unless w is near 2^31.  f32, i16 and u8 compare as float keys (exact
-// for 8- and 16-bit integers), so a NaN marks staged positions outside the
-// array: every comparison with it is false, so no sweep takes it.  f64 keys
-// are order-preserving 64-bit integers, with explicit limits.
+// Positions are offsets from base (x: p, y: w+p, carries inside [0, w+len)):
+// unsigned 32-bit for w < 2^30, else 64-bit.  f32, i16 and u8 compare as
+// float keys (exact for 8- and 16-bit integers), so a NaN marks staged
+// positions outside the array: every comparison with it is false, so no sweep
+// takes it.  f64 keys are order-preserving 64-bit integers, with explicit
+// limits.
 #include <climits>
 #include <cstdint>
 
