@@ -134,13 +134,15 @@ mmf_status mmf_argfilter1d_ex(const void *d_in, int64_t n, int64_t w, mmf_dtype 
     if (elem_size(dtype) == 0) return set_error(MMF_EINVAL, "unknown dtype %d", (int)dtype);
     if (kernel != MMF_KERNEL_AUTO && kernel != MMF_KERNEL_BLOCKSCAN && kernel != MMF_KERNEL_WEDGE)
         return set_error(MMF_ENOTIMPL, "kernel %d does not compute locations", (int)kernel);
-    SeriesDesc sd;
-    mmf_status st = make_series(n, w, MMF_VALID, dtype, &sd);
-    if (st != MMF_OK) return st;
+    // Any window: the block scans over (value, position) pairs carry long
+    // blocks through per-tile aggregates, so the value filter's window limit
+    // does not apply here.
+    if (n < 0) return set_error(MMF_EINVAL, "n = %lld < 0", (long long)n);
+    if (w < 1) return set_error(MMF_EINVAL, "window w = %lld < 1", (long long)w);
     if (kernel == MMF_KERNEL_WEDGE && w > MMF_WEDGE_MAX_WINDOW)
         return set_error(MMF_ENOTIMPL, "the wedge kernel computes locations for windows up to %d",
                          MMF_WEDGE_MAX_WINDOW);
-    if (sd.n_out == 0) return MMF_OK;
+    if (n < w) return MMF_OK;  // no window fits
     if (!d_max && !d_min && !d_argmax && !d_argmin) return set_error(MMF_EINVAL, "every output is NULL");
     if (!d_in) return set_error(MMF_EINVAL, "NULL input with n = %lld", (long long)n);
     const int esz = elem_size(dtype);
@@ -148,7 +150,7 @@ mmf_status mmf_argfilter1d_ex(const void *d_in, int64_t n, int64_t w, mmf_dtype 
         ((uintptr_t)d_argmax % 8) || ((uintptr_t)d_argmin % 8))
         return set_error(MMF_EINVAL, "misaligned pointer");
     LaunchCtx ctx;
-    st = get_ctx(stream, &ctx);
+    const mmf_status st = get_ctx(stream, &ctx);
     if (st != MMF_OK) return st;
     return dispatch_dtype(dtype, [&](auto tag) -> mmf_status {
         using T = decltype(tag);

@@ -84,6 +84,8 @@ def test_argfilter_and_w3_argument_errors_need_no_gpu(lib):
     assert a(16, 10, 3, 0, 16, None, None, None, None, 2) == 7        # the slide has no locations
     assert a(16, 1000, 497, 0, 16, None, None, None, None, 3) == 7    # wedge window limit
     assert a(16, 2, 3, 0, 16, None, None, None, None, 0) == 0         # w > n: nothing to do
+    assert a(16, -1, 3, 0, 16, None, None, None, None, 0) == 1        # n < 0
+    assert a(16, 10, 2 ** 31, 0, 16, None, None, None, None, 0) == 0  # any window (here w > n)
     f = lib.mmf_filter1d_w3
     f.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int] + [ctypes.c_void_p] * 4
     f.restype = ctypes.c_int

@@ -142,3 +142,27 @@ def test_argfilter_positions_beyond_2_31(mmf):
         del am, an, vm, vn
     del x
     torch.cuda.empty_cache()
+
+
+def test_argfilter_window_above_2_30(mmf):
+    """w = 2^30 + 1 (64-bit positions inside the kernel) on a u8 array of
+    2^30 + 100 elements of 128 with planted extremes, whose leftmost positions
+    follow from where they lie: a 255 at 2^29 (in every window), 0 at 5 and
+    at 2^30 + 20, a 255 at 2^30 + 50 (never leftmost)."""
+    n, w = (1 << 30) + 100, (1 << 30) + 1
+    x = torch.full((n,), 128, dtype=torch.uint8, device="cuda")
+    x[1 << 29] = 255
+    x[(1 << 30) + 50] = 255
+    x[5] = 0
+    x[(1 << 30) + 20] = 0
+    am, an, vm, vn = mmf.argfilter1d(x, w)
+    torch.cuda.synchronize()
+    m = n - w + 1
+    exp_max = np.full(m, 1 << 29)
+    exp_min = np.array([5 if j <= 5 else (j if j + w - 1 < (1 << 30) + 20 else (1 << 30) + 20) for j in range(m)])
+    exp_vmin = np.array([0 if (j <= 5 or j + w - 1 >= (1 << 30) + 20) else 128 for j in range(m)])
+    assert np.array_equal(am.cpu().numpy(), exp_max)
+    assert np.array_equal(an.cpu().numpy(), exp_min)
+    assert bool((vm == 255).all()) and np.array_equal(vn.cpu().numpy(), exp_vmin.astype(np.uint8))
+    del x, am, an, vm, vn
+    torch.cuda.empty_cache()
