@@ -44,32 +44,36 @@ def _side(x, w, is_max):
     out_i = np.zeros(n_out, np.int64)
     if w > TILE:
         ntiles = -(-w // TILE)
-        nbo = -(-n_out // w)
-        agg = [[None] * ntiles for _ in range(nbo + 1)]
+        nbo = -(-n_out // w)  # blocks holding outputs; Q reads the block after them
+
+        def tile_agg(b, t):  # leftmost extreme of tile t of block b, or None if empty
+            lo = b * w + t * TILE
+            best = None
+            for i in range(lo, min(lo + TILE, (b + 1) * w, n)):
+                if best is None or gt(x[i], best[0]):
+                    best = (x[i], i)
+            return best
+
+        def keep_left(a, b):  # a's range left of b's
+            if a is None:
+                return b
+            if b is None:
+                return a
+            return b if gt(b[0], a[0]) else a
+
+        pre, suf = [], []
         for b in range(nbo + 1):
-            for t in range(ntiles):
-                lo = b * w + t * TILE
-                hi = min(lo + TILE, (b + 1) * w, n)
-                best = (ident, None)
-                for i in range(lo, max(lo, hi)):
-                    if best[1] is None or gt(x[i], best[0]):
-                        best = (x[i], i)
-                agg[b][t] = best
-        pre = [[None] * ntiles for _ in range(nbo + 1)]
-        suf = [[None] * ntiles for _ in range(nbo + 1)]
-        for b in range(nbo + 1):
-            c = (ident, None)
-            for t in range(ntiles):
-                a = agg[b][t]
-                if c[1] is None or (a[1] is not None and gt(a[0], c[0])):
-                    c = a if a[1] is not None else c
-                pre[b][t] = c
-            c = (ident, None)
+            aggs = [tile_agg(b, t) for t in range(ntiles)]
+            p, acc = [], None
+            for a in aggs:
+                acc = keep_left(acc, a)
+                p.append(acc)
+            q, acc = [None] * ntiles, None
             for t in reversed(range(ntiles)):
-                a = agg[b][t]
-                if a[1] is not None and (c[1] is None or ge(a[0], c[0])):
-                    c = a
-                suf[b][t] = c
+                acc = keep_left(aggs[t], acc)
+                q[t] = acc
+            pre.append(p)
+            suf.append(q)
         tiles = [(b, t) for b in range(nbo) for t in range(ntiles)]
     else:
         ntiles = 0
@@ -87,15 +91,18 @@ def _side(x, w, is_max):
         ys = [x[base + w + p] if p < ln and base + w + p < n else np.nan for p in range(TILE)]
         cq = cs = none
         if ntiles:
-            if t > 0 and pre[b + 1][t - 1][1] is not None:
+            if t > 0 and pre[b + 1][t - 1] is not None:
                 cq = (pre[b + 1][t - 1][0], pre[b + 1][t - 1][1] - base)
-            if t + 1 < ntiles and suf[b][t + 1][1] is not None:
+            if t + 1 < ntiles and suf[b][t + 1] is not None:
                 cs = (suf[b][t + 1][0], suf[b][t + 1][1] - base)
+        # Segment starts and ends among each thread's positions; past the last
+        # tile of a block (phase >= w) a thread has none.
         starts, ends = [], []
         for th in range(NT):
             r = ((th * E) % w) if ntiles == 0 else r0 + th * E
-            starts.append({k for k in range(E) if (r + k) % w == 0 and r + k < w + (0 if ntiles else w * E)})
-            ends.append({k for k in range(E) if (r + k) % w == w - 1})
+            ph = [r + k if ntiles else (r + k) % w for k in range(E)]
+            starts.append({k for k in range(E) if ph[k] == 0})
+            ends.append({k for k in range(E) if ph[k] == w - 1})
         staged = [None] * TILE
         qsum, ssum = [], []
         for th in range(NT):
