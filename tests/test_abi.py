@@ -103,3 +103,36 @@ def test_product_path_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(mmf, "_lib", None)
     with pytest.raises(RuntimeError):
         mmf.load()
+
+
+def test_plain_c_program_uses_the_abi(lib, tmp_path):
+    """The header is plain C (C99, pedantic) and a C program links the shared
+    library and makes host-only calls through it."""
+    import shutil
+    import subprocess
+    from paper_cs_0610046_gb300 import build
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_mmf.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include <string.h>
+#include "mmf.h"
+int main(void) {
+    if (mmf_output_length(10, 3, MMF_VALID) != 8) return 1;
+    if (mmf_output_length(10, 4, MMF_CENTERED_CLIPPED) != 10) return 2;
+    if (mmf_filter1d((const void *)16, 10, 0, MMF_F32, MMF_VALID, (void *)16, NULL, NULL) != MMF_EINVAL) return 3;
+    if (strlen(mmf_last_error()) == 0) return 4;
+    if (strstr(mmf_version(), "sm_103a") == NULL) return 5;
+    printf("ok\n");
+    return 0;
+}
+""")
+    exe = tmp_path / "use_mmf"
+    libdir = os.path.dirname(build.LIB)
+    libname = os.path.basename(build.LIB)
+    cmd = ["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+           str(src), "-o", str(exe), os.path.join(libdir, libname), f"-Wl,-rpath,{libdir}"]
+    subprocess.run(cmd, check=True, capture_output=True, text=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", (out.returncode, out.stdout, out.stderr)
