@@ -95,9 +95,10 @@ mmf_status make_series(int64_t n, int64_t w_or_r, mmf_mode mode, mmf_dtype dt, S
         sd->n_out = n >= w_or_r ? n - w_or_r + 1 : 0;
     } else if (mode == MMF_CENTERED_CLIPPED) {
         if (w_or_r < 0) return set_error(MMF_EINVAL, "radius r = %lld < 0", (long long)w_or_r);
-        // A radius of n-1 already covers the whole array from every centre.
+        // A radius of n-1 already covers the whole array from every centre
+        // (and an empty array has no windows, so 2r+1 never overflows).
         int64_t r = w_or_r;
-        if (n > 0 && r > n - 1) r = n - 1;
+        if (r > n - 1) r = n > 0 ? n - 1 : 0;
         sd->w = 2 * r + 1;
         sd->d = -r;
         sd->n_out = n;

@@ -196,6 +196,9 @@ static mmf_status check2d(int64_t nimg, int64_t H, int64_t W, int64_t pitch, int
     if (elem_size(dt) == 0) return set_error(MMF_EINVAL, "unknown dtype %d", (int)dt);
     if (nimg < 0 || H < 0 || W < 0 || pitch < W) return set_error(MMF_EINVAL, "bad image geometry");
     if (wy < 1 || wx < 1) return set_error(MMF_EINVAL, "windows must be >= 1");
+    // Far beyond what the column pass's shared memory holds; checked first so
+    // that the ring size below stays within an int.
+    if (wy > (int64_t(1) << 20)) return set_error(MMF_ENOTIMPL, "column window %lld too large", (long long)wy);
     if (fuse == 1 && wy > 1 && wx > MMF_FUSED_MAX_WX)
         return set_error(MMF_ENOTIMPL, "the fused 2D kernel handles row windows up to %d", MMF_FUSED_MAX_WX);
     // Column-pass shared memory: P ring plus the tile-aggregate ring.

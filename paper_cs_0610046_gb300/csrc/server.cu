@@ -563,6 +563,9 @@ void mmf_server_destroy(mmf_server *S) {
 mmf_status mmf_stream_open(mmf_server *S, int64_t w, uint64_t *stream_id) {
     if (!S || !stream_id) return set_error(MMF_EINVAL, "NULL argument");
     if (w < 1) return set_error(MMF_EINVAL, "window w = %lld < 1", (long long)w);
+    // Compared in elements so that (w-1)*esz cannot wrap around.
+    if ((uint64_t)(w - 1) > S->stage.size() / (uint64_t)S->esz)
+        return set_error(MMF_ENOMEM, "a window of %lld needs a halo larger than the device budget", (long long)w);
     std::lock_guard<std::mutex> lk(S->mu);
     StreamState ss;
     ss.w = w;
@@ -583,6 +586,9 @@ namespace {
 mmf_status push_locked(mmf_server *S, uint64_t stream_id, const void *h_chunk, int64_t len, void *h_max,
                        void *h_min, int64_t *n_out, uint64_t *ticket) {
     if (len < 0 || (len > 0 && !h_chunk)) return set_error(MMF_EINVAL, "bad chunk");
+    // Compared in elements before any byte count is formed (no wrap-around).
+    if ((uint64_t)len > S->stage.size() / (uint64_t)S->esz)
+        return set_error(MMF_ENOMEM, "chunk larger than the device budget allows");
     if (S->failed != MMF_OK) return set_error(MMF_EDEVICE, "the server failed earlier");
     auto it = S->streams.find(stream_id);
     if (it == S->streams.end() || it->second.closed)
@@ -856,17 +862,24 @@ mmf_status mmf_stream_restore(mmf_server *S, const void *h_buf, size_t buf_bytes
     if (hd.dtype != (int32_t)S->dtype) return set_error(MMF_EINVAL, "snapshot of another dtype");
     if (hd.w < 1 || hd.count < 0 || hd.halo_len != std::min<int64_t>(hd.count, hd.w - 1))
         return set_error(MMF_EINVAL, "inconsistent snapshot header");
+    // The stream's halo must fit the budget (as in mmf_stream_open); checked
+    // before any host buffer is sized from the header.
+    if ((uint64_t)(hd.w - 1) > S->stage.size() / (uint64_t)S->esz)
+        return set_error(MMF_ENOMEM, "a window of %lld needs a halo larger than the device budget",
+                         (long long)hd.w);
+    const size_t body = buf_bytes - sizeof(hd);  // bytes after the header
     std::vector<char> rebuilt;
     const char *halo_bytes = static_cast<const char *>(h_buf) + sizeof(hd);
     if (hd.version == 2u) {
         // A wedge: rebuild an equivalent halo.
-        if (buf_bytes < sizeof(hd) + 16) return set_error(MMF_EINVAL, "truncated snapshot");
+        if (body < 16) return set_error(MMF_EINVAL, "truncated snapshot");
         int64_t nu, nl;
         memcpy(&nu, halo_bytes, 8);
         memcpy(&nl, halo_bytes + 8, 8);
         const size_t rec = 8 + (size_t)S->esz;
+        const uint64_t fits = (body - 16) / rec;  // whole records present in the buffer
         if (nu < 0 || nl < 0 || nu > hd.halo_len || nl > hd.halo_len || (hd.halo_len > 0 && (nu < 1 || nl < 1)) ||
-            buf_bytes < sizeof(hd) + 16 + (size_t)(nu + nl) * rec)
+            (uint64_t)nu > fits || (uint64_t)nl > fits - (uint64_t)nu)
             return set_error(MMF_EINVAL, "truncated or inconsistent wedge snapshot");
         for (int64_t j = 0; j < nu + nl; ++j) {
             int64_t back;
@@ -883,7 +896,7 @@ mmf_status mmf_stream_restore(mmf_server *S, const void *h_buf, size_t buf_bytes
             }
         }
         halo_bytes = rebuilt.data();
-    } else if (buf_bytes < sizeof(hd) + (size_t)hd.halo_len * S->esz) {
+    } else if ((uint64_t)hd.halo_len > body / (uint64_t)S->esz) {
         return set_error(MMF_EINVAL, "truncated snapshot");
     }
     uint64_t id = 0;

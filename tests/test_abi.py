@@ -97,6 +97,24 @@ def test_argfilter_and_w3_argument_errors_need_no_gpu(lib):
     assert f(16, 2, 0, 16, None, None, None) == 0                     # no window of 3
 
 
+def test_extreme_sizes_need_no_gpu(lib):
+    """Sizes near 2^63 are refused (or give nothing) on the host, before any
+    byte count could wrap around."""
+    f = lib.mmf_filter1d
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    assert f(None, 0, 2 ** 62, 0, 1, None, None, None) == 0      # empty envelope, any radius
+    assert f(None, 0, 2 ** 63 - 1, 0, 0, None, None, None) == 0  # empty valid filter, any window
+    ws = lib.mmf_filter2d_workspace
+    ws.argtypes = [ctypes.c_int64] * 5 + [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
+    ws.restype = ctypes.c_int
+    nbytes = ctypes.c_size_t(0)
+    # a column window whose ring size would not fit an int: refused
+    assert ws(1, 2 ** 40, 1, 2 ** 35 + 1, 1, 0, -1, ctypes.byref(nbytes)) == 7
+    assert ws(1, 4096, 4096, 3, 3, 0, 0, ctypes.byref(nbytes)) == 0 and nbytes.value > 0
+
+
 def test_product_path_fails_loudly_without_library(tmp_path, monkeypatch):
     import paper_cs_0610046_gb300 as mmf
     monkeypatch.setattr(mmf, "LIB_PATH", str(tmp_path / "missing.so"))

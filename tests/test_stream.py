@@ -273,6 +273,44 @@ def test_snapshot_64bit_count_and_rejects(mmf):
     assert mmf.device_status() == 0
 
 
+def test_sizes_past_the_budget_are_refused_on_host(mmf):
+    """Windows, chunk lengths and snapshot headers whose byte counts would
+    pass 2^64 are refused before anything is copied (1 MiB budget), and the
+    server keeps serving."""
+    import ctypes
+    import struct
+    srv = mmf.Server(1 << 20, 8, "float32")
+    for w in ((1 << 62) + 1, (1 << 20) + 1):
+        with pytest.raises(mmf.MMFError) as e:
+            srv.open(w)
+        assert e.value.status == 2  # MMF_ENOMEM
+    sid = srv.open(16)
+    x = np.zeros(16, np.float32)
+    n_out, t = ctypes.c_int64(0), ctypes.c_uint64(0)
+    for n in (1 << 62, (1 << 62) + (1 << 61)):  # far past the 16 elements really there
+        st = srv._lib.mmf_stream_push(srv._h, sid, ctypes.c_void_p(x.ctypes.data), n,
+                                      ctypes.c_void_p(x.ctypes.data), None, ctypes.byref(n_out), ctypes.byref(t))
+        assert st == 2
+    for w in ((1 << 62) + 1, (1 << 61) + 1):
+        for version, body in ((1, b"\0" * 64), (2, struct.pack("<qq", 1 << 60, 1 << 60) + b"\0" * 24)):
+            hdr = struct.pack("<IIiiqqq", 0x53464D4D, version, 0, 0, w, w - 1, w - 1)
+            with pytest.raises(mmf.MMFError) as e:
+                srv.restore(hdr + body)
+            assert e.value.status == 2
+    # a wedge whose record count runs past the end of the buffer
+    hdr = struct.pack("<IIiiqqq", 0x53464D4D, 2, 0, 0, 5, 100, 4)
+    with pytest.raises(mmf.MMFError) as e:
+        srv.restore(hdr + struct.pack("<qq", 4, 4) + struct.pack("<qf", 1, 1.0))
+    assert e.value.status == 1  # MMF_EINVAL
+    chunk = synth.uniform(1000, 3, np.float32)
+    om = np.empty(985, np.float32)
+    t2, m = srv.push(sid, chunk, om, None)
+    srv.wait(t2)
+    assert m == 985 and np.array_equal(om, oracle.bf1d(chunk, 16)[0])
+    srv.close()
+    assert mmf.device_status() == 0
+
+
 @pytest.mark.parametrize("kind", ["random_walk", "uniform", "increasing", "decreasing", "constant", "steps"])
 @pytest.mark.parametrize("w", [2, 33, 9001])
 def test_wedge_snapshot_continues_exactly(mmf, kind, w):
