@@ -8,26 +8,35 @@
 //     max[j] = max( S_B[j], agg(blocks strictly between), P_B[k] )
 // where S_B[j] is the maximum from j to the end of its block (a suffix scan)
 // and P_B[k] the maximum from the start of k's block to k (a prefix scan).
-//   * s <  T (tile): B = 2^floor(log2 s); then b(k) is b(j)+1 or b(j)+2 and at
-//     most one block aggregate is needed, read back as P_B at that block's end.
-//   * s >= T: B = T (blocks are tiles); k lies q or q+1 tiles after j
-//     (s = qT + r), and the tiles between contribute tile aggregates kept in a
-//     small ring in shared memory.
-// The thread that owns output j holds S_B[j] in registers; P_B is written to a
-// 3-tile ring of (max, min) pairs in shared memory and read back at offset s.
-// Each input element is read from HBM once (for s >= T the J-side tile is
-// read again about w elements later, normally from L2) and each output is
-// written once.
+// A tile is NT threads x V consecutive elements per thread (f32: 128 x 16).
+// Block modes, by s (the register slide, mode 3, takes w <= 17 for f32 and
+// w <= 9 for the other types instead):
+//   0  s < V:       B = 2^floor(log2 s), blocks inside one thread;
+//   1  s < 32V:     B = 2^floor(log2 s), blocks of 2..16 lanes;
+//   2  s >= 32V:    B = 32V, one block per warp slice.
+// With B = 2^floor(log2 s) (modes 0, 1), k's block is b(j)+1 or b(j)+2, so at
+// most one whole block lies between.  Every thread scans its own V elements
+// (a local prefix for the K role, a local suffix for the J role); the parts
+// of the window outside the two local scans (lane carries inside j's and k's
+// blocks, the whole blocks between) are per-thread constants, so each output
+// is one three-operand max (and min).  Local prefixes go to a 3-tile ring of
+// (max, min) pairs in shared memory and are read back at offset s.  For
+// s >= T (case B, mode 2 only) whole tiles lie between: their aggregates
+// are kept by warp 0 as a sliding two-stack queue (TileQueue) inside a ring
+// of tile aggregates, and the J tile is read a second time, about w elements
+// after its read as a K tile.  Otherwise each input element is read from
+// global memory once, and each output is written once.
 //
 // Work decomposition.  A work item is a contiguous range of output tiles of
-// one series.  A CTA (8 warps, two per SM) owns one item at a time and streams
-// its input tiles in order.  Thread 0 issues 1D bulk TMA copies into a ring of
-// stages (mbarrier transaction counts) right after each CTA barrier, into the
-// stages consumed before it, so it never waits.  Outputs of tile c are formed
-// one iteration later, after the barrier that also serves the scans of tile
-// c+1: one barrier per tile.  Items come from a static round-robin (1D
-// launches) or an atomic ticket (batched plans).  Every wait is bounded; a
-// timeout sets a bit in the device status word and the CTA returns.
+// one series.  A CTA owns one item at a time and streams its input tiles in
+// order.  Each warp reads only its own slice (32V elements) of every tile,
+// so each warp has its own ring of kStages stages fed by 1D bulk copies that
+// its lane 0 issues (one mbarrier per warp and stage), refilling a stage as
+// soon as the warp has read it.  One CTA barrier per tile orders the prefix
+// ring and the block aggregates between warps.  Items come from a static
+// round-robin (1D launches) or an atomic ticket (batched plans).  Every wait
+// is bounded; a timeout sets a bit in the device status word and the CTA
+// returns.
 #pragma once
 #include <cstdint>
 
