@@ -8,9 +8,13 @@
 // Continuous batching: push() queues a chunk and returns a ticket.  A worker
 // thread repeatedly admits queued chunks (FIFO, at most one chunk per stream
 // in flight, while the device-memory budget allows), and runs each admitted
-// batch as: host-to-device copies of the chunks behind their streams' halos,
-// one batched filter launch per kernel group over all of them, one
-// halo-update launch, and device-to-host copies of the outputs.  Batches
+// batch as: the chunks placed behind their streams' halos, one batched filter
+// launch per kernel group over all of them, one halo-update launch, and the
+// outputs returned to the caller's host buffers.  Where the GPU can reach
+// those host buffers itself (pinned memory, or any host memory on a system
+// with pageable-memory access such as NVLink-C2C), a gather kernel reads the
+// chunks and a scatter kernel writes the outputs; otherwise one copy per
+// chunk and per output side is issued.  Batches
 // rotate over a few CUDA streams so that copies and kernels of consecutive
 // batches overlap; chunks that arrive while a batch runs join the next batch
 // as soon as memory and their stream allow.  Completion is observed through
