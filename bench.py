@@ -191,9 +191,19 @@ def cpu_baseline(sample: int):
         for w in WINDOWS:
             oracle.wedge(a[d], w)
     dt1 = time.perf_counter() - t0
+    # The definition itself (the naive row of Table 1, 2w-2 comparisons per
+    # output), single thread, where it is feasible: w <= 1001, on a sample
+    # of min(2^20, 2^28/w) elements per distribution (about a second each).
+    naive = {}
+    for w in (x for x in WINDOWS if x <= 1001):
+        ns = min(sample, 1 << 20, (1 << 28) // w)
+        t0 = time.perf_counter()
+        for d in DISTS:
+            oracle.bf1d(a[d][:ns], w)
+        naive[str(w)] = {"value": len(DISTS) * ns / (time.perf_counter() - t0) / 1e9, "sample": ns}
     elems = len(DISTS) * len(WINDOWS) * sample
     return {"value": elems / dt / 1e9, "unit": "Gelem/s", "cores": used, "kind": "oracle",
-            "single_core_value": elems / dt1 / 1e9,
+            "single_core_value": elems / dt1 / 1e9, "naive_single_core_by_window": naive,
             "sample": f"{sample} elements per distribution x 3 distributions x 4 windows, "
                       f"Algorithm 1 wedge split into {used} chunks with a w-1 halo on {used} threads "
                       f"({dt:.1f} s); single thread {dt1:.1f} s"}
