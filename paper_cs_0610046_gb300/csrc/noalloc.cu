@@ -17,6 +17,7 @@
 // them on one stream.
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 
 #include "launch.h"
 #include "mmf.h"
@@ -53,6 +54,7 @@ struct DevAddr {
     NoAllocTables *ptr = nullptr;
 };
 static DevAddr g_noalloc_addr[64];
+static std::mutex g_noalloc_mu;  // guards the per-device set-up above
 
 int mode_of(mmf_dtype dt, int64_t w) {
     switch (dt) {
@@ -121,16 +123,22 @@ extern "C" mmf_status mmf_filter1d_batched_noalloc(const void *d_in, const int64
     if (st != MMF_OK) return st;
     // Set-up once per device, with that device current: the device address of
     // the table array.  (The first call on a device does this; make it before
-    // any stream capture.)
-    DevAddr &da = g_noalloc_addr[ctx.device];
-    if (!da.ready) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc);
-        if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(no-allocation tables)");
-        da.ptr = static_cast<NoAllocTables *>(p);
-        da.ready = true;
+    // any stream capture.)  It is done under a lock, so that a thread which
+    // finds the set-up done also sees the address (on a weakly ordered CPU a
+    // thread could otherwise see the flag before the pointer).
+    NoAllocTables *tab = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        DevAddr &da = g_noalloc_addr[ctx.device];
+        if (!da.ready) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc);
+            if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(no-allocation tables)");
+            da.ptr = static_cast<NoAllocTables *>(p);
+            da.ready = true;
+        }
+        tab = da.ptr;
     }
-    NoAllocTables *tab = da.ptr;
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemcpyAsync(tab->series, series, nseries * sizeof(SeriesDesc), cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess) e = cudaMemcpyAsync(tab->items, items, ni * sizeof(ItemDesc), cudaMemcpyHostToDevice, cs);
