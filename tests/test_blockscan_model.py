@@ -217,3 +217,27 @@ def test_tile_queue_is_a_sliding_window():
             ring[(c + q + 1) % cap] = (vals[c + q + 1], vals[c + q + 1])
             if q >= 2:
                 tq.slide(c + q)
+
+
+def test_register_slide_windows():
+    """The register slide (windows up to 17 for f32, 9 for the other types):
+    a thread holds its V elements and the HALO that follow them; doubling
+    passes p = 1, 2, .., P2/2 in place, then each window of W = P2 + r is the
+    union of values i and i + r.  Every output must use only the NE = V + HALO
+    values held and equal the window's extreme."""
+    rng = np.random.default_rng(17)
+    for V, HALO, wmax in ((16, 16, 17), (16, 8, 9), (4, 8, 9)):  # f32; i16/u8; f64
+        NE = V + HALO
+        for W in range(1, wmax + 1):
+            P2 = 16 if W >= 16 else 8 if W >= 8 else 4 if W >= 4 else 2 if W >= 2 else 1
+            assert (V - 1) + (W - P2) + P2 - 1 < NE  # the last value read stays in the thread
+            x = rng.integers(-3, 4, size=(200, NE)).astype(float)
+            a = x.copy()
+            p = 1
+            while p < P2:
+                for i in range(NE - p):
+                    a[:, i] = np.maximum(a[:, i], a[:, i + p])
+                p <<= 1
+            got = np.maximum(a[:, :V], a[:, W - P2:W - P2 + V])
+            want = np.stack([x[:, i:i + W].max(axis=1) for i in range(V)], axis=1)
+            assert np.array_equal(got, want), (V, HALO, W)
