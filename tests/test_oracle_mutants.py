@@ -2,8 +2,13 @@
 
 Each case copies ``oracle/mmf_oracle.c``, plants one plausible mistake (a
 short window, a flipped comparison, a wrong deque end, an off-by-one expiry,
-a clipped envelope, a short rectangle), compiles the copy with gcc into a
-temporary library, and runs the pin checks of ``test_oracle`` against it.
+a clipped envelope, a short rectangle; for the arg filter a rightmost tie
+rule or a short window; for the window-3 scheme swapped branches, a stale
+order or a wrong count; for the envelope bound a missing side, the wrong
+envelope side or a missing square root; for the banded warping distance a
+missing diagonal step or a band one too wide), compiles the copy with gcc
+into a temporary library, and runs pin checks against it: a compact set
+here and, for the later functions, the pins of ``test_oracle`` themselves.
 At least one pin must fail for every mutant.  The real oracle is untouched.
 """
 import contextlib
@@ -33,23 +38,38 @@ MUTANTS = {
                              "int64_t e = i + r > n - 1 ? n - 1 : i + r - 1;"),
     "bf2d_short_rows": ("for (int64_t dy = 0; dy < wy; ++dy)",
                         "for (int64_t dy = 0; dy < wy - 1; ++dy)"),
+    "argbf1d_rightmost": ("if (a[k] > a[bx]) bx = k;", "if (a[k] >= a[bx]) bx = k;"),
+    "argbf1d_short_window": ("for (int64_t k = j + 1; k < j + w; ++k) {",
+                             "for (int64_t k = j + 1; k < j + w - 1; ++k) {"),
+    "w3_branches_swapped": ("if (older_greater) {", "if (!older_greater) {"),
+    "w3_stale_order": ("older_greater = prev_gt;", "older_greater = older_gt;"),
+    "w3_count": ("c += 2;", "c += 3;"),
+    "lb_no_lower_side": ("else if (qi < (double)lw)", "else if (0 && qi < (double)lw)"),
+    "lb_wrong_envelope_side": ("if (qi > (double)hi) sum += (qi - (double)hi) * (qi - (double)hi);",
+                               "if (qi > (double)lw) sum += (qi - (double)lw) * (qi - (double)lw);"),
+    "lb_no_sqrt": ("*out = sqrt(sum);", "*out = sum;"),
+    "dtw_no_diagonal": ("if (i > 0 && j > 0 && D[(i - 1) * n + j - 1] < best)",
+                        "if (0 && i > 0 && j > 0 && D[(i - 1) * n + j - 1] < best)"),
+    "dtw_band_too_wide": ("if (i - j > r || j - i > r)", "if (i - j > r + 1 || j - i > r + 1)"),
 }
+
+FUNCS = ("bf1d", "bf1d_at", "wedge", "envelope", "bf2d", "bf2d_at", "argbf1d", "w3", "lb_keogh", "dtw_band")
 
 
 @contextlib.contextmanager
 def _mutant_lib(find, repl):
     src = open(SRC).read()
     assert find in src, find
-    mutated = src.replace(find, repl, 1)
+    mutated = src.replace(find, repl, 1)  # the first occurrence
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "m.c")
         so = os.path.join(d, "m.so")
         open(c, "w").write(mutated)
-        subprocess.check_call(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", "-w", "-o", so, c])
+        subprocess.check_call(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", "-w", "-o", so, c, "-lm"])
         real = oracle._load()
         lib = ctypes.CDLL(so)
         for suf in ("f32", "f64", "i16", "u8"):
-            for fn in ("bf1d", "bf1d_at", "wedge", "envelope", "bf2d", "bf2d_at"):
+            for fn in FUNCS:
                 f = getattr(lib, f"oracle_{fn}_{suf}")
                 g = getattr(real, f"oracle_{fn}_{suf}")
                 f.argtypes, f.restype = g.argtypes, g.restype
@@ -98,12 +118,30 @@ def _pins_hold() -> bool:
     return True
 
 
+def _paper_pins_hold() -> bool:
+    """The pins of test_oracle for the arg filter, the window-3 scheme, the
+    envelope bound and the banded warping distance."""
+    import test_oracle as t
+    try:
+        for dt in (np.float32, np.uint8):
+            t.test_argbf1d_leftmost_extreme(dt)
+            t.test_w3_two_comparisons_per_element(dt)
+        t.test_lb_keogh_worked_example()
+        t.test_lb_keogh_radius_zero_is_euclidean(np.float64)
+        t.test_lb_keogh_below_banded_dtw(np.float64)
+        t.test_lb_keogh_is_monotone_in_radius()
+    except (ValueError, AssertionError):
+        return False
+    return True
+
+
 def test_real_oracle_passes_compact_pins():
     assert _pins_hold()
+    assert _paper_pins_hold()
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_mutant_is_caught(name):
     find, repl = MUTANTS[name]
     with _mutant_lib(find, repl):
-        assert not _pins_hold(), f"planted mistake {name} went unnoticed"
+        assert not (_pins_hold() and _paper_pins_hold()), f"planted mistake {name} went unnoticed"
