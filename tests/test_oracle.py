@@ -395,3 +395,95 @@ def test_argbf1d_leftmost_extreme(dtype):
     c = np.full(50, 7, dtype)
     imx, imn = oracle.argbf1d(c, 5)
     assert np.array_equal(imx, np.arange(46)) and np.array_equal(imn, np.arange(46))
+
+
+EXHAUSTIVE_C = r"""
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+typedef struct { int64_t ncmp, max_size, stale_fronts, steps; } orc_wedge_stats;
+int oracle_bf1d_f64(const double *, int64_t, int64_t, double *, double *);
+int oracle_wedge_f64(const double *, int64_t, int64_t, double *, double *, orc_wedge_stats *);
+int oracle_argbf1d_f64(const double *, int64_t, int64_t, int64_t *, int64_t *);
+int oracle_w3_f64(const double *, int64_t, double *, double *, int64_t *);
+
+static long checked = 0;
+static int check(const double *a, int n) {
+    double bm[16], bn[16], wm[16], wn[16], tm[16], tn[16];
+    int64_t im[16], in[16], c;
+    for (int w = 1; w <= n; ++w) {
+        orc_wedge_stats st;
+        if (oracle_bf1d_f64(a, n, w, bm, bn) || oracle_wedge_f64(a, n, w, wm, wn, &st) ||
+            oracle_argbf1d_f64(a, n, w, im, in)) return 1;
+        for (int j = 0; j + w <= n; ++j) {
+            if (wm[j] != bm[j] || wn[j] != bn[j]) return 2;
+            if (im[j] < j || im[j] >= j + w || a[im[j]] != bm[j]) return 3;
+            if (in[j] < j || in[j] >= j + w || a[in[j]] != bn[j]) return 3;
+            for (int k = j; k < im[j]; ++k) if (a[k] == bm[j]) return 4;  /* leftmost */
+            for (int k = j; k < in[j]; ++k) if (a[k] == bn[j]) return 4;
+        }
+        if (st.ncmp > 3 * n || st.max_size > w + 1 || st.stale_fronts != 0) return 5;
+        ++checked;
+    }
+    if (n >= 3) {
+        if (oracle_w3_f64(a, n, tm, tn, &c) || c != 2 * n - 3) return 6;
+        oracle_bf1d_f64(a, n, 3, bm, bn);
+        for (int j = 0; j + 3 <= n; ++j) if (tm[j] != bm[j] || tn[j] != bn[j]) return 7;
+    }
+    return 0;
+}
+
+int main(void) {
+    double a[16];
+    for (int n = 1; n <= 8; ++n) {       /* every permutation of 0..n-1 */
+        int p[16];
+        for (int i = 0; i < n; ++i) p[i] = i;
+        for (;;) {
+            for (int i = 0; i < n; ++i) a[i] = p[i];
+            int r = check(a, n);
+            if (r) { printf("perm fail %d n=%d\n", r, n); return r; }
+            int i = n - 2;
+            while (i >= 0 && p[i] > p[i + 1]) --i;
+            if (i < 0) break;
+            int j = n - 1;
+            while (p[j] < p[i]) --j;
+            int t = p[i]; p[i] = p[j]; p[j] = t;
+            for (int l = i + 1, h = n - 1; l < h; ++l, --h) { t = p[l]; p[l] = p[h]; p[h] = t; }
+        }
+    }
+    for (int n = 1; n <= 10; ++n) {      /* every array over {0, 1, 2} */
+        long total = 1;
+        for (int i = 0; i < n; ++i) total *= 3;
+        for (long c = 0; c < total; ++c) {
+            long v = c;
+            for (int i = 0; i < n; ++i) { a[i] = (double)(v % 3); v /= 3; }
+            int r = check(a, n);
+            if (r) { printf("ternary fail %d n=%d\n", r, n); return r; }
+        }
+    }
+    printf("ok %ld\n", checked);
+    return 0;
+}
+"""
+
+
+def test_exhaustive_permutations_8_and_ternary_10_in_c(tmp_path):
+    """Every permutation of up to 8 elements and every array of up to 10
+    elements over {0, 1, 2}, every window: Algorithm 1 equals the definition
+    with <= 3n comparisons (Prop. 2), size(U)+size(L) <= w+1 (Prop. 4) and no
+    step with both fronts stale; the arg filter's positions hold the extremes
+    and are the leftmost; the window-3 scheme equals the definition in
+    exactly 2n-3 comparisons.  Run as a C program over the oracle's source
+    (the sizes are too many calls for Python)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    drv = tmp_path / "exhaustive.c"
+    drv.write_text(EXHAUSTIVE_C)
+    exe = tmp_path / "exhaustive"
+    src = os.path.join(os.path.dirname(oracle.__file__), "mmf_oracle.c")
+    subprocess.run(["gcc", "-O2", "-std=c99", str(drv), src, "-lm", "-o", str(exe)], check=True,
+                   capture_output=True, text=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0 and out.stdout.startswith("ok"), out.stdout + out.stderr
