@@ -213,8 +213,10 @@ def test_device_status_clean(mmf):
 @pytest.mark.parametrize("w", [3, 31, 1001, 65537])
 def test_full_size_long_stream_sampled(mmf, w):
     """n = 2^30 fp32 (the long-stream workload), same launch as the bench:
-    sampled windows against the definition, plus the bracketing property
-    max >= min on every output."""
+    sampled windows against the definition (a million random starts for
+    small windows, about 2e9 / w for large ones, plus the ends and a stride
+    through every CTA's range), plus the bracketing property max >= min on
+    every output."""
     n = 1 << 30
     x = synth.torch_by_name("random_walk", n, seed=22, device="cuda")
     mx, mn = mmf.filter1d(x, w)
@@ -222,7 +224,7 @@ def test_full_size_long_stream_sampled(mmf, w):
     m = n - w + 1
     assert bool((mx >= mn).all())
     rng = np.random.default_rng(w)
-    starts = np.concatenate([rng.integers(0, m, size=3000), [0, 1, m - 1, m - 2],
+    starts = np.concatenate([rng.integers(0, m, size=min(1_000_000, 2_000_000_000 // w)), [0, 1, m - 1, m - 2],
                              np.arange(0, m, 4096 * 152 * 7)[:400]]).astype(np.int64)
     a = x.cpu().numpy()
     emx, emn = oracle.bf1d_at(a, w, starts)
