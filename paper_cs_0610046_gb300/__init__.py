@@ -292,6 +292,11 @@ class BatchPlan:
         check(self._lib.mmf_batch_plan_out_offsets(self._h, off.ctypes.data_as(_P64)))
         return off
 
+    def _check_input(self, x):
+        _check_tensor(x, "x")
+        if x.dtype != self.dtype or x.numel() < self.in_len:
+            raise ValueError(f"input must hold {self.in_len} elements of {self.dtype}")
+
     def _outs(self, x, out_max, out_min):
         # Zero-filled: the padding between series (outputs start on 32-byte
         # boundaries) is never written and reads as 0.
@@ -299,12 +304,14 @@ class BatchPlan:
             out_max = torch.zeros(self.out_len, dtype=x.dtype, device=x.device)
         if out_min is None:
             out_min = torch.zeros(self.out_len, dtype=x.dtype, device=x.device)
+        for o, nm in ((out_max, "out_max"), (out_min, "out_min")):
+            _check_tensor(o, nm)
+            if o.dtype != x.dtype or o.numel() < self.out_len:
+                raise ValueError(f"{nm} must hold {self.out_len} elements of {x.dtype}")
         return out_max, out_min
 
     def __call__(self, x, out_max=None, out_min=None, stream=None):
-        _check_tensor(x, "x")
-        if x.dtype != self.dtype or x.numel() < self.in_len:
-            raise ValueError(f"input must hold {self.in_len} elements of {self.dtype}")
+        self._check_input(x)
         out_max, out_min = self._outs(x, out_max, out_min)
         with torch.cuda.device(x.device):
             check(self._lib.mmf_filter1d_batched(self._h, _ptr(x), _ptr(out_max), _ptr(out_min),
@@ -313,6 +320,7 @@ class BatchPlan:
 
     def per_series(self, x, out_max=None, out_min=None, stream=None):
         """The plain form: one mmf_filter1d launch per series."""
+        self._check_input(x)
         out_max, out_min = self._outs(x, out_max, out_min)
         with torch.cuda.device(x.device):
             check(self._lib.mmf_filter1d_per_series(self._h, _ptr(x), _ptr(out_max), _ptr(out_min),
@@ -329,14 +337,16 @@ class BatchPlan:
             raise ValueError(f"x and query must be {self.dtype}")
         if out is None:
             out = torch.empty(self.nseries, dtype=torch.float64, device=x.device)
-        elif out.dtype != torch.float64 or out.numel() < self.nseries:
-            raise ValueError(f"out must hold {self.nseries} float64 values")
+        elif not (isinstance(out, torch.Tensor) and out.is_cuda and out.is_contiguous()) or \
+                out.dtype != torch.float64 or out.numel() < self.nseries:
+            raise ValueError(f"out must be a contiguous CUDA tensor of {self.nseries} float64 values")
         with torch.cuda.device(x.device):
             check(self._lib.mmf_lb_keogh_batched(self._h, _ptr(x), _ptr(query), query.numel(), _ptr(out),
                                                  _VP(_stream_handle(stream))))
         return out
 
     def autotune(self, x, out_max=None, out_min=None, stream=None):
+        self._check_input(x)
         out_max, out_min = self._outs(x, out_max, out_min)
         with torch.cuda.device(x.device):
             check(self._lib.mmf_batch_plan_autotune(self._h, _ptr(x), _ptr(out_max), _ptr(out_min),

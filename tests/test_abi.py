@@ -154,3 +154,18 @@ int main(void) {
     subprocess.run(cmd, check=True, capture_output=True, text=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0 and out.stdout.strip() == "ok", (out.returncode, out.stdout, out.stderr)
+
+
+def test_binding_refuses_host_tensors_for_device_calls():
+    """The device entry points take CUDA tensors only: a CPU tensor is refused
+    before any library call (there is no CPU fallback to fall into)."""
+    import torch
+    import paper_cs_0610046_gb300 as mmf
+    x = torch.arange(100, dtype=torch.float32)
+    for call in (lambda: mmf.filter1d(x, 3), lambda: mmf.filter1d(x, 3, mode="envelope"),
+                 lambda: mmf.argfilter1d(x, 3), lambda: mmf.filter1d_w3(x),
+                 lambda: mmf.filter2d(x.reshape(10, 10), 3, 3)):
+        with pytest.raises(TypeError):
+            call()
+    with pytest.raises(TypeError):
+        mmf.filter1d(torch.arange(100, dtype=torch.int32), 3)  # an unsupported type as well
