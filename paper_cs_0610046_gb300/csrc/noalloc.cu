@@ -1,20 +1,26 @@
-// Batched filter for callers that must not allocate.
+// Batched filter for callers that must not allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while other work holds a
-// fixed device-memory budget (a serving process that reserved its pool up
-// front), real-time or signal-driven paths where an allocation could block or
-// fail, and host callbacks where allocation APIs are not allowed.  This entry
-// point runs the batched kernel with its work tables (series, work items and
-// ticket counters) in a file-scope device array of fixed size instead of
+// Some callers cannot call cudaMalloc: a process that reserved its whole
+// device-memory budget up front (a fixed pool shared by its components), or a
+// latency-bound path on an ordinary host thread where an allocation could
+// block on the driver or fail under memory pressure.  This entry point runs
+// the batched kernel with its work tables (series, work items and ticket
+// counters) in a file-scope device array of fixed size instead of
 // plan-owned allocations.  The caller still passes the input and output
 // buffers.  Each device that loads the library holds this array until the
 // process exits.
+//
+// The tables are built on the host in a static staging image and reach the
+// device as the arguments of small copy kernels (at most about 30 KB each),
+// so no host memory is read by the GPU after the call returns and no large
+// array lives on the caller's stack.
 //
 // The array is shared by every call: a call overwrites the tables left by the
 // previous one and clears the ticket counters itself.  Calls whose kernels
 // overlap on the GPU (from two host threads, or on two streams without
 // ordering between them) race on the tables and give wrong results; order
 // them on one stream.
+#include <cstddef>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -37,6 +43,7 @@ namespace {
 
 constexpr int kGroups = 4;
 constexpr int64_t kMaxItems = MMF_NOALLOC_MAX_ITEMS;
+constexpr int kMaxDevices = 64;  // the same bound as the library's device cache (get_ctx)
 
 struct NoAllocTables {
     int tickets[kGroups];
@@ -44,6 +51,7 @@ struct NoAllocTables {
     SeriesDesc series[MMF_NOALLOC_MAX_SERIES];
     ItemDesc items[kMaxItems];
 };
+static_assert(offsetof(NoAllocTables, series) == 256, "tables start after the counters");
 
 // The work tables.  In host code this name is a stand-in, not a device
 // address: its address is taken with cudaGetSymbolAddress per device.
@@ -53,8 +61,46 @@ struct DevAddr {
     bool ready = false;
     NoAllocTables *ptr = nullptr;
 };
-static DevAddr g_noalloc_addr[64];
-static std::mutex g_noalloc_mu;  // guards the per-device set-up above
+static DevAddr g_noalloc_addr[kMaxDevices];
+
+// Host staging: the image of the tables a call uploads, and the argument
+// block of one copy kernel.  Both are static (no stack arrays, no heap) and
+// guarded by g_noalloc_mu for the whole call.
+constexpr uint32_t kChunk = 30 * 1024;  // payload bytes per copy kernel (kernel arguments <= 32764 bytes)
+struct alignas(16) TableChunk {
+    uint32_t off;    // byte offset in the device tables (a multiple of 8)
+    uint32_t bytes;  // payload bytes, a multiple of 8
+    uint32_t pad[2];
+    uint8_t data[kChunk];
+};
+static_assert(sizeof(TableChunk) <= 32764, "one copy kernel's arguments");
+static NoAllocTables g_img;
+static TableChunk g_chunk;
+static std::mutex g_noalloc_mu;
+
+// Copies one chunk of table bytes from the kernel's arguments into the device
+// tables (one CTA; the arguments are read in place).
+__global__ void noalloc_upload_kernel(const __grid_constant__ TableChunk c, uint8_t *tables) {
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(c.data);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(tables + c.off);
+    for (uint32_t i = threadIdx.x; i < c.bytes / 4; i += blockDim.x) dst[i] = src[i];
+}
+
+// Uploads bytes [off, off + bytes) of the staging image on stream cs.
+cudaError_t upload(uint8_t *d_tables, uint32_t off, uint32_t bytes, cudaStream_t cs) {
+    const uint8_t *img = reinterpret_cast<const uint8_t *>(&g_img);
+    for (uint32_t done = 0; done < bytes; done += kChunk) {
+        const uint32_t b = bytes - done < kChunk ? bytes - done : kChunk;
+        g_chunk.off = off + done;
+        g_chunk.bytes = (b + 7) & ~7u;
+        std::memcpy(g_chunk.data, img + off + done, g_chunk.bytes);
+        void *args[] = {&g_chunk, &d_tables};
+        // The arguments are copied at launch: g_chunk is free again on return.
+        cudaError_t e = cudaLaunchKernel((const void *)noalloc_upload_kernel, dim3(1), dim3(256), args, 0, cs);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
 
 int mode_of(mmf_dtype dt, int64_t w) {
     switch (dt) {
@@ -70,6 +116,7 @@ int mode_of(mmf_dtype dt, int64_t w) {
 extern "C" mmf_status mmf_filter1d_batched_noalloc(const void *d_in, const int64_t *h_len, const int64_t *h_w,
                                                    int64_t nseries, mmf_dtype dtype, mmf_mode mode, void *d_max,
                                                    void *d_min, void *stream) {
+    NvtxRange nvtx_range("mmf_filter1d_batched_noalloc");
     if (nseries < 0 || (nseries > 0 && (!h_len || !h_w))) return set_error(MMF_EINVAL, "bad series description");
     if (nseries > MMF_NOALLOC_MAX_SERIES)
         return set_error(MMF_EINVAL, "%lld series exceed the no-allocation limit of %d", (long long)nseries,
@@ -77,15 +124,20 @@ extern "C" mmf_status mmf_filter1d_batched_noalloc(const void *d_in, const int64
     const int esz = elem_size(dtype);
     if (esz == 0) return set_error(MMF_EINVAL, "unknown dtype %d", (int)dtype);
 
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
     // Series table (inputs packed in order; outputs in order, each series
     // starting on a 32-byte boundary as in a batch plan) and output length.
-    SeriesDesc series[MMF_NOALLOC_MAX_SERIES];
+    SeriesDesc *series = g_img.series;
     int64_t in_pos = 0, out_pos = 0, tiles = 0;
     const int64_t T = tile_of(dtype);
     for (int64_t s = 0; s < nseries; ++s) {
         SeriesDesc sd;
         mmf_status st = make_series(h_len[s], h_w[s], mode, dtype, &sd);
         if (st != MMF_OK) return st;
+        // Positions stay far below 2^63: the input ends (and the outputs,
+        // at most n per series plus 32 bytes of padding) cannot wrap.
+        if (sd.n > INT64_MAX / 2 - in_pos || sd.n_out > INT64_MAX / 2 - out_pos - 32)
+            return set_error(MMF_EINVAL, "series lengths overflow 64-bit positions");
         sd.in_off = in_pos;
         sd.out_off = batch_out_start(out_pos, esz);
         in_pos += sd.n;
@@ -102,7 +154,7 @@ extern "C" mmf_status mmf_filter1d_batched_noalloc(const void *d_in, const int64
     // seg grows with the total so that the items always fit the table.
     int64_t seg = 16;
     while (tiles / seg + nseries > kMaxItems) seg *= 2;
-    ItemDesc items[kMaxItems];
+    ItemDesc *items = g_img.items;
     int64_t group_begin[kGroups + 1];
     int64_t ni = 0;
     for (int g = 0; g < kGroups; ++g) {
@@ -117,32 +169,32 @@ extern "C" mmf_status mmf_filter1d_batched_noalloc(const void *d_in, const int64
         }
     }
     group_begin[kGroups] = ni;
+    std::memset(g_img.tickets, 0, sizeof(g_img.tickets) + sizeof(g_img.pad));
 
     LaunchCtx ctx;
-    mmf_status st = get_ctx(stream, &ctx);
+    mmf_status st = get_ctx(stream, &ctx);  // refuses device ordinals >= kMaxDevices
     if (st != MMF_OK) return st;
+    if (ctx.device < 0 || ctx.device >= kMaxDevices)
+        return set_error(MMF_EINVAL, "device ordinal %d out of range", ctx.device);
     // Set-up once per device, with that device current: the device address of
     // the table array.  (The first call on a device does this; make it before
-    // any stream capture.)  It is done under a lock, so that a thread which
-    // finds the set-up done also sees the address (on a weakly ordered CPU a
-    // thread could otherwise see the flag before the pointer).
-    NoAllocTables *tab = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        DevAddr &da = g_noalloc_addr[ctx.device];
-        if (!da.ready) {
-            void *p = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc);
-            if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(no-allocation tables)");
-            da.ptr = static_cast<NoAllocTables *>(p);
-            da.ready = true;
-        }
-        tab = da.ptr;
+    // any stream capture.)  It runs under the call's lock, so a thread that
+    // finds the set-up done also sees the address.
+    DevAddr &da = g_noalloc_addr[ctx.device];
+    if (!da.ready) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc);
+        if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(no-allocation tables)");
+        da.ptr = static_cast<NoAllocTables *>(p);
+        da.ready = true;
     }
+    NoAllocTables *tab = da.ptr;
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaMemcpyAsync(tab->series, series, nseries * sizeof(SeriesDesc), cudaMemcpyHostToDevice, cs);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(tab->items, items, ni * sizeof(ItemDesc), cudaMemcpyHostToDevice, cs);
-    if (e == cudaSuccess) e = cudaMemsetAsync(tab->tickets, 0, sizeof(tab->tickets), cs);
+    uint8_t *d_tab = reinterpret_cast<uint8_t *>(tab);
+    // Counters and series (contiguous from the start), then the items.
+    cudaError_t e = upload(d_tab, 0, (uint32_t)(offsetof(NoAllocTables, series) + nseries * sizeof(SeriesDesc)), cs);
+    if (e == cudaSuccess && ni > 0)
+        e = upload(d_tab, (uint32_t)offsetof(NoAllocTables, items), (uint32_t)(ni * sizeof(ItemDesc)), cs);
     if (e != cudaSuccess) return cuda_error(e, "upload no-allocation tables");
     for (int g = 0; g < kGroups; ++g) {
         const int64_t n_items = group_begin[g + 1] - group_begin[g];
