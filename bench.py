@@ -257,7 +257,7 @@ def batched_extras(dev, stream, peak, reps=5, envelope_series=1_000_000):
             "series": 4096, "elements": total, "batched_ms": bms, "per_series_ms": pms,
             "batched_over_per_series": pms / bms, "batched_Gelem_s": total / bms / 1e6,
             "batched_GBps": byts / bms / 1e6, "frac": byts / bms / 1e6 / peak,
-            "segments": plan.segments(), "items_per_group": plan.items_per_group}
+            "tuned": plan.knobs(), "items_per_group": plan.items_per_group}
         plan.close()
         del x, om, on
     torch.cuda.empty_cache()
@@ -288,7 +288,7 @@ def envelope_extras(dev, stream, peak, reps=5, envelope_series=1_000_000):
     out["envelope_f32"] = {
         "series": ns, "length": L, "radius": r, "batched_ms": bms, "per_series_ms": pms,
         "batched_over_per_series": pms / bms, "batched_Gelem_s": ns * L / bms / 1e6,
-        "batched_GBps": byts / bms / 1e6, "frac": byts / bms / 1e6 / peak, "segments": plan.segments()}
+        "batched_GBps": byts / bms / 1e6, "frac": byts / bms / 1e6 / peak, "tuned": plan.knobs()}
     # The envelope lower bound of the time-warping distance against one query
     # (same series and radius): the envelope feeds a per-series sum in the
     # kernel and is never stored.  Bytes: the series once, the query, one
@@ -733,6 +733,24 @@ def main():
     if not args.no_cpu and rank == 0 and ws == 1:
         cpu = cpu_baseline(args.cpu_sample)
 
+    # The workload's own targets, carried in the line: the whole step's share
+    # of HBM bandwidth on the long stream, batched over per-series launches on
+    # the uneven and envelope batches, and serving p99 near half saturation.
+    step_bytes = sum(4.0 * n + 8.0 * (n - w + 1) for w in WINDOWS) * len(DISTS) * ws
+    step_gbps = step_bytes / (elapsed_ms / args.steps * 1e-3) / 1e9
+    targets = {"long_stream_step": {"GBps": step_gbps, "frac": step_gbps / peak, "frac_of_8TBps": step_gbps / 8000.0,
+                                    "target_frac_of_8TBps": 0.70}}
+    b = extras.get("batched") or {}
+    if b:
+        targets["batched_over_per_series"] = {k: b[k]["batched_over_per_series"]
+                                              for k in ("uneven_f32", "uneven_f64", "envelope_f32") if k in b}
+        targets["batched_over_per_series"]["target"] = 3.0
+    sv = extras.get("serving") or {}
+    if sv:
+        targets["serving"] = {"p99_ms": sv["headline"]["p99_ms"], "p50_ms": sv["headline"]["p50_ms"],
+                              "load_Gelem_s": sv["headline"]["load_Gelem_s"],
+                              "saturation_Gelem_s": sv["saturation_Gelem_s"]}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "Gelem/s", "n_gpus": ws, "steps": args.steps,
@@ -745,6 +763,8 @@ def main():
             "roofline": roofline, "per_window": breakdown, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": len(launch_events), "clocks": clocks, "device_status": status,
             **extras,
+            # last, so that a record which keeps only the end of the line keeps it
+            "targets": targets,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
