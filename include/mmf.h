@@ -63,8 +63,12 @@ typedef enum {
                                  (Section 2 related work; Table 1 row 2)    */
     MMF_KERNEL_SLIDE = 2,     /* register slide: naive windows of Table 1
                                  row 1, for small w                         */
-    MMF_KERNEL_WEDGE = 3      /* chunked monotonic wedge, Algorithm 1 of
+    MMF_KERNEL_WEDGE = 3,     /* chunked monotonic wedge, Algorithm 1 of
                                  Section 4 per chunk with a w-1 halo        */
+    MMF_KERNEL_FRONT = 4      /* the block scan of windows of a tile or more
+                                 (w - 1 >= 2048 for f32, 4096 for i16/u8;
+                                 not f64) with every CTA on one advancing
+                                 front of output tiles                      */
 } mmf_kernel;
 
 /* Largest window handled: (w - 1) / tile <= MMF_MAX_WINDOW_TILES, where the
@@ -82,7 +86,9 @@ typedef enum {
  *   d_max   output, n-w+1 (VALID, 0 if w > n) or n (CENTERED_CLIPPED)
  *           elements; NULL skips the max side
  *   d_min   same for the min side; NULL skips it (not both NULL)
- * Outputs must not overlap the input.  Allocates nothing.
+ * Outputs must not overlap the input.  Allocates nothing (unless a tuned
+ * dispatch entry selects MMF_KERNEL_FRONT, whose small workspace comes from
+ * the stream-ordered allocator).
  * Returns MMF_OK without touching memory when there are no outputs (w > n or
  * n == 0; pointers may then be NULL).  Otherwise returns MMF_EINVAL for
  * w < 1, r < 0, n < 0, both outputs NULL, a NULL input, or pointers not
@@ -111,10 +117,41 @@ mmf_status mmf_filter1d_host(const void *h_in, int64_t n, int64_t w_or_r, mmf_dt
  * autotuner).  MMF_KERNEL_SLIDE requires w <= 17 for f32, w <= 9 otherwise;
  * MMF_KERNEL_WEDGE computes
  * MMF_VALID windows with w <= MMF_WEDGE_MAX_WINDOW (MMF_EINVAL /
- * MMF_ENOTIMPL otherwise). */
+ * MMF_ENOTIMPL otherwise).  MMF_KERNEL_BLOCKSCAN gives each CTA its own range
+ * of outputs.  MMF_KERNEL_FRONT (windows of a tile or more, not f64, else
+ * MMF_ENOTIMPL) hands output tiles to CTAs in order from a ticket: each tile
+ * is read as the end of some windows and, about w elements later, as the
+ * start of others while it is still in L2, and the aggregates of the whole
+ * tiles inside a window come from the CTAs that read them (published in a
+ * stream-ordered workspace of about 12 bytes per 2048 f32 inputs, taken from
+ * and returned to the stream-ordered allocator on `stream`; MMF_ECUDA if that
+ * allocation fails).  It runs as a cooperative launch.  The built-in
+ * automatic choice does not take it (on the long-stream workload it is
+ * slower than the per-range schedule). */
 mmf_status mmf_filter1d_ex(const void *d_in, int64_t n, int64_t w_or_r, mmf_dtype dtype,
                            mmf_mode mode, void *d_max, void *d_min, void *stream,
                            mmf_kernel kernel);
+
+/* The dispatch table of MMF_KERNEL_AUTO.  Without an entry, AUTO takes the
+ * built-in rule (the register slide for w <= 17 for f32 and w <= 9 for the
+ * other types, MMF_KERNEL_BLOCKSCAN otherwise).  An entry for a
+ * bucket of (dtype, w, n) replaces it wherever its kernel can take the call
+ * (windows: exact up to 32, then powers of two; lengths: powers of four).
+ * The table is process-wide and thread-safe.
+ *
+ * mmf_dispatch_set -- sets the entry of the bucket of (n, w) to `kernel`
+ *   (MMF_KERNEL_AUTO removes it).  MMF_EINVAL for bad sizes or kernels.
+ * mmf_dispatch_get -- the kernel AUTO takes for valid windows of w over n
+ *   elements (the entry, else the built-in rule).
+ * mmf_dispatch_autotune -- times every kernel that can take valid windows of
+ *   w over the n elements of d_in (writing d_max/d_min, n-w+1 each) on
+ *   `stream`, which it synchronises; stores the fastest in the table (and in
+ *   $MMF_AUTOTUNE_CACHE, keyed by GPU name, when that is set; later processes
+ *   read it back) and writes it to *chosen (may be NULL). */
+mmf_status mmf_dispatch_set(mmf_dtype dtype, int64_t n, int64_t w, mmf_kernel kernel);
+mmf_status mmf_dispatch_get(mmf_dtype dtype, int64_t n, int64_t w, mmf_kernel *kernel);
+mmf_status mmf_dispatch_autotune(const void *d_in, int64_t n, int64_t w, mmf_dtype dtype, void *d_max, void *d_min,
+                                 void *stream, mmf_kernel *chosen);
 
 /* Arg-max / arg-min filter (Section 5: the streaming algorithm stores the
  * locations of the extremes, so their positions come at no extra cost):
@@ -220,14 +257,25 @@ mmf_status mmf_batch_plan_out_offsets(const mmf_batch_plan *plan, int64_t *h_off
  * be NULL), the work items per kernel group (0-2 block scans, 3 slide). */
 mmf_status mmf_batch_plan_sizes(const mmf_batch_plan *plan, int64_t *in_len, int64_t *out_len, int64_t *n_items);
 
+/* Tuning knobs of a plan beside the segment lengths: series of at most
+ * short_cut elements (0 .. 1024 for 1-4 byte types, 512 for f64; 0: none)
+ * take the warp-per-series kernel (one warp per series) instead of
+ * block-scan work items (a whole CTA per item); windows of at most slide_max
+ * (1: none; at most 17 for f32, 9 otherwise) take the register slide instead
+ * of block scans.  MMF_EINVAL outside those ranges. */
+mmf_status mmf_batch_plan_set_knobs(mmf_batch_plan *plan, int64_t short_cut, int slide_max);
+mmf_status mmf_batch_plan_get_knobs(const mmf_batch_plan *plan, int64_t *short_cut, int *slide_max);
+
 /* Output tiles per work item of one kernel group (tuning knob). */
 mmf_status mmf_batch_plan_set_segment(mmf_batch_plan *plan, int group, int seg_tiles);
 mmf_status mmf_batch_plan_get_segment(const mmf_batch_plan *plan, int group, int *seg_tiles);
 
-/* Times candidate segment lengths on the given buffers (synchronises the
- * stream) and keeps the fastest per group; with $MMF_AUTOTUNE_CACHE set, the
- * choice is appended to that file, keyed by GPU name and workload shape, and
- * reused by later plans. */
+/* Tunes the plan on the given buffers (synchronises the stream): first the
+ * short-series cut-off (threads per series), then the slide limit (kernel
+ * choice for small windows), each timed over the whole plan, then the
+ * segment length of each block-scan group; keeps the fastest of each.  With
+ * $MMF_AUTOTUNE_CACHE set, the choices are appended to that file, keyed by
+ * GPU name and workload shape, and reused by later plans. */
 mmf_status mmf_batch_plan_autotune(mmf_batch_plan *plan, const void *d_in, void *d_max, void *d_min,
                                    void *stream);
 
@@ -378,26 +426,30 @@ mmf_status mmf_server_stats(mmf_server *server, int reset, mmf_server_stats_t *o
 #define MMF_NOALLOC_MAX_SERIES 512
 #define MMF_NOALLOC_MAX_ITEMS 2048
 
-/* The batched filter for callers that must not allocate device memory (a
- * process that reserved a fixed device-memory pool up front, a real-time path
- * where an allocation may block or fail, a host callback where allocation
- * APIs are not allowed).  The paper has no counterpart to this entry point;
- * it is an interface convenience.
+/* The batched filter for callers that must not allocate device memory: a
+ * process that reserved its whole device-memory budget up front (a fixed
+ * pool shared by its components), or a latency-bound path on an ordinary
+ * host thread where an allocation may block on the driver or fail under
+ * memory pressure.  The paper has no counterpart to this entry point; it is
+ * an interface convenience.
  *
  * Same results as a batch plan over the same series (inputs packed back to
  * back in d_in, outputs in d_max/d_min in series order at the offsets a plan
- * reports, each series on a 32-byte boundary), but it
- * calls no cudaMalloc/cudaFree: its work tables live in one fixed device array
- * of about 70 KB that every GPU which loads the library keeps until the
- * process exits.  At most MMF_NOALLOC_MAX_SERIES series; long series are
- * split into at most MMF_NOALLOC_MAX_ITEMS work items.  Larger requests
- * return MMF_EINVAL.
+ * reports, each series on a 32-byte boundary), but it calls no
+ * cudaMalloc/cudaFree: its work tables live in one fixed device array of
+ * about 74 KB that every GPU which loads the library keeps until the process
+ * exits.  The tables are built in static host memory and passed to the GPU
+ * as kernel arguments, so the GPU reads no host memory after the call
+ * returns.  At most MMF_NOALLOC_MAX_SERIES series; long series are split into
+ * at most MMF_NOALLOC_MAX_ITEMS work items.  Larger requests, and lengths
+ * whose sum would overflow 64-bit positions, return MMF_EINVAL.
  *
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
  * capture.  Every call reuses the same array and clears its counters itself;
- * calls that overlap on the GPU (two host threads, or two unordered streams)
- * race on it and give wrong results. */
+ * calls are serialised on the host, but calls that overlap on the GPU (two
+ * unordered streams) race on the array and give wrong results: order them on
+ * one stream. */
 mmf_status mmf_filter1d_batched_noalloc(const void *d_in, const int64_t *h_len, const int64_t *h_w,
                                         int64_t nseries, mmf_dtype dtype, mmf_mode mode, void *d_max,
                                         void *d_min, void *stream);
@@ -408,6 +460,18 @@ mmf_status mmf_filter1d_batched_noalloc(const void *d_in, const int64_t *h_len, 
  * when a bounded wait runs out (bit 0: pipeline wait timeout).  Synchronises
  * the current device.  Returns MMF_OK and writes the word to *out. */
 mmf_status mmf_device_status(uint32_t *out, int reset);
+
+/* Test hook for the device-side timeout path of the block-scan kernels (the
+ * 1D, batched, 2D row and serving launches).  With starve_copies != 0, the
+ * kernels launched afterwards by this process issue none of their input
+ * copies, so every pipeline wait runs out after wait_limit_cycles SM clocks
+ * (1000 .. 2e9; about 0.5 ns each): the kernel records bit 0 in the device
+ * status word, each warp finishes its current work item without waiting
+ * again, and all warps of each CTA leave together at the item's end.  The
+ * outputs of such a call are unspecified; nothing faults, nothing is left in
+ * flight and the context stays usable.  starve_copies == 0 restores normal
+ * operation.  For tests only. */
+mmf_status mmf_test_set_wait_fault(int starve_copies, int64_t wait_limit_cycles);
 
 /* Thread-local, NUL-terminated description of the last failure. */
 const char *mmf_last_error(void);

@@ -18,7 +18,7 @@ import threading
 import torch
 
 __all__ = ["MMFError", "load", "filter1d", "filter1d_host", "filter1d_w3", "argfilter1d", "output_length",
-           "device_status", "BatchPlan", "filter2d", "Server", "n_outputs", "DTYPES", "KERNELS"]
+           "device_status", "set_wait_fault", "dispatch_set", "dispatch_get", "dispatch_autotune", "BatchPlan", "filter2d", "Server", "n_outputs", "DTYPES", "KERNELS"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmmf.so")
@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "MMF_OK", 1: "MMF_EINVAL", 2: "MMF_ENOMEM", 3: "MMF_ECUDA", 4
                 5: "MMF_ETIMEOUT", 6: "MMF_ECLOSED", 7: "MMF_ENOTIMPL", 8: "MMF_EDEVICE"}
 DTYPES = {torch.float32: 0, torch.float64: 1, torch.int16: 2, torch.uint8: 3}
 MODES = {"valid": 0, "envelope": 1, "centered_clipped": 1}
-KERNELS = {"auto": 0, "blockscan": 1, "slide": 2, "wedge": 3}
+KERNELS = {"auto": 0, "blockscan": 1, "slide": 2, "wedge": 3, "front": 4}
 
 _I64 = ctypes.c_int64
 _VP = ctypes.c_void_p
@@ -106,6 +106,12 @@ _EXTRA_SIGNATURES: dict = {
                                   _INT),
     "mmf_stream_restore": ([_VP, _VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint64)], _INT),
     "mmf_server_pause": ([_VP, _INT], _INT),
+    "mmf_test_set_wait_fault": ([_INT, _I64], _INT),
+    "mmf_dispatch_set": ([_INT, _I64, _I64, _INT], _INT),
+    "mmf_dispatch_get": ([_INT, _I64, _I64, ctypes.POINTER(_INT)], _INT),
+    "mmf_dispatch_autotune": ([_VP, _I64, _I64, _INT, _VP, _VP, _VP, ctypes.POINTER(_INT)], _INT),
+    "mmf_batch_plan_set_knobs": ([_VP, _I64, _INT], _INT),
+    "mmf_batch_plan_get_knobs": ([_VP, _P64, ctypes.POINTER(_INT)], _INT),
     "mmf_filter2d_workspace": ([_I64, _I64, _I64, _I64, _I64, _INT, _INT, ctypes.POINTER(ctypes.c_size_t)], _INT),
     "mmf_filter2d_separable": ([_VP, _I64, _I64, _I64, _I64, _I64, _I64, _INT, _INT, _VP, _VP, _VP,
                                 ctypes.c_size_t, _VP], _INT),
@@ -364,6 +370,17 @@ class BatchPlan:
     def set_segment(self, group: int, tiles: int):
         check(self._lib.mmf_batch_plan_set_segment(self._h, group, tiles))
 
+    def knobs(self):
+        """Tuned knobs beside the segments: ``short_cut`` (series of at most
+        this many elements take one warp each) and ``slide_max`` (windows up
+        to this take the register slide)."""
+        sc, sl = ctypes.c_int64(), ctypes.c_int()
+        check(self._lib.mmf_batch_plan_get_knobs(self._h, ctypes.byref(sc), ctypes.byref(sl)))
+        return {"short_cut": int(sc.value), "slide_max": int(sl.value), "segments": self.segments()}
+
+    def set_knobs(self, short_cut: int, slide_max: int):
+        check(self._lib.mmf_batch_plan_set_knobs(self._h, int(short_cut), int(slide_max)))
+
     def close(self):
         if getattr(self, "_h", None):
             self._lib.mmf_batch_plan_destroy(self._h)
@@ -531,6 +548,47 @@ def n_outputs(count_before: int, chunk_len: int, w: int) -> int:
     """Outputs of a chunk of chunk_len samples pushed after count_before
     samples to a stream with window w (windows ending inside the chunk)."""
     return max(0, count_before + chunk_len - w + 1) - max(0, count_before - w + 1)
+
+
+_KERNEL_NAMES = {v: k for k, v in KERNELS.items()}
+
+
+def dispatch_set(dtype, n: int, w: int, kernel: str) -> None:
+    """Entry of the AUTO dispatch table for the bucket of (dtype, n, w)
+    (``kernel="auto"`` removes it)."""
+    check(load().mmf_dispatch_set(DTYPES[dtype], int(n), int(w), KERNELS[kernel]))
+
+
+def dispatch_get(dtype, n: int, w: int) -> str:
+    """The kernel that ``kernel="auto"`` takes for valid windows of w over n."""
+    k = ctypes.c_int()
+    check(load().mmf_dispatch_get(DTYPES[dtype], int(n), int(w), ctypes.byref(k)))
+    return _KERNEL_NAMES[int(k.value)]
+
+
+def dispatch_autotune(x: torch.Tensor, w: int, out_max=None, out_min=None, stream=None) -> str:
+    """Times every kernel that can filter ``x`` at window w and stores the
+    fastest in the dispatch table (synchronises the stream); returns it."""
+    _check_tensor(x, "x")
+    lib = load()
+    x = x.reshape(-1)
+    m = int(lib.mmf_output_length(x.numel(), w, MODES["valid"]))
+    if out_max is None:
+        out_max = torch.empty(max(m, 1), dtype=x.dtype, device=x.device)
+    if out_min is None:
+        out_min = torch.empty(max(m, 1), dtype=x.dtype, device=x.device)
+    k = ctypes.c_int()
+    with torch.cuda.device(x.device):
+        check(lib.mmf_dispatch_autotune(_ptr(x), x.numel(), int(w), DTYPES[x.dtype], _ptr(out_max), _ptr(out_min),
+                                        _VP(_stream_handle(stream)), ctypes.byref(k)))
+    return _KERNEL_NAMES[int(k.value)]
+
+
+def set_wait_fault(starve_copies: bool, wait_limit_cycles: int = 0) -> None:
+    """Test hook (``mmf_test_set_wait_fault``): block-scan kernels launched
+    while it is on issue no input copies, so their pipeline waits run out
+    after ``wait_limit_cycles`` SM clocks and set bit 0 of the status word."""
+    check(load().mmf_test_set_wait_fault(1 if starve_copies else 0, int(wait_limit_cycles)))
 
 
 def device_status(reset: bool = True) -> int:

@@ -43,14 +43,20 @@ struct Group {
     ItemDesc *d_items = nullptr;
 };
 
-int kernel_mode(mmf_dtype dt, int64_t w) {
+// Kernel group of a series' window: the register slide for w <= slide_max
+// (at most the slide's own limit), else the block-scan mode.
+int kernel_mode(mmf_dtype dt, int64_t w, int slide_max) {
+    const bool slide = w <= slide_max;
     switch (dt) {
-        case MMF_F32: return block_mode<float>(w, true);
-        case MMF_F64: return block_mode<double>(w, true);
-        case MMF_I16: return block_mode<int16_t>(w, true);
-        default: return block_mode<uint8_t>(w, true);
+        case MMF_F32: return block_mode<float>(w, slide);
+        case MMF_F64: return block_mode<double>(w, slide);
+        case MMF_I16: return block_mode<int16_t>(w, slide);
+        default: return block_mode<uint8_t>(w, slide);
     }
 }
+
+// The register slide's own window limit for the type.
+int slide_limit(mmf_dtype dt) { return dt == MMF_F32 ? 17 : 9; }
 
 }  // namespace
 
@@ -65,6 +71,12 @@ struct mmf_batch_plan {
     std::vector<SeriesDesc> series;
     std::vector<int64_t> out_off;  // nseries + 1
     Group groups[kModes];
+    // Tuned knobs beside the segment lengths: series of at most short_cut
+    // elements take the warp-per-series kernel (one warp per series instead
+    // of block-scan items of a whole CTA; 0: none), and windows of at most
+    // slide_max take the register slide (1: none).
+    int64_t short_cut = 0;
+    int slide_max = 1;
     std::vector<int64_t> short_ids;  // series taken by the warp-per-series kernel
     int64_t *d_short = nullptr;
     cudaStream_t short_branch = nullptr;
@@ -83,7 +95,7 @@ struct mmf_batch_plan {
 namespace {
 
 bool is_short(const mmf_batch_plan *p, const SeriesDesc &sd) {
-    return sd.n_out > 0 && sd.n <= short_max_len(elem_size(p->dtype));
+    return sd.n_out > 0 && sd.n <= p->short_cut;
 }
 
 void free_items(mmf_batch_plan *p) {
@@ -104,7 +116,7 @@ mmf_status build_items(mmf_batch_plan *p, int gi) {
     const int64_t seg = (int64_t)std::max(1, g.seg_tiles) * T;
     for (int64_t s = 0; s < p->nseries; ++s) {
         const SeriesDesc &sd = p->series[s];
-        if (sd.n_out <= 0 || is_short(p, sd) || kernel_mode(p->dtype, sd.w) != g.mode) continue;
+        if (sd.n_out <= 0 || is_short(p, sd) || kernel_mode(p->dtype, sd.w, p->slide_max) != g.mode) continue;
         for (int64_t ob = 0; ob < sd.n_out; ob += seg) g.items.push_back({s, ob, std::min(sd.n_out, ob + seg)});
     }
     std::stable_sort(g.items.begin(), g.items.end(), [&](const ItemDesc &a, const ItemDesc &b) {
@@ -119,6 +131,29 @@ mmf_status build_items(mmf_batch_plan *p, int gi) {
     if (e != cudaSuccess) return set_error(MMF_ENOMEM, "plan items: %s", cudaGetErrorString(e));
     e = cudaMemcpy(g.d_items, g.items.data(), g.items.size() * sizeof(ItemDesc), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_error(e, "upload items");
+    return MMF_OK;
+}
+
+// The short-series list and every group's items for the current knobs.
+mmf_status rebuild_all(mmf_batch_plan *p) {
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    p->exec = nullptr;
+    p->short_ids.clear();
+    for (int64_t s = 0; s < p->nseries; ++s)
+        if (is_short(p, p->series[s])) p->short_ids.push_back(s);
+    if (p->d_short) cudaFree(p->d_short);
+    p->d_short = nullptr;
+    if (!p->short_ids.empty()) {
+        cudaError_t e = cudaMalloc(&p->d_short, p->short_ids.size() * sizeof(int64_t));
+        if (e != cudaSuccess) return set_error(MMF_ENOMEM, "plan short-series list: %s", cudaGetErrorString(e));
+        e = cudaMemcpy(p->d_short, p->short_ids.data(), p->short_ids.size() * sizeof(int64_t),
+                       cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_error(e, "upload short-series list");
+    }
+    for (int gi = 0; gi < kModes; ++gi) {
+        mmf_status st = build_items(p, gi);
+        if (st != MMF_OK) return st;
+    }
     return MMF_OK;
 }
 
@@ -240,7 +275,24 @@ __global__ void lb_sqrt_kernel(double *acc, int64_t n) {
         acc[i] = sqrt(acc[i]);
 }
 
-// Autotune cache: one line "key seg_tiles" per entry in $MMF_AUTOTUNE_CACHE.
+// Autotune cache: one line "key value" per entry in $MMF_AUTOTUNE_CACHE (the
+// last entry of a key wins).  Keys name the GPU, dtype, mode and the shape.
+std::string cache_key_plan(const mmf_batch_plan *p, const char *knob) {
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, p->device);
+    int64_t total = 0;
+    for (auto &sd : p->series) total += sd.n;
+    int lt = 0;
+    while ((1ll << (lt + 1)) <= std::max<int64_t>(1, total)) ++lt;
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s|dt%d|m%d|%s|elems2^%d|series%lld", prop.name, (int)p->dtype, (int)p->mode, knob,
+             lt, (long long)p->nseries);
+    std::string k(buf);
+    for (auto &c : k)
+        if (c == ' ') c = '_';
+    return k;
+}
+
 std::string cache_key(const mmf_batch_plan *p, int gi) {
     cudaDeviceProp prop;
     cudaGetDeviceProperties(&prop, p->device);
@@ -288,6 +340,7 @@ extern "C" {
 
 mmf_status mmf_batch_plan_create(const int64_t *h_in_off, const int64_t *h_len, const int64_t *h_w, int64_t nseries,
                                  mmf_dtype dtype, mmf_mode mode, mmf_batch_plan **out) {
+    NvtxRange nvtx_range("mmf_batch_plan_create");
     if (!out) return set_error(MMF_EINVAL, "NULL plan output");
     *out = nullptr;
     if (nseries < 0 || (nseries > 0 && (!h_len || !h_w))) return set_error(MMF_EINVAL, "bad series description");
@@ -342,24 +395,26 @@ mmf_status mmf_batch_plan_create(const int64_t *h_in_off, const int64_t *h_len, 
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->short_branch, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->short_join, cudaEventDisableTiming);
-    for (int64_t s = 0; s < nseries; ++s)
-        if (is_short(p, p->series[s])) p->short_ids.push_back(s);
-    if (e == cudaSuccess && !p->short_ids.empty()) {
-        e = cudaMalloc(&p->d_short, p->short_ids.size() * sizeof(int64_t));
-        if (e == cudaSuccess)
-            e = cudaMemcpy(p->d_short, p->short_ids.data(), p->short_ids.size() * sizeof(int64_t),
-                           cudaMemcpyHostToDevice);
-    }
     if (e != cudaSuccess) {
         mmf_batch_plan_destroy(p);
         return set_error(MMF_ENOMEM, "plan device tables: %s", cudaGetErrorString(e));
     }
+    // Knobs: the built-in choice, or a tuned one cached for this shape.
+    p->short_cut = short_max_len(esz);
+    p->slide_max = slide_limit(dtype);
+    {
+        const int cs = cache_lookup(cache_key_plan(p, "short"));
+        const int cl = cache_lookup(cache_key_plan(p, "slide"));
+        if (cs > 0) p->short_cut = std::min<int64_t>(cs - 1, short_max_len(esz));  // stored + 1 (0 = none)
+        if (cl > 0) p->slide_max = std::min(cl, slide_limit(dtype));
+    }
+    mmf_status rs = rebuild_all(p);
+    if (rs != MMF_OK) {
+        mmf_batch_plan_destroy(p);
+        return rs;
+    }
     for (int gi = 0; gi < kModes; ++gi) {
-        mmf_status st = build_items(p, gi);
-        if (st != MMF_OK) {
-            mmf_batch_plan_destroy(p);
-            return st;
-        }
+        mmf_status st = MMF_OK;
         const int cached = cache_lookup(cache_key(p, gi));
         if (cached > 0 && cached != p->groups[gi].seg_tiles) {
             p->groups[gi].seg_tiles = cached;
@@ -415,6 +470,7 @@ mmf_status mmf_batch_plan_set_segment(mmf_batch_plan *p, int group, int seg_tile
 }
 
 mmf_status mmf_filter1d_batched(mmf_batch_plan *p, const void *d_in, void *d_max, void *d_min, void *stream) {
+    NvtxRange nvtx_range("mmf_filter1d_batched");
     if (!p) return set_error(MMF_EINVAL, "NULL plan");
     if (p->out_len == 0) return MMF_OK;
     if (!d_in || (!d_max && !d_min)) return set_error(MMF_EINVAL, "NULL buffers");
@@ -431,6 +487,7 @@ mmf_status mmf_filter1d_batched(mmf_batch_plan *p, const void *d_in, void *d_max
 
 mmf_status mmf_lb_keogh_batched(mmf_batch_plan *p, const void *d_in, const void *d_query, int64_t n_query,
                                 double *d_lb, void *stream) {
+    NvtxRange nvtx_range("mmf_lb_keogh_batched");
     if (!p) return set_error(MMF_EINVAL, "NULL plan");
     if (p->mode != MMF_CENTERED_CLIPPED) return set_error(MMF_EINVAL, "the lower bound needs an envelope plan");
     if (p->nseries == 0) return MMF_OK;
@@ -459,6 +516,7 @@ mmf_status mmf_lb_keogh_batched(mmf_batch_plan *p, const void *d_in, const void 
 
 mmf_status mmf_filter1d_per_series(const mmf_batch_plan *p, const void *d_in, void *d_max, void *d_min,
                                    void *stream) {
+    NvtxRange nvtx_range("mmf_filter1d_per_series");
     if (!p) return set_error(MMF_EINVAL, "NULL plan");
     const int esz = elem_size(p->dtype);
     for (int64_t s = 0; s < p->nseries; ++s) {
@@ -473,17 +531,81 @@ mmf_status mmf_filter1d_per_series(const mmf_batch_plan *p, const void *d_in, vo
     return MMF_OK;
 }
 
+// Event time of the whole plan (every group and the short series, no graph)
+// on `st`: median of three runs after one warm-up run; < 0 on failure.
+static float time_plan(mmf_batch_plan *p, cudaStream_t st, const void *d_in, void *d_max, void *d_min,
+                       cudaEvent_t e0, cudaEvent_t e1) {
+    float t[3];
+    for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(e0, st);
+        if (enqueue_all(p, st, d_in, d_max, d_min) != MMF_OK) return -1.f;
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return -1.f;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) t[rep - 1] = ms;  // the first run warms up
+    }
+    std::sort(t, t + 3);
+    return t[1];
+}
+
 mmf_status mmf_batch_plan_autotune(mmf_batch_plan *p, const void *d_in, void *d_max, void *d_min, void *stream) {
+    NvtxRange nvtx_range("mmf_batch_plan_autotune");
     if (!p) return set_error(MMF_EINVAL, "NULL plan");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     LaunchCtx ctx;
     mmf_status s = get_ctx(stream, &ctx);
     if (s != MMF_OK) return s;
-    const int cands[] = {1, 2, 4, 8, 16, 32, 64, 128};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    for (int gi = 0; gi < kModes; ++gi) {
+    // 1. Threads per short series: one warp per series for series of at most
+    //    short_cut elements, else block-scan items of a whole CTA.
+    // 2. Kernel choice for small windows: the register slide up to slide_max,
+    //    else the block scans.
+    // 3. Segment length (output tiles per work item) per block-scan group.
+    // Each knob is timed over the whole plan with the others fixed.
+    const int64_t smax = short_max_len(elem_size(p->dtype));
+    const int64_t short_cands[] = {0, smax / 4, smax / 2, smax};
+    const int lmax = slide_limit(p->dtype);
+    const int slide_cands[] = {1, 5, 9, 17};
+    for (int knob = 0; knob < 2 && s == MMF_OK; ++knob) {
+        const int64_t keep_short = p->short_cut;
+        const int keep_slide = p->slide_max;
+        int64_t best_short = keep_short;
+        int best_slide = keep_slide;
+        float best_ms = 1e30f;
+        for (int c = 0; c < 4; ++c) {
+            if (knob == 0) {
+                p->short_cut = short_cands[c];
+            } else {
+                if (slide_cands[c] > lmax) continue;
+                p->slide_max = slide_cands[c];
+            }
+            s = rebuild_all(p);
+            if (s != MMF_OK) break;
+            const float ms = time_plan(p, st, d_in, d_max, d_min, e0, e1);
+            if (ms < 0.f) {
+                s = set_error(MMF_ECUDA, "autotune run failed");
+                break;
+            }
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_short = p->short_cut;
+                best_slide = p->slide_max;
+            }
+        }
+        p->short_cut = knob == 0 ? best_short : keep_short;
+        p->slide_max = knob == 1 ? best_slide : keep_slide;
+        mmf_status s2 = rebuild_all(p);
+        if (s == MMF_OK) s = s2;
+    }
+    if (s == MMF_OK) {
+        cache_store(cache_key_plan(p, "short"), (int)p->short_cut + 1);
+        cache_store(cache_key_plan(p, "slide"), p->slide_max);
+    }
+    const int cands[] = {1, 2, 4, 8, 16, 32, 64, 128};
+    for (int gi = 0; gi < kModes && s == MMF_OK; ++gi) {
         if (p->groups[gi].items.empty()) continue;
         int best = p->groups[gi].seg_tiles;
         float best_ms = 1e30f;
@@ -520,6 +642,26 @@ mmf_status mmf_batch_plan_autotune(mmf_batch_plan *p, const void *d_in, void *d_
     if (p->exec) cudaGraphExecDestroy(p->exec);
     p->exec = nullptr;
     return s;
+}
+
+mmf_status mmf_batch_plan_set_knobs(mmf_batch_plan *p, int64_t short_cut, int slide_max) {
+    if (!p) return set_error(MMF_EINVAL, "NULL plan");
+    const int64_t smax = short_max_len(elem_size(p->dtype));
+    if (short_cut < 0 || short_cut > smax)
+        return set_error(MMF_EINVAL, "short-series cut-off %lld outside [0, %lld]", (long long)short_cut,
+                         (long long)smax);
+    if (slide_max < 1 || slide_max > slide_limit(p->dtype))
+        return set_error(MMF_EINVAL, "slide window limit %d outside [1, %d]", slide_max, slide_limit(p->dtype));
+    p->short_cut = short_cut;
+    p->slide_max = slide_max;
+    return rebuild_all(p);
+}
+
+mmf_status mmf_batch_plan_get_knobs(const mmf_batch_plan *p, int64_t *short_cut, int *slide_max) {
+    if (!p || !short_cut || !slide_max) return set_error(MMF_EINVAL, "NULL argument");
+    *short_cut = p->short_cut;
+    *slide_max = p->slide_max;
+    return MMF_OK;
 }
 
 mmf_status mmf_batch_plan_get_segment(const mmf_batch_plan *p, int group, int *seg_tiles) {

@@ -232,8 +232,27 @@ struct BlockScanParams {
     // excursion of lb_query[i] outside [min, max] to lb_acc[s].
     const void *lb_query;
     double *lb_acc;
+    // Bound of every pipeline wait in SM clocks (0: kWaitLimitCycles), and
+    // test flags (kTestStarveCopies: issue no input copies, so that every
+    // wait runs out; for tests of the timeout path only).
+    long long wait_limit;
+    uint32_t test_flags;
+    uint32_t pad_;
+    // One advancing front (1D series, windows of a tile or more; see
+    // run_front_item): work item i is output tile i, CTA b of the grid of G
+    // takes items b, b+G, b+2G, ...; the aggregates of the whole tiles inside
+    // the windows come from front_slots (two tagged words per global tile,
+    // see front_put), published G items earlier by the item that read the
+    // tile ahead (front_ahead = G), or at the start for the first G+q tiles.
+    // front_last: the last global tile whose aggregate any item takes.
+    // nullptr: items read those tiles themselves.
+    unsigned long long *front_slots;
+    int64_t front_last;
+    int32_t front_ahead;
+    int32_t pad2_;
 };
 static_assert(sizeof(BlockScanParams) <= 256, "parameters are copied to a 256-byte shared slot");
+enum : uint32_t { kTestStarveCopies = 1u };
 
 constexpr int kStages = 4;             // per-warp slice stages (power of two)
 constexpr int kQCap = 1024 + 8;        // tile-aggregate ring (>= max tiles per window + 2)
@@ -365,6 +384,9 @@ template <typename T> struct ItemPlan {
     int mode;    // 0: B < V, 1: V <= B < 32V, 2: B = 32V (one block per warp); 3: register slide
     int NC;      // output tiles in the item
     int klast;   // 1 if some window of the last output tile reaches K tile NC+q
+    int front;   // an item of the advancing front (one output tile, see run_front_item)
+    int la;      // its tile read ahead (relative index q + G), 0 if none
+    int64_t gt0; // global tile index of the item's tile 0 (advancing front)
     int ok;
 };
 
@@ -422,6 +444,9 @@ __device__ __forceinline__ ItemPlan<T> make_plan(const BlockScanParams &P, int64
     ip.NC = span > 0 ? (int)((span + G::T_ - 1) >> G::LGT) : 0;
     ip.klast = span > 0 ? (int)((((span - 1) + s) >> G::LGT) >= ip.NC + ip.q) : 0;
     if (want_mode == 3 && s <= G::SLIDE_S) ip.mode = 3;  // register slide: w <= SLIDE_S + 1
+    ip.front = 0;  // rounds of the advancing front have their own plans (front_plan)
+    ip.la = 0;
+    ip.gt0 = ob >> G::LGT;
     ip.ok = (s >= 0) && (ip.q + 2 <= kQCap) && span >= 0 && span + s + 2 * (int64_t)G::T_ <= kMaxItemSpan &&
             (want_mode < 0 || want_mode == ip.mode);
     return ip;
@@ -544,9 +569,50 @@ __device__ __forceinline__ void copy_pieces(uint8_t *dst, uintptr_t src, uint32_
                     bytes, bar, pol);
 }
 
+// Advancing front, lane 0 of `warp`: issue this warp's slice of its next
+// load.  The CTA's work is one sequence of rounds (output tiles t = b, b+G,
+// b+2G, ...), four loads each: K tile t+q, K tile t+q+1, J tile t and the
+// tile read ahead, t+q+G (a round reads all four even where a window does
+// not reach the second or no item takes the fourth, so that the order is
+// fixed).  Tile positions are computed directly: no per-round set-up.
+template <typename T>
+__device__ __forceinline__ void issue_next_front(int warp) {
+    using G = Geo<T>;
+    using S = Smem<T>;
+    WarpIssue &wi = *S::issue(warp);
+    if (wi.l >= wi.nloads) return;  // the end (or a starved test launch: nloads = -1)
+    const BlockScanParams &P = S::params();
+    const int l = wi.l;
+    const int k = l & 3;
+    const int64_t t = (int64_t)blockIdx.x + (int64_t)(l >> 2) * gridDim.x;
+    const int64_t q = wi.q;
+    const int64_t x = t + (k == 0 ? q : (k == 1 ? q + 1 : (k == 2 ? 0 : q + (int64_t)gridDim.x)));
+    const int64_t a = P.one.d + x * G::T_ + (int64_t)warp * G::SLICE;
+    const T *in = reinterpret_cast<const T *>(P.in) + P.one.in_off;
+    const SliceCopy sc =
+        slice_copy<T, 0>(in, P.one.n, a, reinterpret_cast<const T *>(P.in), P.in_elems);
+    const int stage = wi.issued & (kStages - 1);
+    uint64_t *bar = S::bar(warp, stage);
+    wi.smode[stage] = sc.mode | (sc.shift << 8);
+    if (sc.mode == 2 || sc.mode == 3) {
+        mbar_arrive_expect_tx(bar, 0);
+    } else {
+        fence_proxy_async_smem();
+        // The J tile is read for the last time; the others are read again soon.
+        copy_pieces<T, 0>(S::slice(warp, stage), sc.src, sc.mode == 0 ? 0u : 16u, bar,
+                          k == 2 ? policy_evict_first() : policy_evict_last());
+    }
+    wi.l = l + 1;
+    wi.issued++;
+}
+
 // Lane 0 of `warp`: issue this warp's slice of its next load, if any.
-template <typename T, int MODE>
+template <typename T, int MODE, bool FRONT = false>
 __device__ __forceinline__ void issue_next(int warp) {
+    if constexpr (FRONT) {
+        issue_next_front<T>(warp);
+        return;
+    }
     using G = Geo<T>;
     using S = Smem<T>;
     constexpr int HALO = MODE == 3 ? G::HALO_MAX : 0;
@@ -689,6 +755,34 @@ template <typename T> struct TileQueue {
     }
 };
 
+// Published tile aggregates of the advancing front: global tile g owns two
+// 64-bit words, (max bits | tag << 32) and (min bits | tag << 32), tag =
+// g + 1 (the workspace starts zeroed: no tag).  Each word is stored and
+// loaded whole (single-copy atomic), so a reader that finds the tag in both
+// words has both values; no fence is needed, and writers of one slot store
+// identical words.  Element types whose register form is 32 bits only.
+__device__ __forceinline__ uint32_t rbits(float v) { return __float_as_uint(v); }
+__device__ __forceinline__ uint32_t rbits(int v) { return (uint32_t)v; }
+__device__ __forceinline__ void rfrom(uint32_t b, float &v) { v = __uint_as_float(b); }
+__device__ __forceinline__ void rfrom(uint32_t b, int &v) { v = (int)b; }
+template <typename T>
+__device__ __forceinline__ void front_put(unsigned long long *slot, uint32_t tag, typename Elem<T>::R m,
+                                          typename Elem<T>::R n) {
+    const unsigned long long a = ((unsigned long long)tag << 32) | rbits(m);
+    const unsigned long long b = ((unsigned long long)tag << 32) | rbits(n);
+    asm volatile("st.relaxed.gpu.global.v2.b64 [%0], {%1, %2};" ::"l"(slot), "l"(a), "l"(b) : "memory");
+}
+template <typename T>
+__device__ __forceinline__ bool front_get(const unsigned long long *slot, uint32_t tag, typename Elem<T>::R &m,
+                                          typename Elem<T>::R &n) {
+    unsigned long long a, b;
+    asm volatile("ld.relaxed.gpu.global.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(slot) : "memory");
+    if ((uint32_t)(a >> 32) != tag || (uint32_t)(b >> 32) != tag) return false;
+    rfrom((uint32_t)a, m);
+    rfrom((uint32_t)b, n);
+    return true;
+}
+
 // ------------------------------------------------------------ consumer side
 // Block modes of an item (s = w-1, warp span W = 32V):
 //   0: s < V      B = 2^floor(log2 s) < V: blocks inside a thread
@@ -696,7 +790,7 @@ template <typename T> struct TileQueue {
 //   2: s >= W     B = W: one block per warp; for s >= T also tile aggregates
 // LB: the output stage feeds the envelope lower bound instead of storing
 // (a separate instantiation, so the storing kernels carry none of it).
-template <typename T, int KMODE, bool LB = false>
+template <typename T, int KMODE, bool LB = false, bool FRONT = false>
 struct Consumer {
     using R = typename Elem<T>::R;
     using Pair = typename Elem<T>::Pair;
@@ -708,10 +802,47 @@ struct Consumer {
 
     int tid, lane, warp;
     StageCursor cur;
-    bool failed = false;
+    bool failed = false;         // a wait of this thread ran out
+    long long wait_limit = kWaitLimitCycles;
 
     // CTA barrier (the P ring and block aggregates are shared by all warps).
+    // A warp whose wait ran out still takes every barrier of its work item
+    // (it goes on with identities, without waiting or issuing copies), so no
+    // warp is ever left waiting for one that left; all warps leave together
+    // at the item boundary, whose barrier ORs their failure flags.
     __device__ __forceinline__ void sync() { named_bar_sync(1, G::NT); }
+
+    // Bounded wait of this thread for the warp's current stage.  A thread
+    // whose wait has run out waits no more (its failure flag stays set and is
+    // reported once in the status word); nothing else depends on whether the
+    // lanes of a warp agree, since every lane carries on through the item
+    // and the flags meet at the item boundary's OR barrier.
+    __device__ __forceinline__ bool wait_stage() {
+        if (mbar_try_wait(S::bar(warp, cur.stage), cur.phase)) return true;
+        const bool ok = !failed && mbar_wait_bounded(S::bar(warp, cur.stage), cur.phase, wait_limit);
+        if (!ok && !failed) {
+            report_error(S::params().status, kErrWaitTimeout);
+            failed = true;
+        }
+        return ok;
+    }
+
+    // Before leaving after a failure: wait (bounded) for the copies this warp
+    // still has in flight, so that none lands after the CTA has exited.
+    __device__ __forceinline__ void drain() {
+        if (lane == 0) {
+            StageCursor c = cur;
+            // Loads issued but not read, from the issue count and the cursor
+            // (both modulo 2 kStages; at most kStages apart).
+            const int outstanding =
+                (S::issue(warp)->issued - (int)(cur.phase * kStages + cur.stage)) & (2 * kStages - 1);
+            for (int k = 0; k < outstanding && k < kStages; ++k) {
+                if (!mbar_wait_bounded(S::bar(warp, c.stage), c.phase, wait_limit)) break;
+                c.advance();
+            }
+        }
+        __syncwarp();
+    }
 
     // Identities at this thread's positions of tile x that lie outside the
     // series [0, n) (clipped copies).
@@ -782,12 +913,15 @@ struct Consumer {
     // warp's slice stage, then let lane 0 refill the stage with the warp's
     // next load.  Max-side and min-side copies differ only at positions
     // outside [0, n), which hold identities.
+    // After a failed wait the thread reads whatever the stage holds (every
+    // read stays inside the stage or the series; leaving the values unset
+    // instead would push the arrays to local memory) and the caller carries
+    // on through the item, whose outputs are then unspecified.  The refill is
+    // issued either way: a copy issued after a failure is an ordinary copy
+    // that lands, and the item boundary waits for every copy still in flight
+    // before the CTA leaves.
     __device__ __forceinline__ bool read_tile(const ItemPlan<T> &ip, int x, R (&xm)[V], R (&xn)[V]) {
-        if (!mbar_wait_bounded(S::bar(warp, cur.stage), cur.phase)) {
-            report_error(S::params().status, kErrWaitTimeout);
-            failed = true;
-            return false;
-        }
+        const bool ok = wait_stage();
         const int smode = S::issue(warp)->smode[cur.stage];
         const int mode = smode & 0xff;
         const uint8_t *sb = S::slice(warp, cur.stage);
@@ -830,10 +964,10 @@ struct Consumer {
             }
         }
         __syncwarp();
-        if (lane == 0) issue_next<T, KMODE>(warp);
+        if (lane == 0) issue_next<T, KMODE, FRONT>(warp);
         __syncwarp();
         cur.advance();
-        return true;
+        return ok;
     }
 
     template <int MODE>
@@ -1147,7 +1281,8 @@ struct Consumer {
         }
     }
 
-    // Tile aggregate of K tile x from its warp-block aggregates (warp 0).
+    // Tile aggregate of K tile x from its warp-block aggregates (warp 0),
+    // into the aggregate ring.
     __device__ __forceinline__ void publish_tile_aggregate(int x) const {
         if (warp != 0) return;
         Pair a = lane < NW ? S::kagg()[(x % 3) * NW + lane] : Elem<T>::pair(Elem<T>::lo(), Elem<T>::hi());
@@ -1159,6 +1294,7 @@ struct Consumer {
         }
         if (lane == 0) S::ta()[x % kQCap] = Elem<T>::pair(m, n);
     }
+
 
     // Prefix (and optionally suffix) block scans of one tile's registers.
     // MODE 2 publishes the warp (= block) totals.
@@ -1463,7 +1599,7 @@ struct Consumer {
         const bool kload = c + 1 < ip.NC || ip.klast;  // else no window reaches tile c+1
         if (kload) {
             R xm[V], xn[V];
-            if (!read_tile(ip, c + 1, xm, xn)) return false;
+            read_tile(ip, c + 1, xm, xn);
             R pm[V], pn[V], em, en, gm, gn, hm, hn;
             scan_kj(lgS, xm, xn, xm, xn, pm, pn, em, en, gm, gn, nx.sm, nx.sn, nx.fm, nx.fn, hm, hn);
             k_publish<MODE>(c + 1, pm, pn, em, en, gm, gn);
@@ -1471,6 +1607,121 @@ struct Consumer {
         sync();
         outputs12<MODE>(ip, c, cur.sm, cur.sn, cur.fm, cur.fn, vec);
         return true;
+    }
+
+    // Advancing front, one round: output tile t (relative tile 0; its K
+    // tiles are relative q and q+1).  The whole tiles inside its windows,
+    // t+1 .. t+q-1, enter as published aggregates: tile x was read ahead in
+    // round x-q-G, a whole round of the grid earlier (or at the start, for
+    // x < q+G), so they are normally there when asked for; this round in turn
+    // reads tile t+q+G ahead and publishes it.  Warp 0 starts loading the
+    // aggregates with the round, so that their latency overlaps its reads.
+    // The four stages of the round are always read (see issue_next_front).
+    __device__ __forceinline__ void run_front_round(const ItemPlan<T> &ip, int vec) {
+        constexpr int MODE = 2;
+        constexpr int lgS = 5;
+        const BlockScanParams &P = S::params();
+        const int q = ip.q;
+        // Warp 0, lane l: the published words of tile 1+l (if inside 1..q-1).
+        unsigned long long ea = 0, eb = 0;
+        if (warp == 0 && 1 + lane <= q - 1) {
+            const unsigned long long *slot = P.front_slots + 2 * (ip.gt0 + 1 + lane);
+            asm volatile("ld.relaxed.gpu.global.v2.b64 {%0, %1}, [%2];" : "=l"(ea), "=l"(eb) : "l"(slot));
+        }
+        JState js;
+        R hm, hn;
+        {
+            R xm[V], xn[V];
+            read_tile(ip, q, xm, xn);  // K tile q
+            R pm[V], pn[V], em, en, gm, gn;
+            scan_k(lgS, xm, xn, pm, pn, em, en, gm, gn);
+            k_publish<MODE>(q, pm, pn, em, en, gm, gn);
+        }
+        {
+            R km[V], kn[V], jm[V], jn[V];
+            read_tile(ip, q + 1, km, kn);  // K tile q+1
+            read_tile(ip, 0, jm, jn);      // J tile 0
+            if (ip.klast) {                // some window of the tile reaches K tile q+1
+                R pm[V], pn[V], em, en, gm, gn;
+                scan_kj(lgS, km, kn, jm, jn, pm, pn, em, en, gm, gn, js.sm, js.sn, js.fm, js.fn, hm, hn);
+                k_publish<MODE>(q + 1, pm, pn, em, en, gm, gn);
+            } else {
+                scan_j(lgS, jm, jn, js.sm, js.sn, js.fm, js.fn, hm, hn);
+            }
+        }
+        if (lane == 0) S::jagg()[warp] = Elem<T>::pair(hm, hn);
+        {
+            // The tile read ahead: its maximum and minimum only.
+            R xm[V], xn[V];
+            read_tile(ip, q + (int)gridDim.x, xm, xn);
+            if (ip.la) {
+                R m = xm[0], n = xn[0];
+#pragma unroll
+                for (int i = 1; i < V; ++i) {
+                    m = vmax(m, xm[i]);
+                    n = vmin(n, xn[i]);
+                }
+#pragma unroll
+                for (int d = 16; d >= 1; d >>= 1) {
+                    m = vmax(m, __shfl_xor_sync(0xffffffffu, m, d));
+                    n = vmin(n, __shfl_xor_sync(0xffffffffu, n, d));
+                }
+                if (lane == 0) S::jagg()[NW + warp] = Elem<T>::pair(m, n);
+            }
+        }
+        if (warp == 0) {
+            // Whole tiles 1..q-1: the early words where their tags are there,
+            // else (and for tiles past 1+32) bounded waits for them.
+            bool ok = !failed;
+            R m = Elem<T>::lo(), n = Elem<T>::hi();
+            const long long t0 = clock64();
+            for (int x = 1 + lane; ok && x <= q - 1; x += 32) {
+                const int64_t g = ip.gt0 + x;
+                const uint32_t tag = (uint32_t)(g + 1);
+                R am, an;
+                bool got = false;
+                if (x == 1 + lane && (uint32_t)(ea >> 32) == tag && (uint32_t)(eb >> 32) == tag) {
+                    rfrom((uint32_t)ea, am);
+                    rfrom((uint32_t)eb, an);
+                    got = true;
+                }
+                while (!got && !(got = front_get<T>(P.front_slots + 2 * g, tag, am, an))) {
+                    if (clock64() - t0 > wait_limit) {
+                        ok = false;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+                if (got) {
+                    m = vmax(m, am);
+                    n = vmin(n, an);
+                }
+            }
+#pragma unroll
+            for (int d = 16; d >= 1; d >>= 1) {
+                m = vmax(m, __shfl_xor_sync(0xffffffffu, m, d));
+                n = vmin(n, __shfl_xor_sync(0xffffffffu, n, d));
+            }
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok && !failed) {
+                if (lane == 0) report_error(P.status, kErrWaitTimeout);
+                failed = true;
+            }
+            if (lane == 0) S::tb()[0] = Elem<T>::pair(m, n);
+        }
+        sync();
+        if (ip.la && warp == 0) {
+            Pair a = lane < NW ? S::jagg()[NW + lane] : Elem<T>::pair(Elem<T>::lo(), Elem<T>::hi());
+            R m = Elem<T>::pmax(a), n = Elem<T>::pmin(a);
+#pragma unroll
+            for (int d = NW / 2; d >= 1; d >>= 1) {
+                m = vmax(m, __shfl_xor_sync(0xffffffffu, m, d));
+                n = vmin(n, __shfl_xor_sync(0xffffffffu, n, d));
+            }
+            const int64_t g = ip.gt0 + ip.la;
+            if (lane == 0) front_put<T>(P.front_slots + 2 * g, (uint32_t)(g + 1), m, n);
+        }
+        outputs12<MODE>(ip, 0, js.sm, js.sn, js.fm, js.fn, vec);
     }
 
     template <int MODE>
@@ -1486,7 +1737,7 @@ struct Consumer {
             JState ja, jb;
             {
                 R xm[V], xn[V];
-                if (!read_tile(ip, 0, xm, xn)) return;
+                read_tile(ip, 0, xm, xn);
                 R pm[V], pn[V], em, en, gm, gn, hm, hn;
                 scan_kj(lgS, xm, xn, xm, xn, pm, pn, em, en, gm, gn, ja.sm, ja.sn, ja.fm, ja.fn, hm, hn);
                 k_publish<MODE>(0, pm, pn, em, en, gm, gn);
@@ -1499,7 +1750,7 @@ struct Consumer {
             // w - 1 >= T: K tiles c+q, c+q+1; the J tile c is read again.
             for (int x = 1; x <= q; ++x) {
                 R xm[V], xn[V];
-                if (!read_tile(ip, x, xm, xn)) return;
+                read_tile(ip, x, xm, xn);
                 R pm[V], pn[V], em, en, gm, gn;
                 scan_k(lgS, xm, xn, pm, pn, em, en, gm, gn);
                 k_publish<MODE>(x, pm, pn, em, en, gm, gn);
@@ -1520,14 +1771,14 @@ struct Consumer {
                 R hm, hn;
                 if (kload) {
                     R km[V], kn[V], jm[V], jn[V];
-                    if (!read_tile(ip, xk, km, kn)) return;  // K tile c+q+1
-                    if (!read_tile(ip, c, jm, jn)) return;   // J tile c
+                    read_tile(ip, xk, km, kn);  // K tile c+q+1
+                    read_tile(ip, c, jm, jn);   // J tile c
                     R pm[V], pn[V], em, en, gm, gn;
                     scan_kj(lgS, km, kn, jm, jn, pm, pn, em, en, gm, gn, js.sm, js.sn, js.fm, js.fn, hm, hn);
                     k_publish<MODE>(xk, pm, pn, em, en, gm, gn);
                 } else {
                     R jm[V], jn[V];
-                    if (!read_tile(ip, c, jm, jn)) return;
+                    read_tile(ip, c, jm, jn);
                     scan_j(lgS, jm, jn, js.sm, js.sn, js.fm, js.fn, hm, hn);
                 }
                 if (lane == 0) S::jagg()[(c & 1) * NW + warp] = Elem<T>::pair(hm, hn);
@@ -1550,11 +1801,7 @@ struct Consumer {
     __device__ __forceinline__ bool read_tile_ext(const ItemPlan<T> &ip, int x, R (&xm)[V + G::HALO_MAX],
                                                   R (&xn)[V + G::HALO_MAX]) {
         constexpr int NE = V + G::HALO_MAX;
-        if (!mbar_wait_bounded(S::bar(warp, cur.stage), cur.phase)) {
-            report_error(S::params().status, kErrWaitTimeout);
-            failed = true;
-            return false;
-        }
+        const bool ok = wait_stage();  // as in read_tile: on failure the values are unspecified
         const int smode = S::issue(warp)->smode[cur.stage];
         const int mode = smode & 0xff;
         const uint8_t *sb = S::slice(warp, cur.stage);
@@ -1596,10 +1843,10 @@ struct Consumer {
             }
         }
         __syncwarp();
-        if (lane == 0) issue_next<T, KMODE>(warp);
+        if (lane == 0) issue_next<T, KMODE, FRONT>(warp);
         __syncwarp();
         cur.advance();
-        return true;
+        return ok;
     }
 
     // Windows of W elements straight from registers (the naive row of
@@ -1612,7 +1859,7 @@ struct Consumer {
         const int vec = out_vec(ip);
         for (int c = 0; c < ip.NC; ++c) {
             R am[NE], an[NE];
-            if (!read_tile_ext(ip, c, am, an)) return;
+            read_tile_ext(ip, c, am, an);
 #pragma unroll
             for (int p = 1; p < P2; p <<= 1) {
 #pragma unroll
@@ -1664,7 +1911,7 @@ struct Consumer {
         // ---------------- prologue: tile 0 (case A) or tiles 1..q (case B)
         if (!ip.caseB) {
             R pm[V], pn[V];
-            if (!read_tile(ip, 0, pm, pn)) return;
+            read_tile(ip, 0, pm, pn);
 #pragma unroll
             for (int i = 0; i < V; ++i) { Sc_m[i] = pm[i]; Sc_n[i] = pn[i]; }
             scan_tile<MODE>(ip, pm, pn, true, Sc_m, Sc_n, 0, -1);
@@ -1672,7 +1919,7 @@ struct Consumer {
         } else {
             for (int x = 1; x <= q; ++x) {
                 R pm[V], pn[V];
-                if (!read_tile(ip, x, pm, pn)) return;
+                read_tile(ip, x, pm, pn);
                 scan_tile<MODE>(ip, pm, pn, false, pm, pn, x % 3, -1);
                 if (x == q) ring_write(x, pm, pn);
                 sync();
@@ -1688,7 +1935,7 @@ struct Consumer {
             const bool kload = c + 1 < ip.NC || ip.klast;  // else no window reaches K tile xk
             if (!ip.caseB) {
                 if (kload) {
-                    if (!read_tile(ip, xk, pm, pn)) return;  // K tile c+1 (also J tile of c+1)
+                    read_tile(ip, xk, pm, pn);  // K tile c+1 (also J tile of c+1)
 #pragma unroll
                     for (int i = 0; i < V; ++i) { Sn_m[i] = pm[i]; Sn_n[i] = pn[i]; }
                     scan_tile<MODE>(ip, pm, pn, true, Sn_m, Sn_n, xk % 3, -1);
@@ -1701,8 +1948,8 @@ struct Consumer {
                     for (int i = 0; i < V; ++i) { Sc_m[i] = Sn_m[i]; Sc_n[i] = Sn_n[i]; }
                 }
             } else {
-                if (kload && !read_tile(ip, xk, pm, pn)) return;  // K tile c+q+1
-                if (!read_tile(ip, c, Sn_m, Sn_n)) return;        // J tile c
+                if (kload) read_tile(ip, xk, pm, pn);  // K tile c+q+1
+                read_tile(ip, c, Sn_m, Sn_n);          // J tile c
                 scan_tile<MODE>(ip, pm, pn, true, Sn_m, Sn_n, xk % 3, c & 1, kload);
                 if (kload) ring_write(xk, pm, pn);
                 sync();
@@ -1713,9 +1960,87 @@ struct Consumer {
     }
 };
 
+// Advancing front, at the start of the launch: CTA b publishes the
+// aggregates of global tiles b, b+G, ... inside [1, q+G) (the tiles no item
+// reads ahead), with plain loads; no wait comes before it.
+template <typename T>
+__device__ __forceinline__ void front_prologue(const BlockScanParams &P, int tid, int lane, int warp) {
+    using G = Geo<T>;
+    using R = typename Elem<T>::R;
+    using Pair = typename Elem<T>::Pair;
+    using S = Smem<T>;
+    const SeriesDesc &sd = P.one;
+    const T *in = reinterpret_cast<const T *>(P.in) + sd.in_off;
+    const int64_t end = ((sd.w - 1) >> G::LGT) + P.front_ahead;
+    for (int64_t x = blockIdx.x; x < end; x += gridDim.x) {
+        if (x == 0) continue;  // no window has tile 0 inside
+        R m = Elem<T>::lo(), n = Elem<T>::hi();
+        const int64_t base = sd.d + x * G::T_ + (int64_t)tid * G::V;
+#pragma unroll
+        for (int i = 0; i < G::V; ++i) {
+            const int64_t p = base + i;
+            if (p >= 0 && p < sd.n) {
+                const R v = Elem<T>::load(in[p]);
+                m = vmax(m, v);
+                n = vmin(n, v);
+            }
+        }
+#pragma unroll
+        for (int d = 16; d >= 1; d >>= 1) {
+            m = vmax(m, __shfl_xor_sync(0xffffffffu, m, d));
+            n = vmin(n, __shfl_xor_sync(0xffffffffu, n, d));
+        }
+        if (lane == 0) S::jagg()[warp] = Elem<T>::pair(m, n);
+        named_bar_sync(1, G::NT);
+        if (warp == 0) {
+            Pair a = lane < G::NW ? S::jagg()[lane] : Elem<T>::pair(Elem<T>::lo(), Elem<T>::hi());
+            m = Elem<T>::pmax(a);
+            n = Elem<T>::pmin(a);
+#pragma unroll
+            for (int d = G::NW / 2; d >= 1; d >>= 1) {
+                m = vmax(m, __shfl_xor_sync(0xffffffffu, m, d));
+                n = vmin(n, __shfl_xor_sync(0xffffffffu, n, d));
+            }
+            if (lane == 0) front_put<T>(P.front_slots + 2 * x, (uint32_t)(x + 1), m, n);
+        }
+        named_bar_sync(1, G::NT);
+    }
+}
+
+// The plan of round t of the advancing front (output tile t alone).
+template <typename T>
+__device__ __forceinline__ ItemPlan<T> front_plan(const BlockScanParams &P, int64_t t) {
+    using G = Geo<T>;
+    const SeriesDesc &sd = P.one;
+    ItemPlan<T> ip;
+    ip.series = 0;
+    ip.lb_acc = nullptr;
+    ip.in = reinterpret_cast<const T *>(P.in) + sd.in_off;
+    ip.omax = P.out_max ? reinterpret_cast<T *>(P.out_max) + sd.out_off : nullptr;
+    ip.omin = P.out_min ? reinterpret_cast<T *>(P.out_min) + sd.out_off : nullptr;
+    ip.n = sd.n;
+    ip.o_begin = t << G::LGT;
+    ip.o_end = ip.o_begin + G::T_ < sd.n_out ? ip.o_begin + G::T_ : sd.n_out;
+    ip.p0 = ip.o_begin + sd.d;
+    ip.s = (int)(sd.w - 1);
+    ip.q = ip.s >> G::LGT;
+    ip.caseB = 1;
+    ip.lgB = G::LGV + 5;
+    ip.mode = 2;
+    ip.NC = 1;
+    ip.klast = (int)(((ip.o_end - ip.o_begin - 1) + ip.s) >> G::LGT) >= 1 + ip.q;
+    ip.front = 1;
+    ip.gt0 = t;
+    ip.la = t + ip.q + gridDim.x <= P.front_last ? ip.q + (int)gridDim.x : 0;
+    ip.ok = 1;
+    return ip;
+}
+
 // One instantiation per block mode keeps each one within 128 registers (two
-// CTAs per SM); an item whose mode differs is rejected (kErrBadItem).
-template <typename T, int MODE, bool LB = false>
+// CTAs per SM); an item whose mode differs is rejected (kErrBadItem).  FRONT:
+// the advancing front of one series (mode 2, windows of a tile or more; a
+// cooperative launch), see run_front_round.
+template <typename T, int MODE, bool LB = false, bool FRONT = false>
 __global__ void __launch_bounds__(Geo<T>::NT, (Geo<T>::NT * Elem<T>::V == 4096 && MODE != 3) ? 1 : 2)
     blockscan_kernel(const BlockScanParams P) {
     using S = Smem<T>;
@@ -1726,8 +2051,12 @@ __global__ void __launch_bounds__(Geo<T>::NT, (Geo<T>::NT * Elem<T>::V == 4096 &
         *reinterpret_cast<BlockScanParams *>(S::misc() + Geo<T>::off_params) = P;
         if (P.ticket) {
             // Items for sequence numbers 0..kStages: enough for every warp's
-            // prefetch until the first item boundary.
-            for (; fetched <= kStages; ++fetched) S::queue()[fetched & (kQueue - 1)] = atomicAdd(P.ticket, 1);
+            // prefetch until the first item boundary (items of one load).  In
+            // the advancing front every item has at least two loads, so the
+            // prefetch reaches at most two items ahead: three tickets keep
+            // the CTA's items close to the front.
+            const int nq = P.front_slots ? 3 : kStages + 1;
+            for (; fetched < nq; ++fetched) S::queue()[fetched & (kQueue - 1)] = atomicAdd(P.ticket, 1);
         }
     }
     if (lane == 0) {
@@ -1743,18 +2072,42 @@ __global__ void __launch_bounds__(Geo<T>::NT, (Geo<T>::NT * Elem<T>::V == 4096 &
         wi.q = wi.caseB = wi.ok = wi.NC = wi.klast = 0;
         wi.linear = 0;
         wi.issued = 0;
+        for (int s = 0; s < kStages; ++s) wi.smode[s] = 3;  // empty until a copy is issued
+        if constexpr (FRONT) {
+            // The CTA's rounds, four loads each.
+            const int64_t tiles = (P.one.n_out + Geo<T>::T_ - 1) >> Geo<T>::LGT;
+            const int64_t rounds = tiles > blockIdx.x ? (tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+            wi.nloads = (int32_t)(4 * rounds);
+            wi.q = (int32_t)((P.one.w - 1) >> Geo<T>::LGT);
+        }
+        // Test hook: a warp whose sequence has ended issues nothing, so every
+        // wait of the kernel runs out.
+        if (P.test_flags & kTestStarveCopies) wi.nloads = -1;
         fence_mbar_init();
     }
     __syncthreads();
     if (lane == 0)
-        for (int s = 0; s < kStages; ++s) issue_next<T, MODE>(warp);
+        for (int s = 0; s < kStages; ++s) issue_next<T, MODE, FRONT>(warp);
     __syncwarp();
 
-    Consumer<T, MODE, LB> cs;
+    Consumer<T, MODE, LB, FRONT> cs;
     cs.tid = tid;
     cs.lane = lane;
     cs.warp = warp;
     const BlockScanParams &PS = S::params();
+    cs.wait_limit = PS.wait_limit > 0 ? PS.wait_limit : kWaitLimitCycles;
+    if constexpr (FRONT) {
+        static_assert(MODE == 2 && kCarryRing<T> && !LB, "the advancing front is a mode-2 storing kernel");
+        front_prologue<T>(P, tid, lane, warp);
+        // Round plans from the launch parameters themselves (constant bank).
+        const int64_t tiles = (P.one.n_out + Geo<T>::T_ - 1) >> Geo<T>::LGT;
+        const int vec = cs.out_vec(front_plan<T>(P, 0));  // the same for every round (whole vectors apart)
+        for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+            cs.run_front_round(front_plan<T>(P, t), vec);
+            cs.sync();  // the rings are rewritten by the next round
+        }
+        if (named_bar_sync_or(2, Geo<T>::NT, cs.failed)) cs.drain();
+    } else {
     for (int seq = 0;; ++seq) {
         const int64_t item = item_of<T>(PS, seq);
         if (item >= PS.n_items || item < 0) return;
@@ -1769,30 +2122,35 @@ __global__ void __launch_bounds__(Geo<T>::NT, (Geo<T>::NT * Elem<T>::V == 4096 &
         ItemPlan<T> ip = make_plan<T>(PS, item, MODE);
         if (!ip.ok) {
             // A rejected item occupies one empty stage per warp.
-            if (!mbar_wait_bounded(S::bar(warp, cs.cur.stage), cs.cur.phase)) {
-                report_error(P.status, kErrWaitTimeout);
-                return;
-            }
+            cs.wait_stage();
             __syncwarp();
             if (lane == 0) issue_next<T, MODE>(warp);
             __syncwarp();
             cs.cur.advance();
         } else {
+            // After a failed wait every lane still finishes the item, without
+            // waiting again (its outputs are then unspecified).
             if constexpr (MODE == 3)
                 cs.run_item_slide(ip);
             else if constexpr (MODE == 0 || !kCarryRing<T>)
                 cs.template run_item<MODE>(ip);
             else
                 cs.template run_item12<MODE>(ip);
-            if (cs.failed) return;
         }
         if (nser >= 0) prefetch_l1(PS.series + nser);
-        // The item boundary frees the ring and publishes the queue.
+        // The item boundary frees the ring and publishes the queue.  Every
+        // warp arrives here, failed or not; if any warp failed, all leave
+        // together (after their copies in flight have landed).  The barrier
+        // itself ORs the flags, so every warp takes the same decision.
         if (tid == 0 && PS.ticket) {
             S::queue()[fetched & (kQueue - 1)] = tk;
             ++fetched;
         }
-        named_bar_sync(1, Geo<T>::NT);
+        if (named_bar_sync_or(2, Geo<T>::NT, cs.failed)) {  // its own id: barrier 1 is only bar.sync
+            cs.drain();
+            return;
+        }
+    }
     }
 }
 

@@ -1,6 +1,7 @@
 // C ABI of the library (declared in include/mmf.h): argument checking, dtype
 // dispatch, kernel selection and error reporting.  No C++ exception crosses
 // this boundary; failures return an mmf_status and set a thread-local message.
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -110,6 +111,15 @@ mmf_status make_series(int64_t n, int64_t w_or_r, mmf_mode mode, mmf_dtype dt, S
     return MMF_OK;
 }
 
+static std::atomic<uint32_t> g_test_flags{0};
+static std::atomic<long long> g_test_wait_limit{0};
+
+TestHooks test_hooks() {
+    return TestHooks{g_test_flags.load(std::memory_order_relaxed), g_test_wait_limit.load(std::memory_order_relaxed)};
+}
+
+mmf_kernel dispatch_lookup(mmf_dtype dt, int64_t n, int64_t w);  // dispatch.cu
+
 template <typename F> mmf_status dispatch_dtype(mmf_dtype dt, F &&f) {
     switch (dt) {
         case MMF_F32: return f(float{});
@@ -132,6 +142,7 @@ const char *mmf_version(void) { return "mmf-gb300 0.1 (sm_103a)"; }
 
 mmf_status mmf_argfilter1d_ex(const void *d_in, int64_t n, int64_t w, mmf_dtype dtype, void *d_max, void *d_min,
                               int64_t *d_argmax, int64_t *d_argmin, void *stream, mmf_kernel kernel) {
+    NvtxRange nvtx_range("mmf_argfilter1d_ex");
     if (elem_size(dtype) == 0) return set_error(MMF_EINVAL, "unknown dtype %d", (int)dtype);
     if (kernel != MMF_KERNEL_AUTO && kernel != MMF_KERNEL_BLOCKSCAN && kernel != MMF_KERNEL_WEDGE)
         return set_error(MMF_ENOTIMPL, "kernel %d does not compute locations", (int)kernel);
@@ -169,6 +180,7 @@ mmf_status mmf_argfilter1d(const void *d_in, int64_t n, int64_t w, mmf_dtype dty
 
 mmf_status mmf_filter1d_w3(const void *d_in, int64_t n, mmf_dtype dtype, void *d_max, void *d_min,
                            unsigned long long *d_ncmp, void *stream) {
+    NvtxRange nvtx_range("mmf_filter1d_w3");
     const int esz = elem_size(dtype);
     if (esz == 0) return set_error(MMF_EINVAL, "unknown dtype %d", (int)dtype);
     if (n < 0) return set_error(MMF_EINVAL, "n = %lld", (long long)n);
@@ -197,6 +209,7 @@ int64_t mmf_output_length(int64_t n, int64_t w_or_r, mmf_mode mode) {
 
 mmf_status mmf_filter1d_ex(const void *d_in, int64_t n, int64_t w_or_r, mmf_dtype dtype, mmf_mode mode,
                            void *d_max, void *d_min, void *stream, mmf_kernel kernel) {
+    NvtxRange nvtx_range("mmf_filter1d_ex");
     if (elem_size(dtype) == 0) return set_error(MMF_EINVAL, "unknown dtype %d", (int)dtype);
     SeriesDesc sd;
     mmf_status st = make_series(n, w_or_r, mode, dtype, &sd);
@@ -211,6 +224,25 @@ mmf_status mmf_filter1d_ex(const void *d_in, int64_t n, int64_t w_or_r, mmf_dtyp
     st = get_ctx(stream, &ctx);
     if (st != MMF_OK) return st;
     const int slide_max = dtype == MMF_F32 ? 17 : 9;
+    if (kernel == MMF_KERNEL_AUTO) {
+        // A tuned entry of the dispatch table replaces the built-in rule
+        // where its kernel can take this call.
+        const mmf_kernel k = dispatch_lookup(dtype, n, sd.w);
+        bool ok = false;
+        switch (k) {
+            case MMF_KERNEL_SLIDE: ok = sd.w <= slide_max; break;
+            case MMF_KERNEL_BLOCKSCAN: ok = true; break;
+            case MMF_KERNEL_WEDGE: ok = mode == MMF_VALID && sd.w <= MMF_WEDGE_MAX_WINDOW; break;
+            case MMF_KERNEL_FRONT:
+                ok = dispatch_dtype(dtype, [&](auto tag) -> mmf_status {
+                         using T = decltype(tag);
+                         return front_applies<T>(sd, ctx.sms, 1) ? MMF_OK : MMF_ENOTIMPL;
+                     }) == MMF_OK;
+                break;
+            default: break;
+        }
+        if (ok) kernel = k;
+    }
     if (kernel == MMF_KERNEL_SLIDE && sd.w > slide_max)
         return set_error(MMF_EINVAL, "the register slide handles windows up to %d (w = %lld)", slide_max,
                          (long long)sd.w);
@@ -224,12 +256,16 @@ mmf_status mmf_filter1d_ex(const void *d_in, int64_t n, int64_t w_or_r, mmf_dtyp
             return e == cudaSuccess ? MMF_OK : cuda_error(e, "wedge launch");
         });
     }
-    if (kernel != MMF_KERNEL_AUTO && kernel != MMF_KERNEL_BLOCKSCAN && kernel != MMF_KERNEL_SLIDE)
+    if (kernel != MMF_KERNEL_AUTO && kernel != MMF_KERNEL_BLOCKSCAN && kernel != MMF_KERNEL_SLIDE &&
+        kernel != MMF_KERNEL_FRONT)
         return set_error(MMF_ENOTIMPL, "kernel %d not available", (int)kernel);
-    const bool allow_slide = kernel != MMF_KERNEL_BLOCKSCAN;
+    const bool allow_slide = kernel != MMF_KERNEL_BLOCKSCAN && kernel != MMF_KERNEL_FRONT;
+    const int front = kernel == MMF_KERNEL_FRONT ? 1 : (kernel == MMF_KERNEL_AUTO ? -1 : 0);
     return dispatch_dtype(dtype, [&](auto tag) -> mmf_status {
         using T = decltype(tag);
-        cudaError_t e = blockscan_1d<T>(ctx, d_in, sd, d_max, d_min, allow_slide);
+        if (front == 1 && !front_applies<T>(sd, ctx.sms, 1))
+            return set_error(MMF_ENOTIMPL, "the advancing front takes windows of a tile or more, not f64");
+        cudaError_t e = blockscan_1d<T>(ctx, d_in, sd, d_max, d_min, allow_slide, front);
         return e == cudaSuccess ? MMF_OK : cuda_error(e, "filter launch");
     });
 }
@@ -237,6 +273,19 @@ mmf_status mmf_filter1d_ex(const void *d_in, int64_t n, int64_t w_or_r, mmf_dtyp
 mmf_status mmf_filter1d(const void *d_in, int64_t n, int64_t w_or_r, mmf_dtype dtype, mmf_mode mode, void *d_max,
                         void *d_min, void *stream) {
     return mmf_filter1d_ex(d_in, n, w_or_r, dtype, mode, d_max, d_min, stream, MMF_KERNEL_AUTO);
+}
+
+mmf_status mmf_test_set_wait_fault(int starve_copies, int64_t wait_limit_cycles) {
+    if (starve_copies) {
+        if (wait_limit_cycles < 1000 || wait_limit_cycles > 2000000000LL)
+            return set_error(MMF_EINVAL, "wait limit %lld outside [1000, 2e9] clocks", (long long)wait_limit_cycles);
+        g_test_wait_limit.store(wait_limit_cycles);
+        g_test_flags.store(kTestStarveCopies);
+    } else {
+        g_test_flags.store(0);
+        g_test_wait_limit.store(0);
+    }
+    return MMF_OK;
 }
 
 mmf_status mmf_device_status(uint32_t *out, int reset) {

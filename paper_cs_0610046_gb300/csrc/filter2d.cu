@@ -234,6 +234,7 @@ mmf_status mmf_filter2d_workspace(int64_t nimg, int64_t H, int64_t W, int64_t wy
 mmf_status mmf_filter2d_separable(const void *d_in, int64_t nimg, int64_t H, int64_t W, int64_t pitch, int64_t wy,
                                   int64_t wx, mmf_dtype dtype, int fuse, void *d_max, void *d_min, void *d_work,
                                   size_t work_bytes, void *stream) {
+    NvtxRange nvtx_range("mmf_filter2d_separable");
     mmf_status st = check2d(nimg, H, W, pitch, wy, wx, dtype, fuse);
     if (st != MMF_OK) return st;
     const int64_t Ho = H - wy + 1, Wo = W - wx + 1;

@@ -95,6 +95,7 @@ cudaError_t run_chunk(const LaunchCtx &ctx, const void *in, const SeriesDesc &sd
 
 extern "C" mmf_status mmf_filter1d_host(const void *h_in, int64_t n, int64_t w_or_r, mmf_dtype dtype, mmf_mode mode,
                                         void *h_max, void *h_min, int64_t chunk, void *stream) {
+    NvtxRange nvtx_range("mmf_filter1d_host");
     const int esz = elem_size(dtype);
     if (esz == 0) return set_error(MMF_EINVAL, "unknown dtype %d", (int)dtype);
     SeriesDesc whole;

@@ -3,10 +3,21 @@
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "blockscan.cuh"
 
 namespace mmf {
+
+// NVTX range over the rest of the enclosing scope: each C-ABI call and each
+// server batch shows as a named range in a profiler's timeline (NVTX v3 is
+// header-only; without an attached tool a range costs a pointer test).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 struct LaunchCtx {
     int device;
@@ -15,12 +26,32 @@ struct LaunchCtx {
     cudaStream_t stream;
 };
 
+// Test hook of the block-scan kernels (mmf_test_set_wait_fault): flags and
+// wait bound copied into every launch's parameters.
+struct TestHooks {
+    uint32_t flags;        // kTestStarveCopies or 0
+    long long wait_limit;  // SM clocks; 0: the default bound
+};
+TestHooks test_hooks();
+inline void apply_test_hooks(BlockScanParams &P) {
+    const TestHooks h = test_hooks();
+    P.test_flags = h.flags;
+    P.wait_limit = h.wait_limit;
+}
+
 // One series, statically split into per-CTA items (no allocation).  With
 // allow_slide, small windows (w <= 17 for f32, 9 otherwise) use the register slide
 // instead of block scans.
+// front: -1 automatic, 0 per-CTA ranges, 1 one advancing front (windows of a
+// tile or more, f32/i16/u8; it takes a small stream-ordered workspace of
+// published tile aggregates).
 template <typename T>
 cudaError_t blockscan_1d(const LaunchCtx &ctx, const void *in, const SeriesDesc &sd, void *omax, void *omin,
-                         bool allow_slide);
+                         bool allow_slide, int front = -1);
+
+// Whether blockscan_1d takes the advancing front for this series (front as
+// above; the automatic choice does not take it).
+template <typename T> bool front_applies(const SeriesDesc &sd, int sms, int front);
 
 // The same series description applied to `rows` rows at the given element
 // pitches (row pass of the 2D filter); items are generated arithmetically.

@@ -57,10 +57,13 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t pari
     return ok != 0;
 }
 
+// Default bound of a pipeline wait: about 2 s of SM clock.
+constexpr long long kWaitLimitCycles = 4000000000LL;
+
 // Wait for the phase with the given parity to complete, giving up after
 // roughly `limit_cycles` SM clocks.  Returns false on timeout.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
-                                                  long long limit_cycles = 4000000000LL) {
+                                                  long long limit_cycles = kWaitLimitCycles) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait_sleep(bar, parity, 20000u)) {
@@ -109,6 +112,22 @@ __device__ __forceinline__ void prefetch_l2(const void *p) {
 // Named barrier over `nthreads` threads (a multiple of 32), id 1..15.
 __device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Named barrier that also ORs a predicate over the participating threads:
+// every thread receives the same result, taken at the barrier itself, so a
+// decision based on it (leave the work item) is the same for all of them.
+__device__ __forceinline__ bool named_bar_sync_or(int id, int nthreads, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
 }
 
 __device__ __forceinline__ void report_error(uint32_t *status, uint32_t bits) {

@@ -208,6 +208,7 @@ cudaError_t launch_halo(mmf_server *S, int slot, int n, cudaStream_t st) {
 // With S->mu held: admit one batch and enqueue its work (the lock is dropped
 // around the CUDA calls).  Returns false if nothing could be admitted.
 bool run_batch(mmf_server *S, std::unique_lock<std::mutex> &lk) {
+    NvtxRange nvtx_range("mmf_server_batch");
     const int slot = (int)(S->nbatches % kSlots);
     // The slot's pinned tables and device tables are reused: wait for the
     // batch that last used this slot to have finished its uploads.
@@ -586,6 +587,7 @@ extern "C" {
 
 mmf_status mmf_stream_push(mmf_server *S, uint64_t stream_id, const void *h_chunk, int64_t len, void *h_max,
                            void *h_min, int64_t *n_out, uint64_t *ticket) {
+    NvtxRange nvtx_range("mmf_stream_push");
     if (!S || !ticket) return set_error(MMF_EINVAL, "NULL argument");
     mmf_status st;
     {
@@ -599,6 +601,7 @@ mmf_status mmf_stream_push(mmf_server *S, uint64_t stream_id, const void *h_chun
 mmf_status mmf_stream_push_batch(mmf_server *S, int64_t count, const uint64_t *stream_ids,
                                  const void *const *h_chunks, const int64_t *lens, void *const *h_max,
                                  void *const *h_min, int64_t *n_out, uint64_t *tickets, int64_t *n_done) {
+    NvtxRange nvtx_range("mmf_stream_push_batch");
     if (!S || count < 0 || (count > 0 && (!stream_ids || !h_chunks || !lens || !tickets)))
         return set_error(MMF_EINVAL, "NULL argument");
     mmf_status st = MMF_OK;
@@ -755,6 +758,7 @@ extern "C" {
 
 mmf_status mmf_stream_snapshot(mmf_server *S, uint64_t stream_id, void *h_buf, size_t buf_bytes, size_t *size,
                                int timeout_ms) {
+    NvtxRange nvtx_range("mmf_stream_snapshot");
     if (!S || !size) return set_error(MMF_EINVAL, "NULL argument");
     std::unique_lock<std::mutex> lk(S->mu);
     StreamState ss;
@@ -773,6 +777,7 @@ mmf_status mmf_stream_snapshot(mmf_server *S, uint64_t stream_id, void *h_buf, s
 
 mmf_status mmf_stream_snapshot_wedge(mmf_server *S, uint64_t stream_id, void *h_buf, size_t buf_bytes, size_t *size,
                                      int timeout_ms) {
+    NvtxRange nvtx_range("mmf_stream_snapshot_wedge");
     if (!S || !size) return set_error(MMF_EINVAL, "NULL argument");
     std::unique_lock<std::mutex> lk(S->mu);
     StreamState ss;
@@ -811,6 +816,7 @@ mmf_status mmf_stream_snapshot_wedge(mmf_server *S, uint64_t stream_id, void *h_
 }
 
 mmf_status mmf_stream_restore(mmf_server *S, const void *h_buf, size_t buf_bytes, uint64_t *stream_id) {
+    NvtxRange nvtx_range("mmf_stream_restore");
     if (!S || !h_buf || !stream_id) return set_error(MMF_EINVAL, "NULL argument");
     if (buf_bytes < sizeof(SnapshotHeader)) return set_error(MMF_EINVAL, "snapshot shorter than its header");
     SnapshotHeader hd;

@@ -169,3 +169,14 @@ def test_binding_refuses_host_tensors_for_device_calls():
             call()
     with pytest.raises(TypeError):
         mmf.filter1d(torch.arange(100, dtype=torch.int32), 3)  # an unsupported type as well
+
+
+def test_wait_fault_hook_checks_its_bound(lib):
+    """The timeout test hook takes a bound of 1000 .. 2e9 clocks and can always
+    be switched off (host-side state only; no CUDA call)."""
+    f = lib.mmf_test_set_wait_fault
+    f.argtypes = [ctypes.c_int, ctypes.c_int64]
+    f.restype = ctypes.c_int
+    assert f(1, 10) == 1 and f(1, 3_000_000_000) == 1
+    assert f(1, 200_000) == 0
+    assert f(0, 0) == 0
