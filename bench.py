@@ -511,7 +511,9 @@ def serving_extras(dev, nstreams=10_000, seed=51, duration=0.5,
         rows.append({"offered_chunks_s": rate, "offered_Gelem_s": rate * float(clen.mean()) / 1e9,
                      "achieved_Gelem_s": elems / (t1 - t0) / 1e9, "chunks": int(t_rel.size),
                      "push_calls": len(tickets), "push_s": push_end - t0, "p50_ms": st["p50_ms"],
-                     "p99_ms": st["p99_ms"], "max_ms": st["max_ms"], "batches": st["batches"]})
+                     "p99_ms": st["p99_ms"], "max_ms": st["max_ms"], "batches": st["batches"],
+                     "p99_queue_ms": st["p99_queue_ms"], "p99_service_ms": st["p99_service_ms"],
+                     "max_hold_ms": st["max_hold_ms"]})
         if (t1 - t0) > 1.5 * duration:  # the service no longer keeps up
             break
     srv.close()

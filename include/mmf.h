@@ -332,6 +332,10 @@ typedef struct {
     double max_ms;
     int64_t queued;             /* chunks waiting for admission now */
     int64_t device_bytes_used;  /* budget in use now */
+    double p50_queue_ms, p99_queue_ms;     /* push to admission into a batch */
+    double p50_service_ms, p99_service_ms; /* admission to completion */
+    double max_hold_ms;         /* longest time the worker held the server
+                                   lock while setting up one batch */
 } mmf_server_stats_t;
 
 /* device_budget_bytes: one device allocation shared by stream state, chunk

@@ -426,7 +426,10 @@ def filter2d(x: torch.Tensor, wy: int, wx: int, fuse: int = -1, out_max=None, ou
 class ServerStats(ctypes.Structure):
     _fields_ = [("chunks", ctypes.c_int64), ("elements", ctypes.c_int64), ("batches", ctypes.c_int64),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
-                ("queued", ctypes.c_int64), ("device_bytes_used", ctypes.c_int64)]
+                ("queued", ctypes.c_int64), ("device_bytes_used", ctypes.c_int64),
+                ("p50_queue_ms", ctypes.c_double), ("p99_queue_ms", ctypes.c_double),
+                ("p50_service_ms", ctypes.c_double), ("p99_service_ms", ctypes.c_double),
+                ("max_hold_ms", ctypes.c_double)]
 
 
 _NP_DTYPES = {"float32": 0, "float64": 1, "int16": 2, "uint8": 3}

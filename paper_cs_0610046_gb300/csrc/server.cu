@@ -109,7 +109,8 @@ struct Request {
     void *h_max, *h_min;
     int64_t n_out;
     bool direct;  // the GPU can read/write these host buffers itself
-    Clock::time_point released;
+    Clock::time_point released;  // pushed
+    Clock::time_point admitted;  // taken into a batch
 };
 
 struct StreamState {
@@ -166,7 +167,9 @@ struct mmf_server {
     ChunkCopy *h_copy[kSlots] = {};
     bool pageable_ok = false;  // the device can access pageable host memory
     uint64_t nbatches = 0;
-    std::vector<double> lat_ms;
+    std::vector<double> lat_ms, queue_ms, service_ms;  // per chunk: push to completion, push to admission, admission to completion
+    double max_hold_ms = 0.0;  // longest stretch the worker held the lock in one batch's set-up
+    cudaEvent_t slot_done[kSlots] = {};  // completion of the batch on each slot (reused, never created per batch)
     int64_t done_chunks = 0, done_elems = 0;
 };
 
@@ -209,6 +212,7 @@ cudaError_t launch_halo(mmf_server *S, int slot, int n, cudaStream_t st) {
 // around the CUDA calls).  Returns false if nothing could be admitted.
 bool run_batch(mmf_server *S, std::unique_lock<std::mutex> &lk) {
     NvtxRange nvtx_range("mmf_server_batch");
+    const auto t_lock = Clock::now();
     const int slot = (int)(S->nbatches % kSlots);
     // The slot's pinned tables and device tables are reused: wait for the
     // batch that last used this slot to have finished its uploads.
@@ -245,6 +249,7 @@ bool run_batch(mmf_server *S, std::unique_lock<std::mutex> &lk) {
         ss.count += it->len;
         ss.halo_len = std::min<int64_t>(ss.count, ss.w - 1);
         b.halo_after.push_back(ss.halo_len);
+        b.reqs.back().admitted = t_lock;
         it = S->queue.erase(it);
     }
     if (b.reqs.empty()) return false;
@@ -276,6 +281,7 @@ bool run_batch(mmf_server *S, std::unique_lock<std::mutex> &lk) {
     }
     for (int i = 0; i < n; ++i)
         if (b.reqs[i].n_out > 0) S->h_items[slot][pos[modes[i]]++] = {i, 0, b.reqs[i].n_out};
+    S->max_hold_ms = std::max(S->max_hold_ms, std::chrono::duration<double, std::milli>(Clock::now() - t_lock).count());
     lk.unlock();
 
     cudaStream_t st = S->slots[slot];
@@ -357,7 +363,10 @@ bool run_batch(mmf_server *S, std::unique_lock<std::mutex> &lk) {
         if (e == cudaSuccess && r.h_min)
             e = cudaMemcpyAsync(r.h_min, omin + out_off[i], r.n_out * esz, cudaMemcpyDeviceToHost, st);
     }
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming);
+    // The slot's completion event: the batch that used this slot before was
+    // retired (at most kSlots - 1 batches are in flight when one starts, and
+    // batches retire in order), so the event is free to record again.
+    b.done = S->slot_done[slot];
     if (e == cudaSuccess) e = cudaEventRecord(b.done, st);
     lk.lock();
     if (e != cudaSuccess) {
@@ -386,11 +395,12 @@ void retire(mmf_server *S) {
             }
             S->tickets[r.ticket] = q == cudaSuccess ? kTicketDone : kTicketFailed;
             S->lat_ms.push_back(std::chrono::duration<double, std::milli>(now - r.released).count());
+            S->queue_ms.push_back(std::chrono::duration<double, std::milli>(r.admitted - r.released).count());
+            S->service_ms.push_back(std::chrono::duration<double, std::milli>(now - r.admitted).count());
             S->done_chunks++;
             S->done_elems += r.len;
         }
         if (q != cudaSuccess) S->failed = MMF_ECUDA;
-        if (b.done) cudaEventDestroy(b.done);
         S->inflight.pop_front();
         S->cv_done.notify_all();
     }
@@ -458,6 +468,7 @@ mmf_status mmf_server_create(size_t device_budget_bytes, int max_batch, mmf_dtyp
     for (int k = 0; k < kSlots && e == cudaSuccess; ++k) {
         e = cudaStreamCreateWithFlags(&S->slots[k], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->slot_free[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->slot_done[k], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaMalloc(&S->d_series[k], max_batch * sizeof(SeriesDesc));
         if (e == cudaSuccess) e = cudaMalloc(&S->d_items[k], max_batch * sizeof(ItemDesc));
         if (e == cudaSuccess) e = cudaMalloc(&S->d_halo[k], 2 * max_batch * sizeof(int64_t));
@@ -487,6 +498,12 @@ mmf_status mmf_server_create(size_t device_budget_bytes, int max_batch, mmf_dtyp
             case MMF_U8: blockscan_prepare<uint8_t>(S->device, g); break;
         }
     }
+    // Room for many outstanding tickets and latency samples up front, so that
+    // neither rehashes nor regrows under the lock while chunks stream in.
+    S->tickets.reserve(1 << 20);
+    S->lat_ms.reserve(1 << 20);
+    S->queue_ms.reserve(1 << 20);
+    S->service_ms.reserve(1 << 20);
     S->worker = std::thread(worker_main, S);
     *out = S;
     return MMF_OK;
@@ -505,6 +522,7 @@ void mmf_server_destroy(mmf_server *S) {
         if (S->slots[k]) cudaStreamSynchronize(S->slots[k]);
         if (S->slots[k]) cudaStreamDestroy(S->slots[k]);
         if (S->slot_free[k]) cudaEventDestroy(S->slot_free[k]);
+        if (S->slot_done[k]) cudaEventDestroy(S->slot_done[k]);
         if (S->d_series[k]) cudaFree(S->d_series[k]);
         if (S->d_items[k]) cudaFree(S->d_items[k]);
         if (S->d_halo[k]) cudaFree(S->d_halo[k]);
@@ -895,19 +913,28 @@ mmf_status mmf_server_pause(mmf_server *S, int paused) {
 mmf_status mmf_server_stats(mmf_server *S, int reset, mmf_server_stats_t *out) {
     if (!S || !out) return set_error(MMF_EINVAL, "NULL argument");
     std::lock_guard<std::mutex> lk(S->mu);
-    std::vector<double> v = S->lat_ms;
-    std::sort(v.begin(), v.end());
-    auto pct = [&](double p) { return v.empty() ? 0.0 : v[std::min(v.size() - 1, (size_t)(p * (v.size() - 1) + 0.5))]; };
+    auto pct = [](std::vector<double> v, double p) {
+        std::sort(v.begin(), v.end());
+        return v.empty() ? 0.0 : v[std::min(v.size() - 1, (size_t)(p * (v.size() - 1) + 0.5))];
+    };
     out->chunks = S->done_chunks;
     out->elements = S->done_elems;
     out->batches = (int64_t)S->nbatches;
-    out->p50_ms = pct(0.50);
-    out->p99_ms = pct(0.99);
-    out->max_ms = v.empty() ? 0.0 : v.back();
+    out->p50_ms = pct(S->lat_ms, 0.50);
+    out->p99_ms = pct(S->lat_ms, 0.99);
+    out->max_ms = pct(S->lat_ms, 1.0);
     out->queued = (int64_t)S->queue.size();
     out->device_bytes_used = (int64_t)(S->stage.used() + 2 * S->out.used());
+    out->p50_queue_ms = pct(S->queue_ms, 0.50);
+    out->p99_queue_ms = pct(S->queue_ms, 0.99);
+    out->p50_service_ms = pct(S->service_ms, 0.50);
+    out->p99_service_ms = pct(S->service_ms, 0.99);
+    out->max_hold_ms = S->max_hold_ms;
     if (reset) {
         S->lat_ms.clear();
+        S->queue_ms.clear();
+        S->service_ms.clear();
+        S->max_hold_ms = 0.0;
         S->done_chunks = S->done_elems = 0;
         S->nbatches = 0;
     }

@@ -80,6 +80,9 @@ def test_chunked_equals_whole_array(mmf):
         assert np.array_equal(gm, em) and np.array_equal(gn, en), (len(data), w)
     assert st["chunks"] == sum(len(c) for _, _, c in streams)
     assert st["p99_ms"] >= st["p50_ms"] > 0
+    # Latency splits into the wait for admission and the batch's service.
+    assert st["p99_service_ms"] >= st["p50_service_ms"] > 0 and st["p99_queue_ms"] >= st["p50_queue_ms"] >= 0
+    assert st["p50_queue_ms"] + st["p50_service_ms"] <= 2 * st["p99_ms"] and st["max_hold_ms"] >= 0
 
 
 def test_alone_equals_in_the_mix(mmf):
