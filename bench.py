@@ -657,7 +657,7 @@ def main():
         k["windows"].add(w)
     dom = max(per_k, key=lambda m: per_k[m]["ms"])
     kd = per_k[dom]
-    kname = f"mmf::blockscan_kernel<float, {dom}, false>"
+    kname = f"mmf::blockscan_kernel<float, {dom}, false, false>"
     achieved = kd["bytes"] / (kd["ms"] * 1e-3) / 1e9
     tr = _traffic().get(kname)
     traffic = None
