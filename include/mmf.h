@@ -461,8 +461,10 @@ mmf_status mmf_filter1d_batched_noalloc(const void *d_in, const int64_t *h_len, 
 /* --------------------------------------------------------- device status */
 
 /* Reads (and, if reset != 0, clears) the device status word that kernels set
- * when a bounded wait runs out (bit 0: pipeline wait timeout).  Synchronises
- * the current device.  Returns MMF_OK and writes the word to *out. */
+ * when a bounded wait runs out (bit 0: pipeline wait timeout; bit 1: a work
+ * item of another kernel group; bit 2, range-checked builds only: an index
+ * outside the launch's buffers, whose access was skipped).  Synchronises the
+ * current device.  Returns MMF_OK and writes the word to *out. */
 mmf_status mmf_device_status(uint32_t *out, int reset);
 
 /* Test hook for the device-side timeout path of the block-scan kernels (the
@@ -476,6 +478,15 @@ mmf_status mmf_device_status(uint32_t *out, int reset);
  * flight and the context stays usable.  starve_copies == 0 restores normal
  * operation.  For tests only. */
 mmf_status mmf_test_set_wait_fault(int starve_copies, int64_t wait_limit_cycles);
+
+/* Test hook for the range-checked build (MMF_CHECKED, see build.py): with
+ * elems > 0, block-scan launches afterwards tell their kernels that at most
+ * `elems` input elements may be read, below what they actually read; the
+ * checked kernels then skip the copies and loads past that bound and record
+ * bit 2 of the device status word (the skipped bytes are still inside the
+ * caller's buffer, so nothing outside it is touched either way).  0 restores
+ * normal operation.  For tests only. */
+mmf_status mmf_test_set_input_clip(int64_t elems);
 
 /* Thread-local, NUL-terminated description of the last failure. */
 const char *mmf_last_error(void);

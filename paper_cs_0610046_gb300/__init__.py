@@ -21,7 +21,8 @@ __all__ = ["MMFError", "load", "filter1d", "filter1d_host", "filter1d_w3", "argf
            "device_status", "set_wait_fault", "dispatch_set", "dispatch_get", "dispatch_autotune", "BatchPlan", "filter2d", "Server", "n_outputs", "DTYPES", "KERNELS"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libmmf.so")
+# MMF_CHECKED=1 selects the range-checked build (see build.py).
+LIB_PATH = os.path.join(_HERE, "libmmf_checked.so" if os.environ.get("MMF_CHECKED") == "1" else "libmmf.so")
 
 MMF_OK = 0
 STATUS_NAMES = {0: "MMF_OK", 1: "MMF_EINVAL", 2: "MMF_ENOMEM", 3: "MMF_ECUDA", 4: "MMF_EBUSY",
@@ -107,6 +108,7 @@ _EXTRA_SIGNATURES: dict = {
     "mmf_stream_restore": ([_VP, _VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint64)], _INT),
     "mmf_server_pause": ([_VP, _INT], _INT),
     "mmf_test_set_wait_fault": ([_INT, _I64], _INT),
+    "mmf_test_set_input_clip": ([_I64], _INT),
     "mmf_dispatch_set": ([_INT, _I64, _I64, _INT], _INT),
     "mmf_dispatch_get": ([_INT, _I64, _I64, ctypes.POINTER(_INT)], _INT),
     "mmf_dispatch_autotune": ([_VP, _I64, _I64, _INT, _VP, _VP, _VP, ctypes.POINTER(_INT)], _INT),

@@ -3,6 +3,12 @@
 Each ``csrc/*.cu`` translation unit is compiled in parallel and linked into
 ``paper_cs_0610046_gb300/libmmf.so``.  Run ``python -m
 paper_cs_0610046_gb300.build`` or call :func:`build`.
+
+``build(checked=True)`` (``--checked``) builds ``libmmf_checked.so`` with
+``-DMMF_CHECKED``: the block-scan and short-series kernels range-check their
+copies and direct loads against the launch's readable buffer and record bit 2
+of the device status word instead of touching memory outside it.  The
+binding loads it when ``MMF_CHECKED=1`` is set.
 """
 from __future__ import annotations
 
@@ -18,6 +24,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmmf.so")
+LIB_CHECKED = os.path.join(HERE, "libmmf_checked.so")
+OBJ_CHECKED = os.path.join(HERE, "_build_checked")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
@@ -39,8 +47,8 @@ def _deps():
     return [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "mmf.h")]
 
 
-def _compile(src: str, extra) -> str:
-    obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
+def _compile(src: str, extra, objdir: str = OBJ) -> str:
+    obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
     cmd = [_nvcc(), *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -48,26 +56,29 @@ def _compile(src: str, extra) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Compile and link libmmf.so if any source is newer than it."""
-    if not force and os.path.exists(LIB):
-        t = os.path.getmtime(LIB)
+def build(force: bool = False, verbose: bool = False, extra=(), checked: bool = False) -> str:
+    """Compile and link libmmf.so (or, checked, libmmf_checked.so) if any
+    source is newer than it."""
+    lib, objdir = (LIB_CHECKED, OBJ_CHECKED) if checked else (LIB, OBJ)
+    extra = list(extra) + (["-DMMF_CHECKED"] if checked else [])
+    if not force and os.path.exists(lib):
+        t = os.path.getmtime(lib)
         if all(os.path.getmtime(d) <= t for d in _deps()):
-            return LIB
-    os.makedirs(OBJ, exist_ok=True)
+            return lib
+    os.makedirs(objdir, exist_ok=True)
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, list(extra)), srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+        objs = list(ex.map(lambda s: _compile(s, extra, objdir), srcs))
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     if verbose:
-        print(f"built {LIB}")
-    return LIB
+        print(f"built {lib}")
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose=True)
+    build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv)

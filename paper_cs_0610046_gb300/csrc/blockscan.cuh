@@ -562,6 +562,16 @@ __device__ __forceinline__ void copy_pieces(uint8_t *dst, uintptr_t src, uint32_
                                             uint64_t pol) {
     using G = Geo<T>;
     const uint32_t bytes = (uint32_t)((G::PIECE + HALO) * sizeof(T)) + extra;
+    if constexpr (kChecked) {
+        // The copied bytes must lie inside the launch's readable buffer; a
+        // copy that would leave it is skipped (the stage completes empty).
+        const BlockScanParams &P = Smem<T>::params();
+        const int64_t off = (int64_t)(src - (uintptr_t)P.in);
+        if (!in_range(P.status, off, 0, P.in_elems * (int64_t)sizeof(T) - (int64_t)bytes * G::PIECES + 1)) {
+            mbar_arrive_expect_tx(bar, 0);
+            return;
+        }
+    }
     mbar_arrive_expect_tx(bar, bytes * G::PIECES);
 #pragma unroll
     for (int g = 0; g < G::PIECES; ++g)
@@ -955,7 +965,9 @@ struct Consumer {
 #pragma unroll
             for (int i = 0; i < V; ++i) {
                 const int64_t p = pt + i;
-                if (p < 0 || p >= ip.n) {
+                if (p < 0 || p >= ip.n ||
+                    !in_range(S::params().status, (ip.in - reinterpret_cast<const T *>(S::params().in)) + p, 0,
+                              S::params().in_elems)) {
                     xm[i] = Elem<T>::lo();
                     xn[i] = Elem<T>::hi();
                 } else {
@@ -1834,7 +1846,9 @@ struct Consumer {
 #pragma unroll
             for (int i = 0; i < NE; ++i) {
                 const int64_t p = pt + i;
-                if (p < 0 || p >= ip.n) {
+                if (p < 0 || p >= ip.n ||
+                    !in_range(S::params().status, (ip.in - reinterpret_cast<const T *>(S::params().in)) + p, 0,
+                              S::params().in_elems)) {
                     xm[i] = Elem<T>::lo();
                     xn[i] = Elem<T>::hi();
                 } else {

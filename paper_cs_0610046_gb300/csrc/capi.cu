@@ -113,9 +113,11 @@ mmf_status make_series(int64_t n, int64_t w_or_r, mmf_mode mode, mmf_dtype dt, S
 
 static std::atomic<uint32_t> g_test_flags{0};
 static std::atomic<long long> g_test_wait_limit{0};
+static std::atomic<int64_t> g_test_clip_in{0};
 
 TestHooks test_hooks() {
-    return TestHooks{g_test_flags.load(std::memory_order_relaxed), g_test_wait_limit.load(std::memory_order_relaxed)};
+    return TestHooks{g_test_flags.load(std::memory_order_relaxed), g_test_wait_limit.load(std::memory_order_relaxed),
+                     g_test_clip_in.load(std::memory_order_relaxed)};
 }
 
 mmf_kernel dispatch_lookup(mmf_dtype dt, int64_t n, int64_t w);  // dispatch.cu
@@ -285,6 +287,12 @@ mmf_status mmf_test_set_wait_fault(int starve_copies, int64_t wait_limit_cycles)
         g_test_flags.store(0);
         g_test_wait_limit.store(0);
     }
+    return MMF_OK;
+}
+
+mmf_status mmf_test_set_input_clip(int64_t elems) {
+    if (elems < 0) return set_error(MMF_EINVAL, "negative clip %lld", (long long)elems);
+    g_test_clip_in.store(elems);
     return MMF_OK;
 }
 

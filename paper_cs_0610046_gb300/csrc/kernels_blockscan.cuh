@@ -109,7 +109,6 @@ static cudaError_t blockscan_front(const LaunchCtx &ctx, const void *in, const S
     e = cudaMemsetAsync(ws, 0, bytes, ctx.stream);
     if (e == cudaSuccess) {
         BlockScanParams P{};
-        apply_test_hooks(P);
         P.in = in;
         P.out_max = omax;
         P.out_min = omin;
@@ -124,6 +123,7 @@ static cudaError_t blockscan_front(const LaunchCtx &ctx, const void *in, const S
         const int grid = (int)(tiles < gmax ? tiles : gmax);
         P.front_ahead = grid;
         P.front_last = tiles + q - 2;  // tile t+q-1 of the last output tile t
+        apply_test_hooks(P);
         void *args[] = {(void *)&P};
         e = cudaLaunchCooperativeKernel((const void *)blockscan_kernel<T, 2, false, true>, dim3(grid), dim3(G::NT),
                                         args, smem_of<T>(2), ctx.stream);
@@ -149,7 +149,6 @@ cudaError_t blockscan_1d(const LaunchCtx &ctx, const void *in, const SeriesDesc 
     const int64_t seg_tiles = (tiles + gmax - 1) / gmax;
     const int64_t n_items = (tiles + seg_tiles - 1) / seg_tiles;
     BlockScanParams P{};
-    apply_test_hooks(P);
     P.in = in;
     P.out_max = omax;
     P.out_min = omin;
@@ -161,6 +160,7 @@ cudaError_t blockscan_1d(const LaunchCtx &ctx, const void *in, const SeriesDesc 
     P.ticket = nullptr;
     P.status = ctx.status;
     P.in_elems = sd.in_off + sd.n;
+    apply_test_hooks(P);
     launch_mode<T>(mode, P, (int)n_items, ctx.stream);
     return cudaGetLastError();
 }
@@ -178,7 +178,6 @@ cudaError_t blockscan_rows(const LaunchCtx &ctx, const void *in, const SeriesDes
     const int64_t seg_tiles = tiles < 64 ? tiles : 64;
     const int64_t row_items = (tiles + seg_tiles - 1) / seg_tiles;
     BlockScanParams P{};
-    apply_test_hooks(P);
     P.in = in;
     P.out_max = omax;
     P.out_min = omin;
@@ -191,6 +190,7 @@ cudaError_t blockscan_rows(const LaunchCtx &ctx, const void *in, const SeriesDes
     P.status = ctx.status;
     P.in_elems = (rows - 1) * in_pitch + sd.in_off + sd.n;
     const int64_t gmax = (int64_t)(ctx.sms > 0 ? ctx.sms : 1) * per_sm;
+    apply_test_hooks(P);
     launch_mode<T>(mode, P, (int)(P.n_items < gmax ? P.n_items : gmax), ctx.stream);
     return cudaGetLastError();
 }
@@ -208,7 +208,6 @@ cudaError_t blockscan_table(const LaunchCtx &ctx, int mode, const void *in, int6
     if (e != cudaSuccess) return e;
     if (grid <= 0) grid = (ctx.sms > 0 ? ctx.sms : 1) * per_sm;
     BlockScanParams P{};
-    apply_test_hooks(P);
     P.in = in;
     P.out_max = omax;
     P.out_min = omin;
@@ -221,6 +220,7 @@ cudaError_t blockscan_table(const LaunchCtx &ctx, int mode, const void *in, int6
     P.in_elems = in_elems;
     P.lb_query = lb_query;
     P.lb_acc = lb_acc;
+    apply_test_hooks(P);
     launch_mode<T>(mode, P, grid, ctx.stream);
     return cudaGetLastError();
 }

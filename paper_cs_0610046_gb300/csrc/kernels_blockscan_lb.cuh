@@ -16,7 +16,6 @@ cudaError_t blockscan_table_lb(const LaunchCtx &ctx, int mode, const void *in, i
     if (e != cudaSuccess) return e;
     if (grid <= 0) grid = (ctx.sms > 0 ? ctx.sms : 1) * per_sm;
     BlockScanParams P{};
-    apply_test_hooks(P);
     P.in = in;
     P.series = d_series;
     P.items = d_items;
@@ -26,6 +25,7 @@ cudaError_t blockscan_table_lb(const LaunchCtx &ctx, int mode, const void *in, i
     P.in_elems = in_elems;
     P.lb_query = lb_query;
     P.lb_acc = lb_acc;
+    apply_test_hooks(P);
     launch_mode<T, true>(mode, P, grid, ctx.stream);
     return cudaGetLastError();
 }

@@ -26,17 +26,19 @@ struct LaunchCtx {
     cudaStream_t stream;
 };
 
-// Test hook of the block-scan kernels (mmf_test_set_wait_fault): flags and
-// wait bound copied into every launch's parameters.
+// Test hooks of the block-scan kernels (mmf_test_set_wait_fault,
+// mmf_test_set_input_clip), applied to every launch's finished parameters.
 struct TestHooks {
     uint32_t flags;        // kTestStarveCopies or 0
     long long wait_limit;  // SM clocks; 0: the default bound
+    int64_t clip_in;       // > 0: the readable bound the kernels check is at most this many elements
 };
 TestHooks test_hooks();
 inline void apply_test_hooks(BlockScanParams &P) {
     const TestHooks h = test_hooks();
     P.test_flags = h.flags;
     P.wait_limit = h.wait_limit;
+    if (h.clip_in > 0 && P.in_elems > h.clip_in) P.in_elems = h.clip_in;
 }
 
 // One series, statically split into per-CTA items (no allocation).  With

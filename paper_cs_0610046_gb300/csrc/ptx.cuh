@@ -8,7 +8,15 @@
 namespace mmf {
 
 // Device status word: kernels OR error bits into it instead of trapping.
-enum : uint32_t { kErrWaitTimeout = 1u, kErrBadItem = 2u };
+// kErrRange: a checked build (MMF_CHECKED) found an index outside its range
+// and skipped the access.
+enum : uint32_t { kErrWaitTimeout = 1u, kErrBadItem = 2u, kErrRange = 4u };
+
+#ifdef MMF_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -132,6 +140,20 @@ __device__ __forceinline__ bool named_bar_sync_or(int id, int nthreads, bool pre
 
 __device__ __forceinline__ void report_error(uint32_t *status, uint32_t bits) {
     if (status) atomicOr(status, bits);
+}
+
+// Range check of a global or shared index (a stand-in for a memory
+// sanitizer): in a checked build (MMF_CHECKED) it records kErrRange and
+// returns false when i lies outside [lo, hi), and the caller skips the
+// access; otherwise it is always true and costs nothing.
+__device__ __forceinline__ bool in_range(uint32_t *status, int64_t i, int64_t lo, int64_t hi) {
+    if constexpr (!kChecked) {
+        return true;
+    } else {
+        if (i >= lo && i < hi) return true;
+        report_error(status, kErrRange);
+        return false;
+    }
 }
 
 }  // namespace mmf

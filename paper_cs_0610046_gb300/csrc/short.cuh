@@ -52,7 +52,7 @@ extern __shared__ __align__(16) uint8_t short_smem[];
 // read if they lie inside the buffer and ignored later).
 template <typename T>
 __device__ __forceinline__ void short_load(const T *src, int n, int lane, const T *buf, int64_t buf_n,
-                                           typename Elem<T>::R (&x)[ShortGeo<T>::E]) {
+                                           typename Elem<T>::R (&x)[ShortGeo<T>::E], uint32_t *status) {
     using G = ShortGeo<T>;
     constexpr int E = G::E;
     constexpr int NWD = E * (int)sizeof(T) / 4;
@@ -77,7 +77,9 @@ __device__ __forceinline__ void short_load(const T *src, int n, int lane, const 
         ExtractLoop<T, 0, 0, E>::run(wd, x);
     } else {
 #pragma unroll
-        for (int e = 0; e < E; ++e) x[e] = lane * E + e < n ? Elem<T>::load(__ldg(p + e)) : Elem<T>::lo();
+        for (int e = 0; e < E; ++e)
+            x[e] = lane * E + e < n && in_range(status, (p + e) - buf, 0, buf_n) ? Elem<T>::load(__ldg(p + e))
+                                                                              : Elem<T>::lo();
     }
 }
 
@@ -290,7 +292,7 @@ __global__ void __launch_bounds__(ShortGeo<T>::WARPS * 32, 2) short_kernel(const
         A part = A(0);
         {
             R x[E], r[E];
-            short_load<T>(buf + sd.in_off, n, lane, buf, P.in_elems, x);
+            short_load<T>(buf + sd.in_off, n, lane, buf, P.in_elems, x, P.status);
             short_side<T, true>(x, n, wi, d, n_out, q0, u1, lane, PA, SA, r);
             if constexpr (LB)
                 part += short_lb_side<T, true>(qs, lane, n_out, r);
@@ -300,7 +302,7 @@ __global__ void __launch_bounds__(ShortGeo<T>::WARPS * 32, 2) short_kernel(const
         __syncwarp();  // keeps the next side's loads after this side's stores (register pressure)
         {
             R x[E], r[E];
-            short_load<T>(buf + sd.in_off, n, lane, buf, P.in_elems, x);
+            short_load<T>(buf + sd.in_off, n, lane, buf, P.in_elems, x, P.status);
             short_side<T, false>(x, n, wi, d, n_out, q0, u1, lane, PA, SA, r);
             if constexpr (LB)
                 part += short_lb_side<T, false>(qs, lane, n_out, r);

@@ -180,3 +180,10 @@ def test_wait_fault_hook_checks_its_bound(lib):
     assert f(1, 10) == 1 and f(1, 3_000_000_000) == 1
     assert f(1, 200_000) == 0
     assert f(0, 0) == 0
+
+
+def test_input_clip_hook_is_host_only(lib):
+    f = lib.mmf_test_set_input_clip
+    f.argtypes = [ctypes.c_int64]
+    f.restype = ctypes.c_int
+    assert f(-1) == 1 and f(1 << 20) == 0 and f(0) == 0
