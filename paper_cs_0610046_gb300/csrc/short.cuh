@@ -12,6 +12,14 @@
 // shared array stored element-major (row = position mod E, column = lane), so
 // a warp reading one position per lane touches 32 consecutive words.  Max and
 // min are done one after the other in the same arrays.
+//
+// Windows longer than a lane's E elements (w - 1 >= E) take a second
+// decomposition, short_lanes: the blocks are the lanes themselves (Section
+// 2's decomposition with blocks shorter than the window, as in the block
+// scan's long windows), so the prefix and suffix scans run inside a lane
+// without restarts or carries, max and min in one pass over the loaded
+// values, and the whole lanes a window spans come from per-lane aggregates
+// combined by shuffles.
 #pragma once
 #include <cstdint>
 
@@ -27,7 +35,7 @@ template <typename T> struct ShortGeo {
     static constexpr int NMAX = 32 * E;                  // longest series
     static constexpr int WARPS = 8;                      // per CTA
     static constexpr int ROW = 33;                       // shared row stride (values)
-    static constexpr size_t warp_bytes = 2 * (size_t)E * ROW * sizeof(R);
+    static constexpr size_t warp_bytes = 3 * (size_t)E * ROW * sizeof(R);  // three [E][ROW] arrays
     static constexpr size_t smem_bytes = WARPS * warp_bytes;
     static constexpr size_t smem_bytes_lb = smem_bytes + (size_t)NMAX * sizeof(T);  // + the query
 };
@@ -218,6 +226,193 @@ __device__ __forceinline__ void short_side(typename Elem<T>::R (&v)[ShortGeo<T>:
     __syncwarp();
 }
 
+template <typename R> __device__ __forceinline__ R shfl_down_or(R v, int lane, int dl, R id) {
+    const R t = __shfl_down_sync(0xffffffffu, v, dl);
+    return lane + dl < 32 ? t : id;
+}
+
+// m1 = op over the aggregates of lanes lane+1 .. lane+q-1, m2 = the same
+// through lane+q (lanes past 31 hold identities).  D[k] holds op over lanes
+// lane .. lane+2^k-1; a run of L lanes (1 <= L <= 31) is two overlapping runs
+// of the largest power of two p <= L, one starting at its first lane and one
+// ending at its last; runs of 32 or more lanes reach past lane 31 and are the
+// suffix D[5].  q is the same on every lane.
+template <bool MAX, typename R>
+__device__ __forceinline__ void lane_windows(R a, int lane, int q, R id, R &m1, R &m2) {
+    R D[6];
+    D[0] = a;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) D[k + 1] = sop<MAX>(D[k], shfl_down_or(D[k], lane, 1 << k, id));
+    auto run = [&](int L) -> R {
+        if (L <= 0) return id;
+        if (L >= 32) return shfl_down_or(D[5], lane, 1, id);
+        const int k = 31 - __clz(L), p = 1 << k;
+        R Dk = D[0];
+#pragma unroll
+        for (int kk = 1; kk < 5; ++kk)
+            if (k == kk) Dk = D[kk];
+        return sop<MAX>(shfl_down_or(Dk, lane, 1, id), shfl_down_or(Dk, lane, 1 + L - p, id));
+    };
+    m1 = run(q - 1);
+    m2 = run(q);
+}
+
+// Inclusive scan of the lane aggregates: op over lanes 0 .. lane.
+template <bool MAX, typename R> __device__ __forceinline__ R lane_scan(R a, int lane) {
+#pragma unroll
+    for (int k = 1; k < 32; k <<= 1) {
+        const R t = __shfl_up_sync(0xffffffffu, a, k);
+        if (lane >= k) a = sop<MAX>(t, a);
+    }
+    return a;
+}
+
+// Adds the squared excursion of the query outside the envelope at one
+// position: above the upper envelope or below the lower one (never both:
+// U >= L).
+template <typename T>
+__device__ __forceinline__ typename LbAcc<T>::A lb_term(T qv, typename Elem<T>::R u, typename Elem<T>::R l,
+                                                        typename LbAcc<T>::A part) {
+    using A = typename LbAcc<T>::A;
+    const A qi = (A)qv, U = (A)Elem<T>::store(u), L = (A)Elem<T>::store(l);
+    const A dd = qi > U ? qi - U : (qi < L ? L - qi : A(0));
+    return part + dd * dd;
+}
+
+// One series whose windows are longer than a lane (w - 1 >= E), both sides;
+// returns this lane's part of the envelope lower bound (LB) or zero.
+// Lane j holds positions [jE, jE + E), the last element repeated past the
+// series' end (E-element blocks from position 0; every window reaching past
+// the end holds that element already, so neither side changes).  P: prefix
+// inside the lane's block, to shared memory (PM, PN: element-major
+// [e][lane], column 32 an identity column); S: suffix inside the block (max
+// in registers, min in SN).  With s = w - 1 = q*E + rr, the window starting
+// at position lo = jE + e ends at hi = lo + s in lane j + q (e < E - rr) or
+// j + q + 1, so its extreme is op(S[lo], aggregates of the lanes in between,
+// P[hi]); hi past the last lane reads the identity column (the aggregates
+// in between then run to lane 31).  Lane j forms the outputs o = lo - d of
+// its own positions; outputs whose windows start before position 0 (centred
+// windows, d < 0) are op(lanes before hi's lane, P[hi]).  The outputs go
+// back through shared memory (max to PM, min in place in SN) so that each
+// store instruction writes 32 consecutive outputs.
+// Not inlined: the kernel's other decomposition then keeps its own register
+// allocation (inlined together they spill).
+template <typename T, bool LB>
+__device__ __noinline__ typename LbAcc<T>::A short_lanes(const T *src, const T *buf, int64_t buf_n, uint32_t *status,
+                                                         int n, int w, int d, int n_out, int lane,
+                                                         typename Elem<T>::R *PM, typename Elem<T>::R *PN,
+                                                         typename Elem<T>::R *SN, T *omax, T *omin, const T *qs) {
+    using G = ShortGeo<T>;
+    using R = typename Elem<T>::R;
+    using A = typename LbAcc<T>::A;
+    constexpr int E = G::E, ROW = G::ROW;
+    const R lo_id = Elem<T>::lo(), hi_id = Elem<T>::hi();
+    A part = A(0);
+    R x[E];
+    short_load<T>(src, n, lane, buf, buf_n, x, status);
+    const int base = lane * E;
+    if (base + E > n) {
+        const R last = Elem<T>::load(__ldg(src + n - 1));
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+            if (base + e >= n) x[e] = last;
+    }
+    // The max side's suffix stays in registers, the min side's goes to SN
+    // (both in registers would not fit beside the loaded values).
+    R sm[E];
+    R am, an;  // lane aggregates
+    {
+        R pm = x[0], pn = x[0];
+        PM[lane] = pm;
+        PN[lane] = pn;
+#pragma unroll
+        for (int e = 1; e < E; ++e) {
+            pm = vmax(pm, x[e]);
+            pn = vmin(pn, x[e]);
+            PM[e * ROW + lane] = pm;
+            PN[e * ROW + lane] = pn;
+        }
+        am = pm;
+        an = pn;
+        R sn = x[E - 1];
+        sm[E - 1] = sn;
+        SN[(E - 1) * ROW + lane] = sn;
+#pragma unroll
+        for (int e = E - 2; e >= 0; --e) {
+            sm[e] = vmax(sm[e + 1], x[e]);
+            sn = vmin(sn, x[e]);
+            SN[e * ROW + lane] = sn;
+        }
+    }
+    const int s = w - 1, q = s >> G::LGE, rr = s & (E - 1);
+    R m1m, m2m, m1n, m2n;
+    lane_windows<true>(am, lane, q, lo_id, m1m, m2m);
+    lane_windows<false>(an, lane, q, hi_id, m1n, m2n);
+    __syncwarp();
+    // Outputs of this lane's positions.  Element e reads row (e + rr) mod E
+    // of lane j + q + (e >= E - rr); the choice is the same on every lane.
+    const int c0 = lane + q < 32 ? lane + q : 32, c1 = lane + q + 1 < 32 ? lane + q + 1 : 32;
+    const int i0 = rr * ROW + c0, i1 = (rr - E) * ROW + c1;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const bool far = e >= E - rr;
+        const int i = (far ? i1 : i0) + e * ROW;
+        sm[e] = vmax(vmax(sm[e], far ? m2m : m1m), PM[i]);
+        // SN[e][lane] is this lane's own: the min outputs replace it in place.
+        SN[e * ROW + lane] = vmin(vmin(SN[e * ROW + lane], far ? m2n : m1n), PN[i]);
+    }
+    // Outputs whose windows start before position 0 (d < 0): the window is
+    // [0, hi], the lanes before hi's lane K and P[hi] (K = 32 past the end:
+    // all lanes and the identity column).
+    if (d < 0) {
+        const R xm = lane_scan<true>(am, lane), xn = lane_scan<false>(an, lane);
+        const int cnt = -d < n_out ? -d : n_out;
+        for (int o0 = 0; o0 < cnt; o0 += 32) {
+            const int o = o0 + lane, hi = o + d + s;
+            const int K = (hi >> G::LGE) < 32 ? hi >> G::LGE : 32;
+            const int src_lane = K > 0 ? K - 1 : 0;
+            const R tm = __shfl_sync(0xffffffffu, xm, src_lane), tn = __shfl_sync(0xffffffffu, xn, src_lane);
+            if (o < cnt) {
+                const int i = (hi & (E - 1)) * ROW + K;
+                const R rm = vmax(K > 0 ? tm : lo_id, PM[i]), rn = vmin(K > 0 ? tn : hi_id, PN[i]);
+                if constexpr (LB) {
+                    part = lb_term<T>(qs[o], rm, rn, part);
+                } else {
+                    if (omax) __stcs(omax + o, Elem<T>::store(rm));
+                    if (omin) __stcs(omin + o, Elem<T>::store(rn));
+                }
+            }
+        }
+    }
+    __syncwarp();  // every read of PM done
+#pragma unroll
+    for (int e = 0; e < E; ++e) PM[e * ROW + lane] = sm[e];
+    __syncwarp();
+    // Row k: outputs 32k + lane (max in PM, min in SN), formed by the lane
+    // holding their window start lo = o + d: element lo mod E of lane lo / E,
+    // index ir + k·32/E (o + 32 keeps lo mod E and moves 32/E lanes on).
+    // Outputs before -d came from the clipped windows above.
+    constexpr int CS = 32 / E;
+    const int t0 = lane + d;
+    const int ir = (t0 & (E - 1)) * ROW + (t0 >> G::LGE);
+    const int o_lo = d < 0 ? -d : 0;
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+        const int o = 32 * k + lane;
+        if (o >= o_lo && o < n_out) {
+            const int i = ir + CS * k;
+            if constexpr (LB) {
+                part = lb_term<T>(qs[o], PM[i], SN[i], part);
+            } else {
+                if (omax) __stcs(omax + o, Elem<T>::store(PM[i]));
+                if (omin) __stcs(omin + o, Elem<T>::store(SN[i]));
+            }
+        }
+    }
+    __syncwarp();  // the next series writes PM/PN/SN again
+    return part;
+}
+
 // Outputs of positions 32k + lane (row k) of one side to dst: every row is
 // one coalesced 32-element store.
 template <typename T>
@@ -268,6 +463,13 @@ __global__ void __launch_bounds__(ShortGeo<T>::WARPS * 32, 2) short_kernel(const
         for (int i = threadIdx.x; i < P.lb_n && i < G::NMAX; i += blockDim.x) qs[i] = __ldg(q + i);
         __syncthreads();
     }
+    // Column 32 of PA and SA: identities, read by windows reaching past the
+    // last lane (nothing else writes it).
+    for (int e = lane; e < E; e += 32) {
+        PA[e * G::ROW + 32] = Elem<T>::lo();
+        SA[e * G::ROW + 32] = Elem<T>::hi();
+    }
+    __syncwarp();
     for (int64_t k = (int64_t)blockIdx.x * G::WARPS + wib; k < P.count; k += nwarps) {
         const int64_t sid = P.ids[k];
         const SeriesDesc sd = P.series[sid];
@@ -285,29 +487,37 @@ __global__ void __launch_bounds__(ShortGeo<T>::WARPS * 32, 2) short_kernel(const
         // Windows longer than twice the longest series act like 2·NMAX
         // (every one of them is clipped to the series): 32-bit positions.
         const int wi = (int)(w < 2 * G::NMAX ? w : 2 * G::NMAX);
-        const int q0 = (lane * E) % wi, u1 = (lane * E + E - 1) % wi;
-        // Each side loads the series again (L2-resident): the values of one
-        // side need not stay in registers through the other.
         using A = typename LbAcc<T>::A;
         A part = A(0);
-        {
-            R x[E], r[E];
-            short_load<T>(buf + sd.in_off, n, lane, buf, P.in_elems, x, P.status);
-            short_side<T, true>(x, n, wi, d, n_out, q0, u1, lane, PA, SA, r);
-            if constexpr (LB)
-                part += short_lb_side<T, true>(qs, lane, n_out, r);
-            else if (P.out_max)
-                short_store_rows<T>(reinterpret_cast<T *>(P.out_max) + sd.out_off, lane, n_out, r);
-        }
-        __syncwarp();  // keeps the next side's loads after this side's stores (register pressure)
-        {
-            R x[E], r[E];
-            short_load<T>(buf + sd.in_off, n, lane, buf, P.in_elems, x, P.status);
-            short_side<T, false>(x, n, wi, d, n_out, q0, u1, lane, PA, SA, r);
-            if constexpr (LB)
-                part += short_lb_side<T, false>(qs, lane, n_out, r);
-            else if (P.out_min)
-                short_store_rows<T>(reinterpret_cast<T *>(P.out_min) + sd.out_off, lane, n_out, r);
+        if (wi > E) {
+            T *om = P.out_max ? reinterpret_cast<T *>(P.out_max) + sd.out_off : nullptr;
+            T *on = P.out_min ? reinterpret_cast<T *>(P.out_min) + sd.out_off : nullptr;
+            part = short_lanes<T, LB>(buf + sd.in_off, buf, P.in_elems, P.status, n, wi, d, n_out, lane, PA, SA,
+                                      SA + E * G::ROW, om, on, qs);
+        } else {
+            // Blocks of w elements, one side after the other; each side loads
+            // the series again (L2-resident): the values of one side need not
+            // stay in registers through the other.
+            const int q0 = (lane * E) % wi, u1 = (lane * E + E - 1) % wi;
+            {
+                R x[E], r[E];
+                short_load<T>(buf + sd.in_off, n, lane, buf, P.in_elems, x, P.status);
+                short_side<T, true>(x, n, wi, d, n_out, q0, u1, lane, PA, SA, r);
+                if constexpr (LB)
+                    part += short_lb_side<T, true>(qs, lane, n_out, r);
+                else if (P.out_max)
+                    short_store_rows<T>(reinterpret_cast<T *>(P.out_max) + sd.out_off, lane, n_out, r);
+            }
+            __syncwarp();  // keeps the next side's loads after this side's stores (register pressure)
+            {
+                R x[E], r[E];
+                short_load<T>(buf + sd.in_off, n, lane, buf, P.in_elems, x, P.status);
+                short_side<T, false>(x, n, wi, d, n_out, q0, u1, lane, PA, SA, r);
+                if constexpr (LB)
+                    part += short_lb_side<T, false>(qs, lane, n_out, r);
+                else if (P.out_min)
+                    short_store_rows<T>(reinterpret_cast<T *>(P.out_min) + sd.out_off, lane, n_out, r);
+            }
         }
         if constexpr (LB) {
             // This warp owns the series: the sum needs no atomics (the

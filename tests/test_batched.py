@@ -86,6 +86,42 @@ def test_envelope_batch(mmf, dtype):
     _check_batch(mmf, x.reshape(-1), lens, rs, mode="envelope", dtype=dtype)
 
 
+@pytest.mark.parametrize("dtype", [np.float32, np.float64, np.int16, np.uint8])
+@pytest.mark.parametrize("mode", ["valid", "envelope"])
+def test_short_series_both_decompositions(mmf, dtype, mode):
+    """Series short enough for the warp-per-series kernel (at most 1024
+    elements, 512 for f64), windows on both sides of one lane's 32 (16 for
+    f64) elements: blocks of w elements below, the lanes as blocks above.
+    Ragged lengths, windows of E, E+1, 2E, 2E+1, up to the whole series;
+    radii from 0 past the series' length; unaligned starts, and the last
+    series ending at the buffer's end (its loads cannot read ahead)."""
+    E = 16 if dtype == np.float64 else 32
+    cap = 32 * E
+    rng = np.random.default_rng(7 + E + (mode == "envelope"))
+    lens, ws = [], []
+    for n in list(rng.integers(1, cap + 1, size=120)) + [cap, cap, cap - 1, E + 1, 2 * E + 3, 1]:
+        n = int(n)
+        if mode == "valid":
+            cand = [1, E - 1, E, E + 1, 2 * E, 2 * E + 1, 3 * E + 7, n // 2 + 1, n - 1, n]
+            w = int(rng.choice([c for c in cand if 1 <= c <= n]))
+        else:
+            cand = [0, 1, E // 2 - 1, E // 2, E // 2 + 1, E, E + 3, n // 3, n - 1, n + 5]
+            w = int(rng.choice([c for c in cand if c >= 0]))
+        lens.append(n)
+        ws.append(w)
+    lens, ws = np.array(lens), np.array(ws)
+    gaps = rng.integers(0, 7, size=len(lens))
+    offs = np.cumsum(np.concatenate([[5], (lens + gaps)[:-1]]))
+    total = int(offs[-1] + lens[-1])  # nothing after the last series
+    data = synth.uniform(total, 11, np.float64)
+    if dtype in (np.float32, np.float64):
+        data = data.astype(dtype)
+    else:
+        lo, hi = (0, 255) if dtype == np.uint8 else (-32768, 32767)
+        data = (lo + np.floor(data * (hi - lo + 1))).clip(lo, hi).astype(dtype)
+    _check_batch(mmf, data, lens, ws, mode=mode, in_offsets=offs, dtype=dtype)
+
+
 def test_segments_and_autotune(mmf, tmp_path, monkeypatch):
     monkeypatch.setenv("MMF_AUTOTUNE_CACHE", str(tmp_path / "tune.txt"))
     lens, ws, dists, seeds = synth.uneven_batch(64, seed=8, lo_exp=3.0, hi_exp=5.0)

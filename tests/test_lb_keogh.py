@@ -53,11 +53,13 @@ def _check(mmf, dtype, nser, n, r, seed=1, query=None):
 
 
 @pytest.mark.parametrize("dtype", [np.float32, np.float64, np.int16, np.uint8])
-@pytest.mark.parametrize("n,r", [(1024, 51), (1, 0), (7, 3), (100, 0), (2047, 5), (5000, 200), (9001, 17)])
+@pytest.mark.parametrize("n,r", [(1024, 51), (1, 0), (7, 3), (100, 0), (2047, 5), (5000, 200), (9001, 17),
+                                 (500, 40), (1000, 15), (1000, 16), (300, 299), (700, 5000)])
 def test_lb_keogh_matches_oracle(mmf, dtype, n, r):
     """Lengths below, at and across tiles (ragged ends), radii that take the
     register slide (2r+1 <= 17), the scans inside a thread, across lanes and
-    per warp."""
+    per warp; short series with windows within one lane's elements and
+    beyond (2r+1 = 31 and 33), radii reaching past the series."""
     nser = 40 if n <= 2047 else 6
     _check(mmf, dtype, nser, n, r)
 

@@ -11,12 +11,15 @@ orders exist:
     never both), warps cover 512 consecutive positions;
   * short-series kernel (up to 1024): lane l sums positions 32k + l over k,
     the max side over all its positions first, then the min side; one warp
-    per series.
+    per series;
+  * short-series kernel, windows longer than 32 elements: lane l sums
+    positions 32k + l over k, one term per position (the side outside the
+    envelope), ascending.
 
 Summing m non-negative terms recursively in f32 has a relative error of at
 most (m-1)u (u = 2^-24), a zero term adds nothing, the butterfly adds 5u and
 each term carries at most 2u from its rounded difference: 22u (about 1.3e-6)
-for the block-scan order and 38u (about 2.3e-6) for the short order before
+for the block-scan order and 38u (about 2.3e-6) for both short orders before
 the square root, half of that after it.  This model applies those roundings
 in those orders (numpy float32, the multiply-add done exactly in double and
 rounded once) and checks the result against the oracle's double sum within
@@ -77,10 +80,22 @@ def _short_order(dmax, dmin):
     return float(_butterfly(part)[0])
 
 
+def _short_lanes_order(dmax, dmin):
+    n = dmax.size
+    assert n <= 1024
+    d = np.zeros(1024, np.float32)
+    d[:n] = np.where(dmax > 0, dmax, dmin)
+    rows = d.reshape(32, 32)
+    part = np.zeros((1, 32), np.float32)
+    for k in range(32):
+        part = _fma32(rows[k][None, :], rows[k][None, :], part)
+    return float(_butterfly(part)[0])
+
+
 @pytest.mark.parametrize("far", [False, True])
 def test_f32_bound_rounding_within_the_derived_bounds(far):
     rng = np.random.default_rng(9)
-    worst = {"blockscan": 0.0, "short": 0.0}
+    worst = {"blockscan": 0.0, "short": 0.0, "short_lanes": 0.0}
     for t in range(60):
         n = int(rng.integers(2, 1025)) if t % 2 else int(rng.integers(1025, 6000))
         r = int(rng.integers(0, 80))
@@ -94,6 +109,7 @@ def test_f32_bound_rounding_within_the_derived_bounds(far):
         got = {"blockscan": _blockscan_order(dmax, dmin)}
         if n <= 1024:
             got["short"] = _short_order(dmax, dmin)
+            got["short_lanes"] = _short_lanes_order(dmax, dmin)
         for kind, v in got.items():
             rel = abs(v - exact) / exact
             bound = (22 if kind == "blockscan" else 38) * U * 1.0001
@@ -101,4 +117,4 @@ def test_f32_bound_rounding_within_the_derived_bounds(far):
             rel_sqrt = abs(np.sqrt(v) - np.sqrt(exact)) / np.sqrt(exact)
             assert rel_sqrt <= 2e-6 and rel_sqrt <= 4e-6
             worst[kind] = max(worst[kind], rel)
-    assert worst["blockscan"] > 0 and worst["short"] > 0  # the model really rounds
+    assert worst["blockscan"] > 0 and worst["short"] > 0 and worst["short_lanes"] > 0  # the model really rounds

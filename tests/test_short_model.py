@@ -11,6 +11,8 @@ clipped at the start (lo <= 0) lies in block 0, which begins at position 0,
 so it is P[hi]; a window clipped at the end (hi = n-1) is S[lo] when lo and
 hi share a block (the identities after the series do not change it), else
 op(S[lo], P[hi])."""
+import itertools
+
 import numpy as np
 
 import oracle
@@ -77,3 +79,158 @@ def test_envelopes():
         gm, gn = _model(a, 2 * rr + 1, -rr, n, 256)
         em, en = oracle.envelope(a, r)
         assert np.array_equal(gm, em.astype(np.float64)) and np.array_equal(gn, en.astype(np.float64)), (n, r)
+
+
+# Windows longer than a lane (w - 1 >= E): the blocks are the lanes' own E
+# elements instead (the general block decomposition of Section 2 with blocks
+# shorter than the window), so the prefix and suffix scans never restart
+# inside a lane.  With s = w - 1 = q*E + rr, the window starting at lo (lane
+# j, element e) ends in lane K = j + q (or j + q + 1 when e + rr >= E): its
+# extreme is op(S[lo], aggregates of lanes j+1 .. K-1, P[hi]).  The lane
+# aggregates over the q-1 and q lanes after each lane come from a doubling
+# over lanes (windows of 1, 2, 4, 8, 16 lanes, two overlapping ones per
+# length); lanes past the last hold identities, and so does P at hi past the
+# last lane (the kernel reads an identity column there).  Positions past the
+# series' end repeat its last element (every window reaching past the end
+# holds that element already).  Lane j forms the outputs whose windows start
+# in its own block (o = lo - d); the outputs whose windows start before
+# position 0 (envelopes) take the aggregate of the lanes before hi's lane
+# and P[hi].
+
+
+def _lane_windows(A, q, op, ident):
+    """m1[j] = op(A[j+1 .. j+q-1]), m2[j] = op(A[j+1 .. j+q]), by the
+    kernel's doubling (D[k][x] = op over lanes x .. x+2^k-1, identities past
+    the last lane)."""
+    L = len(A)
+    D = [list(A)]
+    for k in range(5):
+        dl = 1 << k
+        D.append([op(D[k][x], D[k][x + dl] if x + dl < L else ident) for x in range(L)])
+
+    def win(length):
+        out = []
+        for j in range(L):
+            if length <= 0:
+                out.append(ident)
+            elif length >= 32:
+                out.append(D[5][j + 1] if j + 1 < L else ident)
+            else:
+                k = length.bit_length() - 1
+                p = 1 << k
+                u = D[k][j + 1] if j + 1 < L else ident
+                off = 1 + length - p
+                v = D[k][j + off] if j + off < L else ident
+                out.append(op(u, v))
+        return out
+
+    return win(q - 1), win(q)
+
+
+def _model_lanes(a, w, d, n_out, E, mistake=None):
+    lanes = 32
+    cap = lanes * E
+    n = len(a)
+    assert n <= cap and w - 1 >= E
+    s = w - 1
+    q, rr = divmod(s, E)
+    x = np.full(cap, float(a[-1]))  # the last element repeated past the end
+    x[:n] = a.astype(np.float64)
+    if mistake == "identity_pad_one_side":
+        x[n:] = -np.inf  # right for max only
+    res_all = []
+    for op, ident in ((max, -np.inf), (min, np.inf)):
+        P = x.copy()
+        S = x.copy()
+        for j in range(lanes):
+            b = j * E
+            for e in range(1, E):
+                P[b + e] = op(P[b + e - 1], x[b + e])
+            for e in range(E - 2, -1, -1):
+                S[b + e] = op(S[b + e + 1], x[b + e])
+        A = [S[j * E] for j in range(lanes)]
+        m1, m2 = _lane_windows(A, q, op, ident)
+        if mistake == "m_swapped":
+            m1, m2 = m2, m1
+
+        def Pk(K, eh):  # identity column past the last lane
+            return P[K * E + eh] if K < lanes else ident
+
+        res = np.full(n_out, np.nan)
+        for j in range(lanes):
+            for e in range(E):
+                lo = j * E + e
+                o = lo - d
+                if not 0 <= o < n_out:
+                    continue
+                far = e >= E - rr
+                K = j + q + (1 if far else 0)
+                eh = e + rr - (E if far else 0)
+                assert lo + s == K * E + eh
+                assert np.isnan(res[o]), "an output is formed twice"
+                res[o] = op(op(S[lo], m2[j] if far else m1[j]), Pk(min(K, lanes), eh))
+        if d < 0:
+            incl = list(itertools.accumulate(A, op))
+            for o in range(min(-d, n_out)):
+                hi = o + d + s
+                K = min(hi // E, lanes)
+                xk = incl[K - 1] if K > 0 else ident
+                assert np.isnan(res[o]), "an output is formed twice"
+                res[o] = op(xk, Pk(K, hi % E))
+        assert not np.isnan(res).any(), "an output is never formed"
+        res_all.append(res)
+    return res_all
+
+
+def test_lane_blocks_valid_windows():
+    rng = np.random.default_rng(3)
+    for E in (4, 8, 16, 32):
+        cap = 32 * E
+        for _ in range(40 if E < 16 else 12):
+            n = int(rng.integers(E + 1, cap + 1))
+            w = int(rng.integers(E + 1, n + 1))
+            a = synth.random_walk(n, seed=int(rng.integers(1 << 30)), dtype=np.float32)
+            if rng.random() < 0.3:
+                a = rng.integers(0, 3, size=n).astype(np.float32)
+            gm, gn = _model_lanes(a, w, 0, n - w + 1, E)
+            em, en = oracle.bf1d(a, w)
+            assert np.array_equal(gm, em.astype(np.float64)) and np.array_equal(gn, en.astype(np.float64)), (E, n, w)
+
+
+def test_lane_blocks_envelopes():
+    rng = np.random.default_rng(4)
+    for E in (4, 8, 16, 32):
+        cap = 32 * E
+        for _ in range(40 if E < 16 else 12):
+            n = int(rng.integers(1, cap + 1))
+            rr = int(rng.integers(0, n))
+            if 2 * rr < E:
+                continue  # a window of at most a lane: the other decomposition
+            a = synth.random_walk(n, seed=int(rng.integers(1 << 30)), dtype=np.float32)
+            gm, gn = _model_lanes(a, 2 * rr + 1, -rr, n, E)
+            em, en = oracle.envelope(a, rr)
+            assert np.array_equal(gm, em.astype(np.float64)) and np.array_equal(gn, en.astype(np.float64)), (E, n, rr)
+
+
+def test_lane_blocks_edges_and_planted_mistakes():
+    """Windows of exactly E+1 (q = 1, rr = 0), of q whole lanes, longer than
+    the series (clipped envelopes, hi past the last lane), full series; a
+    swapped choice of the between-lane aggregate fails, and so does padding
+    past the end with the max side's identity for both sides."""
+    E = 8
+    cap = 32 * E
+    a = synth.random_walk(cap, seed=9, dtype=np.float32)
+    for w in (E + 1, 2 * E + 1, 3 * E, 31 * E + 1, cap):
+        gm, gn = _model_lanes(a, w, 0, cap - w + 1, E)
+        em, en = oracle.bf1d(a, w)
+        assert np.array_equal(gm, em) and np.array_equal(gn, en), w
+    for n, r in ((cap, cap - 1), (cap, 40), (100, 99), (E + 3, E)):
+        gm, gn = _model_lanes(a[:n], 2 * r + 1, -r, n, E)
+        em, en = oracle.envelope(a[:n], r)
+        assert np.array_equal(gm, em) and np.array_equal(gn, en), (n, r)
+    gm, gn = _model_lanes(a, 3 * E + 5, 0, cap - 3 * E - 4, E, mistake="m_swapped")
+    em, en = oracle.bf1d(a, 3 * E + 5)
+    assert not (np.array_equal(gm, em) and np.array_equal(gn, en))
+    gm, gn = _model_lanes(a[:100], 61, -30, 100, E, mistake="identity_pad_one_side")
+    em, en = oracle.envelope(a[:100], 30)
+    assert np.array_equal(gm, em) and not np.array_equal(gn, en)
