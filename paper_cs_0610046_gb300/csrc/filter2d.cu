@@ -7,6 +7,7 @@
 #include <cstring>
 
 #include "colscan.cuh"
+#include "pack2d.h"
 #include "tile2d.cuh"
 #include "launch.h"
 #include "mmf.h"
@@ -63,7 +64,61 @@ template <typename T> static cudaError_t col_launch(const LaunchCtx &ctx, const 
 static bool tile_fits(int64_t wy, int64_t wx) { return wy <= kTileMaxW && wx <= kTileMaxW; }
 static bool use_fused(int64_t wy, int64_t wx, int fuse) {
     if (wy == 1 || wx == 1) return false;  // a single pass already
-    return fuse == 1 || (fuse < 0 && tile_fits(wy, wx));
+    return fuse == 1 || fuse == 2 || (fuse < 0 && tile_fits(wy, wx));
+}
+
+// The packed kernel (1- and 2-byte types, windows up to kPkMaxWy x
+// pk_max_wx, input rows 4-byte aligned: pointer, pitch and image stride).
+template <typename T>
+static bool pack_applies(const T *in, int64_t H, int64_t pitch, int64_t wy, int64_t wx) {
+    if constexpr (sizeof(T) > 2) {
+        return false;
+    } else {
+        const int64_t rowb = pitch * (int64_t)sizeof(T);
+        return wy <= kPkMaxWy && wx <= pk_max_wx<T>() && ((uintptr_t)in & 3) == 0 && rowb % 4 == 0 &&
+               (H * rowb) % 4 == 0;
+    }
+}
+
+template <typename T>
+static cudaError_t pack_launch(const LaunchCtx &ctx, const T *in, int64_t nimg, int64_t H, int64_t W, int64_t pitch,
+                               int64_t wy, int64_t wx, T *omax, T *omin) {
+    if constexpr (sizeof(T) > 2) {
+        return cudaErrorInvalidValue;
+    } else {
+        Pack2DParams P{};
+        P.in = in;
+        P.out_max = omax;
+        P.out_min = omin;
+        P.nimg = nimg;
+        P.H = H;
+        P.W = W;
+        P.pitch = pitch;
+        P.img_stride = H * pitch;
+        P.Ho = H - wy + 1;
+        P.Wo = W - wx + 1;
+        P.wy = (int)wy;
+        P.wx = (int)wx;
+        constexpr int L = 4 / (int)sizeof(T);  // columns per 32-bit word
+        const int64_t words = (P.Wo + L - 1) / L;
+        P.nchunks = (int)((words + 30) / 31);
+        P.nbands = (int)((P.Ho + kPkBand - 1) / kPkBand);
+        P.tasks = nimg * P.nbands * P.nchunks;
+        const int64_t grid = (P.tasks + kPkThreads / 32 - 1) / (kPkThreads / 32);
+        if (grid <= 0) return cudaSuccess;
+        if (grid > 0x7fffffff) return cudaErrorInvalidValue;
+        switch (wy) {
+            case 1: return pack2d_launch<T, 1>(ctx.stream, P, (unsigned)grid);
+            case 2: return pack2d_launch<T, 2>(ctx.stream, P, (unsigned)grid);
+            case 3: return pack2d_launch<T, 3>(ctx.stream, P, (unsigned)grid);
+            case 4: return pack2d_launch<T, 4>(ctx.stream, P, (unsigned)grid);
+            case 5: return pack2d_launch<T, 5>(ctx.stream, P, (unsigned)grid);
+            case 6: return pack2d_launch<T, 6>(ctx.stream, P, (unsigned)grid);
+            case 7: return pack2d_launch<T, 7>(ctx.stream, P, (unsigned)grid);
+            case 8: return pack2d_launch<T, 8>(ctx.stream, P, (unsigned)grid);
+            default: return pack2d_launch<T, 9>(ctx.stream, P, (unsigned)grid);
+        }
+    }
 }
 
 template <typename T>
@@ -148,6 +203,17 @@ static mmf_status filter2d(const LaunchCtx &ctx, const T *in, int64_t nimg, int6
                            int64_t wy, int64_t wx, int fuse, T *omax, T *omin, void *work) {
     const int64_t Ho = H - wy + 1, Wo = W - wx + 1;
     cudaError_t e = cudaSuccess;
+    if (fuse == 2 || fuse < 0) {
+        if (pack_applies<T>(in, H, pitch, wy, wx)) {
+            e = pack_launch<T>(ctx, in, nimg, H, W, pitch, wy, wx, omax, omin);
+            return e == cudaSuccess ? MMF_OK : cuda_error(e, "packed 2D kernel");
+        }
+        if (fuse == 2)
+            return set_error(MMF_ENOTIMPL,
+                             "the packed 2D kernel takes u8 (windows up to %d x 9) and i16 (up to %d x 5) with "
+                             "4-byte aligned rows",
+                             kPkMaxWy, kPkMaxWy);
+    }
     if (wy == 1) {  // rows only, straight into the outputs
         SeriesDesc sd{0, W, 0, wx, 0, Wo};
         e = blockscan_rows<T>(ctx, in, sd, nimg * H, pitch, Wo, omax, omin);
@@ -196,6 +262,7 @@ static mmf_status check2d(int64_t nimg, int64_t H, int64_t W, int64_t pitch, int
     if (elem_size(dt) == 0) return set_error(MMF_EINVAL, "unknown dtype %d", (int)dt);
     if (nimg < 0 || H < 0 || W < 0 || pitch < W) return set_error(MMF_EINVAL, "bad image geometry");
     if (wy < 1 || wx < 1) return set_error(MMF_EINVAL, "windows must be >= 1");
+    if (fuse < -1 || fuse > 2) return set_error(MMF_EINVAL, "fuse must be -1, 0, 1 or 2 (got %d)", fuse);
     // Far beyond what the column pass's shared memory holds; checked first so
     // that the ring size below stays within an int.
     if (wy > (int64_t(1) << 20)) return set_error(MMF_ENOTIMPL, "column window %lld too large", (long long)wy);

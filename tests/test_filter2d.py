@@ -77,6 +77,79 @@ def test_2d_fused_odd_width_unpaired(mmf, dtype):
             assert np.array_equal(mx[k].cpu().numpy(), em) and np.array_equal(mn[k].cpu().numpy(), en)
 
 
+@pytest.mark.parametrize("dtype", [np.uint8, np.int16])
+def test_2d_packed_every_window(mmf, dtype):
+    """The packed kernel (fuse = 2): every window up to 9 x 9 (9 x 5 for
+    i16); output widths of every residue modulo the word (rows of the dense
+    outputs start at every byte misalignment), several 32-word chunks per
+    row, bands of 64 rows with a ragged last one, against the literal
+    rectangle."""
+    imgs = synth.blobs2d(2, 150, 300, seed=5, dtype=dtype, nblobs=12)
+    if dtype == np.int16:
+        imgs = (imgs.astype(np.int32) - 16000).astype(np.int16)
+    x = torch.from_numpy(imgs).cuda()
+    maxwx = 9 if dtype == np.uint8 else 5
+    for wy in range(1, 10):
+        for wx in range(1, maxwx + 1):
+            mx, mn = mmf.filter2d(x, wy, wx, fuse=2)
+            torch.cuda.synchronize()
+            for k in range(2):
+                em, en = _expect(imgs[k], wy, wx)
+                assert np.array_equal(mx[k].cpu().numpy(), em), (wy, wx, k)
+                assert np.array_equal(mn[k].cpu().numpy(), en), (wy, wx, k)
+    assert mmf.device_status() == 0
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.int16])
+def test_2d_packed_pitch_offsets_and_refusals(mmf, dtype):
+    """Pitched input rows, output buffers starting at every misalignment, a
+    single output column, an image narrower than one word; misaligned input
+    rows are refused by the forced packed kernel and take another kernel in
+    the automatic choice."""
+    full = synth.blobs2d(3, 90, 308, seed=6, dtype=dtype, nblobs=7)
+    base = torch.from_numpy(full).cuda()
+    x = base[:, :, :300]  # pitch 308 elements
+    n, H = 3, 90
+    for wy, wx, off in ((3, 3, 1), (5, 2, 2), (9, 5, 3), (2, 4, 0), (1, 5, 1), (4, 1, 3)):
+        Ho, Wo = H - wy + 1, 300 - wx + 1
+        bm = torch.empty(n * Ho * Wo + 8, dtype=x.dtype, device="cuda")
+        bn = torch.empty(n * Ho * Wo + 8, dtype=x.dtype, device="cuda")
+        om = bm[off:off + n * Ho * Wo].view(n, Ho, Wo)
+        on = bn[(off + 1) % 4:(off + 1) % 4 + n * Ho * Wo].view(n, Ho, Wo)
+        mmf.filter2d(x, wy, wx, fuse=2, out_max=om, out_min=on)
+        torch.cuda.synchronize()
+        for k in range(n):
+            em, en = _expect(full[k, :, :300], wy, wx)
+            assert np.array_equal(om[k].cpu().numpy(), em) and np.array_equal(on[k].cpu().numpy(), en), (wy, wx)
+    maxwx = 9 if dtype == np.uint8 else 5
+    for W, wx in ((maxwx, maxwx), (3, 2), (2, 1)):
+        xs = base[:, :, :W]
+        mx, mn = mmf.filter2d(xs, 3, wx, fuse=2)
+        torch.cuda.synchronize()
+        for k in range(n):
+            em, en = _expect(full[k, :, :W], 3, wx)
+            assert np.array_equal(mx[k].cpu().numpy(), em) and np.array_equal(mn[k].cpu().numpy(), en), (W, wx)
+    xo = base[:, :, 1:301]  # rows start one element off a 4-byte boundary
+    with pytest.raises(mmf.MMFError) as e:
+        mmf.filter2d(xo, 3, 3, fuse=2)
+    assert e.value.status == 7
+    mx, mn = mmf.filter2d(xo, 3, 3)
+    torch.cuda.synchronize()
+    for k in range(n):
+        em, en = _expect(full[k, :, 1:301], 3, 3)
+        assert np.array_equal(mx[k].cpu().numpy(), em) and np.array_equal(mn[k].cpu().numpy(), en)
+    with pytest.raises(mmf.MMFError) as e:
+        mmf.filter2d(x, 10, 3, fuse=2)
+    assert e.value.status == 7
+    with pytest.raises(mmf.MMFError) as e:
+        mmf.filter2d(x.float(), 3, 3, fuse=2)
+    assert e.value.status == 7
+    with pytest.raises(mmf.MMFError) as e:
+        mmf.filter2d(x, 3, 3, fuse=3)
+    assert e.value.status == 1
+    assert mmf.device_status() == 0
+
+
 def test_2d_window_larger_than_image(mmf):
     x = torch.rand(2, 10, 12, device="cuda")
     mx, mn = mmf.filter2d(x, 11, 3)
@@ -104,7 +177,8 @@ def test_2d_full_size_sampled(mmf):
     img = synth.blobs2d(1, 4096, 4096, seed=41, dtype=np.uint8, nblobs=200)
     x = torch.from_numpy(img).cuda()
     rng = np.random.default_rng(4)
-    for wy, wx, fuse in ((3, 3, 0), (3, 3, 1), (15, 15, 0), (15, 15, 1), (63, 63, -1), (255, 1, -1), (1, 255, -1)):
+    for wy, wx, fuse in ((3, 3, 0), (3, 3, 1), (3, 3, 2), (7, 9, 2), (15, 15, 0), (15, 15, 1), (63, 63, -1),
+                         (255, 1, -1), (1, 255, -1)):
         mx, mn = mmf.filter2d(x, wy, wx, fuse=fuse)
         torch.cuda.synchronize()
         ys = rng.integers(0, 4096 - wy + 1, 2000)
