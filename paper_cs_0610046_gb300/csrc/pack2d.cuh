@@ -178,44 +178,55 @@ __device__ __forceinline__ void pk_band(const Pack2DParams &P, int lane, int64_t
     // Input rows y0 .. y1 + WY - 2 feed the band's outputs; rows at or past
     // ylim are not needed and read as 0.
     const int64_t ylim = y1 + WY - 1 < P.H ? y1 + WY - 1 : P.H;
-    auto row = [&](int64_t y, V &m, V &n, bool check) {
+    // A tile's words are all loaded before any of its arithmetic, so that
+    // their loads are in flight together.
+    constexpr int NW = W2 ? 3 : 2;
+    auto load = [&](int64_t y, uint32_t (&w)[NW], bool check) {
         if (check && y >= ylim) {
-            m = n = V{};
+#pragma unroll
+            for (int k = 0; k < NW; ++k) w[k] = 0u;
             return;
         }
         const uint8_t *rp = in + y * pitchb;
-        uint32_t w0, w1, w2 = 0u;
         if (interior) {
             const uint32_t *q = reinterpret_cast<const uint32_t *>(rp) + j;
-            w0 = __ldg(q);
-            w1 = __ldg(q + 1);
-            if (W2) w2 = __ldg(q + 2);
+#pragma unroll
+            for (int k = 0; k < NW; ++k) w[k] = __ldg(q + k);
         } else {
-            w0 = pk_word(rp, j, rb);
-            w1 = pk_word(rp, j + 1, rb);
-            if (W2) w2 = pk_word(rp, j + 2, rb);
+#pragma unroll
+            for (int k = 0; k < NW; ++k) w[k] = pk_word(rp, j + k, rb);
         }
-        Pk<T>::template row<WX>(w0, w1, w2, m, n);
+    };
+    auto row = [&](const uint32_t (&w)[NW], V &m, V &n) {
+        Pk<T>::template row<WX>(w[0], w[1], W2 ? w[NW - 1] : 0u, m, n);
     };
     V cm[kPkRows], cn[kPkRows];  // row results of the current tile
+    {
+        uint32_t w[kPkRows][NW];
 #pragma unroll
-    for (int r = 0; r < kPkRows; ++r) row(y0 + r, cm[r], cn[r], true);
+        for (int r = 0; r < kPkRows; ++r) load(y0 + r, w[r], true);
+#pragma unroll
+        for (int r = 0; r < kPkRows; ++r) row(w[r], cm[r], cn[r]);
+    }
     for (int64_t y = y0; y < y1; y += kPkRows) {
         // Rows y .. y+7 (current) and y+8 .. y+8+WY-2 (the start of the next
         // tile); the rest of the next tile goes straight to its registers.
         // Tiles whose next rows all lie below ylim skip the row checks.
         V am[2 * kPkRows], an[2 * kPkRows];
         const bool check = y + 2 * kPkRows > ylim;
+        uint32_t w[kPkRows][NW];
+#pragma unroll
+        for (int r = 0; r < kPkRows; ++r) load(y + kPkRows + r, w[r], check);
 #pragma unroll
         for (int r = 0; r < kPkRows; ++r) {
             am[r] = cm[r];
             an[r] = cn[r];
             if (r < WY - 1) {
-                row(y + kPkRows + r, am[kPkRows + r], an[kPkRows + r], check);
+                row(w[r], am[kPkRows + r], an[kPkRows + r]);
                 cm[r] = am[kPkRows + r];
                 cn[r] = an[kPkRows + r];
             } else {
-                row(y + kPkRows + r, cm[r], cn[r], check);
+                row(w[r], cm[r], cn[r]);
                 am[kPkRows + r] = an[kPkRows + r] = V{};  // outside these outputs' windows
             }
         }
