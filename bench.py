@@ -413,7 +413,7 @@ def blobs_torch(nimg, H, W, seed, dev, nblobs=200):
 def filter2d_extras(dev, stream, peak, nimg=64, H=4096, W=4096, reps=3):
     """64 images of 4096 x 4096, uint8 and fp32, five windows; row pass then
     column pass (unfused) and, where the windows allow, the fused tile kernel
-    and (uint8) the packed kernel; the fastest is the line's figure.
+    and the register-streaming kernel; the fastest is the line's figure.
     Algorithmic bytes: the image once plus both outputs."""
     import torch
     import paper_cs_0610046_gb300 as mmf
@@ -434,7 +434,7 @@ def filter2d_extras(dev, stream, peak, nimg=64, H=4096, W=4096, reps=3):
             for tag, fuse in (("unfused", 0), ("fused", 1), ("packed", 2)):
                 if fuse == 1 and (wy == 1 or wx == 1 or wx > 31 or wy > 31):
                     continue
-                if fuse == 2 and (name != "u8" or wy > 9 or wx > 9):
+                if fuse == 2 and (wy > 9 or wx > 9):
                     continue
                 mmf.filter2d(x, wy, wx, fuse=fuse, out_max=om, out_min=on, workspace=ws, stream=stream)
                 ms = _events_ms(lambda: mmf.filter2d(x, wy, wx, fuse=fuse, out_max=om, out_min=on, workspace=ws,

@@ -211,12 +211,13 @@ int64_t mmf_output_length(int64_t n, int64_t w_or_r, mmf_mode mode);
  * memory: for wy, wx <= 31 a tile with its halo in shared memory, rows then
  * columns; otherwise the column pass computing each tile's row maxima and
  * minima in registers (wx <= MMF_FUSED_MAX_WX, else MMF_ENOTIMPL); 2 the
- * packed kernel for u8 (windows up to 9 x 9) and i16 (up to 9 rows x 5
- * columns): 4 (2) columns per 32-bit register, per-element SIMD max/min, no
+ * register-streaming kernel for u8 and f32 (windows up to 9 x 9) and i16 (up
+ * to 9 rows x 5 columns): 4 u8 (2 i16) columns packed per 32-bit register
+ * with per-element SIMD max/min, f32 one column per register, no
  * intermediates in memory; needs 4-byte aligned input rows (d_in, the pitch
  * in bytes and the image stride), else MMF_ENOTIMPL; -1 automatic (the
- * packed kernel where it applies, the tile kernel when wy, wx <= 31, else the
- * two passes).  Any other value: MMF_EINVAL.
+ * streaming kernel for u8/i16 where it applies, the tile kernel when wy, wx
+ * <= 31, else the two passes).  Any other value: MMF_EINVAL.
  * Column windows are limited by the column
  * pass's shared memory: up to about 760 rows for f32, 320 for f64 and 1700 for
  * i16/u8 (MMF_ENOTIMPL beyond). */

@@ -5,6 +5,7 @@
 // to a caller-provided workspace; the fused form computes them in registers
 // inside the column pass (no workspace).
 #include <cstring>
+#include <type_traits>
 
 #include "colscan.cuh"
 #include "pack2d.h"
@@ -67,11 +68,13 @@ static bool use_fused(int64_t wy, int64_t wx, int fuse) {
     return fuse == 1 || fuse == 2 || (fuse < 0 && tile_fits(wy, wx));
 }
 
-// The packed kernel (1- and 2-byte types, windows up to kPkMaxWy x
-// pk_max_wx, input rows 4-byte aligned: pointer, pitch and image stride).
+// The register-streaming kernel (u8, i16 packed; f32; windows up to
+// kPkMaxWy x pk_max_wx, input rows 4-byte aligned: pointer, pitch and image
+// stride).
+template <typename T> constexpr bool pack_type() { return sizeof(T) <= 2 || std::is_same<T, float>::value; }
 template <typename T>
 static bool pack_applies(const T *in, int64_t H, int64_t pitch, int64_t wy, int64_t wx) {
-    if constexpr (sizeof(T) > 2) {
+    if constexpr (!pack_type<T>()) {
         return false;
     } else {
         const int64_t rowb = pitch * (int64_t)sizeof(T);
@@ -83,7 +86,7 @@ static bool pack_applies(const T *in, int64_t H, int64_t pitch, int64_t wy, int6
 template <typename T>
 static cudaError_t pack_launch(const LaunchCtx &ctx, const T *in, int64_t nimg, int64_t H, int64_t W, int64_t pitch,
                                int64_t wy, int64_t wx, T *omax, T *omin) {
-    if constexpr (sizeof(T) > 2) {
+    if constexpr (!pack_type<T>()) {
         return cudaErrorInvalidValue;
     } else {
         Pack2DParams P{};
@@ -101,7 +104,8 @@ static cudaError_t pack_launch(const LaunchCtx &ctx, const T *in, int64_t nimg, 
         P.wx = (int)wx;
         constexpr int L = 4 / (int)sizeof(T);  // columns per 32-bit word
         const int64_t words = (P.Wo + L - 1) / L;
-        P.nchunks = (int)((words + 30) / 31);
+        const int chunk = pk_chunk<T>((int)wx);
+        P.nchunks = (int)((words + chunk - 1) / chunk);
         P.nbands = (int)((P.Ho + kPkBand - 1) / kPkBand);
         P.tasks = nimg * P.nbands * P.nchunks;
         const int64_t grid = (P.tasks + kPkThreads / 32 - 1) / (kPkThreads / 32);
@@ -203,15 +207,15 @@ static mmf_status filter2d(const LaunchCtx &ctx, const T *in, int64_t nimg, int6
                            int64_t wy, int64_t wx, int fuse, T *omax, T *omin, void *work) {
     const int64_t Ho = H - wy + 1, Wo = W - wx + 1;
     cudaError_t e = cudaSuccess;
-    if (fuse == 2 || fuse < 0) {
+    if (fuse == 2 || (fuse < 0 && sizeof(T) <= 2)) {
         if (pack_applies<T>(in, H, pitch, wy, wx)) {
             e = pack_launch<T>(ctx, in, nimg, H, W, pitch, wy, wx, omax, omin);
             return e == cudaSuccess ? MMF_OK : cuda_error(e, "packed 2D kernel");
         }
         if (fuse == 2)
             return set_error(MMF_ENOTIMPL,
-                             "the packed 2D kernel takes u8 (windows up to %d x 9) and i16 (up to %d x 5) with "
-                             "4-byte aligned rows",
+                             "the register-streaming 2D kernel takes u8 and f32 (windows up to %d x 9) and i16 "
+                             "(up to %d x 5) with 4-byte aligned rows",
                              kPkMaxWy, kPkMaxWy);
     }
     if (wy == 1) {  // rows only, straight into the outputs

@@ -1,11 +1,16 @@
-// Packed separable 2D filter for 1- and 2-byte elements and small windows
-// (Section 1: the 1D filter on rows, then on columns).  The shared-memory
+// Register-streaming separable 2D filter for small windows (Section 1: the
+// 1D filter on rows, then on columns), f32 and, packed, 1- and 2-byte
+// elements.  The shared-memory
 // tile kernel spends an instruction per element on every step; here every
 // max/min is one 16x2 SIMD instruction (PTX max/min .s16x2, .u16x2): i16
 // words hold 2 neighbouring columns, and a u8 word of 4 columns is held as
 // two u16x2 registers, its even and its odd columns (unpacked once after the
 // load, packed once before the store; the byte-wise intrinsics expand to long
-// instruction sequences on this GPU).
+// instruction sequences on this GPU).  f32 takes one column per thread and
+// word (no packing): each lane loads its own word of a row and takes the
+// window's next columns from the next lanes by shuffles, so the last wx-1
+// lanes of a warp are a halo whose outputs are not stored (its outputs are
+// always word-aligned, so no realignment).
 //
 // One thread per output word (L = 4 / sizeof(T) columns), one warp per 31
 // consecutive words of one band of kPkBand output rows (its lane 31 computes
@@ -58,7 +63,8 @@ template <> struct Pk<int16_t> {
     __device__ static uint32_t pack(V v) { return v.w; }
     // Row window of WX elements from each of the word's columns (elements
     // 0 .. 5 of the 12 bytes w0 w1 w2).
-    template <int WX> __device__ static void row(uint32_t w0, uint32_t w1, uint32_t w2, V &m, V &n) {
+    template <int WX, int NW> __device__ static void row(const uint32_t (&w)[NW], V &m, V &n) {
+        const uint32_t w0 = w[0], w1 = w[1], w2 = NW > 2 ? w[NW > 2 ? 2 : 0] : 0u;
         m = n = V{w0};
 #pragma unroll
         for (int k = 1; k < WX; ++k) {
@@ -96,7 +102,8 @@ template <> struct Pk<uint8_t> {
     // 16-bit lanes, the odd stream 1, 3, .., 11; X[m] = lanes m, m+1 of a
     // stream.  The word shifted by k columns is (E[m], O[m]) for k = 2m and
     // (O[m], E[m+1]) for k = 2m+1.
-    template <int WX> __device__ static void row(uint32_t w0, uint32_t w1, uint32_t w2, V &m, V &n) {
+    template <int WX, int NW> __device__ static void row(const uint32_t (&w)[NW], V &m, V &n) {
+        const uint32_t w0 = w[0], w1 = w[1], w2 = NW > 2 ? w[NW > 2 ? 2 : 0] : 0u;
         uint32_t E[5], O[5];
         E[0] = __byte_perm(w0, 0u, 0x4240);
         O[0] = __byte_perm(w0, 0u, 0x4341);
@@ -118,6 +125,30 @@ template <> struct Pk<uint8_t> {
     }
 };
 
+// f32: one column per word.
+template <> struct Pk<float> {
+    static constexpr int L = 1;
+    struct V {
+        float f;
+    };
+    __device__ static V mx(V a, V b) { return V{fmaxf(a.f, b.f)}; }
+    __device__ static V mn(V a, V b) { return V{fminf(a.f, b.f)}; }
+    __device__ static uint32_t pack(V v) { return __float_as_uint(v.f); }
+    // Row window of WX elements: this lane's word and the next WX-1 lanes'
+    // (every lane of the warp calls it; the last WX-1 lanes get values of
+    // their own, which only their unstored outputs see).
+    template <int WX, int NW> __device__ static void row(const uint32_t (&w)[NW], V &m, V &n) {
+        const float x = __uint_as_float(w[0]);
+        m = n = V{x};
+#pragma unroll
+        for (int k = 1; k < WX; ++k) {
+            const V s{__shfl_down_sync(0xffffffffu, x, k)};
+            m = mx(m, s);
+            n = mn(n, s);
+        }
+    }
+};
+
 // Word j of an input row (bytes [4j, 4j+4)), zero past the row's `rb` bytes.
 __device__ __forceinline__ uint32_t pk_word(const uint8_t *row, int64_t j, int64_t rb) {
     const int64_t b = 4 * j;
@@ -132,8 +163,10 @@ __device__ __forceinline__ uint32_t pk_word(const uint8_t *row, int64_t j, int64
 template <typename T> __device__ __forceinline__ void pk_put(uint8_t *p, uint32_t w, int e) {
     if constexpr (sizeof(T) == 1)
         p[e] = (uint8_t)(w >> (8 * e));
-    else
+    else if constexpr (sizeof(T) == 2)
         reinterpret_cast<uint16_t *>(p)[e] = (uint16_t)(w >> (16 * e));
+    else
+        reinterpret_cast<uint32_t *>(p)[e] = w;
 }
 
 // Stores output word v of columns x0 .. x0+L-1 of one row at byte address
@@ -141,11 +174,12 @@ template <typename T> __device__ __forceinline__ void pk_put(uint8_t *p, uint32_
 // on every lane).  Every lane of the warp calls it (the shuffle); head: this
 // is the row's first warp.
 template <typename T>
-__device__ __forceinline__ void pk_store(uint8_t *ob, uint32_t v, int lane, int64_t x0, int64_t Wo, bool head) {
+__device__ __forceinline__ void pk_store(uint8_t *ob, uint32_t v, int lane, int64_t x0, int64_t Wo, bool head,
+                                         int nst) {
     constexpr int L = Pk<T>::L, SZ = (int)sizeof(T);
     const int a = (int)((uintptr_t)ob & 3);
     const uint32_t nxt = __shfl_down_sync(0xffffffffu, v, 1);
-    if (lane == 31) return;  // the halo word: the next warp's
+    if (lane >= nst) return;  // halo words: the next warp's
     const int h = a ? (4 - a) / SZ : 0;  // elements of this word before the next aligned word
     const uint32_t aw = a ? __funnelshift_r(v, nxt, 8 * (4 - a)) : v;
     uint8_t *ap = ob + (a ? 4 - a : 0);
@@ -168,19 +202,22 @@ __device__ __forceinline__ void pk_store(uint8_t *ob, uint32_t v, int lane, int6
 template <typename T, int WY, int WX>
 __device__ __forceinline__ void pk_band(const Pack2DParams &P, int lane, int64_t j, bool head, int64_t y0, int64_t y1,
                                         const uint8_t *in, uint8_t *omax, uint8_t *omin, int64_t obase) {
+    const int nst = pk_chunk<T>(WX);  // lanes whose words are stored
     using V = typename Pk<T>::V;
     constexpr int L = Pk<T>::L, SZ = (int)sizeof(T);
     constexpr int P2 = WY >= 8 ? 8 : (WY >= 4 ? 4 : (WY >= 2 ? 2 : 1));
-    constexpr bool W2 = (L + WX - 1) * SZ > 8;  // the window reaches a third word
+    // Words read per row: the window's elements from each of the word's
+    // columns lie in words j .. j+NW-1.
+    // (f32: one word, the rest from the next lanes.)
+    constexpr int NW = SZ == 4 ? 1 : (((L + WX - 1) * SZ + 3) / 4 > 2 ? ((L + WX - 1) * SZ + 3) / 4 : 2);
     const int64_t x0 = j * L;                    // first output column of the word
     const int64_t rb = P.W * SZ, pitchb = P.pitch * SZ;
-    const bool interior = 4 * (j + (W2 ? 3 : 2)) <= rb;  // every word read lies inside the row
+    const bool interior = 4 * (j + NW) <= rb;  // every word read lies inside the row
     // Input rows y0 .. y1 + WY - 2 feed the band's outputs; rows at or past
     // ylim are not needed and read as 0.
     const int64_t ylim = y1 + WY - 1 < P.H ? y1 + WY - 1 : P.H;
     // A tile's words are all loaded before any of its arithmetic, so that
     // their loads are in flight together.
-    constexpr int NW = W2 ? 3 : 2;
     auto load = [&](int64_t y, uint32_t (&w)[NW], bool check) {
         if (check && y >= ylim) {
 #pragma unroll
@@ -198,7 +235,7 @@ __device__ __forceinline__ void pk_band(const Pack2DParams &P, int lane, int64_t
         }
     };
     auto row = [&](const uint32_t (&w)[NW], V &m, V &n) {
-        Pk<T>::template row<WX>(w[0], w[1], W2 ? w[NW - 1] : 0u, m, n);
+        Pk<T>::template row<WX, NW>(w, m, n);
     };
     V cm[kPkRows], cn[kPkRows];  // row results of the current tile
     {
@@ -247,8 +284,8 @@ __device__ __forceinline__ void pk_band(const Pack2DParams &P, int lane, int64_t
             const uint32_t vm = Pk<T>::pack(WY > P2 ? Pk<T>::mx(am[r], am[r + WY - P2]) : am[r]);
             const uint32_t vn = Pk<T>::pack(WY > P2 ? Pk<T>::mn(an[r], an[r + WY - P2]) : an[r]);
             const int64_t e0 = (obase + yo * P.Wo + x0) * SZ;  // this lane's first output byte
-            if (omax) pk_store<T>(omax + e0, vm, lane, x0, P.Wo, head);
-            if (omin) pk_store<T>(omin + e0, vn, lane, x0, P.Wo, head);
+            if (omax) pk_store<T>(omax + e0, vm, lane, x0, P.Wo, head, nst);
+            if (omin) pk_store<T>(omin + e0, vn, lane, x0, P.Wo, head, nst);
         }
     }
 }
@@ -261,7 +298,8 @@ __global__ void __launch_bounds__(kPkThreads, 2) pack2d_kernel(const Pack2DParam
     const int64_t chunk = task % P.nchunks;
     const int64_t rest = task / P.nchunks;
     const int64_t band = rest % P.nbands, img = rest / P.nbands;
-    const int64_t j = chunk * 31 + lane;  // word column (input and output; lane 31: the halo)
+    const int64_t j = chunk * pk_chunk<T>(P.wx) + lane;  // word column (input and output; lanes past
+                                                         // the chunk: the halo)
     const bool head = chunk == 0;
     const int64_t y0 = band * kPkBand;
     const int64_t y1 = y0 + kPkBand < P.Ho ? y0 + kPkBand : P.Ho;

@@ -11,7 +11,11 @@ constexpr int kPkThreads = 256;
 constexpr int kPkBand = 64;  // output rows per warp task
 constexpr int kPkRows = 8;   // output rows per step
 constexpr int kPkMaxWy = 9;
-template <typename T> constexpr int pk_max_wx() { return sizeof(T) == 1 ? 9 : 5; }
+template <typename T> constexpr int pk_max_wx() { return sizeof(T) == 2 ? 5 : 9; }
+// Output words per warp: 31 and a halo word for the packed types (their rows
+// are realigned across lanes); for f32, 33 - wx and wx - 1 halo words (the
+// row window's next columns come from the next lanes).
+template <typename T> __host__ __device__ constexpr int pk_chunk(int wx) { return sizeof(T) == 4 ? 33 - wx : 31; }
 
 struct Pack2DParams {
     const void *in;
@@ -19,13 +23,13 @@ struct Pack2DParams {
     int64_t nimg, H, W, pitch, img_stride;  // input geometry (elements)
     int64_t Ho, Wo;                         // outputs: image k row y at out + (k*Ho + y)*Wo
     int32_t wy, wx;
-    int32_t nchunks;  // 31-word chunks per output row (a warp each)
+    int32_t nchunks;  // chunks of pk_chunk words per output row (a warp each)
     int32_t nbands;   // bands of kPkBand output rows per image
     int64_t tasks;    // nimg * nbands * nchunks warp tasks
 };
 
 // Launches pack2d_kernel<T, WY> on `grid` CTAs (explicitly instantiated
-// for T in {uint8_t, int16_t} and WY in 1 .. kPkMaxWy).
+// for T in {uint8_t, int16_t, float} and WY in 1 .. kPkMaxWy).
 template <typename T, int WY> cudaError_t pack2d_launch(cudaStream_t stream, const Pack2DParams &P, unsigned grid);
 
 }  // namespace mmf

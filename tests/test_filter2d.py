@@ -77,18 +77,20 @@ def test_2d_fused_odd_width_unpaired(mmf, dtype):
             assert np.array_equal(mx[k].cpu().numpy(), em) and np.array_equal(mn[k].cpu().numpy(), en)
 
 
-@pytest.mark.parametrize("dtype", [np.uint8, np.int16])
+@pytest.mark.parametrize("dtype", [np.uint8, np.int16, np.float32])
 def test_2d_packed_every_window(mmf, dtype):
-    """The packed kernel (fuse = 2): every window up to 9 x 9 (9 x 5 for
-    i16); output widths of every residue modulo the word (rows of the dense
-    outputs start at every byte misalignment), several 32-word chunks per
-    row, bands of 64 rows with a ragged last one, against the literal
+    """The register-streaming kernel (fuse = 2): every window up to 9 x 9
+    (9 x 5 for i16); output widths of every residue modulo the word (rows of
+    the dense outputs start at every byte misalignment), several warp chunks
+    per row, bands of 64 rows with a ragged last one, against the literal
     rectangle."""
     imgs = synth.blobs2d(2, 150, 300, seed=5, dtype=dtype, nblobs=12)
     if dtype == np.int16:
         imgs = (imgs.astype(np.int32) - 16000).astype(np.int16)
+    if dtype == np.float32:
+        imgs = (imgs - np.float32(0.5)).astype(np.float32)
     x = torch.from_numpy(imgs).cuda()
-    maxwx = 9 if dtype == np.uint8 else 5
+    maxwx = 5 if dtype == np.int16 else 9
     for wy in range(1, 10):
         for wx in range(1, maxwx + 1):
             mx, mn = mmf.filter2d(x, wy, wx, fuse=2)
@@ -100,12 +102,12 @@ def test_2d_packed_every_window(mmf, dtype):
     assert mmf.device_status() == 0
 
 
-@pytest.mark.parametrize("dtype", [np.uint8, np.int16])
+@pytest.mark.parametrize("dtype", [np.uint8, np.int16, np.float32])
 def test_2d_packed_pitch_offsets_and_refusals(mmf, dtype):
     """Pitched input rows, output buffers starting at every misalignment, a
     single output column, an image narrower than one word; misaligned input
     rows are refused by the forced packed kernel and take another kernel in
-    the automatic choice."""
+    the automatic choice (f32 rows are always word-aligned)."""
     full = synth.blobs2d(3, 90, 308, seed=6, dtype=dtype, nblobs=7)
     base = torch.from_numpy(full).cuda()
     x = base[:, :, :300]  # pitch 308 elements
@@ -121,7 +123,7 @@ def test_2d_packed_pitch_offsets_and_refusals(mmf, dtype):
         for k in range(n):
             em, en = _expect(full[k, :, :300], wy, wx)
             assert np.array_equal(om[k].cpu().numpy(), em) and np.array_equal(on[k].cpu().numpy(), en), (wy, wx)
-    maxwx = 9 if dtype == np.uint8 else 5
+    maxwx = 5 if dtype == np.int16 else 9
     for W, wx in ((maxwx, maxwx), (3, 2), (2, 1)):
         xs = base[:, :, :W]
         mx, mn = mmf.filter2d(xs, 3, wx, fuse=2)
@@ -129,11 +131,12 @@ def test_2d_packed_pitch_offsets_and_refusals(mmf, dtype):
         for k in range(n):
             em, en = _expect(full[k, :, :W], 3, wx)
             assert np.array_equal(mx[k].cpu().numpy(), em) and np.array_equal(mn[k].cpu().numpy(), en), (W, wx)
-    xo = base[:, :, 1:301]  # rows start one element off a 4-byte boundary
-    with pytest.raises(mmf.MMFError) as e:
-        mmf.filter2d(xo, 3, 3, fuse=2)
-    assert e.value.status == 7
-    mx, mn = mmf.filter2d(xo, 3, 3)
+    xo = base[:, :, 1:301]  # rows start one element off a 4-byte boundary (not for f32)
+    if dtype != np.float32:
+        with pytest.raises(mmf.MMFError) as e:
+            mmf.filter2d(xo, 3, 3, fuse=2)
+        assert e.value.status == 7
+    mx, mn = mmf.filter2d(xo, 3, 3, fuse=2 if dtype == np.float32 else -1)
     torch.cuda.synchronize()
     for k in range(n):
         em, en = _expect(full[k, :, 1:301], 3, 3)
@@ -142,7 +145,7 @@ def test_2d_packed_pitch_offsets_and_refusals(mmf, dtype):
         mmf.filter2d(x, 10, 3, fuse=2)
     assert e.value.status == 7
     with pytest.raises(mmf.MMFError) as e:
-        mmf.filter2d(x.float(), 3, 3, fuse=2)
+        mmf.filter2d(x.double(), 3, 3, fuse=2)
     assert e.value.status == 7
     with pytest.raises(mmf.MMFError) as e:
         mmf.filter2d(x, 3, 3, fuse=3)

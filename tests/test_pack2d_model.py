@@ -1,10 +1,13 @@
-"""CPU model of the packed 2D kernel for 1- and 2-byte elements (windows up
-to 9 x 9 for u8, 5 x 9 for i16), checked against the oracle's literal
-rectangle maximum and minimum.
+"""CPU model of the register-streaming 2D kernel: packed for 1- and 2-byte
+elements (windows up to 9 x 9 for u8, 9 x 5 for i16), one column per word
+for f32 (up to 9 x 9), checked against the oracle's literal rectangle
+maximum and minimum.
 
 Each thread holds one 32-bit word of 4 (u8) or 2 (i16) output columns and
 streams a band of output rows; a warp covers 31 words of a row and its lane
-31 computes the next warp's first word as well (a halo, for the stores).  Row pass: the input words at the thread's
+31 computes the next warp's first word as well (a halo, for the stores); for
+f32 a warp covers 33 - wx words, the window's next columns coming from the
+next lanes (the last wx - 1 lanes a halo whose outputs are not stored).  Row pass: the input words at the thread's
 columns and the next two, the window's elements taken as byte-shifted words
 (funnel shifts of two neighbouring words) and combined per element (SIMD
 max/min of packed lanes).  Column pass: per tile of 8 output rows, the row
@@ -58,15 +61,22 @@ def _model(img, wy, wx, mistake=None):
     sz = img.dtype.itemsize
     L = 4 // sz
     signed = img.dtype == np.int16
+    f32 = img.dtype == np.float32
     Ho, Wo = H - wy + 1, W - wx + 1
     nwc = -(-Wo // L)
-    nchunks = -(-nwc // 31)
+    chunk_w = 33 - wx if f32 else 31  # f32: the last wx-1 lanes are a halo
+    nchunks = -(-nwc // chunk_w)
     out = {"max": np.zeros(Ho * Wo * sz, np.uint8), "min": np.zeros(Ho * Wo * sz, np.uint8)}
     written = {k: np.zeros(Ho * Wo * sz, np.int32) for k in out}
     raw = img.view(np.uint8).reshape(H, W * sz)
 
     def as_val(e):
+        if f32:
+            return float(np.array([e], np.uint32).view(np.float32)[0])
         return e - (1 << 16) if signed and e >= 1 << 15 else e
+
+    def as_bits(v):
+        return int(np.array([v], np.float32).view(np.uint32)[0]) if f32 else v
 
     def row_result(y, j):
         """(max word, min word) of the window row pass at word column j."""
@@ -75,6 +85,11 @@ def _model(img, wy, wx, mistake=None):
         w0, w1, w2 = (_words(raw[y], j + i) for i in range(3))
         m = n = None
         for k in range(wx):
+            if f32:  # word j + k: the next lanes' words, taken by shuffles
+                ev = [as_val(_words(raw[y], j + k))]
+                m = ev if m is None else [max(a, b) for a, b in zip(m, ev)]
+                n = ev if n is None else [min(a, b) for a, b in zip(n, ev)]
+                continue
             b = k * sz  # the kernel's word choice; a funnel shift takes its count modulo 32
             if b < 4:
                 s = _funnel(w0, w1, 8 * b)
@@ -85,10 +100,10 @@ def _model(img, wy, wx, mistake=None):
             ev = [as_val(e) for e in _elems(s, sz)]
             m = ev if m is None else [max(a, b) for a, b in zip(m, ev)]
             n = ev if n is None else [min(a, b) for a, b in zip(n, ev)]
-        return _pack(m, sz), _pack(n, sz)
+        return _pack([as_bits(v) for v in m], sz), _pack([as_bits(v) for v in n], sz)
 
     def col_op(words, opf):
-        return _pack([opf(vs) for vs in zip(*[[as_val(e) for e in _elems(w, sz)] for w in words])], sz)
+        return _pack([as_bits(opf(vs)) for vs in zip(*[[as_val(e) for e in _elems(w, sz)] for w in words])], sz)
 
     for band in range(-(-Ho // BAND)):
         y0, y1 = band * BAND, min(band * BAND + BAND, Ho)
@@ -96,10 +111,10 @@ def _model(img, wy, wx, mistake=None):
             for y in range(y0, y1):
                 rm = {}
                 for lane in range(32):
-                    j = chunk * 31 + lane
+                    j = chunk * chunk_w + lane
                     rows = [row_result(y + i, j) for i in range(wy)]
                     rm[lane] = (col_op([r[0] for r in rows], max), col_op([r[1] for r in rows], min))
-                ob0 = (y * Wo + chunk * 31 * L) * sz  # byte offset of lane 0's first column
+                ob0 = (y * Wo + chunk * chunk_w * L) * sz  # byte offset of lane 0's first column
                 a = ob0 % 4  # the kernel takes it from the address; the output base is 4-aligned here
                 for side, si in (("max", 0), ("min", 1)):
                     def put(byte_off, col, val):
@@ -109,10 +124,10 @@ def _model(img, wy, wx, mistake=None):
                             written[side][byte_off:byte_off + sz] += 1
                     for lane in range(32):
                         v = rm[lane][si]
-                        x0 = (chunk * 31 + lane) * L
+                        x0 = (chunk * chunk_w + lane) * L
                         ob = ob0 + lane * 4
-                        if lane == 31 and mistake != "halo_stores":
-                            continue  # the halo: the next warp's first word
+                        if lane >= chunk_w and mistake != "halo_stores":
+                            continue  # the halo: the next warp's first words
                         if a == 0:
                             for e in range(L):
                                 put(ob + e * sz, x0 + e, _elems(v, sz)[e])
@@ -129,14 +144,18 @@ def _model(img, wy, wx, mistake=None):
     return (out["max"].view(img.dtype).reshape(Ho, Wo), out["min"].view(img.dtype).reshape(Ho, Wo))
 
 
-@pytest.mark.parametrize("dtype", [np.uint8, np.int16])
+@pytest.mark.parametrize("dtype", [np.uint8, np.int16, np.float32])
 @pytest.mark.parametrize("W", [131, 132, 133, 134, 261])
 def test_packed_model_against_rectangle(dtype, W):
+    if dtype == np.float32 and W not in (133, 261):
+        pytest.skip("f32 words are always aligned: two widths suffice")
     rng = np.random.default_rng(W)
     img = synth.blobs2d(1, 75, W, seed=W, dtype=dtype, nblobs=6)[0]
     if dtype == np.int16:
         img = (img.astype(np.int32) - 16000).astype(np.int16)
-    maxwx = 9 if dtype == np.uint8 else 5
+    if dtype == np.float32:
+        img = (img - np.float32(0.5)).astype(np.float32)  # negative values too
+    maxwx = 5 if dtype == np.int16 else 9
     for wy, wx in ((3, 3), (1, 1), (9, maxwx), (2, 1), (1, 4), (int(rng.integers(1, 10)), int(rng.integers(1, maxwx + 1)))):
         gm, gn = _model(img, wy, wx)
         em, en = oracle.bf2d(img, wy, wx)
@@ -151,7 +170,11 @@ def test_packed_model_planted_mistakes():
         img2 = synth.blobs2d(1, 10, 300, seed=1, dtype=np.uint8, nblobs=3)[0]  # three chunks per row
         _model(img2, 2, 3, mistake="halo_stores")
     # Byte offset 8 (u8 windows of 9, i16 of 5) taken as a shift of 32 wraps
-    # to the middle word.
+    # to the middle word; f32 halo lanes that store overwrite the next warp's
+    # words with wrong values.
     gm, gn = _model(img, 1, 9, mistake="funnel_wrap")
     em, en = oracle.bf2d(img, 1, 9)
     assert not (np.array_equal(gm, em) and np.array_equal(gn, en))
+    imf = synth.blobs2d(1, 10, 80, seed=2, dtype=np.float32, nblobs=3)[0]
+    with pytest.raises(AssertionError, match="written"):
+        _model(imf, 2, 5, mistake="halo_stores")
