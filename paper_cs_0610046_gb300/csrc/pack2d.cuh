@@ -169,31 +169,39 @@ template <typename T> __device__ __forceinline__ void pk_put(uint8_t *p, uint32_
         reinterpret_cast<uint32_t *>(p)[e] = w;
 }
 
-// Stores output word v of columns x0 .. x0+L-1 of one row at byte address
-// ob (see the header: aligned words across lanes; a = ob mod 4 is the same
-// on every lane).  Every lane of the warp calls it (the shuffle); head: this
-// is the row's first warp.
-template <typename T>
-__device__ __forceinline__ void pk_store(uint8_t *ob, uint32_t v, int lane, int64_t x0, int64_t Wo, bool head,
-                                         int nst) {
+// Per-lane store facts, the same for every row of a task: whether the lane
+// stores (halo lanes do not), whether it is the row's first lane (it also
+// stores the elements before the first aligned word), and rem = the row's
+// elements from the lane's first column on (Wo - x0, clamped to [0, 8]).
+struct PkLane {
+    bool st, head;
+    int rem;
+};
+
+// Stores output word v of one row at byte address ob (see the header:
+// aligned words across lanes; ob mod 4 is the same on every lane).  Every
+// lane of the warp calls it (the shuffle).
+template <typename T> __device__ __forceinline__ void pk_store(uint8_t *ob, uint32_t v, const PkLane &pl) {
     constexpr int L = Pk<T>::L, SZ = (int)sizeof(T);
-    const int a = (int)((uintptr_t)ob & 3);
+    // sh: bytes of this word before the next aligned word (0 when aligned: the
+    // funnel shift by 0 is v itself), so no branch on the alignment.
+    const int sh = (int)(-(uintptr_t)ob & 3);
     const uint32_t nxt = __shfl_down_sync(0xffffffffu, v, 1);
-    if (lane >= nst) return;  // halo words: the next warp's
-    const int h = a ? (4 - a) / SZ : 0;  // elements of this word before the next aligned word
-    const uint32_t aw = a ? __funnelshift_r(v, nxt, 8 * (4 - a)) : v;
-    uint8_t *ap = ob + (a ? 4 - a : 0);
-    if (x0 + h + L <= Wo) {
+    if (!pl.st) return;  // halo words: the next warp's
+    const int h = sh / SZ;  // elements of this word before the next aligned word
+    const uint32_t aw = __funnelshift_r(v, nxt, 8 * sh);
+    uint8_t *ap = ob + sh;
+    if (h + L <= pl.rem) {
         __stcs(reinterpret_cast<uint32_t *>(ap), aw);
     } else {
 #pragma unroll
         for (int e = 0; e < L; ++e)
-            if (x0 + h + e < Wo) pk_put<T>(ap, aw, e);
+            if (h + e < pl.rem) pk_put<T>(ap, aw, e);
     }
-    if (head && lane == 0) {
+    if (pl.head && h > 0) {
 #pragma unroll
         for (int e = 0; e < L; ++e)
-            if (e < h && x0 + e < Wo) pk_put<T>(ob, v, e);
+            if (e < h && e < pl.rem) pk_put<T>(ob, v, e);
     }
 }
 
@@ -202,7 +210,13 @@ __device__ __forceinline__ void pk_store(uint8_t *ob, uint32_t v, int lane, int6
 template <typename T, int WY, int WX>
 __device__ __forceinline__ void pk_band(const Pack2DParams &P, int lane, int64_t j, bool head, int64_t y0, int64_t y1,
                                         const uint8_t *in, uint8_t *omax, uint8_t *omin, int64_t obase) {
-    const int nst = pk_chunk<T>(WX);  // lanes whose words are stored
+    PkLane pl;
+    pl.st = lane < pk_chunk<T>(WX);  // halo lanes store nothing
+    pl.head = head && lane == 0;
+    {
+        const int64_t rem = P.Wo - j * Pk<T>::L;
+        pl.rem = rem < 0 ? 0 : (rem > 8 ? 8 : (int)rem);
+    }
     using V = typename Pk<T>::V;
     constexpr int L = Pk<T>::L, SZ = (int)sizeof(T);
     constexpr int P2 = WY >= 8 ? 8 : (WY >= 4 ? 4 : (WY >= 2 ? 2 : 1));
@@ -277,15 +291,15 @@ __device__ __forceinline__ void pk_band(const Pack2DParams &P, int lane, int64_t
                 an[i] = Pk<T>::mn(an[i], an[i + p]);
             }
         }
+        const int64_t e0 = (obase + y * P.Wo + x0) * SZ;  // this lane's first output byte of row y
+        const int64_t rowb = P.Wo * SZ;
 #pragma unroll
         for (int r = 0; r < kPkRows; ++r) {
-            const int64_t yo = y + r;
-            if (yo >= y1) break;  // the same on every lane
+            if (y + r >= y1) break;  // the same on every lane
             const uint32_t vm = Pk<T>::pack(WY > P2 ? Pk<T>::mx(am[r], am[r + WY - P2]) : am[r]);
             const uint32_t vn = Pk<T>::pack(WY > P2 ? Pk<T>::mn(an[r], an[r + WY - P2]) : an[r]);
-            const int64_t e0 = (obase + yo * P.Wo + x0) * SZ;  // this lane's first output byte
-            if (omax) pk_store<T>(omax + e0, vm, lane, x0, P.Wo, head, nst);
-            if (omin) pk_store<T>(omin + e0, vn, lane, x0, P.Wo, head, nst);
+            if (omax) pk_store<T>(omax + e0 + r * rowb, vm, pl);
+            if (omin) pk_store<T>(omin + e0 + r * rowb, vn, pl);
         }
     }
 }
