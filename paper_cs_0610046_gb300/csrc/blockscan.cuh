@@ -642,6 +642,25 @@ __device__ __forceinline__ void issue_next(int warp) {
             wi.issued++;
             return;
         }
+        // Steady state of case B (see load_tile): per output tile c the K tile
+        // c+q+1 (read again later as a J tile: kept in L2) and the J tile c.
+        if (l < wi.nloads && wi.ok && wi.caseB && l >= wi.q) {
+            const int r = l - wi.q;
+            const int c = r >> 1;
+            const bool kt = !(r & 1);
+            const int x = kt ? c + wi.q + 1 : c;
+            if ((wi.klast || r != 2 * (wi.NC - 1)) && x >= wi.fast_lo && x < wi.fast_hi) {
+                const int stage = wi.issued & (kStages - 1);
+                uint64_t *bar = S::bar(warp, stage);
+                wi.smode[stage] = wi.fast_smode;
+                fence_proxy_async_smem();
+                copy_pieces<T, HALO>(S::slice(warp, stage), wi.src0 + (uintptr_t)x * G::T_ * sizeof(T),
+                                     wi.fast_extra, bar, kt ? policy_evict_last() : policy_evict_first());
+                wi.l = l + 1;
+                wi.issued++;
+                return;
+            }
+        }
     }
     if (wi.nloads < 0) return;
     if (wi.l >= wi.nloads) {
