@@ -80,6 +80,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return true;
 }
 
+// 16-byte asynchronous copy global -> shared (both addresses 16-byte
+// aligned); bytes < 16 fills the rest with zeros (0: nothing is read).
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc, int bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(smem_dst)), "l"(gsrc), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // L2 eviction-priority policies for cache hints.
 __device__ __forceinline__ uint64_t policy_evict_first() {
     uint64_t p;

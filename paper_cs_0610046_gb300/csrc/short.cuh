@@ -279,6 +279,50 @@ __device__ __forceinline__ typename LbAcc<T>::A lb_term(T qv, typename Elem<T>::
     return part + dd * dd;
 }
 
+// Staging of a warp's next series in shared memory (4- and 8-byte types:
+// 128 bytes per lane), issued while the current series still forms its
+// outputs: lane l's 16-byte chunk c goes to slot c ^ (l mod 8) of its 128
+// bytes, so that the eight lanes of each 16-byte read phase hit eight
+// different bank groups.  Bytes past the series' end are zero (its last
+// element replaces them after the read).  The copy covers PN's identity
+// column, which the reader writes again.
+template <typename T> constexpr bool short_stages() { return sizeof(T) >= 4; }
+
+template <typename T>
+__device__ __forceinline__ void short_stage(const T *nsrc, int nn, int lane, void *stage) {
+    constexpr int CH = ShortGeo<T>::E * (int)sizeof(T) / 16;  // 8 chunks per lane
+    static_assert(CH == 8, "128 bytes per lane");
+    const char *g = reinterpret_cast<const char *>(nsrc);
+    const int total = nn * (int)sizeof(T);
+    char *sb = reinterpret_cast<char *>(stage) + lane * CH * 16;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+        const int off = (lane * CH + c) * 16;
+        const int bytes = total - off < 0 ? 0 : (total - off > 16 ? 16 : total - off);
+        cp_async16(sb + ((c ^ (lane & (CH - 1))) * 16), bytes ? g + off : g, bytes);
+    }
+    cp_async_commit();
+}
+
+template <typename T>
+__device__ __forceinline__ void short_read_staged(const void *stage, int lane,
+                                                  typename Elem<T>::R (&x)[ShortGeo<T>::E]) {
+    constexpr int E = ShortGeo<T>::E, CH = 8, NWD = E * (int)sizeof(T) / 4;
+    cp_async_wait_all();
+    const uint4 *sb = reinterpret_cast<const uint4 *>(reinterpret_cast<const char *>(stage) + lane * CH * 16);
+    uint32_t wd[NWD];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+        const uint4 v = sb[c ^ (lane & (CH - 1))];
+        wd[4 * c] = v.x;
+        wd[4 * c + 1] = v.y;
+        wd[4 * c + 2] = v.z;
+        wd[4 * c + 3] = v.w;
+    }
+    ExtractLoop<T, 0, 0, E>::run(wd, x);
+    __syncwarp();  // every lane's chunks read before the arrays are written again
+}
+
 // One series whose windows are longer than a lane (w - 1 >= E), both sides;
 // returns this lane's part of the envelope lower bound (LB) or zero.
 // Lane j holds positions [jE, jE + E), the last element repeated past the
@@ -295,13 +339,17 @@ __device__ __forceinline__ typename LbAcc<T>::A lb_term(T qv, typename Elem<T>::
 // windows, d < 0) are op(lanes before hi's lane, P[hi]).  The outputs go
 // back through shared memory (max to PM, min in place in SN) so that each
 // store instruction writes 32 consecutive outputs.
+// staged: the series is already in PN (short_stage by the previous call);
+// nsrc (if not null): the warp's next series, nn elements, to stage in PN once
+// this one no longer reads it.
 // Not inlined: the kernel's other decomposition then keeps its own register
 // allocation (inlined together they spill).
 template <typename T, bool LB>
 __device__ __noinline__ typename LbAcc<T>::A short_lanes(const T *src, const T *buf, int64_t buf_n, uint32_t *status,
                                                          int n, int w, int d, int n_out, int lane,
                                                          typename Elem<T>::R *PM, typename Elem<T>::R *PN,
-                                                         typename Elem<T>::R *SN, T *omax, T *omin, const T *qs) {
+                                                         typename Elem<T>::R *SN, T *omax, T *omin, const T *qs,
+                                                         bool staged, const T *nsrc, int nn) {
     using G = ShortGeo<T>;
     using R = typename Elem<T>::R;
     using A = typename LbAcc<T>::A;
@@ -309,7 +357,18 @@ __device__ __noinline__ typename LbAcc<T>::A short_lanes(const T *src, const T *
     const R lo_id = Elem<T>::lo(), hi_id = Elem<T>::hi();
     A part = A(0);
     R x[E];
-    short_load<T>(src, n, lane, buf, buf_n, x, status);
+    if constexpr (short_stages<T>()) {
+        if (staged) {
+            short_read_staged<T>(PN, lane, x);
+            // The staged copy covered PN's identity column (element e·ROW + 32
+            // lies in another lane's slot): write it again.
+            if (lane < E) PN[lane * ROW + 32] = hi_id;
+        } else {
+            short_load<T>(src, n, lane, buf, buf_n, x, status);
+        }
+    } else {
+        short_load<T>(src, n, lane, buf, buf_n, x, status);
+    }
     const int base = lane * E;
     if (base + E > n) {
         const R last = Elem<T>::load(__ldg(src + n - 1));
@@ -384,7 +443,10 @@ __device__ __noinline__ typename LbAcc<T>::A short_lanes(const T *src, const T *
             }
         }
     }
-    __syncwarp();  // every read of PM done
+    __syncwarp();  // every read of PM and PN done
+    if constexpr (short_stages<T>()) {
+        if (nsrc) short_stage<T>(nsrc, nn, lane, PN);  // lands while the outputs leave
+    }
 #pragma unroll
     for (int e = 0; e < E; ++e) PM[e * ROW + lane] = sm[e];
     __syncwarp();
@@ -470,7 +532,10 @@ __global__ void __launch_bounds__(ShortGeo<T>::WARPS * 32, 2) short_kernel(const
         SA[e * G::ROW + 32] = Elem<T>::hi();
     }
     __syncwarp();
+    bool staged = false;  // this warp's series k is already in shared memory
     for (int64_t k = (int64_t)blockIdx.x * G::WARPS + wib; k < P.count; k += nwarps) {
+        const bool cur_staged = staged;
+        staged = false;
         const int64_t sid = P.ids[k];
         const SeriesDesc sd = P.series[sid];
         const int n = (int)sd.n, d = (int)sd.d, n_out = (int)sd.n_out;
@@ -479,10 +544,21 @@ __global__ void __launch_bounds__(ShortGeo<T>::WARPS * 32, 2) short_kernel(const
             if (n > G::NMAX && lane == 0) report_error(P.status, kErrBadItem);
             continue;
         }
+        // The warp's next series: towards L2 now, and into shared memory
+        // (4- and 8-byte types, 16-byte aligned starts, windows longer than a
+        // lane) once this one, if it takes short_lanes too, no longer needs
+        // the staging array.
+        const T *nsrc = nullptr;
+        int nn = 0;
         if (k + nwarps < P.count) {
-            // Bring this warp's next series towards L2 while this one runs.
             const SeriesDesc nx = P.series[P.ids[k + nwarps]];
             if (lane * E < nx.n) prefetch_l2(buf + nx.in_off + lane * E);
+            const int64_t nwi = nx.w < 2 * G::NMAX ? nx.w : 2 * G::NMAX;
+            if (short_stages<T>() && nx.n <= G::NMAX && nx.n_out > 0 && nwi > E &&
+                (((uintptr_t)(buf + nx.in_off)) & 15) == 0) {
+                nsrc = buf + nx.in_off;
+                nn = (int)nx.n;
+            }
         }
         // Windows longer than twice the longest series act like 2·NMAX
         // (every one of them is clipped to the series): 32-bit positions.
@@ -493,7 +569,8 @@ __global__ void __launch_bounds__(ShortGeo<T>::WARPS * 32, 2) short_kernel(const
             T *om = P.out_max ? reinterpret_cast<T *>(P.out_max) + sd.out_off : nullptr;
             T *on = P.out_min ? reinterpret_cast<T *>(P.out_min) + sd.out_off : nullptr;
             part = short_lanes<T, LB>(buf + sd.in_off, buf, P.in_elems, P.status, n, wi, d, n_out, lane, PA, SA,
-                                      SA + E * G::ROW, om, on, qs);
+                                      SA + E * G::ROW, om, on, qs, cur_staged, nsrc, nn);
+            staged = nsrc != nullptr;
         } else {
             // Blocks of w elements, one side after the other; each side loads
             // the series again (L2-resident): the values of one side need not

@@ -122,6 +122,45 @@ def test_short_series_both_decompositions(mmf, dtype, mode):
     _check_batch(mmf, data, lens, ws, mode=mode, in_offsets=offs, dtype=dtype)
 
 
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("mode", ["valid", "envelope"])
+def test_short_series_many_per_warp(mmf, dtype, mode):
+    """Many more short series than warps (each warp takes about eight in
+    turn), so a warp stages its next series in shared memory while it
+    finishes the current one: windows on both sides of the lane width in
+    random order (a staged series follows a lane-block one; a w-block series
+    stages nothing), 16-byte aligned and unaligned starts, lengths below and
+    at the maximum, every series against the oracle."""
+    E = 16 if dtype == np.float64 else 32
+    cap = 32 * E
+    nser = 20_000
+    rng = np.random.default_rng(23 + E + (mode == "envelope"))
+    lens = np.where(rng.random(nser) < 0.5, cap, rng.integers(1, cap + 1, nser))
+    if mode == "valid":
+        ws = np.minimum(np.where(rng.random(nser) < 0.8, rng.integers(E + 1, 3 * E + 40, nser),
+                                 rng.integers(1, E + 1, nser)), lens)
+    else:
+        ws = np.where(rng.random(nser) < 0.8, rng.integers(E // 2, 3 * E, nser), rng.integers(0, E // 2, nser))
+    step = 16 // np.dtype(dtype).itemsize
+    gaps = np.where(rng.random(nser) < 0.7, (-lens) % step, rng.integers(0, step, nser))  # mostly aligned starts
+    offs = np.cumsum(np.concatenate([[0], (lens + gaps)[:-1]]))
+    total = int(offs[-1] + lens[-1])
+    data = synth.random_walk(total, 29, dtype)
+    plan = mmf.BatchPlan(lens, ws, NP2T[dtype], mode, in_offsets=offs)
+    x = torch.from_numpy(data).cuda()
+    mx, mn = plan(x)
+    torch.cuda.synchronize()
+    off = plan.out_offsets()
+    gm, gn = mx.cpu().numpy(), mn.cpu().numpy()
+    plan.close()
+    for s in range(nser):
+        a = data[offs[s]:offs[s] + lens[s]]
+        em, en = oracle.bf1d(a, int(ws[s])) if mode == "valid" else oracle.envelope(a, int(ws[s]))
+        assert np.array_equal(gm[off[s]:off[s] + em.size], em), f"series {s} max (len {lens[s]}, w {ws[s]})"
+        assert np.array_equal(gn[off[s]:off[s] + en.size], en), f"series {s} min (len {lens[s]}, w {ws[s]})"
+    assert mmf.device_status() == 0
+
+
 def test_segments_and_autotune(mmf, tmp_path, monkeypatch):
     monkeypatch.setenv("MMF_AUTOTUNE_CACHE", str(tmp_path / "tune.txt"))
     lens, ws, dists, seeds = synth.uneven_batch(64, seed=8, lo_exp=3.0, hi_exp=5.0)
