@@ -120,7 +120,13 @@ template <typename T> struct ArgParams {
     long long ntiles;  // tiles per block (w > kArgTile), 0 for whole blocks per CTA
     int len_small;     // positions per CTA for whole blocks
     const Agg<typename AKey<T>::K> *pg, *sg;  // per-tile prefix / suffix aggregates
+    uint32_t *status;  // device status word (range checks of a checked build)
+    long long ng;      // aggregates in each of pg and sg
 };
+
+template <typename K> __device__ __forceinline__ Agg<K> agg_empty() {
+    return Agg<K>{KeyLim<K>::lo(), KeyLim<K>::hi(), LLONG_MAX, LLONG_MAX};
+}
 
 template <typename K, typename P> struct ArgScanSmem {
     VI<K, P> qmx[kArgWarps], qmn[kArgWarps], smx[kArgWarps], smn[kArgWarps];
@@ -141,12 +147,15 @@ template <typename K, typename P> __device__ __forceinline__ VI<K, P> jmin(VI<K,
     return b.v < a.v ? b : a;
 }
 
+// status, n_out: range checks of a checked build (outputs hold n_out each).
 template <typename T, typename P>
 __device__ __forceinline__ void store_side(T *oval, long long *oidx, long long base, int nv,
-                                           const typename AKey<T>::K *vs, const P *ps) {
+                                           const typename AKey<T>::K *vs, const P *ps, uint32_t *status,
+                                           long long n_out) {
     using A = AKey<T>;
     using K = typename A::K;
     const int tid = threadIdx.x;
+    auto ok = [&](const void *p, int nb, const void *b0, int esz) { return in_bytes(status, p, nb, b0, n_out * esz); };
     if (oval) {
         constexpr int VW = 16 / (int)sizeof(T);
         T *o = oval + base;
@@ -160,10 +169,12 @@ __device__ __forceinline__ void store_side(T *oval, long long *oidx, long long b
             } pk;
 #pragma unroll
             for (int e = 0; e < VW; ++e) pk.e[e] = A::store(vs[padk<K>(j + e)]);
-            *reinterpret_cast<uint4 *>(o + j) = pk.u;
+            if (ok(o + j, 16, oval, (int)sizeof(T))) *reinterpret_cast<uint4 *>(o + j) = pk.u;
         }
-        for (int j = tid; j < h; j += kArgThreads) o[j] = A::store(vs[padk<K>(j)]);
-        for (int j = h + nvec * VW + tid; j < nv; j += kArgThreads) o[j] = A::store(vs[padk<K>(j)]);
+        for (int j = tid; j < h; j += kArgThreads)
+            if (ok(o + j, (int)sizeof(T), oval, (int)sizeof(T))) o[j] = A::store(vs[padk<K>(j)]);
+        for (int j = h + nvec * VW + tid; j < nv; j += kArgThreads)
+            if (ok(o + j, (int)sizeof(T), oval, (int)sizeof(T))) o[j] = A::store(vs[padk<K>(j)]);
     }
     if (oidx) {
         long long *o = oidx + base;
@@ -174,11 +185,11 @@ __device__ __forceinline__ void store_side(T *oval, long long *oidx, long long b
             longlong2 v;
             v.x = base + (long long)ps[padk<P>(j)];
             v.y = base + (long long)ps[padk<P>(j + 1)];
-            *reinterpret_cast<longlong2 *>(o + j) = v;
+            if (ok(o + j, 16, oidx, 8)) *reinterpret_cast<longlong2 *>(o + j) = v;
         }
-        if (tid == 0 && h) o[0] = base + (long long)ps[padk<P>(0)];
+        if (tid == 0 && h && ok(o, 8, oidx, 8)) o[0] = base + (long long)ps[padk<P>(0)];
         const int tail = h + 2 * nvec;
-        if (tid == 0 && tail < nv) o[tail] = base + (long long)ps[padk<P>(tail)];
+        if (tid == 0 && tail < nv && ok(o + tail, 8, oidx, 8)) o[tail] = base + (long long)ps[padk<P>(tail)];
     }
 }
 
@@ -228,7 +239,9 @@ __global__ void __launch_bounds__(kArgThreads) argscan_kernel(const ArgParams<T>
 #pragma unroll
             for (int k = 0; k < 2 * kArgE; ++k) {
                 const int i = tid + k * kArgThreads;
-                kv[k] = i < lim ? A::load(__ldg(prm.x + base + i)) : KeyLim<K>::pad();
+                kv[k] = i < lim && in_bytes(prm.status, prm.x + base + i, (int)sizeof(T), prm.x, prm.n * (long long)sizeof(T))
+                            ? A::load(__ldg(prm.x + base + i))
+                            : KeyLim<K>::pad();
             }
         } else {
 #pragma unroll
@@ -237,7 +250,10 @@ __global__ void __launch_bounds__(kArgThreads) argscan_kernel(const ArgParams<T>
                 const int off = k < kArgE ? i : i - kArgTile;
                 const int lim = k < kArgE ? xlim : ylim;
                 const long long src = k < kArgE ? base : base + prm.w;
-                kv[k] = off < lim ? A::load(__ldg(prm.x + src + off)) : KeyLim<K>::pad();
+                kv[k] = off < lim && in_bytes(prm.status, prm.x + src + off, (int)sizeof(T), prm.x,
+                                              prm.n * (long long)sizeof(T))
+                            ? A::load(__ldg(prm.x + src + off))
+                            : KeyLim<K>::pad();
             }
         }
 #pragma unroll
@@ -357,12 +373,14 @@ __global__ void __launch_bounds__(kArgThreads) argscan_kernel(const ArgParams<T>
     V cqa = nmx, cqb = nmn, csa = nmx, csb = nmn;
     if (prm.ntiles != 0) {
         if (t > 0) {
-            const Agg<K> a = prm.pg[(b + 1) * prm.ntiles + t - 1];
+            const long long gi = (b + 1) * prm.ntiles + t - 1;
+            const Agg<K> a = in_range(prm.status, gi, 0, prm.ng) ? prm.pg[gi] : agg_empty<K>();
             cqa = V{a.vmax, (P)(a.imax - base)};
             cqb = V{a.vmin, (P)(a.imin - base)};
         }
         if (t + 1 < prm.ntiles) {
-            const Agg<K> a = prm.sg[b * prm.ntiles + t + 1];
+            const long long gi = b * prm.ntiles + t + 1;
+            const Agg<K> a = in_range(prm.status, gi, 0, prm.ng) ? prm.sg[gi] : agg_empty<K>();
             csa = V{a.vmax, (P)(a.imax - base)};
             csb = V{a.vmin, (P)(a.imin - base)};
         }
@@ -428,8 +446,8 @@ __global__ void __launch_bounds__(kArgThreads) argscan_kernel(const ArgParams<T>
     }
     __syncthreads();
     const int nv = (int)min((long long)len, prm.n_out - base);
-    store_side<T, P>(prm.omax, prm.amax, base, nv, vmx, pmx);
-    store_side<T, P>(prm.omin, prm.amin, base, nv, vmn, pmn);
+    store_side<T, P>(prm.omax, prm.amax, base, nv, vmx, pmx, prm.status, prm.n_out);
+    store_side<T, P>(prm.omin, prm.amin, base, nv, vmn, pmn, prm.status, prm.n_out);
 }
 
 // Both sides of a range, any order of positions: larger (smaller) value,
@@ -470,9 +488,6 @@ template <typename K> __device__ __forceinline__ Agg<K> agg_bcast(const Agg<K> &
     return r;
 }
 
-template <typename K> __device__ __forceinline__ Agg<K> agg_empty() {
-    return Agg<K>{KeyLim<K>::lo(), KeyLim<K>::hi(), LLONG_MAX, LLONG_MAX};
-}
 
 // g[b*ntiles + t] = aggregate of x over tile t of block b (clipped to the
 // block and to the array), for blocks 0..nb-1: one warp per tile (64
@@ -480,7 +495,7 @@ template <typename K> __device__ __forceinline__ Agg<K> agg_empty() {
 // tiles.
 template <typename T>
 __global__ void __launch_bounds__(256) argagg_kernel(const T *x, long long n, long long w, long long ntiles,
-                                                    long long nb, Agg<typename AKey<T>::K> *g) {
+                                                    long long nb, Agg<typename AKey<T>::K> *g, uint32_t *status) {
     using A = AKey<T>;
     using K = typename A::K;
     constexpr int PER_LANE = kArgTile / 32, BATCH = 16;
@@ -500,7 +515,9 @@ __global__ void __launch_bounds__(256) argagg_kernel(const T *x, long long n, lo
 #pragma unroll
             for (int k = 0; k < BATCH; ++k) {
                 const int off = lane + (k0 + k) * 32;
-                v[k] = off < lim ? __ldg(xt + off) : T(0);
+                v[k] = off < lim && in_bytes(status, xt + off, (int)sizeof(T), x, n * (long long)sizeof(T))
+                           ? __ldg(xt + off)
+                           : T(0);
             }
 #pragma unroll
             for (int k = 0; k < BATCH; ++k) {
@@ -521,7 +538,7 @@ __global__ void __launch_bounds__(256) argagg_kernel(const T *x, long long n, lo
         Agg<K> a{vmax, vmin, omax < 0 ? LLONG_MAX : lo + omax, omin < 0 ? LLONG_MAX : lo + omin};
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) agg_join(a, agg_shfl_down(a, d));
-        if (lane == 0) g[u] = a;
+        if (lane == 0 && in_range(status, u, 0, nb * ntiles)) g[u] = a;
     }
 }
 
@@ -529,7 +546,7 @@ __global__ void __launch_bounds__(256) argagg_kernel(const T *x, long long n, lo
 // one warp per block, 32 tiles at a time.
 template <typename K>
 __global__ void __launch_bounds__(kArgThreads) argblock_scan_kernel(const Agg<K> *g, long long ntiles, long long nb,
-                                                                   Agg<K> *pg, Agg<K> *sg) {
+                                                                   Agg<K> *pg, Agg<K> *sg, uint32_t *status) {
     const int lane = threadIdx.x & 31;
     const long long b = (long long)blockIdx.x * kArgWarps + (threadIdx.x >> 5);
     if (b >= nb) return;  // the kernel has no barriers
@@ -537,7 +554,7 @@ __global__ void __launch_bounds__(kArgThreads) argblock_scan_kernel(const Agg<K>
     Agg<K> carry = agg_empty<K>();
     for (long long t0 = 0; t0 < ntiles; t0 += 32) {
         const long long t = t0 + lane;
-        Agg<K> a = t < ntiles ? gb[t] : agg_empty<K>();
+        Agg<K> a = t < ntiles && in_range(status, b * ntiles + t, 0, nb * ntiles) ? gb[t] : agg_empty<K>();
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const Agg<K> l = agg_shfl_up(a, d);
@@ -549,20 +566,20 @@ __global__ void __launch_bounds__(kArgThreads) argblock_scan_kernel(const Agg<K>
         }
         Agg<K> m = carry;
         agg_join(m, a);
-        if (t < ntiles) pg[b * ntiles + t] = m;
+        if (t < ntiles && in_range(status, b * ntiles + t, 0, nb * ntiles)) pg[b * ntiles + t] = m;
         carry = agg_bcast(m, 31);
     }
     carry = agg_empty<K>();
     for (long long t1 = ntiles; t1 > 0; t1 -= 32) {
         const long long t = t1 - 32 + lane;  // lanes below 0 hold nothing
-        Agg<K> a = t >= 0 ? gb[t] : agg_empty<K>();
+        Agg<K> a = t >= 0 && in_range(status, b * ntiles + t, 0, nb * ntiles) ? gb[t] : agg_empty<K>();
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const Agg<K> r = agg_shfl_down(a, d);
             if (lane + d < 32) agg_join(a, r);
         }
         agg_join(a, carry);
-        if (t >= 0) sg[b * ntiles + t] = a;
+        if (t >= 0 && in_range(status, b * ntiles + t, 0, nb * ntiles)) sg[b * ntiles + t] = a;
         carry = agg_bcast(a, 0);
     }
 }
@@ -597,7 +614,7 @@ cudaError_t argscan_1d(const LaunchCtx &ctx, const void *in, int64_t n, int64_t 
     if (n_out <= 0) return cudaSuccess;
     ArgParams<T> prm{static_cast<const T *>(in), n, w, n_out, static_cast<T *>(omax), static_cast<T *>(omin),
                      reinterpret_cast<long long *>(amax), reinterpret_cast<long long *>(amin), 0, 0, nullptr,
-                     nullptr};
+                     nullptr, ctx.status, 0};
     // Offsets from a tile's base stay below w + kArgTile: 32-bit up to 2^30.
     const bool wide = w >= (int64_t(1) << 30);
     if (w <= kArgTile) {
@@ -619,17 +636,18 @@ cudaError_t argscan_1d(const LaunchCtx &ctx, const void *in, int64_t n, int64_t 
     const int64_t sms = ctx.sms > 0 ? ctx.sms : 1;
     const int64_t agg_warps = (int64_t)ng < sms * 64 ? (int64_t)ng : sms * 64;  // 8 CTAs of 8 warps per SM
     argagg_kernel<T><<<(unsigned)((agg_warps + 7) / 8), 256, 0, ctx.stream>>>(static_cast<const T *>(in), n, w,
-                                                                             ntiles, nb, g);
+                                                                             ntiles, nb, g, ctx.status);
     e = cudaGetLastError();
     if (e == cudaSuccess) {
         argblock_scan_kernel<K><<<(unsigned)((nb + kArgWarps - 1) / kArgWarps), kArgThreads, 0, ctx.stream>>>(
-            g, ntiles, nb, pg, sg);
+            g, ntiles, nb, pg, sg, ctx.status);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
         prm.ntiles = ntiles;
         prm.pg = pg;
         prm.sg = sg;
+        prm.ng = (long long)ng;
         e = wide ? arg_launch<T, unsigned long long, 2 * kArgTile>(ctx, prm, nbo * ntiles)
                  : arg_launch<T, unsigned, 2 * kArgTile>(ctx, prm, nbo * ntiles);
     }

@@ -266,6 +266,7 @@ mmf_status capture(mmf_batch_plan *p, const void *in, void *omax, void *omin) {
 
 // Envelope lower bound: accumulators cleared before the launches, square
 // roots taken after them.
+// (Their index is the loop's, below n: nothing to range-check.)
 __global__ void lb_clear_kernel(double *acc, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         acc[i] = 0.0;

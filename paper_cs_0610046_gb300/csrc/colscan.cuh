@@ -44,6 +44,7 @@ struct ColParams {
     int32_t strips;               // column strips per image
     int32_t qcap;                 // tile-aggregate ring entries per thread (>= q+2)
     uint32_t *status;
+    int64_t src_elems, out_elems; // readable elements from each source, writable from each output
 };
 
 constexpr int kColThreads = 256;
@@ -97,13 +98,15 @@ extern __shared__ __align__(16) uint8_t col_smem[];
 
 // Loads one 8-row tile (rows y..y+7 of this thread's columns) of one source;
 // rows outside [0, H) read as the identity `pad`.
+// base, elems: the source buffer (range checks of a checked build).
 template <typename T, int CPT>
-__device__ __forceinline__ void col_tile(const T *col, int64_t pitch, int64_t y, int64_t H,
-                                         typename Elem<T>::R pad,
+__device__ __forceinline__ void col_tile(const ColParams &P, const T *base, const T *col, int64_t pitch, int64_t y,
+                                         int64_t H, typename Elem<T>::R pad,
                                          typename Elem<T>::R (&v)[kColRows][CPT]) {
 #pragma unroll
     for (int r = 0; r < kColRows; ++r) {
-        if (y + r >= 0 && y + r < H) {
+        if (y + r >= 0 && y + r < H &&
+            in_bytes(P.status, col + (y + r) * pitch, CPT * (int)sizeof(T), base, P.src_elems * (int64_t)sizeof(T))) {
             RowVec<T, CPT>::load(col + (y + r) * pitch, v[r]);
         } else {
 #pragma unroll
@@ -117,9 +120,10 @@ template <typename T, int CPT> struct SepSrc {
     using R = typename Elem<T>::R;
     const T *smax, *smin;
     int64_t pitch, H;
+    const ColParams *P;
     __device__ __forceinline__ void tile(int64_t y, R (&vm)[kColRows][CPT], R (&vn)[kColRows][CPT]) const {
-        col_tile<T, CPT>(smax, pitch, y, H, Elem<T>::lo(), vm);
-        col_tile<T, CPT>(smin, pitch, y, H, Elem<T>::hi(), vn);
+        col_tile<T, CPT>(*P, reinterpret_cast<const T *>(P->src_max), smax, pitch, y, H, Elem<T>::lo(), vm);
+        col_tile<T, CPT>(*P, reinterpret_cast<const T *>(P->src_min), smin, pitch, y, H, Elem<T>::hi(), vn);
     }
 };
 
@@ -128,6 +132,12 @@ template <typename T, int CPT> struct FusedSrc {
     const T *img;  // this thread's first column of the image
     int64_t pitch, H;
     int wx;
+    const ColParams *P;
+    __device__ __forceinline__ R ld(const T *p) const {
+        return in_bytes(P->status, p, (int)sizeof(T), P->src_max, P->src_elems * (int64_t)sizeof(T))
+                   ? Elem<T>::load(__ldg(p))
+                   : R(0);
+    }
     __device__ __forceinline__ void tile(int64_t y, R (&vm)[kColRows][CPT], R (&vn)[kColRows][CPT]) const {
 #pragma unroll
         for (int r = 0; r < kColRows; ++r) {
@@ -135,12 +145,12 @@ template <typename T, int CPT> struct FusedSrc {
                 const T *row = img + (y + r) * pitch;
                 R m[CPT], n[CPT];
 #pragma unroll
-                for (int c = 0; c < CPT; ++c) m[c] = n[c] = Elem<T>::load(__ldg(row + c));
+                for (int c = 0; c < CPT; ++c) m[c] = n[c] = ld(row + c);
                 // Elements c+1 .. c+wx-1 of column c; element j serves
                 // every column c with c < j <= c + wx - 1.
 #pragma unroll 4
                 for (int j = 1; j < wx + CPT - 1; ++j) {
-                    const R v = Elem<T>::load(__ldg(row + j));
+                    const R v = ld(row + j);
 #pragma unroll
                     for (int c = 0; c < CPT; ++c)
                         if (j >= c + 1 && j <= c + wx - 1) { m[c] = vmax(m[c], v); n[c] = vmin(n[c], v); }
@@ -155,12 +165,15 @@ template <typename T, int CPT> struct FusedSrc {
     }
 };
 
+// base: the output buffer (range checks of a checked build).
 template <typename T, int CPT>
-__device__ __forceinline__ void col_store(T *col, int64_t pitch, int64_t y, int64_t Ho,
-                                          const typename Elem<T>::R (&v)[kColRows][CPT]) {
+__device__ __forceinline__ void col_store(const ColParams &P, const void *base, T *col, int64_t pitch, int64_t y,
+                                          int64_t Ho, const typename Elem<T>::R (&v)[kColRows][CPT]) {
 #pragma unroll
     for (int r = 0; r < kColRows; ++r)
-        if (y + r < Ho) RowVec<T, CPT>::store(col + (y + r) * pitch, v[r]);
+        if (y + r < Ho &&
+            in_bytes(P.status, col + (y + r) * pitch, CPT * (int)sizeof(T), base, P.out_elems * (int64_t)sizeof(T)))
+            RowVec<T, CPT>::store(col + (y + r) * pitch, v[r]);
 }
 
 template <typename T, int CPT, int W, typename Src>
@@ -192,8 +205,8 @@ __device__ __forceinline__ void col_slide(const ColParams &P, const Src &src, T 
                 on[r][c] = W > P2 ? vmin(an[r], an[r + W - P2]) : an[r];
             }
         }
-        if (omax) col_store<T, CPT>(omax, P.out_pitch, y, Ho, om);
-        if (omin) col_store<T, CPT>(omin, P.out_pitch, y, Ho, on);
+        if (omax) col_store<T, CPT>(P, P.out_max, omax, P.out_pitch, y, Ho, om);
+        if (omin) col_store<T, CPT>(P, P.out_min, omin, P.out_pitch, y, Ho, on);
 #pragma unroll
         for (int r = 0; r < kColRows; ++r)
 #pragma unroll
@@ -316,8 +329,8 @@ __device__ __forceinline__ void col_blocks(const ColParams &P, const Src &src, T
                 on[i][cc] = vmin(vmin(cjn[i][cc], far ? n2 : n1), Elem<T>::pmin(pk));
             }
         }
-        if (omax) col_store<T, CPT>(omax, P.out_pitch, (int64_t)c * kColRows, Ho, om);
-        if (omin) col_store<T, CPT>(omin, P.out_pitch, (int64_t)c * kColRows, Ho, on);
+        if (omax) col_store<T, CPT>(P, P.out_max, omax, P.out_pitch, (int64_t)c * kColRows, Ho, om);
+        if (omin) col_store<T, CPT>(P, P.out_min, omin, P.out_pitch, (int64_t)c * kColRows, Ho, on);
     }
 }
 
@@ -348,11 +361,11 @@ __global__ void __launch_bounds__(kColThreads) colscan_kernel(const ColParams P)
     T *omin = P.out_min ? reinterpret_cast<T *>(P.out_min) + img * P.out_img + x : nullptr;
     if constexpr (FUSED) {
         const FusedSrc<T, CPT> src{reinterpret_cast<const T *>(P.src_max) + img * P.in_img + x, P.in_pitch, P.H,
-                                   P.wx};
+                                   P.wx, &P};
         col_dispatch<T, CPT>(P, src, omax, omin, Ho);
     } else {
         const SepSrc<T, CPT> src{reinterpret_cast<const T *>(P.src_max) + img * P.in_img + x,
-                                 reinterpret_cast<const T *>(P.src_min) + img * P.in_img + x, P.in_pitch, P.H};
+                                 reinterpret_cast<const T *>(P.src_min) + img * P.in_img + x, P.in_pitch, P.H, &P};
         col_dispatch<T, CPT>(P, src, omax, omin, Ho);
     }
 }

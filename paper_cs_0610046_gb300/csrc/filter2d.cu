@@ -102,6 +102,9 @@ static cudaError_t pack_launch(const LaunchCtx &ctx, const T *in, int64_t nimg, 
         P.Wo = W - wx + 1;
         P.wy = (int)wy;
         P.wx = (int)wx;
+        P.status = ctx.status;
+        P.in_bytes = ((nimg - 1) * P.img_stride + (H - 1) * pitch + W) * (int64_t)sizeof(T);
+        P.out_bytes = nimg * P.Ho * P.Wo * (int64_t)sizeof(T);
         constexpr int L = 4 / (int)sizeof(T);  // columns per 32-bit word
         const int64_t words = (P.Wo + L - 1) / L;
         const int chunk = pk_chunk<T>((int)wx);
@@ -143,6 +146,9 @@ static cudaError_t tile_launch(const LaunchCtx &ctx, const T *in, int64_t nimg, 
     P.wx = (int)wx;
     P.tiles_x = (int)((P.Wo + kTC - 1) / kTC);
     P.tiles_y = (int)((P.Ho + kTR - 1) / kTR);
+    P.status = ctx.status;
+    P.in_elems = (nimg - 1) * P.img_stride + (H - 1) * pitch + W;
+    P.out_elems = nimg * P.Ho * P.Wo;
     const int64_t grid = nimg * P.tiles_x * P.tiles_y;
     if (grid <= 0) return cudaSuccess;
     if (grid > 0x7fffffff) return cudaErrorInvalidValue;
@@ -231,6 +237,7 @@ static mmf_status filter2d(const LaunchCtx &ctx, const T *in, int64_t nimg, int6
     P.Wc = Wo;
     P.out_pitch = Wo;
     P.out_img = Ho * Wo;
+    P.out_elems = nimg * Ho * Wo;
     P.wy = (int)wy;
     P.wx = (int)wx;
     const bool fused = use_fused(wy, wx, fuse);
@@ -243,6 +250,7 @@ static mmf_status filter2d(const LaunchCtx &ctx, const T *in, int64_t nimg, int6
         P.src_min = in;
         P.in_pitch = pitch;
         P.in_img = H * pitch;
+        P.src_elems = (nimg - 1) * H * pitch + (H - 1) * pitch + W;
     } else {
         const int64_t wp = mid_pitch(Wo);
         T *rmax = static_cast<T *>(work);
@@ -256,6 +264,7 @@ static mmf_status filter2d(const LaunchCtx &ctx, const T *in, int64_t nimg, int6
         P.src_min = rmin;
         P.in_pitch = wp;
         P.in_img = H * wp;
+        P.src_elems = nimg * H * wp;
     }
     e = col_launch<T>(ctx, P, fused);
     return e == cudaSuccess ? MMF_OK : cuda_error(e, "column pass");

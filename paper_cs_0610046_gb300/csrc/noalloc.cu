@@ -80,21 +80,22 @@ static std::mutex g_noalloc_mu;
 
 // Copies one chunk of table bytes from the kernel's arguments into the device
 // tables (one CTA; the arguments are read in place).
-__global__ void noalloc_upload_kernel(const __grid_constant__ TableChunk c, uint8_t *tables) {
+__global__ void noalloc_upload_kernel(const __grid_constant__ TableChunk c, uint8_t *tables, uint32_t *status) {
     const uint32_t *src = reinterpret_cast<const uint32_t *>(c.data);
     uint32_t *dst = reinterpret_cast<uint32_t *>(tables + c.off);
-    for (uint32_t i = threadIdx.x; i < c.bytes / 4; i += blockDim.x) dst[i] = src[i];
+    for (uint32_t i = threadIdx.x; i < c.bytes / 4; i += blockDim.x)
+        if (in_bytes(status, dst + i, 4, tables, (int64_t)sizeof(NoAllocTables))) dst[i] = src[i];
 }
 
 // Uploads bytes [off, off + bytes) of the staging image on stream cs.
-cudaError_t upload(uint8_t *d_tables, uint32_t off, uint32_t bytes, cudaStream_t cs) {
+cudaError_t upload(uint8_t *d_tables, uint32_t off, uint32_t bytes, cudaStream_t cs, uint32_t *status) {
     const uint8_t *img = reinterpret_cast<const uint8_t *>(&g_img);
     for (uint32_t done = 0; done < bytes; done += kChunk) {
         const uint32_t b = bytes - done < kChunk ? bytes - done : kChunk;
         g_chunk.off = off + done;
         g_chunk.bytes = (b + 7) & ~7u;
         std::memcpy(g_chunk.data, img + off + done, g_chunk.bytes);
-        void *args[] = {&g_chunk, &d_tables};
+        void *args[] = {&g_chunk, &d_tables, &status};
         // The arguments are copied at launch: g_chunk is free again on return.
         cudaError_t e = cudaLaunchKernel((const void *)noalloc_upload_kernel, dim3(1), dim3(256), args, 0, cs);
         if (e != cudaSuccess) return e;
@@ -192,9 +193,10 @@ extern "C" mmf_status mmf_filter1d_batched_noalloc(const void *d_in, const int64
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     uint8_t *d_tab = reinterpret_cast<uint8_t *>(tab);
     // Counters and series (contiguous from the start), then the items.
-    cudaError_t e = upload(d_tab, 0, (uint32_t)(offsetof(NoAllocTables, series) + nseries * sizeof(SeriesDesc)), cs);
+    cudaError_t e =
+        upload(d_tab, 0, (uint32_t)(offsetof(NoAllocTables, series) + nseries * sizeof(SeriesDesc)), cs, ctx.status);
     if (e == cudaSuccess && ni > 0)
-        e = upload(d_tab, (uint32_t)offsetof(NoAllocTables, items), (uint32_t)(ni * sizeof(ItemDesc)), cs);
+        e = upload(d_tab, (uint32_t)offsetof(NoAllocTables, items), (uint32_t)(ni * sizeof(ItemDesc)), cs, ctx.status);
     if (e != cudaSuccess) return cuda_error(e, "upload no-allocation tables");
     for (int g = 0; g < kGroups; ++g) {
         const int64_t n_items = group_begin[g + 1] - group_begin[g];

@@ -40,6 +40,7 @@
 #include <cstdint>
 
 #include "pack2d.h"
+#include "ptx.cuh"
 
 namespace mmf {
 
@@ -149,18 +150,27 @@ template <> struct Pk<float> {
     }
 };
 
+// A 4-byte input word at p (range-checked in a checked build: 0 outside).
+__device__ __forceinline__ uint32_t pk_ld(const Pack2DParams &P, const uint8_t *p) {
+    return in_bytes(P.status, p, 4, P.in, P.in_bytes) ? __ldg(reinterpret_cast<const uint32_t *>(p)) : 0u;
+}
+
 // Word j of an input row (bytes [4j, 4j+4)), zero past the row's `rb` bytes.
-__device__ __forceinline__ uint32_t pk_word(const uint8_t *row, int64_t j, int64_t rb) {
+__device__ __forceinline__ uint32_t pk_word(const Pack2DParams &P, const uint8_t *row, int64_t j, int64_t rb) {
     const int64_t b = 4 * j;
-    if (b + 4 <= rb) return __ldg(reinterpret_cast<const uint32_t *>(row + b));
+    if (b + 4 <= rb) return pk_ld(P, row + b);
     uint32_t w = 0;
     for (int i = 0; i < 4; ++i)
-        if (b + i < rb) w |= (uint32_t)__ldg(row + b + i) << (8 * i);
+        if (b + i < rb && in_bytes(P.status, row + b + i, 1, P.in, P.in_bytes))
+            w |= (uint32_t)__ldg(row + b + i) << (8 * i);
     return w;
 }
 
 // Element e (0 .. L-1) of word w to p, if its column is below Wo.
-template <typename T> __device__ __forceinline__ void pk_put(uint8_t *p, uint32_t w, int e) {
+// ob: the output buffer (range checks of a checked build).
+template <typename T>
+__device__ __forceinline__ void pk_put(const Pack2DParams &P, const uint8_t *ob, uint8_t *p, uint32_t w, int e) {
+    if (!in_bytes(P.status, p + e * (int)sizeof(T), (int)sizeof(T), ob, P.out_bytes)) return;
     if constexpr (sizeof(T) == 1)
         p[e] = (uint8_t)(w >> (8 * e));
     else if constexpr (sizeof(T) == 2)
@@ -181,7 +191,9 @@ struct PkLane {
 // Stores output word v of one row at byte address ob (see the header:
 // aligned words across lanes; ob mod 4 is the same on every lane).  Every
 // lane of the warp calls it (the shuffle).
-template <typename T> __device__ __forceinline__ void pk_store(uint8_t *ob, uint32_t v, const PkLane &pl) {
+template <typename T>
+__device__ __forceinline__ void pk_store(const Pack2DParams &P, const uint8_t *obuf, uint8_t *ob, uint32_t v,
+                                         const PkLane &pl) {
     constexpr int L = Pk<T>::L, SZ = (int)sizeof(T);
     // sh: bytes of this word before the next aligned word (0 when aligned: the
     // funnel shift by 0 is v itself), so no branch on the alignment.
@@ -192,16 +204,16 @@ template <typename T> __device__ __forceinline__ void pk_store(uint8_t *ob, uint
     const uint32_t aw = __funnelshift_r(v, nxt, 8 * sh);
     uint8_t *ap = ob + sh;
     if (h + L <= pl.rem) {
-        __stcs(reinterpret_cast<uint32_t *>(ap), aw);
+        if (in_bytes(P.status, ap, 4, obuf, P.out_bytes)) __stcs(reinterpret_cast<uint32_t *>(ap), aw);
     } else {
 #pragma unroll
         for (int e = 0; e < L; ++e)
-            if (h + e < pl.rem) pk_put<T>(ap, aw, e);
+            if (h + e < pl.rem) pk_put<T>(P, obuf, ap, aw, e);
     }
     if (pl.head && h > 0) {
 #pragma unroll
         for (int e = 0; e < L; ++e)
-            if (e < h && e < pl.rem) pk_put<T>(ob, v, e);
+            if (e < h && e < pl.rem) pk_put<T>(P, obuf, ob, v, e);
     }
 }
 
@@ -242,10 +254,10 @@ __device__ __forceinline__ void pk_band(const Pack2DParams &P, int lane, int64_t
         if (interior) {
             const uint32_t *q = reinterpret_cast<const uint32_t *>(rp) + j;
 #pragma unroll
-            for (int k = 0; k < NW; ++k) w[k] = __ldg(q + k);
+            for (int k = 0; k < NW; ++k) w[k] = pk_ld(P, reinterpret_cast<const uint8_t *>(q + k));
         } else {
 #pragma unroll
-            for (int k = 0; k < NW; ++k) w[k] = pk_word(rp, j + k, rb);
+            for (int k = 0; k < NW; ++k) w[k] = pk_word(P, rp, j + k, rb);
         }
     };
     auto row = [&](const uint32_t (&w)[NW], V &m, V &n) {
@@ -298,8 +310,8 @@ __device__ __forceinline__ void pk_band(const Pack2DParams &P, int lane, int64_t
             if (y + r >= y1) break;  // the same on every lane
             const uint32_t vm = Pk<T>::pack(WY > P2 ? Pk<T>::mx(am[r], am[r + WY - P2]) : am[r]);
             const uint32_t vn = Pk<T>::pack(WY > P2 ? Pk<T>::mn(an[r], an[r + WY - P2]) : an[r]);
-            if (omax) pk_store<T>(omax + e0 + r * rowb, vm, pl);
-            if (omin) pk_store<T>(omin + e0 + r * rowb, vn, pl);
+            if (omax) pk_store<T>(P, omax, omax + e0 + r * rowb, vm, pl);
+            if (omin) pk_store<T>(P, omin, omin + e0 + r * rowb, vn, pl);
         }
     }
 }

@@ -26,6 +26,8 @@ struct Pack2DParams {
     int32_t nchunks;  // chunks of pk_chunk words per output row (a warp each)
     int32_t nbands;   // bands of kPkBand output rows per image
     int64_t tasks;    // nimg * nbands * nchunks warp tasks
+    uint32_t *status;                // device status word (range checks of a checked build)
+    int64_t in_bytes, out_bytes;     // readable bytes from `in`, writable from each output
 };
 
 // Launches pack2d_kernel<T, WY> on `grid` CTAs (explicitly instantiated

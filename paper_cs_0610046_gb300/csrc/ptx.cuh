@@ -155,6 +155,18 @@ __device__ __forceinline__ void report_error(uint32_t *status, uint32_t bits) {
 // sanitizer): in a checked build (MMF_CHECKED) it records kErrRange and
 // returns false when i lies outside [lo, hi), and the caller skips the
 // access; otherwise it is always true and costs nothing.
+// The same for an access of n bytes at p inside a buffer of len bytes at base.
+__device__ __forceinline__ bool in_bytes(uint32_t *status, const void *p, int n, const void *base, int64_t len) {
+    if constexpr (!kChecked) {
+        return true;
+    } else {
+        const int64_t off = reinterpret_cast<const char *>(p) - reinterpret_cast<const char *>(base);
+        if (off >= 0 && off + n <= len) return true;
+        report_error(status, kErrRange);
+        return false;
+    }
+}
+
 __device__ __forceinline__ bool in_range(uint32_t *status, int64_t i, int64_t lo, int64_t hi) {
     if constexpr (!kChecked) {
         return true;

@@ -46,17 +46,18 @@ mmf_status get_ctx(void *stream, LaunchCtx *ctx);
 int elem_size(mmf_dtype dt);
 
 // Copies the new halo of each stream of a batch: the last h_new elements of
-// its staging block [halo | chunk].
+// its staging block [halo | chunk].  lim: elements of the staging arena at
+// base (range checks of a checked build).
 template <typename T>
 __global__ void halo_update_kernel(const SeriesDesc *series, const int64_t *halo_off, const int64_t *h_new,
-                                   T *base, int n) {
+                                   T *base, int n, int64_t lim, uint32_t *status) {
     const int i = blockIdx.x;
     if (i >= n) return;
     const SeriesDesc sd = series[i];
     const int64_t h = h_new[i];
-    const T *src = base + sd.in_off + sd.n - h;
-    T *dst = base + halo_off[i];
-    for (int64_t k = threadIdx.x; k < h; k += blockDim.x) dst[k] = src[k];
+    const int64_t s0 = sd.in_off + sd.n - h, d0 = halo_off[i];
+    for (int64_t k = threadIdx.x; k < h; k += blockDim.x)
+        if (in_range(status, s0 + k, 0, lim) && in_range(status, d0 + k, 0, lim)) base[d0 + k] = base[s0 + k];
 }
 // Per-chunk copy descriptor of a batch (offsets in elements).
 struct ChunkCopy {
@@ -70,25 +71,33 @@ struct ChunkCopy {
 // stream's device state, the chunk straight from host memory (over the
 // CPU-GPU link).  blockIdx.y strides over the chunk.
 template <typename T>
-__global__ void gather_kernel(const ChunkCopy *cc, int n, T *base) {
+__global__ void gather_kernel(const ChunkCopy *cc, int n, T *base, int64_t lim, uint32_t *status) {
     const int i = blockIdx.x;
     if (i >= n) return;
     const ChunkCopy c = cc[i];
     T *stage = base + c.stage_off;
     const int64_t tot = c.halo_len + c.len;
     const int64_t stride = (int64_t)gridDim.y * blockDim.x;
-    for (int64_t k = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; k < tot; k += stride)
-        stage[k] = k < c.halo_len ? base[c.halo_off + k] : static_cast<const T *>(c.h_in)[k - c.halo_len];
+    for (int64_t k = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; k < tot; k += stride) {
+        if (!in_range(status, c.stage_off + k, 0, lim)) continue;
+        if (k < c.halo_len)
+            stage[k] = in_range(status, c.halo_off + k, 0, lim) ? base[c.halo_off + k] : T(0);
+        else
+            stage[k] = static_cast<const T *>(c.h_in)[k - c.halo_len];  // k - halo_len < len: the chunk
+    }
 }
 
 // Writes every chunk's outputs straight to its host buffers.
+// lim: elements of each output half (range checks of a checked build).
 template <typename T>
-__global__ void scatter_kernel(const ChunkCopy *cc, int n, const T *omax, const T *omin) {
+__global__ void scatter_kernel(const ChunkCopy *cc, int n, const T *omax, const T *omin, int64_t lim,
+                               uint32_t *status) {
     const int i = blockIdx.x;
     if (i >= n) return;
     const ChunkCopy c = cc[i];
     const int64_t stride = (int64_t)gridDim.y * blockDim.x;
     for (int64_t k = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; k < c.n_out; k += stride) {
+        if (!in_range(status, c.out_off + k, 0, lim)) continue;
         if (c.h_max) static_cast<T *>(c.h_max)[k] = omax[c.out_off + k];
         if (c.h_min) static_cast<T *>(c.h_min)[k] = omin[c.out_off + k];
     }
@@ -196,14 +205,15 @@ cudaError_t launch_group(mmf_server *S, const LaunchCtx &ctx, int g, int slot, c
     }
 }
 
-cudaError_t launch_halo(mmf_server *S, int slot, int n, cudaStream_t st) {
+cudaError_t launch_halo(mmf_server *S, int slot, int n, cudaStream_t st, uint32_t *status) {
     const int64_t *hoff = S->d_halo[slot];
     const int64_t *hnew = hoff + S->max_batch;
+    const int64_t lim = (int64_t)S->stage_size / S->esz;
     switch (S->dtype) {
-        case MMF_F32: halo_update_kernel<float><<<n, 256, 0, st>>>(S->d_series[slot], hoff, hnew, (float *)S->dev_base, n); break;
-        case MMF_F64: halo_update_kernel<double><<<n, 256, 0, st>>>(S->d_series[slot], hoff, hnew, (double *)S->dev_base, n); break;
-        case MMF_I16: halo_update_kernel<int16_t><<<n, 256, 0, st>>>(S->d_series[slot], hoff, hnew, (int16_t *)S->dev_base, n); break;
-        default: halo_update_kernel<uint8_t><<<n, 256, 0, st>>>(S->d_series[slot], hoff, hnew, (uint8_t *)S->dev_base, n); break;
+        case MMF_F32: halo_update_kernel<float><<<n, 256, 0, st>>>(S->d_series[slot], hoff, hnew, (float *)S->dev_base, n, lim, status); break;
+        case MMF_F64: halo_update_kernel<double><<<n, 256, 0, st>>>(S->d_series[slot], hoff, hnew, (double *)S->dev_base, n, lim, status); break;
+        case MMF_I16: halo_update_kernel<int16_t><<<n, 256, 0, st>>>(S->d_series[slot], hoff, hnew, (int16_t *)S->dev_base, n, lim, status); break;
+        default: halo_update_kernel<uint8_t><<<n, 256, 0, st>>>(S->d_series[slot], hoff, hnew, (uint8_t *)S->dev_base, n, lim, status); break;
     }
     return cudaGetLastError();
 }
@@ -319,13 +329,16 @@ bool run_batch(mmf_server *S, std::unique_lock<std::mutex> &lk) {
     }
     if (e == cudaSuccess && nd > 0)
         e = cudaMemcpyAsync(S->d_copy[slot], S->h_copy[slot], nd * sizeof(ChunkCopy), cudaMemcpyHostToDevice, st);
+    LaunchCtx ctx;
+    if (e == cudaSuccess && get_ctx(st, &ctx) != MMF_OK) e = cudaErrorUnknown;
+    const int64_t stage_lim = (int64_t)S->stage_size / esz, out_lim = (int64_t)S->out_half / esz;
     if (e == cudaSuccess && nd > 0) {
         const dim3 g(nd, (unsigned)std::min<int64_t>(32, (maxlen + 2047) / 2048));
         switch (S->dtype) {
-            case MMF_F32: gather_kernel<float><<<g, 256, 0, st>>>(S->d_copy[slot], nd, (float *)base); break;
-            case MMF_F64: gather_kernel<double><<<g, 256, 0, st>>>(S->d_copy[slot], nd, (double *)base); break;
-            case MMF_I16: gather_kernel<int16_t><<<g, 256, 0, st>>>(S->d_copy[slot], nd, (int16_t *)base); break;
-            default: gather_kernel<uint8_t><<<g, 256, 0, st>>>(S->d_copy[slot], nd, (uint8_t *)base); break;
+            case MMF_F32: gather_kernel<float><<<g, 256, 0, st>>>(S->d_copy[slot], nd, (float *)base, stage_lim, ctx.status); break;
+            case MMF_F64: gather_kernel<double><<<g, 256, 0, st>>>(S->d_copy[slot], nd, (double *)base, stage_lim, ctx.status); break;
+            case MMF_I16: gather_kernel<int16_t><<<g, 256, 0, st>>>(S->d_copy[slot], nd, (int16_t *)base, stage_lim, ctx.status); break;
+            default: gather_kernel<uint8_t><<<g, 256, 0, st>>>(S->d_copy[slot], nd, (uint8_t *)base, stage_lim, ctx.status); break;
         }
         e = cudaGetLastError();
     }
@@ -338,21 +351,19 @@ bool run_batch(mmf_server *S, std::unique_lock<std::mutex> &lk) {
                             cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaEventRecord(S->slot_free[slot], st);
     if (e == cudaSuccess) e = cudaMemsetAsync(S->d_tick[slot], 0, 4 * sizeof(int), st);
-    LaunchCtx ctx;
-    if (e == cudaSuccess && get_ctx(st, &ctx) != MMF_OK) e = cudaErrorUnknown;
     int64_t first = 0;
     for (int g = 0; g < 4 && e == cudaSuccess; ++g) {
         if (counts[g]) e = launch_group(S, ctx, g, slot, S->d_items[slot] + first, counts[g]);
         first += counts[g];
     }
-    if (e == cudaSuccess) e = launch_halo(S, slot, n, st);
+    if (e == cudaSuccess) e = launch_halo(S, slot, n, st, ctx.status);
     if (e == cudaSuccess && nd > 0) {
         const dim3 g(nd, (unsigned)std::min<int64_t>(32, (maxout + 2047) / 2048));
         switch (S->dtype) {
-            case MMF_F32: scatter_kernel<float><<<g, 256, 0, st>>>(S->d_copy[slot], nd, (const float *)omax, (const float *)omin); break;
-            case MMF_F64: scatter_kernel<double><<<g, 256, 0, st>>>(S->d_copy[slot], nd, (const double *)omax, (const double *)omin); break;
-            case MMF_I16: scatter_kernel<int16_t><<<g, 256, 0, st>>>(S->d_copy[slot], nd, (const int16_t *)omax, (const int16_t *)omin); break;
-            default: scatter_kernel<uint8_t><<<g, 256, 0, st>>>(S->d_copy[slot], nd, (const uint8_t *)omax, (const uint8_t *)omin); break;
+            case MMF_F32: scatter_kernel<float><<<g, 256, 0, st>>>(S->d_copy[slot], nd, (const float *)omax, (const float *)omin, out_lim, ctx.status); break;
+            case MMF_F64: scatter_kernel<double><<<g, 256, 0, st>>>(S->d_copy[slot], nd, (const double *)omax, (const double *)omin, out_lim, ctx.status); break;
+            case MMF_I16: scatter_kernel<int16_t><<<g, 256, 0, st>>>(S->d_copy[slot], nd, (const int16_t *)omax, (const int16_t *)omin, out_lim, ctx.status); break;
+            default: scatter_kernel<uint8_t><<<g, 256, 0, st>>>(S->d_copy[slot], nd, (const uint8_t *)omax, (const uint8_t *)omin, out_lim, ctx.status); break;
         }
         e = cudaGetLastError();
     }

@@ -37,6 +37,8 @@ struct Tile2DParams {
     int32_t tiles_x, tiles_y;
     int32_t xs;                  // input tile row stride in shared memory (odd)
     int32_t x_bytes, r_bytes;    // shared-memory regions (16-byte multiples)
+    uint32_t *status;            // device status word (range checks of a checked build)
+    int64_t in_elems, out_elems; // readable elements from `in`, writable from each output
 };
 
 // Shared memory of one tile for windows wy x wx: the input tile and the two
@@ -127,8 +129,10 @@ __device__ __forceinline__ void tile_cols(const T *RM, const T *RN, int rows_in,
         for (int i = 0; i < kRun; ++i) {
             const int64_t y = y0 + r0 + i;
             if (y < P.Ho) {
-                if (omax) omax[y * P.Wo + x] = Elem<T>::store(om[i]);
-                if (omin) omin[y * P.Wo + x] = Elem<T>::store(on[i]);
+                if (omax && in_bytes(P.status, omax + y * P.Wo + x, (int)sizeof(T), P.out_max, P.out_elems * (int64_t)sizeof(T)))
+                    omax[y * P.Wo + x] = Elem<T>::store(om[i]);
+                if (omin && in_bytes(P.status, omin + y * P.Wo + x, (int)sizeof(T), P.out_min, P.out_elems * (int64_t)sizeof(T)))
+                    omin[y * P.Wo + x] = Elem<T>::store(on[i]);
             }
         }
     }
@@ -161,7 +165,10 @@ __global__ void __launch_bounds__(kTThreads, (tile_min_blocks<T, PMAX>())) tile2
         const int64_t y = y0 + r;
         const T *row = src + y * P.pitch + x0;
         for (int c = lane; c < cols_in; c += 32)
-            X[r * xs + c] = (y < P.H && x0 + c < P.W) ? __ldg(row + c) : T(0);
+            X[r * xs + c] = (y < P.H && x0 + c < P.W &&
+                             in_bytes(P.status, row + c, (int)sizeof(T), P.in, P.in_elems * (int64_t)sizeof(T)))
+                                ? __ldg(row + c)
+                                : T(0);
     }
     __syncthreads();
 
@@ -225,7 +232,10 @@ __device__ __forceinline__ void tile_pf_load(const Tile2DParams &P, int64_t tile
 #pragma unroll
         for (int j = 0; j < TilePf<PMAX>::CPL; ++j) {
             const int c = lane + 32 * j;
-            v[i][j] = (r < rows_in && c < cols_in && y < P.H && x0 + c < P.W) ? __ldg(row + c) : T(0);
+            v[i][j] = (r < rows_in && c < cols_in && y < P.H && x0 + c < P.W &&
+                       in_bytes(P.status, row + c, (int)sizeof(T), P.in, P.in_elems * (int64_t)sizeof(T)))
+                          ? __ldg(row + c)
+                          : T(0);
         }
     }
 }

@@ -64,9 +64,14 @@ __device__ __forceinline__ int w3_chunk(const T (&e)[N], int cnt, typename Elem<
 
 template <typename T>
 __global__ void __launch_bounds__(256) w3_kernel(const T *__restrict__ a, long long n, T *omax, T *omin,
-                                                 unsigned long long *ncmp, int vec) {
+                                                 unsigned long long *ncmp, int vec, uint32_t *status) {
     using R = typename Elem<T>::R;
     const long long n_out = n - 2;
+    // Range checks of a checked build (always true otherwise).
+    auto in_ok = [&](const void *p, int nb) { return in_bytes(status, p, nb, a, n * (long long)sizeof(T)); };
+    auto out_ok = [&](const T *base, const void *p, int nb) {
+        return in_bytes(status, p, nb, base, n_out * (long long)sizeof(T));
+    };
     const long long j0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * kW3Out;
     const int lane = threadIdx.x & 31;
     // The warp takes the vector path when all its inputs are in the array.
@@ -81,13 +86,13 @@ __global__ void __launch_bounds__(256) w3_kernel(const T *__restrict__ a, long l
         } ld;
         const uint4 *src = reinterpret_cast<const uint4 *>(a + j0);
 #pragma unroll
-        for (int q = 0; q < NV; ++q) ld.u[q] = __ldg(src + q);
+        for (int q = 0; q < NV; ++q) ld.u[q] = in_ok(src + q, 16) ? __ldg(src + q) : make_uint4(0, 0, 0, 0);
 #pragma unroll
         for (int q = 0; q < kW3Out; ++q) e[q] = ld.v[q];
         T h0 = shfl_down_elem(ld.v[0], 1), h1 = shfl_down_elem(ld.v[1], 1);
         if (lane == 31) {
-            h0 = a[j0 + kW3Out];
-            h1 = a[j0 + kW3Out + 1];
+            h0 = in_ok(a + j0 + kW3Out, (int)sizeof(T)) ? a[j0 + kW3Out] : T(0);
+            h1 = in_ok(a + j0 + kW3Out + 1, (int)sizeof(T)) ? a[j0 + kW3Out + 1] : T(0);
         }
         e[kW3Out] = h0;
         e[kW3Out + 1] = h1;
@@ -95,7 +100,8 @@ __global__ void __launch_bounds__(256) w3_kernel(const T *__restrict__ a, long l
     } else if (j0 < n_out) {
         cnt = (int)min((long long)kW3Out, n_out - j0);
 #pragma unroll
-        for (int q = 0; q < kW3Out + 2; ++q) e[q] = q < cnt + 2 ? a[j0 + q] : T(0);
+        for (int q = 0; q < kW3Out + 2; ++q)
+            e[q] = q < cnt + 2 && in_ok(a + j0 + q, (int)sizeof(T)) ? a[j0 + q] : T(0);
     }
     int c = 0;
     if (cnt > 0) {
@@ -112,11 +118,12 @@ __global__ void __launch_bounds__(256) w3_kernel(const T *__restrict__ a, long l
                 for (int q = 0; q < kW3Out; ++q) st.v[q] = Elem<T>::store(hi[q]);
 #pragma unroll
                 for (int q = 0; q < (int)(kW3Out * sizeof(T) / 16); ++q)
-                    reinterpret_cast<uint4 *>(omax + j0)[q] = st.u[q];
+                    if (out_ok(omax, reinterpret_cast<uint4 *>(omax + j0) + q, 16))
+                        reinterpret_cast<uint4 *>(omax + j0)[q] = st.u[q];
             } else {
 #pragma unroll
                 for (int q = 0; q < kW3Out; ++q)
-                    if (q < cnt) omax[j0 + q] = Elem<T>::store(hi[q]);
+                    if (q < cnt && out_ok(omax, omax + j0 + q, (int)sizeof(T))) omax[j0 + q] = Elem<T>::store(hi[q]);
             }
         }
         if (omin) {
@@ -129,11 +136,12 @@ __global__ void __launch_bounds__(256) w3_kernel(const T *__restrict__ a, long l
                 for (int q = 0; q < kW3Out; ++q) st.v[q] = Elem<T>::store(lo[q]);
 #pragma unroll
                 for (int q = 0; q < (int)(kW3Out * sizeof(T) / 16); ++q)
-                    reinterpret_cast<uint4 *>(omin + j0)[q] = st.u[q];
+                    if (out_ok(omin, reinterpret_cast<uint4 *>(omin + j0) + q, 16))
+                        reinterpret_cast<uint4 *>(omin + j0)[q] = st.u[q];
             } else {
 #pragma unroll
                 for (int q = 0; q < kW3Out; ++q)
-                    if (q < cnt) omin[j0 + q] = Elem<T>::store(lo[q]);
+                    if (q < cnt && out_ok(omin, omin + j0 + q, (int)sizeof(T))) omin[j0 + q] = Elem<T>::store(lo[q]);
             }
         }
     }
@@ -156,7 +164,7 @@ cudaError_t w3_1d(const LaunchCtx &ctx, const void *in, int64_t n, void *omax, v
     const int64_t blocks = (threads + 255) / 256;
     const int vec = ((uintptr_t)in % 16) == 0 && ((uintptr_t)omax % 16) == 0 && ((uintptr_t)omin % 16) == 0;
     w3_kernel<T><<<(unsigned)blocks, 256, 0, ctx.stream>>>(static_cast<const T *>(in), n, static_cast<T *>(omax),
-                                                          static_cast<T *>(omin), ncmp, vec);
+                                                          static_cast<T *>(omin), ncmp, vec, ctx.status);
     return cudaGetLastError();
 }
 

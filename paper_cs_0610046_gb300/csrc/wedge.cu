@@ -217,7 +217,8 @@ template <typename T, bool ARG>
 __global__ void __launch_bounds__(256) wedge_kernel(const T *__restrict__ a, int64_t n, int32_t w, int64_t chunk,
                                                     int vlog2, int ilog2, int vec_in, int vec_out,
                                                     T *__restrict__ omax, T *__restrict__ omin,
-                                                    int64_t *__restrict__ amax, int64_t *__restrict__ amin) {
+                                                    int64_t *__restrict__ amax, int64_t *__restrict__ amin,
+                                                    uint32_t *status) {
     using IO = WedgeIO<T>;
     using R = typename Elem<T>::R;
     using S = WedgeS<T>;
@@ -228,13 +229,18 @@ __global__ void __launch_bounds__(256) wedge_kernel(const T *__restrict__ a, int
     if (j0 >= n_out) return;  // the kernel has no barriers
     const int64_t cnt = chunk < n_out - j0 ? chunk : n_out - j0;
     const T *x = a + j0;
+    // Range checks of a checked build (always true otherwise): k elements of
+    // size sz at p inside a buffer of m elements at base.
+    auto ok = [&](const void *p, int64_t k, int sz, const void *base, int64_t m) {
+        return in_bytes(status, p, (int)(k * sz), base, m * sz);
+    };
     if (w == 1) {  // a window of one element is the element itself
         for (int64_t o = 0; o < cnt; ++o) {
-            const T v = x[o];
-            if (omax) omax[j0 + o] = v;
-            if (omin) omin[j0 + o] = v;
-            if (ARG && amax) amax[j0 + o] = j0 + o;
-            if (ARG && amin) amin[j0 + o] = j0 + o;
+            const T v = ok(x + o, 1, (int)sizeof(T), a, n) ? x[o] : T(0);
+            if (omax && ok(omax + j0 + o, 1, (int)sizeof(T), omax, n_out)) omax[j0 + o] = v;
+            if (omin && ok(omin + j0 + o, 1, (int)sizeof(T), omin, n_out)) omin[j0 + o] = v;
+            if (ARG && amax && ok(amax + j0 + o, 1, 8, amax, n_out)) amax[j0 + o] = j0 + o;
+            if (ARG && amin && ok(amin + j0 + o, 1, 8, amin, n_out)) amin[j0 + o] = j0 + o;
         }
         return;
     }
@@ -255,7 +261,13 @@ __global__ void __launch_bounds__(256) wedge_kernel(const T *__restrict__ a, int
     uint32_t staged = 0;
     auto stage = [&]() {
         uint32_t wd[IO::WORDS];
-        IO::load(x + staged, n - j0 - staged, vec_in != 0, wd);
+        const int64_t avail = n - j0 - staged;
+        if (ok(x + staged, avail < 8 ? avail : 8, (int)sizeof(T), a, n)) {
+            IO::load(x + staged, avail, vec_in != 0, wd);
+        } else {
+#pragma unroll
+            for (int k = 0; k < IO::WORDS; ++k) wd[k] = 0u;
+        }
         IO::stage(q.V, staged & q.vmask, wd);
         staged += 8;
     };
@@ -284,11 +296,12 @@ __global__ void __launch_bounds__(256) wedge_kernel(const T *__restrict__ a, int
             }
         }
         const int64_t left = cnt - o;
-        if (omax) IO::store(omax + j0 + o, left, vec_out != 0, om);
-        if (omin) IO::store(omin + j0 + o, left, vec_out != 0, on);
+        const int64_t nst = left < 8 ? left : 8;
+        if (omax && ok(omax + j0 + o, nst, (int)sizeof(T), omax, n_out)) IO::store(omax + j0 + o, left, vec_out != 0, om);
+        if (omin && ok(omin + j0 + o, nst, (int)sizeof(T), omin, n_out)) IO::store(omin + j0 + o, left, vec_out != 0, on);
         if (ARG) {
-            if (amax) store_index(amax + j0 + o, left, im);
-            if (amin) store_index(amin + j0 + o, left, in_);
+            if (amax && ok(amax + j0 + o, nst, 8, amax, n_out)) store_index(amax + j0 + o, left, im);
+            if (amin && ok(amin + j0 + o, nst, 8, amin, n_out)) store_index(amin + j0 + o, left, in_);
         }
     }
 }
@@ -342,7 +355,7 @@ static cudaError_t wedge_launch(const LaunchCtx &ctx, const void *in, int64_t n,
     const int vec_out = ((uintptr_t)omax % align) == 0 && ((uintptr_t)omin % align) == 0;
     wedge_kernel<T, ARG><<<(unsigned)blocks, tpb, smem, ctx.stream>>>(
         static_cast<const T *>(in), n, (int32_t)w, chunk, vlog2, ilog2, vec_in, vec_out, static_cast<T *>(omax),
-        static_cast<T *>(omin), amax, amin);
+        static_cast<T *>(omin), amax, amin, ctx.status);
     return cudaGetLastError();
 }
 
