@@ -216,8 +216,9 @@ int64_t mmf_output_length(int64_t n, int64_t w_or_r, mmf_mode mode);
  * with per-element SIMD max/min, f32 one column per register, no
  * intermediates in memory; needs 4-byte aligned input rows (d_in, the pitch
  * in bytes and the image stride), else MMF_ENOTIMPL; -1 automatic (the
- * streaming kernel for u8/i16 where it applies, the tile kernel when wy, wx
- * <= 31, else the two passes).  Any other value: MMF_EINVAL.
+ * streaming kernel where it applies, except f32 rows-only windows wider than
+ * 3; the tile kernel when wy, wx <= 31; else the two passes).  Any other
+ * value: MMF_EINVAL.
  * Column windows are limited by the column
  * pass's shared memory: up to about 760 rows for f32, 320 for f64 and 1700 for
  * i16/u8 (MMF_ENOTIMPL beyond). */

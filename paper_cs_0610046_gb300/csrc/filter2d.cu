@@ -146,9 +146,11 @@ static cudaError_t tile_launch(const LaunchCtx &ctx, const T *in, int64_t nimg, 
     P.wx = (int)wx;
     P.tiles_x = (int)((P.Wo + kTC - 1) / kTC);
     P.tiles_y = (int)((P.Ho + kTR - 1) / kTR);
+#ifdef MMF_CHECKED
     P.status = ctx.status;
     P.in_elems = (nimg - 1) * P.img_stride + (H - 1) * pitch + W;
     P.out_elems = nimg * P.Ho * P.Wo;
+#endif
     const int64_t grid = nimg * P.tiles_x * P.tiles_y;
     if (grid <= 0) return cudaSuccess;
     if (grid > 0x7fffffff) return cudaErrorInvalidValue;
@@ -213,7 +215,10 @@ static mmf_status filter2d(const LaunchCtx &ctx, const T *in, int64_t nimg, int6
                            int64_t wy, int64_t wx, int fuse, T *omax, T *omin, void *work) {
     const int64_t Ho = H - wy + 1, Wo = W - wx + 1;
     cudaError_t e = cudaSuccess;
-    if (fuse == 2 || (fuse < 0 && sizeof(T) <= 2)) {
+    // Automatic: the streaming kernel for u8/i16 wherever it applies, for f32
+    // except rows-only windows of more than 3 (the row pass is faster there).
+    const bool auto_pack = sizeof(T) <= 2 || (std::is_same<T, float>::value && !(wy == 1 && wx > 3));
+    if (fuse == 2 || (fuse < 0 && auto_pack)) {
         if (pack_applies<T>(in, H, pitch, wy, wx)) {
             e = pack_launch<T>(ctx, in, nimg, H, W, pitch, wy, wx, omax, omin);
             return e == cudaSuccess ? MMF_OK : cuda_error(e, "packed 2D kernel");

@@ -195,6 +195,11 @@ template <typename T>
 __device__ __forceinline__ void pk_store(const Pack2DParams &P, const uint8_t *obuf, uint8_t *ob, uint32_t v,
                                          const PkLane &pl) {
     constexpr int L = Pk<T>::L, SZ = (int)sizeof(T);
+    if constexpr (SZ == 4) {  // f32 outputs are always word-aligned: no exchange
+        if (pl.st && pl.rem >= 1 && in_bytes(P.status, ob, 4, obuf, P.out_bytes))
+            __stcs(reinterpret_cast<uint32_t *>(ob), v);
+        return;
+    }
     // sh: bytes of this word before the next aligned word (0 when aligned: the
     // funnel shift by 0 is v itself), so no branch on the alignment.
     const int sh = (int)(-(uintptr_t)ob & 3);

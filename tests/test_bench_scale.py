@@ -9,7 +9,8 @@ paths that only the full-size workloads reach:
 * the envelope batch (1e6 z-normalised series of 1024, r = 51) through the
   warp-per-series kernel;
 * the fused 2D filter on 4096 x 4096 f32 images at 3 x 3, where the
-  persistent tile kernel loops over about 13 output tiles per CTA.
+  persistent tile kernel loops over about 13 output tiles per CTA, and the
+  streaming kernel (the automatic choice) covers 64 bands of rows per image.
 
 Outputs are compared with the oracle at sampled windows (every series' or
 image's ends included); the GPU forms are compared with each other at every
@@ -102,13 +103,13 @@ def test_envelope_batch_full_size(mmf):
         assert np.array_equal(hl[off[s]:off[s] + L], el), f"series {s} lower"
 
 
-@pytest.mark.parametrize("fuse", [-1, 1])
+@pytest.mark.parametrize("fuse", [-1, 1, 2])
 def test_2d_f32_full_size_persistent_tiles(mmf, fuse):
-    """Four 4096 x 4096 f32 images at 3 x 3: the automatic choice and the
-    forced fused kernel (both the persistent tile loop) against the literal
-    rectangle at every pixel of each image's first and last two rows and
-    columns and at 20 000 random pixels, and against the two-pass form at
-    every pixel."""
+    """Four 4096 x 4096 f32 images at 3 x 3: the automatic choice (the
+    streaming kernel), the forced tile kernel (its persistent tile loop) and
+    the forced streaming kernel against the literal rectangle at every pixel
+    of each image's first and last two rows and columns and at 20 000 random
+    pixels, and against the two-pass form at every pixel."""
     imgs = synth.blobs2d(4, 4096, 4096, seed=41, dtype=np.float32, nblobs=200)
     x = torch.from_numpy(imgs).cuda()
     mx, mn = mmf.filter2d(x, 3, 3, fuse=fuse)
