@@ -234,3 +234,72 @@ def test_lane_blocks_edges_and_planted_mistakes():
     gm, gn = _model_lanes(a[:100], 61, -30, 100, E, mistake="identity_pad_one_side")
     em, en = oracle.envelope(a[:100], 30)
     assert np.array_equal(gm, em) and not np.array_equal(gn, en)
+
+
+def _lane_envelope_arrays(a, r, E, staged, restore):
+    """The lane-block envelope with the prefix arrays addressed as the kernel
+    does: [E][33] words, element e of lane j at row e, column j, and column
+    32 an identity column that windows reaching past the last lane read.  A
+    staged next series (128 bytes per lane: lane l's words [32l, 32l + 32) of
+    the flat array) covers the min side's array before this series' prefix
+    is written; the kernel then writes the identity column again (restore)."""
+    lanes, ROW = 32, 33
+    n = len(a)
+    cap = lanes * E
+    w, d, s = 2 * r + 1, -r, 2 * r
+    q, rr = divmod(s, E)
+    x = np.full(cap, float(a[-1]))
+    x[:n] = a
+    out = []
+    for side, (op, ident) in enumerate(((max, -np.inf), (min, np.inf))):
+        arr = np.full(E * ROW, np.nan)
+        arr[32::ROW] = ident  # the identity column, written once per kernel
+        if staged and side == 1:
+            arr[:32 * 32] = -1e9  # the next series' staged words (below this series)
+            if restore:
+                arr[32::ROW] = ident
+        P = x.copy()
+        S = x.copy()
+        for j in range(lanes):
+            b = j * E
+            for e in range(1, E):
+                P[b + e] = op(P[b + e - 1], x[b + e])
+            for e in range(E - 2, -1, -1):
+                S[b + e] = op(S[b + e + 1], x[b + e])
+            for e in range(E):
+                arr[e * ROW + j] = P[b + e]  # the prefix pass writes columns 0..31 only
+        A = [S[j * E] for j in range(lanes)]
+        m1, m2 = _lane_windows(A, q, op, ident)
+        incl = list(itertools.accumulate(A, op))
+        res = np.empty(n)
+        for o in range(n):
+            lo = o + d
+            if lo >= 0:
+                j, e = divmod(lo, E)
+                far = e >= E - rr
+                K = min(j + q + (1 if far else 0), 32)
+                eh = e + rr - (E if far else 0)
+                res[o] = op(op(S[lo], m2[j] if far else m1[j]), arr[eh * ROW + K])
+            else:
+                hi = lo + s
+                K = min(hi // E, 32)
+                res[o] = op(incl[K - 1] if K > 0 else ident, arr[(hi % E) * ROW + K])
+        out.append(res)
+    return out
+
+
+def test_staged_series_needs_the_identity_column_again():
+    """Windows reaching past the last lane read the identity column; a staged
+    copy of the next series covers it, so the kernel writes it again: with
+    that, the envelope equals the oracle's; without it, the min side does not
+    (the max side's array is never staged)."""
+    E = 32
+    a = synth.random_walk(32 * E, seed=12, dtype=np.float32).astype(np.float64)
+    r = 51
+    em, en = oracle.envelope(a.astype(np.float32), r)
+    gm, gn = _lane_envelope_arrays(a, r, E, staged=True, restore=True)
+    assert np.array_equal(gm, em) and np.array_equal(gn, en)
+    gm, gn = _lane_envelope_arrays(a, r, E, staged=False, restore=False)
+    assert np.array_equal(gm, em) and np.array_equal(gn, en)
+    gm, gn = _lane_envelope_arrays(a, r, E, staged=True, restore=False)
+    assert np.array_equal(gm, em) and not np.array_equal(gn, en)
