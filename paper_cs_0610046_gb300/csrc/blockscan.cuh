@@ -742,7 +742,9 @@ __device__ __forceinline__ void issue_next(int warp) {
 // B), kept by warp 0 as a two-stack queue inside the tile-aggregate ring:
 // slots [fs, fe) hold suffix maxima up to fe-1, slots [fe, be) raw aggregates
 // whose running max is (bm, bn).  Each step costs O(1) amortised.  Every
-// lane of warp 0 runs it; lanes write identical values.
+// lane of warp 0 runs it; the rebuild is a warp scan (lane l takes slot
+// top - l of each group of 32, newest first), the rest is the same on every
+// lane.
 template <typename T> struct TileQueue {
     using R = typename Elem<T>::R;
     using Pair = typename Elem<T>::Pair;
@@ -761,13 +763,31 @@ template <typename T> struct TileQueue {
         ++fs;
         push(x);
         if (fs >= fe) {
-            R m = Elem<T>::lo(), n = Elem<T>::hi();
-            for (int x = be - 1; x >= fs; --x) {
-                Pair &a = ta(x);
-                m = vmax(m, Elem<T>::pmax(a));
-                n = vmin(n, Elem<T>::pmin(a));
-                a = Elem<T>::pair(m, n);
+            const int lane = threadIdx.x & 31;
+            R cm = Elem<T>::lo(), cn = Elem<T>::hi();  // slots above the group
+            for (int top = be - 1; top >= fs; top -= 32) {
+                const int xl = top - lane;
+                R m = Elem<T>::lo(), n = Elem<T>::hi();
+                if (xl >= fs) {
+                    const Pair a = ta(xl);
+                    m = Elem<T>::pmax(a);
+                    n = Elem<T>::pmin(a);
+                }
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const R um = __shfl_up_sync(0xffffffffu, m, d), un = __shfl_up_sync(0xffffffffu, n, d);
+                    if (lane >= d) {
+                        m = vmax(m, um);
+                        n = vmin(n, un);
+                    }
+                }
+                m = vmax(m, cm);
+                n = vmin(n, cn);
+                if (xl >= fs) ta(xl) = Elem<T>::pair(m, n);
+                cm = __shfl_sync(0xffffffffu, m, 31);
+                cn = __shfl_sync(0xffffffffu, n, 31);
             }
+            __syncwarp();
             bm = Elem<T>::lo();
             bn = Elem<T>::hi();
             fe = be;
@@ -1312,10 +1332,10 @@ struct Consumer {
         }
     }
 
-    // Tile aggregate of K tile x from its warp-block aggregates (warp 0),
+    // Tile aggregate of K tile x from its warp-block aggregates (warp `by`),
     // into the aggregate ring.
-    __device__ __forceinline__ void publish_tile_aggregate(int x) const {
-        if (warp != 0) return;
+    __device__ __forceinline__ void publish_tile_aggregate(int x, int by = 0) const {
+        if (warp != by) return;
         Pair a = lane < NW ? S::kagg()[(x % 3) * NW + lane] : Elem<T>::pair(Elem<T>::lo(), Elem<T>::hi());
         R m = Elem<T>::pmax(a), n = Elem<T>::pmin(a);
 #pragma unroll
@@ -1814,7 +1834,10 @@ struct Consumer {
                 }
                 if (lane == 0) S::jagg()[(c & 1) * NW + warp] = Elem<T>::pair(hm, hn);
                 sync();
-                if (kload) publish_tile_aggregate(xk);
+                // The last warp publishes while warp 0 updates the queue: the
+                // two jobs follow the barrier side by side, and the next
+                // barrier comes between the aggregate and its reader.
+                if (kload) publish_tile_aggregate(xk, NW - 1);
                 if (warp == 0 && c + 1 < ip.NC) {
                     // The range of output tile c+1: drop tile c+1, add tile c+q
                     // (published in the previous step).

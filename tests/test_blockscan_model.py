@@ -50,11 +50,29 @@ class TileQueue:
         self.fs += 1
         self.push(x)
         if self.fs >= self.fe:
-            m, n = -np.inf, np.inf
-            for y in range(self.be - 1, self.fs - 1, -1):
-                a = self.ring[y % self.cap]
-                m, n = max(m, a[0]), min(n, a[1])
-                self.ring[y % self.cap] = (m, n)
+            # As the kernel's warp does it: groups of 32 slots from the newest
+            # down, lane l holding slot top - l, an inclusive scan over the
+            # lanes (shuffles up by 1, 2, .., 16), then the carry of the
+            # slots above the group (lane 31's result of the group before).
+            cm, cn = -np.inf, np.inf
+            top = self.be - 1
+            while top >= self.fs:
+                ys = [top - l for l in range(32)]
+                m = [self.ring[y % self.cap][0] if y >= self.fs else -np.inf for y in ys]
+                n = [self.ring[y % self.cap][1] if y >= self.fs else np.inf for y in ys]
+                d = 1
+                while d < 32:
+                    um, un = list(m), list(n)  # every lane reads before any writes
+                    for l in range(d, 32):
+                        m[l], n[l] = max(m[l], um[l - d]), min(n[l], un[l - d])
+                    d <<= 1
+                m = [max(v, cm) for v in m]
+                n = [min(v, cn) for v in n]
+                for l, y in enumerate(ys):
+                    if y >= self.fs:
+                        self.ring[y % self.cap] = (m[l], n[l])
+                cm, cn = m[31], n[31]
+                top -= 32
             self.bm, self.bn = -np.inf, np.inf
             self.fe = self.be
 
@@ -201,8 +219,8 @@ def test_tile_queue_is_a_sliding_window():
     """The queue alone against a brute-force window over random aggregates,
     with the smallest ring (q + 2 slots), for q = 1..9."""
     rng = np.random.default_rng(3)
-    for q in range(1, 10):
-        vals = rng.integers(0, 5, size=80).astype(float)
+    for q in list(range(1, 10)) + [33, 34, 40, 65, 66, 97]:  # the rebuild spans 1 to 3 lane groups
+        vals = rng.integers(0, 5 if q < 10 else 1000, size=80 + 3 * q).astype(float)
         cap = q + 2
         ring = [None] * cap
         for t in range(1, q + 1):
@@ -210,7 +228,7 @@ def test_tile_queue_is_a_sliding_window():
         tq = TileQueue(ring, cap)
         for t in range(1, q):
             tq.push(t)
-        for c in range(0, 80 - q - 2):
+        for c in range(0, len(vals) - q - 2):
             lo, hi = c + 1, c + q - 1
             want = (max(vals[lo:hi + 1]), min(vals[lo:hi + 1])) if hi >= lo else (-np.inf, np.inf)
             assert tq.query() == want, (q, c)
