@@ -427,7 +427,7 @@ def filter2d_extras(dev, stream, peak, nimg=64, H=4096, W=4096, reps=3):
             Ho, Wo = H - wy + 1, W - wx + 1
             om = torch.empty((nimg, Ho, Wo), dtype=x.dtype, device=dev)
             on = torch.empty((nimg, Ho, Wo), dtype=x.dtype, device=dev)
-            ws = torch.empty(2 * nimg * H * ((Wo + 15) // 16 * 16) * sz if wy > 1 and wx > 1 else 16,
+            ws = torch.empty(max(16, mmf.filter2d_workspace(nimg, H, W, wy, wx, x.dtype, 0)),
                              dtype=torch.uint8, device=dev)
             byts = (nimg * H * W + 2 * nimg * Ho * Wo) * sz
             row = {}

@@ -206,7 +206,10 @@ int64_t mmf_output_length(int64_t n, int64_t w_or_r, mmf_mode mode);
  * d_max + (k*(H-wy+1) + y)*(W-wx+1).  Both windows >= 1; a window of 1 skips
  * that pass.  The row pass writes its two intermediates to `d_work` (16-byte
  * aligned, size from mmf_filter2d_workspace; none needed when wy or wx is 1
- * or when the fused kernel runs).
+ * or when the fused kernel runs).  With work_bytes >= 2 * R * elem_size,
+ * R = (nimg*H-1)*pitch + W-wx+1 rounded up to 16, the row pass filters all
+ * rows as one series (always so for pitch == W at the queried size); with
+ * less, row by row.
  * fuse: 0 row pass then column pass; 1 a fused kernel, no intermediates in
  * memory: for wy, wx <= 31 a tile with its halo in shared memory, rows then
  * columns; otherwise the column pass computing each tile's row maxima and
@@ -217,8 +220,8 @@ int64_t mmf_output_length(int64_t n, int64_t w_or_r, mmf_mode mode);
  * intermediates in memory; needs 4-byte aligned input rows (d_in, the pitch
  * in bytes and the image stride), else MMF_ENOTIMPL; -1 automatic (the
  * streaming kernel where it applies, except f32 rows-only windows wider than
- * 3; the tile kernel when wy, wx <= 31; else the two passes).  Any other
- * value: MMF_EINVAL.
+ * 3; the tile kernel when wy, wx <= 12 for f32/f64, <= 15 for u8/i16; else
+ * the two passes).  Any other value: MMF_EINVAL.
  * Column windows are limited by the column
  * pass's shared memory: up to about 760 rows for f32, 320 for f64 and 1700 for
  * i16/u8 (MMF_ENOTIMPL beyond). */

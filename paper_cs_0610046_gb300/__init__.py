@@ -18,7 +18,7 @@ import threading
 import torch
 
 __all__ = ["MMFError", "load", "filter1d", "filter1d_host", "filter1d_w3", "argfilter1d", "output_length",
-           "device_status", "set_wait_fault", "dispatch_set", "dispatch_get", "dispatch_autotune", "BatchPlan", "filter2d", "Server", "n_outputs", "DTYPES", "KERNELS"]
+           "device_status", "set_wait_fault", "dispatch_set", "dispatch_get", "dispatch_autotune", "BatchPlan", "filter2d", "filter2d_workspace", "Server", "n_outputs", "DTYPES", "KERNELS"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 # MMF_CHECKED=1 selects the range-checked build (see build.py).
@@ -395,6 +395,13 @@ class BatchPlan:
             pass
 
 
+def filter2d_workspace(n: int, H: int, W: int, wy: int, wx: int, dtype: torch.dtype, fuse: int = -1) -> int:
+    """Bytes of workspace filter2d needs for n dense images of H x W."""
+    need = ctypes.c_size_t(0)
+    check(load().mmf_filter2d_workspace(n, H, W, wy, wx, DTYPES[dtype], fuse, ctypes.byref(need)))
+    return need.value
+
+
 def filter2d(x: torch.Tensor, wy: int, wx: int, fuse: int = -1, out_max=None, out_min=None,
              workspace=None, stream=None):
     """Separable 2D max/min filter, valid windows wy x wx, of images
@@ -418,10 +425,11 @@ def filter2d(x: torch.Tensor, wy: int, wx: int, fuse: int = -1, out_max=None, ou
     check(lib.mmf_filter2d_workspace(n, H, W, wy, wx, DTYPES[x.dtype], fuse, ctypes.byref(need)))
     if need.value and (workspace is None or workspace.numel() * workspace.element_size() < need.value):
         workspace = torch.empty(need.value, dtype=torch.uint8, device=x.device)
+    wbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     with torch.cuda.device(x.device):
         check(lib.mmf_filter2d_separable(_ptr(x), n, H, W, pitch, wy, wx, DTYPES[x.dtype], fuse,
                                          _ptr(out_max), _ptr(out_min), _ptr(workspace),
-                                         need.value, _VP(_stream_handle(stream))))
+                                         wbytes, _VP(_stream_handle(stream))))
     return out_max, out_min
 
 

@@ -63,9 +63,14 @@ template <typename T> static cudaError_t col_launch(const LaunchCtx &ctx, const 
 // request (fuse = 1, wx <= MMF_FUSED_MAX_WX), the column pass with row
 // maxima computed per row in registers.
 static bool tile_fits(int64_t wy, int64_t wx) { return wy <= kTileMaxW && wx <= kTileMaxW; }
-static bool use_fused(int64_t wy, int64_t wx, int fuse) {
+// The automatic choice takes the tile kernel up to windows of 12 (4- and
+// 8-byte elements) or 15 (1- and 2-byte): above that its halo and doubling
+// passes cost more than the row pass (one series over all rows) and the
+// column pass together (measured on 32-64 images of 4096 x 4096).
+static bool use_fused(int64_t wy, int64_t wx, int fuse, int esz) {
     if (wy == 1 || wx == 1) return false;  // a single pass already
-    return fuse == 1 || fuse == 2 || (fuse < 0 && tile_fits(wy, wx));
+    const int64_t auto_max = esz >= 4 ? 12 : 15;
+    return fuse == 1 || fuse == 2 || (fuse < 0 && tile_fits(wy, wx) && wy <= auto_max && wx <= auto_max);
 }
 
 // The register-streaming kernel (u8, i16 packed; f32; windows up to
@@ -212,7 +217,7 @@ static int64_t mid_pitch(int64_t Wo) { return (Wo + 15) / 16 * 16; }
 
 template <typename T>
 static mmf_status filter2d(const LaunchCtx &ctx, const T *in, int64_t nimg, int64_t H, int64_t W, int64_t pitch,
-                           int64_t wy, int64_t wx, int fuse, T *omax, T *omin, void *work) {
+                           int64_t wy, int64_t wx, int fuse, T *omax, T *omin, void *work, size_t work_bytes) {
     const int64_t Ho = H - wy + 1, Wo = W - wx + 1;
     cudaError_t e = cudaSuccess;
     // Automatic: the streaming kernel for u8/i16 wherever it applies, for f32
@@ -245,7 +250,7 @@ static mmf_status filter2d(const LaunchCtx &ctx, const T *in, int64_t nimg, int6
     P.out_elems = nimg * Ho * Wo;
     P.wy = (int)wy;
     P.wx = (int)wx;
-    const bool fused = use_fused(wy, wx, fuse);
+    const bool fused = use_fused(wy, wx, fuse, (int)sizeof(T));
     if (fused && tile_fits(wy, wx)) {
         e = tile_launch<T>(ctx, in, nimg, H, W, pitch, wy, wx, omax, omin);
         return e == cudaSuccess ? MMF_OK : cuda_error(e, "fused 2D tile");
@@ -257,19 +262,38 @@ static mmf_status filter2d(const LaunchCtx &ctx, const T *in, int64_t nimg, int6
         P.in_img = H * pitch;
         P.src_elems = (nimg - 1) * H * pitch + (H - 1) * pitch + W;
     } else {
-        const int64_t wp = mid_pitch(Wo);
+        // All rows of all images (stacked, `pitch` apart) read as one series
+        // of n elements: the window starting at stream position r*pitch + x
+        // is row r's window at column x for x < Wo; the others straddle two
+        // rows (or a row's padding) and are never read.  One long series
+        // keeps the long-stream schedule (a few long items per CTA) where a
+        // series per row gives every CTA many items of two or three tiles.
+        // Its intermediates have the input's pitch; when the workspace is
+        // too small for that (a pitch above the width), rows one by one.
+        const int64_t n = (nimg * H - 1) * pitch + W;
+        const int64_t span = mid_pitch(n - wx + 1);
         T *rmax = static_cast<T *>(work);
-        T *rmin = rmax + nimg * H * wp;
-        SeriesDesc sd{0, W, 0, wx, 0, Wo};
-        // Each image row is a row of the input; rows of consecutive images are
-        // `pitch` apart as well (images are stacked).
-        e = blockscan_rows<T>(ctx, in, sd, nimg * H, pitch, wp, rmax, rmin);
-        if (e != cudaSuccess) return cuda_error(e, "row pass");
-        P.src_max = rmax;
-        P.src_min = rmin;
-        P.in_pitch = wp;
-        P.in_img = H * wp;
-        P.src_elems = nimg * H * wp;
+        if (work_bytes / sizeof(T) >= (size_t)(2 * span)) {
+            SeriesDesc sd{0, n, 0, wx, 0, n - wx + 1};
+            e = blockscan_1d<T>(ctx, in, sd, rmax, rmax + span, true, 0);
+            if (e != cudaSuccess) return cuda_error(e, "row pass");
+            P.src_max = rmax;
+            P.src_min = rmax + span;
+            P.in_pitch = pitch;
+            P.in_img = H * pitch;
+            P.src_elems = span;
+        } else {
+            const int64_t wp = mid_pitch(Wo);
+            T *rmin = rmax + nimg * H * wp;
+            SeriesDesc sd{0, W, 0, wx, 0, Wo};
+            e = blockscan_rows<T>(ctx, in, sd, nimg * H, pitch, wp, rmax, rmin);
+            if (e != cudaSuccess) return cuda_error(e, "row pass");
+            P.src_max = rmax;
+            P.src_min = rmin;
+            P.in_pitch = wp;
+            P.in_img = H * wp;
+            P.src_elems = nimg * H * wp;
+        }
     }
     e = col_launch<T>(ctx, P, fused);
     return e == cudaSuccess ? MMF_OK : cuda_error(e, "column pass");
@@ -309,9 +333,12 @@ mmf_status mmf_filter2d_workspace(int64_t nimg, int64_t H, int64_t W, int64_t wy
     if (!bytes) return set_error(MMF_EINVAL, "NULL output");
     mmf_status st = check2d(nimg, H, W, W, wy, wx, dtype, fuse);
     if (st != MMF_OK) return st;
+    // Two intermediates of nimg*H rows of pitch W rounded up to 16 elements:
+    // room for the row pass over dense images as one series (the width
+    // covers both that and the row-by-row form's Wo rounded up).
     const int64_t Wo = W - wx + 1;
-    *bytes = (wy > 1 && wx > 1 && Wo > 0 && H >= wy && !use_fused(wy, wx, fuse))
-                 ? (size_t)(2 * nimg * H * mid_pitch(Wo) * elem_size(dtype))
+    *bytes = (wy > 1 && wx > 1 && Wo > 0 && H >= wy && !use_fused(wy, wx, fuse, elem_size(dtype)))
+                 ? (size_t)(2 * nimg * H * mid_pitch(W) * elem_size(dtype))
                  : 0;
     return MMF_OK;
 }
@@ -336,10 +363,10 @@ mmf_status mmf_filter2d_separable(const void *d_in, int64_t nimg, int64_t H, int
     st = get_ctx(stream, &ctx);
     if (st != MMF_OK) return st;
     switch (dtype) {
-        case MMF_F32: return filter2d<float>(ctx, (const float *)d_in, nimg, H, W, pitch, wy, wx, fuse, (float *)d_max, (float *)d_min, d_work);
-        case MMF_F64: return filter2d<double>(ctx, (const double *)d_in, nimg, H, W, pitch, wy, wx, fuse, (double *)d_max, (double *)d_min, d_work);
-        case MMF_I16: return filter2d<int16_t>(ctx, (const int16_t *)d_in, nimg, H, W, pitch, wy, wx, fuse, (int16_t *)d_max, (int16_t *)d_min, d_work);
-        case MMF_U8: return filter2d<uint8_t>(ctx, (const uint8_t *)d_in, nimg, H, W, pitch, wy, wx, fuse, (uint8_t *)d_max, (uint8_t *)d_min, d_work);
+        case MMF_F32: return filter2d<float>(ctx, (const float *)d_in, nimg, H, W, pitch, wy, wx, fuse, (float *)d_max, (float *)d_min, d_work, work_bytes);
+        case MMF_F64: return filter2d<double>(ctx, (const double *)d_in, nimg, H, W, pitch, wy, wx, fuse, (double *)d_max, (double *)d_min, d_work, work_bytes);
+        case MMF_I16: return filter2d<int16_t>(ctx, (const int16_t *)d_in, nimg, H, W, pitch, wy, wx, fuse, (int16_t *)d_max, (int16_t *)d_min, d_work, work_bytes);
+        case MMF_U8: return filter2d<uint8_t>(ctx, (const uint8_t *)d_in, nimg, H, W, pitch, wy, wx, fuse, (uint8_t *)d_max, (uint8_t *)d_min, d_work, work_bytes);
     }
     return set_error(MMF_EINVAL, "unknown dtype");
 }

@@ -62,6 +62,36 @@ def test_2d_pitched_rows_and_ragged(mmf):
             assert np.array_equal(mx[k].cpu().numpy(), em) and np.array_equal(mn[k].cpu().numpy(), en)
 
 
+def test_2d_row_pass_as_one_series(mmf):
+    """The two-pass form with a workspace large enough for the row pass to
+    filter every row of every image as one series: over padded rows (the
+    windows that straddle a row's padding are computed and never read) and
+    dense ones, against the literal rectangle; then the same pitched images
+    with the queried workspace, which takes the rows one by one."""
+    full = synth.blobs2d(3, 131, 517, seed=5, dtype=np.float32, nblobs=9)
+    base = torch.from_numpy(full).cuda()
+    big = torch.empty(2 * 3 * 131 * 528 * 4, dtype=torch.uint8, device="cuda")
+    for x, width in ((base[:, :, :501], 501), (base, 517)):
+        for wy, wx in ((5, 6), (33, 71), (2, 2), (40, 200), (3, 501 if width == 501 else 517)):
+            for ws in (big, None):
+                mx, mn = mmf.filter2d(x, wy, wx, fuse=0, workspace=ws)
+                torch.cuda.synchronize()
+                for k in range(3):
+                    em, en = _expect(full[k, :, :width], wy, wx)
+                    assert np.array_equal(mx[k].cpu().numpy(), em), (width, wy, wx, ws is None, k)
+                    assert np.array_equal(mn[k].cpu().numpy(), en), (width, wy, wx, ws is None, k)
+    for dtype in (np.uint8, np.int16, np.float64):
+        imgs = synth.blobs2d(2, 70, 150, seed=6, dtype=dtype, nblobs=4)
+        x = torch.from_numpy(imgs).cuda()
+        for wy, wx in ((4, 11), (20, 3)):
+            mx, mn = mmf.filter2d(x, wy, wx, fuse=0)
+            torch.cuda.synchronize()
+            for k in range(2):
+                em, en = _expect(imgs[k], wy, wx)
+                assert np.array_equal(mx[k].cpu().numpy(), em) and np.array_equal(mn[k].cpu().numpy(), en)
+    assert mmf.device_status() == 0
+
+
 @pytest.mark.parametrize("dtype", [np.uint8, np.int16])
 def test_2d_fused_odd_width_unpaired(mmf, dtype):
     """Odd output widths and offset views take the one-column-per-thread
