@@ -458,9 +458,9 @@ mmf_status mmf_server_stats(mmf_server *server, int reset, mmf_server_stats_t *o
  * at most MMF_NOALLOC_MAX_ITEMS work items.  Larger requests, and lengths
  * whose sum would overflow 64-bit positions, return MMF_EINVAL.
  *
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  Every call reuses the same array and clears its counters itself;
+ * The first call on a device also looks up the array's device address (once
+ * per device, with that device current).  Every call reuses the same array
+ * and clears its counters itself;
  * calls are serialised on the host, but calls that overlap on the GPU (two
  * unordered streams) race on the array and give wrong results: order them on
  * one stream. */

@@ -178,9 +178,9 @@ extern "C" mmf_status mmf_filter1d_batched_noalloc(const void *d_in, const int64
     if (ctx.device < 0 || ctx.device >= kMaxDevices)
         return set_error(MMF_EINVAL, "device ordinal %d out of range", ctx.device);
     // Set-up once per device, with that device current: the device address of
-    // the table array.  (The first call on a device does this; make it before
-    // any stream capture.)  It runs under the call's lock, so a thread that
-    // finds the set-up done also sees the address.
+    // the table array (the first call on a device does this).  It runs under
+    // the call's lock, so a thread that finds the set-up done also sees the
+    // address.
     DevAddr &da = g_noalloc_addr[ctx.device];
     if (!da.ready) {
         void *p = nullptr;
