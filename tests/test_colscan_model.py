@@ -93,3 +93,28 @@ def test_column_pass_matches_the_definition():
             gm = _column_blocks(col, wy, max, -np.inf)
             gn = _column_blocks(col, wy, min, np.inf)
             assert np.array_equal(gm, em) and np.array_equal(gn, en), (wy, H)
+
+
+def test_row_pass_as_one_series_over_stacked_rows():
+    """The two-pass 2D filter's row pass reads all rows of all images as one
+    series (rows `pitch` apart, images stacked): the 1D window starting at
+    stream position r*pitch + x is row r's window at column x for x < W-wx+1;
+    windows past that straddle two rows or a row's padding and are not used.
+    Checked with the oracle's own 1D and 2D definitions, padding filled with
+    extreme values so that a window reaching into it would show."""
+    rng = np.random.default_rng(9)
+    for nimg, H, W, pitch, wx in ((2, 5, 17, 17, 4), (3, 4, 20, 23, 7), (1, 6, 9, 16, 9), (2, 3, 33, 40, 1),
+                                  (1, 1, 12, 12, 12)):
+        imgs = synth.random_walk(nimg * H * W, seed=wx + W, dtype=np.float32).reshape(nimg, H, W)
+        buf = np.empty((nimg * H, pitch), np.float32)
+        buf[:, W:] = rng.choice([-1e30, 1e30], size=(nimg * H, pitch - W))
+        buf[:, :W] = imgs.reshape(nimg * H, W)
+        stream = buf.reshape(-1)[:(nimg * H - 1) * pitch + W]
+        smax, smin = oracle.bf1d(stream, wx)
+        Wo = W - wx + 1
+        for k in range(nimg):
+            em, en = oracle.bf2d(imgs[k], 1, wx)
+            for y in range(H):
+                r = k * H + y
+                assert np.array_equal(smax[r * pitch:r * pitch + Wo], em[y]), (nimg, H, W, pitch, wx, k, y)
+                assert np.array_equal(smin[r * pitch:r * pitch + Wo], en[y]), (nimg, H, W, pitch, wx, k, y)
