@@ -1,9 +1,10 @@
 // Separable 2D running max-min filter (Section 1: the 1D filter on rows, then
 // on columns), valid windows: out[y][x] = max over rows y..y+wy-1 and columns
-// x..x+wx-1.  Row pass: the 1D block-scan kernel over strided rows.  Column
-// pass: colscan_kernel (one thread per column).  The row-pass intermediates go
-// to a caller-provided workspace; the fused form computes them in registers
-// inside the column pass (no workspace).
+// x..x+wx-1.  Row pass: the 1D block-scan kernel over all rows read as one
+// series (or row by row when the workspace is too small for the input's
+// pitch).  Column pass: colscan_kernel (one thread per column).  The row-pass
+// intermediates go to a caller-provided workspace; the fused forms (tile,
+// register-streaming, row extremes inside the column pass) need none.
 #include <cstring>
 #include <type_traits>
 
